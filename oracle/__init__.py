@@ -1,0 +1,231 @@
+"""DeepMatching CPU oracle (test infrastructure only).
+
+A plain CPU implementation of the method, written from the paper, that the
+GPU path is checked against.  Only the tests, the smoke check and the bench's
+CPU-baseline leg use it; the library never imports it.
+
+Two builds of one C source (``dm_oracle.c``):
+  * ``prec="f64"`` -- FP64, the paper's order of operations (Algorithm 1).
+  * ``prec="f32"`` -- FP32 canonical mirror: a fixed operation order, own
+    exp/log/pow, compensated 4-child sums; the bit-exact target of the FP32
+    GPU path.
+
+Functions and the passages they follow:
+  descriptors()   Sec. 3.2 "Pixel descriptor"; defaults of Sec. 5.2
+  level0()        Eq. 3-4 (unpooled, unrectified bottom-level maps)
+  pyramid()       Algorithm 1 with Eq. 5-12 and the boundary rule of Sec. 3.2
+  backtrack()     Eq. 13-15 (merge by highest score)
+  reciprocal()    Eq. 16
+  match()         the whole chain
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import platform
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "dm_oracle.c")
+
+DEFAULT_CFG = dict(nu1=1.0, nu2=1.0, nu3=1.0, slope=0.2, mu=0.3, image_scale=255.0, lam=1.4)
+
+
+def _lib_path(prec: str) -> str:
+    return os.path.join(HERE, f"liboracle_{prec}.so")
+
+
+def build(force: bool = False) -> None:
+    """Compile both oracle builds with gcc (no fp contraction; OpenMP)."""
+    for prec, flag in (("f64", "0"), ("f32", "1")):
+        out = _lib_path(prec)
+        if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(SRC):
+            continue
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               f"-DORC_F32={flag}", SRC, "-o", out, "-lm"]
+        if platform.machine() in ("x86_64", "AMD64"):
+            cmd.insert(1, "-mfma")   # hardware fused multiply-add; same results as libm fmaf
+        subprocess.check_call(cmd)
+
+
+_LIBS: dict = {}
+
+
+def _lib(prec: str):
+    if prec not in _LIBS:
+        build()
+        lib = C.CDLL(_lib_path(prec))
+        _LIBS[prec] = lib
+    return _LIBS[prec]
+
+
+def _dtype(prec: str):
+    return np.float32 if prec == "f32" else np.float64
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+@dataclass
+class Geometry:
+    W1: int
+    H1: int
+    W2: int
+    H2: int
+    L: int
+    P0x: int
+    P0y: int
+    Lx: int
+    Ly: int
+    dw: list
+    dh: list
+
+    def npatch(self, level: int) -> int:
+        return self.P0x * self.P0y if level == 0 else self.Lx * self.Ly
+
+
+def geometry(W1: int, H1: int, W2: int, H2: int) -> Geometry:
+    out = np.zeros(5 + 2 * 34, dtype=np.int32)
+    rc = _lib("f64").orc_geometry(W1, H1, W2, H2, _ptr(out))
+    if rc != 0:
+        raise ValueError(f"unsupported sizes {W1}x{H1} / {W2}x{H2}")
+    L = int(out[0])
+    dw = [int(v) for v in out[5:5 + L + 2]]
+    dh = [int(v) for v in out[5 + L + 2:5 + 2 * (L + 2)]]
+    return Geometry(W1, H1, W2, H2, L, int(out[1]), int(out[2]), int(out[3]), int(out[4]), dw, dh)
+
+
+def descriptors(img: np.ndarray, prec: str = "f64", **cfg) -> np.ndarray:
+    c = dict(DEFAULT_CFG, **cfg)
+    img = np.ascontiguousarray(img, dtype=np.float32)
+    H, W = img.shape
+    out = np.zeros((H, W, 9), dtype=_dtype(prec))
+    arr = np.array([c["nu1"], c["nu2"], c["nu3"], c["slope"], c["mu"], c["image_scale"]], dtype=np.float64)
+    rc = _lib(prec).orc_descriptors(_ptr(img), W, H, _ptr(arr), _ptr(out))
+    if rc != 0:
+        raise ValueError("descriptor oracle failed")
+    return out
+
+
+def level0(d1: np.ndarray, d2: np.ndarray, prec: str = "f64", p0: int = 0, p1: int | None = None) -> np.ndarray:
+    dt = _dtype(prec)
+    d1 = np.ascontiguousarray(d1, dtype=dt)
+    d2 = np.ascontiguousarray(d2, dtype=dt)
+    H1, W1, _ = d1.shape
+    H2, W2, _ = d2.shape
+    g = geometry(W1, H1, W2, H2)
+    if p1 is None:
+        p1 = g.P0x * g.P0y
+    out = np.zeros((p1 - p0, H2, W2), dtype=dt)
+    rc = _lib(prec).orc_level0(_ptr(d1), W1, H1, _ptr(d2), W2, H2, p0, p1, _ptr(out))
+    if rc != 0:
+        raise ValueError("level0 oracle failed")
+    return out
+
+
+@dataclass
+class Pyramid:
+    geom: Geometry
+    prec: str
+    pooled: list = field(default_factory=list)   # l = 0..L-1: [npatch(l)][dh[l+1]][dw[l+1]]
+    argmax: list = field(default_factory=list)   # same shapes, uint8 codes (my+1)*3 + (mx+1)
+    top: np.ndarray | None = None                # [npatch(L)][dh[L]][dw[L]]
+    valid: list = field(default_factory=list)    # l = 0..L: [npatch(l)] uint8
+
+
+def pyramid(d1: np.ndarray, d2: np.ndarray, prec: str = "f64", lam: float = DEFAULT_CFG["lam"]) -> Pyramid:
+    dt = _dtype(prec)
+    d1 = np.ascontiguousarray(d1, dtype=dt)
+    d2 = np.ascontiguousarray(d2, dtype=dt)
+    H1, W1, _ = d1.shape
+    H2, W2, _ = d2.shape
+    g = geometry(W1, H1, W2, H2)
+    pyr = Pyramid(g, prec)
+    for l in range(g.L):
+        shape = (g.npatch(l), g.dh[l + 1], g.dw[l + 1])
+        pyr.pooled.append(np.zeros(shape, dtype=dt))
+        pyr.argmax.append(np.zeros(shape, dtype=np.uint8))
+    pyr.top = np.zeros((g.npatch(g.L), g.dh[g.L], g.dw[g.L]), dtype=dt)
+    pyr.valid = [np.zeros(g.npatch(l), dtype=np.uint8) for l in range(g.L + 1)]
+    pp = (C.c_void_p * g.L)(*[a.ctypes.data for a in pyr.pooled])
+    aa = (C.c_void_p * g.L)(*[a.ctypes.data for a in pyr.argmax])
+    vv = (C.c_void_p * (g.L + 1))(*[a.ctypes.data for a in pyr.valid])
+    lib = _lib(prec)
+    lib.orc_pyramid.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_double,
+                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    rc = lib.orc_pyramid(_ptr(d1), W1, H1, _ptr(d2), W2, H2, float(lam), pp, aa, _ptr(pyr.top), vv)
+    if rc != 0:
+        raise ValueError("pyramid oracle failed")
+    return pyr
+
+
+@dataclass
+class Backtrack:
+    bestP_s: np.ndarray    # [P0] best score of each atomic patch (-inf: none)
+    bestP_i: np.ndarray    # [P0] its pixel index ty*W2 + tx (-1: none)
+    bestQ_s: np.ndarray    # [cells] best score per 4x4 cell of I'
+    bestQ_i: np.ndarray    # [cells] its (patch*16 + offset in cell)
+    leaf: np.ndarray | None  # [P0][H2][W2] merged atomic scores (optional)
+    reached: np.ndarray    # [L+1] distinct tuples per level
+
+
+def backtrack(pyr: Pyramid, dense_leaf: bool = False) -> Backtrack:
+    g = pyr.geom
+    dt = _dtype(pyr.prec)
+    n0 = g.npatch(0)
+    ncell = ((g.W2 + 3) // 4) * ((g.H2 + 3) // 4)
+    bt = Backtrack(np.zeros(n0, dt), np.zeros(n0, np.int64), np.zeros(ncell, dt), np.zeros(ncell, np.int64),
+                   np.zeros((n0, g.H2, g.W2), dt) if dense_leaf else None, np.zeros(g.L + 1, np.int64))
+    pp = (C.c_void_p * g.L)(*[a.ctypes.data for a in pyr.pooled])
+    aa = (C.c_void_p * g.L)(*[a.ctypes.data for a in pyr.argmax])
+    vv = (C.c_void_p * (g.L + 1))(*[a.ctypes.data for a in pyr.valid])
+    lib = _lib(pyr.prec)
+    lib.orc_backtrack.argtypes = [C.c_int] * 4 + [C.c_void_p] * 10
+    rc = lib.orc_backtrack(g.W1, g.H1, g.W2, g.H2, pp, aa, _ptr(pyr.top), vv,
+                           _ptr(bt.bestP_s), _ptr(bt.bestP_i), _ptr(bt.bestQ_s), _ptr(bt.bestQ_i),
+                           _ptr(bt.leaf) if dense_leaf else None, _ptr(bt.reached))
+    if rc != 0:
+        raise ValueError("backtrack oracle failed")
+    return bt
+
+
+def reciprocal(pyr: Pyramid, bt: Backtrack) -> np.ndarray:
+    """Rows (x1, y1, x2, y2, score), one per surviving atomic patch, in patch order."""
+    g = pyr.geom
+    out = np.zeros((g.npatch(0), 5), dtype=np.float64)
+    lib = _lib(pyr.prec)
+    lib.orc_reciprocal.argtypes = [C.c_int] * 4 + [C.c_void_p] * 5
+    n = lib.orc_reciprocal(g.W1, g.H1, g.W2, g.H2, _ptr(bt.bestP_s), _ptr(bt.bestP_i),
+                           _ptr(bt.bestQ_s), _ptr(bt.bestQ_i), _ptr(out))
+    if n < 0:
+        raise ValueError("reciprocal oracle failed")
+    return out[:n]
+
+
+def match(img1: np.ndarray, img2: np.ndarray, prec: str = "f64", **cfg):
+    """Descriptors -> pyramid -> backtracking -> reciprocal matches."""
+    c = dict(DEFAULT_CFG, **cfg)
+    lam = c.pop("lam")
+    d1 = descriptors(img1, prec, **c)
+    d2 = descriptors(img2, prec, **c)
+    pyr = pyramid(d1, d2, prec, lam)
+    bt = backtrack(pyr)
+    return reciprocal(pyr, bt), pyr, bt
+
+
+def pow_r(x: float, lam: float, prec: str = "f32") -> float:
+    lib = _lib(prec)
+    lib.orc_pow_r.restype = C.c_double
+    lib.orc_pow_r.argtypes = [C.c_double, C.c_double]
+    return lib.orc_pow_r(float(x), float(lam))
+
+
+def exp_r(z: float, prec: str = "f32") -> float:
+    lib = _lib(prec)
+    lib.orc_exp_r.restype = C.c_double
+    lib.orc_exp_r.argtypes = [C.c_double]
+    return lib.orc_exp_r(float(z))

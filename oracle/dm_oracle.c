@@ -1,0 +1,603 @@
+/*
+ * DeepMatching CPU oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, deliberately unoptimised CPU implementation of the hot path
+ * of DeepMatching (Revaud et al., "DeepMatching: Hierarchical Deformable Dense
+ * Matching"), written from the paper: pixel descriptors (Sec. 3.2), bottom
+ * level correlation (Eq. 3-4), the bottom-up pyramid (Eq. 5-12 and
+ * Algorithm 1, boundary rule of Sec. 3.2), top-down backtracking with merging
+ * (Eq. 13-15) and reciprocal verification (Eq. 16).
+ *
+ * Only the test-suite, the smoke check and the CPU-baseline leg of the bench
+ * may load this file's library.  It shares no source with the CUDA path.
+ *
+ * The file is compiled twice:
+ *   ORC_F32 = 0 : FP64, the method in the paper's own order (Algorithm 1
+ *                 rectifies every map value, then max-pools).
+ *   ORC_F32 = 1 : FP32 "canonical mirror": the same method with one fixed
+ *                 operation order (stated at each step), own exp/log/pow
+ *                 routines, max-pooling on the raw aggregate followed by the
+ *                 power (equal to the paper's order because x -> x^lambda is
+ *                 increasing on [0,1]), and compensated 4-child sums.  It is
+ *                 the bit-exact target of the FP32 GPU path.
+ *
+ * Readings of the paper where it is silent or ambiguous (numbered as in the
+ * design notes):
+ *   c1  Gaussian "radius" nu = standard deviation; taps on [-ceil(3nu), ceil(3nu)],
+ *       renormalised to sum 1; replicate border; nu = 0 is the identity.
+ *   c2  gradient = central differences, replicate border.
+ *   c3  images come in [0,1] and are multiplied by image_scale (255).
+ *   c4  8 orientations k*pi/4, k = 0..7; channel = max(0, <g, dir_k>).
+ *   c5  mu is appended first, then the 9-vector is L2-normalised.
+ *   c6  image-2 window at pixel t covers [t-2, t+1]^2; zero descriptor outside.
+ *   c7  atomic centres 4k+2 <= W-1.
+ *   c8  a level-N patch exists if at least one child exists; average over valid
+ *       children (weight 1/n_valid).
+ *   c9  Theta_i has radius N/8 (a 3x3 max on the child's subsampled grid).
+ *   c10 child i is sampled at q + o_i (sign of Eq. 6 and Eq. 13).
+ *   c11 map domain at level l is ceil(W'/2^l) x ceil(H'/2^l); pooling only over
+ *       in-domain positions; a child sample outside the domain contributes 0.
+ *   c13 argmax = first strict maximum, scan order m_y = -1..1 then m_x = -1..1;
+ *       ties in BestAt/BestAt': higher score, then lower index.
+ *   c14 L = min{l : 4*2^l >= max(W,H)} (image 1); entries = all top positions.
+ *   c15 path score = top value + pooled values along the path, summed top-down.
+ *   c17 BestAt / BestAt' over aligned 4x4 cells (the atomic patch in I, the cell
+ *       floor(t/4) in I'); a tuple survives iff it is the best of both.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef ORC_F32
+#error "compile with -DORC_F32=0 (FP64) or -DORC_F32=1 (FP32 canonical mirror)"
+#endif
+
+#if ORC_F32
+typedef float real;
+#define RFMA(a, b, c) fmaf((a), (b), (c))
+#define RSQRT(x) sqrtf(x)
+#define RNEG_INF (-INFINITY)
+#else
+typedef double real;
+#define RFMA(a, b, c) fma((a), (b), (c))
+#define RSQRT(x) sqrt(x)
+#define RNEG_INF (-INFINITY)
+#endif
+
+#define ORC_MAXL 30
+
+int orc_real_size(void) { return (int)sizeof(real); }
+
+/* ------------------------------------------------------------------------- */
+/* Geometry (Sec. 3.2: G_4, Eq. 7 lattices, Algorithm 1 loop bound)          */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    int W1, H1, W2, H2;
+    int L;            /* number of aggregation iterations (c14) */
+    int P0x, P0y;     /* atomic grid G_4: centres 4k+2 (c7) */
+    int Lx, Ly;       /* lattice 4Z^2 inside image 1, patches of levels >= 1 */
+    int dw[ORC_MAXL + 2], dh[ORC_MAXL + 2]; /* map domain of level l (c11) */
+} geom;
+
+static int ceil_half(int v) { return (v + 1) / 2; }
+
+static int make_geom(int W1, int H1, int W2, int H2, geom* g) {
+    memset(g, 0, sizeof(*g));
+    if (W1 < 4 || H1 < 4 || W2 < 1 || H2 < 1) return -1;
+    g->W1 = W1; g->H1 = H1; g->W2 = W2; g->H2 = H2;
+    int mx = W1 > H1 ? W1 : H1;
+    int L = 0;
+    long N = 4;
+    while (N < mx) { N *= 2; L++; }
+    if (L < 1 || L > ORC_MAXL) return -1;
+    g->L = L;
+    g->P0x = (W1 - 3) / 4 + 1;
+    g->P0y = (H1 - 3) / 4 + 1;
+    g->Lx = (W1 - 1) / 4 + 1;
+    g->Ly = (H1 - 1) / 4 + 1;
+    g->dw[0] = W2; g->dh[0] = H2;
+    for (int l = 1; l <= L + 1; l++) { g->dw[l] = ceil_half(g->dw[l - 1]); g->dh[l] = ceil_half(g->dh[l - 1]); }
+    return 0;
+}
+
+/* out = [L, P0x, P0y, Lx, Ly, dw[0..L+1], dh[0..L+1]] ; returns 0 or -1 */
+int orc_geometry(int W1, int H1, int W2, int H2, int* out) {
+    geom g;
+    if (make_geom(W1, H1, W2, H2, &g)) return -1;
+    out[0] = g.L; out[1] = g.P0x; out[2] = g.P0y; out[3] = g.Lx; out[4] = g.Ly;
+    for (int l = 0; l <= g.L + 1; l++) { out[5 + l] = g.dw[l]; out[5 + (g.L + 2) + l] = g.dh[l]; }
+    return 0;
+}
+
+static int npatch(const geom* g, int l) { return l == 0 ? g->P0x * g->P0y : g->Lx * g->Ly; }
+
+/* Child i of patch (ix, iy) at level l >= 1 (Eq. 5: offset (N/4) o_i = 2^l o_i).
+ * o_0 = (-1,-1), o_1 = (-1,+1), o_2 = (+1,-1), o_3 = (+1,+1), as (x, y).
+ * Returns the child's index at level l-1, or -1 if it lies outside the grid. */
+static int child_index(const geom* g, int l, int ix, int iy, int i) {
+    int ox = (i >= 2) ? 1 : -1, oy = (i & 1) ? 1 : -1;
+    int cx, cy;
+    if (l == 1) {                          /* centre 4ix + 2ox -> atomic index (c - 2)/4 */
+        cx = ix + (ox - 1) / 2; cy = iy + (oy - 1) / 2;
+        if (cx < 0 || cy < 0 || cx >= g->P0x || cy >= g->P0y) return -1;
+        return cy * g->P0x + cx;
+    }
+    int s = 1 << (l - 2);                 /* centre 4ix + 2^l ox -> lattice index ix + 2^(l-2) ox */
+    cx = ix + ox * s; cy = iy + oy * s;
+    if (cx < 0 || cy < 0 || cx >= g->Lx || cy >= g->Ly) return -1;
+    return cy * g->Lx + cx;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Elementary functions.                                                      */
+/* FP64: the C library.  FP32 mirror: own routines with a fixed sequence of   */
+/* correctly rounded float operations, so that an independent implementation  */
+/* following the same recipe reproduces them bit for bit.                     */
+/* ------------------------------------------------------------------------- */
+#if ORC_F32
+static float f_from_bits(uint32_t u) { float f; memcpy(&f, &u, 4); return f; }
+static uint32_t bits_from_f(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
+
+/* 2^n for n in [-126, 127] built from the exponent field. */
+static float pow2i(int n) { return f_from_bits((uint32_t)(n + 127) << 23); }
+
+/* e^z for z <= 0 (clamped at -87).  Cody-Waite reduction z = n ln2 + r with
+ * ln2 split into a 16-bit head (exact products n*head) and a tail, then the
+ * degree-7 Taylor polynomial of e^r, |r| <= ln2/2, in Horner form. */
+static float orc_expf(float z) {
+    if (z < -87.0f) z = -87.0f;
+    float n = rintf(z * 1.44269504f);
+    float r = fmaf(n, -0.693145751953125f, z);
+    r = fmaf(n, -1.42860682e-06f, r);
+    float p = 1.98412698e-04f;              /* 1/7! */
+    p = fmaf(p, r, 1.38888889e-03f);        /* 1/6! */
+    p = fmaf(p, r, 8.33333333e-03f);        /* 1/5! */
+    p = fmaf(p, r, 4.16666667e-02f);        /* 1/4! */
+    p = fmaf(p, r, 1.66666667e-01f);        /* 1/3! */
+    p = fmaf(p, r, 0.5f);
+    p = fmaf(p, r, 1.0f);
+    p = fmaf(p, r, 1.0f);
+    return p * pow2i((int)n);
+}
+
+/* x^lam for x in [0, 1], lam > 0.  x = m 2^e with m in [sqrt(1/2), sqrt(2)];
+ * log2 m = (2/ln2) atanh(f), f = (m-1)/(m+1), odd series to f^13;
+ * lam*e is split exactly (head + fma residual); 2^g, |g| <= 1/2, by the
+ * degree-7 Taylor polynomial of e^(g ln2). */
+static float orc_powf(float x, float lam) {
+    if (!(x > 0.0f)) return 0.0f;
+    int eadj = 0;
+    if (x < 1.17549435e-38f) { x = x * 16777216.0f; eadj = -24; }   /* subnormal input */
+    uint32_t b = bits_from_f(x);
+    int e = (int)((b >> 23) & 0xffu) - 127 + eadj;
+    float m = f_from_bits((b & 0x7fffffu) | 0x3f800000u);
+    if (m > 1.41421356f) { m = m * 0.5f; e = e + 1; }
+    float f = (m - 1.0f) / (m + 1.0f);
+    float f2 = f * f;
+    float s = 7.69230769e-02f;               /* 1/13 */
+    s = fmaf(s, f2, 9.09090909e-02f);       /* 1/11 */
+    s = fmaf(s, f2, 1.11111111e-01f);       /* 1/9 */
+    s = fmaf(s, f2, 1.42857143e-01f);       /* 1/7 */
+    s = fmaf(s, f2, 2.00000000e-01f);       /* 1/5 */
+    s = fmaf(s, f2, 3.33333333e-01f);       /* 1/3 */
+    s = fmaf(s, f2, 1.0f);
+    float l2m = (2.88539008f * f) * s;      /* 2/ln2 * f * s */
+    float fe = (float)e;
+    float a = lam * fe;
+    float aerr = fmaf(lam, fe, -a);
+    float n1 = rintf(a);
+    float g = ((a - n1) + aerr) + lam * l2m;
+    float n2 = rintf(g);
+    g = g - n2;
+    float p = 1.52527338e-05f;               /* ln2^7/7! */
+    p = fmaf(p, g, 1.54035304e-04f);        /* ln2^6/6! */
+    p = fmaf(p, g, 1.33335581e-03f);        /* ln2^5/5! */
+    p = fmaf(p, g, 9.61812911e-03f);        /* ln2^4/4! */
+    p = fmaf(p, g, 5.55041087e-02f);        /* ln2^3/3! */
+    p = fmaf(p, g, 2.40226507e-01f);        /* ln2^2/2! */
+    p = fmaf(p, g, 6.93147181e-01f);        /* ln2 */
+    p = fmaf(p, g, 1.0f);
+    int nt = (int)n1 + (int)n2;
+    if (nt < -149 - 2) return 0.0f;
+    int na = nt / 2, nb = nt - na;
+    return (p * pow2i(na)) * pow2i(nb);
+}
+#define REXP(z) orc_expf(z)
+#define RPOW(x, l) orc_powf((x), (l))
+#else
+#define REXP(z) exp(z)
+#define RPOW(x, l) pow((x), (l))
+#endif
+
+/* exported for the accuracy pin of the FP32 routines */
+double orc_pow_r(double x, double lam) { return (double)RPOW((real)x, (real)lam); }
+double orc_exp_r(double z) { return (double)REXP((real)z); }
+
+/* ------------------------------------------------------------------------- */
+/* Pixel descriptors (Sec. 3.2 "Pixel descriptor"; parameters of Sec. 5.2)    */
+/* ------------------------------------------------------------------------- */
+
+/* Gaussian taps of standard deviation nu (reading c1), computed in double and
+ * rounded once to the working precision.  Returns the radius R (0 = identity). */
+static int gauss_taps(double nu, real* w, int cap) {
+    if (!(nu > 0.0)) { w[0] = (real)1.0; return 0; }
+    int R = (int)ceil(3.0 * nu);
+    if (2 * R + 1 > cap) R = (cap - 1) / 2;
+    double t[65], sum = 0.0;
+    for (int j = -R; j <= R; j++) { t[j + R] = exp(-(double)(j * j) / (2.0 * nu * nu)); sum += t[j + R]; }
+    for (int j = 0; j <= 2 * R; j++) w[j] = (real)(t[j] / sum);
+    return R;
+}
+
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* Separable smoothing of nch interleaved channels: horizontal pass, then
+ * vertical; each output is acc = fma(w_j, in_j, acc) for j = -R..R from 0. */
+static void smooth(real* buf, int W, int H, int nch, int ch0, int chn, const real* w, int R, real* tmp) {
+    if (R == 0) return;
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++)
+            for (int c = ch0; c < ch0 + chn; c++) {
+                real acc = 0;
+                for (int j = -R; j <= R; j++)
+                    acc = RFMA(w[j + R], buf[((size_t)y * W + clampi(x + j, 0, W - 1)) * nch + c], acc);
+                tmp[((size_t)y * W + x) * nch + c] = acc;
+            }
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++)
+            for (int c = ch0; c < ch0 + chn; c++) {
+                real acc = 0;
+                for (int j = -R; j <= R; j++)
+                    acc = RFMA(w[j + R], tmp[((size_t)clampi(y + j, 0, H - 1) * W + x) * nch + c], acc);
+                buf[((size_t)y * W + x) * nch + c] = acc;
+            }
+}
+
+/* cfg = {nu1, nu2, nu3, slope, mu, image_scale}.  out: [H][W][9]. */
+int orc_descriptors(const float* img, int W, int H, const double* cfg, real* out) {
+    if (W < 1 || H < 1) return -1;
+    const real slope = (real)cfg[3], mu = (real)cfg[4], scale = (real)cfg[5];
+    real w1[65], w2[65], w3[65];
+    int R1 = gauss_taps(cfg[0], w1, 65), R2 = gauss_taps(cfg[1], w2, 65), R3 = gauss_taps(cfg[2], w3, 65);
+    size_t n = (size_t)W * H;
+    real* s = (real*)malloc(n * sizeof(real));
+    real* o = (real*)malloc(n * 8 * sizeof(real));
+    real* tmp = (real*)malloc(n * 8 * sizeof(real));
+    if (!s || !o || !tmp) { free(s); free(o); free(tmp); return -2; }
+    for (size_t i = 0; i < n; i++) s[i] = (real)img[i] * scale;          /* c3 */
+    smooth(s, W, H, 1, 0, 1, w1, R1, tmp);                                 /* nu1 */
+    /* 8 orientations (c4): exact direction table, r = sqrt(1/2) */
+    const real r = (real)0.70710678118654752;
+    const real dc[8] = {1, r, 0, -r, -1, -r, 0, r};
+    const real ds[8] = {0, r, 1, r, 0, -r, -1, -r};
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            real gx = (s[(size_t)y * W + clampi(x + 1, 0, W - 1)] - s[(size_t)y * W + clampi(x - 1, 0, W - 1)]) * (real)0.5;
+            real gy = (s[(size_t)clampi(y + 1, 0, H - 1) * W + x] - s[(size_t)clampi(y - 1, 0, H - 1) * W + x]) * (real)0.5;
+            for (int k = 0; k < 8; k++) {
+                real v = RFMA(gx, dc[k], gy * ds[k]);
+                o[((size_t)y * W + x) * 8 + k] = v > 0 ? v : (real)0;
+            }
+        }
+    smooth(o, W, H, 8, 0, 8, w2, R2, tmp);                                 /* nu2 */
+    for (size_t i = 0; i < n * 8; i++) {                                   /* sigmoid cap */
+        real t = slope * o[i];
+        real e = REXP(-t);
+        real d = (real)1 + e;
+        o[i] = (real)2 / d - (real)1;
+    }
+    smooth(o, W, H, 8, 0, 8, w3, R3, tmp);                                 /* nu3 */
+    for (size_t i = 0; i < n; i++) {                                       /* [8 channels, mu] / norm (c5) */
+        real acc = 0;
+        for (int k = 0; k < 8; k++) acc = RFMA(o[i * 8 + k], o[i * 8 + k], acc);
+        acc = RFMA(mu, mu, acc);
+        real nrm = RSQRT(acc);
+        for (int k = 0; k < 8; k++) out[i * 9 + k] = o[i * 8 + k] / nrm;
+        out[i * 9 + 8] = mu / nrm;
+    }
+    free(s); free(o); free(tmp);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Bottom-level correlation (Eq. 3-4)                                         */
+/* ------------------------------------------------------------------------- */
+
+/* sim of the atomic patch p (grid index) of I with the 4x4 window of I' at
+ * pixel (tx, ty): (1/16) sum over the 16 pixels of the 9-D dot products.
+ * Window convention (c6): centre 2 <-> pixels 0..3, i.e. [t-2, t+1]^2;
+ * descriptors of I' are zero outside the image, and so are those of the
+ * pixels of a partial atomic patch that fall outside I (c7).
+ * Order: dx = 0..3 (outer), channel c = 0..8, dy = 0..3 (inner), one fma per
+ * term from acc = 0, then one multiplication by 1/16. */
+static real corr0(const real* d1, int W1, int H1, const real* d2, int W2, int H2, int px, int py, int tx, int ty) {
+    real acc = 0;
+    for (int dx = 0; dx < 4; dx++)
+        for (int c = 0; c < 9; c++)
+            for (int dy = 0; dy < 4; dy++) {
+                int x2 = tx - 2 + dx, y2 = ty - 2 + dy;
+                int x1 = px - 2 + dx, y1 = py - 2 + dy;
+                if (x2 < 0 || y2 < 0 || x2 >= W2 || y2 >= H2) continue;   /* zero term */
+                if (x1 >= W1 || y1 >= H1) continue;   /* partial atomic patch (c7): zero term */
+                real a = d1[((size_t)y1 * W1 + x1) * 9 + c];
+                real b = d2[((size_t)y2 * W2 + x2) * 9 + c];
+                acc = RFMA(a, b, acc);
+            }
+    return acc * (real)0.0625;
+}
+
+/* Unpooled, unrectified C_0 for patches [p0, p1): out [p1-p0][H2][W2]. */
+int orc_level0(const real* d1, int W1, int H1, const real* d2, int W2, int H2, int p0, int p1, real* out) {
+    geom g;
+    if (make_geom(W1, H1, W2, H2, &g)) return -1;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int p = p0; p < p1; p++) {
+        int px = 4 * (p % g.P0x) + 2, py = 4 * (p / g.P0x) + 2;
+        real* o = out + (size_t)(p - p0) * W2 * H2;
+        for (int ty = 0; ty < H2; ty++)
+            for (int tx = 0; tx < W2; tx++) o[(size_t)ty * W2 + tx] = corr0(d1, W1, H1, d2, W2, H2, px, py, tx, ty);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Max-pooling + subsampling (Eq. 8-9) of one map: dst(r) = max over the      */
+/* in-domain positions 2r+m, m in {-1,0,1}^2; argmax code (my+1)*3 + (mx+1).  */
+/* ------------------------------------------------------------------------- */
+static void pool_map(const real* src, int sw, int sh, real* dst, uint8_t* am, int dw, int dh, int rectify_after, real lam) {
+    for (int ry = 0; ry < dh; ry++)
+        for (int rx = 0; rx < dw; rx++) {
+            real best = RNEG_INF;
+            int code = 4;
+            for (int my = -1; my <= 1; my++)
+                for (int mx = -1; mx <= 1; mx++) {
+                    int x = 2 * rx + mx, y = 2 * ry + my;
+                    if (x < 0 || y < 0 || x >= sw || y >= sh) continue;
+                    real v = src[(size_t)y * sw + x];
+                    if (v > best) { best = v; code = (my + 1) * 3 + (mx + 1); }
+                }
+            dst[(size_t)ry * dw + rx] = rectify_after ? RPOW(best, lam) : best;
+            am[(size_t)ry * dw + rx] = (uint8_t)code;
+        }
+}
+
+/* ------------------------------------------------------------------------- */
+/* The multi-level correlation pyramid (Algorithm 1, Eq. 12, boundary rule)   */
+/*                                                                            */
+/* pooled[l] : [npatch(l)][dh[l+1]][dw[l+1]]  = (S o P)(C_l), l = 0..L-1      */
+/* amax[l]   : same shape, argmax codes                                       */
+/* top       : [npatch(L)][dh[L]][dw[L]]       = C_L                          */
+/* valid[l]  : [npatch(l)] patch membership of G_{4*2^l}, l = 0..L            */
+/* ------------------------------------------------------------------------- */
+int orc_pyramid(const real* d1, int W1, int H1, const real* d2, int W2, int H2, double lambda,
+                real** pooled, uint8_t** amax, real* top, uint8_t** valid) {
+    geom g;
+    if (make_geom(W1, H1, W2, H2, &g)) return -1;
+    const real lam = (real)lambda;
+    const int L = g.L;
+
+    /* level 0: correlate, rectify, pool (FP64: Algorithm 1 order; FP32: pool then power) */
+    int n0 = npatch(&g, 0);
+    memset(valid[0], 1, (size_t)n0);
+#pragma omp parallel
+    {
+        real* map = (real*)malloc((size_t)W2 * H2 * sizeof(real));
+#pragma omp for schedule(dynamic, 1)
+        for (int p = 0; p < n0; p++) {
+            int px = 4 * (p % g.P0x) + 2, py = 4 * (p / g.P0x) + 2;
+            for (int ty = 0; ty < H2; ty++)
+                for (int tx = 0; tx < W2; tx++) {
+                    real c = corr0(d1, W1, H1, d2, W2, H2, px, py, tx, ty);
+                    map[(size_t)ty * W2 + tx] = ORC_F32 ? c : RPOW(c, lam);
+                }
+            size_t off = (size_t)p * g.dw[1] * g.dh[1];
+            pool_map(map, W2, H2, pooled[0] + off, amax[0] + off, g.dw[1], g.dh[1], ORC_F32, lam);
+        }
+        free(map);
+    }
+
+    /* levels 1..L: shift-average of the children's pooled maps, rectify, pool */
+    for (int l = 1; l <= L; l++) {
+        const int np = npatch(&g, l);
+        const int mw = g.dw[l], mh = g.dh[l];
+        const int cw = g.dw[l], ch = g.dh[l];      /* child pooled maps live on the same domain */
+        for (int p = 0; p < np; p++) {
+            int any = 0;
+            for (int i = 0; i < 4; i++) {
+                int c = child_index(&g, l, p % g.Lx, p / g.Lx, i);
+                if (c >= 0 && valid[l - 1][c]) any = 1;
+            }
+            valid[l][p] = (uint8_t)any;
+        }
+#pragma omp parallel
+        {
+            real* map = (real*)malloc((size_t)mw * mh * sizeof(real));
+#pragma omp for schedule(dynamic, 1)
+            for (int p = 0; p < np; p++) {
+                if (!valid[l][p]) continue;
+                int ci[4], n = 0;
+                for (int i = 0; i < 4; i++) {
+                    int c = child_index(&g, l, p % g.Lx, p / g.Lx, i);
+                    ci[i] = (c >= 0 && valid[l - 1][c]) ? c : -1;
+                    if (ci[i] >= 0) n++;
+                }
+                for (int qy = 0; qy < mh; qy++)
+                    for (int qx = 0; qx < mw; qx++) {
+#if ORC_F32
+                        /* compensated sum (Knuth TwoSum) over valid children, i = 0..3 */
+                        float s = 0.0f, comp = 0.0f;
+#else
+                        double s = 0.0;
+#endif
+                        for (int i = 0; i < 4; i++) {
+                            if (ci[i] < 0) continue;
+                            int ox = (i >= 2) ? 1 : -1, oy = (i & 1) ? 1 : -1;
+                            int rx = qx + ox, ry = qy + oy;
+                            real v = 0;
+                            if (rx >= 0 && ry >= 0 && rx < cw && ry < ch)
+                                v = pooled[l - 1][(size_t)ci[i] * cw * ch + (size_t)ry * cw + rx];
+#if ORC_F32
+                            float t = s + v;
+                            float bp = t - s;
+                            float err = (s - (t - bp)) + (v - bp);
+                            s = t;
+                            comp = comp + err;
+#else
+                            s += v;
+#endif
+                        }
+#if ORC_F32
+                        float a = (s + comp) / (float)n;
+                        map[(size_t)qy * mw + qx] = a;                      /* rectified after pooling */
+#else
+                        map[(size_t)qy * mw + qx] = RPOW(s / (double)n, lam);
+#endif
+                    }
+                if (l < L) {
+                    size_t off = (size_t)p * g.dw[l + 1] * g.dh[l + 1];
+                    pool_map(map, mw, mh, pooled[l] + off, amax[l] + off, g.dw[l + 1], g.dh[l + 1], ORC_F32, lam);
+                } else {
+                    real* dst = top + (size_t)p * mw * mh;
+                    for (size_t k = 0; k < (size_t)mw * mh; k++) dst[k] = ORC_F32 ? RPOW(map[k], lam) : map[k];
+                }
+            }
+            free(map);
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Backtracking with merging (Eq. 13-15) and reciprocal verification (Eq. 16) */
+/*                                                                            */
+/* The tuple set M starts as every top-level position of every valid patch    */
+/* with its score C_L.  One application of B maps each tuple (l, p, q, s) to  */
+/* its children (l-1, p_i, t_i = 2(q+o_i)+m_i, s + C_{l-1,p_i}(t_i)); tuples   */
+/* equal in (l, p, t) are merged keeping the highest score.  The merged set   */
+/* of one level is held in a dense score array (-inf = absent).               */
+/* At the atomic level the tuples are reduced on the fly into                */
+/*   BestAt(p)   : best tuple of atomic patch p (its own 4x4 cell of I),       */
+/*   BestAt'(c)  : best tuple whose t lies in the 4x4 cell c of I'.            */
+/* leaf (optional, [P0][H2][W2]): the merged atomic scores themselves.        */
+/* reached[l]   : number of distinct tuples at level l (l = 0..L).            */
+/* ------------------------------------------------------------------------- */
+
+static int better(real s, long long idx, real bs, long long bidx) {
+    return s > bs || (s == bs && idx < bidx);
+}
+
+int orc_backtrack(int W1, int H1, int W2, int H2, real** pooled, uint8_t** amax, const real* top, uint8_t** valid,
+                  real* bestP_s, long long* bestP_i, real* bestQ_s, long long* bestQ_i, real* leaf, long long* reached) {
+    geom g;
+    if (make_geom(W1, H1, W2, H2, &g)) return -1;
+    const int L = g.L;
+    const int n0 = npatch(&g, 0);
+    const int CW = (W2 + 3) / 4, CH = (H2 + 3) / 4;
+    for (int p = 0; p < n0; p++) { bestP_s[p] = RNEG_INF; bestP_i[p] = -1; }
+    for (int c = 0; c < CW * CH; c++) { bestQ_s[c] = RNEG_INF; bestQ_i[c] = -1; }
+    if (leaf) for (size_t k = 0; k < (size_t)n0 * W2 * H2; k++) leaf[k] = RNEG_INF;
+    for (int l = 0; l <= L; l++) reached[l] = 0;
+
+    /* current merged set, level L */
+    const int npL = npatch(&g, L);
+    size_t ncur = (size_t)npL * g.dw[L] * g.dh[L];
+    real* cur = (real*)malloc(ncur * sizeof(real));
+    if (!cur) return -2;
+    for (int p = 0; p < npL; p++)
+        for (size_t k = 0; k < (size_t)g.dw[L] * g.dh[L]; k++) {
+            size_t o = (size_t)p * g.dw[L] * g.dh[L] + k;
+            cur[o] = valid[L][p] ? top[o] : RNEG_INF;
+            if (valid[L][p]) reached[L]++;  /* one tuple per (p, q) */
+        }
+
+    for (int l = L; l >= 1; l--) {
+        const int mw = g.dw[l], mh = g.dh[l];           /* domain of the current level's positions q */
+        const int tw = g.dw[l - 1], th = g.dh[l - 1];   /* domain of the children's positions t */
+        const int npc = npatch(&g, l - 1);
+        real* nxt = NULL;
+        if (l - 1 >= 1) {
+            nxt = (real*)malloc((size_t)npc * tw * th * sizeof(real));
+            if (!nxt) { free(cur); return -2; }
+            for (size_t k = 0; k < (size_t)npc * tw * th; k++) nxt[k] = RNEG_INF;
+        }
+        const int np = npatch(&g, l);
+        for (int p = 0; p < np; p++) {
+            if (!valid[l][p]) continue;
+            for (int qy = 0; qy < mh; qy++)
+                for (int qx = 0; qx < mw; qx++) {
+                    real s = cur[(size_t)p * mw * mh + (size_t)qy * mw + qx];
+                    if (s == RNEG_INF) continue;
+                    for (int i = 0; i < 4; i++) {
+                        int c = child_index(&g, l, p % g.Lx, p / g.Lx, i);
+                        if (c < 0 || !valid[l - 1][c]) continue;
+                        int ox = (i >= 2) ? 1 : -1, oy = (i & 1) ? 1 : -1;
+                        int rx = qx + ox, ry = qy + oy;              /* Eq. 13: 2(q + o_i) + m_i */
+                        if (rx < 0 || ry < 0 || rx >= mw || ry >= mh) continue;
+                        size_t ro = (size_t)c * mw * mh + (size_t)ry * mw + rx;
+                        int code = amax[l - 1][ro];
+                        int tx = 2 * rx + (code % 3 - 1), ty = 2 * ry + (code / 3 - 1);
+                        real s2 = s + pooled[l - 1][ro];              /* Eq. 14: s + C_{N/2,p_i}(p'_i) */
+                        if (l - 1 >= 1) {
+                            real* d = &nxt[(size_t)c * tw * th + (size_t)ty * tw + tx];
+                            if (s2 > *d) *d = s2;
+                        } else {
+                            long long tidx = (long long)ty * W2 + tx;
+                            if (leaf) {
+                                real* d = &leaf[(size_t)c * W2 * H2 + tidx];
+                                if (s2 > *d) *d = s2;
+                            }
+                            if (better(s2, tidx, bestP_s[c], bestP_i[c])) { bestP_s[c] = s2; bestP_i[c] = tidx; }
+                            int cell = (ty / 4) * CW + tx / 4;
+                            long long qidx = (long long)c * 16 + (ty % 4) * 4 + (tx % 4);
+                            if (better(s2, qidx, bestQ_s[cell], bestQ_i[cell])) { bestQ_s[cell] = s2; bestQ_i[cell] = qidx; }
+                        }
+                    }
+                }
+        }
+        free(cur);
+        cur = nxt;
+        if (l - 1 >= 1) {
+            long long cnt = 0;
+            for (size_t k = 0; k < (size_t)npc * tw * th; k++) cnt += (cur[k] != RNEG_INF);
+            reached[l - 1] = cnt;
+        }
+    }
+    if (leaf) {
+        long long cnt = 0;
+        for (size_t k = 0; k < (size_t)n0 * W2 * H2; k++) cnt += (leaf[k] != RNEG_INF);
+        reached[0] = cnt;
+    } else {
+        reached[0] = -1;   /* not counted without the dense leaf array */
+    }
+    free(cur);
+    return 0;
+}
+
+/* Reciprocal verification (Eq. 16, reading c17): keep the best tuple of each
+ * atomic patch iff it is also the best tuple of its 4x4 cell of I'.  Output in
+ * patch order: out[k] = {x1, y1, x2, y2, score}.  Returns the count. */
+int orc_reciprocal(int W1, int H1, int W2, int H2, const real* bestP_s, const long long* bestP_i,
+                   const real* bestQ_s, const long long* bestQ_i, double* out) {
+    geom g;
+    if (make_geom(W1, H1, W2, H2, &g)) return -1;
+    (void)bestQ_s;
+    const int CW = (W2 + 3) / 4;
+    int n = 0;
+    for (int p = 0; p < g.P0x * g.P0y; p++) {
+        if (bestP_i[p] < 0) continue;
+        long long t = bestP_i[p];
+        int tx = (int)(t % W2), ty = (int)(t / W2);
+        int cell = (ty / 4) * CW + tx / 4;
+        long long qidx = (long long)p * 16 + (ty % 4) * 4 + (tx % 4);
+        if (bestQ_i[cell] != qidx) continue;
+        out[5 * n + 0] = 4 * (p % g.P0x) + 2;
+        out[5 * n + 1] = 4 * (p / g.P0x) + 2;
+        out[5 * n + 2] = tx;
+        out[5 * n + 3] = ty;
+        out[5 * n + 4] = (double)bestP_s[p];
+        n++;
+    }
+    return n;
+}

@@ -1,0 +1,516 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: brute force
+on tiny inputs, closed forms, invariants, special cases.  Numbering follows the
+pin list in the design notes (P1..P11).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1506_07656_gb300 import synth
+
+
+def _rand_desc(W, H, seed):
+    return synth.random_descriptor_field(W, H, seed)
+
+
+# --------------------------------------------------------------------------- #
+# P1: bottom-level correlation == brute-force 144-term dot products (Eq. 3-4)  #
+# --------------------------------------------------------------------------- #
+@pytest.mark.parametrize("W1,H1,W2,H2", [(13, 10, 9, 11), (12, 8, 12, 8), (7, 5, 3, 2)])
+def test_p1_level0_bruteforce(oracle_mod, W1, H1, W2, H2):
+    d1 = _rand_desc(W1, H1, 1)
+    d2 = _rand_desc(W2, H2, 2)
+    P0x, P0y = (W1 - 3) // 4 + 1, (H1 - 3) // 4 + 1
+    pad = np.zeros((H2 + 3, W2 + 3, 9))
+    pad[2:2 + H2, 2:2 + W2] = d2
+    pad1 = np.zeros((H1 + 4, W1 + 4, 9))                 # partial atomic patches read zeros
+    pad1[:H1, :W1] = d1
+    exp = np.zeros((P0x * P0y, H2, W2))
+    for iy in range(P0y):
+        for ix in range(P0x):
+            px, py = 4 * ix + 2, 4 * iy + 2
+            win = pad1[py - 2:py + 2, px - 2:px + 2]        # pixels p-2 .. p+1
+            for ty in range(H2):
+                for tx in range(W2):
+                    exp[iy * P0x + ix, ty, tx] = np.sum(win * pad[ty:ty + 4, tx:tx + 4]) / 16.0
+    got = oracle_mod.level0(d1, d2, "f64")
+    np.testing.assert_allclose(got, exp, rtol=0, atol=1e-15)
+    got32 = oracle_mod.level0(d1, d2, "f32")
+    np.testing.assert_allclose(got32, exp, rtol=0, atol=2e-6)
+    # a map value equals 1 only for identical windows: correlate I with itself
+    same = oracle_mod.level0(d1, d1, "f64")
+    for iy in range(P0y):
+        for ix in range(P0x):
+            if 4 * ix + 3 <= W1 - 1 and 4 * iy + 3 <= H1 - 1:   # whole window inside I
+                assert abs(same[iy * P0x + ix, 4 * iy + 2, 4 * ix + 2] - 1.0) < 1e-14
+
+
+# --------------------------------------------------------------------------- #
+# P2: iterative pyramid == memo-free recursive evaluation of Eq. 6            #
+# --------------------------------------------------------------------------- #
+def _recursive_C(d1, d2, lam, l, px, py, x, y, C0cache):
+    """Literal Eq. 6 (with rectification, Eq. 11) at pixel (x, y) of I'.
+
+    C_{4,p}(x') = C0(p, x')^lam.  For N = 4*2^l: average over the children
+    p + 2^l o_i that exist of the max of C_{N/2, child} over the 3x3 points
+    x' + 2^l o_i + 2^(l-1) m that lie inside I' (0 if the centre itself lies
+    outside I'), then ^lam.  Patch existence: an atomic patch exists if its
+    centre 4k+2 <= W-1; a level-l patch exists if one of its children exists.
+    """
+    H1, W1, _ = d1.shape
+    H2, W2, _ = d2.shape
+    if l == 0:
+        return C0cache[(px, py)][y, x] ** lam
+    s = 1 << l
+    h = s // 2
+    tot, n = 0.0, 0
+    for i in range(4):
+        ox = 1 if i >= 2 else -1
+        oy = 1 if (i & 1) else -1
+        cx, cy = px + s * ox, py + s * oy
+        if not _exists(W1, H1, l - 1, cx, cy):
+            continue
+        n += 1
+        sx, sy = x + s * ox, y + s * oy
+        if not (0 <= sx < W2 and 0 <= sy < H2):
+            continue
+        best = -1.0
+        for my in (-1, 0, 1):
+            for mx in (-1, 0, 1):
+                u, v = sx + h * mx, sy + h * my
+                if 0 <= u < W2 and 0 <= v < H2:
+                    best = max(best, _recursive_C(d1, d2, lam, l - 1, cx, cy, u, v, C0cache))
+        tot += best
+    return (tot / n) ** lam
+
+
+def _exists(W1, H1, l, cx, cy):
+    if l == 0:
+        return cx % 4 == 2 and cy % 4 == 2 and 2 <= cx <= W1 - 1 and 2 <= cy <= H1 - 1
+    if cx < 0 or cy < 0 or cx > W1 - 1 or cy > H1 - 1 or cx % 4 or cy % 4:
+        return False
+    s = 1 << l
+    return any(_exists(W1, H1, l - 1, cx + s * (1 if i >= 2 else -1), cy + s * (1 if i & 1 else -1))
+               for i in range(4))
+
+
+@pytest.mark.parametrize("W1,H1,W2,H2,seed", [(16, 12, 16, 12, 3), (21, 14, 18, 13, 4), (24, 20, 11, 23, 5)])
+def test_p2_recursive_eq6(oracle_mod, W1, H1, W2, H2, seed):
+    lam = 1.4
+    d1 = _rand_desc(W1, H1, seed)
+    d2 = _rand_desc(W2, H2, seed + 100)
+    pyr = oracle_mod.pyramid(d1, d2, "f64", lam)
+    g = pyr.geom
+    C0 = oracle_mod.level0(d1, d2, "f64")
+    C0cache = {}
+    for p in range(g.P0x * g.P0y):
+        C0cache[(4 * (p % g.P0x) + 2, 4 * (p // g.P0x) + 2)] = C0[p]
+    for l in range(g.L + 1):
+        npl = g.npatch(l)
+        for p in range(npl):
+            if l == 0:
+                px, py = 4 * (p % g.P0x) + 2, 4 * (p // g.P0x) + 2
+            else:
+                px, py = 4 * (p % g.Lx), 4 * (p // g.Lx)
+            ok = _exists(W1, H1, l, px, py)
+            assert bool(pyr.valid[l][p]) == ok
+            if not ok:
+                continue
+            s = 1 << l
+            if l == g.L:
+                for qy in range(g.dh[l]):
+                    for qx in range(g.dw[l]):
+                        want = _recursive_C(d1, d2, lam, l, px, py, s * qx, s * qy, C0cache)
+                        assert abs(pyr.top[p, qy, qx] - want) <= 1e-13
+            else:
+                # pooled value at r = max over the 3x3 of level-l points 2r+m inside I'
+                for ry in range(g.dh[l + 1]):
+                    for rx in range(g.dw[l + 1]):
+                        best = -1.0
+                        for my in (-1, 0, 1):
+                            for mx in (-1, 0, 1):
+                                u, v = s * (2 * rx + mx), s * (2 * ry + my)
+                                if 0 <= u < W2 and 0 <= v < H2:
+                                    best = max(best, _recursive_C(d1, d2, lam, l, px, py, u, v, C0cache))
+                        assert abs(pyr.pooled[l][p, ry, rx] - best) <= 1e-13
+    # the FP32 mirror (pool before the power, compensated sums) agrees closely
+    p32 = oracle_mod.pyramid(d1.astype(np.float32), d2.astype(np.float32), "f32", lam)
+    for l in range(g.L):
+        np.testing.assert_allclose(p32.pooled[l], pyr.pooled[l], rtol=2e-5, atol=1e-7)
+    np.testing.assert_allclose(p32.top, pyr.top, rtol=2e-5, atol=1e-7)
+
+
+# --------------------------------------------------------------------------- #
+# P3 (+P9): merged backtracking == exhaustive path enumeration (Eq. 13-15)    #
+# --------------------------------------------------------------------------- #
+def _enumerate_paths(pyr):
+    """Every path from every top entry, no merging: leaf (patch, t, score, entry)."""
+    g = pyr.geom
+    dt = pyr.top.dtype
+    L = g.L
+    P, QY, QX = np.nonzero(np.ones_like(pyr.top, dtype=bool))
+    keep = pyr.valid[L][P].astype(bool)
+    P, QY, QX = P[keep], QY[keep], QX[keep]
+    S = pyr.top[P, QY, QX].astype(dt)
+    EP, EQX, EQY = P.copy(), QX.copy(), QY.copy()
+    for l in range(L, 0, -1):
+        nP, nX, nY, nS, nE, nEX, nEY = [], [], [], [], [], [], []
+        mw, mh = g.dw[l], g.dh[l]
+        for i in range(4):
+            ox = 1 if i >= 2 else -1
+            oy = 1 if (i & 1) else -1
+            if l == 1:
+                cx = P % g.Lx + (ox - 1) // 2
+                cy = P // g.Lx + (oy - 1) // 2
+                ok = (cx >= 0) & (cy >= 0) & (cx < g.P0x) & (cy < g.P0y)
+                c = cy * g.P0x + cx
+            else:
+                s = 1 << (l - 2)
+                cx = P % g.Lx + ox * s
+                cy = P // g.Lx + oy * s
+                ok = (cx >= 0) & (cy >= 0) & (cx < g.Lx) & (cy < g.Ly)
+                c = cy * g.Lx + cx
+            c = np.where(ok, c, 0)
+            ok &= pyr.valid[l - 1][c].astype(bool)
+            rx, ry = QX + ox, QY + oy
+            ok &= (rx >= 0) & (ry >= 0) & (rx < mw) & (ry < mh)
+            rx, ry = np.where(ok, rx, 0), np.where(ok, ry, 0)
+            code = pyr.argmax[l - 1][c, ry, rx].astype(np.int64)
+            tx = 2 * rx + code % 3 - 1
+            ty = 2 * ry + code // 3 - 1
+            s2 = (S + pyr.pooled[l - 1][c, ry, rx]).astype(dt)
+            nP.append(c[ok]); nX.append(tx[ok]); nY.append(ty[ok]); nS.append(s2[ok])
+            nE.append(EP[ok]); nEX.append(EQX[ok]); nEY.append(EQY[ok])
+        P, QX, QY, S = np.concatenate(nP), np.concatenate(nX), np.concatenate(nY), np.concatenate(nS)
+        EP, EQX, EQY = np.concatenate(nE), np.concatenate(nEX), np.concatenate(nEY)
+    return P, QX, QY, S, EP, EQX, EQY
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("W,H,seed", [(64, 48, 11), (37, 29, 12)])
+def test_p3_backtrack_vs_enumeration(oracle_mod, prec, W, H, seed):
+    pr = synth.make_pair_smooth(W, H, seed=seed)
+    d1 = oracle_mod.descriptors(pr.img1, prec)
+    d2 = oracle_mod.descriptors(pr.img2, prec)
+    pyr = oracle_mod.pyramid(d1, d2, prec)
+    bt = oracle_mod.backtrack(pyr, dense_leaf=True)
+    g = pyr.geom
+    P, TX, TY, S, EP, EQX, EQY = _enumerate_paths(pyr)
+    n_paths_bound = int(pyr.valid[g.L].sum()) * g.dw[g.L] * g.dh[g.L] * 4 ** g.L
+    assert 0 < len(P) <= n_paths_bound
+    leaf = np.full((g.npatch(0), g.H2, g.W2), -np.inf, dtype=pyr.top.dtype)
+    np.maximum.at(leaf, (P, TY, TX), S)
+    # merging by highest score at every level == max over all paths (exact)
+    np.testing.assert_array_equal(bt.leaf, leaf)
+    assert bt.reached[0] == int(np.isfinite(leaf).sum())
+    # BestAt per atomic patch
+    for p in range(g.npatch(0)):
+        row = leaf[p].ravel()
+        if not np.isfinite(row).any():
+            assert bt.bestP_i[p] == -1
+            continue
+        m = row.max()
+        assert bt.bestP_s[p] == m and bt.bestP_i[p] == int(np.flatnonzero(row == m)[0])
+    # P9: deformation bound, every leaf within 2^L - 1 of its entry's rigid motion
+    L = g.L
+    epx, epy = 4 * (EP % g.Lx), 4 * (EP // g.Lx)
+    ax, ay = 4 * (P % g.P0x) + 2, 4 * (P // g.P0x) + 2
+    devx = TX - (ax + (1 << L) * EQX - epx)
+    devy = TY - (ay + (1 << L) * EQY - epy)
+    assert np.abs(devx).max() <= (1 << L) - 1 and np.abs(devy).max() <= (1 << L) - 1
+
+
+# --------------------------------------------------------------------------- #
+# P4: every map value lies in (0, 1] (unit non-negative descriptors, mu > 0)  #
+# --------------------------------------------------------------------------- #
+def test_p4_value_range(oracle_mod):
+    pr = synth.make_pair_smooth(64, 48, seed=5)
+    for prec in ("f64", "f32"):
+        d1 = oracle_mod.descriptors(pr.img1, prec)
+        d2 = oracle_mod.descriptors(pr.img2, prec)
+        pyr = oracle_mod.pyramid(d1, d2, prec)
+        g = pyr.geom
+        # level 0: every window overlaps I' in at least its own pixel -> C0 > 0
+        v = pyr.pooled[0]
+        assert v.min() > 0 and v.max() <= 1.0
+        for l in range(1, g.L + 1):
+            A = pyr.pooled[l] if l < g.L else pyr.top
+            v = A[pyr.valid[l].astype(bool)]
+            assert v.min() >= 0 and v.max() <= 1.0
+        # a top value is 0 only where every existing child is sampled outside the domain
+        L, mw, mh = g.L, g.dw[g.L], g.dh[g.L]
+        s = 1 << (L - 2)
+        for p in np.flatnonzero(pyr.valid[L]):
+            ix, iy = p % g.Lx, p // g.Lx
+            for qy in range(mh):
+                for qx in range(mw):
+                    inside = False
+                    for i in range(4):
+                        ox, oy = (1 if i >= 2 else -1), (1 if i & 1 else -1)
+                        cx, cy = ix + ox * s, iy + oy * s
+                        if 0 <= cx < g.Lx and 0 <= cy < g.Ly and pyr.valid[L - 1][cy * g.Lx + cx]:
+                            inside |= (0 <= qx + ox < mw and 0 <= qy + oy < mh)
+                    assert (pyr.top[p, qy, qx] > 0) == inside
+
+
+def _descendants_of_top(pyr):
+    """Atomic patches reachable from an existing top patch through existing children."""
+    g = pyr.geom
+    cur = pyr.valid[g.L].astype(bool)
+    for l in range(g.L, 0, -1):
+        nxt = np.zeros(g.npatch(l - 1), dtype=bool)
+        for p in np.flatnonzero(cur):
+            ix, iy = p % g.Lx, p // g.Lx
+            for i in range(4):
+                ox, oy = (1 if i >= 2 else -1), (1 if i & 1 else -1)
+                if l == 1:
+                    cx, cy, nx, ny = ix + (ox - 1) // 2, iy + (oy - 1) // 2, g.P0x, g.P0y
+                else:
+                    s = 1 << (l - 2)
+                    cx, cy, nx, ny = ix + ox * s, iy + oy * s, g.Lx, g.Ly
+                if 0 <= cx < nx and 0 <= cy < ny and pyr.valid[l - 1][cy * nx + cx]:
+                    nxt[cy * nx + cx] = True
+        cur = nxt
+    return cur
+
+
+# --------------------------------------------------------------------------- #
+# P5: pure integer translation with margin -> every patch matches p + t,      #
+#     score L + 1                                                             #
+# --------------------------------------------------------------------------- #
+@pytest.mark.parametrize("W,H,tx,ty", [(32, 24, 3, -5), (40, 28, -7, 2)])
+def test_p5_translation(oracle_mod, W, H, tx, ty):
+    mx = max(W, H)
+    L = 0
+    while 4 * (1 << L) < mx:
+        L += 1
+    M = 1 << (L + 1)
+    W2, H2 = W + 2 * M, H + 2 * M
+    canvas = _rand_desc(W2, H2, 77)
+    # desc1(x) = desc2(x + t + M): I' is I translated by t, plus a margin M
+    ox, oy = M + tx, M + ty
+    d1 = canvas[oy:oy + H, ox:ox + W].copy()
+    for prec in ("f64", "f32"):
+        dt = np.float64 if prec == "f64" else np.float32
+        pyr = oracle_mod.pyramid(d1.astype(dt), canvas.astype(dt), prec)
+        bt = oracle_mod.backtrack(pyr)
+        m = oracle_mod.reciprocal(pyr, bt)
+        g = pyr.geom
+        assert g.L == L
+        # exactly the atomic patches that descend from an existing top patch match
+        reach = _descendants_of_top(pyr)
+        assert reach.sum() >= 0.8 * g.npatch(0)
+        got = ((m[:, 1] - 2) // 4 * g.P0x + (m[:, 0] - 2) // 4).astype(int)
+        np.testing.assert_array_equal(got, np.flatnonzero(reach))
+        np.testing.assert_array_equal(m[:, 2] - m[:, 0], ox)
+        np.testing.assert_array_equal(m[:, 3] - m[:, 1], oy)
+        tol = 1e-12 if prec == "f64" else 1e-5
+        assert np.abs(m[:, 4] - (L + 1)).max() < tol
+
+
+# --------------------------------------------------------------------------- #
+# P6: identity warp through the descriptor step                               #
+# --------------------------------------------------------------------------- #
+def test_p6_identity(oracle_mod):
+    pr = synth.make_pair_smooth(64, 48, seed=9)
+    for prec in ("f64", "f32"):
+        m, pyr, bt = oracle_mod.match(pr.img1, pr.img1, prec)
+        g = pyr.geom
+        assert len(m) == g.npatch(0)
+        np.testing.assert_array_equal(m[:, 0], m[:, 2])
+        np.testing.assert_array_equal(m[:, 1], m[:, 3])
+        tol = 1e-12 if prec == "f64" else 1e-5
+        assert np.abs(m[:, 4] - (g.L + 1)).max() < tol
+
+
+# --------------------------------------------------------------------------- #
+# P7: shift equivariance (translation invariance "by construction", Sec. 3.4) #
+# --------------------------------------------------------------------------- #
+def test_p7_shift_equivariance(oracle_mod):
+    W1, H1 = 24, 20
+    d1 = _rand_desc(W1, H1, 21)
+    L = 3                                   # 4 * 2^3 = 32 >= 24
+    u = (1, 2)
+    sx, sy = (1 << L) * u[0], (1 << L) * u[1]
+    W2, H2 = 96, 80
+    canvas = _rand_desc(W2 + sx, H2 + sy, 22)
+    d2 = canvas[sy:, sx:].copy()            # d2(x) = canvas(x + s)
+    d2b = canvas[:H2, :W2].copy()           # d2b(x) = canvas(x) = d2(x - s)
+    a = oracle_mod.pyramid(d1, d2, "f64")
+    b = oracle_mod.pyramid(d1, d2b, "f64")
+    g = a.geom
+    assert g.L == L
+    margin = 1 << (L + 3)
+    for l in range(g.L + 1):
+        k = 1 << (l + 1) if l < g.L else 1 << l      # pixel spacing of the stored map
+        A = a.pooled[l] if l < g.L else a.top
+        B = b.pooled[l] if l < g.L else b.top
+        dx, dy = sx // k, sy // k
+        for ry in range(A.shape[1]):
+            for rx in range(A.shape[2]):
+                x, y = rx * k, ry * k
+                if not (margin <= x <= W2 - margin and margin <= y <= H2 - margin):
+                    continue
+                if not (margin <= x + sx <= W2 - margin and margin <= y + sy <= H2 - margin):
+                    continue
+                assert np.array_equal(A[:, ry, rx], B[:, ry + dy, rx + dx])
+
+
+# --------------------------------------------------------------------------- #
+# P8: operator invariants (max-pool, rectification, argmax)                   #
+# --------------------------------------------------------------------------- #
+def test_p8_operator_invariants(oracle_mod):
+    d1 = _rand_desc(20, 16, 31)
+    d2 = _rand_desc(19, 17, 32)
+    lam = 1.4
+    for prec in ("f64", "f32"):
+        dt = np.float64 if prec == "f64" else np.float32
+        pyr = oracle_mod.pyramid(d1.astype(dt), d2.astype(dt), prec, lam)
+        C0 = oracle_mod.level0(d1.astype(dt), d2.astype(dt), prec)
+        g = pyr.geom
+        P = pyr.pooled[0]
+        A = pyr.argmax[0]
+        for ry in range(g.dh[1]):
+            for rx in range(g.dw[1]):
+                # pooled value = rectified map value at the argmax, and >= the centre
+                code = A[:, ry, rx].astype(int)
+                tx, ty = 2 * rx + code % 3 - 1, 2 * ry + code // 3 - 1
+                src = C0[np.arange(len(code)), ty, tx].astype(np.float64)
+                np.testing.assert_allclose(P[:, ry, rx], src ** lam, rtol=4e-7 if prec == "f32" else 1e-15)
+                assert np.all(P[:, ry, rx] >= (C0[:, 2 * ry, 2 * rx].astype(np.float64) ** lam) * (1 - 4e-7))
+                # the argmax is the first maximum in scan order over in-domain points
+                for p in range(len(code)):
+                    vals = []
+                    for my in (-1, 0, 1):
+                        for mx in (-1, 0, 1):
+                            x, y = 2 * rx + mx, 2 * ry + my
+                            vals.append(C0[p, y, x] if (0 <= x < g.W2 and 0 <= y < g.H2) else -np.inf)
+                    assert code[p] == int(np.argmax(np.array(vals)))
+    # rectification is increasing on [0, 1] and fixes 0 and 1
+    xs = np.linspace(0.0, 1.0, 20001)
+    ys = np.array([oracle_mod.pow_r(x, lam, "f32") for x in xs])
+    assert np.all(np.diff(ys) >= 0) and ys[0] == 0.0 and ys[-1] == 1.0
+
+
+# --------------------------------------------------------------------------- #
+# P10: boundary rule -- the corner patch has one child, weight 1 (Sec. 3.2)   #
+# --------------------------------------------------------------------------- #
+def test_p10_boundary_weights(oracle_mod):
+    d1 = _rand_desc(40, 36, 41)
+    d2 = _rand_desc(30, 26, 42)
+    lam = 1.4
+    pyr = oracle_mod.pyramid(d1, d2, "f64", lam)
+    g = pyr.geom
+    for l in range(1, g.L + 1):
+        assert pyr.valid[l][0] == 1
+        # child 3 of the corner patch (0,0): offset (+1,+1)
+        child = 0 if l == 1 else (1 << (l - 2)) * g.Lx + (1 << (l - 2))
+        mw, mh = g.dw[l], g.dh[l]
+        Pc = pyr.pooled[l - 1][child]
+        A = np.zeros((mh, mw))
+        for qy in range(mh):
+            for qx in range(mw):
+                if qx + 1 < mw and qy + 1 < mh:
+                    A[qy, qx] = Pc[qy + 1, qx + 1]
+        C = A ** lam                       # one valid child, weight 1 instead of 1/4
+        if l == g.L:
+            np.testing.assert_allclose(pyr.top[0], C, rtol=1e-15, atol=0)
+        else:
+            # pooled corner map = 3x3 max-pool of C
+            for ry in range(g.dh[l + 1]):
+                for rx in range(g.dw[l + 1]):
+                    ys = [2 * ry + m for m in (-1, 0, 1) if 0 <= 2 * ry + m < mh]
+                    xs = [2 * rx + m for m in (-1, 0, 1) if 0 <= 2 * rx + m < mw]
+                    assert abs(pyr.pooled[l][0, ry, rx] - C[np.ix_(ys, xs)].max()) <= 1e-15
+
+
+# --------------------------------------------------------------------------- #
+# P11: descriptors -- unit norm, closed forms on constant and ramp images     #
+# --------------------------------------------------------------------------- #
+def _sig(x, slope=0.2):
+    return 2.0 / (1.0 + math.exp(-slope * x)) - 1.0
+
+
+def test_p11_descriptor_closed_forms(oracle_mod):
+    mu = 0.3
+    # constant image: no gradient -> (0, ..., 0, 1)
+    d = oracle_mod.descriptors(np.full((20, 24), 0.37, np.float32), "f64")
+    np.testing.assert_allclose(d[..., :8], 0.0, atol=0)
+    np.testing.assert_allclose(d[..., 8], 1.0, rtol=1e-15)
+    # ramps: in the interior the smoothing keeps a linear image linear
+    W, H = 48, 40
+    r = math.sqrt(0.5)
+    cases = {
+        "x": (np.tile(np.arange(W, dtype=np.float64) / (2 * W), (H, 1)), (1.0, 0.0)),
+        "y": (np.tile((np.arange(H, dtype=np.float64) / (2 * H))[:, None], (1, W)), (0.0, 1.0)),
+        "-x": (np.tile(1.0 - np.arange(W, dtype=np.float64) / (2 * W), (H, 1)), (-1.0, 0.0)),
+    }
+    for name, (img, (ux, uy)) in cases.items():
+        img32 = img.astype(np.float32)
+        d = oracle_mod.descriptors(img32, "f64")
+        # gradient in image_scale units: per-pixel step of the ramp times 255
+        step = 255.0 * (float(img32[1, 1]) - float(img32[0, 0])) if name != "x" and name != "-x" else None
+        if name == "x":
+            g = 255.0 * float(img32[5, 21] - img32[5, 20])
+        elif name == "-x":
+            g = 255.0 * float(img32[5, 20] - img32[5, 21])
+        else:
+            g = 255.0 * float(img32[21, 5] - img32[20, 5])
+        gx, gy = g * ux, g * uy
+        dirs = [(math.cos(k * math.pi / 4), math.sin(k * math.pi / 4)) for k in range(8)]
+        v = np.array([_sig(max(0.0, gx * c + gy * s)) for (c, s) in dirs] + [mu])
+        v = v / np.linalg.norm(v)
+        inner = d[15:H - 15, 15:W - 15]
+        np.testing.assert_allclose(inner, np.broadcast_to(v, inner.shape), rtol=0, atol=2e-5)
+    # unit norm and 9th component = mu / ||[v, mu]|| on a generic image
+    pr = synth.make_pair_smooth(40, 32, seed=3)
+    for prec in ("f64", "f32"):
+        d = oracle_mod.descriptors(pr.img1, prec).astype(np.float64)
+        np.testing.assert_allclose(np.linalg.norm(d, axis=-1), 1.0, rtol=0, atol=1e-6 if prec == "f32" else 1e-14)
+        assert d.min() >= 0.0
+
+
+# --------------------------------------------------------------------------- #
+# Own FP32 elementary functions: accuracy against FP64                         #
+# --------------------------------------------------------------------------- #
+def test_own_pow_exp_accuracy(oracle_mod):
+    rng = np.random.default_rng(0)
+    xs = np.concatenate([rng.random(3000), 10.0 ** rng.uniform(-30, 0, 3000), [1.0, 0.5, 0.25]])
+    for lam in (1.4, 1.0, 2.0, 0.7):
+        lam32 = float(np.float32(lam))
+        for x in xs:
+            x32 = float(np.float32(x))
+            got = oracle_mod.pow_r(x32, lam32, "f32")
+            want = x32 ** lam32
+            if want < 1e-37:
+                continue
+            ulp = float(np.spacing(np.float32(want)))
+            assert abs(got - want) <= 4 * ulp, (x32, lam, got, want)   # stated bound: 4 ulp
+    for z in np.concatenate([-rng.random(2000) * 87.0, [0.0, -1e-8, -0.5]]):
+        z32 = float(np.float32(z))
+        got = oracle_mod.exp_r(z32, "f32")
+        want = math.exp(z32)
+        assert abs(got - want) <= 2 * float(np.spacing(np.float32(want))), (z32, got, want)
+
+
+def test_paper_constants_fixture():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.txt")
+    vals = {}
+    for line in open(path):
+        line = line.split("#")[0].strip()
+        if line:
+            k, v = line.split("=")
+            vals[k.strip()] = float(v)
+    import oracle
+    d = oracle.DEFAULT_CFG
+    assert (d["lam"], d["nu1"], d["nu2"], d["nu3"], d["slope"], d["mu"]) == (
+        vals["lambda"], vals["nu1"], vals["nu2"], vals["nu3"], vals["slope"], vals["mu"])
+    # deformation limits of Sec. 3.4: (N +/- 2 d_N)/N with d_N = 2^l - 1 -> 3/2 and 1/2
+    l = 40
+    N, dN = 4 * 2 ** l, 2 ** l - 1
+    assert abs((N + 2 * dN) / N - vals["scale_max"]) < 1e-9
+    assert abs((N - 2 * dN) / N - vals["scale_min"]) < 1e-9
