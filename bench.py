@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Throughput of the DeepMatching hot path on GB300: pairs/s at 1024x436.
+
+One step = one dm_match call on one synthetic 1024x436 pair already resident
+in HBM: descriptors of both images, the level-0 correlation with fused
+pooling, the pyramid levels, backtracking with merging and reciprocal
+verification.  The pyramid of one pair is ~21 GB, far larger than the
+126 MB L2, so every step streams from HBM (no flush needed).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank matches its own pair on its own GPU (independent
+replicas, weak scaling); rank 0 prints one JSON line.
+
+--impl reference times the CPU oracle (FP32 canonical build, as it stands) on
+this host's cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pairs/s at 1024x436"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "bf16", "auto"], default="auto")
+    ap.add_argument("--width", type=int, default=1024)
+    ap.add_argument("--height", type=int, default=436)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _pair(W, H, seed):
+    from paper_1506_07656_gb300 import synth
+    return synth.make_pair_smooth(W, H, seed=seed, max_disp=120.0)
+
+
+# --------------------------------------------------------------------------- #
+# Clocks sampled during the timed region                                      #
+# --------------------------------------------------------------------------- #
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- #
+# CPU oracle on a bounded sample                                             #
+# --------------------------------------------------------------------------- #
+def oracle_sample_rate(pair, target_s: float = 12.0, max_patches: int | None = None):
+    """Time the FP32 oracle's level-0 correlation + pooling (the stage that is
+    >95% of its work) on a subset of the atomic patches of `pair`; return the
+    pairs/s it implies for the whole pair, the threads used and a description."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    d1 = oracle.descriptors(pair.img1, "f32")
+    d2 = oracle.descriptors(pair.img2, "f32")
+    t_desc = time.perf_counter() - t0
+    H1, W1 = pair.img1.shape
+    H2, W2 = pair.img2.shape
+    g = oracle.geometry(W1, H1, W2, H2)
+    n0 = g.P0x * g.P0y
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    probe = min(n0, max(cores, 8))
+    t0 = time.perf_counter()
+    oracle.level0_pooled(d1, d2, np.arange(probe), "f32")
+    per = (time.perf_counter() - t0) / probe
+    k = int(min(n0, max(probe, target_s / max(per, 1e-9))))
+    if max_patches:
+        k = min(k, max_patches)
+    rng = np.random.default_rng(0)
+    sel = np.sort(rng.choice(n0, size=k, replace=False))
+    t0 = time.perf_counter()
+    oracle.level0_pooled(d1, d2, sel, "f32")
+    t = time.perf_counter() - t0
+    per_pair = t * n0 / k + t_desc
+    desc = (f"FP32 oracle level-0 correlation+pooling of {k} of {n0} atomic patches of one "
+            f"{W1}x{H1} pair ({t:.1f} s), scaled to all patches, plus both descriptors ({t_desc:.2f} s); "
+            f"pyramid levels >= 1 and backtracking not timed (<5% of the oracle's work)")
+    return 1.0 / per_pair, cores, desc, k, n0
+
+
+# --------------------------------------------------------------------------- #
+# Reference arm: the oracle, as it stands, on the host cores                 #
+# --------------------------------------------------------------------------- #
+def run_reference(a):
+    import numpy as np
+
+    import oracle
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    oracle.build()
+    pair = _pair(a.width, a.height, 1000)
+    d1 = oracle.descriptors(pair.img1, "f32")
+    d2 = oracle.descriptors(pair.img2, "f32")
+    g = oracle.geometry(a.width, a.height, a.width, a.height)
+    n0 = g.P0x * g.P0y
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    k = min(n0, 4 * cores)
+    rng = np.random.default_rng(1)
+    times = []
+    for s in range(a.warmup + a.steps):
+        sel = np.sort(rng.choice(n0, size=k, replace=False))
+        t0 = time.perf_counter()
+        oracle.level0_pooled(d1, d2, sel, "f32")
+        dt = time.perf_counter() - t0
+        if s >= a.warmup:
+            times.append(dt)
+    per_pair = sum(times) / len(times) * n0 / k
+    value = 1.0 / per_pair
+    sample = (f"each step: FP32 oracle level-0 correlation+pooling of {k} random atomic patches of {n0} "
+              f"(one {a.width}x{a.height} pair), scaled to the whole pair")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": per_pair * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"one {a.width}x{a.height} pair, value noise + smooth warp (max 120 px)",
+                   "width": a.width, "height": a.height},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------- #
+# Our arm                                                                    #
+# --------------------------------------------------------------------------- #
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1506_07656_gb300 import dm
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dm.load()
+    W, H = a.width, a.height
+    prec_name = "fp32" if a.precision == "auto" else a.precision
+    prec = dm.DM_BF16 if prec_name == "bf16" else dm.DM_FP32
+    ctx = dm.Context(prec, device=local)
+    pair = _pair(W, H, 1000 + rank)
+    d1 = torch.from_numpy(pair.img1).cuda()
+    d2 = torch.from_numpy(pair.img2).cuda()
+    ws = ctx.workspace("match", W, H, W, H)
+    geo = dm.dm_geometry(W, H, W, H)
+    n0 = geo["n_patch0"]
+    out = torch.empty((n0, 5), dtype=torch.float32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(a.warmup):
+        dm.dm_match(ctx.ctx, d1, d2, ws, out, cnt, stream)
+    torch.cuda.synchronize()
+    status, reached = dm.dm_read_status(ctx.ctx, ws, geo["L"] + 1, stream)
+    n_matches = int(cnt.item())
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        dm.dm_timing_start(ctx.ctx, a.steps)
+        ev0.record(stream)
+        for _ in range(a.steps):
+            dm.dm_match(ctx.ctx, d1, d2, ws, out, cnt, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    stages, ncalls, launches = dm.dm_timing_read(ctx.ctx)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * a.steps / (ms_max / 1e3)
+
+    # end to end through the public API with host buffers (copies inside)
+    h1 = torch.from_numpy(pair.img1).pin_memory()
+    h2 = torch.from_numpy(pair.img2).pin_memory()
+    hout = torch.empty((n0, 5), dtype=torch.float32).pin_memory()
+    for _ in range(max(1, a.warmup)):
+        dm.dm_match_host(ctx.ctx, h1, h2, ws, hout, stream)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        dm.dm_match_host(ctx.ctx, h1, h2, ws, hout, stream)
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * a.steps / float(te.item())
+
+    if rank == 0:
+        peaks = {}
+        pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        if os.path.exists(pk):
+            peaks = json.load(open(pk))
+        props = torch.cuda.get_device_properties(local)
+        nsm = props.multi_processor_count
+        corr_ms = stages["level0_correlation"] / max(ncalls, 1)
+        flop = 2.0 * 144 * n0 * W * H
+        achieved = flop / (corr_ms / 1e3) / 1e12
+        if prec == dm.DM_FP32:
+            sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+            peak = nsm * 128 * 2 * sm_max * 1e6 / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": None, "kernel": "k_corr0_f32 (level-0 correlation + fused pool/power)",
+                    "peak_source": f"FP32 FMA pipes: {nsm} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz (nominal max clock)",
+                    "algorithmic_flop_per_launch": flop, "launch_ms": corr_ms}
+        else:
+            peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": None, "kernel": "level-0 correlation on tcgen05 (BF16)",
+                    "peak_source": "bf16_tflops_sustained of measured" if peaks else "fallback 1.7 PFLOP/s sustained",
+                    "algorithmic_flop_per_launch": flop, "launch_ms": corr_ms}
+        # pyramid levels >= 1: algorithmic bytes = read every pooled map of levels 0..L-1 once,
+        # write pooled maps (4 B) + argmax (1 B) of levels 1..L-1 and the top (4 B)
+        L = geo["L"]
+        dw, dh = geo["dw"], geo["dh"]
+        n1 = geo["n_patch"]
+        rd = sum((n0 if l == 0 else n1) * dw[l + 1] * dh[l + 1] * 4 for l in range(L))
+        wr = sum(n1 * dw[l + 1] * dh[l + 1] * 5 for l in range(1, L)) + n1 * dw[L] * dh[L] * 4
+        lev_ms = stages["levels"] / max(ncalls, 1)
+        hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+        levels_gbs = (rd + wr) / (lev_ms / 1e3) / 1e9
+
+        cpu = None
+        if world == 1 and not a.no_cpu_baseline:
+            rate, cores, sample, _, _ = oracle_sample_rate(pair)
+            cpu = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": sample}
+        clocks = clk.summary()
+        line = {
+            "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == dm.DM_FP32 else "bf16", "data": "synthetic",
+            "config": {"workload": f"one {W}x{H} pair per GPU per step, seeded 4-octave value noise, smooth warp "
+                                   f"max 120 px (+5% gain, sigma 0.01 noise)",
+                       "width": W, "height": H, "precision": prec_name, "L": L, "atomic_patches": n0,
+                       "l2": "working set ~21 GB per pair >> 126 MB L2; no flush needed",
+                       "matches": n_matches, "device_status": status,
+                       "merged_tuples_per_level": reached},
+            "roofline": roof,
+            "levels_hbm": {"achieved": levels_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": levels_gbs / hbm_peak,
+                           "algorithmic_bytes": rd + wr, "ms": lev_ms},
+            "stages_ms": {k: v / max(ncalls, 1) for k, v in stages.items()},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": 2 * W * H * 4,
+                    "d2h_bytes_per_step": n0 * 20 + 4},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    ctx.close()
+    return 0
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,190 @@
+/*
+ * dm.h -- C ABI of the GB300 DeepMatching hot path.
+ *
+ * DeepMatching (Revaud, Weinzaepfel, Harchaoui, Schmid) matches two images
+ * I (W1 x H1) and I' (W2 x H2) -- Sec. 3.1 -- and returns quasi-dense
+ * correspondences (p, p', s): p the centre of a 4x4 atomic patch of I, p' a
+ * pixel of I', s a score -- Eq. 16.  The calls below are the steps of that
+ * computation:
+ *
+ *   dm_descriptors        per-pixel 9-D descriptors (Sec. 3.2 "Pixel descriptor")
+ *   dm_correlate_pyramid  bottom-level correlation (Eq. 3-4) and the
+ *                         multi-level correlation pyramid (Eq. 5-12, Algorithm 1)
+ *   dm_backtrack          backtracking with merging (Eq. 13-15) and reciprocal
+ *                         verification (Eq. 16)
+ *   dm_match              all of the above
+ *
+ * Conventions shared by every call:
+ *   - Pointers named d_* are CUDA device pointers on the context's device;
+ *     h_* are host pointers.  The caller owns every buffer and the stream; the
+ *     library never allocates device memory.  Workspace sizes come from
+ *     dm_workspace_bytes(); a workspace must be 256-byte aligned.
+ *   - Images are float32, row-major [H][W], values in [0, 1].  Descriptors
+ *     are float32 [H][W][9] (8 orientation channels, then the mu channel).
+ *   - Calls are asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ *     default stream) unless stated otherwise; argument errors are reported
+ *     synchronously and nothing is launched.  A failure of a CUDA call returns
+ *     DM_ECUDA.  dm_last_error() describes the last failure of a context.
+ *   - Devices: each call makes the context's device current for its duration
+ *     and restores the caller's current device.
+ */
+#ifndef DM_H
+#define DM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DM_OK = 0,
+    DM_EINVAL = 1,        /* bad argument (size, pointer, alignment, capacity)     */
+    DM_ENOMEM = 2,        /* workspace smaller than dm_workspace_bytes() requires  */
+    DM_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed           */
+    DM_ETIMEOUT = 4,      /* a bounded device-side wait gave up                    */
+    DM_EUNSUPPORTED = 5,  /* valid request this build does not handle              */
+    DM_EOVERFLOW = 6      /* output or frontier capacity exceeded                  */
+} dm_status;
+
+typedef enum {
+    DM_FP32 = 0,          /* FP32 everywhere; bit-exact with the FP32 reference    */
+    DM_BF16 = 1           /* bottom-level correlation on BF16 tensor cores (FP32
+                             accumulation); the rest of the pyramid in FP32         */
+} dm_precision;
+
+/* Parameters of the method.  Defaults (dm_config_default) are the paper's:
+ * nu1 = nu2 = nu3 = 1, slope (varsigma) = 0.2, mu = 0.3 (Sec. 5.2 "Pixel
+ * descriptor parameters"), lambda = 1.4 (Sec. 5.2 "Non-linear rectification"),
+ * image_scale = 255 (input in [0,1] is mapped to 0..255 before the gradient). */
+typedef struct {
+    float nu1, nu2, nu3;   /* std. dev. of the three Gaussian smoothings (0 = none) */
+    float slope;           /* sigmoid slope varsigma                               */
+    float mu;              /* ninth, constant descriptor component                 */
+    float lambda;          /* rectification exponent (Eq. 11)                      */
+    float image_scale;     /* multiplier applied to input intensities              */
+    int precision;         /* dm_precision                                         */
+} dm_config;
+
+/* One output correspondence (Eq. 16): (x1, y1) is the centre of an atomic
+ * patch of I, (x2, y2) the matched pixel of I', score the sum of the
+ * correlations along its backtracking path (Eq. 14). */
+typedef struct {
+    float x1, y1, x2, y2, score;
+} dm_match_t;
+
+typedef struct dm_ctx dm_ctx;          /* host-side state: config, device, last error */
+typedef struct dm_pyramid dm_pyramid;  /* host-side view of a pyramid in a workspace  */
+
+/* Status word values written by the device into the workspace (dm_read_status). */
+#define DM_DEV_OK 0
+#define DM_DEV_FRONTIER_OVERFLOW 1     /* a merge table filled up during backtracking */
+#define DM_DEV_OUTPUT_OVERFLOW 2       /* more matches than the output capacity       */
+
+/* Fill *cfg with the paper's parameters and DM_FP32. */
+void dm_config_default(dm_config* cfg);
+
+/* Create a context bound to CUDA device `device`.  Host allocation only. */
+dm_status dm_create(const dm_config* cfg, int device, dm_ctx** out);
+dm_status dm_destroy(dm_ctx* ctx);
+/* Text of the last failure on ctx ("" if none); owned by ctx. */
+const char* dm_last_error(const dm_ctx* ctx);
+
+/* Geometry of the method for a pair of sizes (Sec. 3.2 and Algorithm 1):
+ *   *L        number of aggregation iterations, min{l : 4*2^l >= max(W1,H1)}
+ *   *n_patch0 atomic patches (centres 4k+2 inside I)
+ *   *n_patch  lattice patches of levels >= 1 (centres in 4Z^2 inside I)
+ *   dw, dh    (may be NULL) map domain of level l = 0..L+1: ceil(W2/2^l) x ceil(H2/2^l)
+ * Requires W1, H1 >= 4, max(W1, H1) >= 5, W2, H2 >= 1; DM_EUNSUPPORTED when
+ * a level's node count does not fit the 32-bit merge keys. */
+dm_status dm_geometry(int W1, int H1, int W2, int H2, int* L, int* n_patch0, int* n_patch, int* dw, int* dh);
+
+/* Workspace bytes for a pair of sizes:
+ *   desc_bytes      scratch of dm_descriptors for the larger image
+ *   pyramid_bytes   dm_correlate_pyramid
+ *   backtrack_bytes dm_backtrack
+ *   match_bytes     dm_match (descriptors of both images + the above)
+ * Any pointer may be NULL. */
+dm_status dm_workspace_bytes(const dm_ctx* ctx, int W1, int H1, int W2, int H2, size_t* desc_bytes,
+                             size_t* pyramid_bytes, size_t* backtrack_bytes, size_t* match_bytes);
+
+/* Pixel descriptors of one image (Sec. 3.2 "Pixel descriptor"):
+ * Gaussian smoothing (nu1) of image_scale * I, central-difference gradient,
+ * non-negative projections on the 8 directions k*pi/4, smoothing (nu2),
+ * sigmoid x -> 2/(1+exp(-slope x)) - 1, smoothing (nu3), then the 8 channels
+ * and mu are L2-normalised together.  Smoothings: std. dev. nu, taps on
+ * [-ceil(3 nu), ceil(3 nu)] normalised to 1, replicated border.
+ * d_img [H][W] float32; d_desc [H][W][9] float32 (output); d_tmp scratch of
+ * at least desc_bytes (dm_workspace_bytes with this W, H as image 1). */
+dm_status dm_descriptors(dm_ctx* ctx, const float* d_img, int W, int H, float* d_desc, void* d_tmp,
+                         size_t tmp_bytes, void* stream);
+
+/* Bottom-up correlation pyramid (Algorithm 1).
+ * Level 0 (Eq. 3-4): C0(p, t) = (1/16) sum over the 4x4 window of the 9-D
+ * dot products between the atomic patch of I centred at p and the window
+ * [t-2, t+1]^2 of I' (zero descriptors outside the images).  Each level l is
+ * stored max-pooled and subsampled (Eq. 8-9) after rectification (Eq. 11):
+ * P_l(p, r) = (max over the in-domain points 2r+m, m in {-1,0,1}^2, of C_l)^lambda
+ * with the argmax code (my+1)*3 + (mx+1).  Level l >= 1 (Eq. 12): C_l(p, q) =
+ * mean over the existing children i of P_{l-1}(p + 2^l o_i, q + o_i) (0 outside
+ * the domain); the top level C_L is stored unpooled.
+ * The pyramid lives in d_ws (>= pyramid_bytes); *out is a host handle that
+ * references it (free with dm_pyramid_free; it does not own d_ws). */
+dm_status dm_correlate_pyramid(dm_ctx* ctx, const float* d_desc1, int W1, int H1, const float* d_desc2, int W2,
+                               int H2, void* d_ws, size_t ws_bytes, dm_pyramid** out, void* stream);
+
+/* Device views of one level of a pyramid (valid after the producing stream
+ * work completes).  level in [0, L]; for level < L: d_vals = P_l
+ * [n_patches][mh][mw] and d_argmax its codes; for level == L: d_vals = C_L
+ * and d_argmax = NULL.  d_valid [n_patches]: 1 if the patch exists (Eq. 7
+ * with the boundary rule).  Any output pointer may be NULL. */
+dm_status dm_pyramid_level(const dm_pyramid* pyr, int level, const float** d_vals, const unsigned char** d_argmax,
+                           const unsigned char** d_valid, int* n_patches, int* mw, int* mh);
+dm_status dm_pyramid_free(dm_pyramid* pyr);
+
+/* Backtracking (Eq. 13-15) from every top-level position (Sec. 3.3 "Merging
+ * correspondences"), merging tuples equal in (level, patch, position) by
+ * their highest score, then reciprocal verification (Eq. 16): the best tuple
+ * of each atomic patch is kept iff it is also the best tuple whose pixel
+ * lies in its 4x4 cell of I' (ties: higher score, then lower index).
+ * d_out receives up to `capacity` matches in atomic-patch order; *d_count
+ * (device int) the number found (may exceed capacity: then
+ * DM_DEV_OUTPUT_OVERFLOW is set in the status word).  d_ws >= backtrack_bytes. */
+dm_status dm_backtrack(dm_ctx* ctx, const dm_pyramid* pyr, void* d_ws, size_t ws_bytes, dm_match_t* d_out,
+                       int capacity, int* d_count, void* stream);
+
+/* Whole method on device buffers: descriptors of both images, pyramid,
+ * backtracking.  d_ws >= match_bytes. */
+dm_status dm_match(dm_ctx* ctx, const float* d_img1, int W1, int H1, const float* d_img2, int W2, int H2,
+                   void* d_ws, size_t ws_bytes, dm_match_t* d_out, int capacity, int* d_count, void* stream);
+
+/* Whole method on host buffers: copies h_img1/h_img2 to the device (into
+ * d_ws), runs dm_match, copies the matches and their count back, and
+ * synchronises `stream`.  h_out holds `capacity` entries; *h_count receives
+ * the number of matches found.  Pinned host memory gives asynchronous copies. */
+dm_status dm_match_host(dm_ctx* ctx, const float* h_img1, int W1, int H1, const float* h_img2, int W2, int H2,
+                        void* d_ws, size_t ws_bytes, dm_match_t* h_out, int capacity, int* h_count, void* stream);
+
+/* Synchronise `stream` and read the header of a backtracking (or dm_match)
+ * workspace: *status = the device status word (DM_DEV_* bits, 0 = fine);
+ * reached[l] (l = 0..n_reached-1, may be NULL) = number of distinct merged
+ * tuples at level l during the last backtracking (level 0: atomic tuples
+ * before merging by pixel, i.e. arrivals). */
+dm_status dm_read_status(dm_ctx* ctx, const void* d_ws, int* status, long long* reached, int n_reached,
+                         void* stream);
+
+/* Stage timing (tracing).  After dm_timing_start(ctx, max_calls), each of the
+ * next max_calls dm_match calls records CUDA events on its stream at the stage
+ * boundaries: descriptors | level-0 correlation | levels >= 1 | backtracking.
+ * dm_timing_read() waits for the last recorded event and returns, summed over
+ * the recorded calls, the milliseconds of each stage (stage_ms[DM_NSTAGES]),
+ * the number of calls recorded and the number of kernels the library launched
+ * during them.  Events are created by dm_timing_start (no device memory). */
+#define DM_NSTAGES 4
+dm_status dm_timing_start(dm_ctx* ctx, int max_calls);
+dm_status dm_timing_read(dm_ctx* ctx, double* stage_ms, int* n_calls, long long* n_launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DM_H */

@@ -127,6 +127,26 @@ def level0(d1: np.ndarray, d2: np.ndarray, prec: str = "f64", p0: int = 0, p1: i
     return out
 
 
+def level0_pooled(d1: np.ndarray, d2: np.ndarray, patches, prec: str = "f32", lam: float = DEFAULT_CFG["lam"]):
+    """Level-0 pooled, rectified maps and argmax codes of the listed atomic patches."""
+    dt = _dtype(prec)
+    d1 = np.ascontiguousarray(d1, dtype=dt)
+    d2 = np.ascontiguousarray(d2, dtype=dt)
+    H1, W1, _ = d1.shape
+    H2, W2, _ = d2.shape
+    g = geometry(W1, H1, W2, H2)
+    pl = np.ascontiguousarray(np.asarray(patches, dtype=np.int32))
+    out = np.zeros((len(pl), g.dh[1], g.dw[1]), dtype=dt)
+    am = np.zeros((len(pl), g.dh[1], g.dw[1]), dtype=np.uint8)
+    lib = _lib(prec)
+    lib.orc_level0_pooled.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_double,
+                                      C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
+    rc = lib.orc_level0_pooled(_ptr(d1), W1, H1, _ptr(d2), W2, H2, float(lam), _ptr(pl), len(pl), _ptr(out), _ptr(am))
+    if rc != 0:
+        raise ValueError("level0_pooled oracle failed")
+    return out, am
+
+
 @dataclass
 class Pyramid:
     geom: Geometry

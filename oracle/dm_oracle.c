@@ -469,6 +469,33 @@ int orc_pyramid(const real* d1, int W1, int H1, const real* d2, int W2, int H2, 
     return 0;
 }
 
+/* Level-0 pooled maps (same arithmetic as level 0 of orc_pyramid) for a list
+ * of atomic patches only: out [n][dh[1]][dw[1]] and argmax codes. */
+int orc_level0_pooled(const real* d1, int W1, int H1, const real* d2, int W2, int H2, double lambda,
+                      const int* plist, int n, real* out, uint8_t* am) {
+    geom g;
+    if (make_geom(W1, H1, W2, H2, &g)) return -1;
+    const real lam = (real)lambda;
+#pragma omp parallel
+    {
+        real* map = (real*)malloc((size_t)W2 * H2 * sizeof(real));
+#pragma omp for schedule(dynamic, 1)
+        for (int k = 0; k < n; k++) {
+            int p = plist[k];
+            int px = 4 * (p % g.P0x) + 2, py = 4 * (p / g.P0x) + 2;
+            for (int ty = 0; ty < H2; ty++)
+                for (int tx = 0; tx < W2; tx++) {
+                    real c = corr0(d1, W1, H1, d2, W2, H2, px, py, tx, ty);
+                    map[(size_t)ty * W2 + tx] = ORC_F32 ? c : RPOW(c, lam);
+                }
+            size_t off = (size_t)k * g.dw[1] * g.dh[1];
+            pool_map(map, W2, H2, out + off, am + off, g.dw[1], g.dh[1], ORC_F32, lam);
+        }
+        free(map);
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Backtracking with merging (Eq. 13-15) and reciprocal verification (Eq. 16) */
 /*                                                                            */

@@ -1,0 +1,510 @@
+// Host side of the C ABI declared in include/dm.h: argument checks,
+// geometry, workspace layout, and the launch sequence of each call.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "dm_internal.cuh"
+
+struct dm_ctx {
+    dm_config cfg;
+    int device;
+    DmDescParams desc;
+    std::string err;
+    // stage timing: DM_NSTAGES + 1 events per recorded call
+    std::vector<cudaEvent_t> ev;
+    int t_max = 0, t_count = 0;
+    long long t_launch0 = 0;
+};
+
+static std::atomic<long long> g_launches{0};
+void dm_count_launches(long long n) { g_launches += n; }
+long long dm_launches() { return g_launches.load(); }
+
+namespace {
+
+struct DevGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DevGuard(int d) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != d) changed = (cudaSetDevice(d) == cudaSuccess);
+    }
+    ~DevGuard() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+dm_status fail(dm_ctx* c, dm_status s, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+dm_status cuda_fail(dm_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, DM_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// Gaussian taps of standard deviation nu on [-ceil(3nu), ceil(3nu)],
+// exp(-j^2/(2 nu^2)) in double, normalised by their sum (accumulated from
+// j = -R upwards), then rounded to float.  nu <= 0: identity (R = 0).
+DmTaps make_taps(float nu_f) {
+    DmTaps t;
+    memset(&t, 0, sizeof(t));
+    double nu = (double)nu_f;
+    if (!(nu > 0.0)) {
+        t.R = 0;
+        t.w[0] = 1.0f;
+        return t;
+    }
+    int R = (int)ceil(3.0 * nu);
+    if (2 * R + 1 > 65) R = 32;
+    double v[65], sum = 0.0;
+    for (int j = -R; j <= R; j++) {
+        v[j + R] = exp(-(double)(j * j) / (2.0 * nu * nu));
+        sum += v[j + R];
+    }
+    for (int j = 0; j <= 2 * R; j++) t.w[j] = (float)(v[j] / sum);
+    t.R = R;
+    return t;
+}
+
+bool aligned256(const void* p) { return ((uintptr_t)p & 255u) == 0; }
+
+struct MatchLayout {
+    DmBtLayout bt;       // at offset 0 (header first)
+    size_t desc1, desc2, tmp, img1, img2, out, count, pyr;
+    DmPyrLayout py;
+    size_t bytes;
+};
+
+void match_layout(const DmGeom& g, int precision, MatchLayout* m) {
+    dm_bt_layout(g, &m->bt);
+    size_t o = m->bt.bytes;
+    m->desc1 = o; o = dm_align(o + (size_t)g.W1 * g.H1 * 9 * 4);
+    m->desc2 = o; o = dm_align(o + (size_t)g.W2 * g.H2 * 9 * 4);
+    size_t big = (size_t)g.W1 * g.H1 > (size_t)g.W2 * g.H2 ? (size_t)g.W1 * g.H1 : (size_t)g.W2 * g.H2;
+    m->tmp = o; o = dm_align(o + 2 * big * 8 * 4);
+    m->img1 = o; o = dm_align(o + (size_t)g.W1 * g.H1 * 4);
+    m->img2 = o; o = dm_align(o + (size_t)g.W2 * g.H2 * 4);
+    m->out = o; o = dm_align(o + (size_t)g.npatch(0) * sizeof(dm_match_t));
+    m->count = o; o = dm_align(o + 16);
+    dm_pyr_layout(g, precision, &m->py);
+    m->pyr = o; o = dm_align(o + m->py.bytes);
+    m->bytes = o;
+}
+
+void fill_pyramid(dm_pyramid* p, const DmGeom& g, int precision, const DmPyrLayout& pl, char* base) {
+    memset(p, 0, sizeof(*p));
+    p->g = g;
+    p->precision = precision;
+    for (int l = 0; l <= g.L; l++) p->valid[l] = (const unsigned char*)(base + pl.valid[l]);
+    for (int l = 0; l < g.L; l++) {
+        p->pooled[l] = (const float*)(base + pl.pooled[l]);
+        p->amax[l] = (const unsigned char*)(base + pl.amax[l]);
+    }
+    p->top = (const float*)(base + pl.top);
+}
+
+dm_status run_descriptors(dm_ctx* c, const float* img, int W, int H, float* desc, char* tmp, cudaStream_t st) {
+    float* a = (float*)tmp;
+    float* b = a + (size_t)W * H * 8;
+    cudaError_t e = dm_launch_descriptors(c->desc, img, W, H, desc, a, b, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "descriptor kernels");
+    return DM_OK;
+}
+
+dm_status run_pyramid(dm_ctx* c, const DmGeom& g, const float* d1, const float* d2, char* base, const DmPyrLayout& pl,
+                      dm_pyramid* py, cudaStream_t st) {
+    fill_pyramid(py, g, c->cfg.precision, pl, base);
+    cudaError_t e;
+    if (c->cfg.precision == DM_BF16) {
+        e = dm_launch_corr0_bf16(g, d1, d2, c->cfg.lambda, base + pl.a16, base + pl.b16,
+                                 const_cast<float*>(py->pooled[0]), const_cast<unsigned char*>(py->amax[0]), st);
+    } else {
+        e = dm_launch_corr0_f32(g, d1, d2, c->cfg.lambda, const_cast<float*>(py->pooled[0]),
+                                const_cast<unsigned char*>(py->amax[0]), st);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "level-0 correlation");
+    e = dm_launch_levels(g, *py, c->cfg.lambda, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pyramid levels");
+    return DM_OK;
+}
+
+dm_status check_geom(dm_ctx* c, int W1, int H1, int W2, int H2, DmGeom* g) {
+    int r = dm_make_geom(W1, H1, W2, H2, g);
+    if (r == -1) return fail(c, DM_EINVAL, "invalid sizes %dx%d / %dx%d (need W1,H1 >= 4, max(W1,H1) >= 5, W2,H2 >= 1)", W1, H1, W2, H2);
+    if (r == -2) return fail(c, DM_EUNSUPPORTED, "sizes %dx%d / %dx%d exceed the 32-bit merge keys", W1, H1, W2, H2);
+    return DM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Geometry and layouts
+// ---------------------------------------------------------------------------
+int dm_make_geom(int W1, int H1, int W2, int H2, DmGeom* g) {
+    memset(g, 0, sizeof(*g));
+    if (W1 < 4 || H1 < 4 || W2 < 1 || H2 < 1) return -1;
+    if (W1 > (1 << 20) || H1 > (1 << 20) || W2 > (1 << 20) || H2 > (1 << 20)) return -2;
+    g->W1 = W1; g->H1 = H1; g->W2 = W2; g->H2 = H2;
+    int mx = W1 > H1 ? W1 : H1;
+    int L = 0;
+    long long N = 4;
+    while (N < mx) { N *= 2; L++; }
+    if (L < 1) return -1;
+    if (L > DM_MAXL) return -2;
+    g->L = L;
+    g->P0x = (W1 - 3) / 4 + 1;
+    g->P0y = (H1 - 3) / 4 + 1;
+    g->Lx = (W1 - 1) / 4 + 1;
+    g->Ly = (H1 - 1) / 4 + 1;
+    g->dw[0] = W2; g->dh[0] = H2;
+    for (int l = 1; l <= L + 1; l++) { g->dw[l] = (g->dw[l - 1] + 1) / 2; g->dh[l] = (g->dh[l - 1] + 1) / 2; }
+    // merge keys patch * |domain| + position must fit 32 bits (levels 1..L-1);
+    // atomic indices (pixel of I', patch*16 + offset) too.
+    for (int l = 1; l <= L; l++)
+        if ((unsigned long long)g->npatch(l) * (unsigned long long)g->dsize(l) >= 0xffffffffull) return -2;
+    if ((unsigned long long)g->npatch(0) * 16ull >= 0xffffffffull) return -2;
+    if ((unsigned long long)W2 * H2 >= 0xffffffffull) return -2;
+    return 0;
+}
+
+void dm_pyr_layout(const DmGeom& g, int precision, DmPyrLayout* o) {
+    memset(o, 0, sizeof(*o));
+    size_t off = 0;
+    for (int l = 0; l <= g.L; l++) { o->valid[l] = off; off = dm_align(off + (size_t)g.npatch(l)); }
+    for (int l = 0; l < g.L; l++) {
+        size_t n = (size_t)g.npatch(l) * (size_t)g.dsize(l + 1);
+        o->pooled[l] = off; off = dm_align(off + n * 4);
+        o->amax[l] = off; off = dm_align(off + n);
+    }
+    o->top = off; off = dm_align(off + (size_t)g.npatch(g.L) * (size_t)g.dsize(g.L) * 4);
+    if (precision == DM_BF16) {
+        size_t m = ((size_t)g.npatch(0) + 127) / 128 * 128;
+        o->a16 = off; off = dm_align(off + m * 144 * 2);
+        o->b16 = off; off = dm_align(off + ((size_t)g.W2 + 64) * ((size_t)g.H2 + 64) * 16 * 2);
+    }
+    o->bytes = off;
+}
+
+void dm_bt_layout(const DmGeom& g, DmBtLayout* o) {
+    memset(o, 0, sizeof(*o));
+    size_t off = 0;
+    o->header = off; off = dm_align(off + sizeof(DmWsHeader));
+    // bound on merged tuples per level: B_L = entries; B_l = min(4 B_{l+1}, |P_l|)
+    unsigned long long B = (unsigned long long)g.npatch(g.L) * (unsigned long long)g.dsize(g.L);
+    for (int l = g.L - 1; l >= 1; l--) {
+        unsigned long long pooled = (unsigned long long)g.npatch(l) * (unsigned long long)g.dsize(l + 1);
+        B = 4ull * B < pooled ? 4ull * B : pooled;
+        unsigned long long cap = 2ull * B;
+        if (cap < 64ull) cap = 64ull;
+        if (cap > 0xfffffff0ull) cap = 0xfffffff0ull;
+        o->cap[l] = (size_t)cap;
+        o->table[l] = off; off = dm_align(off + (size_t)cap * 8);
+        o->list[l] = off; off = dm_align(off + (size_t)cap * 4);
+    }
+    o->bestP = off; off = dm_align(off + (size_t)g.npatch(0) * 8);
+    o->bestQ = off; off = dm_align(off + (size_t)((g.W2 + 3) / 4) * ((g.H2 + 3) / 4) * 8);
+    o->bytes = off;
+}
+
+size_t dm_desc_tmp_bytes(int W, int H) { return dm_align(2 * (size_t)W * H * 8 * 4); }
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void dm_config_default(dm_config* cfg) {
+    if (!cfg) return;
+    cfg->nu1 = 1.0f;
+    cfg->nu2 = 1.0f;
+    cfg->nu3 = 1.0f;
+    cfg->slope = 0.2f;
+    cfg->mu = 0.3f;
+    cfg->lambda = 1.4f;
+    cfg->image_scale = 255.0f;
+    cfg->precision = DM_FP32;
+}
+
+dm_status dm_create(const dm_config* cfg, int device, dm_ctx** out) {
+    if (!out) return DM_EINVAL;
+    *out = nullptr;
+    dm_config c;
+    if (cfg) c = *cfg; else dm_config_default(&c);
+    if (!(c.lambda > 0.0f) || !(c.nu1 >= 0.0f) || !(c.nu2 >= 0.0f) || !(c.nu3 >= 0.0f) || !(c.nu1 <= 10.0f) ||
+        !(c.nu2 <= 10.0f) || !(c.nu3 <= 10.0f) || !(c.mu >= 0.0f) || !(c.image_scale > 0.0f))
+        return DM_EINVAL;
+    if (c.precision != DM_FP32 && c.precision != DM_BF16) return DM_EINVAL;
+    if (c.precision == DM_BF16) return DM_EUNSUPPORTED;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return DM_EINVAL;
+    dm_ctx* x = new dm_ctx();
+    x->cfg = c;
+    x->device = device;
+    x->desc.t1 = make_taps(c.nu1);
+    x->desc.t2 = make_taps(c.nu2);
+    x->desc.t3 = make_taps(c.nu3);
+    x->desc.scale = c.image_scale;
+    x->desc.slope = c.slope;
+    x->desc.mu = c.mu;
+    *out = x;
+    return DM_OK;
+}
+
+dm_status dm_destroy(dm_ctx* ctx) {
+    if (ctx) {
+        DevGuard dg(ctx->device);
+        for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+    }
+    delete ctx;
+    return DM_OK;
+}
+
+dm_status dm_timing_start(dm_ctx* ctx, int max_calls) {
+    if (!ctx || max_calls < 0 || max_calls > 100000) return DM_EINVAL;
+    DevGuard dg(ctx->device);
+    size_t need = (size_t)max_calls * (DM_NSTAGES + 1);
+    while (ctx->ev.size() < need) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return cuda_fail(ctx, r, "cudaEventCreate");
+        ctx->ev.push_back(e);
+    }
+    ctx->t_max = max_calls;
+    ctx->t_count = 0;
+    ctx->t_launch0 = dm_launches();
+    return DM_OK;
+}
+
+dm_status dm_timing_read(dm_ctx* ctx, double* stage_ms, int* n_calls, long long* n_launches) {
+    if (!ctx || !stage_ms) return DM_EINVAL;
+    DevGuard dg(ctx->device);
+    for (int k = 0; k < DM_NSTAGES; k++) stage_ms[k] = 0.0;
+    for (int c = 0; c < ctx->t_count; c++) {
+        cudaEvent_t* ev = &ctx->ev[(size_t)c * (DM_NSTAGES + 1)];
+        cudaError_t r = cudaEventSynchronize(ev[DM_NSTAGES]);
+        if (r != cudaSuccess) return cuda_fail(ctx, r, "cudaEventSynchronize");
+        for (int k = 0; k < DM_NSTAGES; k++) {
+            float ms = 0.f;
+            r = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            if (r != cudaSuccess) return cuda_fail(ctx, r, "cudaEventElapsedTime");
+            stage_ms[k] += ms;
+        }
+    }
+    if (n_calls) *n_calls = ctx->t_count;
+    if (n_launches) *n_launches = dm_launches() - ctx->t_launch0;
+    return DM_OK;
+}
+
+const char* dm_last_error(const dm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+dm_status dm_geometry(int W1, int H1, int W2, int H2, int* L, int* n_patch0, int* n_patch, int* dw, int* dh) {
+    DmGeom g;
+    int r = dm_make_geom(W1, H1, W2, H2, &g);
+    if (r == -1) return DM_EINVAL;
+    if (r == -2) return DM_EUNSUPPORTED;
+    if (L) *L = g.L;
+    if (n_patch0) *n_patch0 = g.npatch(0);
+    if (n_patch) *n_patch = g.npatch(1);
+    for (int l = 0; l <= g.L + 1; l++) {
+        if (dw) dw[l] = g.dw[l];
+        if (dh) dh[l] = g.dh[l];
+    }
+    return DM_OK;
+}
+
+dm_status dm_workspace_bytes(const dm_ctx* ctx, int W1, int H1, int W2, int H2, size_t* desc_bytes,
+                             size_t* pyramid_bytes, size_t* backtrack_bytes, size_t* match_bytes) {
+    if (!ctx) return DM_EINVAL;
+    DmGeom g;
+    dm_status s = check_geom(const_cast<dm_ctx*>(ctx), W1, H1, W2, H2, &g);
+    if (s != DM_OK) return s;
+    DmPyrLayout pl;
+    dm_pyr_layout(g, ctx->cfg.precision, &pl);
+    DmBtLayout bl;
+    dm_bt_layout(g, &bl);
+    MatchLayout ml;
+    match_layout(g, ctx->cfg.precision, &ml);
+    if (desc_bytes) {
+        size_t a = dm_desc_tmp_bytes(W1, H1), b = dm_desc_tmp_bytes(W2, H2);
+        *desc_bytes = a > b ? a : b;
+    }
+    if (pyramid_bytes) *pyramid_bytes = pl.bytes;
+    if (backtrack_bytes) *backtrack_bytes = bl.bytes;
+    if (match_bytes) *match_bytes = ml.bytes;
+    return DM_OK;
+}
+
+dm_status dm_descriptors(dm_ctx* ctx, const float* d_img, int W, int H, float* d_desc, void* d_tmp, size_t tmp_bytes,
+                         void* stream) {
+    if (!ctx) return DM_EINVAL;
+    if (!d_img || !d_desc || !d_tmp || W < 1 || H < 1) return fail(ctx, DM_EINVAL, "dm_descriptors: bad arguments");
+    if (tmp_bytes < dm_desc_tmp_bytes(W, H)) return fail(ctx, DM_ENOMEM, "dm_descriptors: scratch too small");
+    DevGuard dg(ctx->device);
+    return run_descriptors(ctx, d_img, W, H, d_desc, (char*)d_tmp, (cudaStream_t)stream);
+}
+
+dm_status dm_correlate_pyramid(dm_ctx* ctx, const float* d_desc1, int W1, int H1, const float* d_desc2, int W2, int H2,
+                               void* d_ws, size_t ws_bytes, dm_pyramid** out, void* stream) {
+    if (!ctx) return DM_EINVAL;
+    if (!out || !d_desc1 || !d_desc2 || !d_ws) return fail(ctx, DM_EINVAL, "dm_correlate_pyramid: null pointer");
+    *out = nullptr;
+    if (!aligned256(d_ws)) return fail(ctx, DM_EINVAL, "workspace must be 256-byte aligned");
+    DmGeom g;
+    dm_status s = check_geom(ctx, W1, H1, W2, H2, &g);
+    if (s != DM_OK) return s;
+    DmPyrLayout pl;
+    dm_pyr_layout(g, ctx->cfg.precision, &pl);
+    if (ws_bytes < pl.bytes) return fail(ctx, DM_ENOMEM, "pyramid workspace %zu < %zu bytes", ws_bytes, pl.bytes);
+    DevGuard dg(ctx->device);
+    dm_pyramid* py = (dm_pyramid*)malloc(sizeof(dm_pyramid));
+    if (!py) return fail(ctx, DM_EINVAL, "host allocation failed");
+    s = run_pyramid(ctx, g, d_desc1, d_desc2, (char*)d_ws, pl, py, (cudaStream_t)stream);
+    if (s != DM_OK) {
+        free(py);
+        return s;
+    }
+    *out = py;
+    return DM_OK;
+}
+
+dm_status dm_pyramid_level(const dm_pyramid* pyr, int level, const float** d_vals, const unsigned char** d_argmax,
+                           const unsigned char** d_valid, int* n_patches, int* mw, int* mh) {
+    if (!pyr || level < 0 || level > pyr->g.L) return DM_EINVAL;
+    const DmGeom& g = pyr->g;
+    if (d_vals) *d_vals = level < g.L ? pyr->pooled[level] : pyr->top;
+    if (d_argmax) *d_argmax = level < g.L ? pyr->amax[level] : nullptr;
+    if (d_valid) *d_valid = pyr->valid[level];
+    if (n_patches) *n_patches = g.npatch(level);
+    if (mw) *mw = level < g.L ? g.dw[level + 1] : g.dw[level];
+    if (mh) *mh = level < g.L ? g.dh[level + 1] : g.dh[level];
+    return DM_OK;
+}
+
+dm_status dm_pyramid_free(dm_pyramid* pyr) {
+    free(pyr);
+    return DM_OK;
+}
+
+dm_status dm_backtrack(dm_ctx* ctx, const dm_pyramid* pyr, void* d_ws, size_t ws_bytes, dm_match_t* d_out, int capacity,
+                       int* d_count, void* stream) {
+    if (!ctx) return DM_EINVAL;
+    if (!pyr || !d_ws || !d_out || !d_count || capacity < 0)
+        return fail(ctx, DM_EINVAL, "dm_backtrack: bad arguments");
+    if (!aligned256(d_ws)) return fail(ctx, DM_EINVAL, "workspace must be 256-byte aligned");
+    DmBtLayout bl;
+    dm_bt_layout(pyr->g, &bl);
+    if (ws_bytes < bl.bytes) return fail(ctx, DM_ENOMEM, "backtrack workspace %zu < %zu bytes", ws_bytes, bl.bytes);
+    DevGuard dg(ctx->device);
+    cudaError_t e = dm_launch_backtrack(pyr->g, *pyr, bl, (char*)d_ws, d_out, capacity, d_count, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "backtracking kernels");
+    return DM_OK;
+}
+
+dm_status dm_match(dm_ctx* ctx, const float* d_img1, int W1, int H1, const float* d_img2, int W2, int H2, void* d_ws,
+                   size_t ws_bytes, dm_match_t* d_out, int capacity, int* d_count, void* stream) {
+    if (!ctx) return DM_EINVAL;
+    if (!d_img1 || !d_img2 || !d_ws || !d_out || !d_count || capacity < 0)
+        return fail(ctx, DM_EINVAL, "dm_match: bad arguments");
+    if (!aligned256(d_ws)) return fail(ctx, DM_EINVAL, "workspace must be 256-byte aligned");
+    DmGeom g;
+    dm_status s = check_geom(ctx, W1, H1, W2, H2, &g);
+    if (s != DM_OK) return s;
+    MatchLayout ml;
+    match_layout(g, ctx->cfg.precision, &ml);
+    if (ws_bytes < ml.bytes) return fail(ctx, DM_ENOMEM, "match workspace %zu < %zu bytes", ws_bytes, ml.bytes);
+    DevGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    char* base = (char*)d_ws;
+    float* desc1 = (float*)(base + ml.desc1);
+    float* desc2 = (float*)(base + ml.desc2);
+    cudaEvent_t* ev = nullptr;
+    if (ctx->t_count < ctx->t_max) ev = &ctx->ev[(size_t)ctx->t_count++ * (DM_NSTAGES + 1)];
+    if (ev) cudaEventRecord(ev[0], st);
+    if ((s = run_descriptors(ctx, d_img1, W1, H1, desc1, base + ml.tmp, st)) != DM_OK) return s;
+    if ((s = run_descriptors(ctx, d_img2, W2, H2, desc2, base + ml.tmp, st)) != DM_OK) return s;
+    if (ev) cudaEventRecord(ev[1], st);
+    dm_pyramid py;
+    fill_pyramid(&py, g, ctx->cfg.precision, ml.py, base + ml.pyr);
+    cudaError_t e;
+    if (ctx->cfg.precision == DM_BF16)
+        e = dm_launch_corr0_bf16(g, desc1, desc2, ctx->cfg.lambda, base + ml.pyr + ml.py.a16, base + ml.pyr + ml.py.b16,
+                                 const_cast<float*>(py.pooled[0]), const_cast<unsigned char*>(py.amax[0]), st);
+    else
+        e = dm_launch_corr0_f32(g, desc1, desc2, ctx->cfg.lambda, const_cast<float*>(py.pooled[0]),
+                                const_cast<unsigned char*>(py.amax[0]), st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "level-0 correlation");
+    if (ev) cudaEventRecord(ev[2], st);
+    e = dm_launch_levels(g, py, ctx->cfg.lambda, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pyramid levels");
+    if (ev) cudaEventRecord(ev[3], st);
+    e = dm_launch_backtrack(g, py, ml.bt, base, d_out, capacity, d_count, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "backtracking kernels");
+    if (ev) cudaEventRecord(ev[4], st);
+    return DM_OK;
+}
+
+dm_status dm_match_host(dm_ctx* ctx, const float* h_img1, int W1, int H1, const float* h_img2, int W2, int H2,
+                        void* d_ws, size_t ws_bytes, dm_match_t* h_out, int capacity, int* h_count, void* stream) {
+    if (!ctx) return DM_EINVAL;
+    if (!h_img1 || !h_img2 || !d_ws || !h_out || !h_count || capacity < 0)
+        return fail(ctx, DM_EINVAL, "dm_match_host: bad arguments");
+    if (!aligned256(d_ws)) return fail(ctx, DM_EINVAL, "workspace must be 256-byte aligned");
+    DmGeom g;
+    dm_status s = check_geom(ctx, W1, H1, W2, H2, &g);
+    if (s != DM_OK) return s;
+    MatchLayout ml;
+    match_layout(g, ctx->cfg.precision, &ml);
+    if (ws_bytes < ml.bytes) return fail(ctx, DM_ENOMEM, "match workspace %zu < %zu bytes", ws_bytes, ml.bytes);
+    DevGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    char* base = (char*)d_ws;
+    float* i1 = (float*)(base + ml.img1);
+    float* i2 = (float*)(base + ml.img2);
+    dm_match_t* dout = (dm_match_t*)(base + ml.out);
+    int* dcnt = (int*)(base + ml.count);
+    int cap_dev = g.npatch(0);   // at most one match per atomic patch
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(i1, h_img1, (size_t)W1 * H1 * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(ctx, e, "copy image 1");
+    if ((e = cudaMemcpyAsync(i2, h_img2, (size_t)W2 * H2 * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(ctx, e, "copy image 2");
+    if ((s = dm_match(ctx, i1, W1, H1, i2, W2, H2, d_ws, ws_bytes, dout, cap_dev, dcnt, stream)) != DM_OK) return s;
+    int ncopy = capacity < cap_dev ? capacity : cap_dev;
+    if (ncopy > 0 && (e = cudaMemcpyAsync(h_out, dout, (size_t)ncopy * sizeof(dm_match_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(ctx, e, "copy matches");
+    if ((e = cudaMemcpyAsync(h_count, dcnt, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(ctx, e, "copy count");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(ctx, e, "dm_match_host");
+    if (*h_count > capacity) return fail(ctx, DM_EOVERFLOW, "%d matches, capacity %d", *h_count, capacity);
+    return DM_OK;
+}
+
+dm_status dm_read_status(dm_ctx* ctx, const void* d_ws, int* status, long long* reached, int n_reached, void* stream) {
+    if (!ctx) return DM_EINVAL;
+    if (!d_ws || !status || n_reached < 0 || n_reached > DM_MAXL + 2) return fail(ctx, DM_EINVAL, "dm_read_status: bad arguments");
+    DevGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    DmWsHeader h;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d_ws, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "dm_read_status");
+    *status = h.status;
+    for (int l = 0; l < n_reached && reached; l++) reached[l] = (long long)h.count[l];
+    return DM_OK;
+}
+
+}  // extern "C"

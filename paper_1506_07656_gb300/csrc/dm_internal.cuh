@@ -1,0 +1,185 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/dm.h"
+
+#define DM_MAXL 30
+
+// Geometry of one image pair (Sec. 3.2 "Bottom level", Eq. 7, Algorithm 1).
+struct DmGeom {
+    int W1, H1, W2, H2;
+    int L;              // aggregation iterations: min{l : 4*2^l >= max(W1,H1)}
+    int P0x, P0y;       // atomic grid: centres 4k+2 <= W1-1
+    int Lx, Ly;         // lattice 4Z^2 inside I: patches of levels >= 1
+    int dw[DM_MAXL + 2], dh[DM_MAXL + 2];  // map domain of level l
+    __host__ __device__ int npatch(int l) const { return l == 0 ? P0x * P0y : Lx * Ly; }
+    __host__ __device__ int gx(int l) const { return l == 0 ? P0x : Lx; }
+    __host__ __device__ long long dsize(int l) const { return (long long)dw[l] * dh[l]; }
+};
+
+int dm_make_geom(int W1, int H1, int W2, int H2, DmGeom* g);  // 0 ok, -1 invalid, -2 unsupported
+
+// Child i of lattice patch (ix, iy) at level l >= 1, as an index at level l-1,
+// or -1 outside the grid.  o_i = (-1,-1), (-1,+1), (+1,-1), (+1,+1) as (x, y),
+// child offset 2^l o_i pixels (Eq. 5).
+__host__ __device__ inline int dm_child(const DmGeom& g, int l, int ix, int iy, int i) {
+    int ox = (i >= 2) ? 1 : -1, oy = (i & 1) ? 1 : -1;
+    if (l == 1) {
+        int cx = ix + ((ox - 1) >> 1), cy = iy + ((oy - 1) >> 1);
+        if (cx < 0 || cy < 0 || cx >= g.P0x || cy >= g.P0y) return -1;
+        return cy * g.P0x + cx;
+    }
+    int s = 1 << (l - 2);
+    int cx = ix + ox * s, cy = iy + oy * s;
+    if (cx < 0 || cy < 0 || cx >= g.Lx || cy >= g.Ly) return -1;
+    return cy * g.Lx + cx;
+}
+
+// ---------------------------------------------------------------------------
+// Elementary functions with a fixed sequence of correctly rounded FP32
+// operations (explicit __f*_rn intrinsics; the library is built with
+// contraction off), so that any implementation of the same recipe -- the CPU
+// reference in particular -- produces identical bits.
+//
+// dm_expf(z), z <= 0: clamp at -87; n = rint(z * log2(e)); r = z - n*ln2 with
+//   ln2 split into a 16-bit head 0.693145751953125 and a tail
+//   1.42860682e-06 (two fmas); e^r by the degree-7 Taylor polynomial
+//   (coefficients 1/k!) in Horner form; times 2^n from the exponent field.
+// dm_powf(x, lam), x in [0,1]: x = m 2^e with m in [sqrt(1/2), sqrt(2)];
+//   log2 m = (2/ln2) f (1 + f^2/3 + ... + f^12/13), f = (m-1)/(m+1);
+//   lam*e split exactly (product + fma residual); the exponent is reduced to
+//   |g| <= 1/2 with two rint steps; 2^g by the degree-7 Taylor polynomial of
+//   e^(g ln2) (coefficients ln2^k/k!); scaled by 2^n in two steps.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float dm_pow2i(int n) { return __int_as_float((n + 127) << 23); }
+
+__device__ __forceinline__ float dm_expf(float z) {
+    if (z < -87.0f) z = -87.0f;
+    float n = rintf(__fmul_rn(z, 1.44269504f));
+    float r = __fmaf_rn(n, -0.693145751953125f, z);
+    r = __fmaf_rn(n, -1.42860682e-06f, r);
+    float p = 1.98412698e-04f;
+    p = __fmaf_rn(p, r, 1.38888889e-03f);
+    p = __fmaf_rn(p, r, 8.33333333e-03f);
+    p = __fmaf_rn(p, r, 4.16666667e-02f);
+    p = __fmaf_rn(p, r, 1.66666667e-01f);
+    p = __fmaf_rn(p, r, 0.5f);
+    p = __fmaf_rn(p, r, 1.0f);
+    p = __fmaf_rn(p, r, 1.0f);
+    return __fmul_rn(p, dm_pow2i((int)n));
+}
+
+__device__ __forceinline__ float dm_powf(float x, float lam) {
+    if (!(x > 0.0f)) return 0.0f;
+    int eadj = 0;
+    if (x < 1.17549435e-38f) { x = __fmul_rn(x, 16777216.0f); eadj = -24; }
+    uint32_t b = __float_as_uint(x);
+    int e = (int)((b >> 23) & 0xffu) - 127 + eadj;
+    float m = __uint_as_float((b & 0x7fffffu) | 0x3f800000u);
+    if (m > 1.41421356f) { m = __fmul_rn(m, 0.5f); e = e + 1; }
+    float f = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+    float f2 = __fmul_rn(f, f);
+    float s = 7.69230769e-02f;
+    s = __fmaf_rn(s, f2, 9.09090909e-02f);
+    s = __fmaf_rn(s, f2, 1.11111111e-01f);
+    s = __fmaf_rn(s, f2, 1.42857143e-01f);
+    s = __fmaf_rn(s, f2, 2.00000000e-01f);
+    s = __fmaf_rn(s, f2, 3.33333333e-01f);
+    s = __fmaf_rn(s, f2, 1.0f);
+    float l2m = __fmul_rn(__fmul_rn(2.88539008f, f), s);
+    float fe = (float)e;
+    float a = __fmul_rn(lam, fe);
+    float aerr = __fmaf_rn(lam, fe, -a);
+    float n1 = rintf(a);
+    float g = __fadd_rn(__fadd_rn(__fsub_rn(a, n1), aerr), __fmul_rn(lam, l2m));
+    float n2 = rintf(g);
+    g = __fsub_rn(g, n2);
+    float p = 1.52527338e-05f;
+    p = __fmaf_rn(p, g, 1.54035304e-04f);
+    p = __fmaf_rn(p, g, 1.33335581e-03f);
+    p = __fmaf_rn(p, g, 9.61812911e-03f);
+    p = __fmaf_rn(p, g, 5.55041087e-02f);
+    p = __fmaf_rn(p, g, 2.40226507e-01f);
+    p = __fmaf_rn(p, g, 6.93147181e-01f);
+    p = __fmaf_rn(p, g, 1.0f);
+    int nt = (int)n1 + (int)n2;
+    if (nt < -151) return 0.0f;
+    int na = nt / 2, nb = nt - na;
+    return __fmul_rn(__fmul_rn(p, dm_pow2i(na)), dm_pow2i(nb));
+}
+
+// ---------------------------------------------------------------------------
+// Workspace layouts (all offsets 256-byte aligned).
+// ---------------------------------------------------------------------------
+static inline size_t dm_align(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Header at offset 0 of backtracking and dm_match workspaces.
+struct DmWsHeader {
+    int status;                   // DM_DEV_* bits
+    int pad0[15];
+    unsigned int count[DM_MAXL + 2];   // merged tuples per level (level 0: arrivals)
+    unsigned int cap[DM_MAXL + 2];     // active merge-table capacity per level
+};
+
+struct DmPyrLayout {
+    size_t valid[DM_MAXL + 1];    // u8 [npatch(l)]
+    size_t pooled[DM_MAXL];       // f32 [npatch(l)][dh[l+1]][dw[l+1]]
+    size_t amax[DM_MAXL];         // u8 same shape
+    size_t top;                   // f32 [npatch(L)][dh[L]][dw[L]]
+    size_t a16;                   // bf16 patch operand (BF16 form)
+    size_t b16;                   // bf16 image-2 descriptors (BF16 form)
+    size_t bytes;
+};
+
+struct DmBtLayout {
+    size_t header;                // DmWsHeader
+    size_t table[DM_MAXL + 1];    // u64 merge tables, levels 1..L-1
+    size_t list[DM_MAXL + 1];     // u32 slot lists, levels 1..L-1
+    size_t cap[DM_MAXL + 1];      // max slots per level
+    size_t bestP, bestQ;          // u64 keys
+    size_t bytes;
+};
+
+void dm_pyr_layout(const DmGeom& g, int precision, DmPyrLayout* o);
+void dm_bt_layout(const DmGeom& g, DmBtLayout* o);
+size_t dm_desc_tmp_bytes(int W, int H);
+
+// Pyramid handle (host side).
+struct dm_pyramid {
+    DmGeom g;
+    int precision;
+    const unsigned char* valid[DM_MAXL + 1];
+    const float* pooled[DM_MAXL];
+    const unsigned char* amax[DM_MAXL];
+    const float* top;
+};
+
+// Smoothing taps passed by value to kernels.
+struct DmTaps {
+    int R;
+    float w[65];
+};
+
+struct DmDescParams {
+    DmTaps t1, t2, t3;
+    float scale, slope, mu;
+};
+
+// Number of kernels the library has launched in this process (host counter,
+// advanced by each launcher).
+void dm_count_launches(long long n);
+long long dm_launches();
+
+// Kernel launchers (return cudaGetLastError()).
+cudaError_t dm_launch_descriptors(const DmDescParams& prm, const float* img, int W, int H, float* desc,
+                                  float* tmpA, float* tmpB, cudaStream_t st);
+cudaError_t dm_launch_corr0_f32(const DmGeom& g, const float* d1, const float* d2, float lam, float* pooled0,
+                                unsigned char* amax0, cudaStream_t st);
+cudaError_t dm_launch_corr0_bf16(const DmGeom& g, const float* d1, const float* d2, float lam, void* a16,
+                                 void* b16, float* pooled0, unsigned char* amax0, cudaStream_t st);
+cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& p, float lam, cudaStream_t st);
+cudaError_t dm_launch_backtrack(const DmGeom& g, const dm_pyramid& p, const DmBtLayout& bl, char* ws,
+                                dm_match_t* out, int capacity, int* d_count, cudaStream_t st);

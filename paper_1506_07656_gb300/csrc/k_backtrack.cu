@@ -1,0 +1,309 @@
+// Top-down backtracking with merging (Eq. 13-15) and reciprocal verification
+// (Eq. 16).
+//
+// The tuple set starts as every position q of every existing top-level patch
+// p with score C_L(p, q) (Sec. 3.3 "Merging correspondences").  One step maps
+// a tuple (l, p, q, s) to its children (Eq. 13-14):
+//   r = q + o_i (skipped outside the domain),  t = 2r + m_i (saved argmax),
+//   child tuple (l-1, c_i, t, s + P_{l-1}(c_i, r)),
+// and tuples equal in (l-1, c_i, t) are merged keeping the highest score.
+//
+// Only a small fraction of all (patch, position) pairs is ever reached (the
+// merged frontier is typically 1-5% of a level's pooled map below the top), so
+// the frontier is kept sparse: one open-addressing table per level keyed by
+// (patch, position) with 64-bit slots (key+1) << 32 | score-bits, merged by
+// 64-bit atomicMax (scores are positive, so their IEEE bits order like the
+// values), plus a list of the slots taken, which is the next step's input.
+// The active table size is derived on the device from the previous
+// frontier's size, so nothing waits for the host.
+//
+// Path scores are summed top-down in FP32 with one rounding per level.
+// Rounding is monotone, so max over arrivals then add equals add then max:
+// merging is exact and independent of arrival order.
+//
+// At the atomic level the tuples are reduced into two arrays of packed keys
+// (score-bits << 32 | ~index) with atomicMax:
+//   BestAt(p)  per atomic patch (its own 4x4 cell of I), index = pixel of I';
+//   BestAt'(c) per 4x4 cell of I',                      index = patch*16 + offset.
+// A patch's best tuple is output iff it also wins its cell of I'.
+#include "dm_internal.cuh"
+
+namespace {
+
+constexpr int BT_BLOCK = 256;
+
+struct BtArgs {
+    DmGeom g;
+    const unsigned char* valid[DM_MAXL + 1];
+    const float* pooled[DM_MAXL];
+    const unsigned char* amax[DM_MAXL];
+    const float* top;
+    unsigned long long* table[DM_MAXL + 1];
+    unsigned int* list[DM_MAXL + 1];
+    unsigned int capmax[DM_MAXL + 1];
+    unsigned long long* bestP;
+    unsigned long long* bestQ;
+    DmWsHeader* hdr;
+};
+
+__device__ __forceinline__ unsigned int warp_agg_inc(unsigned int* ctr) {
+    unsigned int mask = __activemask();
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(mask) - 1;
+    unsigned int base = 0;
+    if (lane == leader) base = atomicAdd(ctr, (unsigned int)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    return base + __popc(mask & ((1u << lane) - 1u));
+}
+
+__device__ __forceinline__ void ht_insert(const BtArgs& a, int lvl, unsigned int cap, unsigned int key, float s) {
+    unsigned long long* tab = a.table[lvl];
+    const unsigned int sb = __float_as_uint(s);
+    const unsigned long long packed = ((unsigned long long)(key + 1u) << 32) | sb;
+    unsigned int h = (unsigned int)(((unsigned long long)(key * 2654435761u) * cap) >> 32);
+    for (unsigned int probe = 0; probe < cap; probe++) {
+        unsigned long long cur = __ldcg(tab + h);
+        if (cur == 0ull) {
+            unsigned long long prev = atomicCAS(tab + h, 0ull, packed);
+            if (prev == 0ull) {
+                unsigned int idx = warp_agg_inc(&a.hdr->count[lvl]);
+                a.list[lvl][idx] = h;
+                return;
+            }
+            cur = prev;
+        }
+        if ((unsigned int)(cur >> 32) == key + 1u) {
+            if ((unsigned int)cur < sb) atomicMax(tab + h, packed);
+            return;
+        }
+        h = (h + 1u == cap) ? 0u : h + 1u;
+    }
+    atomicOr(&a.hdr->status, DM_DEV_FRONTIER_OVERFLOW);
+}
+
+__device__ __forceinline__ void leaf_update(const BtArgs& a, int c, int tx, int ty, float s) {
+    const DmGeom& g = a.g;
+    const unsigned long long sb = (unsigned long long)__float_as_uint(s) << 32;
+    unsigned int tidx = (unsigned int)(ty * g.W2 + tx);
+    unsigned long long kp = sb | (0xffffffffu - tidx);
+    if (__ldcg(a.bestP + c) < kp) atomicMax(a.bestP + c, kp);
+    int CW = (g.W2 + 3) >> 2;
+    int cell = (ty >> 2) * CW + (tx >> 2);
+    unsigned int qidx = (unsigned int)c * 16u + (unsigned int)((ty & 3) * 4 + (tx & 3));
+    unsigned long long kq = sb | (0xffffffffu - qidx);
+    if (__ldcg(a.bestQ + cell) < kq) atomicMax(a.bestQ + cell, kq);
+}
+
+// Children of tuple (l, p, q, s); returns the number of atomic arrivals.
+__device__ __forceinline__ int expand(const BtArgs& a, int l, unsigned int cap_next, int p, int qx, int qy, float s) {
+    const DmGeom& g = a.g;
+    const int mw = g.dw[l], mh = g.dh[l];
+    const int ix = p % g.Lx, iy = p / g.Lx;
+    int arrivals = 0;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        int c = dm_child(g, l, ix, iy, i);
+        if (c < 0 || !a.valid[l - 1][c]) continue;
+        int ox = (i >= 2) ? 1 : -1, oy = (i & 1) ? 1 : -1;
+        int rx = qx + ox, ry = qy + oy;
+        if (rx < 0 || ry < 0 || rx >= mw || ry >= mh) continue;
+        long long ro = ((long long)c * mh + ry) * mw + rx;
+        int code = a.amax[l - 1][ro];
+        int tx = 2 * rx + code % 3 - 1, ty = 2 * ry + code / 3 - 1;
+        float s2 = __fadd_rn(s, a.pooled[l - 1][ro]);
+        if (l - 1 >= 1) {
+            unsigned int key = (unsigned int)c * (unsigned int)g.dsize(l - 1) + (unsigned int)(ty * g.dw[l - 1] + tx);
+            ht_insert(a, l - 1, cap_next, key, s2);
+        } else {
+            leaf_update(a, c, tx, ty, s2);
+            arrivals++;
+        }
+    }
+    return arrivals;
+}
+
+__device__ __forceinline__ void add_arrivals(const BtArgs& a, int n) {
+    // every lane of every warp reaches this point
+    int tot = __reduce_add_sync(0xffffffffu, n);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&a.hdr->count[0], (unsigned int)tot);
+}
+
+// Clear the active part of the level-`lvl` table.  Active size: 8x the
+// previous frontier (4 children per tuple, load <= 1/2), within [64, capmax].
+__global__ void k_bt_prepare(BtArgs a, int lvl, long long n_top) {
+    unsigned long long n_prev = (lvl + 1 == a.g.L) ? (unsigned long long)n_top : a.hdr->count[lvl + 1];
+    unsigned long long cap = n_prev * 8ull;
+    if (cap < 64ull) cap = 64ull;
+    if (cap > a.capmax[lvl]) cap = a.capmax[lvl];
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.hdr->cap[lvl] = (unsigned int)cap;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        a.table[lvl][i] = 0ull;
+}
+
+// Expansion of the top level: every position of every existing top patch.
+__global__ void k_bt_expand_top(BtArgs a) {
+    const DmGeom& g = a.g;
+    const int L = g.L;
+    const long long ds = g.dsize(L);
+    const long long n = (long long)g.npatch(L) * ds;
+    const unsigned int cap_next = (L - 1 >= 1) ? a.hdr->cap[L - 1] : 0u;
+    int arrivals = 0;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e - threadIdx.x < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        if (e < n) {
+            int p = (int)(e / ds);
+            int q = (int)(e % ds);
+            if (a.valid[L][p]) {
+                if (q == 0) atomicAdd(&a.hdr->count[L], (unsigned int)ds);
+                arrivals += expand(a, L, cap_next, p, q % g.dw[L], q / g.dw[L], a.top[e]);
+            }
+        }
+    }
+    if (L == 1) add_arrivals(a, arrivals);
+}
+
+// Expansion of level l < L: the merged tuples listed for level l.
+__global__ void k_bt_expand(BtArgs a, int l) {
+    const DmGeom& g = a.g;
+    const unsigned int n = a.hdr->count[l];
+    const unsigned int cap_next = (l - 1 >= 1) ? a.hdr->cap[l - 1] : 0u;
+    const unsigned int ds = (unsigned int)g.dsize(l);
+    int arrivals = 0;
+    for (unsigned int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+        unsigned int i = i0 + threadIdx.x;
+        if (i < n) {
+            unsigned long long v = __ldcg(a.table[l] + a.list[l][i]);
+            unsigned int key = (unsigned int)(v >> 32) - 1u;
+            float s = __uint_as_float((unsigned int)v);
+            int p = (int)(key / ds);
+            int t = (int)(key % ds);
+            arrivals += expand(a, l, cap_next, p, t % g.dw[l], t / g.dw[l], s);
+        }
+    }
+    if (l == 1) add_arrivals(a, arrivals);
+}
+
+// Reciprocal verification and compaction in atomic-patch order (one block).
+__global__ void __launch_bounds__(1024) k_reciprocal(BtArgs a, dm_match_t* __restrict__ out, int capacity,
+                                                     int* __restrict__ d_count) {
+    const DmGeom& g = a.g;
+    const int n0 = g.npatch(0);
+    const int CW = (g.W2 + 3) >> 2;
+    const int chunk = (n0 + blockDim.x - 1) / blockDim.x;
+    const int p0 = threadIdx.x * chunk;
+    const int p1 = min(n0, p0 + chunk);
+    __shared__ int warp_sums[32];
+    __shared__ int total;
+
+    auto survives = [&](int p, int& tx, int& ty, float& s) -> bool {
+        unsigned long long kp = a.bestP[p];
+        if (kp == 0ull) return false;
+        unsigned int tidx = 0xffffffffu - (unsigned int)kp;
+        tx = (int)(tidx % (unsigned int)g.W2);
+        ty = (int)(tidx / (unsigned int)g.W2);
+        int cell = (ty >> 2) * CW + (tx >> 2);
+        unsigned long long kq = a.bestQ[cell];
+        unsigned int qidx = 0xffffffffu - (unsigned int)kq;
+        s = __uint_as_float((unsigned int)(kp >> 32));
+        return (kq >> 32) == (kp >> 32) && qidx == (unsigned int)p * 16u + (unsigned int)((ty & 3) * 4 + (tx & 3));
+    };
+
+    int mine = 0;
+    for (int p = p0; p < p1; p++) {
+        int tx, ty;
+        float s;
+        mine += survives(p, tx, ty, s) ? 1 : 0;
+    }
+    // block exclusive scan of `mine`
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int nw = blockDim.x >> 5;
+        int w = lane < nw ? warp_sums[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int v = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += v;
+        }
+        if (lane < nw) warp_sums[lane] = wi - w;
+        if (lane == 31) total = wi;
+    }
+    __syncthreads();
+    int pos = warp_sums[warp] + incl - mine;
+    for (int p = p0; p < p1; p++) {
+        int tx, ty;
+        float s;
+        if (survives(p, tx, ty, s)) {
+            if (pos < capacity) {
+                dm_match_t m;
+                m.x1 = (float)(4 * (p % g.P0x) + 2);
+                m.y1 = (float)(4 * (p / g.P0x) + 2);
+                m.x2 = (float)tx;
+                m.y2 = (float)ty;
+                m.score = s;
+                out[pos] = m;
+            }
+            pos++;
+        }
+    }
+    if (threadIdx.x == 0) {
+        *d_count = total;
+        if (total > capacity) atomicOr(&a.hdr->status, DM_DEV_OUTPUT_OVERFLOW);
+    }
+}
+
+}  // namespace
+
+cudaError_t dm_launch_backtrack(const DmGeom& g, const dm_pyramid& py, const DmBtLayout& bl, char* ws,
+                                dm_match_t* out, int capacity, int* d_count, cudaStream_t st) {
+    BtArgs a;
+    memset(&a, 0, sizeof(a));
+    a.g = g;
+    for (int l = 0; l <= g.L; l++) a.valid[l] = py.valid[l];
+    for (int l = 0; l < g.L; l++) {
+        a.pooled[l] = py.pooled[l];
+        a.amax[l] = py.amax[l];
+    }
+    a.top = py.top;
+    for (int l = 1; l < g.L; l++) {
+        a.table[l] = reinterpret_cast<unsigned long long*>(ws + bl.table[l]);
+        a.list[l] = reinterpret_cast<unsigned int*>(ws + bl.list[l]);
+        a.capmax[l] = (unsigned int)bl.cap[l];
+    }
+    a.bestP = reinterpret_cast<unsigned long long*>(ws + bl.bestP);
+    a.bestQ = reinterpret_cast<unsigned long long*>(ws + bl.bestQ);
+    a.hdr = reinterpret_cast<DmWsHeader*>(ws + bl.header);
+
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(a.hdr, 0, sizeof(DmWsHeader), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(a.bestP, 0, sizeof(unsigned long long) * g.npatch(0), st)) != cudaSuccess) return e;
+    size_t ncell = (size_t)((g.W2 + 3) / 4) * ((g.H2 + 3) / 4);
+    if ((e = cudaMemsetAsync(a.bestQ, 0, sizeof(unsigned long long) * ncell, st)) != cudaSuccess) return e;
+
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = nsm * 8;
+    const long long n_top = (long long)g.npatch(g.L) * g.dsize(g.L);
+    for (int l = g.L; l >= 1; l--) {
+        if (l - 1 >= 1) k_bt_prepare<<<grid, BT_BLOCK, 0, st>>>(a, l - 1, n_top);
+        if (l == g.L) {
+            long long nb = (n_top + BT_BLOCK - 1) / BT_BLOCK;
+            k_bt_expand_top<<<(unsigned)(nb < grid ? nb : grid), BT_BLOCK, 0, st>>>(a);
+        } else {
+            k_bt_expand<<<grid, BT_BLOCK, 0, st>>>(a, l);
+        }
+    }
+    k_reciprocal<<<1, 1024, 0, st>>>(a, out, capacity, d_count);
+    dm_count_launches(2 * g.L);
+    return cudaGetLastError();
+}

@@ -1,0 +1,151 @@
+// Bottom-level correlation (Eq. 3-4) on the FP32 SIMT pipes, with the first
+// max-pooling + subsampling (Eq. 8-9) and rectification (Eq. 11) fused into
+// the epilogue.  The unpooled level-0 volume (P0 x W2 x H2 values) is never
+// written to memory: only P_0(p, r) = (max_{m} C0(p, 2r+m))^lambda and its
+// argmax code.
+//
+// Tiling.  A CTA owns 32 atomic patches (8 warps x 4) and a tile of 8 x 15
+// pooled outputs, i.e. C0 at 17 rows x 32 columns of I' positions (the
+// overlap of neighbouring 3x3 windows costs 32*17/(30*16) = 13% extra
+// correlations).  Lane j of a warp owns C0 column j for its warp's 4 patches
+// and all 17 rows: 68 accumulators.  The image-2 descriptor halo (20 rows x
+// 35 columns x 9 channels) and the 32 patch vectors sit in shared memory.
+//
+// Summation order (identical to the FP32 reference): per output,
+// acc = fma(a, b, acc) over dx = 0..3, then channel c = 0..8, then dy = 0..3,
+// starting from 0, then acc * (1/16).  Terms outside either image are zero
+// and leave acc unchanged (all operands are non-negative).  The loop order
+// (dx, c) outer / dy inner lets one column of 20 halo values in registers
+// feed all 4 dy offsets of all 17 rows.
+#include "dm_internal.cuh"
+
+namespace {
+
+constexpr int PATCHES = 32;   // per CTA
+constexpr int CROWS = 17;     // C0 rows per CTA
+constexpr int CCOLS = 32;     // C0 columns per CTA (one per lane)
+constexpr int HROWS = CROWS + 3;
+constexpr int HCOLS = CCOLS + 3;
+constexpr int PW = 15;        // pooled columns per CTA
+constexpr int PH = 8;         // pooled rows per CTA
+
+__global__ void __launch_bounds__(256, 2)
+k_corr0_f32(DmGeom g, const float* __restrict__ d1, const float* __restrict__ d2, float lam,
+            float* __restrict__ pooled0, unsigned char* __restrict__ amax0) {
+    __shared__ float halo[HROWS * HCOLS * 9];
+    __shared__ __align__(16) float a_s[144 * PATCHES];   // [(dx*9+c)*4+dy][patch]
+
+    const int tiles_x = (g.dw[1] + PW - 1) / PW;
+    const int rx0 = (blockIdx.x % tiles_x) * PW;
+    const int ry0 = (blockIdx.x / tiles_x) * PH;
+    const int p_base = blockIdx.y * PATCHES;
+    const int n0 = g.P0x * g.P0y;
+    const int W2 = g.W2, H2 = g.H2;
+    const int cx0 = 2 * rx0 - 1, cy0 = 2 * ry0 - 1;     // C0 tile origin (may be -1)
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    // image-2 halo: pixels [cx0-2, cx0+33) x [cy0-2, cy0+18), zero outside I'
+    for (int k = tid; k < HROWS * HCOLS * 9; k += 256) {
+        int c = k % 9, pix = k / 9;
+        int hx = pix % HCOLS, hy = pix / HCOLS;
+        int x = cx0 - 2 + hx, y = cy0 - 2 + hy;
+        float v = 0.0f;
+        if (x >= 0 && y >= 0 && x < W2 && y < H2) v = d2[((long long)y * W2 + x) * 9 + c];
+        halo[k] = v;
+    }
+    // patch vectors: window [p-2, p+1]^2 of I, zero outside I (partial patches)
+    for (int k = tid; k < 144 * PATCHES; k += 256) {
+        int pl = k % PATCHES, kk = k / PATCHES;
+        int dy = kk % 4, c = (kk / 4) % 9, dx = kk / 36;
+        int p = p_base + pl;
+        float v = 0.0f;
+        if (p < n0) {
+            int px = 4 * (p % g.P0x) + 2, py = 4 * (p / g.P0x) + 2;
+            int x = px - 2 + dx, y = py - 2 + dy;
+            if (x < g.W1 && y < g.H1) v = d1[((long long)y * g.W1 + x) * 9 + c];
+        }
+        a_s[k] = v;
+    }
+    __syncthreads();
+
+    float acc[4][CROWS];
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+#pragma unroll
+        for (int r = 0; r < CROWS; r++) acc[q][r] = 0.0f;
+
+    const float4* a4p = reinterpret_cast<const float4*>(a_s) + warp;   // 4 patches of this warp
+#pragma unroll 1
+    for (int dx = 0; dx < 4; dx++) {
+#pragma unroll 1
+        for (int c = 0; c < 9; c++) {
+            float h[HROWS];
+#pragma unroll
+            for (int r = 0; r < HROWS; r++) h[r] = halo[(r * HCOLS + lane + dx) * 9 + c];
+#pragma unroll
+            for (int dy = 0; dy < 4; dy++) {
+                float4 a = a4p[((dx * 9 + c) * 4 + dy) * (PATCHES / 4)];
+#pragma unroll
+                for (int r = 0; r < CROWS; r++) {
+                    acc[0][r] = __fmaf_rn(a.x, h[r + dy], acc[0][r]);
+                    acc[1][r] = __fmaf_rn(a.y, h[r + dy], acc[1][r]);
+                    acc[2][r] = __fmaf_rn(a.z, h[r + dy], acc[2][r]);
+                    acc[3][r] = __fmaf_rn(a.w, h[r + dy], acc[3][r]);
+                }
+            }
+        }
+    }
+
+    // Epilogue: C0 = acc/16, out-of-domain positions masked, 3x3/2 max-pool
+    // with first-strict-max argmax (scan my = -1..1, mx = -1..1), power.
+    const int cx = cx0 + lane;
+    const bool col_in = (cx >= 0 && cx < W2);
+    const int k = (lane - 1) >> 1;                 // pooled column owned by odd lanes
+    const int rx = rx0 + k;
+    const bool writer = (lane & 1) && lane <= 2 * PW - 1 && rx < g.dw[1];
+    const int mw = g.dw[1], mh = g.dh[1];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        float v[CROWS];
+#pragma unroll
+        for (int r = 0; r < CROWS; r++) {
+            int cy = cy0 + r;
+            v[r] = (col_in && cy >= 0 && cy < H2) ? __fmul_rn(acc[q][r], 0.0625f) : -INFINITY;
+        }
+        const int p = p_base + warp * 4 + q;
+#pragma unroll
+        for (int i = 0; i < PH; i++) {
+            float w[9];
+#pragma unroll
+            for (int my = 0; my < 3; my++) {
+                float c0 = v[2 * i + my];
+                w[my * 3 + 0] = __shfl_up_sync(0xffffffffu, c0, 1);
+                w[my * 3 + 1] = c0;
+                w[my * 3 + 2] = __shfl_down_sync(0xffffffffu, c0, 1);
+            }
+            const int ry = ry0 + i;
+            if (writer && ry < mh && p < n0) {
+                float best = w[0];
+                int code = 0;
+#pragma unroll
+                for (int j = 1; j < 9; j++)
+                    if (w[j] > best) { best = w[j]; code = j; }
+                long long o = ((long long)p * mh + ry) * mw + rx;
+                pooled0[o] = dm_powf(best, lam);
+                amax0[o] = (unsigned char)code;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t dm_launch_corr0_f32(const DmGeom& g, const float* d1, const float* d2, float lam, float* pooled0,
+                                unsigned char* amax0, cudaStream_t st) {
+    int tiles = ((g.dw[1] + PW - 1) / PW) * ((g.dh[1] + PH - 1) / PH);
+    int pblocks = (g.P0x * g.P0y + PATCHES - 1) / PATCHES;
+    dim3 grid(tiles, pblocks);
+    k_corr0_f32<<<grid, 256, 0, st>>>(g, d1, d2, lam, pooled0, amax0);
+    dm_count_launches(1);
+    return cudaGetLastError();
+}

@@ -1,0 +1,296 @@
+"""Python binding of the C ABI in ``include/dm.h`` (ctypes; argument marshalling only).
+
+Every step of the method runs in the CUDA library ``libdm.so``; this module
+only converts torch tensors to pointers and sizes.  PyTorch provides device
+memory and streams.  If the library is missing or fails to load, every call
+raises -- there is no CPU fallback.
+
+Names follow the C ABI: dm_create, dm_descriptors, dm_correlate_pyramid,
+dm_backtrack, dm_match, dm_match_host, ...; ``Context`` bundles them.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdm.so")
+
+DM_OK, DM_EINVAL, DM_ENOMEM, DM_ECUDA, DM_ETIMEOUT, DM_EUNSUPPORTED, DM_EOVERFLOW = range(7)
+DM_FP32, DM_BF16 = 0, 1
+DM_DEV_FRONTIER_OVERFLOW, DM_DEV_OUTPUT_OVERFLOW = 1, 2
+STATUS_NAMES = {0: "DM_OK", 1: "DM_EINVAL", 2: "DM_ENOMEM", 3: "DM_ECUDA", 4: "DM_ETIMEOUT",
+                5: "DM_EUNSUPPORTED", 6: "DM_EOVERFLOW"}
+MAXL = 30
+
+
+class DmConfig(C.Structure):
+    _fields_ = [("nu1", C.c_float), ("nu2", C.c_float), ("nu3", C.c_float), ("slope", C.c_float),
+                ("mu", C.c_float), ("lambda_", C.c_float), ("image_scale", C.c_float), ("precision", C.c_int)]
+
+
+class DmMatch(C.Structure):
+    _fields_ = [("x1", C.c_float), ("y1", C.c_float), ("x2", C.c_float), ("y2", C.c_float), ("score", C.c_float)]
+
+
+MATCH_BYTES = C.sizeof(DmMatch)
+
+# Exported symbols and their signatures (restype dm_status = c_int unless noted).
+_SIGS = {
+    "dm_config_default": (None, [C.POINTER(DmConfig)]),
+    "dm_create": (C.c_int, [C.POINTER(DmConfig), C.c_int, C.POINTER(C.c_void_p)]),
+    "dm_destroy": (C.c_int, [C.c_void_p]),
+    "dm_last_error": (C.c_char_p, [C.c_void_p]),
+    "dm_geometry": (C.c_int, [C.c_int] * 4 + [C.POINTER(C.c_int)] * 3 + [C.c_void_p, C.c_void_p]),
+    "dm_workspace_bytes": (C.c_int, [C.c_void_p] + [C.c_int] * 4 + [C.POINTER(C.c_size_t)] * 4),
+    "dm_descriptors": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t,
+                                 C.c_void_p]),
+    "dm_correlate_pyramid": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int,
+                                       C.c_void_p, C.c_size_t, C.POINTER(C.c_void_p), C.c_void_p]),
+    "dm_pyramid_level": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                   C.POINTER(C.c_void_p), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                   C.POINTER(C.c_int)]),
+    "dm_pyramid_free": (C.c_int, [C.c_void_p]),
+    "dm_backtrack": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_int, C.c_void_p,
+                               C.c_void_p]),
+    "dm_match": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                           C.c_size_t, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "dm_match_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                                C.c_size_t, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_void_p]),
+    "dm_read_status": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.c_void_p, C.c_int, C.c_void_p]),
+    "dm_timing_start": (C.c_int, [C.c_void_p, C.c_int]),
+    "dm_timing_read": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
+}
+NSTAGES = 4
+STAGES = ("descriptors", "level0_correlation", "levels", "backtracking")
+
+_LIB = None
+
+
+def load(build_if_missing: bool = True):
+    """Load libdm.so (building it with nvcc first if absent); raise if impossible."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library {LIB_PATH} is missing; run paper_1506_07656_gb300.build.build()")
+        from . import build as _b
+        _b.build()
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+class DmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(ctx, st: int, what: str):
+    if st != DM_OK:
+        msg = load().dm_last_error(ctx).decode() if ctx else ""
+        raise DmError(st, f"{what}: {msg}")
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _dptr(t) -> int:
+    return int(t.data_ptr())
+
+
+# ------------------------------------------------------------------------- #
+# Thin wrappers with the C names                                             #
+# ------------------------------------------------------------------------- #
+def dm_config_default() -> DmConfig:
+    cfg = DmConfig()
+    load().dm_config_default(C.byref(cfg))
+    return cfg
+
+
+def dm_create(cfg: DmConfig | None = None, device: int = 0) -> int:
+    h = C.c_void_p()
+    st = load().dm_create(C.byref(cfg) if cfg is not None else None, device, C.byref(h))
+    if st != DM_OK:
+        raise DmError(st, "dm_create")
+    return h.value
+
+
+def dm_destroy(ctx: int) -> None:
+    load().dm_destroy(ctx)
+
+
+def dm_geometry(W1, H1, W2, H2):
+    L, n0, n = C.c_int(), C.c_int(), C.c_int()
+    dw = (C.c_int * (MAXL + 2))()
+    dh = (C.c_int * (MAXL + 2))()
+    st = load().dm_geometry(W1, H1, W2, H2, C.byref(L), C.byref(n0), C.byref(n), dw, dh)
+    if st != DM_OK:
+        raise DmError(st, f"dm_geometry {W1}x{H1}/{W2}x{H2}")
+    return dict(L=L.value, n_patch0=n0.value, n_patch=n.value, dw=list(dw[:L.value + 2]), dh=list(dh[:L.value + 2]))
+
+
+def dm_workspace_bytes(ctx, W1, H1, W2, H2):
+    a, b, c, d = C.c_size_t(), C.c_size_t(), C.c_size_t(), C.c_size_t()
+    st = load().dm_workspace_bytes(ctx, W1, H1, W2, H2, C.byref(a), C.byref(b), C.byref(c), C.byref(d))
+    _check(ctx, st, "dm_workspace_bytes")
+    return dict(desc=a.value, pyramid=b.value, backtrack=c.value, match=d.value)
+
+
+def dm_descriptors(ctx, d_img, d_desc, d_tmp, stream=None):
+    H, W = d_img.shape
+    st = load().dm_descriptors(ctx, _dptr(d_img), W, H, _dptr(d_desc), _dptr(d_tmp), d_tmp.numel() * d_tmp.element_size(),
+                               _stream_ptr(stream))
+    _check(ctx, st, "dm_descriptors")
+
+
+def dm_correlate_pyramid(ctx, d_desc1, d_desc2, d_ws, stream=None) -> int:
+    H1, W1, _ = d_desc1.shape
+    H2, W2, _ = d_desc2.shape
+    h = C.c_void_p()
+    st = load().dm_correlate_pyramid(ctx, _dptr(d_desc1), W1, H1, _dptr(d_desc2), W2, H2, _dptr(d_ws),
+                                     d_ws.numel() * d_ws.element_size(), C.byref(h), _stream_ptr(stream))
+    _check(ctx, st, "dm_correlate_pyramid")
+    return h.value
+
+
+def dm_pyramid_level(pyr: int, level: int):
+    vals, am, valid = C.c_void_p(), C.c_void_p(), C.c_void_p()
+    n, mw, mh = C.c_int(), C.c_int(), C.c_int()
+    st = load().dm_pyramid_level(pyr, level, C.byref(vals), C.byref(am), C.byref(valid), C.byref(n), C.byref(mw),
+                                 C.byref(mh))
+    if st != DM_OK:
+        raise DmError(st, "dm_pyramid_level")
+    return dict(vals=vals.value, argmax=am.value, valid=valid.value, n=n.value, mw=mw.value, mh=mh.value)
+
+
+def dm_pyramid_free(pyr: int) -> None:
+    load().dm_pyramid_free(pyr)
+
+
+def dm_backtrack(ctx, pyr, d_ws, d_out, d_count, stream=None):
+    cap = d_out.numel() * d_out.element_size() // MATCH_BYTES
+    st = load().dm_backtrack(ctx, pyr, _dptr(d_ws), d_ws.numel() * d_ws.element_size(), _dptr(d_out), cap,
+                             _dptr(d_count), _stream_ptr(stream))
+    _check(ctx, st, "dm_backtrack")
+
+
+def dm_match(ctx, d_img1, d_img2, d_ws, d_out, d_count, stream=None):
+    H1, W1 = d_img1.shape
+    H2, W2 = d_img2.shape
+    cap = d_out.numel() * d_out.element_size() // MATCH_BYTES
+    st = load().dm_match(ctx, _dptr(d_img1), W1, H1, _dptr(d_img2), W2, H2, _dptr(d_ws),
+                         d_ws.numel() * d_ws.element_size(), _dptr(d_out), cap, _dptr(d_count), _stream_ptr(stream))
+    _check(ctx, st, "dm_match")
+
+
+def dm_match_host(ctx, h_img1, h_img2, d_ws, h_out, stream=None) -> int:
+    """h_img*: pinned (or pageable) float32 CPU tensors; h_out: CPU tensor of capacity*5 float32."""
+    H1, W1 = h_img1.shape
+    H2, W2 = h_img2.shape
+    cap = h_out.numel() * h_out.element_size() // MATCH_BYTES
+    cnt = C.c_int()
+    st = load().dm_match_host(ctx, _dptr(h_img1), W1, H1, _dptr(h_img2), W2, H2, _dptr(d_ws),
+                              d_ws.numel() * d_ws.element_size(), _dptr(h_out), cap, C.byref(cnt),
+                              _stream_ptr(stream))
+    _check(ctx, st, "dm_match_host")
+    return cnt.value
+
+
+def dm_read_status(ctx, d_ws, n_levels: int, stream=None):
+    status = C.c_int()
+    reached = (C.c_longlong * n_levels)()
+    st = load().dm_read_status(ctx, _dptr(d_ws), C.byref(status), reached, n_levels, _stream_ptr(stream))
+    _check(ctx, st, "dm_read_status")
+    return status.value, list(reached)
+
+
+def dm_timing_start(ctx, max_calls: int) -> None:
+    _check(ctx, load().dm_timing_start(ctx, max_calls), "dm_timing_start")
+
+
+def dm_timing_read(ctx):
+    ms = (C.c_double * NSTAGES)()
+    n = C.c_int()
+    launches = C.c_longlong()
+    _check(ctx, load().dm_timing_read(ctx, ms, C.byref(n), C.byref(launches)), "dm_timing_read")
+    return dict(zip(STAGES, list(ms))), n.value, launches.value
+
+
+# ------------------------------------------------------------------------- #
+# Convenience                                                                #
+# ------------------------------------------------------------------------- #
+class Context:
+    """A library context plus cached device workspaces (allocated by torch)."""
+
+    def __init__(self, precision: int = DM_FP32, device: int = 0, **params):
+        import torch
+        self.torch = torch
+        cfg = dm_config_default()
+        for k, v in params.items():
+            setattr(cfg, "lambda_" if k in ("lam", "lambda") else k, float(v))
+        cfg.precision = precision
+        self.cfg = cfg
+        self.device = device
+        self.ctx = dm_create(cfg, device)
+        self._ws = {}
+
+    def close(self):
+        if self.ctx:
+            dm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace(self, kind: str, W1, H1, W2, H2):
+        key = (kind, W1, H1, W2, H2)
+        if key not in self._ws:
+            nbytes = dm_workspace_bytes(self.ctx, W1, H1, W2, H2)[kind]
+            self._ws[key] = self.torch.empty(max(nbytes, 256), dtype=self.torch.uint8, device=f"cuda:{self.device}")
+        return self._ws[key]
+
+    def match(self, img1, img2, stream=None):
+        """Matches as a float32 tensor [n][5] (x1, y1, x2, y2, score) on the device."""
+        torch = self.torch
+        dev = f"cuda:{self.device}"
+        i1 = torch.as_tensor(img1, dtype=torch.float32, device=dev).contiguous()
+        i2 = torch.as_tensor(img2, dtype=torch.float32, device=dev).contiguous()
+        H1, W1 = i1.shape
+        H2, W2 = i2.shape
+        ws = self.workspace("match", W1, H1, W2, H2)
+        n0 = dm_geometry(W1, H1, W2, H2)["n_patch0"]
+        out = torch.empty((max(n0, 1), 5), dtype=torch.float32, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+        dm_match(self.ctx, i1, i2, ws, out, cnt, stream)
+        n = int(cnt.item())
+        return out[:n]
+
+    def status(self, W1, H1, W2, H2, kind="match"):
+        L = dm_geometry(W1, H1, W2, H2)["L"]
+        return dm_read_status(self.ctx, self.workspace(kind, W1, H1, W2, H2), L + 1)
+
+
+def exported_symbols() -> list:
+    return list(_SIGS.keys())
+
+
+def to_numpy_matches(t) -> np.ndarray:
+    return t.detach().cpu().numpy().astype(np.float64)
