@@ -173,6 +173,32 @@ dm_status dm_match_host(dm_ctx* ctx, const float* h_img1, int W1, int H1, const 
 dm_status dm_read_status(dm_ctx* ctx, const void* d_ws, int* status, long long* reached, int n_reached,
                          void* stream);
 
+/* Backtracking without any caller workspace.
+ * No counterpart in the paper: this entry point exists for callers that cannot
+ * allocate device memory or hand the library a workspace -- plug-ins inside a
+ * host application that owns all device memory and forbids allocations after
+ * start-up, or latency-critical loops that must never call cudaMalloc (it can
+ * synchronise the device).  It does what dm_backtrack does, with the same
+ * kernels and results, but its scratch (merge tables, slot lists, BestAt /
+ * BestAt' keys, status header) is a fixed device array of
+ * DM_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads the
+ * library holds until the process exits.  The caller still passes the pyramid
+ * (input) and d_out / d_count (outputs), as for dm_backtrack.
+ *   - Pairs whose backtracking scratch (backtrack_bytes of dm_workspace_bytes)
+ *     exceeds DM_NOALLOC_SCRATCH_BYTES are refused with DM_ENOMEM and a message
+ *     (32 MiB holds pairs up to about 128 x 96 pixels).
+ *   - It calls no cudaMalloc, cudaFree or other allocating routine.  Its first
+ *     call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *     and caches it; make that first call before any stream capture.
+ *   - Every call uses the same array and leaves its contents behind; each call
+ *     clears what must start empty.  Calls that overlap on the GPU (other
+ *     streams, other threads) race on the array: serialise them.
+ *   - The device status word is not readable through dm_read_status; an output
+ *     overflow still shows as *d_count > capacity. */
+#define DM_NOALLOC_SCRATCH_BYTES (32u << 20)
+dm_status dm_backtrack_noalloc(dm_ctx* ctx, const dm_pyramid* pyr, dm_match_t* d_out, int capacity, int* d_count,
+                               void* stream);
+
 /* Stage timing (tracing).  After dm_timing_start(ctx, max_calls), each of the
  * next max_calls dm_match calls records CUDA events on its stream at the stage
  * boundaries: descriptors | level-0 correlation | levels >= 1 | backtracking.

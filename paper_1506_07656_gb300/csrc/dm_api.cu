@@ -151,6 +151,9 @@ dm_status check_geom(dm_ctx* c, int W1, int H1, int W2, int H2, DmGeom* g) {
 
 }  // namespace
 
+dm_status dm_set_error(dm_ctx* ctx, dm_status s, const char* msg) { return fail(ctx, s, "%s", msg); }
+int dm_ctx_device(const dm_ctx* ctx) { return ctx->device; }
+
 // ---------------------------------------------------------------------------
 // Geometry and layouts
 // ---------------------------------------------------------------------------

@@ -168,6 +168,10 @@ struct DmDescParams {
     float scale, slope, mu;
 };
 
+// Record an error message on a context and return `s`; device of a context.
+dm_status dm_set_error(dm_ctx* ctx, dm_status s, const char* msg);
+int dm_ctx_device(const dm_ctx* ctx);
+
 // Number of kernels the library has launched in this process (host counter,
 // advanced by each launcher).
 void dm_count_launches(long long n);

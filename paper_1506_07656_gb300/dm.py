@@ -60,6 +60,7 @@ _SIGS = {
     "dm_match_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                 C.c_size_t, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_void_p]),
     "dm_read_status": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.c_void_p, C.c_int, C.c_void_p]),
+    "dm_backtrack_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "dm_timing_start": (C.c_int, [C.c_void_p, C.c_int]),
     "dm_timing_read": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
 }
@@ -217,6 +218,16 @@ def dm_read_status(ctx, d_ws, n_levels: int, stream=None):
     st = load().dm_read_status(ctx, _dptr(d_ws), C.byref(status), reached, n_levels, _stream_ptr(stream))
     _check(ctx, st, "dm_read_status")
     return status.value, list(reached)
+
+
+def dm_backtrack_noalloc(ctx, pyr, d_out, d_count, stream=None):
+    """Backtracking with the library's fixed internal scratch (no workspace argument)."""
+    cap = d_out.numel() * d_out.element_size() // MATCH_BYTES
+    st = load().dm_backtrack_noalloc(ctx, pyr, _dptr(d_out), cap, _dptr(d_count), _stream_ptr(stream))
+    _check(ctx, st, "dm_backtrack_noalloc")
+
+
+NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 def dm_timing_start(ctx, max_calls: int) -> None:
