@@ -192,24 +192,9 @@ def run_reference(a):
 # --------------------------------------------------------------------------- #
 # Our arm                                                                    #
 # --------------------------------------------------------------------------- #
-def run_ours(a):
-    import torch
-    import torch.distributed as dist
-
-    from paper_1506_07656_gb300 import dm
-
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    dm.load()
+def _measure(dm, torch, dist, ctx, pair, a, world, local, stream):
+    """Time K dm_match steps on device-resident images, then K dm_match_host steps."""
     W, H = a.width, a.height
-    prec_name = "fp32" if a.precision == "auto" else a.precision
-    prec = dm.DM_BF16 if prec_name == "bf16" else dm.DM_FP32
-    ctx = dm.Context(prec, device=local)
-    pair = _pair(W, H, 1000 + rank)
     d1 = torch.from_numpy(pair.img1).cuda()
     d2 = torch.from_numpy(pair.img2).cuda()
     ws = ctx.workspace("match", W, H, W, H)
@@ -217,14 +202,11 @@ def run_ours(a):
     n0 = geo["n_patch0"]
     out = torch.empty((n0, 5), dtype=torch.float32, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
-    stream = torch.cuda.current_stream()
-
     for _ in range(a.warmup):
         dm.dm_match(ctx.ctx, d1, d2, ws, out, cnt, stream)
     torch.cuda.synchronize()
     status, reached = dm.dm_read_status(ctx.ctx, ws, geo["L"] + 1, stream)
     n_matches = int(cnt.item())
-
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -244,8 +226,6 @@ def run_ours(a):
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
-    value = world * a.steps / (ms_max / 1e3)
-
     # end to end through the public API with host buffers (copies inside)
     h1 = torch.from_numpy(pair.img1).pin_memory()
     h2 = torch.from_numpy(pair.img2).pin_memory()
@@ -261,71 +241,119 @@ def run_ours(a):
     te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * a.steps / float(te.item())
+    return dict(ms=ms_max, value=world * a.steps / (ms_max / 1e3), stages={k: v / max(ncalls, 1) for k, v in stages.items()},
+                launches=launches, e2e=world * a.steps / float(te.item()), status=status, reached=reached,
+                matches=n_matches, clocks=clk.summary(), geo=geo)
+
+
+def _rooflines(r, prec_bf16, W, H, peaks, nsm):
+    geo = r["geo"]
+    n0 = geo["n_patch0"]
+    corr_ms = r["stages"]["level0_correlation"]
+    flop = 2.0 * 144 * n0 * W * H
+    achieved = flop / (corr_ms / 1e3) / 1e12
+    if not prec_bf16:
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = nsm * 128 * 2 * sm_max * 1e6 / 1e12
+        corr = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_corr0_f32 (level-0 correlation + fused pool/power, FP32 FMA pipes)",
+                "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
+                "algorithmic_flop_per_launch": flop, "launch_ms": corr_ms}
+    else:
+        peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        corr = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_corr0_tc (level-0 correlation on tcgen05, BF16 in / FP32 accumulate, fused pool/power)",
+                "peak_source": ("bf16_tflops_sustained of measured" if "bf16_tflops_sustained" in peaks
+                                else "fallback 1.7 PFLOP/s sustained"),
+                "algorithmic_flop_per_launch": flop, "launch_ms": corr_ms}
+    # pyramid levels >= 1: read every pooled map of levels 0..L-1 once (4 B), write the
+    # pooled maps (4 B) + argmax (1 B) of levels 1..L-1 and the top (4 B)
+    L, dw, dh, n1 = geo["L"], geo["dw"], geo["dh"], geo["n_patch"]
+    rd = sum((n0 if l == 0 else n1) * dw[l + 1] * dh[l + 1] * 4 for l in range(L))
+    wr = sum(n1 * dw[l + 1] * dh[l + 1] * 5 for l in range(1, L)) + n1 * dw[L] * dh[L] * 4
+    lev_ms = r["stages"]["levels"]
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    gbs = (rd + wr) / (lev_ms / 1e3) / 1e9
+    lev = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak, "traffic": None,
+           "kernel": "k_level_pool_tiled + k_level_top (pyramid levels >= 1)",
+           "peak_source": "hbm_gbs of measured" if "hbm_gbs" in peaks else "fallback 6.8 TB/s",
+           "algorithmic_bytes_per_launch_set": rd + wr, "launch_ms": lev_ms}
+    return corr, lev
+
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1506_07656_gb300 import dm
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dm.load()
+    W, H = a.width, a.height
+    pair = _pair(W, H, 1000 + rank)
+    stream = torch.cuda.current_stream()
+    precs = ["fp32", "bf16"] if a.precision == "auto" else [a.precision]
+    res = {}
+    for pn in precs:
+        ctx = dm.Context(dm.DM_BF16 if pn == "bf16" else dm.DM_FP32, device=local)
+        res[pn] = _measure(dm, torch, dist, ctx, pair, a, world, local, stream)
+        ctx.close()
+        del ctx
+        torch.cuda.empty_cache()
+    head = "bf16" if "bf16" in res else precs[0]
+    r = res[head]
 
     if rank == 0:
         peaks = {}
         pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
         if os.path.exists(pk):
             peaks = json.load(open(pk))
-        props = torch.cuda.get_device_properties(local)
-        nsm = props.multi_processor_count
-        corr_ms = stages["level0_correlation"] / max(ncalls, 1)
-        flop = 2.0 * 144 * n0 * W * H
-        achieved = flop / (corr_ms / 1e3) / 1e12
-        if prec == dm.DM_FP32:
-            sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-            peak = nsm * 128 * 2 * sm_max * 1e6 / 1e12
-            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": None, "kernel": "k_corr0_f32 (level-0 correlation + fused pool/power)",
-                    "peak_source": f"FP32 FMA pipes: {nsm} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz (nominal max clock)",
-                    "algorithmic_flop_per_launch": flop, "launch_ms": corr_ms}
-        else:
-            peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
-            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": None, "kernel": "level-0 correlation on tcgen05 (BF16)",
-                    "peak_source": "bf16_tflops_sustained of measured" if peaks else "fallback 1.7 PFLOP/s sustained",
-                    "algorithmic_flop_per_launch": flop, "launch_ms": corr_ms}
-        # pyramid levels >= 1: algorithmic bytes = read every pooled map of levels 0..L-1 once,
-        # write pooled maps (4 B) + argmax (1 B) of levels 1..L-1 and the top (4 B)
-        L = geo["L"]
-        dw, dh = geo["dw"], geo["dh"]
-        n1 = geo["n_patch"]
-        rd = sum((n0 if l == 0 else n1) * dw[l + 1] * dh[l + 1] * 4 for l in range(L))
-        wr = sum(n1 * dw[l + 1] * dh[l + 1] * 5 for l in range(1, L)) + n1 * dw[L] * dh[L] * 4
-        lev_ms = stages["levels"] / max(ncalls, 1)
-        hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-        levels_gbs = (rd + wr) / (lev_ms / 1e3) / 1e9
-
+        nsm = torch.cuda.get_device_properties(local).multi_processor_count
+        corr, lev = _rooflines(r, head == "bf16", W, H, peaks, nsm)
+        # the dominant kernel of the headline path gets the roofline object
+        dominant = corr if r["stages"]["level0_correlation"] >= r["stages"]["levels"] else lev
         cpu = None
         if world == 1 and not a.no_cpu_baseline:
             rate, cores, sample, _, _ = oracle_sample_rate(pair)
             cpu = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": sample}
-        clocks = clk.summary()
+        geo = r["geo"]
+        paths = {}
+        for pn, rr in res.items():
+            c2, l2 = _rooflines(rr, pn == "bf16", W, H, peaks, nsm)
+            paths[pn] = {"pairs_per_s": rr["value"], "ms_per_step": rr["ms"] / a.steps, "stages_ms": rr["stages"],
+                         "e2e_pairs_per_s": rr["e2e"], "level0": {"achieved": c2["achieved"], "frac": c2["frac"],
+                                                                 "bound": c2["bound"]},
+                         "levels_hbm_frac": l2["frac"], "matches": rr["matches"], "device_status": rr["status"]}
         line = {
-            "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if prec == dm.DM_FP32 else "bf16", "data": "synthetic",
+            "metric": METRIC, "value": r["value"], "unit": "pairs/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": r["ms"] / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16" if head == "bf16" else "f32", "data": "synthetic",
             "config": {"workload": f"one {W}x{H} pair per GPU per step, seeded 4-octave value noise, smooth warp "
-                                   f"max 120 px (+5% gain, sigma 0.01 noise)",
-                       "width": W, "height": H, "precision": prec_name, "L": L, "atomic_patches": n0,
+                                   f"max 120 px (+5% gain, sigma 0.01 noise); level-0 correlation in "
+                                   f"{'BF16 on tcgen05 tensor cores, FP32 accumulation' if head == 'bf16' else 'FP32'}, "
+                                   f"pyramid and backtracking in FP32",
+                       "width": W, "height": H, "precision": head, "L": geo["L"], "atomic_patches": geo["n_patch0"],
                        "l2": "working set ~21 GB per pair >> 126 MB L2; no flush needed",
-                       "matches": n_matches, "device_status": status,
-                       "merged_tuples_per_level": reached},
-            "roofline": roof,
-            "levels_hbm": {"achieved": levels_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": levels_gbs / hbm_peak,
-                           "algorithmic_bytes": rd + wr, "ms": lev_ms},
-            "stages_ms": {k: v / max(ncalls, 1) for k, v in stages.items()},
+                       "matches": r["matches"], "device_status": r["status"],
+                       "merged_tuples_per_level": r["reached"]},
+            "roofline": dominant,
+            "rooflines": {"level0": corr, "levels": lev},
+            "paths": paths,
+            "stages_ms": r["stages"],
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": 2 * W * H * 4,
-                    "d2h_bytes_per_step": n0 * 20 + 4},
-            "gpu_launches": launches,
-            "clocks": clocks,
+            "e2e": {"value": r["e2e"], "unit": "pairs/s", "h2d_bytes_per_step": 2 * W * H * 4,
+                    "d2h_bytes_per_step": geo["n_patch0"] * 20 + 4},
+            "gpu_launches": r["launches"],
+            "clocks": r["clocks"],
         }
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
-    ctx.close()
     return 0
 
 

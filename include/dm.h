@@ -80,6 +80,7 @@ typedef struct dm_pyramid dm_pyramid;  /* host-side view of a pyramid in a works
 #define DM_DEV_OK 0
 #define DM_DEV_FRONTIER_OVERFLOW 1     /* a merge table filled up during backtracking */
 #define DM_DEV_OUTPUT_OVERFLOW 2       /* more matches than the output capacity       */
+#define DM_DEV_TIMEOUT 4               /* a bounded wait inside a pyramid kernel gave up */
 
 /* Fill *cfg with the paper's parameters and DM_FP32. */
 void dm_config_default(dm_config* cfg);
@@ -165,8 +166,9 @@ dm_status dm_match(dm_ctx* ctx, const float* d_img1, int W1, int H1, const float
 dm_status dm_match_host(dm_ctx* ctx, const float* h_img1, int W1, int H1, const float* h_img2, int W2, int H2,
                         void* d_ws, size_t ws_bytes, dm_match_t* h_out, int capacity, int* h_count, void* stream);
 
-/* Synchronise `stream` and read the header of a backtracking (or dm_match)
- * workspace: *status = the device status word (DM_DEV_* bits, 0 = fine);
+/* Synchronise `stream` and read the header at offset 0 of a pyramid,
+ * backtracking or dm_match workspace: *status = DM_DEV_* bits (0 = fine;
+ * DM_DEV_TIMEOUT if a bounded device-side wait of the pyramid step gave up);
  * reached[l] (l = 0..n_reached-1, may be NULL) = number of distinct merged
  * tuples at level l during the last backtracking (level 0: atomic tuples
  * before merging by pixel, i.e. arrivals). */

@@ -126,11 +126,12 @@ dm_status run_descriptors(dm_ctx* c, const float* img, int W, int H, float* desc
 }
 
 dm_status run_pyramid(dm_ctx* c, const DmGeom& g, const float* d1, const float* d2, char* base, const DmPyrLayout& pl,
-                      dm_pyramid* py, cudaStream_t st) {
+                      dm_pyramid* py, int* d_status, cudaStream_t st) {
     fill_pyramid(py, g, c->cfg.precision, pl, base);
     cudaError_t e;
+    if ((e = cudaMemsetAsync(d_status, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(c, e, "clear status");
     if (c->cfg.precision == DM_BF16) {
-        e = dm_launch_corr0_bf16(g, d1, d2, c->cfg.lambda, base + pl.a16, base + pl.b16,
+        e = dm_launch_corr0_bf16(g, d1, d2, c->cfg.lambda, base + pl.a16, d_status,
                                  const_cast<float*>(py->pooled[0]), const_cast<unsigned char*>(py->amax[0]), st);
     } else {
         e = dm_launch_corr0_f32(g, d1, d2, c->cfg.lambda, const_cast<float*>(py->pooled[0]),
@@ -187,6 +188,7 @@ int dm_make_geom(int W1, int H1, int W2, int H2, DmGeom* g) {
 void dm_pyr_layout(const DmGeom& g, int precision, DmPyrLayout* o) {
     memset(o, 0, sizeof(*o));
     size_t off = 0;
+    o->header = off; off = dm_align(off + sizeof(DmWsHeader));
     for (int l = 0; l <= g.L; l++) { o->valid[l] = off; off = dm_align(off + (size_t)g.npatch(l)); }
     for (int l = 0; l < g.L; l++) {
         size_t n = (size_t)g.npatch(l) * (size_t)g.dsize(l + 1);
@@ -194,11 +196,7 @@ void dm_pyr_layout(const DmGeom& g, int precision, DmPyrLayout* o) {
         o->amax[l] = off; off = dm_align(off + n);
     }
     o->top = off; off = dm_align(off + (size_t)g.npatch(g.L) * (size_t)g.dsize(g.L) * 4);
-    if (precision == DM_BF16) {
-        size_t m = ((size_t)g.npatch(0) + 127) / 128 * 128;
-        o->a16 = off; off = dm_align(off + m * 144 * 2);
-        o->b16 = off; off = dm_align(off + ((size_t)g.W2 + 64) * ((size_t)g.H2 + 64) * 16 * 2);
-    }
+    if (precision == DM_BF16) { o->a16 = off; off = dm_align(off + dm_corr0_bf16_a_bytes(g)); }
     o->bytes = off;
 }
 
@@ -251,7 +249,6 @@ dm_status dm_create(const dm_config* cfg, int device, dm_ctx** out) {
         !(c.nu2 <= 10.0f) || !(c.nu3 <= 10.0f) || !(c.mu >= 0.0f) || !(c.image_scale > 0.0f))
         return DM_EINVAL;
     if (c.precision != DM_FP32 && c.precision != DM_BF16) return DM_EINVAL;
-    if (c.precision == DM_BF16) return DM_EUNSUPPORTED;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return DM_EINVAL;
     dm_ctx* x = new dm_ctx();
@@ -375,7 +372,13 @@ dm_status dm_correlate_pyramid(dm_ctx* ctx, const float* d_desc1, int W1, int H1
     DevGuard dg(ctx->device);
     dm_pyramid* py = (dm_pyramid*)malloc(sizeof(dm_pyramid));
     if (!py) return fail(ctx, DM_EINVAL, "host allocation failed");
-    s = run_pyramid(ctx, g, d_desc1, d_desc2, (char*)d_ws, pl, py, (cudaStream_t)stream);
+    DmWsHeader* hdr = reinterpret_cast<DmWsHeader*>((char*)d_ws + pl.header);
+    cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(DmWsHeader), (cudaStream_t)stream);   // no backtracking here
+    if (e != cudaSuccess) {
+        free(py);
+        return cuda_fail(ctx, e, "clear header");
+    }
+    s = run_pyramid(ctx, g, d_desc1, d_desc2, (char*)d_ws, pl, py, &hdr->pyr_status, (cudaStream_t)stream);
     if (s != DM_OK) {
         free(py);
         return s;
@@ -412,7 +415,11 @@ dm_status dm_backtrack(dm_ctx* ctx, const dm_pyramid* pyr, void* d_ws, size_t ws
     dm_bt_layout(pyr->g, &bl);
     if (ws_bytes < bl.bytes) return fail(ctx, DM_ENOMEM, "backtrack workspace %zu < %zu bytes", ws_bytes, bl.bytes);
     DevGuard dg(ctx->device);
-    cudaError_t e = dm_launch_backtrack(pyr->g, *pyr, bl, (char*)d_ws, d_out, capacity, d_count, (cudaStream_t)stream);
+    // a stand-alone backtracking workspace carries no pyramid status
+    cudaError_t e = cudaMemsetAsync(&reinterpret_cast<DmWsHeader*>((char*)d_ws + bl.header)->pyr_status, 0, sizeof(int),
+                                    (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "clear status");
+    e = dm_launch_backtrack(pyr->g, *pyr, bl, (char*)d_ws, d_out, capacity, d_count, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "backtracking kernels");
     return DM_OK;
 }
@@ -443,8 +450,10 @@ dm_status dm_match(dm_ctx* ctx, const float* d_img1, int W1, int H1, const float
     dm_pyramid py;
     fill_pyramid(&py, g, ctx->cfg.precision, ml.py, base + ml.pyr);
     cudaError_t e;
+    int* d_status = &reinterpret_cast<DmWsHeader*>(base + ml.bt.header)->pyr_status;
+    if ((e = cudaMemsetAsync(d_status, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(ctx, e, "clear status");
     if (ctx->cfg.precision == DM_BF16)
-        e = dm_launch_corr0_bf16(g, desc1, desc2, ctx->cfg.lambda, base + ml.pyr + ml.py.a16, base + ml.pyr + ml.py.b16,
+        e = dm_launch_corr0_bf16(g, desc1, desc2, ctx->cfg.lambda, base + ml.pyr + ml.py.a16, d_status,
                                  const_cast<float*>(py.pooled[0]), const_cast<unsigned char*>(py.amax[0]), st);
     else
         e = dm_launch_corr0_f32(g, desc1, desc2, ctx->cfg.lambda, const_cast<float*>(py.pooled[0]),
@@ -505,7 +514,7 @@ dm_status dm_read_status(dm_ctx* ctx, const void* d_ws, int* status, long long* 
     cudaError_t e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = cudaMemcpy(&h, d_ws, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "dm_read_status");
-    *status = h.status;
+    *status = h.status | (h.pyr_status ? DM_DEV_TIMEOUT : 0);
     for (int l = 0; l < n_reached && reached; l++) reached[l] = (long long)h.count[l];
     return DM_OK;
 }

@@ -118,19 +118,20 @@ static inline size_t dm_align(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // Header at offset 0 of backtracking and dm_match workspaces.
 struct DmWsHeader {
-    int status;                   // DM_DEV_* bits
-    int pad0[15];
+    int status;                   // DM_DEV_* bits of the backtracking step
+    int pyr_status;               // nonzero: a bounded wait of a pyramid kernel gave up
+    int pad0[14];
     unsigned int count[DM_MAXL + 2];   // merged tuples per level (level 0: arrivals)
     unsigned int cap[DM_MAXL + 2];     // active merge-table capacity per level
 };
 
 struct DmPyrLayout {
+    size_t header;                // DmWsHeader (pyr_status used)
     size_t valid[DM_MAXL + 1];    // u8 [npatch(l)]
     size_t pooled[DM_MAXL];       // f32 [npatch(l)][dh[l+1]][dw[l+1]]
     size_t amax[DM_MAXL];         // u8 same shape
     size_t top;                   // f32 [npatch(L)][dh[L]][dw[L]]
-    size_t a16;                   // bf16 patch operand (BF16 form)
-    size_t b16;                   // bf16 image-2 descriptors (BF16 form)
+    size_t a16;                   // bf16 patch operand tiles (BF16 form)
     size_t bytes;
 };
 
@@ -183,7 +184,8 @@ cudaError_t dm_launch_descriptors(const DmDescParams& prm, const float* img, int
 cudaError_t dm_launch_corr0_f32(const DmGeom& g, const float* d1, const float* d2, float lam, float* pooled0,
                                 unsigned char* amax0, cudaStream_t st);
 cudaError_t dm_launch_corr0_bf16(const DmGeom& g, const float* d1, const float* d2, float lam, void* a16,
-                                 void* b16, float* pooled0, unsigned char* amax0, cudaStream_t st);
+                                 void* status, float* pooled0, unsigned char* amax0, cudaStream_t st);
+size_t dm_corr0_bf16_a_bytes(const DmGeom& g);
 cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& p, float lam, cudaStream_t st);
 cudaError_t dm_launch_backtrack(const DmGeom& g, const dm_pyramid& p, const DmBtLayout& bl, char* ws,
                                 dm_match_t* out, int capacity, int* d_count, cudaStream_t st);

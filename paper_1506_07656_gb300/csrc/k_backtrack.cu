@@ -284,7 +284,10 @@ cudaError_t dm_launch_backtrack(const DmGeom& g, const dm_pyramid& py, const DmB
     a.hdr = reinterpret_cast<DmWsHeader*>(ws + bl.header);
 
     cudaError_t e;
-    if ((e = cudaMemsetAsync(a.hdr, 0, sizeof(DmWsHeader), st)) != cudaSuccess) return e;
+    // clear the backtracking part of the header (status word, counts, table sizes);
+    // pyr_status belongs to the pyramid step that ran before
+    if ((e = cudaMemsetAsync(&a.hdr->status, 0, sizeof(int), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(a.hdr->count, 0, sizeof(a.hdr->count) + sizeof(a.hdr->cap), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(a.bestP, 0, sizeof(unsigned long long) * g.npatch(0), st)) != cudaSuccess) return e;
     size_t ncell = (size_t)((g.W2 + 3) / 4) * ((g.H2 + 3) / 4);
     if ((e = cudaMemsetAsync(a.bestQ, 0, sizeof(unsigned long long) * ncell, st)) != cudaSuccess) return e;

@@ -8,8 +8,13 @@
 // pooled outputs, i.e. C0 at 17 rows x 32 columns of I' positions (the
 // overlap of neighbouring 3x3 windows costs 32*17/(30*16) = 13% extra
 // correlations).  Lane j of a warp owns C0 column j for its warp's 4 patches
-// and all 17 rows: 68 accumulators.  The image-2 descriptor halo (20 rows x
-// 35 columns x 9 channels) and the 32 patch vectors sit in shared memory.
+// and all 17 rows: 68 accumulators, held as 34 float2 pairs (patches 0,1 and
+// 2,3) so that one packed FP32x2 fma (__ffma2_rn) updates two patches: the
+// instruction issue rate, not the FMA pipes, limited the scalar version.
+// The image-2 descriptor halo (20 rows x 35 columns x 9 channels) is stored
+// with each value duplicated (h, h) so a single 64-bit shared load yields the
+// packed operand; the 32 patch vectors sit in shared memory as
+// [(dx*9+c)*4+dy][patch].
 //
 // Summation order (identical to the FP32 reference): per output,
 // acc = fma(a, b, acc) over dx = 0..3, then channel c = 0..8, then dy = 0..3,
@@ -17,6 +22,11 @@
 // and leave acc unchanged (all operands are non-negative).  The loop order
 // (dx, c) outer / dy inner lets one column of 20 halo values in registers
 // feed all 4 dy offsets of all 17 rows.
+//
+// Epilogue: x1/16, out-of-domain positions masked to -inf, 3x3/2 max-pool
+// across lanes (shuffles) and rows with the first strict maximum in scan
+// order; the maxima and argmax codes are staged in shared memory, then all
+// 256 threads raise them to lambda and store rows of 15 consecutive outputs.
 #include "dm_internal.cuh"
 
 namespace {
@@ -28,12 +38,15 @@ constexpr int HROWS = CROWS + 3;
 constexpr int HCOLS = CCOLS + 3;
 constexpr int PW = 15;        // pooled columns per CTA
 constexpr int PH = 8;         // pooled rows per CTA
+constexpr int HALO_N = HROWS * HCOLS * 9;
+constexpr size_t SMEM_BYTES = (size_t)HALO_N * 8 + (size_t)144 * PATCHES * 4;
 
 __global__ void __launch_bounds__(256, 2)
 k_corr0_f32(DmGeom g, const float* __restrict__ d1, const float* __restrict__ d2, float lam,
             float* __restrict__ pooled0, unsigned char* __restrict__ amax0) {
-    __shared__ float halo[HROWS * HCOLS * 9];
-    __shared__ __align__(16) float a_s[144 * PATCHES];   // [(dx*9+c)*4+dy][patch]
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* halo = reinterpret_cast<float2*>(smem);                       // [HROWS][HCOLS][9] (h, h)
+    float* a_s = reinterpret_cast<float*>(smem + (size_t)HALO_N * 8);     // [(dx*9+c)*4+dy][patch]
 
     const int tiles_x = (g.dw[1] + PW - 1) / PW;
     const int rx0 = (blockIdx.x % tiles_x) * PW;
@@ -45,13 +58,16 @@ k_corr0_f32(DmGeom g, const float* __restrict__ d1, const float* __restrict__ d2
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     // image-2 halo: pixels [cx0-2, cx0+33) x [cy0-2, cy0+18), zero outside I'
-    for (int k = tid; k < HROWS * HCOLS * 9; k += 256) {
-        int c = k % 9, pix = k / 9;
+    for (int pix = tid; pix < HROWS * HCOLS; pix += 256) {
         int hx = pix % HCOLS, hy = pix / HCOLS;
         int x = cx0 - 2 + hx, y = cy0 - 2 + hy;
-        float v = 0.0f;
-        if (x >= 0 && y >= 0 && x < W2 && y < H2) v = d2[((long long)y * W2 + x) * 9 + c];
-        halo[k] = v;
+        bool in = (x >= 0 && y >= 0 && x < W2 && y < H2);
+        const float* src = d2 + ((long long)y * W2 + x) * 9;
+#pragma unroll
+        for (int c = 0; c < 9; c++) {
+            float v = in ? __ldg(src + c) : 0.0f;
+            halo[pix * 9 + c] = make_float2(v, v);
+        }
     }
     // patch vectors: window [p-2, p+1]^2 of I, zero outside I (partial patches)
     for (int k = tid; k < 144 * PATCHES; k += 256) {
@@ -62,57 +78,57 @@ k_corr0_f32(DmGeom g, const float* __restrict__ d1, const float* __restrict__ d2
         if (p < n0) {
             int px = 4 * (p % g.P0x) + 2, py = 4 * (p / g.P0x) + 2;
             int x = px - 2 + dx, y = py - 2 + dy;
-            if (x < g.W1 && y < g.H1) v = d1[((long long)y * g.W1 + x) * 9 + c];
+            if (x < g.W1 && y < g.H1) v = __ldg(d1 + ((long long)y * g.W1 + x) * 9 + c);
         }
         a_s[k] = v;
     }
     __syncthreads();
 
-    float acc[4][CROWS];
+    float2 acc01[CROWS], acc23[CROWS];
 #pragma unroll
-    for (int q = 0; q < 4; q++)
-#pragma unroll
-        for (int r = 0; r < CROWS; r++) acc[q][r] = 0.0f;
+    for (int r = 0; r < CROWS; r++) {
+        acc01[r] = make_float2(0.0f, 0.0f);
+        acc23[r] = make_float2(0.0f, 0.0f);
+    }
 
     const float4* a4p = reinterpret_cast<const float4*>(a_s) + warp;   // 4 patches of this warp
 #pragma unroll 1
     for (int dx = 0; dx < 4; dx++) {
 #pragma unroll 1
         for (int c = 0; c < 9; c++) {
-            float h[HROWS];
+            float2 h[HROWS];
 #pragma unroll
             for (int r = 0; r < HROWS; r++) h[r] = halo[(r * HCOLS + lane + dx) * 9 + c];
 #pragma unroll
             for (int dy = 0; dy < 4; dy++) {
                 float4 a = a4p[((dx * 9 + c) * 4 + dy) * (PATCHES / 4)];
+                float2 a01 = make_float2(a.x, a.y), a23 = make_float2(a.z, a.w);
 #pragma unroll
                 for (int r = 0; r < CROWS; r++) {
-                    acc[0][r] = __fmaf_rn(a.x, h[r + dy], acc[0][r]);
-                    acc[1][r] = __fmaf_rn(a.y, h[r + dy], acc[1][r]);
-                    acc[2][r] = __fmaf_rn(a.z, h[r + dy], acc[2][r]);
-                    acc[3][r] = __fmaf_rn(a.w, h[r + dy], acc[3][r]);
+                    acc01[r] = __ffma2_rn(a01, h[r + dy], acc01[r]);
+                    acc23[r] = __ffma2_rn(a23, h[r + dy], acc23[r]);
                 }
             }
         }
     }
+    __syncthreads();   // halo and patch vectors are no longer needed: reuse the space
 
-    // Epilogue: C0 = acc/16, out-of-domain positions masked, 3x3/2 max-pool
-    // with first-strict-max argmax (scan my = -1..1, mx = -1..1), power.
+    float* best_s = reinterpret_cast<float*>(smem);                                  // [32][PH][PW]
+    unsigned char* code_s = smem + (size_t)PATCHES * PH * PW * 4;                    // [32][PH][PW]
     const int cx = cx0 + lane;
     const bool col_in = (cx >= 0 && cx < W2);
-    const int k = (lane - 1) >> 1;                 // pooled column owned by odd lanes
-    const int rx = rx0 + k;
-    const bool writer = (lane & 1) && lane <= 2 * PW - 1 && rx < g.dw[1];
-    const int mw = g.dw[1], mh = g.dh[1];
+    const int k = (lane - 1) >> 1;                 // pooled column owned by odd lanes 1..29
+    const bool writer = (lane & 1) && lane <= 2 * PW - 1;
 #pragma unroll
     for (int q = 0; q < 4; q++) {
         float v[CROWS];
 #pragma unroll
         for (int r = 0; r < CROWS; r++) {
+            float a = (q == 0) ? acc01[r].x : (q == 1) ? acc01[r].y : (q == 2) ? acc23[r].x : acc23[r].y;
             int cy = cy0 + r;
-            v[r] = (col_in && cy >= 0 && cy < H2) ? __fmul_rn(acc[q][r], 0.0625f) : -INFINITY;
+            v[r] = (col_in && cy >= 0 && cy < H2) ? __fmul_rn(a, 0.0625f) : -INFINITY;
         }
-        const int p = p_base + warp * 4 + q;
+        const int pl = warp * 4 + q;
 #pragma unroll
         for (int i = 0; i < PH; i++) {
             float w[9];
@@ -123,17 +139,26 @@ k_corr0_f32(DmGeom g, const float* __restrict__ d1, const float* __restrict__ d2
                 w[my * 3 + 1] = c0;
                 w[my * 3 + 2] = __shfl_down_sync(0xffffffffu, c0, 1);
             }
-            const int ry = ry0 + i;
-            if (writer && ry < mh && p < n0) {
+            if (writer) {
                 float best = w[0];
                 int code = 0;
 #pragma unroll
                 for (int j = 1; j < 9; j++)
                     if (w[j] > best) { best = w[j]; code = j; }
-                long long o = ((long long)p * mh + ry) * mw + rx;
-                pooled0[o] = dm_powf(best, lam);
-                amax0[o] = (unsigned char)code;
+                best_s[(pl * PH + i) * PW + k] = best;
+                code_s[(pl * PH + i) * PW + k] = (unsigned char)code;
             }
+        }
+    }
+    __syncthreads();
+    const int mw = g.dw[1], mh = g.dh[1];
+    for (int e = tid; e < PATCHES * PH * PW; e += 256) {
+        int kk = e % PW, i = (e / PW) % PH, pl = e / (PW * PH);
+        int p = p_base + pl, rx = rx0 + kk, ry = ry0 + i;
+        if (p < n0 && rx < mw && ry < mh) {
+            long long o = ((long long)p * mh + ry) * mw + rx;
+            pooled0[o] = dm_powf(best_s[e], lam);
+            amax0[o] = code_s[e];
         }
     }
 }
@@ -145,7 +170,15 @@ cudaError_t dm_launch_corr0_f32(const DmGeom& g, const float* d1, const float* d
     int tiles = ((g.dw[1] + PW - 1) / PW) * ((g.dh[1] + PH - 1) / PH);
     int pblocks = (g.P0x * g.P0y + PATCHES - 1) / PATCHES;
     dim3 grid(tiles, pblocks);
-    k_corr0_f32<<<grid, 256, 0, st>>>(g, d1, d2, lam, pooled0, amax0);
+    static unsigned long long attr_set = 0;   // one bit per device: >48 KB dynamic shared memory opted in
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !(attr_set & (1ull << dev))) {
+        cudaError_t e = cudaFuncSetAttribute(k_corr0_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set |= 1ull << dev;
+    }
+    k_corr0_f32<<<grid, 256, SMEM_BYTES, st>>>(g, d1, d2, lam, pooled0, amax0);
     dm_count_launches(1);
     return cudaGetLastError();
 }

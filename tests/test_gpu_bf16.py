@@ -1,0 +1,110 @@
+"""BF16 tensor-core form of the level-0 correlation (tcgen05) against the FP32 path.
+
+The BF16 form rounds the 9-D pixel descriptors to bfloat16 (8-bit mantissa)
+before the level-0 dot products (FP32 accumulation) and uses the hardware
+power for the level-0 rectification; the rest of the pyramid is the FP32
+code.  Stated tolerances (relative to the FP32 path on the same descriptors):
+  * pyramid maps: max relative error per level <= 1e-2 (bf16 rounding of each
+    operand is <= 2^-9 relative; a 144-term non-negative dot product keeps that
+    bound; pooling and averaging do not amplify it);
+  * argmax codes and final matches may differ only on near-ties: at least 90%
+    of the level-0 argmax codes and 80% of the matched patches agree.
+"""
+import numpy as np
+import pytest
+
+from paper_1506_07656_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+MAP_RTOL = 1e-2
+ARGMAX_AGREE = 0.90
+MATCH_AGREE = 0.80
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1506_07656_gb300 import build, dm
+    build.build()
+    c32 = dm.Context(dm.DM_FP32)
+    c16 = dm.Context(dm.DM_BF16)
+    yield torch, dm, c32, c16
+    c32.close()
+    c16.close()
+
+
+def _levels(torch, dm, ctx, d1, d2):
+    H1, W1, _ = d1.shape
+    H2, W2, _ = d2.shape
+    ws = torch.empty(dm.dm_workspace_bytes(ctx.ctx, W1, H1, W2, H2)["pyramid"], dtype=torch.uint8, device="cuda")
+    h = dm.dm_correlate_pyramid(ctx.ctx, d1, d2, ws)
+    torch.cuda.synchronize()
+    st, _ = dm.dm_read_status(ctx.ctx, ws, 1)
+    assert st == 0
+    g = dm.dm_geometry(W1, H1, W2, H2)
+    out = []
+    for l in range(g["L"] + 1):
+        info = dm.dm_pyramid_level(h, l)
+        n, mw, mh = info["n"], info["mw"], info["mh"]
+        ov = info["vals"] - ws.data_ptr()
+        vals = ws[ov:ov + n * mw * mh * 4].view(torch.float32).reshape(n, mh, mw).cpu().numpy()
+        oa = (info["argmax"] or ws.data_ptr()) - ws.data_ptr()
+        am = ws[oa:oa + n * mw * mh].reshape(n, mh, mw).cpu().numpy() if info["argmax"] else None
+        ovl = info["valid"] - ws.data_ptr()
+        valid = ws[ovl:ovl + n].cpu().numpy().astype(bool)
+        out.append((vals, am, valid))
+    dm.dm_pyramid_free(h)
+    return out
+
+
+CASES = [(64, 48, 64, 48, 1), (37, 29, 37, 29, 2), (130, 70, 130, 70, 3), (41, 23, 53, 35, 4), (512, 224, 512, 224, 5)]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_bf16_pyramid_close_to_fp32(env, case):
+    torch, dm, c32, c16 = env
+    W1, H1, W2, H2, seed = case
+    if (W1, H1) == (W2, H2):
+        pr = synth.make_pair_smooth(W1, H1, seed)
+        i1, i2 = pr.img1, pr.img2
+    else:
+        rng = np.random.default_rng(seed)
+        i1 = synth.value_noise(W1, H1, rng).astype(np.float32)
+        i2 = synth.value_noise(W2, H2, rng).astype(np.float32)
+    descs = []
+    for img in (i1, i2):
+        H, W = img.shape
+        d = torch.empty((H, W, 9), dtype=torch.float32, device="cuda")
+        dm.dm_descriptors(c32.ctx, torch.from_numpy(img).cuda(), d, c32.workspace("desc", W1, H1, W2, H2))
+        descs.append(d)
+    a = _levels(torch, dm, c32, *descs)
+    b = _levels(torch, dm, c16, *descs)
+    for l, ((va, aa, ma), (vb, ab, mb)) in enumerate(zip(a, b)):
+        np.testing.assert_array_equal(ma, mb)
+        x, y = va[ma], vb[mb]
+        rel = np.abs(x - y) / np.maximum(np.abs(x), 1e-30)
+        print(f"level {l}: max rel err {rel.max():.3e}")
+        assert rel.max() <= MAP_RTOL, (l, rel.max())
+        if l == 0:
+            agree = np.mean(aa[ma] == ab[mb])
+            print(f"level 0 argmax agreement {agree:.4f}")
+            assert agree >= ARGMAX_AGREE
+
+
+def test_bf16_matches_close_to_fp32(env):
+    torch, dm, c32, c16 = env
+    pr = synth.make_pair_motif(256, 192, seed=8, max_disp=20.0)
+    m32 = c32.match(pr.img1, pr.img2).cpu().numpy()
+    m16 = c16.match(pr.img1, pr.img2).cpu().numpy()
+    k32 = {(r[0], r[1]): (r[2], r[3]) for r in m32}
+    k16 = {(r[0], r[1]): (r[2], r[3]) for r in m16}
+    keys = set(k32) | set(k16)
+    agree = sum(k32.get(k) == k16.get(k) for k in keys) / len(keys)
+    print(f"matches fp32 {len(m32)} bf16 {len(m16)} agreement {agree:.4f}")
+    assert agree >= MATCH_AGREE
+    assert synth.accuracy_at(m16, pr.flow, 10.0) >= synth.accuracy_at(m32, pr.flow, 10.0) - 0.05
+    st, _ = c16.status(256, 192, 256, 192)
+    assert st == 0
