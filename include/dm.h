@@ -136,11 +136,14 @@ dm_status dm_correlate_pyramid(dm_ctx* ctx, const float* d_desc1, int W1, int H1
 
 /* Device views of one level of a pyramid (valid after the producing stream
  * work completes).  level in [0, L]; for level < L: d_vals = P_l
- * [n_patches][mh][mw] and d_argmax its codes; for level == L: d_vals = C_L
- * and d_argmax = NULL.  d_valid [n_patches]: 1 if the patch exists (Eq. 7
- * with the boundary rule).  Any output pointer may be NULL. */
+ * [n_patches][mh][pitch] (columns mw..pitch-1 are row padding, not data) and
+ * d_argmax its codes in the same layout; for level == L: d_vals = C_L
+ * [n_patches][mh][mw] (pitch = mw) and d_argmax = NULL.  d_valid [n_patches]:
+ * 1 if the patch exists (Eq. 7 with the boundary rule).  Pooled rows are
+ * padded to a multiple of 8 values so that every row starts 32-byte aligned.
+ * Any output pointer may be NULL. */
 dm_status dm_pyramid_level(const dm_pyramid* pyr, int level, const float** d_vals, const unsigned char** d_argmax,
-                           const unsigned char** d_valid, int* n_patches, int* mw, int* mh);
+                           const unsigned char** d_valid, int* n_patches, int* mw, int* mh, int* pitch);
 dm_status dm_pyramid_free(dm_pyramid* pyr);
 
 /* Backtracking (Eq. 13-15) from every top-level position (Sec. 3.3 "Merging

@@ -191,7 +191,7 @@ void dm_pyr_layout(const DmGeom& g, int precision, DmPyrLayout* o) {
     o->header = off; off = dm_align(off + sizeof(DmWsHeader));
     for (int l = 0; l <= g.L; l++) { o->valid[l] = off; off = dm_align(off + (size_t)g.npatch(l)); }
     for (int l = 0; l < g.L; l++) {
-        size_t n = (size_t)g.npatch(l) * (size_t)g.dsize(l + 1);
+        size_t n = (size_t)g.npatch(l) * (size_t)g.psize(l + 1);
         o->pooled[l] = off; off = dm_align(off + n * 4);
         o->amax[l] = off; off = dm_align(off + n);
     }
@@ -388,7 +388,7 @@ dm_status dm_correlate_pyramid(dm_ctx* ctx, const float* d_desc1, int W1, int H1
 }
 
 dm_status dm_pyramid_level(const dm_pyramid* pyr, int level, const float** d_vals, const unsigned char** d_argmax,
-                           const unsigned char** d_valid, int* n_patches, int* mw, int* mh) {
+                           const unsigned char** d_valid, int* n_patches, int* mw, int* mh, int* pitch) {
     if (!pyr || level < 0 || level > pyr->g.L) return DM_EINVAL;
     const DmGeom& g = pyr->g;
     if (d_vals) *d_vals = level < g.L ? pyr->pooled[level] : pyr->top;
@@ -397,6 +397,7 @@ dm_status dm_pyramid_level(const dm_pyramid* pyr, int level, const float** d_val
     if (n_patches) *n_patches = g.npatch(level);
     if (mw) *mw = level < g.L ? g.dw[level + 1] : g.dw[level];
     if (mh) *mh = level < g.L ? g.dh[level + 1] : g.dh[level];
+    if (pitch) *pitch = level < g.L ? g.pitch(level + 1) : g.dw[level];
     return DM_OK;
 }
 

@@ -18,6 +18,10 @@ struct DmGeom {
     __host__ __device__ int npatch(int l) const { return l == 0 ? P0x * P0y : Lx * Ly; }
     __host__ __device__ int gx(int l) const { return l == 0 ? P0x : Lx; }
     __host__ __device__ long long dsize(int l) const { return (long long)dw[l] * dh[l]; }
+    // row pitch (floats) of a stored pooled map on domain l: width rounded up to 8,
+    // so every row starts 32-byte aligned (vector stores, 16-byte async copies)
+    __host__ __device__ int pitch(int l) const { return (dw[l] + 7) & ~7; }
+    __host__ __device__ long long psize(int l) const { return (long long)pitch(l) * dh[l]; }
 };
 
 int dm_make_geom(int W1, int H1, int W2, int H2, DmGeom* g);  // 0 ok, -1 invalid, -2 unsupported
@@ -128,7 +132,7 @@ struct DmWsHeader {
 struct DmPyrLayout {
     size_t header;                // DmWsHeader (pyr_status used)
     size_t valid[DM_MAXL + 1];    // u8 [npatch(l)]
-    size_t pooled[DM_MAXL];       // f32 [npatch(l)][dh[l+1]][dw[l+1]]
+    size_t pooled[DM_MAXL];       // f32 [npatch(l)][dh[l+1]][pitch(l+1)]
     size_t amax[DM_MAXL];         // u8 same shape
     size_t top;                   // f32 [npatch(L)][dh[L]][dw[L]]
     size_t a16;                   // bf16 patch operand tiles (BF16 form)

@@ -107,7 +107,7 @@ __device__ __forceinline__ int expand(const BtArgs& a, int l, unsigned int cap_n
         int ox = (i >= 2) ? 1 : -1, oy = (i & 1) ? 1 : -1;
         int rx = qx + ox, ry = qy + oy;
         if (rx < 0 || ry < 0 || rx >= mw || ry >= mh) continue;
-        long long ro = ((long long)c * mh + ry) * mw + rx;
+        long long ro = ((long long)c * mh + ry) * g.pitch(l) + rx;     // pooled map P_{l-1} lives on domain l
         int code = a.amax[l - 1][ro];
         int tx = 2 * rx + code % 3 - 1, ty = 2 * ry + code / 3 - 1;
         float s2 = __fadd_rn(s, a.pooled[l - 1][ro]);

@@ -21,12 +21,15 @@
 // y = 2 ry0 - 1 + ly (ly < 15); they cover the 3x3 windows of the 8 x 7
 // pooled outputs (rx0 + k, ry0 + j), centre lx = 2k + 1, ly = 2j + 1.
 //
-// Warp roles (192 threads, one CTA per SM, persistent over work units
+// Warp roles (448 threads, one CTA per SM, persistent over work units
 // (N-tile, M-chunk)): warp 0 issues the bulk copies of A (3-stage ring),
-// warp 1 allocates TMEM and one lane issues the MMAs and commits, warps 2-5
-// (one per TMEM lane quadrant) read the accumulators with tcgen05.ld, pool
-// with the first-strict-maximum argmax rule (scan my = -1..1, then mx), and
-// store P_0 = (max / 16)^lambda (MUFU-based power) and the argmax code.
+// warp 1 allocates TMEM and one lane issues the MMAs and commits, warps 2-13
+// drain the accumulators: three warps per TMEM lane quadrant, each on a band
+// of pooled rows (0-2, 3-4, 5-6), read them with tcgen05.ld, pool with the
+// first-strict-maximum argmax rule (scan my = -1..1, then mx), and store
+// P_0 = (max / 16)^lambda (MUFU-based power) and the argmax code.  Twelve
+// draining warps keep enough independent work in flight to hide ALU latency;
+// four were latency-bound.
 // Every mbarrier wait is bounded; on timeout the kernel records an error in
 // *err, stops issuing work, releases TMEM and returns.
 #include <cuda_bf16.h>
@@ -46,7 +49,8 @@ constexpr int A_TILE = BM * KD * 2;           // 36864
 constexpr int B_TILE = BN * KD * 2;           // 73728
 constexpr int STAGES = 3;
 constexpr int M_CHUNK = 110;                  // M-tiles per work unit
-constexpr int THREADS = 192;
+constexpr int EPI_WARPS = 12;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr size_t SMEM = (size_t)B_TILE + (size_t)STAGES * A_TILE + 256;
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 
@@ -113,6 +117,99 @@ __global__ void k_pack_a(DmGeom g, const float* __restrict__ d1, __nv_bfloat16* 
     *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(v);
 }
 
+struct EpiArgs {
+    uint32_t taddr;     // TMEM address of this warp's lane quadrant, column 0
+    int row;            // accumulator row (patch within the M-tile)
+    int m0, cx0, cy0, rx0, ry0, W2, H2, mw, mh, pitch, n0;
+    float lam;
+    bool interior;      // every C0 position of the N-tile lies inside I'
+};
+
+// Pool pooled rows [J0, J1) of one accumulator (C0 rows 2*J0 .. 2*J1) for this
+// thread's patch, release the accumulator, then store.
+template <int J0, int J1>
+__device__ __forceinline__ void epilogue_band(const EpiArgs& e, uint32_t b, int j, uint32_t bar_empty,
+                                              float* __restrict__ pooled0, unsigned char* __restrict__ amax0) {
+    constexpr int NJ = J1 - J0;
+    float best[NJ][PX];
+    int code[NJ][PX];
+#pragma unroll
+    for (int y = 0; y < NJ; y++)
+#pragma unroll
+        for (int x = 0; x < PX; x++) { best[y][x] = -INFINITY; code[y][x] = 4; }
+    const uint32_t taddr = e.taddr + b * BN;
+#pragma unroll
+    for (int ly = 2 * J0; ly <= 2 * J1; ly++) {
+        uint32_t r[CX];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                       "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                     : "r"(taddr + ly * CX));
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r[16]) : "r"(taddr + ly * CX + 16));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float v[CX];
+#pragma unroll
+        for (int lx = 0; lx < CX; lx++) v[lx] = __uint_as_float(r[lx]);
+        if (!e.interior) {
+            const int ty = e.cy0 + ly;
+            const bool rin = ty >= 0 && ty < e.H2;
+#pragma unroll
+            for (int lx = 0; lx < CX; lx++) {
+                const int tx = e.cx0 + lx;
+                if (!(rin && tx >= 0 && tx < e.W2)) v[lx] = -INFINITY;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < PX; k++) {
+            float h = v[2 * k];
+            int hc = 0;
+            if (v[2 * k + 1] > h) { h = v[2 * k + 1]; hc = 1; }
+            if (v[2 * k + 2] > h) { h = v[2 * k + 2]; hc = 2; }
+            // C0 row ly is m_y = -1 of pooled row ly/2 (even ly), m_y = 0 of (ly-1)/2 (odd),
+            // m_y = +1 of ly/2 - 1 (even ly); rows arrive in scan order
+            if ((ly & 1) == 0) {
+                if (ly / 2 - 1 >= J0) {
+                    const int jj = ly / 2 - 1 - J0;
+                    if (h > best[jj][k]) { best[jj][k] = h; code[jj][k] = 6 + hc; }
+                }
+                if (ly / 2 < J1) {
+                    const int jj = ly / 2 - J0;
+                    if (h > best[jj][k]) { best[jj][k] = h; code[jj][k] = hc; }
+                }
+            } else {
+                const int jj = (ly - 1) / 2 - J0;
+                if (h > best[jj][k]) { best[jj][k] = h; code[jj][k] = 3 + hc; }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    mbar_arrive(bar_empty);
+    const int p = (e.m0 + j) * BM + e.row;
+    if (p >= e.n0) return;
+#pragma unroll
+    for (int y = 0; y < NJ; y++) {
+        const int ry = e.ry0 + J0 + y;
+        if (ry >= e.mh) break;
+        // rows are padded to a multiple of 8 floats and rx0 is a multiple of 8, so the
+        // 8 outputs of a row always fit and are 32-byte aligned (padding columns
+        // receive values that nothing reads)
+        const long long o = ((long long)p * e.mh + ry) * e.pitch + e.rx0;
+        {
+            float4 f0, f1;
+            f0.x = __powf(best[y][0] * 0.0625f, e.lam); f0.y = __powf(best[y][1] * 0.0625f, e.lam);
+            f0.z = __powf(best[y][2] * 0.0625f, e.lam); f0.w = __powf(best[y][3] * 0.0625f, e.lam);
+            f1.x = __powf(best[y][4] * 0.0625f, e.lam); f1.y = __powf(best[y][5] * 0.0625f, e.lam);
+            f1.z = __powf(best[y][6] * 0.0625f, e.lam); f1.w = __powf(best[y][7] * 0.0625f, e.lam);
+            *reinterpret_cast<float4*>(pooled0 + o) = f0;
+            *reinterpret_cast<float4*>(pooled0 + o + 4) = f1;
+            uint2 cc;
+            cc.x = (uint32_t)code[y][0] | ((uint32_t)code[y][1] << 8) | ((uint32_t)code[y][2] << 16) | ((uint32_t)code[y][3] << 24);
+            cc.y = (uint32_t)code[y][4] | ((uint32_t)code[y][5] << 8) | ((uint32_t)code[y][6] << 16) | ((uint32_t)code[y][7] << 24);
+            *reinterpret_cast<uint2*>(amax0 + o) = cc;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(THREADS, 1)
 k_corr0_tc(DmGeom g, const __nv_bfloat16* __restrict__ a16, const float* __restrict__ d2, float lam,
            float* __restrict__ pooled0, unsigned char* __restrict__ amax0, int n_mtiles, int* __restrict__ err) {
@@ -133,7 +230,7 @@ k_corr0_tc(DmGeom g, const __nv_bfloat16* __restrict__ a16, const float* __restr
         }
         for (int b = 0; b < 2; b++) {
             mbar_init(bar_acc_full + 8 * b, 1);
-            mbar_init(bar_acc_empty + 8 * b, 128);
+            mbar_init(bar_acc_empty + 8 * b, 32 * EPI_WARPS);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -146,7 +243,7 @@ k_corr0_tc(DmGeom g, const __nv_bfloat16* __restrict__ a16, const float* __restr
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_holder;
 
-    const int W2 = g.W2, H2 = g.H2, mw = g.dw[1], mh = g.dh[1];
+    const int W2 = g.W2, H2 = g.H2, mw = g.dw[1], mh = g.dh[1], pitch = g.pitch(1);
     const int n0 = g.P0x * g.P0y;
     const int tiles_x = (mw + PX - 1) / PX, tiles_y = (mh + PY - 1) / PY;
     const int mchunks = (n_mtiles + M_CHUNK - 1) / M_CHUNK;
@@ -211,98 +308,19 @@ k_corr0_tc(DmGeom g, const __nv_bfloat16* __restrict__ a16, const float* __restr
                 }
             }
         } else {
-            // epilogue: warps 2..5 -> TMEM lane quadrants 2, 3, 0, 1
+            // epilogue: warp w drains TMEM lane quadrant w % 4, pooled-row band (w - 2) / 4
             const int quad = warp & 3;
-            const int row = quad * 32 + lane;
+            const int part = (warp - 2) >> 2;
             const bool interior = cx0 >= 0 && cy0 >= 0 && cx0 + CX <= W2 && cy0 + CY <= H2;
+            const EpiArgs ea{tmem + ((uint32_t)(quad * 32) << 16), quad * 32 + lane, m0, cx0, cy0, rx0, ry0, W2, H2, mw,
+                             mh, pitch, n0, lam, interior};
             for (int j = 0; j < nt; j++) {
                 const uint32_t ai = acc_it + j, b = ai & 1, aph = (ai >> 1) & 1;
                 if (!mbar_wait(bar_acc_full + 8 * b, aph, abort_flag, err)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                float best[PY][PX];
-                int code[PY][PX];
-#pragma unroll
-                for (int y = 0; y < PY; y++)
-#pragma unroll
-                    for (int x = 0; x < PX; x++) { best[y][x] = -INFINITY; code[y][x] = 4; }
-                const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + b * BN;
-#pragma unroll
-                for (int ly = 0; ly < CY; ly++) {
-                    uint32_t r[CX];
-                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                                 : "r"(taddr + ly * CX));
-                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r[16]) : "r"(taddr + ly * CX + 16));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    float v[CX];
-#pragma unroll
-                    for (int lx = 0; lx < CX; lx++) v[lx] = __uint_as_float(r[lx]);
-                    if (!interior) {
-                        const int ty = cy0 + ly;
-                        const bool rin = ty >= 0 && ty < H2;
-#pragma unroll
-                        for (int lx = 0; lx < CX; lx++) {
-                            const int tx = cx0 + lx;
-                            if (!(rin && tx >= 0 && tx < W2)) v[lx] = -INFINITY;
-                        }
-                    }
-#pragma unroll
-                    for (int k = 0; k < PX; k++) {
-                        float h = v[2 * k];
-                        int hc = 0;
-                        if (v[2 * k + 1] > h) { h = v[2 * k + 1]; hc = 1; }
-                        if (v[2 * k + 2] > h) { h = v[2 * k + 2]; hc = 2; }
-                        // row ly is m_y = -1 of pooled row ly/2 (even ly), m_y = 0 of (ly-1)/2 (odd),
-                        // m_y = +1 of ly/2 - 1 (even ly >= 2); rows arrive in scan order
-                        if ((ly & 1) == 0) {
-                            if (ly / 2 - 1 >= 0) {
-                                const int jj = ly / 2 - 1;
-                                if (h > best[jj][k]) { best[jj][k] = h; code[jj][k] = 6 + hc; }
-                            }
-                            if (ly / 2 < PY) {
-                                const int jj = ly / 2;
-                                if (h > best[jj][k]) { best[jj][k] = h; code[jj][k] = hc; }
-                            }
-                        } else {
-                            const int jj = (ly - 1) / 2;
-                            if (h > best[jj][k]) { best[jj][k] = h; code[jj][k] = 3 + hc; }
-                        }
-                    }
-                }
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                mbar_arrive(bar_acc_empty + 8 * b);
-                // power and stores (this thread's patch)
-                const int p = (m0 + j) * BM + row;
-                if (p < n0) {
-#pragma unroll
-                    for (int y = 0; y < PY; y++) {
-                        const int ry = ry0 + y;
-                        if (ry >= mh) break;
-                        const long long o = ((long long)p * mh + ry) * mw + rx0;
-                        if (rx0 + PX <= mw && (o & 7) == 0) {
-                            float4 f0, f1;
-                            f0.x = __powf(best[y][0] * 0.0625f, lam); f0.y = __powf(best[y][1] * 0.0625f, lam);
-                            f0.z = __powf(best[y][2] * 0.0625f, lam); f0.w = __powf(best[y][3] * 0.0625f, lam);
-                            f1.x = __powf(best[y][4] * 0.0625f, lam); f1.y = __powf(best[y][5] * 0.0625f, lam);
-                            f1.z = __powf(best[y][6] * 0.0625f, lam); f1.w = __powf(best[y][7] * 0.0625f, lam);
-                            *reinterpret_cast<float4*>(pooled0 + o) = f0;
-                            *reinterpret_cast<float4*>(pooled0 + o + 4) = f1;
-                            uint2 cc;
-                            cc.x = (uint32_t)code[y][0] | ((uint32_t)code[y][1] << 8) | ((uint32_t)code[y][2] << 16) | ((uint32_t)code[y][3] << 24);
-                            cc.y = (uint32_t)code[y][4] | ((uint32_t)code[y][5] << 8) | ((uint32_t)code[y][6] << 16) | ((uint32_t)code[y][7] << 24);
-                            *reinterpret_cast<uint2*>(amax0 + o) = cc;
-                        } else {
-#pragma unroll
-                            for (int x = 0; x < PX; x++) {
-                                if (rx0 + x < mw) {
-                                    pooled0[o + x] = __powf(best[y][x] * 0.0625f, lam);
-                                    amax0[o + x] = (unsigned char)code[y][x];
-                                }
-                            }
-                        }
-                    }
-                }
+                if (part == 0) epilogue_band<0, 3>(ea, b, j, bar_acc_empty + 8 * b, pooled0, amax0);
+                else if (part == 1) epilogue_band<3, 5>(ea, b, j, bar_acc_empty + 8 * b, pooled0, amax0);
+                else epilogue_band<5, 7>(ea, b, j, bar_acc_empty + 8 * b, pooled0, amax0);
             }
         }
         a_it += nt;

@@ -151,12 +151,12 @@ k_corr0_f32(DmGeom g, const float* __restrict__ d1, const float* __restrict__ d2
         }
     }
     __syncthreads();
-    const int mw = g.dw[1], mh = g.dh[1];
+    const int mw = g.dw[1], mh = g.dh[1], pitch = g.pitch(1);
     for (int e = tid; e < PATCHES * PH * PW; e += 256) {
         int kk = e % PW, i = (e / PW) % PH, pl = e / (PW * PH);
         int p = p_base + pl, rx = rx0 + kk, ry = ry0 + i;
         if (p < n0 && rx < mw && ry < mh) {
-            long long o = ((long long)p * mh + ry) * mw + rx;
+            long long o = ((long long)p * mh + ry) * pitch + rx;
             pooled0[o] = dm_powf(best_s[e], lam);
             amax0[o] = code_s[e];
         }

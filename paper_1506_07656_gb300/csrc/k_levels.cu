@@ -9,15 +9,18 @@
 // rounded once and divided by n; pooling is on the unrectified average and the
 // power is applied to the pooled value (x -> x^lambda is increasing on [0,1]).
 //
-// This pass is bound by HBM bandwidth.  A CTA owns one patch and a tile of
-// 32 x 8 pooled outputs: it stages the 4 child-map windows it needs (65 x 17
-// values each, zero outside the domain) in shared memory with coalesced row
-// loads, forms the 65 x 17 averages once, then pools them.  Patches vary
-// fastest in the grid, so the (up to 4) parents that read the same child
-// window run at about the same time and the repeat reads hit L2: HBM sees each
-// child map about once.  Algorithmic bytes per stored output: 4 x 4 B of child
-// values read (each child value feeds 4 outputs' worth of area) + 4 B + 1 B
-// written.
+// This pass streams the pooled maps of the level below (bandwidth) and does
+// a fixed amount of arithmetic per stored output (4 compensated averages,
+// a 9-way max with argmax, one power).  A CTA owns one patch and a tile of
+// 32 x 16 pooled outputs (two per thread): it stages the 4 child-map windows
+// it needs in shared memory with 16-byte asynchronous copies (rows of the
+// pooled maps are padded to 8 floats, so every window row starts aligned; the
+// copy's source size zero-fills whatever lies outside the domain), forms the
+// 65 x 33 averages once, then pools them.  Patches vary fastest in the grid,
+// so the (up to 4) parents that read the same child window run at about the
+// same time and the repeat reads hit L2.  Algorithmic bytes per stored
+// output: 16 B of child values read (each child value is shared by 4
+// parents), 4 + 1 B written.
 #include "dm_internal.cuh"
 
 namespace {
@@ -45,7 +48,7 @@ struct Kids {
     int n;
 };
 
-__device__ __forceinline__ float child_mean(const Kids& k, int qx, int qy, int mw, int mh) {
+__device__ __forceinline__ float child_mean(const Kids& k, int qx, int qy, int mw, int mh, int pitch) {
     float s = 0.0f, comp = 0.0f;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
@@ -53,7 +56,7 @@ __device__ __forceinline__ float child_mean(const Kids& k, int qx, int qy, int m
         int ox = (i >= 2) ? 1 : -1, oy = (i & 1) ? 1 : -1;
         int rx = qx + ox, ry = qy + oy;
         float v = 0.0f;
-        if (rx >= 0 && ry >= 0 && rx < mw && ry < mh) v = __ldg(k.base[i] + (long long)ry * mw + rx);
+        if (rx >= 0 && ry >= 0 && rx < mw && ry < mh) v = __ldg(k.base[i] + (long long)ry * pitch + rx);
         float t = __fadd_rn(s, v);
         float bp = __fsub_rn(t, s);
         float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
@@ -67,7 +70,7 @@ __device__ __forceinline__ float child_mean(const Kids& k, int qx, int qy, int m
 __device__ __forceinline__ bool load_kids(const DmGeom& g, int l, int p, const unsigned char* __restrict__ vprev,
                                           const float* __restrict__ prev, Kids& k) {
     int ix = p % g.Lx, iy = p / g.Lx;
-    long long cs = (long long)g.dw[l] * g.dh[l];     // child pooled map size (domain of level l)
+    long long cs = g.psize(l);     // child pooled map size (domain of level l, padded rows)
     k.n = 0;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
@@ -82,8 +85,10 @@ __device__ __forceinline__ bool load_kids(const DmGeom& g, int l, int p, const u
     return k.n > 0;
 }
 
-constexpr int TW = 32, TH = 8;                 // pooled outputs per CTA (lane, warp)
-constexpr int AW = 2 * TW + 1, AH = 2 * TH + 1;  // averages per CTA
+constexpr int TW = 32, TH = 16;                // pooled outputs per CTA (lane, 2 x warp)
+constexpr int AW = 2 * TW + 1, AH = 2 * TH + 1;  // averages per CTA (65 x 33)
+constexpr int KW = 72;                           // staged child columns: 18 aligned float4
+constexpr int LEVEL_THREADS = 256;
 
 // x / n rounded once, for n in 1..4: multiplications by 1, 1/2, 1/4 are exact,
 // so they equal the correctly rounded quotient; n = 3 divides.
@@ -91,85 +96,99 @@ __device__ __forceinline__ float div_n(float x, int n) {
     return n == 3 ? __fdiv_rn(x, 3.0f) : __fmul_rn(x, n == 4 ? 0.25f : (n == 2 ? 0.5f : 1.0f));
 }
 
-// Level l in [1, L-1], shared-memory tiled: grid (patch, tile), 8 warps.
-// Rows of every staged window are spread over warps and columns over lanes,
-// so each staged value costs one asynchronous 4-byte copy and a few integer
-// operations (the previous per-element div/mod dominated the instruction count).
-__global__ void __launch_bounds__(256) k_level_pool_tiled(DmGeom g, int l, const unsigned char* __restrict__ vprev,
-                                                          const unsigned char* __restrict__ vcur,
-                                                          const float* __restrict__ prev, float* __restrict__ out,
-                                                          unsigned char* __restrict__ amax, float lam) {
-    __shared__ float kid[4][AH][AW];
+// Level l in [1, L-1]: grid (patch, tile).
+__global__ void __launch_bounds__(LEVEL_THREADS) k_level_pool_tiled(DmGeom g, int l, const unsigned char* __restrict__ vprev,
+                                                                    const unsigned char* __restrict__ vcur,
+                                                                    const float* __restrict__ prev, float* __restrict__ out,
+                                                                    unsigned char* __restrict__ amax, float lam) {
+    __shared__ __align__(16) float kid[4][AH][KW];
     __shared__ float avg[AH][AW];
+    __shared__ int kid_index[4];
     const int p = blockIdx.x;
     if (!vcur[p]) return;
-    const int ow = g.dw[l + 1], oh = g.dh[l + 1];
-    const int mw = g.dw[l], mh = g.dh[l];
+    const int ow = g.dw[l + 1], oh = g.dh[l + 1], opitch = g.pitch(l + 1);
+    const int mw = g.dw[l], mh = g.dh[l], mpitch = g.pitch(l);
     const int tiles_x = (ow + TW - 1) / TW;
     const int rx0 = (blockIdx.y % tiles_x) * TW, ry0 = (blockIdx.y / tiles_x) * TH;
     const int qx0 = 2 * rx0 - 1, qy0 = 2 * ry0 - 1;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    Kids k;
-    load_kids(g, l, p, vprev, prev, k);
-    // Stage the child windows (child i is sampled at q + o_i); a source size of
-    // 0 fills zeros outside the domain or for a missing child.
+    const int xa = 2 * rx0 - 4;                      // aligned first staged child column
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < 4) {
+        int c = dm_child(g, l, p % g.Lx, p / g.Lx, tid);
+        kid_index[tid] = (c >= 0 && vprev[c]) ? c : -1;
+    }
+    __syncthreads();
+    int n = 0;
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-        const int ox = (i >= 2) ? 1 : -1, oy = (i & 1) ? 1 : -1;
-        const float* base = k.base[i];
-        for (int ay = warp; ay < AH; ay += 8) {
-            const int ry = qy0 + ay + oy;
-            const bool row_in = base != nullptr && ry >= 0 && ry < mh;
-            const float* rowp = row_in ? base + (long long)ry * mw : prev;
-            const unsigned dst0 = (unsigned)__cvta_generic_to_shared(&kid[i][ay][0]);
-#pragma unroll
-            for (int ax = lane; ax < AW; ax += 32) {
-                const int rx = qx0 + ax + ox;
-                const bool in = row_in && rx >= 0 && rx < mw;
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;"
-                             :: "r"(dst0 + 4u * ax), "l"(in ? rowp + rx : prev), "r"(in ? 4 : 0) : "memory");
-            }
+    for (int i = 0; i < 4; i++) n += kid_index[i] >= 0;
+    // stage: child i, window rows qy0 + oy_i + [0, AH), columns xa + [0, KW)
+    const long long cs = (long long)mpitch * mh;
+    for (int e = tid; e < 4 * AH * (KW / 4); e += LEVEL_THREADS) {
+        const int i = e / (AH * (KW / 4));
+        const int rem = e - i * (AH * (KW / 4));
+        const int ay = rem / (KW / 4), v4 = rem - ay * (KW / 4);
+        const int oy = (i & 1) ? 1 : -1;
+        const int c = kid_index[i];
+        const int ry = qy0 + ay + oy, x = xa + 4 * v4;
+        int bytes = 0;
+        const float* src = prev;
+        if (c >= 0 && ry >= 0 && ry < mh && x >= 0 && x < mw) {
+            bytes = min(16, 4 * (mw - x));
+            src = prev + c * cs + (long long)ry * mpitch + x;
         }
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(&kid[i][ay][4 * v4]);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(bytes) : "memory");
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
-    // averages: compensated sum over existing children in order i = 0..3, / n
-    for (int ay = warp; ay < AH; ay += 8) {
+    // averages: compensated sum over existing children in order i = 0..3, / n.
+    // Average (ay, ax) uses child i at staged column ax + ox_i + 3.
+    for (int ay = warp; ay < AH; ay += LEVEL_THREADS / 32) {
 #pragma unroll
         for (int ax = lane; ax < AW; ax += 32) {
             float s = 0.0f, comp = 0.0f;
 #pragma unroll
             for (int i = 0; i < 4; i++) {
-                if (k.base[i] == nullptr) continue;
-                float v = kid[i][ay][ax];
+                if (kid_index[i] < 0) continue;
+                const int ox = (i >= 2) ? 1 : -1;
+                float v = kid[i][ay][ax + ox + 3];
                 float t = __fadd_rn(s, v);
                 float bp = __fsub_rn(t, s);
                 float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
                 s = t;
                 comp = __fadd_rn(comp, err);
             }
-            avg[ay][ax] = div_n(__fadd_rn(s, comp), k.n);
+            avg[ay][ax] = div_n(__fadd_rn(s, comp), n);
         }
     }
     __syncthreads();
     // 3x3 / 2 max-pool over in-domain averages, first strict maximum, power
-    const int rx = rx0 + lane, ry = ry0 + warp;
-    if (rx >= ow || ry >= oh) return;
-    float best = -INFINITY;
-    int code = 4;
+    const int rx = rx0 + lane;
+    if (rx >= ow) return;
+    const bool interior = qx0 >= 0 && qy0 >= 0 && qx0 + AW <= mw && qy0 + AH <= mh;
 #pragma unroll
-    for (int my = -1; my <= 1; my++) {
+    for (int h = 0; h < 2; h++) {
+        const int ty = warp + 8 * h;
+        const int ry = ry0 + ty;
+        if (ry >= oh) break;
+        float best = -INFINITY;
+        int code = 4;
 #pragma unroll
-        for (int mx = -1; mx <= 1; mx++) {
-            int qx = 2 * rx + mx, qy = 2 * ry + my;
-            if (qx < 0 || qy < 0 || qx >= mw || qy >= mh) continue;
-            float a = avg[2 * warp + 1 + my][2 * lane + 1 + mx];
-            if (a > best) { best = a; code = (my + 1) * 3 + (mx + 1); }
+        for (int my = -1; my <= 1; my++) {
+#pragma unroll
+            for (int mx = -1; mx <= 1; mx++) {
+                if (!interior) {
+                    int qx = 2 * rx + mx, qy = 2 * ry + my;
+                    if (qx < 0 || qy < 0 || qx >= mw || qy >= mh) continue;
+                }
+                float a = avg[2 * ty + 1 + my][2 * lane + 1 + mx];
+                if (a > best) { best = a; code = (my + 1) * 3 + (mx + 1); }
+            }
         }
+        long long o = ((long long)p * oh + ry) * opitch + rx;
+        out[o] = dm_powf(best, lam);
+        amax[o] = (unsigned char)code;
     }
-    long long o = (long long)p * ow * oh + (long long)ry * ow + rx;
-    out[o] = dm_powf(best, lam);
-    amax[o] = (unsigned char)code;
 }
 
 // Top level L: C_L = (mean of children)^lambda over the domain of level L.
@@ -183,7 +202,7 @@ __global__ void k_level_top(DmGeom g, int l, const unsigned char* __restrict__ v
     if (q >= mw * mh) return;
     Kids k;
     load_kids(g, l, p, vprev, prev, k);
-    float a = child_mean(k, q % mw, q / mw, mw, mh);
+    float a = child_mean(k, q % mw, q / mw, mw, mh, g.pitch(l));
     top[(long long)p * mw * mh + q] = dm_powf(a, lam);
 }
 
@@ -198,7 +217,7 @@ cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& py, float lam, c
         if (l < g.L) {
             int tiles = ((g.dw[l + 1] + TW - 1) / TW) * ((g.dh[l + 1] + TH - 1) / TH);
             dim3 grid(np, tiles);
-            k_level_pool_tiled<<<grid, TW * TH, 0, st>>>(g, l, py.valid[l - 1], py.valid[l], py.pooled[l - 1],
+            k_level_pool_tiled<<<grid, LEVEL_THREADS, 0, st>>>(g, l, py.valid[l - 1], py.valid[l], py.pooled[l - 1],
                                                          const_cast<float*>(py.pooled[l]),
                                                          const_cast<unsigned char*>(py.amax[l]), lam);
         } else {

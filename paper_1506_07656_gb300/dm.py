@@ -51,7 +51,7 @@ _SIGS = {
                                        C.c_void_p, C.c_size_t, C.POINTER(C.c_void_p), C.c_void_p]),
     "dm_pyramid_level": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                    C.POINTER(C.c_void_p), C.POINTER(C.c_int), C.POINTER(C.c_int),
-                                   C.POINTER(C.c_int)]),
+                                   C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "dm_pyramid_free": (C.c_int, [C.c_void_p]),
     "dm_backtrack": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_int, C.c_void_p,
                                C.c_void_p]),
@@ -171,12 +171,29 @@ def dm_correlate_pyramid(ctx, d_desc1, d_desc2, d_ws, stream=None) -> int:
 
 def dm_pyramid_level(pyr: int, level: int):
     vals, am, valid = C.c_void_p(), C.c_void_p(), C.c_void_p()
-    n, mw, mh = C.c_int(), C.c_int(), C.c_int()
+    n, mw, mh, pitch = C.c_int(), C.c_int(), C.c_int(), C.c_int()
     st = load().dm_pyramid_level(pyr, level, C.byref(vals), C.byref(am), C.byref(valid), C.byref(n), C.byref(mw),
-                                 C.byref(mh))
+                                 C.byref(mh), C.byref(pitch))
     if st != DM_OK:
         raise DmError(st, "dm_pyramid_level")
-    return dict(vals=vals.value, argmax=am.value, valid=valid.value, n=n.value, mw=mw.value, mh=mh.value)
+    return dict(vals=vals.value, argmax=am.value, valid=valid.value, n=n.value, mw=mw.value, mh=mh.value,
+                pitch=pitch.value)
+
+
+def read_level(ws, info):
+    """Copy one pyramid level (values, argmax or None, valid) to host numpy arrays, padding dropped."""
+    import torch
+    n, mw, mh, pitch = info["n"], info["mw"], info["mh"], info["pitch"]
+    base = ws.data_ptr()
+    ov = info["vals"] - base
+    vals = ws[ov:ov + n * mh * pitch * 4].view(torch.float32).reshape(n, mh, pitch)[:, :, :mw].cpu().numpy()
+    am = None
+    if info["argmax"]:
+        oa = info["argmax"] - base
+        am = ws[oa:oa + n * mh * pitch].reshape(n, mh, pitch)[:, :, :mw].cpu().numpy()
+    ovl = info["valid"] - base
+    valid = ws[ovl:ovl + n].cpu().numpy()
+    return vals, am, valid
 
 
 def dm_pyramid_free(pyr: int) -> None:

@@ -47,15 +47,8 @@ def _levels(torch, dm, ctx, d1, d2):
     g = dm.dm_geometry(W1, H1, W2, H2)
     out = []
     for l in range(g["L"] + 1):
-        info = dm.dm_pyramid_level(h, l)
-        n, mw, mh = info["n"], info["mw"], info["mh"]
-        ov = info["vals"] - ws.data_ptr()
-        vals = ws[ov:ov + n * mw * mh * 4].view(torch.float32).reshape(n, mh, mw).cpu().numpy()
-        oa = (info["argmax"] or ws.data_ptr()) - ws.data_ptr()
-        am = ws[oa:oa + n * mw * mh].reshape(n, mh, mw).cpu().numpy() if info["argmax"] else None
-        ovl = info["valid"] - ws.data_ptr()
-        valid = ws[ovl:ovl + n].cpu().numpy().astype(bool)
-        out.append((vals, am, valid))
+        vals, am, valid = dm.read_level(ws, dm.dm_pyramid_level(h, l))
+        out.append((vals, am, valid.astype(bool)))
     dm.dm_pyramid_free(h)
     return out
 

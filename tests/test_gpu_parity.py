@@ -61,19 +61,7 @@ def _gpu_pyramid(torch, ctx, d1, d2):
     h = dm.dm_correlate_pyramid(ctx.ctx, t1, t2, ws)
     torch.cuda.synchronize()
     g = dm.dm_geometry(W1, H1, W2, H2)
-    levels = []
-    for l in range(g["L"] + 1):
-        info = dm.dm_pyramid_level(h, l)
-        n, mw, mh = info["n"], info["mw"], info["mh"]
-        off_v = info["vals"] - ws.data_ptr()
-        vals = ws[off_v:off_v + n * mw * mh * 4].view(torch.float32).reshape(n, mh, mw).cpu().numpy()
-        off_valid = info["valid"] - ws.data_ptr()
-        valid = ws[off_valid:off_valid + n].cpu().numpy()
-        am = None
-        if info["argmax"]:
-            off_a = info["argmax"] - ws.data_ptr()
-            am = ws[off_a:off_a + n * mw * mh].reshape(n, mh, mw).cpu().numpy()
-        levels.append((vals, am, valid))
+    levels = [dm.read_level(ws, dm.dm_pyramid_level(h, l)) for l in range(g["L"] + 1)]
     return h, ws, levels
 
 
