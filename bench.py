@@ -41,6 +41,8 @@ def _args():
     ap.add_argument("--width", type=int, default=1024)
     ap.add_argument("--height", type=int, default=436)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched (CUDA graph) measurement")
+    ap.add_argument("--batch-replays", type=int, default=3)
     return ap.parse_args()
 
 
@@ -246,6 +248,48 @@ def _measure(dm, torch, dist, ctx, pair, a, world, local, stream):
                 matches=n_matches, clocks=clk.summary(), geo=geo)
 
 
+BATCH_SIZES = [(320, 240), (640, 480), (1024, 436), (1242, 375)]
+
+
+def _measure_batch(dm, torch, ctx, a, rank):
+    """Batched form: 48 pairs, 12 of each size, value noise + smooth warp with
+    per-pair seeds, matched by dm_match_batch inside one captured CUDA graph;
+    time graph replays with CUDA events."""
+    from paper_1506_07656_gb300 import synth
+    items = []
+    for k in range(48):
+        W, H = BATCH_SIZES[k % 4]
+        pr = synth.make_pair_smooth(W, H, seed=5000 + 100 * rank + k, max_disp=0.1 * max(W, H), with_flow=False)
+        n0 = dm.dm_geometry(W, H, W, H)["n_patch0"]
+        items.append((torch.from_numpy(pr.img1).cuda(), torch.from_numpy(pr.img2).cuda(),
+                      torch.empty((n0, 5), dtype=torch.float32, device="cuda"),
+                      torch.zeros(1, dtype=torch.int32, device="cuda")))
+    pairs = dm.make_pairs(items)
+    ws = torch.empty(dm.dm_batch_workspace_bytes(ctx.ctx, pairs), dtype=torch.uint8, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        dm.dm_match_batch(ctx.ctx, pairs, ws, side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        dm.dm_match_batch(ctx.ctx, pairs, ws, side)
+    graph.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.batch_replays):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.batch_replays
+    n_match = int(sum(int(it[3].item()) for it in items))
+    del graph, ws
+    return {"pairs": 48, "sizes": [f"{w}x{h}" for w, h in BATCH_SIZES], "per_size": 12,
+            "pairs_per_s": 48 / (ms / 1e3), "ms_per_batch": ms, "replays": a.batch_replays,
+            "graph": "one CUDA graph of dm_match_batch (all 48 pairs), replayed", "matches": n_match}
+
+
 def _rooflines(r, prec_bf16, W, H, peaks, nsm):
     geo = r["geo"]
     n0 = geo["n_patch0"]
@@ -307,6 +351,14 @@ def run_ours(a):
         torch.cuda.empty_cache()
     head = "bf16" if "bf16" in res else precs[0]
     r = res[head]
+    batch = None
+    if not a.no_batch:
+        ctx = dm.Context(dm.DM_BF16 if head == "bf16" else dm.DM_FP32, device=local)
+        batch = _measure_batch(dm, torch, ctx, a, rank)
+        batch["precision"] = head
+        ctx.close()
+        del ctx
+        torch.cuda.empty_cache()
 
     if rank == 0:
         peaks = {}
@@ -344,6 +396,7 @@ def run_ours(a):
             "roofline": dominant,
             "rooflines": {"level0": corr, "levels": lev},
             "paths": paths,
+            "batched": batch,
             "stages_ms": r["stages"],
             "cpu_baseline": cpu,
             "e2e": {"value": r["e2e"], "unit": "pairs/s", "h2d_bytes_per_step": 2 * W * H * 4,

@@ -140,7 +140,7 @@ dm_status dm_correlate_pyramid(dm_ctx* ctx, const float* d_desc1, int W1, int H1
  * d_argmax its codes in the same layout; for level == L: d_vals = C_L
  * [n_patches][mh][mw] (pitch = mw) and d_argmax = NULL.  d_valid [n_patches]:
  * 1 if the patch exists (Eq. 7 with the boundary rule).  Pooled rows are
- * padded to a multiple of 8 values so that every row starts 32-byte aligned.
+ * padded to a multiple of 16 values so that every row starts 16-byte aligned.
  * Any output pointer may be NULL. */
 dm_status dm_pyramid_level(const dm_pyramid* pyr, int level, const float** d_vals, const unsigned char** d_argmax,
                            const unsigned char** d_valid, int* n_patches, int* mw, int* mh, int* pitch);
@@ -177,6 +177,27 @@ dm_status dm_match_host(dm_ctx* ctx, const float* h_img1, int W1, int H1, const 
  * before merging by pixel, i.e. arrivals). */
 dm_status dm_read_status(dm_ctx* ctx, const void* d_ws, int* status, long long* reached, int n_reached,
                          void* stream);
+
+/* One image pair of a batch (device buffers, as for dm_match). */
+typedef struct {
+    const float* d_img1;
+    int W1, H1;
+    const float* d_img2;
+    int W2, H2;
+    dm_match_t* d_out;
+    int capacity;
+    int* d_count;
+} dm_pair;
+
+/* Batched form.  Matches n pairs, of possibly different sizes, one after the
+ * other on `stream` with one shared workspace (d_ws >= the largest
+ * match_bytes over the pairs, from dm_batch_workspace_bytes).  Nothing in the
+ * sequence synchronises with the host, so the whole batch can be captured in
+ * a CUDA graph and replayed (make one uncaptured call first so that one-time
+ * per-device set-up does not happen inside the capture).  Arguments of every
+ * pair are checked before anything is launched. */
+dm_status dm_batch_workspace_bytes(const dm_ctx* ctx, int n, const dm_pair* pairs, size_t* bytes);
+dm_status dm_match_batch(dm_ctx* ctx, int n, const dm_pair* pairs, void* d_ws, size_t ws_bytes, void* stream);
 
 /* Backtracking without any caller workspace.
  * No counterpart in the paper: this entry point exists for callers that cannot

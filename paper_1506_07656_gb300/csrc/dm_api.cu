@@ -506,6 +506,43 @@ dm_status dm_match_host(dm_ctx* ctx, const float* h_img1, int W1, int H1, const 
     return DM_OK;
 }
 
+dm_status dm_batch_workspace_bytes(const dm_ctx* ctx, int n, const dm_pair* pairs, size_t* bytes) {
+    if (!ctx || n < 0 || (n > 0 && !pairs) || !bytes) return DM_EINVAL;
+    size_t best = 256;
+    for (int k = 0; k < n; k++) {
+        size_t mb = 0;
+        dm_status s = dm_workspace_bytes(ctx, pairs[k].W1, pairs[k].H1, pairs[k].W2, pairs[k].H2, nullptr, nullptr,
+                                         nullptr, &mb);
+        if (s != DM_OK) return s;
+        if (mb > best) best = mb;
+    }
+    *bytes = best;
+    return DM_OK;
+}
+
+dm_status dm_match_batch(dm_ctx* ctx, int n, const dm_pair* pairs, void* d_ws, size_t ws_bytes, void* stream) {
+    if (!ctx) return DM_EINVAL;
+    if (n < 0 || (n > 0 && !pairs) || !d_ws) return fail(ctx, DM_EINVAL, "dm_match_batch: bad arguments");
+    for (int k = 0; k < n; k++) {     // validate everything before launching anything
+        const dm_pair& q = pairs[k];
+        if (!q.d_img1 || !q.d_img2 || !q.d_out || !q.d_count || q.capacity < 0)
+            return fail(ctx, DM_EINVAL, "dm_match_batch: pair %d: null pointer or negative capacity", k);
+        DmGeom g;
+        dm_status s = check_geom(ctx, q.W1, q.H1, q.W2, q.H2, &g);
+        if (s != DM_OK) return s;
+        MatchLayout ml;
+        match_layout(g, ctx->cfg.precision, &ml);
+        if (ws_bytes < ml.bytes) return fail(ctx, DM_ENOMEM, "dm_match_batch: pair %d needs %zu workspace bytes", k, ml.bytes);
+    }
+    for (int k = 0; k < n; k++) {
+        const dm_pair& q = pairs[k];
+        dm_status s = dm_match(ctx, q.d_img1, q.W1, q.H1, q.d_img2, q.W2, q.H2, d_ws, ws_bytes, q.d_out, q.capacity,
+                               q.d_count, stream);
+        if (s != DM_OK) return s;
+    }
+    return DM_OK;
+}
+
 dm_status dm_read_status(dm_ctx* ctx, const void* d_ws, int* status, long long* reached, int n_reached, void* stream) {
     if (!ctx) return DM_EINVAL;
     if (!d_ws || !status || n_reached < 0 || n_reached > DM_MAXL + 2) return fail(ctx, DM_EINVAL, "dm_read_status: bad arguments");

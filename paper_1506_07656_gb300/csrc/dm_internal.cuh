@@ -18,9 +18,10 @@ struct DmGeom {
     __host__ __device__ int npatch(int l) const { return l == 0 ? P0x * P0y : Lx * Ly; }
     __host__ __device__ int gx(int l) const { return l == 0 ? P0x : Lx; }
     __host__ __device__ long long dsize(int l) const { return (long long)dw[l] * dh[l]; }
-    // row pitch (floats) of a stored pooled map on domain l: width rounded up to 8,
-    // so every row starts 32-byte aligned (vector stores, 16-byte async copies)
-    __host__ __device__ int pitch(int l) const { return (dw[l] + 7) & ~7; }
+    // row pitch (elements) of a stored pooled map on domain l: width rounded up to
+    // 16, so every row of the f32 values and of the u8 argmax codes starts
+    // 16-byte aligned (vector stores, 16-byte async copies, TMA tensor stores)
+    __host__ __device__ int pitch(int l) const { return (dw[l] + 15) & ~15; }
     __host__ __device__ long long psize(int l) const { return (long long)pitch(l) * dh[l]; }
 };
 

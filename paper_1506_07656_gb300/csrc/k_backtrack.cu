@@ -95,27 +95,42 @@ __device__ __forceinline__ void leaf_update(const BtArgs& a, int c, int tx, int 
 }
 
 // Children of tuple (l, p, q, s); returns the number of atomic arrivals.
+// The (up to 4) children's pooled values and argmax codes are loaded first,
+// all independent, so their memory latencies overlap; the merges follow.
 __device__ __forceinline__ int expand(const BtArgs& a, int l, unsigned int cap_next, int p, int qx, int qy, float s) {
     const DmGeom& g = a.g;
-    const int mw = g.dw[l], mh = g.dh[l];
+    const int mw = g.dw[l], mh = g.dh[l], pitch = g.pitch(l);    // pooled map P_{l-1} lives on domain l
     const int ix = p % g.Lx, iy = p / g.Lx;
+    int cc[4], rxs[4], rys[4];
+    float val[4];
+    int code[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        cc[i] = -1;
+        int c = dm_child(g, l, ix, iy, i);
+        int ox = (i >= 2) ? 1 : -1, oy = (i & 1) ? 1 : -1;
+        int rx = qx + ox, ry = qy + oy;
+        if (c >= 0 && rx >= 0 && ry >= 0 && rx < mw && ry < mh && a.valid[l - 1][c]) {
+            cc[i] = c;
+            rxs[i] = rx;
+            rys[i] = ry;
+            long long ro = ((long long)c * mh + ry) * pitch + rx;
+            code[i] = a.amax[l - 1][ro];
+            val[i] = a.pooled[l - 1][ro];
+        }
+    }
     int arrivals = 0;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
-        int c = dm_child(g, l, ix, iy, i);
-        if (c < 0 || !a.valid[l - 1][c]) continue;
-        int ox = (i >= 2) ? 1 : -1, oy = (i & 1) ? 1 : -1;
-        int rx = qx + ox, ry = qy + oy;
-        if (rx < 0 || ry < 0 || rx >= mw || ry >= mh) continue;
-        long long ro = ((long long)c * mh + ry) * g.pitch(l) + rx;     // pooled map P_{l-1} lives on domain l
-        int code = a.amax[l - 1][ro];
-        int tx = 2 * rx + code % 3 - 1, ty = 2 * ry + code / 3 - 1;
-        float s2 = __fadd_rn(s, a.pooled[l - 1][ro]);
+        if (cc[i] < 0) continue;
+        const int rx = rxs[i], ry = rys[i];
+        const int tx = 2 * rx + code[i] % 3 - 1, ty = 2 * ry + code[i] / 3 - 1;
+        const float s2 = __fadd_rn(s, val[i]);
         if (l - 1 >= 1) {
-            unsigned int key = (unsigned int)c * (unsigned int)g.dsize(l - 1) + (unsigned int)(ty * g.dw[l - 1] + tx);
+            unsigned int key = (unsigned int)cc[i] * (unsigned int)g.dsize(l - 1) + (unsigned int)(ty * g.dw[l - 1] + tx);
             ht_insert(a, l - 1, cap_next, key, s2);
         } else {
-            leaf_update(a, c, tx, ty, s2);
+            leaf_update(a, cc[i], tx, ty, s2);
             arrivals++;
         }
     }

@@ -12,26 +12,35 @@
 //      matrix; 18 core matrices along K per 8-row group, 2304 bytes), so one
 //      36,864-byte bulk copy (cp.async.bulk, TMA engine) moves a tile to
 //      shared memory.
-//   B: the implicit im2col of I' for one N-tile of 17 x 15 positions (255 of
-//      the 256 rows), built in shared memory by all warps in the same layout
-//      and kept resident while the CTA sweeps a chunk of up to 110 M-tiles.
-//   D: 128 lanes x 256 FP32 columns of TMEM; two accumulators (512 columns)
-//      let the epilogue drain one tile while the next is multiplied.
-// Pooling geometry: the N-tile's positions are x = 2 rx0 - 1 + lx (lx < 17),
-// y = 2 ry0 - 1 + ly (ly < 15); they cover the 3x3 windows of the 8 x 7
+//   B: the implicit im2col of I' for one N-tile of 33 x 7 positions (231 of
+//      the 240 rows of the MMA), built in shared memory by all warps in the
+//      same layout and kept resident while the CTA sweeps a chunk of M-tiles.
+//   D: 128 lanes x 240 FP32 columns of TMEM; two accumulators (columns 0 and
+//      256) let the epilogue drain one tile while the next is multiplied.
+// Pooling geometry: the N-tile's positions are x = 2 rx0 - 1 + lx (lx < 33),
+// y = 2 ry0 - 1 + ly (ly < 7); they cover the 3x3 windows of the 16 x 3
 // pooled outputs (rx0 + k, ry0 + j), centre lx = 2k + 1, ly = 2j + 1.
 //
-// Warp roles (448 threads, one CTA per SM, persistent over work units
-// (N-tile, M-chunk)): warp 0 issues the bulk copies of A (3-stage ring),
-// warp 1 allocates TMEM and one lane issues the MMAs and commits, warps 2-13
-// drain the accumulators: three warps per TMEM lane quadrant, each on a band
-// of pooled rows (0-2, 3-4, 5-6), read them with tcgen05.ld, pool with the
-// first-strict-maximum argmax rule (scan my = -1..1, then mx), and store
-// P_0 = (max / 16)^lambda (MUFU-based power) and the argmax code.  Twelve
-// draining warps keep enough independent work in flight to hide ALU latency;
-// four were latency-bound.
+// Output path.  P_0 is stored patch-major ([patch][row][pitch]), so the 16
+// pooled values of one tile row of one patch are 64 contiguous bytes (16 for
+// the argmax codes).  Plain per-thread stores scatter each warp store over 32
+// patches (32 sectors per instruction) and saturate L1.  Instead the
+// epilogue writes each tile's 128 x 3 x 16 outputs into a shared-memory
+// staging buffer (double-buffered) and one thread hands it to the TMA engine
+// with two 3-D tensor stores (values, codes); the tensor maps clip rows and
+// columns outside the maps and patches past the last one.
+//
+// Warp roles (576 threads, one CTA per SM, persistent over work units
+// (N-tile, M-chunk)): warp 0 issues the bulk copies of A (2-stage ring),
+// warp 1 allocates TMEM and one lane issues the MMAs and commits, warps 2-17
+// drain the accumulators: four warps per TMEM lane quadrant, each owning four
+// of the sixteen pooled columns (C0 columns 8w'..8w'+8) over the three pooled
+// rows: 14 tcgen05.ld, one wait, pool with the first-strict-maximum argmax
+// rule (scan my = -1..1, then mx), release the accumulator, raise to lambda
+// (MUFU-based power), stage, store through TMA.
 // Every mbarrier wait is bounded; on timeout the kernel records an error in
 // *err, stops issuing work, releases TMEM and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "dm_internal.cuh"
@@ -41,18 +50,28 @@ namespace {
 constexpr int BM = 128;                       // patches per M-tile (TMEM lanes)
 constexpr int KD = 144;                       // 4 x 4 x 9
 constexpr int KSTEPS = KD / 16;               // MMAs per tile
-constexpr int CX = 17, CY = 15;               // C0 positions per N-tile
-constexpr int BN = 256;                       // CX * CY = 255, padded
-constexpr int PX = 8, PY = 7;                 // pooled outputs per N-tile
+constexpr int CX = 33, CY = 7;                // C0 positions per N-tile
+constexpr int BN = 240;                       // CX * CY = 231, padded to a multiple of 16
+constexpr int PX = 16, PY = 3;                // pooled outputs per N-tile
 constexpr int GROUP = (KD / 8) * 128;         // 2304 bytes per 8-row group
 constexpr int A_TILE = BM * KD * 2;           // 36864
-constexpr int B_TILE = BN * KD * 2;           // 73728
-constexpr int STAGES = 3;
+constexpr int B_TILE = BN * KD * 2;           // 69120
+constexpr int STAGES = 2;
 constexpr int M_CHUNK = 110;                  // M-tiles per work unit
-constexpr int EPI_WARPS = 12;
-constexpr int THREADS = 64 + 32 * EPI_WARPS;
-constexpr size_t SMEM = (size_t)B_TILE + (size_t)STAGES * A_TILE + 256;
-constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
+constexpr int EPI_WARPS = 16;
+constexpr int EPI_THREADS = 32 * EPI_WARPS;
+constexpr int THREADS = 64 + EPI_THREADS;
+constexpr int OUT_F = BM * PY * PX * 4;       // 24576: staged values of one tile
+constexpr int OUT_C = BM * PY * PX;           // 6144: staged argmax codes of one tile
+// shared-memory map (1024-byte aligned pieces)
+constexpr int OFF_B = 0;
+constexpr int OFF_A = 69632;
+constexpr int OFF_F = OFF_A + STAGES * A_TILE;      // 143360
+constexpr int OFF_C = OFF_F + 2 * OUT_F;            // 192512
+constexpr int OFF_BAR = OFF_C + 2 * OUT_C;          // 204800
+constexpr size_t SMEM = (size_t)OFF_BAR + 256;
+constexpr long long WAIT_CYCLES = 4000000000LL;     // ~2 s at 2 GHz
+static_assert(OFF_A >= B_TILE, "B tile overlaps A stages");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -94,6 +113,8 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(bar) : "memory");
 }
 
+__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, %0;" :: "n"(EPI_THREADS) : "memory"); }
+
 // Pack the patch vectors of I into BF16 M-tiles (zero rows past the last patch).
 __global__ void k_pack_a(DmGeom g, const float* __restrict__ d1, __nv_bfloat16* __restrict__ a16, int n_mtiles) {
     const long long total = (long long)n_mtiles * BM * (KD / 8);
@@ -120,47 +141,53 @@ __global__ void k_pack_a(DmGeom g, const float* __restrict__ d1, __nv_bfloat16* 
 struct EpiArgs {
     uint32_t taddr;     // TMEM address of this warp's lane quadrant, column 0
     int row;            // accumulator row (patch within the M-tile)
-    int m0, cx0, cy0, rx0, ry0, W2, H2, mw, mh, pitch, n0;
+    int part;           // pooled columns 4*part .. 4*part+3
+    int cx0, cy0, W2, H2;
     float lam;
     bool interior;      // every C0 position of the N-tile lies inside I'
 };
 
-// Pool pooled rows [J0, J1) of one accumulator (C0 rows 2*J0 .. 2*J1) for this
-// thread's patch, release the accumulator, then store.
-template <int J0, int J1>
-__device__ __forceinline__ void epilogue_band(const EpiArgs& e, uint32_t b, int j, uint32_t bar_empty,
-                                              float* __restrict__ pooled0, unsigned char* __restrict__ amax0) {
-    constexpr int NJ = J1 - J0;
-    float best[NJ][PX];
-    int code[NJ][PX];
+// Pool this thread's 4 x 3 outputs of one accumulator, release the
+// accumulator, and write the powered values and codes to the staging buffer.
+__device__ __forceinline__ void epilogue_tile(const EpiArgs& e, uint32_t b, uint32_t bar_empty, float* stage_f,
+                                              unsigned char* stage_c) {
+    uint32_t r[CY][9];
+    const uint32_t taddr = e.taddr + b * 256 + 8 * e.part;
 #pragma unroll
-    for (int y = 0; y < NJ; y++)
-#pragma unroll
-        for (int x = 0; x < PX; x++) { best[y][x] = -INFINITY; code[y][x] = 4; }
-    const uint32_t taddr = e.taddr + b * BN;
-#pragma unroll
-    for (int ly = 2 * J0; ly <= 2 * J1; ly++) {
-        uint32_t r[CX];
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                       "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+    for (int ly = 0; ly < CY; ly++) {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(r[ly][0]), "=r"(r[ly][1]), "=r"(r[ly][2]), "=r"(r[ly][3]), "=r"(r[ly][4]), "=r"(r[ly][5]),
+                       "=r"(r[ly][6]), "=r"(r[ly][7])
                      : "r"(taddr + ly * CX));
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r[16]) : "r"(taddr + ly * CX + 16));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        float v[CX];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r[ly][8]) : "r"(taddr + ly * CX + 8));
+    }
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    mbar_arrive(bar_empty);
+
+    float best[PY][4];
+    int code[PY][4];
 #pragma unroll
-        for (int lx = 0; lx < CX; lx++) v[lx] = __uint_as_float(r[lx]);
+    for (int y = 0; y < PY; y++)
+#pragma unroll
+        for (int x = 0; x < 4; x++) { best[y][x] = -INFINITY; code[y][x] = 4; }
+    const int tx0 = e.cx0 + 8 * e.part;
+#pragma unroll
+    for (int ly = 0; ly < CY; ly++) {
+        float v[9];
+#pragma unroll
+        for (int c = 0; c < 9; c++) v[c] = __uint_as_float(r[ly][c]);
         if (!e.interior) {
             const int ty = e.cy0 + ly;
             const bool rin = ty >= 0 && ty < e.H2;
 #pragma unroll
-            for (int lx = 0; lx < CX; lx++) {
-                const int tx = e.cx0 + lx;
-                if (!(rin && tx >= 0 && tx < e.W2)) v[lx] = -INFINITY;
+            for (int c = 0; c < 9; c++) {
+                const int tx = tx0 + c;
+                if (!(rin && tx >= 0 && tx < e.W2)) v[c] = -INFINITY;
             }
         }
 #pragma unroll
-        for (int k = 0; k < PX; k++) {
+        for (int k = 0; k < 4; k++) {
             float h = v[2 * k];
             int hc = 0;
             if (v[2 * k + 1] > h) { h = v[2 * k + 1]; hc = 1; }
@@ -168,55 +195,45 @@ __device__ __forceinline__ void epilogue_band(const EpiArgs& e, uint32_t b, int 
             // C0 row ly is m_y = -1 of pooled row ly/2 (even ly), m_y = 0 of (ly-1)/2 (odd),
             // m_y = +1 of ly/2 - 1 (even ly); rows arrive in scan order
             if ((ly & 1) == 0) {
-                if (ly / 2 - 1 >= J0) {
-                    const int jj = ly / 2 - 1 - J0;
+                if (ly >= 2) {
+                    const int jj = ly / 2 - 1;
                     if (h > best[jj][k]) { best[jj][k] = h; code[jj][k] = 6 + hc; }
                 }
-                if (ly / 2 < J1) {
-                    const int jj = ly / 2 - J0;
+                if (ly / 2 < PY) {
+                    const int jj = ly / 2;
                     if (h > best[jj][k]) { best[jj][k] = h; code[jj][k] = hc; }
                 }
             } else {
-                const int jj = (ly - 1) / 2 - J0;
+                const int jj = (ly - 1) / 2;
                 if (h > best[jj][k]) { best[jj][k] = h; code[jj][k] = 3 + hc; }
             }
         }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    mbar_arrive(bar_empty);
-    const int p = (e.m0 + j) * BM + e.row;
-    if (p >= e.n0) return;
+    // staging layout = the TMA box [patch][row][16 columns]
 #pragma unroll
-    for (int y = 0; y < NJ; y++) {
-        const int ry = e.ry0 + J0 + y;
-        if (ry >= e.mh) break;
-        // rows are padded to a multiple of 8 floats and rx0 is a multiple of 8, so the
-        // 8 outputs of a row always fit and are 32-byte aligned (padding columns
-        // receive values that nothing reads)
-        const long long o = ((long long)p * e.mh + ry) * e.pitch + e.rx0;
-        {
-            float4 f0, f1;
-            f0.x = __powf(best[y][0] * 0.0625f, e.lam); f0.y = __powf(best[y][1] * 0.0625f, e.lam);
-            f0.z = __powf(best[y][2] * 0.0625f, e.lam); f0.w = __powf(best[y][3] * 0.0625f, e.lam);
-            f1.x = __powf(best[y][4] * 0.0625f, e.lam); f1.y = __powf(best[y][5] * 0.0625f, e.lam);
-            f1.z = __powf(best[y][6] * 0.0625f, e.lam); f1.w = __powf(best[y][7] * 0.0625f, e.lam);
-            *reinterpret_cast<float4*>(pooled0 + o) = f0;
-            *reinterpret_cast<float4*>(pooled0 + o + 4) = f1;
-            uint2 cc;
-            cc.x = (uint32_t)code[y][0] | ((uint32_t)code[y][1] << 8) | ((uint32_t)code[y][2] << 16) | ((uint32_t)code[y][3] << 24);
-            cc.y = (uint32_t)code[y][4] | ((uint32_t)code[y][5] << 8) | ((uint32_t)code[y][6] << 16) | ((uint32_t)code[y][7] << 24);
-            *reinterpret_cast<uint2*>(amax0 + o) = cc;
-        }
+    for (int y = 0; y < PY; y++) {
+        float4 f;
+        f.x = __powf(best[y][0] * 0.0625f, e.lam);
+        f.y = __powf(best[y][1] * 0.0625f, e.lam);
+        f.z = __powf(best[y][2] * 0.0625f, e.lam);
+        f.w = __powf(best[y][3] * 0.0625f, e.lam);
+        const int o = (e.row * PY + y) * PX + 4 * e.part;
+        *reinterpret_cast<float4*>(stage_f + o) = f;
+        *reinterpret_cast<uint32_t*>(stage_c + o) =
+            (uint32_t)code[y][0] | ((uint32_t)code[y][1] << 8) | ((uint32_t)code[y][2] << 16) | ((uint32_t)code[y][3] << 24);
     }
 }
 
 __global__ void __launch_bounds__(THREADS, 1)
 k_corr0_tc(DmGeom g, const __nv_bfloat16* __restrict__ a16, const float* __restrict__ d2, float lam,
-           float* __restrict__ pooled0, unsigned char* __restrict__ amax0, int n_mtiles, int* __restrict__ err) {
+           const __grid_constant__ CUtensorMap tmap_f, const __grid_constant__ CUtensorMap tmap_c, int n_mtiles,
+           int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* sB = smem;
-    unsigned char* sA = smem + B_TILE;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sA + STAGES * A_TILE);
+    unsigned char* sB = smem + OFF_B;
+    unsigned char* sA = smem + OFF_A;
+    float* sF = reinterpret_cast<float*>(smem + OFF_F);
+    unsigned char* sC = smem + OFF_C;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OFF_BAR);
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
     const uint32_t bar_full = smem_u32(bars), bar_empty = smem_u32(bars + STAGES);
@@ -230,7 +247,7 @@ k_corr0_tc(DmGeom g, const __nv_bfloat16* __restrict__ a16, const float* __restr
         }
         for (int b = 0; b < 2; b++) {
             mbar_init(bar_acc_full + 8 * b, 1);
-            mbar_init(bar_acc_empty + 8 * b, 32 * EPI_WARPS);
+            mbar_init(bar_acc_empty + 8 * b, EPI_THREADS);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -243,12 +260,12 @@ k_corr0_tc(DmGeom g, const __nv_bfloat16* __restrict__ a16, const float* __restr
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_holder;
 
-    const int W2 = g.W2, H2 = g.H2, mw = g.dw[1], mh = g.dh[1], pitch = g.pitch(1);
-    const int n0 = g.P0x * g.P0y;
+    const int W2 = g.W2, H2 = g.H2, mw = g.dw[1], mh = g.dh[1];
     const int tiles_x = (mw + PX - 1) / PX, tiles_y = (mh + PY - 1) / PY;
     const int mchunks = (n_mtiles + M_CHUNK - 1) / M_CHUNK;
     const int n_units = tiles_x * tiles_y * mchunks;
     uint32_t a_it = 0, acc_it = 0;
+    const bool store_leader = (warp == 2 && lane == 0);
 
     for (int unit = blockIdx.x; unit < n_units; unit += gridDim.x) {
         const int ntile = unit / mchunks, mc = unit % mchunks;
@@ -256,7 +273,7 @@ k_corr0_tc(DmGeom g, const __nv_bfloat16* __restrict__ a16, const float* __restr
         const int rx0 = (ntile % tiles_x) * PX, ry0 = (ntile / tiles_x) * PY;
         const int cx0 = 2 * rx0 - 1, cy0 = 2 * ry0 - 1;
 
-        // B: implicit im2col of I' for this N-tile (zero outside I' and in row 255)
+        // B: implicit im2col of I' for this N-tile (zero outside I' and in rows 231..239)
         for (int ch = tid; ch < BN * (KD / 8); ch += THREADS) {
             const int n = ch / (KD / 8), kc = ch % (KD / 8);
             const int lx = n % CX, ly = n / CX;
@@ -294,7 +311,7 @@ k_corr0_tc(DmGeom g, const __nv_bfloat16* __restrict__ a16, const float* __restr
                     if (!mbar_wait(bar_full + 8 * s, ph, abort_flag, err)) break;
                     if (!mbar_wait(bar_acc_empty + 8 * b, aph ^ 1, abort_flag, err)) break;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t d_tmem = tmem + b * BN;
+                    const uint32_t d_tmem = tmem + b * 256;
                     const uint32_t a_base = smem_u32(sA + s * A_TILE), b_base = smem_u32(sB);
 #pragma unroll
                     for (int k = 0; k < KSTEPS; k++) {
@@ -308,19 +325,34 @@ k_corr0_tc(DmGeom g, const __nv_bfloat16* __restrict__ a16, const float* __restr
                 }
             }
         } else {
-            // epilogue: warp w drains TMEM lane quadrant w % 4, pooled-row band (w - 2) / 4
+            // epilogue: warp w drains TMEM lane quadrant w % 4, pooled columns of part (w - 2) / 4
             const int quad = warp & 3;
-            const int part = (warp - 2) >> 2;
-            const bool interior = cx0 >= 0 && cy0 >= 0 && cx0 + CX <= W2 && cy0 + CY <= H2;
-            const EpiArgs ea{tmem + ((uint32_t)(quad * 32) << 16), quad * 32 + lane, m0, cx0, cy0, rx0, ry0, W2, H2, mw,
-                             mh, pitch, n0, lam, interior};
+            const EpiArgs ea{tmem + ((uint32_t)(quad * 32) << 16), quad * 32 + lane, (warp - 2) >> 2, cx0, cy0, W2, H2,
+                             lam, cx0 >= 0 && cy0 >= 0 && cx0 + CX <= W2 && cy0 + CY <= H2};
             for (int j = 0; j < nt; j++) {
                 const uint32_t ai = acc_it + j, b = ai & 1, aph = (ai >> 1) & 1;
-                if (!mbar_wait(bar_acc_full + 8 * b, aph, abort_flag, err)) break;
+                const bool ok = mbar_wait(bar_acc_full + 8 * b, aph, abort_flag, err);
+                // the staging buffer of this tile was last used two tiles ago: its
+                // TMA store must have finished reading before it is overwritten
+                if (store_leader) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                epi_barrier();
+                if (*abort_flag || !ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                if (part == 0) epilogue_band<0, 3>(ea, b, j, bar_acc_empty + 8 * b, pooled0, amax0);
-                else if (part == 1) epilogue_band<3, 5>(ea, b, j, bar_acc_empty + 8 * b, pooled0, amax0);
-                else epilogue_band<5, 7>(ea, b, j, bar_acc_empty + 8 * b, pooled0, amax0);
+                float* stf = sF + b * (OUT_F / 4);
+                unsigned char* stc = sC + b * OUT_C;
+                epilogue_tile(ea, b, bar_acc_empty + 8 * b, stf, stc);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                epi_barrier();
+                if (store_leader) {
+                    const int z = (m0 + j) * BM;
+                    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"
+                                 :: "l"(reinterpret_cast<uint64_t>(&tmap_f)), "r"(rx0), "r"(ry0), "r"(z), "r"(smem_u32(stf))
+                                 : "memory");
+                    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"
+                                 :: "l"(reinterpret_cast<uint64_t>(&tmap_c)), "r"(rx0), "r"(ry0), "r"(z), "r"(smem_u32(stc))
+                                 : "memory");
+                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                }
             }
         }
         a_it += nt;
@@ -328,8 +360,38 @@ k_corr0_tc(DmGeom g, const __nv_bfloat16* __restrict__ a16, const float* __restr
         __syncthreads();   // the epilogue has consumed every accumulator: the tensor core is done with sB
         if (*abort_flag) break;
     }
+    if (store_leader) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     __syncthreads();
     if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512));
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// 3-D map of a pooled level-0 array [n0][mh][pitch] (elements of `esize` bytes),
+// logical extent mw x mh x n0, box 16 x 3 x 128.
+bool make_map(CUtensorMap* m, void* base, CUtensorMapDataType dt, int esize, const DmGeom& g) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)g.dw[1], (cuuint64_t)g.dh[1], (cuuint64_t)g.npatch(0)};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.pitch(1) * esize, (cuuint64_t)g.pitch(1) * g.dh[1] * esize};
+    const cuuint32_t box[3] = {PX, PY, BM};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(m, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
@@ -343,6 +405,10 @@ cudaError_t dm_launch_corr0_bf16(const DmGeom& g, const float* d1, const float* 
                                  float* pooled0, unsigned char* amax0, cudaStream_t st) {
     const int n0 = g.npatch(0);
     const int n_mtiles = (n0 + BM - 1) / BM;
+    CUtensorMap mf, mc;
+    if (!make_map(&mf, pooled0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g) ||
+        !make_map(&mc, amax0, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, g))
+        return cudaErrorNotSupported;
     {
         long long total = (long long)n_mtiles * BM * (KD / 8);
         k_pack_a<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(g, d1, reinterpret_cast<__nv_bfloat16*>(a16), n_mtiles);
@@ -359,8 +425,8 @@ cudaError_t dm_launch_corr0_bf16(const DmGeom& g, const float* d1, const float* 
     const int tiles = ((g.dw[1] + PX - 1) / PX) * ((g.dh[1] + PY - 1) / PY);
     const int units = tiles * ((n_mtiles + M_CHUNK - 1) / M_CHUNK);
     const int grid = units < nsm ? units : nsm;
-    k_corr0_tc<<<grid, THREADS, SMEM, st>>>(g, reinterpret_cast<const __nv_bfloat16*>(a16), d2, lam, pooled0, amax0,
-                                           n_mtiles, reinterpret_cast<int*>(status));
+    k_corr0_tc<<<grid, THREADS, SMEM, st>>>(g, reinterpret_cast<const __nv_bfloat16*>(a16), d2, lam, mf, mc, n_mtiles,
+                                           reinterpret_cast<int*>(status));
     dm_count_launches(2);
     return cudaGetLastError();
 }

@@ -118,48 +118,61 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_pool_tiled(DmGeom g, in
         kid_index[tid] = (c >= 0 && vprev[c]) ? c : -1;
     }
     __syncthreads();
+    int ci[4];
+    const float* cbase[4];
     int n = 0;
 #pragma unroll
-    for (int i = 0; i < 4; i++) n += kid_index[i] >= 0;
+    for (int i = 0; i < 4; i++) {
+        ci[i] = kid_index[i];
+        cbase[i] = ci[i] >= 0 ? prev + (long long)ci[i] * g.psize(l) : prev;
+        n += ci[i] >= 0;
+    }
     // stage: child i, window rows qy0 + oy_i + [0, AH), columns xa + [0, KW)
-    const long long cs = (long long)mpitch * mh;
-    for (int e = tid; e < 4 * AH * (KW / 4); e += LEVEL_THREADS) {
-        const int i = e / (AH * (KW / 4));
-        const int rem = e - i * (AH * (KW / 4));
-        const int ay = rem / (KW / 4), v4 = rem - ay * (KW / 4);
+    constexpr int ROWV = KW / 4, PER_KID = AH * ROWV;
+    const unsigned kid_s = (unsigned)__cvta_generic_to_shared(&kid[0][0][0]);
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
         const int oy = (i & 1) ? 1 : -1;
-        const int c = kid_index[i];
-        const int ry = qy0 + ay + oy, x = xa + 4 * v4;
-        int bytes = 0;
-        const float* src = prev;
-        if (c >= 0 && ry >= 0 && ry < mh && x >= 0 && x < mw) {
-            bytes = min(16, 4 * (mw - x));
-            src = prev + c * cs + (long long)ry * mpitch + x;
+        for (int e = tid; e < PER_KID; e += LEVEL_THREADS) {
+            const int ay = e / ROWV, v4 = e - ay * ROWV;
+            const int ry = qy0 + ay + oy, x = xa + 4 * v4;
+            int bytes = 0;
+            const float* src = prev;
+            if (ci[i] >= 0 && ry >= 0 && ry < mh && x >= 0 && x < mw) {
+                bytes = min(16, 4 * (mw - x));
+                src = cbase[i] + (long long)ry * mpitch + x;
+            }
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                         :: "r"(kid_s + 16u * (unsigned)(i * PER_KID + e)), "l"(src), "r"(bytes) : "memory");
         }
-        const unsigned dst = (unsigned)__cvta_generic_to_shared(&kid[i][ay][4 * v4]);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(bytes) : "memory");
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
-    // averages: compensated sum over existing children in order i = 0..3, / n.
-    // Average (ay, ax) uses child i at staged column ax + ox_i + 3.
-    for (int ay = warp; ay < AH; ay += LEVEL_THREADS / 32) {
+    // averages over a flat index: compensated sum over existing children in
+    // order i = 0..3 (the first existing child starts the sum: 0 + v = v
+    // exactly, so this equals starting from zero), then / n.  Average (ay, ax)
+    // uses child i at staged column ax + ox_i + 3.
+    for (int e = tid; e < AH * AW; e += LEVEL_THREADS) {
+        const int ay = e / AW, ax = e - ay * AW;
+        float s = 0.0f, comp = 0.0f;
+        bool first = true;
 #pragma unroll
-        for (int ax = lane; ax < AW; ax += 32) {
-            float s = 0.0f, comp = 0.0f;
-#pragma unroll
-            for (int i = 0; i < 4; i++) {
-                if (kid_index[i] < 0) continue;
-                const int ox = (i >= 2) ? 1 : -1;
-                float v = kid[i][ay][ax + ox + 3];
-                float t = __fadd_rn(s, v);
-                float bp = __fsub_rn(t, s);
-                float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
+        for (int i = 0; i < 4; i++) {
+            if (ci[i] < 0) continue;
+            const int ox = (i >= 2) ? 1 : -1;
+            const float v = kid[i][ay][ax + ox + 3];
+            if (first) {
+                s = v;
+                first = false;
+            } else {
+                const float t = __fadd_rn(s, v);
+                const float bp = __fsub_rn(t, s);
+                const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
                 s = t;
                 comp = __fadd_rn(comp, err);
             }
-            avg[ay][ax] = div_n(__fadd_rn(s, comp), n);
         }
+        avg[ay][ax] = div_n(__fadd_rn(s, comp), n);
     }
     __syncthreads();
     // 3x3 / 2 max-pool over in-domain averages, first strict maximum, power

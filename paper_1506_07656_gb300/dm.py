@@ -37,6 +37,11 @@ class DmMatch(C.Structure):
 
 MATCH_BYTES = C.sizeof(DmMatch)
 
+
+class DmPair(C.Structure):
+    _fields_ = [("d_img1", C.c_void_p), ("W1", C.c_int), ("H1", C.c_int), ("d_img2", C.c_void_p), ("W2", C.c_int),
+                ("H2", C.c_int), ("d_out", C.c_void_p), ("capacity", C.c_int), ("d_count", C.c_void_p)]
+
 # Exported symbols and their signatures (restype dm_status = c_int unless noted).
 _SIGS = {
     "dm_config_default": (None, [C.POINTER(DmConfig)]),
@@ -60,6 +65,8 @@ _SIGS = {
     "dm_match_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                 C.c_size_t, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_void_p]),
     "dm_read_status": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.c_void_p, C.c_int, C.c_void_p]),
+    "dm_batch_workspace_bytes": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_size_t)]),
+    "dm_match_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "dm_backtrack_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "dm_timing_start": (C.c_int, [C.c_void_p, C.c_int]),
     "dm_timing_read": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
@@ -235,6 +242,29 @@ def dm_read_status(ctx, d_ws, n_levels: int, stream=None):
     st = load().dm_read_status(ctx, _dptr(d_ws), C.byref(status), reached, n_levels, _stream_ptr(stream))
     _check(ctx, st, "dm_read_status")
     return status.value, list(reached)
+
+
+def make_pairs(items):
+    """items: list of (d_img1, d_img2, d_out, d_count) torch tensors -> ctypes array of DmPair."""
+    arr = (DmPair * len(items))()
+    for k, (i1, i2, out, cnt) in enumerate(items):
+        H1, W1 = i1.shape
+        H2, W2 = i2.shape
+        arr[k] = DmPair(_dptr(i1), W1, H1, _dptr(i2), W2, H2, _dptr(out),
+                        out.numel() * out.element_size() // MATCH_BYTES, _dptr(cnt))
+    return arr
+
+
+def dm_batch_workspace_bytes(ctx, pairs) -> int:
+    b = C.c_size_t()
+    _check(ctx, load().dm_batch_workspace_bytes(ctx, len(pairs), pairs, C.byref(b)), "dm_batch_workspace_bytes")
+    return b.value
+
+
+def dm_match_batch(ctx, pairs, d_ws, stream=None):
+    st = load().dm_match_batch(ctx, len(pairs), pairs, _dptr(d_ws), d_ws.numel() * d_ws.element_size(),
+                               _stream_ptr(stream))
+    _check(ctx, st, "dm_match_batch")
 
 
 def dm_backtrack_noalloc(ctx, pyr, d_out, d_count, stream=None):

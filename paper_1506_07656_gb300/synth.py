@@ -110,7 +110,7 @@ def _smooth_field(W, H, rng, max_disp, cell):
 
 
 def make_pair_smooth(W: int, H: int, seed: int, max_disp: float = 6.0,
-                     gain: float = 1.05, noise_sigma: float = 0.01) -> Pair:
+                     gain: float = 1.05, noise_sigma: float = 0.01, with_flow: bool = True) -> Pair:
     """Value-noise image warped by a seeded smooth displacement field.
 
     I1 = 4-octave value noise in [0,1].  I2(x') = gain * I1(x' - d(x')) + N(0, sigma^2),
@@ -128,8 +128,11 @@ def make_pair_smooth(W: int, H: int, seed: int, max_disp: float = 6.0,
     img2 = gain * bilinear(img1, xs - src[0], ys - src[1])
     img2 = img2 + rng.normal(0.0, noise_sigma, size=img2.shape)
     img2 = np.clip(img2, 0.0, 1.0)
-    flow = _invert_backward_map(lambda x, y: x - d_at(x, y)[0],
-                                lambda x, y: y - d_at(x, y)[1], W, H)
+    if with_flow:
+        flow = _invert_backward_map(lambda x, y: x - d_at(x, y)[0],
+                                    lambda x, y: y - d_at(x, y)[1], W, H)
+    else:
+        flow = np.zeros((H, W, 2))
     return Pair(img1.astype(np.float32), img2.astype(np.float32), flow.astype(np.float32), seed,
                 f"value-noise {W}x{H}, smooth warp max {max_disp}px, gain {gain}, noise {noise_sigma}")
 

@@ -1,0 +1,99 @@
+"""Batched form: dm_match_batch over pairs of mixed sizes, and its CUDA-graph replay.
+
+Each pair of a batch must give exactly the matches dm_match gives for it
+alone; a captured graph of the batch, replayed on new image contents written
+into the same input buffers, must give the matches of those new images.
+"""
+import numpy as np
+import pytest
+
+from paper_1506_07656_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(64, 48), (37, 29), (96, 72), (130, 70), (64, 48)]
+
+
+@pytest.fixture(scope="module", params=["fp32", "bf16"])
+def env(request):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1506_07656_gb300 import build, dm
+    build.build()
+    ctx = dm.Context(dm.DM_BF16 if request.param == "bf16" else dm.DM_FP32)
+    yield torch, dm, ctx
+    ctx.close()
+
+
+def _alloc(torch, dm, sizes, seed0):
+    items, host = [], []
+    for k, (W, H) in enumerate(sizes):
+        pr = synth.make_pair_smooth(W, H, seed=seed0 + k)
+        n0 = dm.dm_geometry(W, H, W, H)["n_patch0"]
+        i1 = torch.from_numpy(pr.img1).cuda()
+        i2 = torch.from_numpy(pr.img2).cuda()
+        out = torch.zeros((n0, 5), dtype=torch.float32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+        items.append((i1, i2, out, cnt))
+        host.append(pr)
+    return items, host
+
+
+def _single(ctx, pr):
+    return ctx.match(pr.img1, pr.img2).cpu().numpy()
+
+
+def test_batch_equals_single_pairs(env):
+    torch, dm, ctx = env
+    items, host = _alloc(torch, dm, SIZES, 40)
+    pairs = dm.make_pairs(items)
+    ws = torch.empty(dm.dm_batch_workspace_bytes(ctx.ctx, pairs), dtype=torch.uint8, device="cuda")
+    dm.dm_match_batch(ctx.ctx, pairs, ws)
+    torch.cuda.synchronize()
+    for (i1, i2, out, cnt), pr in zip(items, host):
+        n = int(cnt.item())
+        np.testing.assert_array_equal(out[:n].cpu().numpy(), _single(ctx, pr))
+
+
+def test_batch_graph_replay(env):
+    torch, dm, ctx = env
+    items, host = _alloc(torch, dm, SIZES, 60)
+    pairs = dm.make_pairs(items)
+    ws = torch.empty(dm.dm_batch_workspace_bytes(ctx.ctx, pairs), dtype=torch.uint8, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        dm.dm_match_batch(ctx.ctx, pairs, ws, side)       # uncaptured first call
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        dm.dm_match_batch(ctx.ctx, pairs, ws, side)
+    for rep, seed0 in enumerate((80, 100)):
+        new = [synth.make_pair_smooth(W, H, seed=seed0 + k) for k, (W, H) in enumerate(SIZES)]
+        for (i1, i2, out, cnt), pr in zip(items, new):
+            i1.copy_(torch.from_numpy(pr.img1))
+            i2.copy_(torch.from_numpy(pr.img2))
+            out.zero_()
+            cnt.zero_()
+        torch.cuda.synchronize()
+        graph.replay()
+        torch.cuda.synchronize()
+        for (i1, i2, out, cnt), pr in zip(items, new):
+            n = int(cnt.item())
+            np.testing.assert_array_equal(out[:n].cpu().numpy(), _single(ctx, pr))
+
+
+def test_batch_rejects_bad_pair_before_launch(env):
+    torch, dm, ctx = env
+    items, _ = _alloc(torch, dm, [(64, 48)], 120)
+    bad = list(items) + [(torch.zeros((3, 3), device="cuda"), torch.zeros((3, 3), device="cuda"),
+                          torch.zeros((1, 5), device="cuda"), torch.zeros(1, dtype=torch.int32, device="cuda"))]
+    pairs = dm.make_pairs(bad)
+    ws = torch.empty(1 << 24, dtype=torch.uint8, device="cuda")
+    items[0][3].fill_(-7)
+    with pytest.raises(dm.DmError) as e:
+        dm.dm_match_batch(ctx.ctx, pairs, ws)
+    assert e.value.status == dm.DM_EINVAL
+    torch.cuda.synchronize()
+    assert int(items[0][3].item()) == -7        # nothing ran for the valid first pair either
