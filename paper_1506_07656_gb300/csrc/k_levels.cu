@@ -88,6 +88,7 @@ __device__ __forceinline__ bool load_kids(const DmGeom& g, int l, int p, const u
 constexpr int TW = 32, TH = 16;                // pooled outputs per CTA (lane, 2 x warp)
 constexpr int AW = 2 * TW + 1, AH = 2 * TH + 1;  // averages per CTA (65 x 33)
 constexpr int KW = 72;                           // staged child columns: 18 aligned float4
+constexpr int AWP = 68;                          // padded row of the averages (16-byte aligned rows)
 constexpr int LEVEL_THREADS = 256;
 
 // x / n rounded once, for n in 1..4: multiplications by 1, 1/2, 1/4 are exact,
@@ -96,13 +97,78 @@ __device__ __forceinline__ float div_n(float x, int n) {
     return n == 3 ? __fdiv_rn(x, 3.0f) : __fmul_rn(x, n == 4 ? 0.25f : (n == 2 ? 0.5f : 1.0f));
 }
 
+// Knuth TwoSum step of the compensated child sum.
+__device__ __forceinline__ void two_sum_add(float& s, float& comp, float v) {
+    const float t = __fadd_rn(s, v);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
+    s = t;
+    comp = __fadd_rn(comp, err);
+}
+
+// Average at staged position (ay, column c of child 0's frame) from the four
+// child windows: child i contributes kid[i][ay][ax + ox_i + 3].
+template <bool ALL4>
+__device__ __forceinline__ float4 avg4(const float (*kid)[AH][KW], int ay, int ax, const int* ci, int n) {
+    // children with ox = -1 (i = 0, 1) read columns ax+2 .. ax+5 (8-byte aligned),
+    // children with ox = +1 (i = 2, 3) read columns ax+4 .. ax+7 (16-byte aligned)
+    float v[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        if (!ALL4 && ci[i] < 0) continue;
+        if (i < 2) {
+            const float2 a = *reinterpret_cast<const float2*>(&kid[i][ay][ax + 2]);
+            const float2 b = *reinterpret_cast<const float2*>(&kid[i][ay][ax + 4]);
+            v[i][0] = a.x; v[i][1] = a.y; v[i][2] = b.x; v[i][3] = b.y;
+        } else {
+            const float4 a = *reinterpret_cast<const float4*>(&kid[i][ay][ax + 4]);
+            v[i][0] = a.x; v[i][1] = a.y; v[i][2] = a.z; v[i][3] = a.w;
+        }
+    }
+    float r[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        if (ALL4) {
+            float s = v[0][c], comp = 0.0f;
+            two_sum_add(s, comp, v[1][c]);
+            two_sum_add(s, comp, v[2][c]);
+            two_sum_add(s, comp, v[3][c]);
+            r[c] = __fmul_rn(__fadd_rn(s, comp), 0.25f);
+        } else {
+            float s = 0.0f, comp = 0.0f;
+            bool first = true;
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                if (ci[i] < 0) continue;
+                if (first) { s = v[i][c]; first = false; }
+                else two_sum_add(s, comp, v[i][c]);
+            }
+            r[c] = div_n(__fadd_rn(s, comp), n);
+        }
+    }
+    return make_float4(r[0], r[1], r[2], r[3]);
+}
+
+__device__ __forceinline__ float avg1(const float (*kid)[AH][KW], int ay, int ax, const int* ci, int n) {
+    float s = 0.0f, comp = 0.0f;
+    bool first = true;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        if (ci[i] < 0) continue;
+        const float v = kid[i][ay][ax + ((i >= 2) ? 1 : -1) + 3];
+        if (first) { s = v; first = false; }
+        else two_sum_add(s, comp, v);
+    }
+    return div_n(__fadd_rn(s, comp), n);
+}
+
 // Level l in [1, L-1]: grid (patch, tile).
 __global__ void __launch_bounds__(LEVEL_THREADS) k_level_pool_tiled(DmGeom g, int l, const unsigned char* __restrict__ vprev,
                                                                     const unsigned char* __restrict__ vcur,
                                                                     const float* __restrict__ prev, float* __restrict__ out,
                                                                     unsigned char* __restrict__ amax, float lam) {
     __shared__ __align__(16) float kid[4][AH][KW];
-    __shared__ float avg[AH][AW];
+    __shared__ __align__(16) float avg[AH][AWP];
     __shared__ int kid_index[4];
     const int p = blockIdx.x;
     if (!vcur[p]) return;
@@ -148,32 +214,16 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_pool_tiled(DmGeom g, in
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
-    // averages over a flat index: compensated sum over existing children in
-    // order i = 0..3 (the first existing child starts the sum: 0 + v = v
-    // exactly, so this equals starting from zero), then / n.  Average (ay, ax)
-    // uses child i at staged column ax + ox_i + 3.
-    for (int e = tid; e < AH * AW; e += LEVEL_THREADS) {
-        const int ay = e / AW, ax = e - ay * AW;
-        float s = 0.0f, comp = 0.0f;
-        bool first = true;
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-            if (ci[i] < 0) continue;
-            const int ox = (i >= 2) ? 1 : -1;
-            const float v = kid[i][ay][ax + ox + 3];
-            if (first) {
-                s = v;
-                first = false;
-            } else {
-                const float t = __fadd_rn(s, v);
-                const float bp = __fsub_rn(t, s);
-                const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
-                s = t;
-                comp = __fadd_rn(comp, err);
-            }
-        }
-        avg[ay][ax] = div_n(__fadd_rn(s, comp), n);
+    // averages: compensated sum over existing children in order i = 0..3 (the
+    // first existing child starts the sum: 0 + v = v exactly, so this equals
+    // starting from zero), then / n; four adjacent columns per item.
+    constexpr int G4 = (AW - 1) / 4;                 // 16 groups of 4 columns, then column 64
+    for (int e = tid; e < AH * G4; e += LEVEL_THREADS) {
+        const int ay = e / G4, ax = 4 * (e - ay * G4);
+        const float4 a = (n == 4) ? avg4<true>(kid, ay, ax, ci, n) : avg4<false>(kid, ay, ax, ci, n);
+        *reinterpret_cast<float4*>(&avg[ay][ax]) = a;
     }
+    for (int ay = tid; ay < AH; ay += LEVEL_THREADS) avg[ay][AW - 1] = avg1(kid, ay, AW - 1, ci, n);
     __syncthreads();
     // 3x3 / 2 max-pool over in-domain averages, first strict maximum, power
     const int rx = rx0 + lane;
