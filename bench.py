@@ -290,6 +290,13 @@ def _measure_batch(dm, torch, ctx, a, rank):
             "graph": "one CUDA graph of dm_match_batch (all 48 pairs), replayed", "matches": n_match}
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
+# ncu captures summarised in profiles/, scaled from the 512x224 capture to the
+# 1024x436 workload by the number of pooled outputs (x15.1).  None where no
+# capture of the current kernel version exists.
+TRAFFIC_1024x436 = {"level0_bf16": 16.7e9, "level0_fp32": None, "levels": None}
+
+
 def _rooflines(r, prec_bf16, W, H, peaks, nsm):
     geo = r["geo"]
     n0 = geo["n_patch0"]
@@ -300,13 +307,13 @@ def _rooflines(r, prec_bf16, W, H, peaks, nsm):
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         peak = nsm * 128 * 2 * sm_max * 1e6 / 1e12
         corr = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_corr0_f32 (level-0 correlation + fused pool/power, FP32 FMA pipes)",
+                "traffic": TRAFFIC_1024x436["level0_fp32"] if (W, H) == (1024, 436) else None, "kernel": "k_corr0_f32 (level-0 correlation + fused pool/power, FP32 FMA pipes)",
                 "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
                 "algorithmic_flop_per_launch": flop, "launch_ms": corr_ms}
     else:
         peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
         corr = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_corr0_tc (level-0 correlation on tcgen05, BF16 in / FP32 accumulate, fused pool/power)",
+                "traffic": TRAFFIC_1024x436["level0_bf16"] if (W, H) == (1024, 436) else None, "kernel": "k_corr0_tc (level-0 correlation on tcgen05, BF16 in / FP32 accumulate, fused pool/power)",
                 "peak_source": ("bf16_tflops_sustained of measured" if "bf16_tflops_sustained" in peaks
                                 else "fallback 1.7 PFLOP/s sustained"),
                 "algorithmic_flop_per_launch": flop, "launch_ms": corr_ms}
@@ -318,7 +325,8 @@ def _rooflines(r, prec_bf16, W, H, peaks, nsm):
     lev_ms = r["stages"]["levels"]
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     gbs = (rd + wr) / (lev_ms / 1e3) / 1e9
-    lev = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak, "traffic": None,
+    lev = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+           "traffic": TRAFFIC_1024x436["levels"] if (W, H) == (1024, 436) else None,
            "kernel": "k_level_pool_tiled + k_level_top (pyramid levels >= 1)",
            "peak_source": "hbm_gbs of measured" if "hbm_gbs" in peaks else "fallback 6.8 TB/s",
            "algorithmic_bytes_per_launch_set": rd + wr, "launch_ms": lev_ms}

@@ -237,6 +237,26 @@ def match(img1: np.ndarray, img2: np.ndarray, prec: str = "f64", **cfg):
     return reciprocal(pyr, bt), pyr, bt
 
 
+def loss_grad(d1: np.ndarray, d2: np.ndarray, prec: str = "f64", lam: float = DEFAULT_CFG["lam"]):
+    """Differentiable form: loss = sum over existing top patches of max_q C_L, and
+    its gradients with respect to both descriptor fields (small inputs only)."""
+    dt = _dtype(prec)
+    d1 = np.ascontiguousarray(d1, dtype=dt)
+    d2 = np.ascontiguousarray(d2, dtype=dt)
+    H1, W1, _ = d1.shape
+    H2, W2, _ = d2.shape
+    g1 = np.zeros_like(d1)
+    g2 = np.zeros_like(d2)
+    loss = C.c_double()
+    lib = _lib(prec)
+    lib.orc_loss_grad.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_double,
+                                  C.c_void_p, C.c_void_p, C.c_void_p]
+    rc = lib.orc_loss_grad(_ptr(d1), W1, H1, _ptr(d2), W2, H2, float(lam), C.byref(loss), _ptr(g1), _ptr(g2))
+    if rc != 0:
+        raise ValueError("loss_grad oracle failed")
+    return loss.value, g1, g2
+
+
 def pow_r(x: float, lam: float, prec: str = "f32") -> float:
     lib = _lib(prec)
     lib.orc_pow_r.restype = C.c_double

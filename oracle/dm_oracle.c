@@ -628,3 +628,170 @@ int orc_reciprocal(int W1, int H1, int W2, int H2, const real* bestP_s, const lo
     }
     return n;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Differentiable form (adjoint of Algorithm 1; the paper has no loss).       */
+/* Loss = sum over existing top patches p of max_q C_L(p, q) (first maximum). */
+/* Gradients with respect to both descriptor fields, by the chain rule        */
+/* through the rectification (Eq. 11), the shifted average (Eq. 12), the      */
+/* max-pooling with its argmax (Eq. 9) and the correlation (Eq. 3-4).  Plain  */
+/* dense arrays and loops in the forward's order; the unpooled maps of every  */
+/* level are kept (small inputs only).                                        */
+/* ------------------------------------------------------------------------- */
+int orc_loss_grad(const real* d1, int W1, int H1, const real* d2, int W2, int H2, double lambda, double* loss,
+                  real* g1, real* g2) {
+    geom g;
+    if (make_geom(W1, H1, W2, H2, &g)) return -1;
+    const real lam = (real)lambda;
+    const int L = g.L;
+    /* forward, keeping everything: U[l] = unrectified map A_l (l >= 1) or C0 (l = 0)
+     * on domain l; P[l] pooled rectified maps on domain l+1 with argmax. */
+    real* U[ORC_MAXL + 1];
+    real* P[ORC_MAXL];
+    uint8_t* M[ORC_MAXL];
+    uint8_t* V[ORC_MAXL + 1];
+    for (int l = 0; l <= L; l++) {
+        U[l] = (real*)calloc((size_t)npatch(&g, l) * g.dw[l] * g.dh[l], sizeof(real));
+        V[l] = (uint8_t*)calloc((size_t)npatch(&g, l), 1);
+        if (l < L) {
+            P[l] = (real*)calloc((size_t)npatch(&g, l) * g.dw[l + 1] * g.dh[l + 1], sizeof(real));
+            M[l] = (uint8_t*)calloc((size_t)npatch(&g, l) * g.dw[l + 1] * g.dh[l + 1], 1);
+        }
+    }
+    const int n0 = npatch(&g, 0);
+    memset(V[0], 1, (size_t)n0);
+    for (int p = 0; p < n0; p++) {
+        int px = 4 * (p % g.P0x) + 2, py = 4 * (p / g.P0x) + 2;
+        for (int ty = 0; ty < H2; ty++)
+            for (int tx = 0; tx < W2; tx++) U[0][((size_t)p * H2 + ty) * W2 + tx] = corr0(d1, W1, H1, d2, W2, H2, px, py, tx, ty);
+    }
+    for (int l = 0; l <= L; l++) {
+        const int np = npatch(&g, l), mw = g.dw[l], mh = g.dh[l];
+        if (l >= 1) {
+            for (int p = 0; p < np; p++) {
+                int n = 0;
+                for (int i = 0; i < 4; i++) {
+                    int c = child_index(&g, l, p % g.Lx, p / g.Lx, i);
+                    if (c >= 0 && V[l - 1][c]) n++;
+                }
+                V[l][p] = n > 0;
+                if (!n) continue;
+                for (int qy = 0; qy < mh; qy++)
+                    for (int qx = 0; qx < mw; qx++) {
+                        real s = 0;
+                        for (int i = 0; i < 4; i++) {
+                            int c = child_index(&g, l, p % g.Lx, p / g.Lx, i);
+                            if (c < 0 || !V[l - 1][c]) continue;
+                            int rx = qx + ((i >= 2) ? 1 : -1), ry = qy + ((i & 1) ? 1 : -1);
+                            if (rx >= 0 && ry >= 0 && rx < mw && ry < mh) s += P[l - 1][((size_t)c * mh + ry) * mw + rx];
+                        }
+                        U[l][((size_t)p * mh + qy) * mw + qx] = s / n;
+                    }
+            }
+        }
+        if (l < L) {   /* pool the rectified map */
+            const int ow = g.dw[l + 1], oh = g.dh[l + 1];
+            for (int p = 0; p < np; p++) {
+                if (!V[l][p]) continue;
+                for (int ry = 0; ry < oh; ry++)
+                    for (int rx = 0; rx < ow; rx++) {
+                        real best = RNEG_INF;
+                        int code = 4;
+                        for (int my = -1; my <= 1; my++)
+                            for (int mx = -1; mx <= 1; mx++) {
+                                int x = 2 * rx + mx, y = 2 * ry + my;
+                                if (x < 0 || y < 0 || x >= mw || y >= mh) continue;
+                                real v = RPOW(U[l][((size_t)p * mh + y) * mw + x], lam);
+                                if (v > best) { best = v; code = (my + 1) * 3 + (mx + 1); }
+                            }
+                        P[l][((size_t)p * oh + ry) * ow + rx] = best;
+                        M[l][((size_t)p * oh + ry) * ow + rx] = (uint8_t)code;
+                    }
+            }
+        }
+    }
+    /* adjoints: dU[l] on the unrectified maps */
+    real* dU[ORC_MAXL + 1];
+    for (int l = 0; l <= L; l++) dU[l] = (real*)calloc((size_t)npatch(&g, l) * g.dw[l] * g.dh[l], sizeof(real));
+    double total = 0.0;
+    {
+        const int np = npatch(&g, L), mw = g.dw[L], mh = g.dh[L];
+        for (int p = 0; p < np; p++) {
+            if (!V[L][p]) continue;
+            real best = RNEG_INF;
+            int qb = 0;
+            for (int q = 0; q < mw * mh; q++) {
+                real v = RPOW(U[L][(size_t)p * mw * mh + q], lam);
+                if (v > best) { best = v; qb = q; }
+            }
+            total += (double)best;
+            real u = U[L][(size_t)p * mw * mh + qb];
+            dU[L][(size_t)p * mw * mh + qb] = u > 0 ? lam * RPOW(u, lam - 1) : 0;   /* d(u^lam)/du */
+        }
+    }
+    for (int l = L; l >= 1; l--) {
+        const int np = npatch(&g, l), mw = g.dw[l], mh = g.dh[l];
+        real* dP = (real*)calloc((size_t)npatch(&g, l - 1) * mw * mh, sizeof(real));
+        for (int p = 0; p < np; p++) {
+            if (!V[l][p]) continue;
+            int n = 0;
+            for (int i = 0; i < 4; i++) {
+                int c = child_index(&g, l, p % g.Lx, p / g.Lx, i);
+                if (c >= 0 && V[l - 1][c]) n++;
+            }
+            for (int qy = 0; qy < mh; qy++)
+                for (int qx = 0; qx < mw; qx++) {
+                    real d = dU[l][((size_t)p * mh + qy) * mw + qx];
+                    if (d == 0) continue;
+                    for (int i = 0; i < 4; i++) {
+                        int c = child_index(&g, l, p % g.Lx, p / g.Lx, i);
+                        if (c < 0 || !V[l - 1][c]) continue;
+                        int rx = qx + ((i >= 2) ? 1 : -1), ry = qy + ((i & 1) ? 1 : -1);
+                        if (rx >= 0 && ry >= 0 && rx < mw && ry < mh) dP[((size_t)c * mh + ry) * mw + rx] += d / n;
+                    }
+                }
+        }
+        /* pooled value = (U at the argmax)^lam */
+        const int cw = g.dw[l - 1], ch = g.dh[l - 1];
+        for (int c = 0; c < npatch(&g, l - 1); c++) {
+            if (!V[l - 1][c]) continue;
+            for (int ry = 0; ry < mh; ry++)
+                for (int rx = 0; rx < mw; rx++) {
+                    real d = dP[((size_t)c * mh + ry) * mw + rx];
+                    if (d == 0) continue;
+                    int code = M[l - 1][((size_t)c * mh + ry) * mw + rx];
+                    int tx = 2 * rx + code % 3 - 1, ty = 2 * ry + code / 3 - 1;
+                    real u = U[l - 1][((size_t)c * ch + ty) * cw + tx];
+                    dU[l - 1][((size_t)c * ch + ty) * cw + tx] += u > 0 ? d * lam * RPOW(u, lam - 1) : 0;
+                }
+        }
+        free(dP);
+    }
+    /* level 0: C0(p, t) = (1/16) sum a_p[k] b_t[k] */
+    memset(g1, 0, sizeof(real) * (size_t)W1 * H1 * 9);
+    memset(g2, 0, sizeof(real) * (size_t)W2 * H2 * 9);
+    for (int p = 0; p < n0; p++) {
+        int px = 4 * (p % g.P0x) + 2, py = 4 * (p / g.P0x) + 2;
+        for (int ty = 0; ty < H2; ty++)
+            for (int tx = 0; tx < W2; tx++) {
+                real d = dU[0][((size_t)p * H2 + ty) * W2 + tx];
+                if (d == 0) continue;
+                d = d / 16;
+                for (int dy = 0; dy < 4; dy++)
+                    for (int dx = 0; dx < 4; dx++) {
+                        int x1 = px - 2 + dx, y1 = py - 2 + dy, x2 = tx - 2 + dx, y2 = ty - 2 + dy;
+                        if (x1 >= W1 || y1 >= H1 || x2 < 0 || y2 < 0 || x2 >= W2 || y2 >= H2) continue;
+                        for (int c = 0; c < 9; c++) {
+                            g1[((size_t)y1 * W1 + x1) * 9 + c] += d * d2[((size_t)y2 * W2 + x2) * 9 + c];
+                            g2[((size_t)y2 * W2 + x2) * 9 + c] += d * d1[((size_t)y1 * W1 + x1) * 9 + c];
+                        }
+                    }
+            }
+    }
+    *loss = total;
+    for (int l = 0; l <= L; l++) {
+        free(U[l]); free(V[l]); free(dU[l]);
+        if (l < L) { free(P[l]); free(M[l]); }
+    }
+    return 0;
+}

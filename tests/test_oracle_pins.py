@@ -514,3 +514,40 @@ def test_paper_constants_fixture():
     N, dN = 4 * 2 ** l, 2 ** l - 1
     assert abs((N + 2 * dN) / N - vals["scale_max"]) < 1e-9
     assert abs((N - 2 * dN) / N - vals["scale_min"]) < 1e-9
+
+
+# --------------------------------------------------------------------------- #
+# P12: gradient of the differentiable form == central finite differences      #
+# --------------------------------------------------------------------------- #
+@pytest.mark.parametrize("W1,H1,W2,H2,seed", [(20, 16, 22, 15, 1), (13, 9, 11, 12, 2)])
+def test_p12_gradient_finite_differences(oracle_mod, W1, H1, W2, H2, seed):
+    d1 = _rand_desc(W1, H1, seed)
+    d2 = _rand_desc(W2, H2, seed + 50)
+    loss, g1, g2 = oracle_mod.loss_grad(d1, d2)
+    rng = np.random.default_rng(seed)
+    h = 1e-6
+    checked = 0
+    for which, d, g in ((1, d1, g1), (2, d2, g2)):
+        flat = np.flatnonzero(np.abs(g) > 0)
+        picks = np.concatenate([rng.choice(flat, size=min(20, len(flat)), replace=False),
+                                rng.choice(g.size, size=5, replace=False)])
+        for k in picks:
+            dp, dm = d.copy(), d.copy()
+            dp.flat[k] += h
+            dm.flat[k] -= h
+            lp = oracle_mod.loss_grad(dp if which == 1 else d1, dp if which == 2 else d2)[0]
+            lm = oracle_mod.loss_grad(dm if which == 1 else d1, dm if which == 2 else d2)[0]
+            fd = (lp - lm) / (2 * h)
+            # a step that flips an argmax makes the loss non-smooth: skip such entries
+            # (detected by a half step disagreeing with the full step)
+            dp2, dm2 = d.copy(), d.copy()
+            dp2.flat[k] += h / 2
+            dm2.flat[k] -= h / 2
+            lp2 = oracle_mod.loss_grad(dp2 if which == 1 else d1, dp2 if which == 2 else d2)[0]
+            lm2 = oracle_mod.loss_grad(dm2 if which == 1 else d1, dm2 if which == 2 else d2)[0]
+            fd2 = (lp2 - lm2) / h
+            if abs(fd - fd2) > 1e-4 * max(1.0, abs(fd)):
+                continue
+            assert abs(fd - g.flat[k]) <= 1e-5 * max(1.0, abs(fd)), (which, k, fd, g.flat[k])
+            checked += 1
+    assert checked >= 40
