@@ -178,6 +178,23 @@ dm_status dm_match_host(dm_ctx* ctx, const float* h_img1, int W1, int H1, const 
 dm_status dm_read_status(dm_ctx* ctx, const void* d_ws, int* status, long long* reached, int n_reached,
                          void* stream);
 
+/* Differentiable form (the paper defines no loss; see the design notes).
+ * loss = sum over the existing top-level patches p of max_q C_L(p, q) (first
+ * maximum), for the pyramid `pyr` built by dm_correlate_pyramid from d_desc1 /
+ * d_desc2 (which must be unchanged).  Writes *d_loss (device float; summed in
+ * double over patches in patch order), d_parts[p] (device, optional: the
+ * per-patch maxima, [n_patch]) and, unless d_g1 or d_g2 is NULL, the
+ * gradients d loss / d desc1 ([H1][W1][9]) and d loss / d desc2 ([H2][W2][9]).
+ * The backward follows the forward exactly: through the power (Eq. 11), the
+ * shifted average (Eq. 12), the max-pooling argmax saved by the forward
+ * (Eq. 9) and the level-0 correlation (Eq. 3-4), whose values at the argmax
+ * positions are recomputed instead of stored; level 0 is processed in chunks
+ * of patches so that its dense block stays below 1 GiB.  All sums have a
+ * fixed order: the gradient is deterministic.  d_ws >= dm_grad_workspace_bytes. */
+dm_status dm_grad_workspace_bytes(const dm_ctx* ctx, int W1, int H1, int W2, int H2, size_t* bytes);
+dm_status dm_loss_grad(dm_ctx* ctx, const dm_pyramid* pyr, const float* d_desc1, const float* d_desc2, void* d_ws,
+                       size_t ws_bytes, float* d_loss, float* d_parts, float* d_g1, float* d_g2, void* stream);
+
 /* One image pair of a batch (device buffers, as for dm_match). */
 typedef struct {
     const float* d_img1;

@@ -506,6 +506,36 @@ dm_status dm_match_host(dm_ctx* ctx, const float* h_img1, int W1, int H1, const 
     return DM_OK;
 }
 
+dm_status dm_grad_workspace_bytes(const dm_ctx* ctx, int W1, int H1, int W2, int H2, size_t* bytes) {
+    if (!ctx || !bytes) return DM_EINVAL;
+    DmGeom g;
+    dm_status s = check_geom(const_cast<dm_ctx*>(ctx), W1, H1, W2, H2, &g);
+    if (s != DM_OK) return s;
+    DmGradLayout gl;
+    dm_grad_layout(g, &gl);
+    *bytes = gl.bytes;
+    return DM_OK;
+}
+
+dm_status dm_loss_grad(dm_ctx* ctx, const dm_pyramid* pyr, const float* d_desc1, const float* d_desc2, void* d_ws,
+                       size_t ws_bytes, float* d_loss, float* d_parts, float* d_g1, float* d_g2, void* stream) {
+    if (!ctx) return DM_EINVAL;
+    if (!pyr || !d_desc1 || !d_desc2 || !d_ws || !d_loss) return fail(ctx, DM_EINVAL, "dm_loss_grad: bad arguments");
+    if (!aligned256(d_ws)) return fail(ctx, DM_EINVAL, "workspace must be 256-byte aligned");
+    DmGradLayout gl;
+    dm_grad_layout(pyr->g, &gl);
+    if (ws_bytes < gl.bytes) return fail(ctx, DM_ENOMEM, "gradient workspace %zu < %zu bytes", ws_bytes, gl.bytes);
+    DevGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = dm_launch_loss_grad(pyr->g, *pyr, d_desc1, d_desc2, ctx->cfg.lambda, gl, (char*)d_ws, d_loss, d_g1, d_g2, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gradient kernels");
+    if (d_parts) {
+        e = cudaMemcpyAsync(d_parts, (char*)d_ws + gl.parts, sizeof(float) * pyr->g.npatch(pyr->g.L), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "copy per-patch maxima");
+    }
+    return DM_OK;
+}
+
 dm_status dm_batch_workspace_bytes(const dm_ctx* ctx, int n, const dm_pair* pairs, size_t* bytes) {
     if (!ctx || n < 0 || (n > 0 && !pairs) || !bytes) return DM_EINVAL;
     size_t best = 256;

@@ -149,7 +149,20 @@ struct DmBtLayout {
     size_t bytes;
 };
 
+// Workspace of the differentiable form (gradient of the top-maxima loss).
+struct DmGradLayout {
+    size_t parts;                 // f32 [npatch(L)] per-patch maxima
+    size_t dA[DM_MAXL + 1];       // f32 [npatch(l)][dh[l]][dw[l]], l = 1..L
+    size_t dP[DM_MAXL];           // f32 pooled layout, l = 0..L-1
+    size_t Am, Bm;                // f32 [n0][144] patch vectors, [W2*H2][144] image-2 im2col
+    size_t G1, Gim;               // f32 [n0][144], [W2*H2][144] level-0 products
+    size_t dC;                    // f32 [chunk][W2*H2] dense dC0 block
+    int chunk;                    // patches per level-0 chunk
+    size_t bytes;
+};
+
 void dm_pyr_layout(const DmGeom& g, int precision, DmPyrLayout* o);
+void dm_grad_layout(const DmGeom& g, DmGradLayout* o);
 void dm_bt_layout(const DmGeom& g, DmBtLayout* o);
 size_t dm_desc_tmp_bytes(int W, int H);
 
@@ -192,5 +205,7 @@ cudaError_t dm_launch_corr0_bf16(const DmGeom& g, const float* d1, const float* 
                                  void* status, float* pooled0, unsigned char* amax0, cudaStream_t st);
 size_t dm_corr0_bf16_a_bytes(const DmGeom& g);
 cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& p, float lam, cudaStream_t st);
+cudaError_t dm_launch_loss_grad(const DmGeom& g, const dm_pyramid& py, const float* d1, const float* d2, float lam,
+                                const DmGradLayout& gl, char* ws, float* d_loss, float* g1, float* g2, cudaStream_t st);
 cudaError_t dm_launch_backtrack(const DmGeom& g, const dm_pyramid& p, const DmBtLayout& bl, char* ws,
                                 dm_match_t* out, int capacity, int* d_count, cudaStream_t st);

@@ -1,0 +1,383 @@
+// Differentiable form: loss = sum over existing top patches p of
+// max_q C_L(p, q) (first maximum), and its gradient with respect to both
+// descriptor fields (the paper has no loss; this is the adjoint of
+// Algorithm 1).  The backward runs through
+//   the rectification  C = A^lambda                  (Eq. 11),
+//   the shifted average A_l = mean_i P_{l-1}(c_i, q+o_i)   (Eq. 12),
+//   the max-pooling with its saved argmax            (Eq. 8-9),
+//   the level-0 correlation C0 = (1/16) a_p . b_t    (Eq. 3-4).
+// Everything is a gather with a fixed summation order, so the gradient is
+// deterministic.  Per level two dense arrays are used: dA_l on the map
+// domain of level l (unrectified averages) and dP_l in the pooled layout.
+// Level 0 is recomputed rather than stored: the unrectified C0 at an argmax
+// position is one 144-term dot product, and the two level-0 products
+//   G1[p][k] = (1/16) sum_t dC0(p,t) b_t[k],   Gim[t][k] = (1/16) sum_p dC0(p,t) a_p[k]
+// are dense FP32 GEMMs over chunks of patches (the dense dC0 block of a chunk
+// is the only large temporary), followed by the scatter of G1 onto the
+// atomic windows of I and the col2im gather of Gim onto the pixels of I'.
+#include "dm_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ void two_sum_add(float& s, float& comp, float v) {
+    const float t = __fadd_rn(s, v);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
+    s = t;
+    comp = __fadd_rn(comp, err);
+}
+
+// Unrectified average of lattice patch p at level l >= 1, position (qx, qy),
+// exactly as the forward computes it; *n_out = number of existing children.
+__device__ float level_average(const DmGeom& g, int l, int p, int qx, int qy, const unsigned char* vprev,
+                               const float* prev, int* n_out) {
+    const int mw = g.dw[l], mh = g.dh[l], pitch = g.pitch(l);
+    float s = 0.0f, comp = 0.0f;
+    int n = 0;
+    bool first = true;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        int c = dm_child(g, l, p % g.Lx, p / g.Lx, i);
+        if (c < 0 || !vprev[c]) continue;
+        n++;
+        int ox = (i >= 2) ? 1 : -1, oy = (i & 1) ? 1 : -1;
+        int rx = qx + ox, ry = qy + oy;
+        float v = 0.0f;
+        if (rx >= 0 && ry >= 0 && rx < mw && ry < mh) v = prev[(long long)c * g.psize(l) + (long long)ry * pitch + rx];
+        if (first) { s = v; first = false; }
+        else two_sum_add(s, comp, v);
+    }
+    *n_out = n;
+    if (n == 0) return 0.0f;
+    return __fdiv_rn(__fadd_rn(s, comp), (float)n);
+}
+
+__device__ __forceinline__ float dpow(float x, float lam) {   // d(x^lam)/dx for x in [0, 1]
+    return x > 0.0f ? __fmul_rn(lam, dm_powf(x, lam - 1.0f)) : 0.0f;
+}
+
+// Top level: per existing patch, the first maximum of C_L, its value, and
+// dA_L = d(A^lam)/dA at that position (zero elsewhere).
+__global__ void k_adj_top(DmGeom g, const unsigned char* __restrict__ vL, const unsigned char* __restrict__ vprev,
+                          const float* __restrict__ top, const float* __restrict__ prev, float lam,
+                          float* __restrict__ dA, float* __restrict__ parts) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int L = g.L;
+    if (p >= g.npatch(L)) return;
+    const int nq = g.dw[L] * g.dh[L];
+    float* d = dA + (long long)p * nq;
+    for (int q = 0; q < nq; q++) d[q] = 0.0f;
+    if (!vL[p]) { parts[p] = 0.0f; return; }
+    const float* t = top + (long long)p * nq;
+    float best = -INFINITY;
+    int qb = 0;
+    for (int q = 0; q < nq; q++)
+        if (t[q] > best) { best = t[q]; qb = q; }
+    parts[p] = best;
+    int n;
+    const float a = level_average(g, L, p, qb % g.dw[L], qb / g.dw[L], vprev, prev, &n);
+    d[qb] = dpow(a, lam);
+}
+
+// Deterministic sum of the per-patch maxima (one block).
+__global__ void k_adj_loss(const float* __restrict__ parts, int n, float* __restrict__ loss) {
+    __shared__ double acc[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)parts[i];
+    acc[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) acc[threadIdx.x] += acc[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = (float)acc[0];
+}
+
+// dP_{l-1}(c, r) = sum over the parents p_i = c - 2^l o_i of c (i = 0..3, in
+// order) of dA_l(p_i, r - o_i) / n(p_i).  Grid: (positions of domain l, child).
+__global__ void k_adj_pooled(DmGeom g, int l, const unsigned char* __restrict__ vcur,
+                             const unsigned char* __restrict__ vprev, const float* __restrict__ dA,
+                             float* __restrict__ dP) {
+    const int c = blockIdx.y;
+    const int mw = g.dw[l], mh = g.dh[l], pitch = g.pitch(l);
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= mw * mh) return;
+    const int rx = r % mw, ry = r / mw;
+    float sum = 0.0f;
+    if (vprev[c]) {
+        const int cx = l == 1 ? c % g.P0x : c % g.Lx, cy = l == 1 ? c / g.P0x : c / g.Lx;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int ox = (i >= 2) ? 1 : -1, oy = (i & 1) ? 1 : -1;
+            int ix, iy;
+            if (l == 1) { ix = cx + (1 - ox) / 2; iy = cy + (1 - oy) / 2; }
+            else { const int s = 1 << (l - 2); ix = cx - ox * s; iy = cy - oy * s; }
+            if (ix < 0 || iy < 0 || ix >= g.Lx || iy >= g.Ly) continue;
+            const int p = iy * g.Lx + ix;
+            if (!vcur[p]) continue;
+            const int qx = rx - ox, qy = ry - oy;
+            if (qx < 0 || qy < 0 || qx >= mw || qy >= mh) continue;
+            int n = 0;
+            for (int j = 0; j < 4; j++) {
+                int cj = dm_child(g, l, ix, iy, j);
+                if (cj >= 0 && vprev[cj]) n++;
+            }
+            const float d = dA[((long long)p * mh + qy) * mw + qx];
+            if (d != 0.0f) sum = __fadd_rn(sum, __fdiv_rn(d, (float)n));
+        }
+    }
+    dP[(long long)c * g.psize(l) + (long long)ry * pitch + rx] = sum;
+}
+
+// dA_{m}(c, t) for m = l-1 >= 1: sum over the pooled positions r whose argmax
+// is t (r = floor/ceil(t/2) per axis, ascending) of dP_m(c, r) * lam A^(lam-1),
+// A the unrectified average at t.  Grid: (positions of domain m, patch).
+__global__ void k_adj_unpool(DmGeom g, int m, const unsigned char* __restrict__ vm, const unsigned char* __restrict__ vprev,
+                             const float* __restrict__ prev, const float* __restrict__ dP,
+                             const unsigned char* __restrict__ amax, float lam, float* __restrict__ dA) {
+    const int c = blockIdx.y;
+    const int tw = g.dw[m], th = g.dh[m];
+    const int pw = g.dw[m + 1], ph = g.dh[m + 1], pitch = g.pitch(m + 1);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tw * th) return;
+    const int tx = t % tw, ty = t / tw;
+    float sum = 0.0f;
+    if (vm[c]) {
+        float dsum = 0.0f;
+        for (int ry = ty >> 1; ry <= (ty + 1) >> 1; ry++) {
+            if (ry >= ph) continue;
+            for (int rx = tx >> 1; rx <= (tx + 1) >> 1; rx++) {
+                if (rx >= pw) continue;
+                const long long o = (long long)c * g.psize(m + 1) + (long long)ry * pitch + rx;
+                const int code = amax[o];
+                if (2 * rx + code % 3 - 1 != tx || 2 * ry + code / 3 - 1 != ty) continue;
+                dsum = __fadd_rn(dsum, dP[o]);
+            }
+        }
+        if (dsum != 0.0f) {
+            int n;
+            const float a = level_average(g, m, c, tx, ty, vprev, prev, &n);
+            sum = __fmul_rn(dsum, dpow(a, lam));
+        }
+    }
+    dA[((long long)c * th + ty) * tw + tx] = sum;
+}
+
+// Patch vectors (A, [n0][144]) and the image-2 im2col (B, [W2*H2][144]) in FP32,
+// k = (dy*4 + dx)*9 + c; zero outside the images.
+__global__ void k_adj_im2col(DmGeom g, const float* __restrict__ d1, const float* __restrict__ d2,
+                             float* __restrict__ Am, float* __restrict__ Bm) {
+    const long long n0 = g.npatch(0), T = (long long)g.W2 * g.H2;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (n0 + T) * 144) return;
+    const int k = (int)(idx % 144);
+    const long long row = idx / 144;
+    const int dy = k / 36, dx = (k / 9) % 4, ch = k % 9;
+    if (row < n0) {
+        const int p = (int)row;
+        const int x = 4 * (p % g.P0x) + dx, y = 4 * (p / g.P0x) + dy;
+        Am[row * 144 + k] = (x < g.W1 && y < g.H1) ? d1[((long long)y * g.W1 + x) * 9 + ch] : 0.0f;
+    } else {
+        const long long t = row - n0;
+        const int tx = (int)(t % g.W2), ty = (int)(t / g.W2);
+        const int x = tx - 2 + dx, y = ty - 2 + dy;
+        Bm[t * 144 + k] = (x >= 0 && y >= 0 && x < g.W2 && y < g.H2) ? d2[((long long)y * g.W2 + x) * 9 + ch] : 0.0f;
+    }
+}
+
+// dC0 for patches [p0, p0 + pc): dense [pc][W2*H2]; nonzero only at argmax
+// positions of the pooled level-0 map, where dC0 = sum dP0 * lam C0^(lam-1)
+// with C0 recomputed as the 144-term dot product.
+__global__ void k_adj_dc0(DmGeom g, int p0, int pc, const float* __restrict__ dP0, const unsigned char* __restrict__ amax0,
+                          const float* __restrict__ Am, const float* __restrict__ Bm, float lam, float* __restrict__ dC) {
+    const int pl = blockIdx.y;
+    const int p = p0 + pl;
+    const int W2 = g.W2, H2 = g.H2;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= W2 * H2 || pl >= pc) return;
+    const int tx = t % W2, ty = t / W2;
+    const int pw = g.dw[1], ph = g.dh[1], pitch = g.pitch(1);
+    float dsum = 0.0f;
+    for (int ry = ty >> 1; ry <= (ty + 1) >> 1; ry++) {
+        if (ry >= ph) continue;
+        for (int rx = tx >> 1; rx <= (tx + 1) >> 1; rx++) {
+            if (rx >= pw) continue;
+            const long long o = (long long)p * g.psize(1) + (long long)ry * pitch + rx;
+            const int code = amax0[o];
+            if (2 * rx + code % 3 - 1 != tx || 2 * ry + code / 3 - 1 != ty) continue;
+            dsum = __fadd_rn(dsum, dP0[o]);
+        }
+    }
+    float out = 0.0f;
+    if (dsum != 0.0f) {
+        const float* a = Am + (long long)p * 144;
+        const float* b = Bm + (long long)t * 144;
+        float acc = 0.0f;
+        for (int k = 0; k < 144; k++) acc = __fmaf_rn(a[k], b[k], acc);
+        out = __fmul_rn(dsum, dpow(__fmul_rn(acc, 0.0625f), lam));
+    }
+    dC[(long long)pl * W2 * H2 + t] = out;
+}
+
+// C[m][n] (+)= alpha * sum_k A(m,k) B[k][n], A(m,k) = TRANS_A ? A[k*lda + m] : A[m*lda + k];
+// 64 x 48 tiles, K steps of 16, 256 threads, 4 x 3 outputs per thread.
+template <bool TRANS_A, bool ACCUM>
+__global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, float alpha, const float* __restrict__ A, long long lda,
+                                               const float* __restrict__ B, int ldb, float* __restrict__ C, int ldc) {
+    constexpr int BM = 64, BN = 48, BK = 16;
+    __shared__ float As[BK][BM + 4];
+    __shared__ float Bs[BK][BN];
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int tid = threadIdx.x;
+    const int tm = (tid % 16) * 4, tn = (tid / 16) * 3;
+    float acc[4][3] = {};
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        for (int e = tid; e < BM * BK; e += 256) {
+            int mm, kk;
+            if (TRANS_A) { mm = e % BM; kk = e / BM; }
+            else { kk = e % BK; mm = e / BK; }
+            const int gm = m0 + mm, gk = k0 + kk;
+            float v = 0.0f;
+            if (gm < M && gk < K) v = TRANS_A ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
+            As[kk][mm] = v;
+        }
+        for (int e = tid; e < BK * BN; e += 256) {
+            const int nn = e % BN, kk = e / BN;
+            const int gn = n0 + nn, gk = k0 + kk;
+            Bs[kk][nn] = (gn < N && gk < K) ? B[(long long)gk * ldb + gn] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk++) {
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) acc[i][j] = __fmaf_rn(As[kk][tm + i], Bs[kk][tn + j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const int gm = m0 + tm + i, gn = n0 + tn + j;
+            if (gm < M && gn < N) {
+                float* o = C + (long long)gm * ldc + gn;
+                const float v = __fmul_rn(alpha, acc[i][j]);
+                *o = ACCUM ? __fadd_rn(*o, v) : v;
+            }
+        }
+}
+
+// g1[y][x][c] = G1[patch of (x, y)][(y%4*4 + x%4)*9 + c] (0 outside every atomic window).
+__global__ void k_adj_g1(DmGeom g, const float* __restrict__ G1, float* __restrict__ g1) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)g.W1 * g.H1 * 9) return;
+    const int ch = (int)(idx % 9);
+    const long long pix = idx / 9;
+    const int x = (int)(pix % g.W1), y = (int)(pix / g.W1);
+    const int px = x / 4, py = y / 4;
+    float v = 0.0f;
+    if (px < g.P0x && py < g.P0y) v = G1[((long long)py * g.P0x + px) * 144 + ((y % 4) * 4 + (x % 4)) * 9 + ch];
+    g1[idx] = v;
+}
+
+// g2[u][c] = sum over the 16 windows t = u + (2 - dx, 2 - dy) inside I' of Gim[t][(dy*4+dx)*9 + c].
+__global__ void k_adj_g2(DmGeom g, const float* __restrict__ Gim, float* __restrict__ g2) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)g.W2 * g.H2 * 9) return;
+    const int ch = (int)(idx % 9);
+    const long long pix = idx / 9;
+    const int x = (int)(pix % g.W2), y = (int)(pix / g.W2);
+    float s = 0.0f;
+    for (int dy = 0; dy < 4; dy++)
+        for (int dx = 0; dx < 4; dx++) {
+            const int tx = x + 2 - dx, ty = y + 2 - dy;
+            if (tx < 0 || ty < 0 || tx >= g.W2 || ty >= g.H2) continue;
+            s = __fadd_rn(s, Gim[((long long)ty * g.W2 + tx) * 144 + (dy * 4 + dx) * 9 + ch]);
+        }
+    g2[idx] = s;
+}
+
+inline unsigned nb(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+void dm_grad_layout(const DmGeom& g, DmGradLayout* o) {
+    memset(o, 0, sizeof(*o));
+    size_t off = 0;
+    o->parts = off; off = dm_align(off + (size_t)g.npatch(g.L) * 4);
+    for (int l = 1; l <= g.L; l++) { o->dA[l] = off; off = dm_align(off + (size_t)g.npatch(l) * g.dsize(l) * 4); }
+    for (int l = 0; l < g.L; l++) { o->dP[l] = off; off = dm_align(off + (size_t)g.npatch(l) * g.psize(l + 1) * 4); }
+    const size_t T = (size_t)g.W2 * g.H2;
+    o->Am = off; off = dm_align(off + (size_t)g.npatch(0) * 144 * 4);
+    o->Bm = off; off = dm_align(off + T * 144 * 4);
+    o->G1 = off; off = dm_align(off + (size_t)g.npatch(0) * 144 * 4);
+    o->Gim = off; off = dm_align(off + T * 144 * 4);
+    // dense dC0 block of one chunk of patches: at most 1 GiB, at least one patch
+    size_t pc = (size_t)1 << 30;
+    pc /= (T * 4);
+    if (pc < 1) pc = 1;
+    if (pc > (size_t)g.npatch(0)) pc = (size_t)g.npatch(0);
+    o->chunk = (int)pc;
+    o->dC = off; off = dm_align(off + pc * T * 4);
+    o->bytes = off;
+}
+
+cudaError_t dm_launch_loss_grad(const DmGeom& g, const dm_pyramid& py, const float* d1, const float* d2, float lam,
+                                const DmGradLayout& gl, char* ws, float* d_loss, float* g1, float* g2, cudaStream_t st) {
+    const int L = g.L;
+    float* parts = reinterpret_cast<float*>(ws + gl.parts);
+    long long launches = 0;
+    k_adj_top<<<nb(g.npatch(L), 128), 128, 0, st>>>(g, py.valid[L], py.valid[L - 1], py.top, py.pooled[L - 1], lam,
+                                                    reinterpret_cast<float*>(ws + gl.dA[L]), parts);
+    k_adj_loss<<<1, 256, 0, st>>>(parts, g.npatch(L), d_loss);
+    launches += 2;
+    if (!g1 || !g2) {   // loss only
+        dm_count_launches(launches);
+        return cudaGetLastError();
+    }
+    for (int l = L; l >= 1; l--) {
+        const int np_child = g.npatch(l - 1);
+        dim3 grid(nb(g.dsize(l), 128), np_child);
+        k_adj_pooled<<<grid, 128, 0, st>>>(g, l, py.valid[l], py.valid[l - 1], reinterpret_cast<const float*>(ws + gl.dA[l]),
+                                           reinterpret_cast<float*>(ws + gl.dP[l - 1]));
+        launches++;
+        if (l - 1 >= 1) {
+            dim3 g2d(nb(g.dsize(l - 1), 128), g.npatch(l - 1));
+            k_adj_unpool<<<g2d, 128, 0, st>>>(g, l - 1, py.valid[l - 1], py.valid[l - 2], py.pooled[l - 2],
+                                              reinterpret_cast<const float*>(ws + gl.dP[l - 1]), py.amax[l - 1], lam,
+                                              reinterpret_cast<float*>(ws + gl.dA[l - 1]));
+            launches++;
+        }
+    }
+    float* Am = reinterpret_cast<float*>(ws + gl.Am);
+    float* Bm = reinterpret_cast<float*>(ws + gl.Bm);
+    float* G1 = reinterpret_cast<float*>(ws + gl.G1);
+    float* Gim = reinterpret_cast<float*>(ws + gl.Gim);
+    float* dC = reinterpret_cast<float*>(ws + gl.dC);
+    const long long n0 = g.npatch(0), T = (long long)g.W2 * g.H2;
+    k_adj_im2col<<<nb((n0 + T) * 144, 256), 256, 0, st>>>(g, d1, d2, Am, Bm);
+    launches++;
+    for (long long p0 = 0; p0 < n0; p0 += gl.chunk) {
+        const int pc = (int)(n0 - p0 < gl.chunk ? n0 - p0 : gl.chunk);
+        dim3 gd(nb(T, 128), pc);
+        k_adj_dc0<<<gd, 128, 0, st>>>(g, (int)p0, pc, reinterpret_cast<const float*>(ws + gl.dP[0]), py.amax[0], Am, Bm,
+                                      lam, dC);
+        // G1[p0 .. p0+pc) = (1/16) dC [pc x T] * Bm [T x 144]
+        dim3 gg1(nb(pc, 64), nb(144, 48));
+        k_sgemm<false, false><<<gg1, 256, 0, st>>>(pc, 144, (int)T, 0.0625f, dC, T, Bm, 144, G1 + p0 * 144, 144);
+        // Gim (+)= (1/16) dC^T [T x pc] * Am[p0 .. p0+pc) [pc x 144]
+        dim3 gg2(nb(T, 64), nb(144, 48));
+        if (p0 == 0)
+            k_sgemm<true, false><<<gg2, 256, 0, st>>>((int)T, 144, pc, 0.0625f, dC, T, Am + p0 * 144, 144, Gim, 144);
+        else
+            k_sgemm<true, true><<<gg2, 256, 0, st>>>((int)T, 144, pc, 0.0625f, dC, T, Am + p0 * 144, 144, Gim, 144);
+        launches += 3;
+    }
+    k_adj_g1<<<nb((long long)g.W1 * g.H1 * 9, 256), 256, 0, st>>>(g, G1, g1);
+    k_adj_g2<<<nb(T * 9, 256), 256, 0, st>>>(g, Gim, g2);
+    launches += 2;
+    dm_count_launches(launches);
+    return cudaGetLastError();
+}

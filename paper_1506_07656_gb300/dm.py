@@ -65,6 +65,8 @@ _SIGS = {
     "dm_match_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                 C.c_size_t, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_void_p]),
     "dm_read_status": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.c_void_p, C.c_int, C.c_void_p]),
+    "dm_grad_workspace_bytes": (C.c_int, [C.c_void_p] + [C.c_int] * 4 + [C.POINTER(C.c_size_t)]),
+    "dm_loss_grad": (C.c_int, [C.c_void_p] * 5 + [C.c_size_t] + [C.c_void_p] * 5),
     "dm_batch_workspace_bytes": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_size_t)]),
     "dm_match_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "dm_backtrack_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
@@ -242,6 +244,20 @@ def dm_read_status(ctx, d_ws, n_levels: int, stream=None):
     st = load().dm_read_status(ctx, _dptr(d_ws), C.byref(status), reached, n_levels, _stream_ptr(stream))
     _check(ctx, st, "dm_read_status")
     return status.value, list(reached)
+
+
+def dm_grad_workspace_bytes(ctx, W1, H1, W2, H2) -> int:
+    b = C.c_size_t()
+    _check(ctx, load().dm_grad_workspace_bytes(ctx, W1, H1, W2, H2, C.byref(b)), "dm_grad_workspace_bytes")
+    return b.value
+
+
+def dm_loss_grad(ctx, pyr, d_desc1, d_desc2, d_ws, d_loss, d_parts=None, d_g1=None, d_g2=None, stream=None):
+    st = load().dm_loss_grad(ctx, pyr, _dptr(d_desc1), _dptr(d_desc2), _dptr(d_ws), d_ws.numel() * d_ws.element_size(),
+                             _dptr(d_loss), _dptr(d_parts) if d_parts is not None else None,
+                             _dptr(d_g1) if d_g1 is not None else None, _dptr(d_g2) if d_g2 is not None else None,
+                             _stream_ptr(stream))
+    _check(ctx, st, "dm_loss_grad")
 
 
 def make_pairs(items):

@@ -1,0 +1,136 @@
+"""Differentiable form on the GPU: loss = sum of the top-level maxima and its
+gradient with respect to both descriptor fields.
+
+Checked against the FP64 oracle gradient (which is itself pinned by central
+finite differences) and against central finite differences of the GPU loss
+(h = 1e-3) on 256x256 pairs.  Tolerances: relative L2 error of the gradient
+vs FP64 <= 2e-3 (FP32 arithmetic through L+1 levels of powers); finite
+differences within 1.5e-2 relative or 2e-3 absolute (FP32 loss differences
+divided by 2h), skipping entries where the steps h, h/2, h/4 disagree (an
+argmax flips inside the stencil, where the loss has a kink).
+"""
+import numpy as np
+import pytest
+
+from paper_1506_07656_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1506_07656_gb300 import build, dm
+    build.build()
+    ctx = dm.Context(dm.DM_FP32)
+    yield torch, dm, ctx
+    ctx.close()
+
+
+def _gpu_loss_grad(torch, dm, ctx, d1, d2, want_grad=True):
+    t1 = torch.as_tensor(np.ascontiguousarray(d1, dtype=np.float32), device="cuda")
+    t2 = torch.as_tensor(np.ascontiguousarray(d2, dtype=np.float32), device="cuda")
+    H1, W1, _ = t1.shape
+    H2, W2, _ = t2.shape
+    wsp = torch.empty(dm.dm_workspace_bytes(ctx.ctx, W1, H1, W2, H2)["pyramid"], dtype=torch.uint8, device="cuda")
+    h = dm.dm_correlate_pyramid(ctx.ctx, t1, t2, wsp)
+    wsg = torch.empty(dm.dm_grad_workspace_bytes(ctx.ctx, W1, H1, W2, H2), dtype=torch.uint8, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    nL = dm.dm_geometry(W1, H1, W2, H2)["n_patch"]
+    parts = torch.zeros(nL, dtype=torch.float32, device="cuda")
+    g1 = torch.zeros_like(t1) if want_grad else None
+    g2 = torch.zeros_like(t2) if want_grad else None
+    dm.dm_loss_grad(ctx.ctx, h, t1, t2, wsg, loss, parts, g1, g2)
+    torch.cuda.synchronize()
+    dm.dm_pyramid_free(h)
+    out = (float(loss.item()), parts.cpu().numpy().astype(np.float64))
+    if want_grad:
+        out += (g1.cpu().numpy().astype(np.float64), g2.cpu().numpy().astype(np.float64))
+    return out
+
+
+@pytest.mark.parametrize("W1,H1,W2,H2,seed", [(20, 16, 22, 15, 1), (37, 29, 41, 23, 2)])
+def test_gradient_matches_fp64_oracle_random(env, oracle_mod, W1, H1, W2, H2, seed):
+    torch, dm, ctx = env
+    d1 = synth.random_descriptor_field(W1, H1, seed).astype(np.float32)
+    d2 = synth.random_descriptor_field(W2, H2, seed + 7).astype(np.float32)
+    loss, parts, g1, g2 = _gpu_loss_grad(torch, dm, ctx, d1, d2)
+    lo, o1, o2 = oracle_mod.loss_grad(d1.astype(np.float64), d2.astype(np.float64))
+    assert abs(loss - lo) <= 1e-5 * abs(lo)
+    for got, want in ((g1, o1), (g2, o2)):
+        rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+        assert rel <= 2e-3, rel
+
+
+def test_gradient_matches_fp64_oracle_images(env, oracle_mod):
+    torch, dm, ctx = env
+    pr = synth.make_pair_smooth(64, 48, seed=4)
+    d1 = oracle_mod.descriptors(pr.img1, "f32")
+    d2 = oracle_mod.descriptors(pr.img2, "f32")
+    loss, parts, g1, g2 = _gpu_loss_grad(torch, dm, ctx, d1, d2)
+    lo, o1, o2 = oracle_mod.loss_grad(d1.astype(np.float64), d2.astype(np.float64))
+    assert abs(loss - lo) <= 1e-5 * abs(lo)
+    for got, want in ((g1, o1), (g2, o2)):
+        rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+        assert rel <= 2e-3, rel
+
+
+def test_gradient_finite_differences_256(env):
+    """Two 256x256 pairs, 64 random entries each (32 per descriptor field); the
+    loss has many kinks at this step size, so at least 20 smooth entries are
+    required to agree."""
+    torch, dm, ctx = env
+    rng = np.random.default_rng(0)
+    h = 1e-3
+    checked = 0
+    for k in range(2):
+        pr = synth.make_pair_smooth(256, 256, seed=300 + k, max_disp=16.0)
+        H, W = pr.img1.shape
+        d = []
+        for img in (pr.img1, pr.img2):
+            t = torch.empty((H, W, 9), dtype=torch.float32, device="cuda")
+            dm.dm_descriptors(ctx.ctx, torch.from_numpy(img).cuda(), t, ctx.workspace("desc", W, H, W, H))
+            d.append(t.cpu().numpy())
+        _, parts0, g1, g2 = _gpu_loss_grad(torch, dm, ctx, d[0], d[1])
+        for which, g in ((0, g1), (1, g2)):
+            nz = np.flatnonzero(np.abs(g) > 1e-3 * np.abs(g).max())
+            for idx in rng.choice(nz, size=32, replace=False):
+                diffs = []
+                for step in (h, h / 2, h / 4):
+                    dp = [x.copy() for x in d]
+                    dm_ = [x.copy() for x in d]
+                    dp[which].flat[idx] += step
+                    dm_[which].flat[idx] -= step
+                    _, pp = _gpu_loss_grad(torch, dm, ctx, dp[0], dp[1], want_grad=False)
+                    _, pm = _gpu_loss_grad(torch, dm, ctx, dm_[0], dm_[1], want_grad=False)
+                    diffs.append(np.sum(pp - pm) / (2 * step))     # unaffected patches cancel exactly
+                fd = diffs[0]
+                # the loss is a max of smooth functions: where an argmax flips within the
+                # stencil the three step sizes disagree, and such entries are skipped
+                if max(diffs) - min(diffs) > 1e-2 * max(abs(fd), 1e-1):
+                    continue
+                a = g.flat[idx]
+                assert abs(fd - a) <= max(1.5e-2 * abs(a), 2e-3), (which, idx, diffs, a)
+                checked += 1
+    assert checked >= 20
+
+
+def test_autograd_function(env):
+    torch, dm, ctx = env
+    from paper_1506_07656_gb300.autograd import top_max_loss
+    pr = synth.make_pair_smooth(64, 48, seed=5)
+    d = []
+    for img in (pr.img1, pr.img2):
+        t = torch.empty((48, 64, 9), dtype=torch.float32, device="cuda")
+        dm.dm_descriptors(ctx.ctx, torch.from_numpy(img).cuda(), t, ctx.workspace("desc", 64, 48, 64, 48))
+        d.append(t)
+    x1 = d[0].clone().requires_grad_(True)
+    x2 = d[1].clone().requires_grad_(True)
+    loss = top_max_loss(x1, x2, ctx)
+    (3.0 * loss).backward()
+    l0, _, g1, g2 = _gpu_loss_grad(torch, dm, ctx, d[0].cpu().numpy(), d[1].cpu().numpy())
+    assert abs(float(loss.item()) - l0) == 0.0
+    np.testing.assert_array_equal(x1.grad.cpu().numpy(), (3.0 * g1).astype(np.float32))
+    np.testing.assert_array_equal(x2.grad.cpu().numpy(), (3.0 * g2).astype(np.float32))
