@@ -37,7 +37,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "bf16", "auto"], default="auto")
+    ap.add_argument("--precision", choices=["fp32", "bf16", "fp8", "auto"], default="auto")
     ap.add_argument("--width", type=int, default=1024)
     ap.add_argument("--height", type=int, default=436)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -297,13 +297,17 @@ def _measure_batch(dm, torch, ctx, a, rank):
 TRAFFIC_1024x436 = {"level0_bf16": 16.7e9, "level0_fp32": None, "levels": None}
 
 
-def _rooflines(r, prec_bf16, W, H, peaks, nsm):
+def _prec_code(dm, name):
+    return {"fp32": dm.DM_FP32, "bf16": dm.DM_BF16, "fp8": dm.DM_FP8_E4M3}[name]
+
+
+def _rooflines(r, prec, W, H, peaks, nsm):
     geo = r["geo"]
     n0 = geo["n_patch0"]
     corr_ms = r["stages"]["level0_correlation"]
     flop = 2.0 * 144 * n0 * W * H
     achieved = flop / (corr_ms / 1e3) / 1e12
-    if not prec_bf16:
+    if prec == "fp32":
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         peak = nsm * 128 * 2 * sm_max * 1e6 / 1e12
         corr = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -311,11 +315,16 @@ def _rooflines(r, prec_bf16, W, H, peaks, nsm):
                 "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
                 "algorithmic_flop_per_launch": flop, "launch_ms": corr_ms}
     else:
-        peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        # FP8 takes the measured bf16 peak x the nominal dense ratio 4.5 / 2.25
+        ratio = 2.0 if prec == "fp8" else 1.0
+        peak = float(peaks.get("bf16_tflops_sustained", 1700.0)) * ratio
+        src = ("bf16_tflops_sustained of measured" if "bf16_tflops_sustained" in peaks
+               else "fallback 1.7 PFLOP/s sustained")
         corr = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": TRAFFIC_1024x436["level0_bf16"] if (W, H) == (1024, 436) else None, "kernel": "k_corr0_tc (level-0 correlation on tcgen05, BF16 in / FP32 accumulate, fused pool/power)",
-                "peak_source": ("bf16_tflops_sustained of measured" if "bf16_tflops_sustained" in peaks
-                                else "fallback 1.7 PFLOP/s sustained"),
+                "traffic": TRAFFIC_1024x436.get("level0_" + prec) if (W, H) == (1024, 436) else None,
+                "kernel": f"k_corr0_tc<{prec.upper()}> (level-0 correlation on tcgen05, {prec.upper()} in / FP32 "
+                          f"accumulate, fused pool/power)",
+                "peak_source": src + (" x 2 (nominal fp8/bf16 dense ratio)" if prec == "fp8" else ""),
                 "algorithmic_flop_per_launch": flop, "launch_ms": corr_ms}
     # pyramid levels >= 1: read every pooled map of levels 0..L-1 once (4 B), write the
     # pooled maps (4 B) + argmax (1 B) of levels 1..L-1 and the top (4 B)
@@ -349,10 +358,10 @@ def run_ours(a):
     W, H = a.width, a.height
     pair = _pair(W, H, 1000 + rank)
     stream = torch.cuda.current_stream()
-    precs = ["fp32", "bf16"] if a.precision == "auto" else [a.precision]
+    precs = ["fp32", "bf16", "fp8"] if a.precision == "auto" else [a.precision]
     res = {}
     for pn in precs:
-        ctx = dm.Context(dm.DM_BF16 if pn == "bf16" else dm.DM_FP32, device=local)
+        ctx = dm.Context(_prec_code(dm, pn), device=local)
         res[pn] = _measure(dm, torch, dist, ctx, pair, a, world, local, stream)
         ctx.close()
         del ctx
@@ -361,7 +370,7 @@ def run_ours(a):
     r = res[head]
     batch = None
     if not a.no_batch:
-        ctx = dm.Context(dm.DM_BF16 if head == "bf16" else dm.DM_FP32, device=local)
+        ctx = dm.Context(_prec_code(dm, head), device=local)
         batch = _measure_batch(dm, torch, ctx, a, rank)
         batch["precision"] = head
         ctx.close()
@@ -374,7 +383,7 @@ def run_ours(a):
         if os.path.exists(pk):
             peaks = json.load(open(pk))
         nsm = torch.cuda.get_device_properties(local).multi_processor_count
-        corr, lev = _rooflines(r, head == "bf16", W, H, peaks, nsm)
+        corr, lev = _rooflines(r, head, W, H, peaks, nsm)
         # the dominant kernel of the headline path gets the roofline object
         dominant = corr if r["stages"]["level0_correlation"] >= r["stages"]["levels"] else lev
         cpu = None
@@ -384,7 +393,7 @@ def run_ours(a):
         geo = r["geo"]
         paths = {}
         for pn, rr in res.items():
-            c2, l2 = _rooflines(rr, pn == "bf16", W, H, peaks, nsm)
+            c2, l2 = _rooflines(rr, pn, W, H, peaks, nsm)
             paths[pn] = {"pairs_per_s": rr["value"], "ms_per_step": rr["ms"] / a.steps, "stages_ms": rr["stages"],
                          "e2e_pairs_per_s": rr["e2e"], "level0": {"achieved": c2["achieved"], "frac": c2["frac"],
                                                                  "bound": c2["bound"]},
@@ -392,10 +401,10 @@ def run_ours(a):
         line = {
             "metric": METRIC, "value": r["value"], "unit": "pairs/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": r["ms"] / a.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16" if head == "bf16" else "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": {"bf16": "bf16", "fp8": "fp8_e4m3", "fp32": "f32"}[head], "data": "synthetic",
             "config": {"workload": f"one {W}x{H} pair per GPU per step, seeded 4-octave value noise, smooth warp "
                                    f"max 120 px (+5% gain, sigma 0.01 noise); level-0 correlation in "
-                                   f"{'BF16 on tcgen05 tensor cores, FP32 accumulation' if head == 'bf16' else 'FP32'}, "
+                                   f"{'FP32' if head == 'fp32' else head.upper() + ' on tcgen05 tensor cores, FP32 accumulation'}, "
                                    f"pyramid and backtracking in FP32",
                        "width": W, "height": H, "precision": head, "L": geo["L"], "atomic_patches": geo["n_patch0"],
                        "l2": "working set ~21 GB per pair >> 126 MB L2; no flush needed",

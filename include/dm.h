@@ -49,8 +49,13 @@ typedef enum {
 
 typedef enum {
     DM_FP32 = 0,          /* FP32 everywhere; bit-exact with the FP32 reference    */
-    DM_BF16 = 1           /* bottom-level correlation on BF16 tensor cores (FP32
+    DM_BF16 = 1,          /* bottom-level correlation on BF16 tensor cores (FP32
                              accumulation); the rest of the pyramid in FP32         */
+    DM_FP8_E4M3 = 2       /* bottom-level correlation on FP8 (E4M3) tensor cores:
+                             each patch vector of I scaled by its own power of two
+                             so that its largest entry lies in [224, 448], the
+                             descriptors of I' scaled by 256; FP32 accumulation,
+                             scales undone before the power; the rest in FP32     */
 } dm_precision;
 
 /* Parameters of the method.  Defaults (dm_config_default) are the paper's:

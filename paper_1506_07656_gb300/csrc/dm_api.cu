@@ -130,9 +130,9 @@ dm_status run_pyramid(dm_ctx* c, const DmGeom& g, const float* d1, const float* 
     fill_pyramid(py, g, c->cfg.precision, pl, base);
     cudaError_t e;
     if ((e = cudaMemsetAsync(d_status, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(c, e, "clear status");
-    if (c->cfg.precision == DM_BF16) {
-        e = dm_launch_corr0_bf16(g, d1, d2, c->cfg.lambda, base + pl.a16, d_status,
-                                 const_cast<float*>(py->pooled[0]), const_cast<unsigned char*>(py->amax[0]), st);
+    if (c->cfg.precision != DM_FP32) {
+        e = dm_launch_corr0_tc(g, c->cfg.precision, d1, d2, c->cfg.lambda, base + pl.a16, d_status,
+                               const_cast<float*>(py->pooled[0]), const_cast<unsigned char*>(py->amax[0]), st);
     } else {
         e = dm_launch_corr0_f32(g, d1, d2, c->cfg.lambda, const_cast<float*>(py->pooled[0]),
                                 const_cast<unsigned char*>(py->amax[0]), st);
@@ -196,7 +196,7 @@ void dm_pyr_layout(const DmGeom& g, int precision, DmPyrLayout* o) {
         o->amax[l] = off; off = dm_align(off + n);
     }
     o->top = off; off = dm_align(off + (size_t)g.npatch(g.L) * (size_t)g.dsize(g.L) * 4);
-    if (precision == DM_BF16) { o->a16 = off; off = dm_align(off + dm_corr0_bf16_a_bytes(g)); }
+    if (precision != DM_FP32) { o->a16 = off; off = dm_align(off + dm_corr0_tc_a_bytes(g, precision)); }
     o->bytes = off;
 }
 
@@ -248,7 +248,7 @@ dm_status dm_create(const dm_config* cfg, int device, dm_ctx** out) {
     if (!(c.lambda > 0.0f) || !(c.nu1 >= 0.0f) || !(c.nu2 >= 0.0f) || !(c.nu3 >= 0.0f) || !(c.nu1 <= 10.0f) ||
         !(c.nu2 <= 10.0f) || !(c.nu3 <= 10.0f) || !(c.mu >= 0.0f) || !(c.image_scale > 0.0f))
         return DM_EINVAL;
-    if (c.precision != DM_FP32 && c.precision != DM_BF16) return DM_EINVAL;
+    if (c.precision != DM_FP32 && c.precision != DM_BF16 && c.precision != DM_FP8_E4M3) return DM_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return DM_EINVAL;
     dm_ctx* x = new dm_ctx();
@@ -453,9 +453,9 @@ dm_status dm_match(dm_ctx* ctx, const float* d_img1, int W1, int H1, const float
     cudaError_t e;
     int* d_status = &reinterpret_cast<DmWsHeader*>(base + ml.bt.header)->pyr_status;
     if ((e = cudaMemsetAsync(d_status, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(ctx, e, "clear status");
-    if (ctx->cfg.precision == DM_BF16)
-        e = dm_launch_corr0_bf16(g, desc1, desc2, ctx->cfg.lambda, base + ml.pyr + ml.py.a16, d_status,
-                                 const_cast<float*>(py.pooled[0]), const_cast<unsigned char*>(py.amax[0]), st);
+    if (ctx->cfg.precision != DM_FP32)
+        e = dm_launch_corr0_tc(g, ctx->cfg.precision, desc1, desc2, ctx->cfg.lambda, base + ml.pyr + ml.py.a16,
+                               d_status, const_cast<float*>(py.pooled[0]), const_cast<unsigned char*>(py.amax[0]), st);
     else
         e = dm_launch_corr0_f32(g, desc1, desc2, ctx->cfg.lambda, const_cast<float*>(py.pooled[0]),
                                 const_cast<unsigned char*>(py.amax[0]), st);

@@ -136,7 +136,7 @@ struct DmPyrLayout {
     size_t pooled[DM_MAXL];       // f32 [npatch(l)][dh[l+1]][pitch(l+1)]
     size_t amax[DM_MAXL];         // u8 same shape
     size_t top;                   // f32 [npatch(L)][dh[L]][dw[L]]
-    size_t a16;                   // bf16 patch operand tiles (BF16 form)
+    size_t a16;                   // packed patch operand tiles of the tensor-core forms (BF16, E4M3 + scales)
     size_t bytes;
 };
 
@@ -201,9 +201,11 @@ cudaError_t dm_launch_descriptors(const DmDescParams& prm, const float* img, int
                                   float* tmpA, float* tmpB, cudaStream_t st);
 cudaError_t dm_launch_corr0_f32(const DmGeom& g, const float* d1, const float* d2, float lam, float* pooled0,
                                 unsigned char* amax0, cudaStream_t st);
-cudaError_t dm_launch_corr0_bf16(const DmGeom& g, const float* d1, const float* d2, float lam, void* a16,
-                                 void* status, float* pooled0, unsigned char* amax0, cudaStream_t st);
-size_t dm_corr0_bf16_a_bytes(const DmGeom& g);
+// tcgen05 level-0 correlation, precision DM_BF16 or DM_FP8_E4M3; abuf holds
+// dm_corr0_tc_a_bytes(g, precision) bytes of packed operands.
+cudaError_t dm_launch_corr0_tc(const DmGeom& g, int precision, const float* d1, const float* d2, float lam, void* abuf,
+                               void* status, float* pooled0, unsigned char* amax0, cudaStream_t st);
+size_t dm_corr0_tc_a_bytes(const DmGeom& g, int precision);
 cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& p, float lam, cudaStream_t st);
 cudaError_t dm_launch_loss_grad(const DmGeom& g, const dm_pyramid& py, const float* d1, const float* d2, float lam,
                                 const DmGradLayout& gl, char* ws, float* d_loss, float* g1, float* g2, cudaStream_t st);

@@ -38,10 +38,17 @@
 // rows: 14 tcgen05.ld, one wait, pool with the first-strict-maximum argmax
 // rule (scan my = -1..1, then mx), release the accumulator, raise to lambda
 // (MUFU-based power), stage, store through TMA.
+// FP8 form: the same kernel with E4M3 operands (tcgen05.mma kind::f8f6f4,
+// K padded 144 -> 160, five MMAs of K = 32).  Each patch vector is scaled by a
+// power of two that brings its largest entry into (224, 448] (E4M3's top
+// binade), the image-2 descriptor field by one power of two chosen the same way
+// from its largest entry (a grid-wide max reduction first); the epilogue undoes
+// both scales per accumulator row before the power.
 // Every mbarrier wait is bounded; on timeout the kernel records an error in
 // *err, stops issuing work, releases TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "dm_internal.cuh"
 
@@ -49,45 +56,58 @@ namespace {
 
 constexpr int BM = 128;                       // patches per M-tile (TMEM lanes)
 constexpr int KD = 144;                       // 4 x 4 x 9
-constexpr int KSTEPS = KD / 16;               // MMAs per tile
 constexpr int CX = 33, CY = 7;                // C0 positions per N-tile
 constexpr int BN = 240;                       // CX * CY = 231, padded to a multiple of 16
 constexpr int PX = 16, PY = 3;                // pooled outputs per N-tile
-constexpr int GROUP = (KD / 8) * 128;         // 2304 bytes per 8-row group
-constexpr int A_TILE = BM * KD * 2;           // 36864
-constexpr int B_TILE = BN * KD * 2;           // 69120
-constexpr int STAGES = 2;
 constexpr int M_CHUNK = 110;                  // M-tiles per work unit
 constexpr int EPI_WARPS = 16;
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
 constexpr int THREADS = 64 + EPI_THREADS;
 constexpr int OUT_F = BM * PY * PX * 4;       // 24576: staged values of one tile
 constexpr int OUT_C = BM * PY * PX;           // 6144: staged argmax codes of one tile
-// shared-memory map (1024-byte aligned pieces)
-constexpr int OFF_B = 0;
-constexpr int OFF_A = 69632;
-constexpr int OFF_F = OFF_A + STAGES * A_TILE;      // 143360
-constexpr int OFF_C = OFF_F + 2 * OUT_F;            // 192512
-constexpr int OFF_BAR = OFF_C + 2 * OUT_C;          // 204800
-constexpr size_t SMEM = (size_t)OFF_BAR + 256;
 constexpr long long WAIT_CYCLES = 4000000000LL;     // ~2 s at 2 GHz
-static_assert(OFF_A >= B_TILE, "B tile overlaps A stages");
+
+enum { FMT_BF16 = 0, FMT_E4M3 = 1 };
+
+// Operand format traits: K padded to the MMA step, bytes per element,
+// instruction descriptor (D = F32; A = B = BF16 for kind::f16, E4M3 for kind::f8f6f4),
+// and the shared-memory map.
+template <int FMT>
+struct Fmt {
+    static constexpr int KP = FMT == FMT_BF16 ? 144 : 160;
+    static constexpr int ESZ = FMT == FMT_BF16 ? 2 : 1;
+    static constexpr int KSTEP = FMT == FMT_BF16 ? 16 : 32;
+    static constexpr int KSTEPS = KP / KSTEP;
+    static constexpr int ROWB = KP * ESZ;              // bytes per operand row
+    static constexpr int CHUNKS = ROWB / 16;           // 16-byte core-matrix rows along K
+    static constexpr int EPC = 16 / ESZ;               // elements per 16-byte chunk
+    static constexpr int GROUP = CHUNKS * 128;         // bytes per 8-row group
+    static constexpr int A_TILE = BM * ROWB;
+    static constexpr int B_TILE = BN * ROWB;
+    static constexpr int STAGES = FMT == FMT_BF16 ? 2 : 3;
+    static constexpr int OFF_B = 0;
+    static constexpr int OFF_A = ((B_TILE + 1023) / 1024) * 1024;
+    static constexpr int OFF_F = ((OFF_A + STAGES * A_TILE + 1023) / 1024) * 1024;
+    static constexpr int OFF_C = OFF_F + 2 * OUT_F;
+    static constexpr int OFF_BAR = OFF_C + 2 * OUT_C;
+    static constexpr size_t SMEM = (size_t)OFF_BAR + 256;
+    static constexpr uint32_t IDESC = (1u << 4) | (FMT == FMT_BF16 ? ((1u << 7) | (1u << 10)) : 0u) |
+                                      ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+};
+static_assert(Fmt<FMT_BF16>::SMEM <= 232448 && Fmt<FMT_E4M3>::SMEM <= 232448, "shared memory");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // tcgen05 shared-memory matrix descriptor, no swizzle: start address,
 // leading-dimension byte offset (between core matrices along K), stride byte
 // offset (between 8-row groups), fixed field 0b001 at bit 46.
-__device__ __forceinline__ uint64_t make_desc(uint32_t addr) {
+__device__ __forceinline__ uint64_t make_desc(uint32_t addr, uint32_t group) {
     uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
     d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((uint32_t)(GROUP >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)((group >> 4) & 0x3FFF) << 32;
     d |= (uint64_t)1 << 46;
     return d;
 }
-
-// instruction descriptor kind::f16: D = F32, A = B = BF16, both K-major, N, M
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err) {
     long long t0 = clock64();
@@ -117,11 +137,12 @@ __device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, %0;" :
 
 // Pack the patch vectors of I into BF16 M-tiles (zero rows past the last patch).
 __global__ void k_pack_a(DmGeom g, const float* __restrict__ d1, __nv_bfloat16* __restrict__ a16, int n_mtiles) {
-    const long long total = (long long)n_mtiles * BM * (KD / 8);
+    using F = Fmt<FMT_BF16>;
+    const long long total = (long long)n_mtiles * BM * F::CHUNKS;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
-    const int kc = (int)(idx % (KD / 8));
-    const int pm = (int)(idx / (KD / 8));
+    const int kc = (int)(idx % F::CHUNKS);
+    const int pm = (int)(idx / F::CHUNKS);
     const int n0 = g.P0x * g.P0y;
     __align__(16) __nv_bfloat16 v[8];
     const int px = 4 * (pm % g.P0x) + 2, py = 4 * (pm / g.P0x) + 2;
@@ -134,8 +155,69 @@ __global__ void k_pack_a(DmGeom g, const float* __restrict__ d1, __nv_bfloat16* 
         v[e] = __float2bfloat16_rn(f);
     }
     const int t = pm / BM, r = pm % BM;
-    char* dst = reinterpret_cast<char*>(a16) + (long long)t * A_TILE + (r >> 3) * GROUP + kc * 128 + (r & 7) * 16;
+    char* dst = reinterpret_cast<char*>(a16) + (long long)t * F::A_TILE + (r >> 3) * F::GROUP + kc * 128 + (r & 7) * 16;
     *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(v);
+}
+
+// Power of two s with m * s in (224, 448] (E4M3's top binade; 448 = its largest
+// finite value), 1 for m = 0.
+__device__ __forceinline__ float e4m3_scale(float m) {
+    if (!(m > 0.0f)) return 1.0f;
+    int e;
+    frexpf(448.0f / fmaxf(m, 1e-30f), &e);   // 448/m = f * 2^e, f in [0.5, 1): 2^(e-1) <= 448/m
+    return ldexpf(1.0f, e - 1);
+}
+
+// Largest |entry| of the image-2 descriptor field, as the bits of a
+// non-negative float (monotone as an unsigned integer), into *bmax (zeroed first).
+__global__ void k_absmax(const float* __restrict__ d, long long n, unsigned int* __restrict__ bmax) {
+    float m = 0.0f;
+    const long long n4 = (reinterpret_cast<uintptr_t>(d) & 15) == 0 ? n >> 2 : 0;   // float4 loads only when aligned
+    const float4* d4 = reinterpret_cast<const float4*>(d);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+        const float4 v = __ldg(d4 + i);
+        m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+    for (long long i = 4 * n4 + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(d[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(bmax, __float_as_uint(m));
+}
+
+// Pack the patch vectors into E4M3 M-tiles with a per-patch power-of-two scale
+// s_p bringing the largest entry into [224, 448]; inv_scale[p] = 1 / s_p.
+__global__ void k_pack_a8(DmGeom g, const float* __restrict__ d1, unsigned char* __restrict__ a8,
+                          float* __restrict__ inv_scale, int n_mtiles) {
+    using F = Fmt<FMT_E4M3>;
+    const int pm = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pm >= n_mtiles * BM) return;
+    const int n0 = g.P0x * g.P0y;
+    const int px = 4 * (pm % g.P0x) + 2, py = 4 * (pm / g.P0x) + 2;
+    float vals[KD];
+    float m = 0.0f;
+#pragma unroll 4
+    for (int k = 0; k < KD; k++) {
+        int dy = k / 36, dx = (k / 9) % 4, c = k % 9;
+        int x = px - 2 + dx, y = py - 2 + dy;
+        float f = (pm < n0 && x < g.W1 && y < g.H1) ? __ldg(d1 + ((long long)y * g.W1 + x) * 9 + c) : 0.0f;
+        vals[k] = f;
+        m = fmaxf(m, fabsf(f));
+    }
+    const float s = e4m3_scale(m);
+    inv_scale[pm] = 1.0f / s;
+    const int t = pm / BM, r = pm % BM;
+    char* base = reinterpret_cast<char*>(a8) + (long long)t * F::A_TILE + (r >> 3) * F::GROUP + (r & 7) * 16;
+#pragma unroll
+    for (int kc = 0; kc < F::CHUNKS; kc++) {
+        __align__(16) unsigned char q[16];
+#pragma unroll
+        for (int e = 0; e < 16; e++) {
+            const int k = kc * 16 + e;
+            q[e] = k < KD ? (unsigned char)__nv_cvt_float_to_fp8(vals[k] * s, __NV_SATFINITE, __NV_E4M3) : 0;
+        }
+        *reinterpret_cast<uint4*>(base + kc * 128) = *reinterpret_cast<const uint4*>(q);
+    }
 }
 
 struct EpiArgs {
@@ -149,8 +231,10 @@ struct EpiArgs {
 
 // Pool this thread's 4 x 3 outputs of one accumulator, release the
 // accumulator, and write the powered values and codes to the staging buffer.
-__device__ __forceinline__ void epilogue_tile(const EpiArgs& e, uint32_t b, uint32_t bar_empty, float* stage_f,
-                                              unsigned char* stage_c) {
+// `mult` turns an accumulator value into C0 (1/16, times the inverse operand
+// scales of the FP8 form; positive, so pooling on raw accumulators is exact).
+__device__ __forceinline__ void epilogue_tile(const EpiArgs& e, uint32_t b, uint32_t bar_empty, float mult,
+                                              float* stage_f, unsigned char* stage_c) {
     uint32_t r[CY][9];
     const uint32_t taddr = e.taddr + b * 256 + 8 * e.part;
 #pragma unroll
@@ -213,10 +297,10 @@ __device__ __forceinline__ void epilogue_tile(const EpiArgs& e, uint32_t b, uint
 #pragma unroll
     for (int y = 0; y < PY; y++) {
         float4 f;
-        f.x = __powf(best[y][0] * 0.0625f, e.lam);
-        f.y = __powf(best[y][1] * 0.0625f, e.lam);
-        f.z = __powf(best[y][2] * 0.0625f, e.lam);
-        f.w = __powf(best[y][3] * 0.0625f, e.lam);
+        f.x = __powf(best[y][0] * mult, e.lam);
+        f.y = __powf(best[y][1] * mult, e.lam);
+        f.z = __powf(best[y][2] * mult, e.lam);
+        f.w = __powf(best[y][3] * mult, e.lam);
         const int o = (e.row * PY + y) * PX + 4 * e.part;
         *reinterpret_cast<float4*>(stage_f + o) = f;
         *reinterpret_cast<uint32_t*>(stage_c + o) =
@@ -224,24 +308,29 @@ __device__ __forceinline__ void epilogue_tile(const EpiArgs& e, uint32_t b, uint
     }
 }
 
+template <int FMT>
 __global__ void __launch_bounds__(THREADS, 1)
-k_corr0_tc(DmGeom g, const __nv_bfloat16* __restrict__ a16, const float* __restrict__ d2, float lam,
-           const __grid_constant__ CUtensorMap tmap_f, const __grid_constant__ CUtensorMap tmap_c, int n_mtiles,
+k_corr0_tc(DmGeom g, const unsigned char* __restrict__ apack, const float* __restrict__ inv_sa,
+           const unsigned int* __restrict__ bmax, const float* __restrict__ d2,
+           float lam, const __grid_constant__ CUtensorMap tmap_f, const __grid_constant__ CUtensorMap tmap_c, int n_mtiles,
            int* __restrict__ err) {
+    using F = Fmt<FMT>;
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* sB = smem + OFF_B;
-    unsigned char* sA = smem + OFF_A;
-    float* sF = reinterpret_cast<float*>(smem + OFF_F);
-    unsigned char* sC = smem + OFF_C;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OFF_BAR);
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
+    unsigned char* sB = smem + F::OFF_B;
+    unsigned char* sA = smem + F::OFF_A;
+    float* sF = reinterpret_cast<float*>(smem + F::OFF_F);
+    unsigned char* sC = smem + F::OFF_C;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + F::OFF_BAR);
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * F::STAGES + 4);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
-    const uint32_t bar_full = smem_u32(bars), bar_empty = smem_u32(bars + STAGES);
-    const uint32_t bar_acc_full = smem_u32(bars + 2 * STAGES), bar_acc_empty = smem_u32(bars + 2 * STAGES + 2);
+    const uint32_t bar_full = smem_u32(bars), bar_empty = smem_u32(bars + F::STAGES);
+    const uint32_t bar_acc_full = smem_u32(bars + 2 * F::STAGES), bar_acc_empty = smem_u32(bars + 2 * F::STAGES + 2);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // image-2 operand scale of the FP8 form (power of two from the field's maximum)
+    const float s_b = FMT == FMT_E4M3 ? e4m3_scale(__uint_as_float(*bmax)) : 1.0f;
     if (tid == 0) {
-        for (int s = 0; s < STAGES; s++) {
+        for (int s = 0; s < F::STAGES; s++) {
             mbar_init(bar_full + 8 * s, 1);
             mbar_init(bar_empty + 8 * s, 1);
         }
@@ -261,6 +350,7 @@ k_corr0_tc(DmGeom g, const __nv_bfloat16* __restrict__ a16, const float* __restr
     const uint32_t tmem = *tmem_holder;
 
     const int W2 = g.W2, H2 = g.H2, mw = g.dw[1], mh = g.dh[1];
+    const int n0 = g.P0x * g.P0y;
     const int tiles_x = (mw + PX - 1) / PX, tiles_y = (mh + PY - 1) / PY;
     const int mchunks = (n_mtiles + M_CHUNK - 1) / M_CHUNK;
     const int n_units = tiles_x * tiles_y * mchunks;
@@ -273,21 +363,27 @@ k_corr0_tc(DmGeom g, const __nv_bfloat16* __restrict__ a16, const float* __restr
         const int rx0 = (ntile % tiles_x) * PX, ry0 = (ntile / tiles_x) * PY;
         const int cx0 = 2 * rx0 - 1, cy0 = 2 * ry0 - 1;
 
-        // B: implicit im2col of I' for this N-tile (zero outside I' and in rows 231..239)
-        for (int ch = tid; ch < BN * (KD / 8); ch += THREADS) {
-            const int n = ch / (KD / 8), kc = ch % (KD / 8);
+        // B: implicit im2col of I' for this N-tile (zero outside I', past K = 144
+        // and in rows 231..239), one 16-byte core-matrix row per item
+        for (int ch = tid; ch < BN * F::CHUNKS; ch += THREADS) {
+            const int n = ch / F::CHUNKS, kc = ch % F::CHUNKS;
             const int lx = n % CX, ly = n / CX;
             const int tx = cx0 + lx, ty = cy0 + ly;
-            __align__(16) __nv_bfloat16 v[8];
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-            for (int e = 0; e < 8; e++) {
-                int k = kc * 8 + e;
-                int dy = k / 36, dx = (k / 9) % 4, c = k % 9;
-                int x = tx - 2 + dx, y = ty - 2 + dy;
-                float f = (n < CX * CY && x >= 0 && y >= 0 && x < W2 && y < H2) ? __ldg(d2 + ((long long)y * W2 + x) * 9 + c) : 0.0f;
-                v[e] = __float2bfloat16_rn(f);
+            for (int e = 0; e < F::EPC; e++) {
+                const int k = kc * F::EPC + e;
+                const int dy = k / 36, dx = (k / 9) % 4, c = k % 9;
+                const int x = tx - 2 + dx, y = ty - 2 + dy;
+                const float f = (k < KD && n < CX * CY && x >= 0 && y >= 0 && x < W2 && y < H2)
+                                    ? __ldg(d2 + ((long long)y * W2 + x) * 9 + c) : 0.0f;
+                if (FMT == FMT_BF16) {
+                    w[e >> 1] |= (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(f)) << (16 * (e & 1));
+                } else {
+                    w[e >> 2] |= (uint32_t)__nv_cvt_float_to_fp8(f * s_b, __NV_SATFINITE, __NV_E4M3) << (8 * (e & 3));
+                }
             }
-            *reinterpret_cast<uint4*>(sB + (n >> 3) * GROUP + kc * 128 + (n & 7) * 16) = *reinterpret_cast<const uint4*>(v);
+            *reinterpret_cast<uint4*>(sB + (n >> 3) * F::GROUP + kc * 128 + (n & 7) * 16) = make_uint4(w[0], w[1], w[2], w[3]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -295,30 +391,34 @@ k_corr0_tc(DmGeom g, const __nv_bfloat16* __restrict__ a16, const float* __restr
         if (warp == 0) {
             if (lane == 0) {
                 for (int j = 0; j < nt; j++) {
-                    const uint32_t it = a_it + j, s = it % STAGES, ph = (it / STAGES) & 1;
+                    const uint32_t it = a_it + j, s = it % F::STAGES, ph = (it / F::STAGES) & 1;
                     if (!mbar_wait(bar_empty + 8 * s, ph ^ 1, abort_flag, err)) break;
-                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar_full + 8 * s), "r"(A_TILE) : "memory");
-                    const char* src = reinterpret_cast<const char*>(a16) + (long long)(m0 + j) * A_TILE;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar_full + 8 * s), "r"(F::A_TILE) : "memory");
+                    const unsigned char* src = apack + (long long)(m0 + j) * F::A_TILE;
                     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                                 :: "r"(smem_u32(sA + s * A_TILE)), "l"(src), "r"(A_TILE), "r"(bar_full + 8 * s) : "memory");
+                                 :: "r"(smem_u32(sA + s * F::A_TILE)), "l"(src), "r"(F::A_TILE), "r"(bar_full + 8 * s) : "memory");
                 }
             }
         } else if (warp == 1) {
             if (lane == 0) {
                 for (int j = 0; j < nt; j++) {
-                    const uint32_t it = a_it + j, s = it % STAGES, ph = (it / STAGES) & 1;
+                    const uint32_t it = a_it + j, s = it % F::STAGES, ph = (it / F::STAGES) & 1;
                     const uint32_t ai = acc_it + j, b = ai & 1, aph = (ai >> 1) & 1;
                     if (!mbar_wait(bar_full + 8 * s, ph, abort_flag, err)) break;
                     if (!mbar_wait(bar_acc_empty + 8 * b, aph ^ 1, abort_flag, err)) break;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t d_tmem = tmem + b * 256;
-                    const uint32_t a_base = smem_u32(sA + s * A_TILE), b_base = smem_u32(sB);
+                    const uint32_t a_base = smem_u32(sA + s * F::A_TILE), b_base = smem_u32(sB);
 #pragma unroll
-                    for (int k = 0; k < KSTEPS; k++) {
-                        uint64_t ad = make_desc(a_base + k * 256), bd = make_desc(b_base + k * 256);
-                        uint32_t acc = k > 0;
-                        asm volatile("{.reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;}"
-                                     :: "r"(d_tmem), "l"(ad), "l"(bd), "r"(IDESC), "r"(acc) : "memory");
+                    for (int k = 0; k < F::KSTEPS; k++) {
+                        const uint64_t ad = make_desc(a_base + k * 256, F::GROUP), bd = make_desc(b_base + k * 256, F::GROUP);
+                        const uint32_t acc = k > 0;
+                        if (FMT == FMT_BF16)
+                            asm volatile("{.reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;}"
+                                         :: "r"(d_tmem), "l"(ad), "l"(bd), "r"(F::IDESC), "r"(acc) : "memory");
+                        else
+                            asm volatile("{.reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;}"
+                                         :: "r"(d_tmem), "l"(ad), "l"(bd), "r"(F::IDESC), "r"(acc) : "memory");
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(bar_empty + 8 * s) : "memory");
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(bar_acc_full + 8 * b) : "memory");
@@ -338,9 +438,14 @@ k_corr0_tc(DmGeom g, const __nv_bfloat16* __restrict__ a16, const float* __restr
                 epi_barrier();
                 if (*abort_flag || !ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                float mult = 0.0625f;
+                if (FMT == FMT_E4M3) {
+                    const int p = (m0 + j) * BM + ea.row;
+                    mult = 0.0625f * ((p < n0 ? inv_sa[p] : 1.0f) / s_b);
+                }
                 float* stf = sF + b * (OUT_F / 4);
                 unsigned char* stc = sC + b * OUT_C;
-                epilogue_tile(ea, b, bar_acc_empty + 8 * b, stf, stc);
+                epilogue_tile(ea, b, bar_acc_empty + 8 * b, mult, stf, stc);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 epi_barrier();
                 if (store_leader) {
@@ -394,39 +499,64 @@ bool make_map(CUtensorMap* m, void* base, CUtensorMapDataType dt, int esize, con
               CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-}  // namespace
-
-size_t dm_corr0_bf16_a_bytes(const DmGeom& g) {
-    size_t n_mtiles = ((size_t)g.npatch(0) + BM - 1) / BM;
-    return n_mtiles * A_TILE;
-}
-
-cudaError_t dm_launch_corr0_bf16(const DmGeom& g, const float* d1, const float* d2, float lam, void* a16, void* status,
-                                 float* pooled0, unsigned char* amax0, cudaStream_t st) {
-    const int n0 = g.npatch(0);
-    const int n_mtiles = (n0 + BM - 1) / BM;
-    CUtensorMap mf, mc;
-    if (!make_map(&mf, pooled0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g) ||
-        !make_map(&mc, amax0, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, g))
-        return cudaErrorNotSupported;
-    {
-        long long total = (long long)n_mtiles * BM * (KD / 8);
-        k_pack_a<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(g, d1, reinterpret_cast<__nv_bfloat16*>(a16), n_mtiles);
-    }
+template <int FMT>
+cudaError_t launch_tc(const DmGeom& g, const unsigned char* apack, const float* inv_sa, const unsigned int* bmax,
+                      const float* d2, float lam,
+                      const CUtensorMap& mf, const CUtensorMap& mc, int n_mtiles, int* status, cudaStream_t st) {
+    using F = Fmt<FMT>;
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     static unsigned long long attr_set = 0;
     if (dev < 64 && !(attr_set & (1ull << dev))) {
-        cudaError_t e = cudaFuncSetAttribute(k_corr0_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+        cudaError_t e = cudaFuncSetAttribute(k_corr0_tc<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::SMEM);
         if (e != cudaSuccess) return e;
         attr_set |= 1ull << dev;
     }
     const int tiles = ((g.dw[1] + PX - 1) / PX) * ((g.dh[1] + PY - 1) / PY);
     const int units = tiles * ((n_mtiles + M_CHUNK - 1) / M_CHUNK);
     const int grid = units < nsm ? units : nsm;
-    k_corr0_tc<<<grid, THREADS, SMEM, st>>>(g, reinterpret_cast<const __nv_bfloat16*>(a16), d2, lam, mf, mc, n_mtiles,
-                                           reinterpret_cast<int*>(status));
-    dm_count_launches(2);
+    k_corr0_tc<FMT><<<grid, THREADS, F::SMEM, st>>>(g, apack, inv_sa, bmax, d2, lam, mf, mc, n_mtiles, status);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+// Packed-operand buffer: A tiles; FP8 form also the per-patch inverse scales
+// (f32 [n_mtiles * 128]) and the image-2 maximum (one u32).
+size_t dm_corr0_tc_a_bytes(const DmGeom& g, int precision) {
+    const size_t n_mtiles = ((size_t)g.npatch(0) + BM - 1) / BM;
+    if (precision == DM_FP8_E4M3)
+        return dm_align(n_mtiles * Fmt<FMT_E4M3>::A_TILE) + dm_align(n_mtiles * BM * sizeof(float)) + sizeof(unsigned int);
+    return n_mtiles * Fmt<FMT_BF16>::A_TILE;
+}
+
+cudaError_t dm_launch_corr0_tc(const DmGeom& g, int precision, const float* d1, const float* d2, float lam, void* abuf,
+                               void* status, float* pooled0, unsigned char* amax0, cudaStream_t st) {
+    const int n0 = g.npatch(0);
+    const int n_mtiles = (n0 + BM - 1) / BM;
+    CUtensorMap mf, mc;
+    if (!make_map(&mf, pooled0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g) ||
+        !make_map(&mc, amax0, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, g))
+        return cudaErrorNotSupported;
+    unsigned char* apack = reinterpret_cast<unsigned char*>(abuf);
+    cudaError_t e;
+    if (precision == DM_FP8_E4M3) {
+        const size_t a_bytes = dm_align((size_t)n_mtiles * Fmt<FMT_E4M3>::A_TILE);
+        float* inv_sa = reinterpret_cast<float*>(apack + a_bytes);
+        unsigned int* bmax = reinterpret_cast<unsigned int*>(apack + a_bytes + dm_align((size_t)n_mtiles * BM * sizeof(float)));
+        if ((e = cudaMemsetAsync(bmax, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
+        const long long n2 = (long long)g.W2 * g.H2 * 9;
+        const long long blocks = (n2 / 4 + 255) / 256;
+        k_absmax<<<(unsigned)(blocks < 1216 ? (blocks > 0 ? blocks : 1) : 1216), 256, 0, st>>>(d2, n2, bmax);
+        k_pack_a8<<<(unsigned)((n_mtiles * BM + 127) / 128), 128, 0, st>>>(g, d1, apack, inv_sa, n_mtiles);
+        e = launch_tc<FMT_E4M3>(g, apack, inv_sa, bmax, d2, lam, mf, mc, n_mtiles, reinterpret_cast<int*>(status), st);
+        dm_count_launches(3);
+    } else {
+        long long total = (long long)n_mtiles * BM * Fmt<FMT_BF16>::CHUNKS;
+        k_pack_a<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(g, d1, reinterpret_cast<__nv_bfloat16*>(apack), n_mtiles);
+        e = launch_tc<FMT_BF16>(g, apack, nullptr, nullptr, d2, lam, mf, mc, n_mtiles, reinterpret_cast<int*>(status), st);
+        dm_count_launches(2);
+    }
+    return e;
 }

@@ -19,7 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdm.so")
 
 DM_OK, DM_EINVAL, DM_ENOMEM, DM_ECUDA, DM_ETIMEOUT, DM_EUNSUPPORTED, DM_EOVERFLOW = range(7)
-DM_FP32, DM_BF16 = 0, 1
+DM_FP32, DM_BF16, DM_FP8_E4M3 = 0, 1, 2
 DM_DEV_FRONTIER_OVERFLOW, DM_DEV_OUTPUT_OVERFLOW, DM_DEV_TIMEOUT = 1, 2, 4
 STATUS_NAMES = {0: "DM_OK", 1: "DM_EINVAL", 2: "DM_ENOMEM", 3: "DM_ECUDA", 4: "DM_ETIMEOUT",
                 5: "DM_EUNSUPPORTED", 6: "DM_EOVERFLOW"}

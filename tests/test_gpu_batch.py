@@ -14,14 +14,14 @@ pytestmark = pytest.mark.gpu
 SIZES = [(64, 48), (37, 29), (96, 72), (130, 70), (64, 48)]
 
 
-@pytest.fixture(scope="module", params=["fp32", "bf16"])
+@pytest.fixture(scope="module", params=["fp32", "bf16", "fp8"])
 def env(request):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1506_07656_gb300 import build, dm
     build.build()
-    ctx = dm.Context(dm.DM_BF16 if request.param == "bf16" else dm.DM_FP32)
+    ctx = dm.Context({"fp32": dm.DM_FP32, "bf16": dm.DM_BF16, "fp8": dm.DM_FP8_E4M3}[request.param])
     yield torch, dm, ctx
     ctx.close()
 
