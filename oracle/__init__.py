@@ -7,7 +7,7 @@ CPU-baseline leg use it; the library never imports it.
 Two builds of one C source (``dm_oracle.c``):
   * ``prec="f64"`` -- FP64, the paper's order of operations (Algorithm 1).
   * ``prec="f32"`` -- FP32 canonical mirror: a fixed operation order, own
-    exp/log/pow, compensated 4-child sums; the bit-exact target of the FP32
+    exp/log/pow, 4-child sums in child order; the bit-exact target of the FP32
     GPU path.
 
 Functions and the passages they follow:

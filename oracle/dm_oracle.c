@@ -18,7 +18,7 @@
  *                 operation order (stated at each step), own exp/log/pow
  *                 routines, max-pooling on the raw aggregate followed by the
  *                 power (equal to the paper's order because x -> x^lambda is
- *                 increasing on [0,1]), and compensated 4-child sums.  It is
+ *                 increasing on [0,1]), and 4-child sums in child order.  It is
  *                 the bit-exact target of the FP32 GPU path.
  *
  * Readings of the paper where it is silent or ambiguous (numbered as in the
@@ -426,8 +426,8 @@ int orc_pyramid(const real* d1, int W1, int H1, const real* d2, int W2, int H2, 
                 for (int qy = 0; qy < mh; qy++)
                     for (int qx = 0; qx < mw; qx++) {
 #if ORC_F32
-                        /* compensated sum (Knuth TwoSum) over valid children, i = 0..3 */
-                        float s = 0.0f, comp = 0.0f;
+                        /* plain FP32 sum over valid children in order i = 0..3 (one rounding per addition) */
+                        float s = 0.0f;
 #else
                         double s = 0.0;
 #endif
@@ -438,18 +438,10 @@ int orc_pyramid(const real* d1, int W1, int H1, const real* d2, int W2, int H2, 
                             real v = 0;
                             if (rx >= 0 && ry >= 0 && rx < cw && ry < ch)
                                 v = pooled[l - 1][(size_t)ci[i] * cw * ch + (size_t)ry * cw + rx];
-#if ORC_F32
-                            float t = s + v;
-                            float bp = t - s;
-                            float err = (s - (t - bp)) + (v - bp);
-                            s = t;
-                            comp = comp + err;
-#else
                             s += v;
-#endif
                         }
 #if ORC_F32
-                        float a = (s + comp) / (float)n;
+                        float a = s / (float)n;
                         map[(size_t)qy * mw + qx] = a;                      /* rectified after pooling */
 #else
                         map[(size_t)qy * mw + qx] = RPOW(s / (double)n, lam);

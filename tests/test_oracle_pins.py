@@ -136,7 +136,7 @@ def test_p2_recursive_eq6(oracle_mod, W1, H1, W2, H2, seed):
                                 if 0 <= u < W2 and 0 <= v < H2:
                                     best = max(best, _recursive_C(d1, d2, lam, l, px, py, u, v, C0cache))
                         assert abs(pyr.pooled[l][p, ry, rx] - best) <= 1e-13
-    # the FP32 mirror (pool before the power, compensated sums) agrees closely
+    # the FP32 mirror (pool before the power, sums in child order) agrees closely
     p32 = oracle_mod.pyramid(d1.astype(np.float32), d2.astype(np.float32), "f32", lam)
     for l in range(g.L):
         np.testing.assert_allclose(p32.pooled[l], pyr.pooled[l], rtol=2e-5, atol=1e-7)
