@@ -138,7 +138,7 @@ dm_status run_pyramid(dm_ctx* c, const DmGeom& g, const float* d1, const float* 
                                 const_cast<unsigned char*>(py->amax[0]), st);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "level-0 correlation");
-    e = dm_launch_levels(g, *py, c->cfg.lambda, st);
+    e = dm_launch_levels(g, *py, c->cfg.lambda, d_status, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "pyramid levels");
     return DM_OK;
 }
@@ -461,7 +461,7 @@ dm_status dm_match(dm_ctx* ctx, const float* d_img1, int W1, int H1, const float
                                 const_cast<unsigned char*>(py.amax[0]), st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "level-0 correlation");
     if (ev) cudaEventRecord(ev[2], st);
-    e = dm_launch_levels(g, py, ctx->cfg.lambda, st);
+    e = dm_launch_levels(g, py, ctx->cfg.lambda, d_status, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "pyramid levels");
     if (ev) cudaEventRecord(ev[3], st);
     e = dm_launch_backtrack(g, py, ml.bt, base, d_out, capacity, d_count, st);

@@ -1,5 +1,6 @@
 // Internal declarations shared by the CUDA translation units of the library.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
@@ -196,6 +197,13 @@ int dm_ctx_device(const dm_ctx* ctx);
 void dm_count_launches(long long n);
 long long dm_launches();
 
+// Tiled tensor map (cuTensorMapEncodeTiled, reached through the runtime's
+// driver entry point): no interleave, no swizzle, zero fill outside the
+// extent, element strides 1.  False if the entry point is unavailable or the
+// map is rejected (base not 16-byte aligned, stride not a multiple of 16 B, ...).
+bool dm_encode_tiled(CUtensorMap* m, CUtensorMapDataType dt, int rank, void* base, const cuuint64_t* dims,
+                     const cuuint64_t* strides_bytes, const cuuint32_t* box);
+
 // Kernel launchers (return cudaGetLastError()).
 cudaError_t dm_launch_descriptors(const DmDescParams& prm, const float* img, int W, int H, float* desc,
                                   float* tmpA, float* tmpB, cudaStream_t st);
@@ -206,7 +214,7 @@ cudaError_t dm_launch_corr0_f32(const DmGeom& g, const float* d1, const float* d
 cudaError_t dm_launch_corr0_tc(const DmGeom& g, int precision, const float* d1, const float* d2, float lam, void* abuf,
                                void* status, float* pooled0, unsigned char* amax0, cudaStream_t st);
 size_t dm_corr0_tc_a_bytes(const DmGeom& g, int precision);
-cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& p, float lam, cudaStream_t st);
+cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& p, float lam, int* status, cudaStream_t st);
 cudaError_t dm_launch_loss_grad(const DmGeom& g, const dm_pyramid& py, const float* d1, const float* d2, float lam,
                                 const DmGradLayout& gl, char* ws, float* d_loss, float* g1, float* g2, cudaStream_t st);
 cudaError_t dm_launch_backtrack(const DmGeom& g, const dm_pyramid& p, const DmBtLayout& bl, char* ws,

@@ -19,22 +19,13 @@
 
 namespace {
 
-__device__ __forceinline__ void two_sum_add(float& s, float& comp, float v) {
-    const float t = __fadd_rn(s, v);
-    const float bp = __fsub_rn(t, s);
-    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
-    s = t;
-    comp = __fadd_rn(comp, err);
-}
-
 // Unrectified average of lattice patch p at level l >= 1, position (qx, qy),
 // exactly as the forward computes it; *n_out = number of existing children.
 __device__ float level_average(const DmGeom& g, int l, int p, int qx, int qy, const unsigned char* vprev,
                                const float* prev, int* n_out) {
     const int mw = g.dw[l], mh = g.dh[l], pitch = g.pitch(l);
-    float s = 0.0f, comp = 0.0f;
+    float s = 0.0f;
     int n = 0;
-    bool first = true;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         int c = dm_child(g, l, p % g.Lx, p / g.Lx, i);
@@ -44,12 +35,11 @@ __device__ float level_average(const DmGeom& g, int l, int p, int qx, int qy, co
         int rx = qx + ox, ry = qy + oy;
         float v = 0.0f;
         if (rx >= 0 && ry >= 0 && rx < mw && ry < mh) v = prev[(long long)c * g.psize(l) + (long long)ry * pitch + rx];
-        if (first) { s = v; first = false; }
-        else two_sum_add(s, comp, v);
+        s = __fadd_rn(s, v);
     }
     *n_out = n;
     if (n == 0) return 0.0f;
-    return __fdiv_rn(__fadd_rn(s, comp), (float)n);
+    return __fdiv_rn(s, (float)n);
 }
 
 __device__ __forceinline__ float dpow(float x, float lam) {   // d(x^lam)/dx for x in [0, 1]

@@ -470,33 +470,13 @@ k_corr0_tc(DmGeom g, const unsigned char* __restrict__ apack, const float* __res
     if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512));
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-    }
-    return fn;
-}
-
 // 3-D map of a pooled level-0 array [n0][mh][pitch] (elements of `esize` bytes),
 // logical extent mw x mh x n0, box 16 x 3 x 128.
 bool make_map(CUtensorMap* m, void* base, CUtensorMapDataType dt, int esize, const DmGeom& g) {
-    EncodeTiledFn fn = encode_fn();
-    if (!fn) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)g.dw[1], (cuuint64_t)g.dh[1], (cuuint64_t)g.npatch(0)};
     const cuuint64_t strides[2] = {(cuuint64_t)g.pitch(1) * esize, (cuuint64_t)g.pitch(1) * g.dh[1] * esize};
     const cuuint32_t box[3] = {PX, PY, BM};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    return fn(m, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return dm_encode_tiled(m, dt, 3, base, dims, strides, box);
 }
 
 template <int FMT>
@@ -521,6 +501,26 @@ cudaError_t launch_tc(const DmGeom& g, const unsigned char* apack, const float* 
 }
 
 }  // namespace
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+bool dm_encode_tiled(CUtensorMap* m, CUtensorMapDataType dt, int rank, void* base, const cuuint64_t* dims,
+                     const cuuint64_t* strides_bytes, const cuuint32_t* box) {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    if (!fn) return false;
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    return fn(m, dt, (cuuint32_t)rank, base, dims, strides_bytes, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 // Packed-operand buffer: A tiles; FP8 form also the per-patch inverse scales
 // (f32 [n_mtiles * 128]) and the image-2 maximum (one u32).

@@ -5,17 +5,19 @@
 // and, below the top, the stored pooled map
 //   P_l(p, r) = (max over in-domain m of C_l(p, 2r + m))^lambda   + argmax code,
 // or at the top C_L(p, q) = (C_l(p, q))^lambda.
-// The children's sum is a compensated (TwoSum) sum in child order i = 0..3,
-// rounded once and divided by n; pooling is on the unrectified average and the
-// power is applied to the pooled value (x -> x^lambda is increasing on [0,1]).
+// The children's sum is a plain FP32 sum in child order i = 0..3 (one
+// rounding per addition), then divided by n; pooling is on the unrectified
+// average and the power is applied to the pooled value (x -> x^lambda is
+// increasing on [0,1]).
 //
 // This pass streams the pooled maps of the level below (bandwidth) and does
-// a fixed amount of arithmetic per stored output (4 compensated averages,
+// a fixed amount of arithmetic per stored output (~4 averages of 4 values,
 // a 9-way max with argmax, one power).  A CTA owns one patch and a tile of
-// 32 x 16 pooled outputs (two per thread): it stages the 4 child-map windows
-// it needs in shared memory with 16-byte asynchronous copies (rows of the
-// pooled maps are padded to 8 floats, so every window row starts aligned; the
-// copy's source size zero-fills whatever lies outside the domain), forms the
+// 32 x 16 pooled outputs (two per thread): one thread stages the 4 child-map
+// windows it needs (72 x 33 floats each) in shared memory with 3-D TMA tensor
+// loads (rows of the pooled maps are padded to 16 floats and the window's
+// first column is a multiple of 4, so every load starts 16-byte aligned; the
+// tensor map zero-fills whatever lies outside the domain), the CTA forms the
 // 65 x 33 averages once, then pools them.  Patches vary fastest in the grid,
 // so the (up to 4) parents that read the same child window run at about the
 // same time and the repeat reads hit L2.  Algorithmic bytes per stored
@@ -49,7 +51,7 @@ struct Kids {
 };
 
 __device__ __forceinline__ float child_mean(const Kids& k, int qx, int qy, int mw, int mh, int pitch) {
-    float s = 0.0f, comp = 0.0f;
+    float s = 0.0f;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         if (k.base[i] == nullptr) continue;
@@ -57,13 +59,9 @@ __device__ __forceinline__ float child_mean(const Kids& k, int qx, int qy, int m
         int rx = qx + ox, ry = qy + oy;
         float v = 0.0f;
         if (rx >= 0 && ry >= 0 && rx < mw && ry < mh) v = __ldg(k.base[i] + (long long)ry * pitch + rx);
-        float t = __fadd_rn(s, v);
-        float bp = __fsub_rn(t, s);
-        float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
-        s = t;
-        comp = __fadd_rn(comp, err);
+        s = __fadd_rn(s, v);
     }
-    return __fdiv_rn(__fadd_rn(s, comp), (float)k.n);
+    return __fdiv_rn(s, (float)k.n);
 }
 
 
@@ -87,9 +85,12 @@ __device__ __forceinline__ bool load_kids(const DmGeom& g, int l, int p, const u
 
 constexpr int TW = 32, TH = 16;                // pooled outputs per CTA (lane, 2 x warp)
 constexpr int AW = 2 * TW + 1, AH = 2 * TH + 1;  // averages per CTA (65 x 33)
-constexpr int KW = 72;                           // staged child columns: 18 aligned float4
+constexpr int KW = 72;                           // staged child columns (TMA box width)
+constexpr int KIDF = 2400;                       // floats per staged window: 33 x 72 = 2376, padded to 128 B
 constexpr int AWP = 68;                          // padded row of the averages (16-byte aligned rows)
 constexpr int LEVEL_THREADS = 256;
+constexpr unsigned KID_BYTES = AH * KW * 4;      // bytes one TMA window load delivers
+constexpr long long LEVEL_WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 
 // x / n rounded once, for n in 1..4: multiplications by 1, 1/2, 1/4 are exact,
 // so they equal the correctly rounded quotient; n = 3 divides.
@@ -97,31 +98,23 @@ __device__ __forceinline__ float div_n(float x, int n) {
     return n == 3 ? __fdiv_rn(x, 3.0f) : __fmul_rn(x, n == 4 ? 0.25f : (n == 2 ? 0.5f : 1.0f));
 }
 
-// Knuth TwoSum step of the compensated child sum.
-__device__ __forceinline__ void two_sum_add(float& s, float& comp, float v) {
-    const float t = __fadd_rn(s, v);
-    const float bp = __fsub_rn(t, s);
-    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
-    s = t;
-    comp = __fadd_rn(comp, err);
-}
-
-// Average at staged position (ay, column c of child 0's frame) from the four
-// child windows: child i contributes kid[i][ay][ax + ox_i + 3].
+// Averages at staged row ay, columns ax .. ax+3 of child 0's frame, from the
+// four child windows: child i contributes kid[i][ay][ax + ox_i + 3].
 template <bool ALL4>
-__device__ __forceinline__ float4 avg4(const float (*kid)[AH][KW], int ay, int ax, const int* ci, int n) {
+__device__ __forceinline__ float4 avg4(const float* kid, int ay, int ax, const int* ci, int n) {
     // children with ox = -1 (i = 0, 1) read columns ax+2 .. ax+5 (8-byte aligned),
     // children with ox = +1 (i = 2, 3) read columns ax+4 .. ax+7 (16-byte aligned)
     float v[4][4];
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         if (!ALL4 && ci[i] < 0) continue;
+        const float* row = kid + i * KIDF + ay * KW;
         if (i < 2) {
-            const float2 a = *reinterpret_cast<const float2*>(&kid[i][ay][ax + 2]);
-            const float2 b = *reinterpret_cast<const float2*>(&kid[i][ay][ax + 4]);
+            const float2 a = *reinterpret_cast<const float2*>(row + ax + 2);
+            const float2 b = *reinterpret_cast<const float2*>(row + ax + 4);
             v[i][0] = a.x; v[i][1] = a.y; v[i][2] = b.x; v[i][3] = b.y;
         } else {
-            const float4 a = *reinterpret_cast<const float4*>(&kid[i][ay][ax + 4]);
+            const float4 a = *reinterpret_cast<const float4*>(row + ax + 4);
             v[i][0] = a.x; v[i][1] = a.y; v[i][2] = a.z; v[i][3] = a.w;
         }
     }
@@ -129,94 +122,100 @@ __device__ __forceinline__ float4 avg4(const float (*kid)[AH][KW], int ay, int a
 #pragma unroll
     for (int c = 0; c < 4; c++) {
         if (ALL4) {
-            float s = v[0][c], comp = 0.0f;
-            two_sum_add(s, comp, v[1][c]);
-            two_sum_add(s, comp, v[2][c]);
-            two_sum_add(s, comp, v[3][c]);
-            r[c] = __fmul_rn(__fadd_rn(s, comp), 0.25f);
+            r[c] = __fmul_rn(__fadd_rn(__fadd_rn(__fadd_rn(v[0][c], v[1][c]), v[2][c]), v[3][c]), 0.25f);
         } else {
-            float s = 0.0f, comp = 0.0f;
-            bool first = true;
+            float s = 0.0f;
 #pragma unroll
-            for (int i = 0; i < 4; i++) {
-                if (ci[i] < 0) continue;
-                if (first) { s = v[i][c]; first = false; }
-                else two_sum_add(s, comp, v[i][c]);
-            }
-            r[c] = div_n(__fadd_rn(s, comp), n);
+            for (int i = 0; i < 4; i++)
+                if (ci[i] >= 0) s = __fadd_rn(s, v[i][c]);
+            r[c] = div_n(s, n);
         }
     }
     return make_float4(r[0], r[1], r[2], r[3]);
 }
 
-__device__ __forceinline__ float avg1(const float (*kid)[AH][KW], int ay, int ax, const int* ci, int n) {
-    float s = 0.0f, comp = 0.0f;
-    bool first = true;
+__device__ __forceinline__ float avg1(const float* kid, int ay, int ax, const int* ci, int n) {
+    float s = 0.0f;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         if (ci[i] < 0) continue;
-        const float v = kid[i][ay][ax + ((i >= 2) ? 1 : -1) + 3];
-        if (first) { s = v; first = false; }
-        else two_sum_add(s, comp, v);
+        s = __fadd_rn(s, kid[i * KIDF + ay * KW + ax + ((i >= 2) ? 1 : -1) + 3]);
     }
-    return div_n(__fadd_rn(s, comp), n);
+    return div_n(s, n);
 }
 
-// Level l in [1, L-1]: grid (patch, tile).
-__global__ void __launch_bounds__(LEVEL_THREADS) k_level_pool_tiled(DmGeom g, int l, const unsigned char* __restrict__ vprev,
+// Level l in [1, L-1]: grid (patch, tile).  `tmap` maps the pooled maps of
+// level l-1 as a 3-D array (columns dw[l], rows dh[l], patches) with a
+// 72 x 33 x 1 box.
+__global__ void __launch_bounds__(LEVEL_THREADS) k_level_pool_tiled(DmGeom g, int l, const __grid_constant__ CUtensorMap tmap,
+                                                                    const unsigned char* __restrict__ vprev,
                                                                     const unsigned char* __restrict__ vcur,
-                                                                    const float* __restrict__ prev, float* __restrict__ out,
-                                                                    unsigned char* __restrict__ amax, float lam) {
-    __shared__ __align__(16) float kid[4][AH][KW];
+                                                                    float* __restrict__ out,
+                                                                    unsigned char* __restrict__ amax, float lam,
+                                                                    int* __restrict__ err) {
+    __shared__ __align__(128) float kid[4 * KIDF];
     __shared__ __align__(16) float avg[AH][AWP];
     __shared__ int kid_index[4];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_s;
     const int p = blockIdx.x;
     if (!vcur[p]) return;
     const int ow = g.dw[l + 1], oh = g.dh[l + 1], opitch = g.pitch(l + 1);
-    const int mw = g.dw[l], mh = g.dh[l], mpitch = g.pitch(l);
+    const int mw = g.dw[l], mh = g.dh[l];
     const int tiles_x = (ow + TW - 1) / TW;
     const int rx0 = (blockIdx.y % tiles_x) * TW, ry0 = (blockIdx.y / tiles_x) * TH;
     const int qx0 = 2 * rx0 - 1, qy0 = 2 * ry0 - 1;
-    const int xa = 2 * rx0 - 4;                      // aligned first staged child column
+    const int xa = 2 * rx0 - 4;                      // first staged child column (multiple of 4: 16-byte aligned)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t bar_s = (uint32_t)__cvta_generic_to_shared(&bar);
     if (tid < 4) {
         int c = dm_child(g, l, p % g.Lx, p / g.Lx, tid);
         kid_index[tid] = (c >= 0 && vprev[c]) ? c : -1;
     }
+    if (tid == 0) {
+        abort_s = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar_s) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     __syncthreads();
     int ci[4];
-    const float* cbase[4];
     int n = 0;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         ci[i] = kid_index[i];
-        cbase[i] = ci[i] >= 0 ? prev + (long long)ci[i] * g.psize(l) : prev;
         n += ci[i] >= 0;
     }
     // stage: child i, window rows qy0 + oy_i + [0, AH), columns xa + [0, KW)
-    constexpr int ROWV = KW / 4, PER_KID = AH * ROWV;
-    const unsigned kid_s = (unsigned)__cvta_generic_to_shared(&kid[0][0][0]);
+    if (tid == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar_s), "r"(KID_BYTES * n) : "memory");
+        const uint32_t kid_s = (uint32_t)__cvta_generic_to_shared(kid);
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-        const int oy = (i & 1) ? 1 : -1;
-        for (int e = tid; e < PER_KID; e += LEVEL_THREADS) {
-            const int ay = e / ROWV, v4 = e - ay * ROWV;
-            const int ry = qy0 + ay + oy, x = xa + 4 * v4;
-            int bytes = 0;
-            const float* src = prev;
-            if (ci[i] >= 0 && ry >= 0 && ry < mh && x >= 0 && x < mw) {
-                bytes = min(16, 4 * (mw - x));
-                src = cbase[i] + (long long)ry * mpitch + x;
-            }
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
-                         :: "r"(kid_s + 16u * (unsigned)(i * PER_KID + e)), "l"(src), "r"(bytes) : "memory");
+        for (int i = 0; i < 4; i++) {
+            if (ci[i] < 0) continue;
+            const int oy = (i & 1) ? 1 : -1;
+            asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                         :: "r"(kid_s + (uint32_t)(i * KIDF * 4)), "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(xa),
+                            "r"(qy0 + oy), "r"(ci[i]), "r"(bar_s)
+                         : "memory");
         }
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
+    {
+        const long long t0 = clock64();
+        uint32_t done = 0;
+        while (!done) {
+            asm volatile("{.reg .pred q; mbarrier.try_wait.parity.shared::cta.b64 q, [%1], 0; selp.u32 %0, 1, 0, q;}"
+                         : "=r"(done) : "r"(bar_s) : "memory");
+            if (!done && clock64() - t0 > LEVEL_WAIT_CYCLES) {
+                atomicOr(err, 1);
+                abort_s = 1;
+                break;
+            }
+        }
+    }
     __syncthreads();
-    // averages: compensated sum over existing children in order i = 0..3 (the
-    // first existing child starts the sum: 0 + v = v exactly, so this equals
-    // starting from zero), then / n; four adjacent columns per item.
+    if (abort_s) return;
+    // averages: sum over existing children in order i = 0..3, then / n; four
+    // adjacent columns per item.
     constexpr int G4 = (AW - 1) / 4;                 // 16 groups of 4 columns, then column 64
     for (int e = tid; e < AH * G4; e += LEVEL_THREADS) {
         const int ay = e / G4, ax = 4 * (e - ay * G4);
@@ -271,18 +270,26 @@ __global__ void k_level_top(DmGeom g, int l, const unsigned char* __restrict__ v
 
 }  // namespace
 
-cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& py, float lam, cudaStream_t st) {
+cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& py, float lam, int* status, cudaStream_t st) {
     const int B = 128;
     int n0 = g.npatch(0), np = g.npatch(1);
     k_fill_u8<<<(n0 + 255) / 256, 256, 0, st>>>(const_cast<unsigned char*>(py.valid[0]), n0, 1);
     for (int l = 1; l <= g.L; l++) {
         k_valid<<<(np + 255) / 256, 256, 0, st>>>(g, l, py.valid[l - 1], const_cast<unsigned char*>(py.valid[l]));
         if (l < g.L) {
+            // pooled maps of level l-1: [npatch(l-1)][dh[l]][pitch(l)] floats
+            CUtensorMap tm;
+            const cuuint64_t dims[3] = {(cuuint64_t)g.dw[l], (cuuint64_t)g.dh[l], (cuuint64_t)g.npatch(l - 1)};
+            const cuuint64_t strides[2] = {(cuuint64_t)g.pitch(l) * 4, (cuuint64_t)g.psize(l) * 4};
+            const cuuint32_t box[3] = {KW, AH, 1};
+            if (!dm_encode_tiled(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(py.pooled[l - 1]), dims,
+                                 strides, box))
+                return cudaErrorNotSupported;
             int tiles = ((g.dw[l + 1] + TW - 1) / TW) * ((g.dh[l + 1] + TH - 1) / TH);
             dim3 grid(np, tiles);
-            k_level_pool_tiled<<<grid, LEVEL_THREADS, 0, st>>>(g, l, py.valid[l - 1], py.valid[l], py.pooled[l - 1],
+            k_level_pool_tiled<<<grid, LEVEL_THREADS, 0, st>>>(g, l, tm, py.valid[l - 1], py.valid[l],
                                                          const_cast<float*>(py.pooled[l]),
-                                                         const_cast<unsigned char*>(py.amax[l]), lam);
+                                                         const_cast<unsigned char*>(py.amax[l]), lam, status);
         } else {
             int n = g.dw[l] * g.dh[l];
             dim3 grid((n + B - 1) / B, np);

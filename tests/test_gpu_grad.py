@@ -3,11 +3,10 @@ gradient with respect to both descriptor fields.
 
 Checked against the FP64 oracle gradient (which is itself pinned by central
 finite differences) and against central finite differences of the GPU loss
-(h = 1e-3) on 256x256 pairs.  Tolerances: relative L2 error of the gradient
+(h = 8e-3) on 256x256 pairs.  Tolerances: relative L2 error of the gradient
 vs FP64 <= 2e-3 (FP32 arithmetic through L+1 levels of powers); finite
 differences within 1.5e-2 relative or 2e-3 absolute (FP32 loss differences
-divided by 2h), skipping entries where the steps h, h/2, h/4 disagree (an
-argmax flips inside the stencil, where the loss has a kink).
+divided by 2h), skipping entries at kinks of the loss (see the test).
 """
 import numpy as np
 import pytest
@@ -78,13 +77,18 @@ def test_gradient_matches_fp64_oracle_images(env, oracle_mod):
 
 
 def test_gradient_finite_differences_256(env):
-    """Two 256x256 pairs, 64 random entries each (32 per descriptor field); the
-    loss has many kinks at this step size, so at least 20 smooth entries are
-    required to agree."""
+    """Two 256x256 pairs, 128 random entries in all (32 per descriptor field per
+    pair).  The FP32 loss difference carries rounding noise of order 1e-6 / h,
+    so the step is large (h = 8e-3; measured median error 1.3e-4 there,
+    growing as 1/h below).  The loss is a max of smooth functions: where an
+    argmax flips inside [x - h, x + h], or x sits on an exact tie, central
+    differences measure a mix of two slopes.  Such entries are recognised by
+    the analytic gradient itself, which then differs between x - h, x and
+    x + h, and are skipped.  At least 75% of the entries must be checked."""
     torch, dm, ctx = env
     rng = np.random.default_rng(0)
-    h = 1e-3
-    checked = 0
+    h = 8e-3
+    checked = total = 0
     for k in range(2):
         pr = synth.make_pair_smooth(256, 256, seed=300 + k, max_disp=16.0)
         H, W = pr.img1.shape
@@ -97,24 +101,22 @@ def test_gradient_finite_differences_256(env):
         for which, g in ((0, g1), (1, g2)):
             nz = np.flatnonzero(np.abs(g) > 1e-3 * np.abs(g).max())
             for idx in rng.choice(nz, size=32, replace=False):
-                diffs = []
-                for step in (h, h / 2, h / 4):
-                    dp = [x.copy() for x in d]
-                    dm_ = [x.copy() for x in d]
-                    dp[which].flat[idx] += step
-                    dm_[which].flat[idx] -= step
-                    _, pp = _gpu_loss_grad(torch, dm, ctx, dp[0], dp[1], want_grad=False)
-                    _, pm = _gpu_loss_grad(torch, dm, ctx, dm_[0], dm_[1], want_grad=False)
-                    diffs.append(np.sum(pp - pm) / (2 * step))     # unaffected patches cancel exactly
-                fd = diffs[0]
-                # the loss is a max of smooth functions: where an argmax flips within the
-                # stencil the three step sizes disagree, and such entries are skipped
-                if max(diffs) - min(diffs) > 1e-2 * max(abs(fd), 1e-1):
-                    continue
+                total += 1
                 a = g.flat[idx]
-                assert abs(fd - a) <= max(1.5e-2 * abs(a), 2e-3), (which, idx, diffs, a)
+                dp = [x.copy() for x in d]
+                dm_ = [x.copy() for x in d]
+                dp[which].flat[idx] += h
+                dm_[which].flat[idx] -= h
+                _, pp, *gp = _gpu_loss_grad(torch, dm, ctx, dp[0], dp[1])
+                _, pm, *gm = _gpu_loss_grad(torch, dm, ctx, dm_[0], dm_[1])
+                ap, am = gp[which].flat[idx], gm[which].flat[idx]
+                if max(abs(ap - a), abs(am - a)) > 2e-3 + 2e-2 * abs(a):
+                    continue                                    # kink inside the stencil
+                fd = np.sum(pp - pm) / (2 * h)                  # unaffected patches cancel exactly
+                assert abs(fd - a) <= max(1.5e-2 * abs(a), 2e-3), (k, which, idx, fd, a, ap, am)
                 checked += 1
-    assert checked >= 20
+    print(f"finite differences: {checked} of {total} entries checked")
+    assert checked >= 0.75 * total
 
 
 def test_autograd_function(env):
