@@ -7,7 +7,8 @@ CPU-baseline leg use it; the library never imports it.
 Two builds of one C source (``dm_oracle.c``):
   * ``prec="f64"`` -- FP64, the paper's order of operations (Algorithm 1).
   * ``prec="f32"`` -- FP32 canonical mirror: a fixed operation order, own
-    exp/log/pow, 4-child sums in child order; the bit-exact target of the FP32
+    exp/log/pow, compensated (or plain) 4-child sums in child order, exact
+    fixed-point path scores; the bit-exact target of the FP32
     GPU path.
 
 Functions and the passages they follow:
@@ -157,7 +158,10 @@ class Pyramid:
     valid: list = field(default_factory=list)    # l = 0..L: [npatch(l)] uint8
 
 
-def pyramid(d1: np.ndarray, d2: np.ndarray, prec: str = "f64", lam: float = DEFAULT_CFG["lam"]) -> Pyramid:
+def pyramid(d1: np.ndarray, d2: np.ndarray, prec: str = "f64", lam: float = DEFAULT_CFG["lam"],
+            compensated: bool = True) -> Pyramid:
+    """Level maps of Algorithm 1.  `compensated` selects the FP32 mirror's
+    child sum (TwoSum-compensated or plain, both in child order); FP64 ignores it."""
     dt = _dtype(prec)
     d1 = np.ascontiguousarray(d1, dtype=dt)
     d2 = np.ascontiguousarray(d2, dtype=dt)
@@ -175,9 +179,10 @@ def pyramid(d1: np.ndarray, d2: np.ndarray, prec: str = "f64", lam: float = DEFA
     aa = (C.c_void_p * g.L)(*[a.ctypes.data for a in pyr.argmax])
     vv = (C.c_void_p * (g.L + 1))(*[a.ctypes.data for a in pyr.valid])
     lib = _lib(prec)
-    lib.orc_pyramid.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_double,
+    lib.orc_pyramid.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int,
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
-    rc = lib.orc_pyramid(_ptr(d1), W1, H1, _ptr(d2), W2, H2, float(lam), pp, aa, _ptr(pyr.top), vv)
+    rc = lib.orc_pyramid(_ptr(d1), W1, H1, _ptr(d2), W2, H2, float(lam), int(bool(compensated)), pp, aa,
+                         _ptr(pyr.top), vv)
     if rc != 0:
         raise ValueError("pyramid oracle failed")
     return pyr
@@ -226,13 +231,13 @@ def reciprocal(pyr: Pyramid, bt: Backtrack) -> np.ndarray:
     return out[:n]
 
 
-def match(img1: np.ndarray, img2: np.ndarray, prec: str = "f64", **cfg):
+def match(img1: np.ndarray, img2: np.ndarray, prec: str = "f64", compensated: bool = True, **cfg):
     """Descriptors -> pyramid -> backtracking -> reciprocal matches."""
     c = dict(DEFAULT_CFG, **cfg)
     lam = c.pop("lam")
     d1 = descriptors(img1, prec, **c)
     d2 = descriptors(img2, prec, **c)
-    pyr = pyramid(d1, d2, prec, lam)
+    pyr = pyramid(d1, d2, prec, lam, compensated)
     bt = backtrack(pyr)
     return reciprocal(pyr, bt), pyr, bt
 

@@ -18,8 +18,13 @@
  *                 operation order (stated at each step), own exp/log/pow
  *                 routines, max-pooling on the raw aggregate followed by the
  *                 power (equal to the paper's order because x -> x^lambda is
- *                 increasing on [0,1]), and 4-child sums in child order.  It is
- *                 the bit-exact target of the FP32 GPU path.
+ *                 increasing on [0,1]), 4-child sums in child order
+ *                 (compensated with Knuth's TwoSum by default, plain on
+ *                 request), and path scores accumulated exactly in unsigned
+ *                 32-bit fixed point with 28 fractional bits (each term
+ *                 rounded to the nearest multiple of 2^-28, the sum rounded
+ *                 to FP32 once at the end).  It is the bit-exact target of
+ *                 the FP32 GPU path.
  *
  * Readings of the paper where it is silent or ambiguous (numbered as in the
  * design notes):
@@ -40,7 +45,8 @@
  *   c13 argmax = first strict maximum, scan order m_y = -1..1 then m_x = -1..1;
  *       ties in BestAt/BestAt': higher score, then lower index.
  *   c14 L = min{l : 4*2^l >= max(W,H)} (image 1); entries = all top positions.
- *   c15 path score = top value + pooled values along the path, summed top-down.
+ *   c15 path score = top value + pooled values along the path, summed top-down
+ *       (FP32 mirror: exact fixed-point sum, see the path-score helpers).
  *   c17 BestAt / BestAt' over aligned 4x4 cells (the atomic patch in I, the cell
  *       floor(t/4) in I'); a tuple survives iff it is the best of both.
  */
@@ -371,7 +377,7 @@ static void pool_map(const real* src, int sw, int sh, real* dst, uint8_t* am, in
 /* top       : [npatch(L)][dh[L]][dw[L]]       = C_L                          */
 /* valid[l]  : [npatch(l)] patch membership of G_{4*2^l}, l = 0..L            */
 /* ------------------------------------------------------------------------- */
-int orc_pyramid(const real* d1, int W1, int H1, const real* d2, int W2, int H2, double lambda,
+int orc_pyramid(const real* d1, int W1, int H1, const real* d2, int W2, int H2, double lambda, int compensated,
                 real** pooled, uint8_t** amax, real* top, uint8_t** valid) {
     geom g;
     if (make_geom(W1, H1, W2, H2, &g)) return -1;
@@ -426,8 +432,10 @@ int orc_pyramid(const real* d1, int W1, int H1, const real* d2, int W2, int H2, 
                 for (int qy = 0; qy < mh; qy++)
                     for (int qx = 0; qx < mw; qx++) {
 #if ORC_F32
-                        /* plain FP32 sum over valid children in order i = 0..3 (one rounding per addition) */
-                        float s = 0.0f;
+                        /* FP32 sum over valid children in order i = 0..3: Knuth TwoSum with a
+                         * running compensation, rounded once at the end (compensated), or one
+                         * rounding per addition (plain) */
+                        float s = 0.0f, comp = 0.0f;
 #else
                         double s = 0.0;
 #endif
@@ -438,10 +446,20 @@ int orc_pyramid(const real* d1, int W1, int H1, const real* d2, int W2, int H2, 
                             real v = 0;
                             if (rx >= 0 && ry >= 0 && rx < cw && ry < ch)
                                 v = pooled[l - 1][(size_t)ci[i] * cw * ch + (size_t)ry * cw + rx];
+#if ORC_F32
+                            float t = s + v;
+                            if (compensated) {
+                                float bp = t - s;
+                                float err = (s - (t - bp)) + (v - bp);
+                                comp = comp + err;
+                            }
+                            s = t;
+#else
                             s += v;
+#endif
                         }
 #if ORC_F32
-                        float a = s / (float)n;
+                        float a = (s + comp) / (float)n;
                         map[(size_t)qy * mw + qx] = a;                      /* rectified after pooling */
 #else
                         map[(size_t)qy * mw + qx] = RPOW(s / (double)n, lam);
@@ -503,8 +521,28 @@ int orc_level0_pooled(const real* d1, int W1, int H1, const real* d2, int W2, in
 /* reached[l]   : number of distinct tuples at level l (l = 0..L).            */
 /* ------------------------------------------------------------------------- */
 
-static int better(real s, long long idx, real bs, long long bidx) {
-    return s > bs || (s == bs && idx < bidx);
+/* Path scores (reading c15).  FP64: plain double sums.  FP32 mirror: unsigned
+ * fixed point with 28 fractional bits; every term (a map value in [0, 1]) is
+ * rounded to the nearest multiple of 2^-28 (ties to even) and the sum of the
+ * L + 1 terms (< 16) is exact, hence independent of order and of the merging;
+ * it is rounded to FP32 once, at the end. */
+#if ORC_F32
+typedef uint32_t pscore;
+#define PS_NONE 0xFFFFFFFFu
+static pscore ps_term(real v) { return (pscore)nearbyintf(v * 268435456.0f); }
+static real ps_value(pscore s) { return (real)s * (1.0f / 268435456.0f); }
+#else
+typedef double pscore;
+#define PS_NONE (-INFINITY)
+static pscore ps_term(real v) { return v; }
+static real ps_value(pscore s) { return s; }
+#endif
+
+/* merge: keep the larger score (PS_NONE = absent) */
+static int ps_greater(pscore s, pscore cur) { return cur == PS_NONE || s > cur; }
+
+static int better(pscore s, long long idx, pscore bs, long long bidx) {
+    return bs == PS_NONE || s > bs || (s == bs && idx < bidx);
 }
 
 int orc_backtrack(int W1, int H1, int W2, int H2, real** pooled, uint8_t** amax, const real* top, uint8_t** valid,
@@ -514,20 +552,28 @@ int orc_backtrack(int W1, int H1, int W2, int H2, real** pooled, uint8_t** amax,
     const int L = g.L;
     const int n0 = npatch(&g, 0);
     const int CW = (W2 + 3) / 4, CH = (H2 + 3) / 4;
-    for (int p = 0; p < n0; p++) { bestP_s[p] = RNEG_INF; bestP_i[p] = -1; }
-    for (int c = 0; c < CW * CH; c++) { bestQ_s[c] = RNEG_INF; bestQ_i[c] = -1; }
-    if (leaf) for (size_t k = 0; k < (size_t)n0 * W2 * H2; k++) leaf[k] = RNEG_INF;
+    pscore* bP = (pscore*)malloc((size_t)n0 * sizeof(pscore));
+    pscore* bQ = (pscore*)malloc((size_t)CW * CH * sizeof(pscore));
+    if (!bP || !bQ) { free(bP); free(bQ); return -2; }
+    for (int p = 0; p < n0; p++) { bP[p] = PS_NONE; bestP_i[p] = -1; }
+    for (int c = 0; c < CW * CH; c++) { bQ[c] = PS_NONE; bestQ_i[c] = -1; }
+    pscore* lf = NULL;
+    if (leaf) {
+        lf = (pscore*)malloc((size_t)n0 * W2 * H2 * sizeof(pscore));
+        if (!lf) { free(bP); free(bQ); return -2; }
+        for (size_t k = 0; k < (size_t)n0 * W2 * H2; k++) lf[k] = PS_NONE;
+    }
     for (int l = 0; l <= L; l++) reached[l] = 0;
 
     /* current merged set, level L */
     const int npL = npatch(&g, L);
     size_t ncur = (size_t)npL * g.dw[L] * g.dh[L];
-    real* cur = (real*)malloc(ncur * sizeof(real));
-    if (!cur) return -2;
+    pscore* cur = (pscore*)malloc(ncur * sizeof(pscore));
+    if (!cur) { free(bP); free(bQ); free(lf); return -2; }
     for (int p = 0; p < npL; p++)
         for (size_t k = 0; k < (size_t)g.dw[L] * g.dh[L]; k++) {
             size_t o = (size_t)p * g.dw[L] * g.dh[L] + k;
-            cur[o] = valid[L][p] ? top[o] : RNEG_INF;
+            cur[o] = valid[L][p] ? ps_term(top[o]) : PS_NONE;
             if (valid[L][p]) reached[L]++;  /* one tuple per (p, q) */
         }
 
@@ -535,19 +581,19 @@ int orc_backtrack(int W1, int H1, int W2, int H2, real** pooled, uint8_t** amax,
         const int mw = g.dw[l], mh = g.dh[l];           /* domain of the current level's positions q */
         const int tw = g.dw[l - 1], th = g.dh[l - 1];   /* domain of the children's positions t */
         const int npc = npatch(&g, l - 1);
-        real* nxt = NULL;
+        pscore* nxt = NULL;
         if (l - 1 >= 1) {
-            nxt = (real*)malloc((size_t)npc * tw * th * sizeof(real));
-            if (!nxt) { free(cur); return -2; }
-            for (size_t k = 0; k < (size_t)npc * tw * th; k++) nxt[k] = RNEG_INF;
+            nxt = (pscore*)malloc((size_t)npc * tw * th * sizeof(pscore));
+            if (!nxt) { free(cur); free(bP); free(bQ); free(lf); return -2; }
+            for (size_t k = 0; k < (size_t)npc * tw * th; k++) nxt[k] = PS_NONE;
         }
         const int np = npatch(&g, l);
         for (int p = 0; p < np; p++) {
             if (!valid[l][p]) continue;
             for (int qy = 0; qy < mh; qy++)
                 for (int qx = 0; qx < mw; qx++) {
-                    real s = cur[(size_t)p * mw * mh + (size_t)qy * mw + qx];
-                    if (s == RNEG_INF) continue;
+                    pscore s = cur[(size_t)p * mw * mh + (size_t)qy * mw + qx];
+                    if (s == PS_NONE) continue;
                     for (int i = 0; i < 4; i++) {
                         int c = child_index(&g, l, p % g.Lx, p / g.Lx, i);
                         if (c < 0 || !valid[l - 1][c]) continue;
@@ -557,20 +603,20 @@ int orc_backtrack(int W1, int H1, int W2, int H2, real** pooled, uint8_t** amax,
                         size_t ro = (size_t)c * mw * mh + (size_t)ry * mw + rx;
                         int code = amax[l - 1][ro];
                         int tx = 2 * rx + (code % 3 - 1), ty = 2 * ry + (code / 3 - 1);
-                        real s2 = s + pooled[l - 1][ro];              /* Eq. 14: s + C_{N/2,p_i}(p'_i) */
+                        pscore s2 = s + ps_term(pooled[l - 1][ro]);   /* Eq. 14: s + C_{N/2,p_i}(p'_i) */
                         if (l - 1 >= 1) {
-                            real* d = &nxt[(size_t)c * tw * th + (size_t)ty * tw + tx];
-                            if (s2 > *d) *d = s2;
+                            pscore* d = &nxt[(size_t)c * tw * th + (size_t)ty * tw + tx];
+                            if (ps_greater(s2, *d)) *d = s2;
                         } else {
                             long long tidx = (long long)ty * W2 + tx;
-                            if (leaf) {
-                                real* d = &leaf[(size_t)c * W2 * H2 + tidx];
-                                if (s2 > *d) *d = s2;
+                            if (lf) {
+                                pscore* d = &lf[(size_t)c * W2 * H2 + tidx];
+                                if (ps_greater(s2, *d)) *d = s2;
                             }
-                            if (better(s2, tidx, bestP_s[c], bestP_i[c])) { bestP_s[c] = s2; bestP_i[c] = tidx; }
+                            if (better(s2, tidx, bP[c], bestP_i[c])) { bP[c] = s2; bestP_i[c] = tidx; }
                             int cell = (ty / 4) * CW + tx / 4;
                             long long qidx = (long long)c * 16 + (ty % 4) * 4 + (tx % 4);
-                            if (better(s2, qidx, bestQ_s[cell], bestQ_i[cell])) { bestQ_s[cell] = s2; bestQ_i[cell] = qidx; }
+                            if (better(s2, qidx, bQ[cell], bestQ_i[cell])) { bQ[cell] = s2; bestQ_i[cell] = qidx; }
                         }
                     }
                 }
@@ -579,18 +625,27 @@ int orc_backtrack(int W1, int H1, int W2, int H2, real** pooled, uint8_t** amax,
         cur = nxt;
         if (l - 1 >= 1) {
             long long cnt = 0;
-            for (size_t k = 0; k < (size_t)npc * tw * th; k++) cnt += (cur[k] != RNEG_INF);
+            for (size_t k = 0; k < (size_t)npc * tw * th; k++) cnt += (cur[k] != PS_NONE);
             reached[l - 1] = cnt;
         }
     }
-    if (leaf) {
+    /* scores out, rounded once */
+    for (int p = 0; p < n0; p++) bestP_s[p] = bP[p] == PS_NONE ? RNEG_INF : ps_value(bP[p]);
+    for (int c = 0; c < CW * CH; c++) bestQ_s[c] = bQ[c] == PS_NONE ? RNEG_INF : ps_value(bQ[c]);
+    if (lf) {
         long long cnt = 0;
-        for (size_t k = 0; k < (size_t)n0 * W2 * H2; k++) cnt += (leaf[k] != RNEG_INF);
+        for (size_t k = 0; k < (size_t)n0 * W2 * H2; k++) {
+            cnt += (lf[k] != PS_NONE);
+            leaf[k] = lf[k] == PS_NONE ? RNEG_INF : ps_value(lf[k]);
+        }
         reached[0] = cnt;
     } else {
         reached[0] = -1;   /* not counted without the dense leaf array */
     }
     free(cur);
+    free(bP);
+    free(bQ);
+    free(lf);
     return 0;
 }
 

@@ -136,11 +136,63 @@ def test_p2_recursive_eq6(oracle_mod, W1, H1, W2, H2, seed):
                                 if 0 <= u < W2 and 0 <= v < H2:
                                     best = max(best, _recursive_C(d1, d2, lam, l, px, py, u, v, C0cache))
                         assert abs(pyr.pooled[l][p, ry, rx] - best) <= 1e-13
-    # the FP32 mirror (pool before the power, sums in child order) agrees closely
-    p32 = oracle_mod.pyramid(d1.astype(np.float32), d2.astype(np.float32), "f32", lam)
-    for l in range(g.L):
-        np.testing.assert_allclose(p32.pooled[l], pyr.pooled[l], rtol=2e-5, atol=1e-7)
-    np.testing.assert_allclose(p32.top, pyr.top, rtol=2e-5, atol=1e-7)
+    # the FP32 mirror (pool before the power, compensated or plain sums in child
+    # order) agrees closely
+    for comp in (True, False):
+        p32 = oracle_mod.pyramid(d1.astype(np.float32), d2.astype(np.float32), "f32", lam, compensated=comp)
+        for l in range(g.L):
+            np.testing.assert_allclose(p32.pooled[l], pyr.pooled[l], rtol=2e-5, atol=1e-7)
+        np.testing.assert_allclose(p32.top, pyr.top, rtol=2e-5, atol=1e-7)
+
+
+def test_compensated_child_sums_are_closer_to_fp64(oracle_mod):
+    """The two FP32 child sums on the same FP32 inputs: the TwoSum-compensated
+    average is the FP32 rounding of an almost exact sum, the plain one carries
+    up to three roundings, so against the FP64 average of the same inputs the
+    compensated form is never further than 1 ulp and on average closer."""
+    d1 = synth.random_descriptor_field(24, 20, 3).astype(np.float32)
+    d2 = synth.random_descriptor_field(26, 18, 4).astype(np.float32)
+    pc = oracle_mod.pyramid(d1, d2, "f32", compensated=True)
+    pp = oracle_mod.pyramid(d1, d2, "f32", compensated=False)
+    # identical level-0 maps (the child sum starts at level 1)
+    np.testing.assert_array_equal(pc.pooled[0], pp.pooled[0])
+    g = pc.geom
+    # level 1 from the same level-0 maps: FP64 average of the children, then the
+    # FP32 power of each form's pooled maximum compared through its argmax
+    errs_c, errs_p = [], []
+    for p in range(g.npatch(1)):
+        if not pc.valid[1][p]:
+            continue
+        kids = []
+        for i in range(4):
+            ox = 1 if i >= 2 else -1
+            oy = 1 if (i & 1) else -1
+            cx = p % g.Lx + (ox - 1) // 2
+            cy = p // g.Lx + (oy - 1) // 2
+            if 0 <= cx < g.P0x and 0 <= cy < g.P0y:
+                kids.append((cy * g.P0x + cx, ox, oy))
+        mw, mh = g.dw[1], g.dh[1]
+        exact = np.zeros((mh, mw))
+        for c, ox, oy in kids:
+            src = pc.pooled[0][c].astype(np.float64)
+            sh = np.zeros((mh, mw))
+            ys, xs = np.mgrid[0:mh, 0:mw]
+            ok = (xs + ox >= 0) & (xs + ox < mw) & (ys + oy >= 0) & (ys + oy < mh)
+            sh[ok] = src[(ys + oy)[ok], (xs + ox)[ok]]
+            exact += sh
+        exact /= len(kids)
+        for pyr, errs in ((pc, errs_c), (pp, errs_p)):
+            if g.L > 1:
+                am = pyr.argmax[1][p]
+                ry, rx = np.mgrid[0:am.shape[0], 0:am.shape[1]]
+                qx = np.clip(2 * rx + am % 3 - 1, 0, mw - 1)
+                qy = np.clip(2 * ry + am // 3 - 1, 0, mh - 1)
+                want = np.power(exact[qy, qx], 1.4)
+                got = pyr.pooled[1][p].astype(np.float64)
+                errs.append(np.abs(got - want) / want)
+    ec, ep = np.concatenate([e.ravel() for e in errs_c]), np.concatenate([e.ravel() for e in errs_p])
+    assert ec.mean() <= ep.mean()
+    assert ec.max() <= 4.0 * 2.0 ** -23      # power accuracy (4 ulp) dominates
 
 
 # --------------------------------------------------------------------------- #
@@ -154,7 +206,10 @@ def _enumerate_paths(pyr):
     P, QY, QX = np.nonzero(np.ones_like(pyr.top, dtype=bool))
     keep = pyr.valid[L][P].astype(bool)
     P, QY, QX = P[keep], QY[keep], QX[keep]
-    S = pyr.top[P, QY, QX].astype(dt)
+    # FP32 mirror: path scores are exact sums of terms rounded to multiples of 2^-28
+    fixed = dt == np.float32
+    term = (lambda v: np.rint(v.astype(np.float32) * np.float32(2.0 ** 28)).astype(np.int64)) if fixed else (lambda v: v)
+    S = term(pyr.top[P, QY, QX])
     EP, EQX, EQY = P.copy(), QX.copy(), QY.copy()
     for l in range(L, 0, -1):
         nP, nX, nY, nS, nE, nEX, nEY = [], [], [], [], [], [], []
@@ -181,11 +236,13 @@ def _enumerate_paths(pyr):
             code = pyr.argmax[l - 1][c, ry, rx].astype(np.int64)
             tx = 2 * rx + code % 3 - 1
             ty = 2 * ry + code // 3 - 1
-            s2 = (S + pyr.pooled[l - 1][c, ry, rx]).astype(dt)
+            s2 = S + term(pyr.pooled[l - 1][c, ry, rx])
             nP.append(c[ok]); nX.append(tx[ok]); nY.append(ty[ok]); nS.append(s2[ok])
             nE.append(EP[ok]); nEX.append(EQX[ok]); nEY.append(EQY[ok])
         P, QX, QY, S = np.concatenate(nP), np.concatenate(nX), np.concatenate(nY), np.concatenate(nS)
         EP, EQX, EQY = np.concatenate(nE), np.concatenate(nEX), np.concatenate(nEY)
+    if fixed:
+        S = (S.astype(np.float32) * np.float32(2.0 ** -28)).astype(np.float32)   # rounded once
     return P, QX, QY, S, EP, EQX, EQY
 
 
