@@ -69,6 +69,11 @@ typedef struct {
     float lambda;          /* rectification exponent (Eq. 11)                      */
     float image_scale;     /* multiplier applied to input intensities              */
     int precision;         /* dm_precision                                         */
+    int compensated;       /* 1 (default): the 4-child sums of the pyramid (Eq. 12)
+                              are Knuth-TwoSum compensated, rounded once; 0: plain
+                              FP32 sums in child order.  Path scores (Eq. 14) are
+                              always exact: terms rounded to multiples of 2^-28,
+                              summed in 32-bit fixed point, rounded to FP32 once */
 } dm_config;
 
 /* One output correspondence (Eq. 16): (x1, y1) is the centre of an atomic
@@ -87,7 +92,7 @@ typedef struct dm_pyramid dm_pyramid;  /* host-side view of a pyramid in a works
 #define DM_DEV_OUTPUT_OVERFLOW 2       /* more matches than the output capacity       */
 #define DM_DEV_TIMEOUT 4               /* a bounded wait inside a pyramid kernel gave up */
 
-/* Fill *cfg with the paper's parameters and DM_FP32. */
+/* Fill *cfg with the paper's parameters, DM_FP32 and compensated = 1. */
 void dm_config_default(dm_config* cfg);
 
 /* Create a context bound to CUDA device `device`.  Host allocation only. */

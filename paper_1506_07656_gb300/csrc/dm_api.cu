@@ -105,10 +105,11 @@ void match_layout(const DmGeom& g, int precision, MatchLayout* m) {
     m->bytes = o;
 }
 
-void fill_pyramid(dm_pyramid* p, const DmGeom& g, int precision, const DmPyrLayout& pl, char* base) {
+void fill_pyramid(dm_pyramid* p, const DmGeom& g, int precision, int compensated, const DmPyrLayout& pl, char* base) {
     memset(p, 0, sizeof(*p));
     p->g = g;
     p->precision = precision;
+    p->compensated = compensated;
     for (int l = 0; l <= g.L; l++) p->valid[l] = (const unsigned char*)(base + pl.valid[l]);
     for (int l = 0; l < g.L; l++) {
         p->pooled[l] = (const float*)(base + pl.pooled[l]);
@@ -127,7 +128,7 @@ dm_status run_descriptors(dm_ctx* c, const float* img, int W, int H, float* desc
 
 dm_status run_pyramid(dm_ctx* c, const DmGeom& g, const float* d1, const float* d2, char* base, const DmPyrLayout& pl,
                       dm_pyramid* py, int* d_status, cudaStream_t st) {
-    fill_pyramid(py, g, c->cfg.precision, pl, base);
+    fill_pyramid(py, g, c->cfg.precision, c->cfg.compensated, pl, base);
     cudaError_t e;
     if ((e = cudaMemsetAsync(d_status, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(c, e, "clear status");
     if (c->cfg.precision != DM_FP32) {
@@ -169,6 +170,7 @@ int dm_make_geom(int W1, int H1, int W2, int H2, DmGeom* g) {
     while (N < mx) { N *= 2; L++; }
     if (L < 1) return -1;
     if (L > DM_MAXL) return -2;
+    if (L > 14) return -2;   // fixed-point path scores: L + 1 terms below 2^28 each fit 32 bits
     g->L = L;
     g->P0x = (W1 - 3) / 4 + 1;
     g->P0y = (H1 - 3) / 4 + 1;
@@ -238,6 +240,7 @@ void dm_config_default(dm_config* cfg) {
     cfg->lambda = 1.4f;
     cfg->image_scale = 255.0f;
     cfg->precision = DM_FP32;
+    cfg->compensated = 1;
 }
 
 dm_status dm_create(const dm_config* cfg, int device, dm_ctx** out) {
@@ -249,6 +252,7 @@ dm_status dm_create(const dm_config* cfg, int device, dm_ctx** out) {
         !(c.nu2 <= 10.0f) || !(c.nu3 <= 10.0f) || !(c.mu >= 0.0f) || !(c.image_scale > 0.0f))
         return DM_EINVAL;
     if (c.precision != DM_FP32 && c.precision != DM_BF16 && c.precision != DM_FP8_E4M3) return DM_EINVAL;
+    if (c.compensated != 0 && c.compensated != 1) return DM_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return DM_EINVAL;
     dm_ctx* x = new dm_ctx();
@@ -449,7 +453,7 @@ dm_status dm_match(dm_ctx* ctx, const float* d_img1, int W1, int H1, const float
     if ((s = run_descriptors(ctx, d_img2, W2, H2, desc2, base + ml.tmp, st)) != DM_OK) return s;
     if (ev) cudaEventRecord(ev[1], st);
     dm_pyramid py;
-    fill_pyramid(&py, g, ctx->cfg.precision, ml.py, base + ml.pyr);
+    fill_pyramid(&py, g, ctx->cfg.precision, ctx->cfg.compensated, ml.py, base + ml.pyr);
     cudaError_t e;
     int* d_status = &reinterpret_cast<DmWsHeader*>(base + ml.bt.header)->pyr_status;
     if ((e = cudaMemsetAsync(d_status, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(ctx, e, "clear status");

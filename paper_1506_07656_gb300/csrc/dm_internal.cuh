@@ -171,6 +171,7 @@ size_t dm_desc_tmp_bytes(int W, int H);
 struct dm_pyramid {
     DmGeom g;
     int precision;
+    int compensated;              // child sums of Eq. 12: TwoSum-compensated (1) or plain (0)
     const unsigned char* valid[DM_MAXL + 1];
     const float* pooled[DM_MAXL];
     const unsigned char* amax[DM_MAXL];

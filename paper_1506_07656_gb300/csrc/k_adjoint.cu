@@ -20,26 +20,32 @@
 namespace {
 
 // Unrectified average of lattice patch p at level l >= 1, position (qx, qy),
-// exactly as the forward computes it; *n_out = number of existing children.
+// exactly as the forward computes it (child order, TwoSum-compensated when
+// `comp`); *n_out = number of existing children.
 __device__ float level_average(const DmGeom& g, int l, int p, int qx, int qy, const unsigned char* vprev,
-                               const float* prev, int* n_out) {
+                               const float* prev, bool comp, int* n_out) {
     const int mw = g.dw[l], mh = g.dh[l], pitch = g.pitch(l);
-    float s = 0.0f;
+    float s = 0.0f, c = 0.0f;
     int n = 0;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
-        int c = dm_child(g, l, p % g.Lx, p / g.Lx, i);
-        if (c < 0 || !vprev[c]) continue;
+        int ch = dm_child(g, l, p % g.Lx, p / g.Lx, i);
+        if (ch < 0 || !vprev[ch]) continue;
         n++;
         int ox = (i >= 2) ? 1 : -1, oy = (i & 1) ? 1 : -1;
         int rx = qx + ox, ry = qy + oy;
         float v = 0.0f;
-        if (rx >= 0 && ry >= 0 && rx < mw && ry < mh) v = prev[(long long)c * g.psize(l) + (long long)ry * pitch + rx];
-        s = __fadd_rn(s, v);
+        if (rx >= 0 && ry >= 0 && rx < mw && ry < mh) v = prev[(long long)ch * g.psize(l) + (long long)ry * pitch + rx];
+        const float t = __fadd_rn(s, v);
+        if (comp) {
+            const float bp = __fsub_rn(t, s);
+            c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp)));
+        }
+        s = t;
     }
     *n_out = n;
     if (n == 0) return 0.0f;
-    return __fdiv_rn(s, (float)n);
+    return __fdiv_rn(__fadd_rn(s, c), (float)n);
 }
 
 __device__ __forceinline__ float dpow(float x, float lam) {   // d(x^lam)/dx for x in [0, 1]
@@ -49,7 +55,7 @@ __device__ __forceinline__ float dpow(float x, float lam) {   // d(x^lam)/dx for
 // Top level: per existing patch, the first maximum of C_L, its value, and
 // dA_L = d(A^lam)/dA at that position (zero elsewhere).
 __global__ void k_adj_top(DmGeom g, const unsigned char* __restrict__ vL, const unsigned char* __restrict__ vprev,
-                          const float* __restrict__ top, const float* __restrict__ prev, float lam,
+                          const float* __restrict__ top, const float* __restrict__ prev, float lam, int comp,
                           float* __restrict__ dA, float* __restrict__ parts) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const int L = g.L;
@@ -65,7 +71,7 @@ __global__ void k_adj_top(DmGeom g, const unsigned char* __restrict__ vL, const 
         if (t[q] > best) { best = t[q]; qb = q; }
     parts[p] = best;
     int n;
-    const float a = level_average(g, L, p, qb % g.dw[L], qb / g.dw[L], vprev, prev, &n);
+    const float a = level_average(g, L, p, qb % g.dw[L], qb / g.dw[L], vprev, prev, comp != 0, &n);
     d[qb] = dpow(a, lam);
 }
 
@@ -124,7 +130,7 @@ __global__ void k_adj_pooled(DmGeom g, int l, const unsigned char* __restrict__ 
 // A the unrectified average at t.  Grid: (positions of domain m, patch).
 __global__ void k_adj_unpool(DmGeom g, int m, const unsigned char* __restrict__ vm, const unsigned char* __restrict__ vprev,
                              const float* __restrict__ prev, const float* __restrict__ dP,
-                             const unsigned char* __restrict__ amax, float lam, float* __restrict__ dA) {
+                             const unsigned char* __restrict__ amax, float lam, int comp, float* __restrict__ dA) {
     const int c = blockIdx.y;
     const int tw = g.dw[m], th = g.dh[m];
     const int pw = g.dw[m + 1], ph = g.dh[m + 1], pitch = g.pitch(m + 1);
@@ -146,7 +152,7 @@ __global__ void k_adj_unpool(DmGeom g, int m, const unsigned char* __restrict__ 
         }
         if (dsum != 0.0f) {
             int n;
-            const float a = level_average(g, m, c, tx, ty, vprev, prev, &n);
+            const float a = level_average(g, m, c, tx, ty, vprev, prev, comp != 0, &n);
             sum = __fmul_rn(dsum, dpow(a, lam));
         }
     }
@@ -320,7 +326,7 @@ cudaError_t dm_launch_loss_grad(const DmGeom& g, const dm_pyramid& py, const flo
     float* parts = reinterpret_cast<float*>(ws + gl.parts);
     long long launches = 0;
     k_adj_top<<<nb(g.npatch(L), 128), 128, 0, st>>>(g, py.valid[L], py.valid[L - 1], py.top, py.pooled[L - 1], lam,
-                                                    reinterpret_cast<float*>(ws + gl.dA[L]), parts);
+                                                    py.compensated, reinterpret_cast<float*>(ws + gl.dA[L]), parts);
     k_adj_loss<<<1, 256, 0, st>>>(parts, g.npatch(L), d_loss);
     launches += 2;
     if (!g1 || !g2) {   // loss only
@@ -337,7 +343,7 @@ cudaError_t dm_launch_loss_grad(const DmGeom& g, const dm_pyramid& py, const flo
             dim3 g2d(nb(g.dsize(l - 1), 128), g.npatch(l - 1));
             k_adj_unpool<<<g2d, 128, 0, st>>>(g, l - 1, py.valid[l - 1], py.valid[l - 2], py.pooled[l - 2],
                                               reinterpret_cast<const float*>(ws + gl.dP[l - 1]), py.amax[l - 1], lam,
-                                              reinterpret_cast<float*>(ws + gl.dA[l - 1]));
+                                              py.compensated, reinterpret_cast<float*>(ws + gl.dA[l - 1]));
             launches++;
         }
     }

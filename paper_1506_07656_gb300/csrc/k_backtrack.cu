@@ -11,18 +11,20 @@
 // Only a small fraction of all (patch, position) pairs is ever reached (the
 // merged frontier is typically 1-5% of a level's pooled map below the top), so
 // the frontier is kept sparse: one open-addressing table per level keyed by
-// (patch, position) with 64-bit slots (key+1) << 32 | score-bits, merged by
-// 64-bit atomicMax (scores are positive, so their IEEE bits order like the
-// values), plus a list of the slots taken, which is the next step's input.
+// (patch, position) with 64-bit slots (key+1) << 32 | score, merged by 64-bit
+// atomicMax, plus a list of the slots taken, which is the next step's input.
 // The active table size is derived on the device from the previous
 // frontier's size, so nothing waits for the host.
 //
-// Path scores are summed top-down in FP32 with one rounding per level.
-// Rounding is monotone, so max over arrivals then add equals add then max:
-// merging is exact and independent of arrival order.
+// Path scores are exact: each term (a map value in [0, 1]) is rounded to the
+// nearest multiple of 2^-28 and the terms are summed as unsigned 32-bit fixed
+// point (L + 1 < 16 terms, so no overflow).  The sum is exact, so merging by
+// maximum is independent of arrival order, and the fixed-point score orders
+// like its value in the 32-bit score field of a slot.  It is rounded to FP32
+// once, when a match is written.
 //
 // At the atomic level the tuples are reduced into two arrays of packed keys
-// (score-bits << 32 | ~index) with atomicMax:
+// (score << 32 | ~index) with atomicMax:
 //   BestAt(p)  per atomic patch (its own 4x4 cell of I), index = pixel of I';
 //   BestAt'(c) per 4x4 cell of I',                      index = patch*16 + offset.
 // A patch's best tuple is output iff it also wins its cell of I'.
@@ -31,6 +33,12 @@
 namespace {
 
 constexpr int BT_BLOCK = 256;
+
+// Path-score term: v in [0, 1] to unsigned fixed point, 28 fractional bits,
+// round to nearest even (v * 2^28 is exact in FP32).
+__device__ __forceinline__ unsigned int ps_term(float v) { return __float2uint_rn(__fmul_rn(v, 268435456.0f)); }
+// Fixed-point score to FP32, rounded once.
+__device__ __forceinline__ float ps_value(unsigned int s) { return __fmul_rn(__uint2float_rn(s), 0x1p-28f); }
 
 struct BtArgs {
     DmGeom g;
@@ -56,9 +64,8 @@ __device__ __forceinline__ unsigned int warp_agg_inc(unsigned int* ctr) {
     return base + __popc(mask & ((1u << lane) - 1u));
 }
 
-__device__ __forceinline__ void ht_insert(const BtArgs& a, int lvl, unsigned int cap, unsigned int key, float s) {
+__device__ __forceinline__ void ht_insert(const BtArgs& a, int lvl, unsigned int cap, unsigned int key, unsigned int sb) {
     unsigned long long* tab = a.table[lvl];
-    const unsigned int sb = __float_as_uint(s);
     const unsigned long long packed = ((unsigned long long)(key + 1u) << 32) | sb;
     unsigned int h = (unsigned int)(((unsigned long long)(key * 2654435761u) * cap) >> 32);
     for (unsigned int probe = 0; probe < cap; probe++) {
@@ -81,9 +88,9 @@ __device__ __forceinline__ void ht_insert(const BtArgs& a, int lvl, unsigned int
     atomicOr(&a.hdr->status, DM_DEV_FRONTIER_OVERFLOW);
 }
 
-__device__ __forceinline__ void leaf_update(const BtArgs& a, int c, int tx, int ty, float s) {
+__device__ __forceinline__ void leaf_update(const BtArgs& a, int c, int tx, int ty, unsigned int s) {
     const DmGeom& g = a.g;
-    const unsigned long long sb = (unsigned long long)__float_as_uint(s) << 32;
+    const unsigned long long sb = (unsigned long long)s << 32;
     unsigned int tidx = (unsigned int)(ty * g.W2 + tx);
     unsigned long long kp = sb | (0xffffffffu - tidx);
     if (__ldcg(a.bestP + c) < kp) atomicMax(a.bestP + c, kp);
@@ -97,7 +104,7 @@ __device__ __forceinline__ void leaf_update(const BtArgs& a, int c, int tx, int 
 // Children of tuple (l, p, q, s); returns the number of atomic arrivals.
 // The (up to 4) children's pooled values and argmax codes are loaded first,
 // all independent, so their memory latencies overlap; the merges follow.
-__device__ __forceinline__ int expand(const BtArgs& a, int l, unsigned int cap_next, int p, int qx, int qy, float s) {
+__device__ __forceinline__ int expand(const BtArgs& a, int l, unsigned int cap_next, int p, int qx, int qy, unsigned int s) {
     const DmGeom& g = a.g;
     const int mw = g.dw[l], mh = g.dh[l], pitch = g.pitch(l);    // pooled map P_{l-1} lives on domain l
     const int ix = p % g.Lx, iy = p / g.Lx;
@@ -125,7 +132,7 @@ __device__ __forceinline__ int expand(const BtArgs& a, int l, unsigned int cap_n
         if (cc[i] < 0) continue;
         const int rx = rxs[i], ry = rys[i];
         const int tx = 2 * rx + code[i] % 3 - 1, ty = 2 * ry + code[i] / 3 - 1;
-        const float s2 = __fadd_rn(s, val[i]);
+        const unsigned int s2 = s + ps_term(val[i]);
         if (l - 1 >= 1) {
             unsigned int key = (unsigned int)cc[i] * (unsigned int)g.dsize(l - 1) + (unsigned int)(ty * g.dw[l - 1] + tx);
             ht_insert(a, l - 1, cap_next, key, s2);
@@ -171,7 +178,7 @@ __global__ void k_bt_expand_top(BtArgs a) {
             int q = (int)(e % ds);
             if (a.valid[L][p]) {
                 if (q == 0) atomicAdd(&a.hdr->count[L], (unsigned int)ds);
-                arrivals += expand(a, L, cap_next, p, q % g.dw[L], q / g.dw[L], a.top[e]);
+                arrivals += expand(a, L, cap_next, p, q % g.dw[L], q / g.dw[L], ps_term(a.top[e]));
             }
         }
     }
@@ -190,7 +197,7 @@ __global__ void k_bt_expand(BtArgs a, int l) {
         if (i < n) {
             unsigned long long v = __ldcg(a.table[l] + a.list[l][i]);
             unsigned int key = (unsigned int)(v >> 32) - 1u;
-            float s = __uint_as_float((unsigned int)v);
+            const unsigned int s = (unsigned int)v;
             int p = (int)(key / ds);
             int t = (int)(key % ds);
             arrivals += expand(a, l, cap_next, p, t % g.dw[l], t / g.dw[l], s);
@@ -220,7 +227,7 @@ __global__ void __launch_bounds__(1024) k_reciprocal(BtArgs a, dm_match_t* __res
         int cell = (ty >> 2) * CW + (tx >> 2);
         unsigned long long kq = a.bestQ[cell];
         unsigned int qidx = 0xffffffffu - (unsigned int)kq;
-        s = __uint_as_float((unsigned int)(kp >> 32));
+        s = ps_value((unsigned int)(kp >> 32));
         return (kq >> 32) == (kp >> 32) && qidx == (unsigned int)p * 16u + (unsigned int)((ty & 3) * 4 + (tx & 3));
     };
 

@@ -5,14 +5,14 @@
 // and, below the top, the stored pooled map
 //   P_l(p, r) = (max over in-domain m of C_l(p, 2r + m))^lambda   + argmax code,
 // or at the top C_L(p, q) = (C_l(p, q))^lambda.
-// The children's sum is a plain FP32 sum in child order i = 0..3 (one
-// rounding per addition), then divided by n; pooling is on the unrectified
-// average and the power is applied to the pooled value (x -> x^lambda is
-// increasing on [0,1]).
+// The children's sum runs in child order i = 0..3, Knuth-TwoSum compensated
+// and rounded once (default) or plain (one rounding per addition), then is
+// divided by n; pooling is on the unrectified average and the power is
+// applied to the pooled value (x -> x^lambda is increasing on [0,1]).
 //
 // This pass streams the pooled maps of the level below (bandwidth) and does
 // a fixed amount of arithmetic per stored output (~4 averages of 4 values,
-// a 9-way max with argmax, one power).  A CTA owns one patch and a tile of
+// a 9-way max with argmax, one power): it is bound by instruction issue.  A CTA owns one patch and a tile of
 // 32 x 16 pooled outputs (two per thread): one thread stages the 4 child-map
 // windows it needs (72 x 33 floats each) in shared memory with 3-D TMA tensor
 // loads (rows of the pooled maps are padded to 16 floats and the window's
@@ -50,8 +50,26 @@ struct Kids {
     int n;
 };
 
+// Knuth TwoSum step of the compensated child sum.
+__device__ __forceinline__ void two_sum_add(float& s, float& comp, float v) {
+    const float t = __fadd_rn(s, v);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
+    s = t;
+    comp = __fadd_rn(comp, err);
+}
+
+// Child sum step: compensated or plain.  The first existing child starts the
+// sum (0 + v = v exactly, the same as starting from zero).
+template <bool COMP>
+__device__ __forceinline__ void child_add(float& s, float& comp, float v) {
+    if (COMP) two_sum_add(s, comp, v);
+    else s = __fadd_rn(s, v);
+}
+
+template <bool COMP>
 __device__ __forceinline__ float child_mean(const Kids& k, int qx, int qy, int mw, int mh, int pitch) {
-    float s = 0.0f;
+    float s = 0.0f, comp = 0.0f;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         if (k.base[i] == nullptr) continue;
@@ -59,9 +77,9 @@ __device__ __forceinline__ float child_mean(const Kids& k, int qx, int qy, int m
         int rx = qx + ox, ry = qy + oy;
         float v = 0.0f;
         if (rx >= 0 && ry >= 0 && rx < mw && ry < mh) v = __ldg(k.base[i] + (long long)ry * pitch + rx);
-        s = __fadd_rn(s, v);
+        child_add<COMP>(s, comp, v);
     }
-    return __fdiv_rn(s, (float)k.n);
+    return __fdiv_rn(__fadd_rn(s, comp), (float)k.n);
 }
 
 
@@ -100,7 +118,7 @@ __device__ __forceinline__ float div_n(float x, int n) {
 
 // Averages at staged row ay, columns ax .. ax+3 of child 0's frame, from the
 // four child windows: child i contributes kid[i][ay][ax + ox_i + 3].
-template <bool ALL4>
+template <bool COMP, bool ALL4>
 __device__ __forceinline__ float4 avg4(const float* kid, int ay, int ax, const int* ci, int n) {
     // children with ox = -1 (i = 0, 1) read columns ax+2 .. ax+5 (8-byte aligned),
     // children with ox = +1 (i = 2, 3) read columns ax+4 .. ax+7 (16-byte aligned)
@@ -121,32 +139,38 @@ __device__ __forceinline__ float4 avg4(const float* kid, int ay, int ax, const i
     float r[4];
 #pragma unroll
     for (int c = 0; c < 4; c++) {
+        float s = 0.0f, comp = 0.0f;
         if (ALL4) {
-            r[c] = __fmul_rn(__fadd_rn(__fadd_rn(__fadd_rn(v[0][c], v[1][c]), v[2][c]), v[3][c]), 0.25f);
+            s = v[0][c];
+            child_add<COMP>(s, comp, v[1][c]);
+            child_add<COMP>(s, comp, v[2][c]);
+            child_add<COMP>(s, comp, v[3][c]);
+            r[c] = __fmul_rn(COMP ? __fadd_rn(s, comp) : s, 0.25f);
         } else {
-            float s = 0.0f;
 #pragma unroll
             for (int i = 0; i < 4; i++)
-                if (ci[i] >= 0) s = __fadd_rn(s, v[i][c]);
-            r[c] = div_n(s, n);
+                if (ci[i] >= 0) child_add<COMP>(s, comp, v[i][c]);
+            r[c] = div_n(COMP ? __fadd_rn(s, comp) : s, n);
         }
     }
     return make_float4(r[0], r[1], r[2], r[3]);
 }
 
+template <bool COMP>
 __device__ __forceinline__ float avg1(const float* kid, int ay, int ax, const int* ci, int n) {
-    float s = 0.0f;
+    float s = 0.0f, comp = 0.0f;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         if (ci[i] < 0) continue;
-        s = __fadd_rn(s, kid[i * KIDF + ay * KW + ax + ((i >= 2) ? 1 : -1) + 3]);
+        child_add<COMP>(s, comp, kid[i * KIDF + ay * KW + ax + ((i >= 2) ? 1 : -1) + 3]);
     }
-    return div_n(s, n);
+    return div_n(COMP ? __fadd_rn(s, comp) : s, n);
 }
 
 // Level l in [1, L-1]: grid (patch, tile).  `tmap` maps the pooled maps of
 // level l-1 as a 3-D array (columns dw[l], rows dh[l], patches) with a
 // 72 x 33 x 1 box.
+template <bool COMP>
 __global__ void __launch_bounds__(LEVEL_THREADS) k_level_pool_tiled(DmGeom g, int l, const __grid_constant__ CUtensorMap tmap,
                                                                     const unsigned char* __restrict__ vprev,
                                                                     const unsigned char* __restrict__ vcur,
@@ -219,10 +243,10 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_pool_tiled(DmGeom g, in
     constexpr int G4 = (AW - 1) / 4;                 // 16 groups of 4 columns, then column 64
     for (int e = tid; e < AH * G4; e += LEVEL_THREADS) {
         const int ay = e / G4, ax = 4 * (e - ay * G4);
-        const float4 a = (n == 4) ? avg4<true>(kid, ay, ax, ci, n) : avg4<false>(kid, ay, ax, ci, n);
+        const float4 a = (n == 4) ? avg4<COMP, true>(kid, ay, ax, ci, n) : avg4<COMP, false>(kid, ay, ax, ci, n);
         *reinterpret_cast<float4*>(&avg[ay][ax]) = a;
     }
-    for (int ay = tid; ay < AH; ay += LEVEL_THREADS) avg[ay][AW - 1] = avg1(kid, ay, AW - 1, ci, n);
+    for (int ay = tid; ay < AH; ay += LEVEL_THREADS) avg[ay][AW - 1] = avg1<COMP>(kid, ay, AW - 1, ci, n);
     __syncthreads();
     // 3x3 / 2 max-pool over in-domain averages, first strict maximum, power
     const int rx = rx0 + lane;
@@ -254,6 +278,7 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_pool_tiled(DmGeom g, in
 }
 
 // Top level L: C_L = (mean of children)^lambda over the domain of level L.
+template <bool COMP>
 __global__ void k_level_top(DmGeom g, int l, const unsigned char* __restrict__ vprev,
                             const unsigned char* __restrict__ vcur, const float* __restrict__ prev,
                             float* __restrict__ top, float lam) {
@@ -264,7 +289,7 @@ __global__ void k_level_top(DmGeom g, int l, const unsigned char* __restrict__ v
     if (q >= mw * mh) return;
     Kids k;
     load_kids(g, l, p, vprev, prev, k);
-    float a = child_mean(k, q % mw, q / mw, mw, mh, g.pitch(l));
+    float a = child_mean<COMP>(k, q % mw, q / mw, mw, mh, g.pitch(l));
     top[(long long)p * mw * mh + q] = dm_powf(a, lam);
 }
 
@@ -287,14 +312,14 @@ cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& py, float lam, i
                 return cudaErrorNotSupported;
             int tiles = ((g.dw[l + 1] + TW - 1) / TW) * ((g.dh[l + 1] + TH - 1) / TH);
             dim3 grid(np, tiles);
-            k_level_pool_tiled<<<grid, LEVEL_THREADS, 0, st>>>(g, l, tm, py.valid[l - 1], py.valid[l],
-                                                         const_cast<float*>(py.pooled[l]),
-                                                         const_cast<unsigned char*>(py.amax[l]), lam, status);
+            auto kern = py.compensated ? k_level_pool_tiled<true> : k_level_pool_tiled<false>;
+            kern<<<grid, LEVEL_THREADS, 0, st>>>(g, l, tm, py.valid[l - 1], py.valid[l], const_cast<float*>(py.pooled[l]),
+                                                 const_cast<unsigned char*>(py.amax[l]), lam, status);
         } else {
             int n = g.dw[l] * g.dh[l];
             dim3 grid((n + B - 1) / B, np);
-            k_level_top<<<grid, B, 0, st>>>(g, l, py.valid[l - 1], py.valid[l], py.pooled[l - 1],
-                                             const_cast<float*>(py.top), lam);
+            auto kern = py.compensated ? k_level_top<true> : k_level_top<false>;
+            kern<<<grid, B, 0, st>>>(g, l, py.valid[l - 1], py.valid[l], py.pooled[l - 1], const_cast<float*>(py.top), lam);
         }
     }
     dm_count_launches(1 + 2 * g.L);

@@ -28,7 +28,8 @@ MAXL = 30
 
 class DmConfig(C.Structure):
     _fields_ = [("nu1", C.c_float), ("nu2", C.c_float), ("nu3", C.c_float), ("slope", C.c_float),
-                ("mu", C.c_float), ("lambda_", C.c_float), ("image_scale", C.c_float), ("precision", C.c_int)]
+                ("mu", C.c_float), ("lambda_", C.c_float), ("image_scale", C.c_float), ("precision", C.c_int),
+                ("compensated", C.c_int)]
 
 
 class DmMatch(C.Structure):
@@ -316,7 +317,10 @@ class Context:
         self.torch = torch
         cfg = dm_config_default()
         for k, v in params.items():
-            setattr(cfg, "lambda_" if k in ("lam", "lambda") else k, float(v))
+            if k == "compensated":
+                cfg.compensated = int(bool(v))
+            else:
+                setattr(cfg, "lambda_" if k in ("lam", "lambda") else k, float(v))
         cfg.precision = precision
         self.cfg = cfg
         self.device = device

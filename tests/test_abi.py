@@ -82,3 +82,4 @@ def test_config_defaults_are_the_papers(lib):
     assert abs(c.slope - vals["slope"]) < 1e-6
     assert (c.nu1, c.nu2, c.nu3) == (vals["nu1"], vals["nu2"], vals["nu3"])
     assert c.precision == dm.DM_FP32
+    assert c.compensated == 1

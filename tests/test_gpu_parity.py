@@ -36,6 +36,15 @@ def ctx(torch_cuda):
     c.close()
 
 
+@pytest.fixture(scope="module")
+def ctx_plain(torch_cuda, ctx):
+    """FP32 path with plain (uncompensated) child sums."""
+    from paper_1506_07656_gb300 import dm
+    c = dm.Context(dm.DM_FP32, compensated=0)
+    yield c
+    c.close()
+
+
 def _dev(torch, a, dtype=None):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype or torch.float32, device="cuda")
 
@@ -119,13 +128,15 @@ def test_descriptors_bit_exact(torch_cuda, ctx, oracle_mod, case):
         np.testing.assert_array_equal(got, want)
 
 
+@pytest.mark.parametrize("compensated", [True, False])
 @pytest.mark.parametrize("case", CASES)
-def test_pyramid_and_matches_bit_exact(torch_cuda, ctx, oracle_mod, case):
+def test_pyramid_and_matches_bit_exact(torch_cuda, ctx, ctx_plain, oracle_mod, case, compensated):
     W1, H1, W2, H2 = case[:4]
     img1, img2 = _pair(*case)
     d1 = oracle_mod.descriptors(img1, "f32")
     d2 = oracle_mod.descriptors(img2, "f32")
-    pyr = oracle_mod.pyramid(d1, d2, "f32")
+    pyr = oracle_mod.pyramid(d1, d2, "f32", compensated=compensated)
+    ctx = ctx if compensated else ctx_plain
     h, ws, levels = _gpu_pyramid(torch_cuda, ctx, d1, d2)
     try:
         _compare_pyramids(pyr, levels)
