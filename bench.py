@@ -43,6 +43,8 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (CUDA graph) measurement")
     ap.add_argument("--batch-replays", type=int, default=3)
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the default launch shapes instead of autotuning them first")
     return ap.parse_args()
 
 
@@ -200,6 +202,7 @@ def _measure(dm, torch, dist, ctx, pair, a, world, local, stream):
     d1 = torch.from_numpy(pair.img1).cuda()
     d2 = torch.from_numpy(pair.img2).cuda()
     ws = ctx.workspace("match", W, H, W, H)
+    tuned = dm.dm_autotune(ctx.ctx, d1, d2, ws) if a.autotune else dm.dm_tuned_config(ctx.ctx, W, H, W, H)
     geo = dm.dm_geometry(W, H, W, H)
     n0 = geo["n_patch0"]
     out = torch.empty((n0, 5), dtype=torch.float32, device="cuda")
@@ -245,7 +248,7 @@ def _measure(dm, torch, dist, ctx, pair, a, world, local, stream):
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     return dict(ms=ms_max, value=world * a.steps / (ms_max / 1e3), stages={k: v / max(ncalls, 1) for k, v in stages.items()},
                 launches=launches, e2e=world * a.steps / float(te.item()), status=status, reached=reached,
-                matches=n_matches, clocks=clk.summary(), geo=geo)
+                matches=n_matches, clocks=clk.summary(), geo=geo, tuned=tuned)
 
 
 BATCH_SIZES = [(320, 240), (640, 480), (1024, 436), (1242, 375)]
@@ -266,6 +269,11 @@ def _measure_batch(dm, torch, ctx, a, rank):
                       torch.zeros(1, dtype=torch.int32, device="cuda")))
     pairs = dm.make_pairs(items)
     ws = torch.empty(dm.dm_batch_workspace_bytes(ctx.ctx, pairs), dtype=torch.uint8, device="cuda")
+    # autotune the launch shapes once per size, on the first pair of that size (before capture)
+    tuned = {}
+    for k in range(4):
+        W, H = BATCH_SIZES[k]
+        tuned[f"{W}x{H}"] = dm.dm_autotune(ctx.ctx, items[k][0], items[k][1], ws)
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(side):
@@ -287,7 +295,8 @@ def _measure_batch(dm, torch, ctx, a, rank):
     del graph, ws
     return {"pairs": 48, "sizes": [f"{w}x{h}" for w, h in BATCH_SIZES], "per_size": 12,
             "pairs_per_s": 48 / (ms / 1e3), "ms_per_batch": ms, "replays": a.batch_replays,
-            "graph": "one CUDA graph of dm_match_batch (all 48 pairs), replayed", "matches": n_match}
+            "graph": "one CUDA graph of dm_match_batch (all 48 pairs), replayed", "matches": n_match,
+            "autotuned": tuned}
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
@@ -397,7 +406,8 @@ def run_ours(a):
             paths[pn] = {"pairs_per_s": rr["value"], "ms_per_step": rr["ms"] / a.steps, "stages_ms": rr["stages"],
                          "e2e_pairs_per_s": rr["e2e"], "level0": {"achieved": c2["achieved"], "frac": c2["frac"],
                                                                  "bound": c2["bound"]},
-                         "levels_hbm_frac": l2["frac"], "matches": rr["matches"], "device_status": rr["status"]}
+                         "levels_hbm_frac": l2["frac"], "matches": rr["matches"], "device_status": rr["status"],
+                         "launch_shapes": rr["tuned"]}
         line = {
             "metric": METRIC, "value": r["value"], "unit": "pairs/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": r["ms"] / a.steps, "higher_is_better": True, "scaling": "weak",
@@ -408,7 +418,7 @@ def run_ours(a):
                                    f"pyramid and backtracking in FP32",
                        "width": W, "height": H, "precision": head, "L": geo["L"], "atomic_patches": geo["n_patch0"],
                        "l2": "working set ~21 GB per pair >> 126 MB L2; no flush needed",
-                       "matches": r["matches"], "device_status": r["status"],
+                       "matches": r["matches"], "device_status": r["status"], "launch_shapes": r["tuned"],
                        "merged_tuples_per_level": r["reached"]},
             "roofline": dominant,
             "rooflines": {"level0": corr, "levels": lev},

@@ -6,7 +6,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <array>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -21,7 +24,18 @@ struct dm_ctx {
     std::vector<cudaEvent_t> ev;
     int t_max = 0, t_count = 0;
     long long t_launch0 = 0;
+    // autotuner results per pair size (W1, H1, W2, H2)
+    std::mutex tune_mu;
+    std::map<std::array<int, 4>, DmTune> tuned;
 };
+
+namespace {
+DmTune tune_for(dm_ctx* c, const DmGeom& g) {
+    std::lock_guard<std::mutex> lk(c->tune_mu);
+    auto it = c->tuned.find({g.W1, g.H1, g.W2, g.H2});
+    return it == c->tuned.end() ? DM_TUNE_DEFAULT : it->second;
+}
+}  // namespace
 
 static std::atomic<long long> g_launches{0};
 void dm_count_launches(long long n) { g_launches += n; }
@@ -105,11 +119,13 @@ void match_layout(const DmGeom& g, int precision, MatchLayout* m) {
     m->bytes = o;
 }
 
-void fill_pyramid(dm_pyramid* p, const DmGeom& g, int precision, int compensated, const DmPyrLayout& pl, char* base) {
+void fill_pyramid(dm_pyramid* p, const DmGeom& g, int precision, int compensated, const DmTune& tune, const DmPyrLayout& pl,
+                  char* base) {
     memset(p, 0, sizeof(*p));
     p->g = g;
     p->precision = precision;
     p->compensated = compensated;
+    p->tune = tune;
     for (int l = 0; l <= g.L; l++) p->valid[l] = (const unsigned char*)(base + pl.valid[l]);
     for (int l = 0; l < g.L; l++) {
         p->pooled[l] = (const float*)(base + pl.pooled[l]);
@@ -128,12 +144,13 @@ dm_status run_descriptors(dm_ctx* c, const float* img, int W, int H, float* desc
 
 dm_status run_pyramid(dm_ctx* c, const DmGeom& g, const float* d1, const float* d2, char* base, const DmPyrLayout& pl,
                       dm_pyramid* py, int* d_status, cudaStream_t st) {
-    fill_pyramid(py, g, c->cfg.precision, c->cfg.compensated, pl, base);
+    fill_pyramid(py, g, c->cfg.precision, c->cfg.compensated, tune_for(c, g), pl, base);
     cudaError_t e;
     if ((e = cudaMemsetAsync(d_status, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(c, e, "clear status");
     if (c->cfg.precision != DM_FP32) {
         e = dm_launch_corr0_tc(g, c->cfg.precision, d1, d2, c->cfg.lambda, base + pl.a16, d_status,
-                               const_cast<float*>(py->pooled[0]), const_cast<unsigned char*>(py->amax[0]), st);
+                               const_cast<float*>(py->pooled[0]), const_cast<unsigned char*>(py->amax[0]),
+                               py->tune.m_chunk, st);
     } else {
         e = dm_launch_corr0_f32(g, d1, d2, c->cfg.lambda, const_cast<float*>(py->pooled[0]),
                                 const_cast<unsigned char*>(py->amax[0]), st);
@@ -453,13 +470,14 @@ dm_status dm_match(dm_ctx* ctx, const float* d_img1, int W1, int H1, const float
     if ((s = run_descriptors(ctx, d_img2, W2, H2, desc2, base + ml.tmp, st)) != DM_OK) return s;
     if (ev) cudaEventRecord(ev[1], st);
     dm_pyramid py;
-    fill_pyramid(&py, g, ctx->cfg.precision, ctx->cfg.compensated, ml.py, base + ml.pyr);
+    fill_pyramid(&py, g, ctx->cfg.precision, ctx->cfg.compensated, tune_for(ctx, g), ml.py, base + ml.pyr);
     cudaError_t e;
     int* d_status = &reinterpret_cast<DmWsHeader*>(base + ml.bt.header)->pyr_status;
     if ((e = cudaMemsetAsync(d_status, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(ctx, e, "clear status");
     if (ctx->cfg.precision != DM_FP32)
         e = dm_launch_corr0_tc(g, ctx->cfg.precision, desc1, desc2, ctx->cfg.lambda, base + ml.pyr + ml.py.a16,
-                               d_status, const_cast<float*>(py.pooled[0]), const_cast<unsigned char*>(py.amax[0]), st);
+                               d_status, const_cast<float*>(py.pooled[0]), const_cast<unsigned char*>(py.amax[0]),
+                               py.tune.m_chunk, st);
     else
         e = dm_launch_corr0_f32(g, desc1, desc2, ctx->cfg.lambda, const_cast<float*>(py.pooled[0]),
                                 const_cast<unsigned char*>(py.amax[0]), st);
@@ -574,6 +592,131 @@ dm_status dm_match_batch(dm_ctx* ctx, int n, const dm_pair* pairs, void* d_ws, s
                                q.d_count, stream);
         if (s != DM_OK) return s;
     }
+    return DM_OK;
+}
+
+// Autotuner.  Each stage's candidates run back to back on the caller's pair,
+// each timed twice with CUDA events (the faster run counts); a candidate
+// replaces the current choice only if it is at least 2% faster, so timing
+// noise keeps the defaults.
+dm_status dm_autotune(dm_ctx* ctx, const float* d_img1, int W1, int H1, const float* d_img2, int W2, int H2, void* d_ws,
+                      size_t ws_bytes, int* chosen, void* stream) {
+    if (!ctx) return DM_EINVAL;
+    if (!d_img1 || !d_img2 || !d_ws) return fail(ctx, DM_EINVAL, "dm_autotune: bad arguments");
+    if (!aligned256(d_ws)) return fail(ctx, DM_EINVAL, "workspace must be 256-byte aligned");
+    DmGeom g;
+    dm_status s = check_geom(ctx, W1, H1, W2, H2, &g);
+    if (s != DM_OK) return s;
+    MatchLayout ml;
+    match_layout(g, ctx->cfg.precision, &ml);
+    if (ws_bytes < ml.bytes) return fail(ctx, DM_ENOMEM, "match workspace %zu < %zu bytes", ws_bytes, ml.bytes);
+    DevGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    char* base = (char*)d_ws;
+    float* desc1 = (float*)(base + ml.desc1);
+    float* desc2 = (float*)(base + ml.desc2);
+    if ((s = run_descriptors(ctx, d_img1, W1, H1, desc1, base + ml.tmp, st)) != DM_OK) return s;
+    if ((s = run_descriptors(ctx, d_img2, W2, H2, desc2, base + ml.tmp, st)) != DM_OK) return s;
+    DmTune best = DM_TUNE_DEFAULT;
+    dm_pyramid py;
+    fill_pyramid(&py, g, ctx->cfg.precision, ctx->cfg.compensated, best, ml.py, base + ml.pyr);
+    int* d_status = &reinterpret_cast<DmWsHeader*>(base + ml.bt.header)->pyr_status;
+    dm_match_t* dout = (dm_match_t*)(base + ml.out);
+    int* dcnt = (int*)(base + ml.count);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(ctx, cudaGetLastError(), "dm_autotune: events");
+    }
+    cudaError_t err = cudaSuccess;
+    // time one run of `stage` (best of two), in ms; < 0 on a CUDA error
+    auto timed = [&](auto&& stage) -> float {
+        float bestms = -1.0f;
+        for (int r = 0; r < 2; r++) {
+            cudaEventRecord(e0, st);
+            cudaError_t e = stage();
+            cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) { err = e; return -1.0f; }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (bestms < 0.0f || ms < bestms) bestms = ms;
+        }
+        return bestms;
+    };
+    auto pick = [](float cand, float& cur) { if (cand >= 0.0f && cand < 0.98f * cur) { cur = cand; return true; } return false; };
+    cudaMemsetAsync(d_status, 0, sizeof(int), st);
+    // level 0: M-tiles per work unit (tensor-core forms only)
+    auto level0 = [&]() -> cudaError_t {
+        if (ctx->cfg.precision == DM_FP32)
+            return dm_launch_corr0_f32(g, desc1, desc2, ctx->cfg.lambda, const_cast<float*>(py.pooled[0]),
+                                       const_cast<unsigned char*>(py.amax[0]), st);
+        return dm_launch_corr0_tc(g, ctx->cfg.precision, desc1, desc2, ctx->cfg.lambda, base + ml.pyr + ml.py.a16, d_status,
+                                  const_cast<float*>(py.pooled[0]), const_cast<unsigned char*>(py.amax[0]),
+                                  py.tune.m_chunk, st);
+    };
+    float cur = timed(level0);
+    if (ctx->cfg.precision != DM_FP32) {
+        const int n_mtiles = (g.npatch(0) + 127) / 128;
+        const int splits[] = {1, 2, 3, 4, 6, 8};
+        for (int k : splits) {
+            const int mc = (n_mtiles + k - 1) / k;
+            if (mc == DM_TUNE_DEFAULT.m_chunk) continue;
+            py.tune.m_chunk = mc;
+            if (pick(timed(level0), cur)) best.m_chunk = mc;
+        }
+        py.tune.m_chunk = best.m_chunk;
+    }
+    // levels: pooled rows per CTA tile
+    auto levels = [&]() { return dm_launch_levels(g, py, ctx->cfg.lambda, d_status, st); };
+    cur = timed(levels);
+    py.tune.level_th = 8;
+    if (pick(timed(levels), cur)) best.level_th = 8;
+    py.tune.level_th = best.level_th;
+    // backtracking: CTAs per SM of the expansion kernels
+    auto backtrack = [&]() { return dm_launch_backtrack(g, py, ml.bt, base, dout, g.npatch(0), dcnt, st); };
+    cur = timed(backtrack);
+    const int mults[] = {2, 4, 16, 32};
+    for (int m : mults) {
+        py.tune.bt_mult = m;
+        if (pick(timed(backtrack), cur)) best.bt_mult = m;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return cuda_fail(ctx, err, "dm_autotune");
+    DmWsHeader h;
+    if ((err = cudaMemcpy(&h, base + ml.bt.header, sizeof(h), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(ctx, err, "dm_autotune: status");
+    if (h.pyr_status || h.status) return fail(ctx, DM_ETIMEOUT, "dm_autotune: device status %d / %d", h.pyr_status, h.status);
+    {
+        std::lock_guard<std::mutex> lk(ctx->tune_mu);
+        ctx->tuned[{W1, H1, W2, H2}] = best;
+    }
+    if (chosen) { chosen[0] = best.m_chunk; chosen[1] = best.level_th; chosen[2] = best.bt_mult; }
+    return DM_OK;
+}
+
+dm_status dm_tuned_config(dm_ctx* ctx, int W1, int H1, int W2, int H2, int* chosen) {
+    if (!ctx || !chosen) return DM_EINVAL;
+    DmGeom g;
+    dm_status s = check_geom(ctx, W1, H1, W2, H2, &g);
+    if (s != DM_OK) return s;
+    const DmTune t = tune_for(ctx, g);
+    chosen[0] = t.m_chunk;
+    chosen[1] = t.level_th;
+    chosen[2] = t.bt_mult;
+    return DM_OK;
+}
+
+dm_status dm_set_tuned_config(dm_ctx* ctx, int W1, int H1, int W2, int H2, const int* chosen) {
+    if (!ctx || !chosen) return DM_EINVAL;
+    if (chosen[0] < 1 || (chosen[1] != 8 && chosen[1] != 16) || chosen[2] < 1 || chosen[2] > 64)
+        return fail(ctx, DM_EINVAL, "dm_set_tuned_config: invalid launch shapes %d %d %d", chosen[0], chosen[1], chosen[2]);
+    DmGeom g;
+    dm_status s = check_geom(ctx, W1, H1, W2, H2, &g);
+    if (s != DM_OK) return s;
+    std::lock_guard<std::mutex> lk(ctx->tune_mu);
+    ctx->tuned[{W1, H1, W2, H2}] = DmTune{chosen[0], chosen[1], chosen[2]};
     return DM_OK;
 }
 

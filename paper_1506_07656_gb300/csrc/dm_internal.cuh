@@ -167,11 +167,23 @@ void dm_grad_layout(const DmGeom& g, DmGradLayout* o);
 void dm_bt_layout(const DmGeom& g, DmBtLayout* o);
 size_t dm_desc_tmp_bytes(int W, int H);
 
+// Launch shapes the autotuner chooses among (every choice computes identical
+// results): M-tiles of 128 patches per work unit of the tensor-core level-0
+// kernel, pooled rows per CTA tile of the level kernel (8 or 16), CTAs per SM
+// of the backtracking expansion kernels.
+struct DmTune {
+    int m_chunk;
+    int level_th;
+    int bt_mult;
+};
+constexpr DmTune DM_TUNE_DEFAULT = {110, 16, 8};
+
 // Pyramid handle (host side).
 struct dm_pyramid {
     DmGeom g;
     int precision;
     int compensated;              // child sums of Eq. 12: TwoSum-compensated (1) or plain (0)
+    DmTune tune;                  // launch shapes for this pair's size
     const unsigned char* valid[DM_MAXL + 1];
     const float* pooled[DM_MAXL];
     const unsigned char* amax[DM_MAXL];
@@ -213,7 +225,7 @@ cudaError_t dm_launch_corr0_f32(const DmGeom& g, const float* d1, const float* d
 // tcgen05 level-0 correlation, precision DM_BF16 or DM_FP8_E4M3; abuf holds
 // dm_corr0_tc_a_bytes(g, precision) bytes of packed operands.
 cudaError_t dm_launch_corr0_tc(const DmGeom& g, int precision, const float* d1, const float* d2, float lam, void* abuf,
-                               void* status, float* pooled0, unsigned char* amax0, cudaStream_t st);
+                               void* status, float* pooled0, unsigned char* amax0, int m_chunk, cudaStream_t st);
 size_t dm_corr0_tc_a_bytes(const DmGeom& g, int precision);
 cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& p, float lam, int* status, cudaStream_t st);
 cudaError_t dm_launch_loss_grad(const DmGeom& g, const dm_pyramid& py, const float* d1, const float* d2, float lam,

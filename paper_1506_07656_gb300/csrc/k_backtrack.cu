@@ -317,7 +317,7 @@ cudaError_t dm_launch_backtrack(const DmGeom& g, const dm_pyramid& py, const DmB
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = nsm * 8;
+    const int grid = nsm * (py.tune.bt_mult > 0 ? py.tune.bt_mult : 8);
     const long long n_top = (long long)g.npatch(g.L) * g.dsize(g.L);
     for (int l = g.L; l >= 1; l--) {
         if (l - 1 >= 1) k_bt_prepare<<<grid, BT_BLOCK, 0, st>>>(a, l - 1, n_top);

@@ -59,7 +59,6 @@ constexpr int KD = 144;                       // 4 x 4 x 9
 constexpr int CX = 33, CY = 7;                // C0 positions per N-tile
 constexpr int BN = 240;                       // CX * CY = 231, padded to a multiple of 16
 constexpr int PX = 16, PY = 3;                // pooled outputs per N-tile
-constexpr int M_CHUNK = 110;                  // M-tiles per work unit
 constexpr int EPI_WARPS = 16;
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
 constexpr int THREADS = 64 + EPI_THREADS;
@@ -313,7 +312,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 k_corr0_tc(DmGeom g, const unsigned char* __restrict__ apack, const float* __restrict__ inv_sa,
            const unsigned int* __restrict__ bmax, const float* __restrict__ d2,
            float lam, const __grid_constant__ CUtensorMap tmap_f, const __grid_constant__ CUtensorMap tmap_c, int n_mtiles,
-           int* __restrict__ err) {
+           int m_chunk, int* __restrict__ err) {
     using F = Fmt<FMT>;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sB = smem + F::OFF_B;
@@ -352,14 +351,14 @@ k_corr0_tc(DmGeom g, const unsigned char* __restrict__ apack, const float* __res
     const int W2 = g.W2, H2 = g.H2, mw = g.dw[1], mh = g.dh[1];
     const int n0 = g.P0x * g.P0y;
     const int tiles_x = (mw + PX - 1) / PX, tiles_y = (mh + PY - 1) / PY;
-    const int mchunks = (n_mtiles + M_CHUNK - 1) / M_CHUNK;
+    const int mchunks = (n_mtiles + m_chunk - 1) / m_chunk;
     const int n_units = tiles_x * tiles_y * mchunks;
     uint32_t a_it = 0, acc_it = 0;
     const bool store_leader = (warp == 2 && lane == 0);
 
     for (int unit = blockIdx.x; unit < n_units; unit += gridDim.x) {
         const int ntile = unit / mchunks, mc = unit % mchunks;
-        const int m0 = mc * M_CHUNK, m1 = min(n_mtiles, m0 + M_CHUNK), nt = m1 - m0;
+        const int m0 = mc * m_chunk, m1 = min(n_mtiles, m0 + m_chunk), nt = m1 - m0;
         const int rx0 = (ntile % tiles_x) * PX, ry0 = (ntile / tiles_x) * PY;
         const int cx0 = 2 * rx0 - 1, cy0 = 2 * ry0 - 1;
 
@@ -482,7 +481,7 @@ bool make_map(CUtensorMap* m, void* base, CUtensorMapDataType dt, int esize, con
 template <int FMT>
 cudaError_t launch_tc(const DmGeom& g, const unsigned char* apack, const float* inv_sa, const unsigned int* bmax,
                       const float* d2, float lam,
-                      const CUtensorMap& mf, const CUtensorMap& mc, int n_mtiles, int* status, cudaStream_t st) {
+                      const CUtensorMap& mf, const CUtensorMap& mc, int n_mtiles, int m_chunk, int* status, cudaStream_t st) {
     using F = Fmt<FMT>;
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
@@ -494,9 +493,9 @@ cudaError_t launch_tc(const DmGeom& g, const unsigned char* apack, const float* 
         attr_set |= 1ull << dev;
     }
     const int tiles = ((g.dw[1] + PX - 1) / PX) * ((g.dh[1] + PY - 1) / PY);
-    const int units = tiles * ((n_mtiles + M_CHUNK - 1) / M_CHUNK);
+    const int units = tiles * ((n_mtiles + m_chunk - 1) / m_chunk);
     const int grid = units < nsm ? units : nsm;
-    k_corr0_tc<FMT><<<grid, THREADS, F::SMEM, st>>>(g, apack, inv_sa, bmax, d2, lam, mf, mc, n_mtiles, status);
+    k_corr0_tc<FMT><<<grid, THREADS, F::SMEM, st>>>(g, apack, inv_sa, bmax, d2, lam, mf, mc, n_mtiles, m_chunk, status);
     return cudaGetLastError();
 }
 
@@ -532,9 +531,10 @@ size_t dm_corr0_tc_a_bytes(const DmGeom& g, int precision) {
 }
 
 cudaError_t dm_launch_corr0_tc(const DmGeom& g, int precision, const float* d1, const float* d2, float lam, void* abuf,
-                               void* status, float* pooled0, unsigned char* amax0, cudaStream_t st) {
+                               void* status, float* pooled0, unsigned char* amax0, int m_chunk, cudaStream_t st) {
     const int n0 = g.npatch(0);
     const int n_mtiles = (n0 + BM - 1) / BM;
+    if (m_chunk < 1) m_chunk = 1;
     CUtensorMap mf, mc;
     if (!make_map(&mf, pooled0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g) ||
         !make_map(&mc, amax0, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, g))
@@ -550,12 +550,12 @@ cudaError_t dm_launch_corr0_tc(const DmGeom& g, int precision, const float* d1, 
         const long long blocks = (n2 / 4 + 255) / 256;
         k_absmax<<<(unsigned)(blocks < 1216 ? (blocks > 0 ? blocks : 1) : 1216), 256, 0, st>>>(d2, n2, bmax);
         k_pack_a8<<<(unsigned)((n_mtiles * BM + 127) / 128), 128, 0, st>>>(g, d1, apack, inv_sa, n_mtiles);
-        e = launch_tc<FMT_E4M3>(g, apack, inv_sa, bmax, d2, lam, mf, mc, n_mtiles, reinterpret_cast<int*>(status), st);
+        e = launch_tc<FMT_E4M3>(g, apack, inv_sa, bmax, d2, lam, mf, mc, n_mtiles, m_chunk, reinterpret_cast<int*>(status), st);
         dm_count_launches(3);
     } else {
         long long total = (long long)n_mtiles * BM * Fmt<FMT_BF16>::CHUNKS;
         k_pack_a<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(g, d1, reinterpret_cast<__nv_bfloat16*>(apack), n_mtiles);
-        e = launch_tc<FMT_BF16>(g, apack, nullptr, nullptr, d2, lam, mf, mc, n_mtiles, reinterpret_cast<int*>(status), st);
+        e = launch_tc<FMT_BF16>(g, apack, nullptr, nullptr, d2, lam, mf, mc, n_mtiles, m_chunk, reinterpret_cast<int*>(status), st);
         dm_count_launches(2);
     }
     return e;

@@ -101,13 +101,22 @@ __device__ __forceinline__ bool load_kids(const DmGeom& g, int l, int p, const u
     return k.n > 0;
 }
 
-constexpr int TW = 32, TH = 16;                // pooled outputs per CTA (lane, 2 x warp)
-constexpr int AW = 2 * TW + 1, AH = 2 * TH + 1;  // averages per CTA (65 x 33)
+constexpr int TW = 32;                           // pooled columns per CTA tile (one per lane)
+constexpr int AW = 2 * TW + 1;                   // average columns per CTA (65)
 constexpr int KW = 72;                           // staged child columns (TMA box width)
-constexpr int KIDF = 2400;                       // floats per staged window: 33 x 72 = 2376, padded to 128 B
 constexpr int AWP = 68;                          // padded row of the averages (16-byte aligned rows)
 constexpr int LEVEL_THREADS = 256;
-constexpr unsigned KID_BYTES = AH * KW * 4;      // bytes one TMA window load delivers
+
+// CTA tile of TW x TH pooled outputs (TH = 8 or 16, chosen by the autotuner):
+// AH rows of averages, child windows of KW x AH floats (KIDF with padding to
+// 128 bytes), KID_BYTES delivered by one TMA window load.
+template <int TH_>
+struct LevelTile {
+    static constexpr int TH = TH_;
+    static constexpr int AH = 2 * TH + 1;
+    static constexpr int KIDF = ((AH * KW + 31) / 32) * 32;
+    static constexpr unsigned KID_BYTES = AH * KW * 4;
+};
 constexpr long long LEVEL_WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 
 // x / n rounded once, for n in 1..4: multiplications by 1, 1/2, 1/4 are exact,
@@ -118,7 +127,7 @@ __device__ __forceinline__ float div_n(float x, int n) {
 
 // Averages at staged row ay, columns ax .. ax+3 of child 0's frame, from the
 // four child windows: child i contributes kid[i][ay][ax + ox_i + 3].
-template <bool COMP, bool ALL4>
+template <int KIDF, bool COMP, bool ALL4>
 __device__ __forceinline__ float4 avg4(const float* kid, int ay, int ax, const int* ci, int n) {
     // children with ox = -1 (i = 0, 1) read columns ax+2 .. ax+5 (8-byte aligned),
     // children with ox = +1 (i = 2, 3) read columns ax+4 .. ax+7 (16-byte aligned)
@@ -156,7 +165,7 @@ __device__ __forceinline__ float4 avg4(const float* kid, int ay, int ax, const i
     return make_float4(r[0], r[1], r[2], r[3]);
 }
 
-template <bool COMP>
+template <int KIDF, bool COMP>
 __device__ __forceinline__ float avg1(const float* kid, int ay, int ax, const int* ci, int n) {
     float s = 0.0f, comp = 0.0f;
 #pragma unroll
@@ -170,13 +179,15 @@ __device__ __forceinline__ float avg1(const float* kid, int ay, int ax, const in
 // Level l in [1, L-1]: grid (patch, tile).  `tmap` maps the pooled maps of
 // level l-1 as a 3-D array (columns dw[l], rows dh[l], patches) with a
 // 72 x 33 x 1 box.
-template <bool COMP>
+template <bool COMP, int TH>
 __global__ void __launch_bounds__(LEVEL_THREADS) k_level_pool_tiled(DmGeom g, int l, const __grid_constant__ CUtensorMap tmap,
                                                                     const unsigned char* __restrict__ vprev,
                                                                     const unsigned char* __restrict__ vcur,
                                                                     float* __restrict__ out,
                                                                     unsigned char* __restrict__ amax, float lam,
                                                                     int* __restrict__ err) {
+    using T = LevelTile<TH>;
+    constexpr int AH = T::AH, KIDF = T::KIDF;
     __shared__ __align__(128) float kid[4 * KIDF];
     __shared__ __align__(16) float avg[AH][AWP];
     __shared__ int kid_index[4];
@@ -211,7 +222,7 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_pool_tiled(DmGeom g, in
     }
     // stage: child i, window rows qy0 + oy_i + [0, AH), columns xa + [0, KW)
     if (tid == 0) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar_s), "r"(KID_BYTES * n) : "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar_s), "r"(T::KID_BYTES * n) : "memory");
         const uint32_t kid_s = (uint32_t)__cvta_generic_to_shared(kid);
 #pragma unroll
         for (int i = 0; i < 4; i++) {
@@ -243,17 +254,17 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_pool_tiled(DmGeom g, in
     constexpr int G4 = (AW - 1) / 4;                 // 16 groups of 4 columns, then column 64
     for (int e = tid; e < AH * G4; e += LEVEL_THREADS) {
         const int ay = e / G4, ax = 4 * (e - ay * G4);
-        const float4 a = (n == 4) ? avg4<COMP, true>(kid, ay, ax, ci, n) : avg4<COMP, false>(kid, ay, ax, ci, n);
+        const float4 a = (n == 4) ? avg4<KIDF, COMP, true>(kid, ay, ax, ci, n) : avg4<KIDF, COMP, false>(kid, ay, ax, ci, n);
         *reinterpret_cast<float4*>(&avg[ay][ax]) = a;
     }
-    for (int ay = tid; ay < AH; ay += LEVEL_THREADS) avg[ay][AW - 1] = avg1<COMP>(kid, ay, AW - 1, ci, n);
+    for (int ay = tid; ay < AH; ay += LEVEL_THREADS) avg[ay][AW - 1] = avg1<KIDF, COMP>(kid, ay, AW - 1, ci, n);
     __syncthreads();
     // 3x3 / 2 max-pool over in-domain averages, first strict maximum, power
     const int rx = rx0 + lane;
     if (rx >= ow) return;
     const bool interior = qx0 >= 0 && qy0 >= 0 && qx0 + AW <= mw && qy0 + AH <= mh;
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
+    for (int h = 0; h < TH / 8; h++) {
         const int ty = warp + 8 * h;
         const int ry = ry0 + ty;
         if (ry >= oh) break;
@@ -303,16 +314,18 @@ cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& py, float lam, i
         k_valid<<<(np + 255) / 256, 256, 0, st>>>(g, l, py.valid[l - 1], const_cast<unsigned char*>(py.valid[l]));
         if (l < g.L) {
             // pooled maps of level l-1: [npatch(l-1)][dh[l]][pitch(l)] floats
+            const int th = py.tune.level_th == 8 ? 8 : 16;
             CUtensorMap tm;
             const cuuint64_t dims[3] = {(cuuint64_t)g.dw[l], (cuuint64_t)g.dh[l], (cuuint64_t)g.npatch(l - 1)};
             const cuuint64_t strides[2] = {(cuuint64_t)g.pitch(l) * 4, (cuuint64_t)g.psize(l) * 4};
-            const cuuint32_t box[3] = {KW, AH, 1};
+            const cuuint32_t box[3] = {KW, (cuuint32_t)(2 * th + 1), 1};
             if (!dm_encode_tiled(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(py.pooled[l - 1]), dims,
                                  strides, box))
                 return cudaErrorNotSupported;
-            int tiles = ((g.dw[l + 1] + TW - 1) / TW) * ((g.dh[l + 1] + TH - 1) / TH);
+            int tiles = ((g.dw[l + 1] + TW - 1) / TW) * ((g.dh[l + 1] + th - 1) / th);
             dim3 grid(np, tiles);
-            auto kern = py.compensated ? k_level_pool_tiled<true> : k_level_pool_tiled<false>;
+            auto kern = th == 8 ? (py.compensated ? k_level_pool_tiled<true, 8> : k_level_pool_tiled<false, 8>)
+                                : (py.compensated ? k_level_pool_tiled<true, 16> : k_level_pool_tiled<false, 16>);
             kern<<<grid, LEVEL_THREADS, 0, st>>>(g, l, tm, py.valid[l - 1], py.valid[l], const_cast<float*>(py.pooled[l]),
                                                  const_cast<unsigned char*>(py.amax[l]), lam, status);
         } else {

@@ -71,6 +71,10 @@ _SIGS = {
     "dm_batch_workspace_bytes": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_size_t)]),
     "dm_match_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "dm_backtrack_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "dm_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                              C.c_size_t, C.POINTER(C.c_int), C.c_void_p]),
+    "dm_tuned_config": (C.c_int, [C.c_void_p] + [C.c_int] * 4 + [C.POINTER(C.c_int)]),
+    "dm_set_tuned_config": (C.c_int, [C.c_void_p] + [C.c_int] * 4 + [C.POINTER(C.c_int)]),
     "dm_timing_start": (C.c_int, [C.c_void_p, C.c_int]),
     "dm_timing_read": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
 }
@@ -293,6 +297,30 @@ def dm_backtrack_noalloc(ctx, pyr, d_out, d_count, stream=None):
 
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
+TUNE_KEYS = ("m_chunk", "level_tile_rows", "bt_ctas_per_sm")
+
+
+def dm_autotune(ctx, d_img1, d_img2, d_ws, stream=None) -> dict:
+    """Time the launch-shape candidates on this pair; keep the fastest for its sizes."""
+    H1, W1 = d_img1.shape
+    H2, W2 = d_img2.shape
+    out = (C.c_int * 3)()
+    st = load().dm_autotune(ctx, _dptr(d_img1), W1, H1, _dptr(d_img2), W2, H2, _dptr(d_ws),
+                            d_ws.numel() * d_ws.element_size(), out, _stream_ptr(stream))
+    _check(ctx, st, "dm_autotune")
+    return dict(zip(TUNE_KEYS, list(out)))
+
+
+def dm_tuned_config(ctx, W1, H1, W2, H2) -> dict:
+    out = (C.c_int * 3)()
+    _check(ctx, load().dm_tuned_config(ctx, W1, H1, W2, H2, out), "dm_tuned_config")
+    return dict(zip(TUNE_KEYS, list(out)))
+
+
+def dm_set_tuned_config(ctx, W1, H1, W2, H2, cfg: dict) -> None:
+    arr = (C.c_int * 3)(*[int(cfg[k]) for k in TUNE_KEYS])
+    _check(ctx, load().dm_set_tuned_config(ctx, W1, H1, W2, H2, arr), "dm_set_tuned_config")
+
 
 def dm_timing_start(ctx, max_calls: int) -> None:
     _check(ctx, load().dm_timing_start(ctx, max_calls), "dm_timing_start")
@@ -360,6 +388,16 @@ class Context:
         dm_match(self.ctx, i1, i2, ws, out, cnt, stream)
         n = int(cnt.item())
         return out[:n]
+
+    def autotune(self, img1, img2, stream=None) -> dict:
+        """Autotune the launch shapes for pairs of these images' sizes."""
+        torch = self.torch
+        dev = f"cuda:{self.device}"
+        i1 = torch.as_tensor(img1, dtype=torch.float32, device=dev).contiguous()
+        i2 = torch.as_tensor(img2, dtype=torch.float32, device=dev).contiguous()
+        H1, W1 = i1.shape
+        H2, W2 = i2.shape
+        return dm_autotune(self.ctx, i1, i2, self.workspace("match", W1, H1, W2, H2), stream)
 
     def status(self, W1, H1, W2, H2, kind="match"):
         L = dm_geometry(W1, H1, W2, H2)["L"]
