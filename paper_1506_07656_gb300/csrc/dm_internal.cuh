@@ -138,6 +138,7 @@ struct DmPyrLayout {
     size_t amax[DM_MAXL];         // u8 same shape
     size_t top;                   // f32 [npatch(L)][dh[L]][dw[L]]
     size_t a16;                   // packed patch operand tiles of the tensor-core forms (BF16, E4M3 + scales)
+    size_t kids;                  // int4 [npatch(1)]: existing children of each lattice patch (-1 absent), current level
     size_t bytes;
 };
 
@@ -184,6 +185,7 @@ struct dm_pyramid {
     int precision;
     int compensated;              // child sums of Eq. 12: TwoSum-compensated (1) or plain (0)
     DmTune tune;                  // launch shapes for this pair's size
+    int4* kids;                   // scratch: per-level child table of the level kernels
     const unsigned char* valid[DM_MAXL + 1];
     const float* pooled[DM_MAXL];
     const unsigned char* amax[DM_MAXL];

@@ -27,17 +27,22 @@
 
 namespace {
 
-// valid[l][p] = 1 iff some child exists (Eq. 7 with the boundary rule).
-__global__ void k_valid(DmGeom g, int l, const unsigned char* __restrict__ vprev, unsigned char* __restrict__ v) {
+// valid[l][p] = 1 iff some child exists (Eq. 7 with the boundary rule), and
+// kids[p] = the existing children (index into level l-1, -1 where absent).
+__global__ void k_valid(DmGeom g, int l, const unsigned char* __restrict__ vprev, unsigned char* __restrict__ v,
+                        int4* __restrict__ kids) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= g.Lx * g.Ly) return;
     int ix = p % g.Lx, iy = p / g.Lx;
+    int c[4];
     unsigned char any = 0;
     for (int i = 0; i < 4; i++) {
-        int c = dm_child(g, l, ix, iy, i);
-        if (c >= 0 && vprev[c]) any = 1;
+        c[i] = dm_child(g, l, ix, iy, i);
+        if (c[i] >= 0 && !vprev[c[i]]) c[i] = -1;
+        if (c[i] >= 0) any = 1;
     }
     v[p] = any;
+    kids[p] = make_int4(c[0], c[1], c[2], c[3]);
 }
 
 __global__ void k_fill_u8(unsigned char* p, int n, unsigned char val) {
@@ -181,8 +186,7 @@ __device__ __forceinline__ float avg1(const float* kid, int ay, int ax, const in
 // 72 x 33 x 1 box.
 template <bool COMP, int TH>
 __global__ void __launch_bounds__(LEVEL_THREADS) k_level_pool_tiled(DmGeom g, int l, const __grid_constant__ CUtensorMap tmap,
-                                                                    const unsigned char* __restrict__ vprev,
-                                                                    const unsigned char* __restrict__ vcur,
+                                                                    const int4* __restrict__ kids,
                                                                     float* __restrict__ out,
                                                                     unsigned char* __restrict__ amax, float lam,
                                                                     int* __restrict__ err) {
@@ -190,11 +194,14 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_pool_tiled(DmGeom g, in
     constexpr int AH = T::AH, KIDF = T::KIDF;
     __shared__ __align__(128) float kid[4 * KIDF];
     __shared__ __align__(16) float avg[AH][AWP];
-    __shared__ int kid_index[4];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int abort_s;
     const int p = blockIdx.x;
-    if (!vcur[p]) return;
+    // the patch's existing children (one broadcast load); none: the patch does not exist
+    const int4 kc = __ldg(kids + p);
+    const int ci[4] = {kc.x, kc.y, kc.z, kc.w};
+    const int n = (ci[0] >= 0) + (ci[1] >= 0) + (ci[2] >= 0) + (ci[3] >= 0);
+    if (n == 0) return;
     const int ow = g.dw[l + 1], oh = g.dh[l + 1], opitch = g.pitch(l + 1);
     const int mw = g.dw[l], mh = g.dh[l];
     const int tiles_x = (ow + TW - 1) / TW;
@@ -203,25 +210,11 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_pool_tiled(DmGeom g, in
     const int xa = 2 * rx0 - 4;                      // first staged child column (multiple of 4: 16-byte aligned)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t bar_s = (uint32_t)__cvta_generic_to_shared(&bar);
-    if (tid < 4) {
-        int c = dm_child(g, l, p % g.Lx, p / g.Lx, tid);
-        kid_index[tid] = (c >= 0 && vprev[c]) ? c : -1;
-    }
+    // stage: child i, window rows qy0 + oy_i + [0, AH), columns xa + [0, KW)
     if (tid == 0) {
         abort_s = 0;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar_s) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    int ci[4];
-    int n = 0;
-#pragma unroll
-    for (int i = 0; i < 4; i++) {
-        ci[i] = kid_index[i];
-        n += ci[i] >= 0;
-    }
-    // stage: child i, window rows qy0 + oy_i + [0, AH), columns xa + [0, KW)
-    if (tid == 0) {
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar_s), "r"(T::KID_BYTES * n) : "memory");
         const uint32_t kid_s = (uint32_t)__cvta_generic_to_shared(kid);
 #pragma unroll
@@ -234,6 +227,7 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_pool_tiled(DmGeom g, in
                          : "memory");
         }
     }
+    __syncthreads();                                 // barrier initialised
     {
         const long long t0 = clock64();
         uint32_t done = 0;
@@ -259,28 +253,48 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_pool_tiled(DmGeom g, in
     }
     for (int ay = tid; ay < AH; ay += LEVEL_THREADS) avg[ay][AW - 1] = avg1<KIDF, COMP>(kid, ay, AW - 1, ci, n);
     __syncthreads();
-    // 3x3 / 2 max-pool over in-domain averages, first strict maximum, power
+    // 3x3 / 2 max-pool over in-domain averages, first strict maximum, power.
+    // A thread owns R = TH/8 vertically adjacent outputs (rows R*warp ..), so
+    // the horizontal 3-maxima of the 2R+1 average rows it reads are formed once
+    // (a row shared by two outputs serves both); rows are then merged in scan
+    // order m_y = -1, 0, 1, which keeps the first strict maximum.
+    constexpr int R = TH / 8;
     const int rx = rx0 + lane;
     if (rx >= ow) return;
     const bool interior = qx0 >= 0 && qy0 >= 0 && qx0 + AW <= mw && qy0 + AH <= mh;
+    const int ty0 = R * warp;
+    float hv[2 * R + 1];
+    int hc[2 * R + 1];
 #pragma unroll
-    for (int h = 0; h < TH / 8; h++) {
-        const int ty = warp + 8 * h;
-        const int ry = ry0 + ty;
+    for (int k = 0; k < 2 * R + 1; k++) {
+        const int ay = 2 * ty0 + k;                  // average row; map row qy0 + ay
+        const int qy = qy0 + ay;
+        float best = -INFINITY;
+        int code = 0;
+        if (interior || (qy >= 0 && qy < mh)) {
+#pragma unroll
+            for (int mx = -1; mx <= 1; mx++) {
+                if (!interior) {
+                    const int qx = 2 * rx + mx;
+                    if (qx < 0 || qx >= mw) continue;
+                }
+                const float a = avg[ay][2 * lane + 1 + mx];
+                if (a > best) { best = a; code = mx + 1; }
+            }
+        }
+        hv[k] = best;
+        hc[k] = code;
+    }
+#pragma unroll
+    for (int j = 0; j < R; j++) {
+        const int ry = ry0 + ty0 + j;
         if (ry >= oh) break;
         float best = -INFINITY;
         int code = 4;
 #pragma unroll
-        for (int my = -1; my <= 1; my++) {
-#pragma unroll
-            for (int mx = -1; mx <= 1; mx++) {
-                if (!interior) {
-                    int qx = 2 * rx + mx, qy = 2 * ry + my;
-                    if (qx < 0 || qy < 0 || qx >= mw || qy >= mh) continue;
-                }
-                float a = avg[2 * ty + 1 + my][2 * lane + 1 + mx];
-                if (a > best) { best = a; code = (my + 1) * 3 + (mx + 1); }
-            }
+        for (int my = 0; my < 3; my++) {
+            const float v = hv[2 * j + my];
+            if (v > best) { best = v; code = my * 3 + hc[2 * j + my]; }
         }
         long long o = ((long long)p * oh + ry) * opitch + rx;
         out[o] = dm_powf(best, lam);
@@ -311,7 +325,7 @@ cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& py, float lam, i
     int n0 = g.npatch(0), np = g.npatch(1);
     k_fill_u8<<<(n0 + 255) / 256, 256, 0, st>>>(const_cast<unsigned char*>(py.valid[0]), n0, 1);
     for (int l = 1; l <= g.L; l++) {
-        k_valid<<<(np + 255) / 256, 256, 0, st>>>(g, l, py.valid[l - 1], const_cast<unsigned char*>(py.valid[l]));
+        k_valid<<<(np + 255) / 256, 256, 0, st>>>(g, l, py.valid[l - 1], const_cast<unsigned char*>(py.valid[l]), py.kids);
         if (l < g.L) {
             // pooled maps of level l-1: [npatch(l-1)][dh[l]][pitch(l)] floats
             const int th = py.tune.level_th == 8 ? 8 : 16;
@@ -326,7 +340,7 @@ cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& py, float lam, i
             dim3 grid(np, tiles);
             auto kern = th == 8 ? (py.compensated ? k_level_pool_tiled<true, 8> : k_level_pool_tiled<false, 8>)
                                 : (py.compensated ? k_level_pool_tiled<true, 16> : k_level_pool_tiled<false, 16>);
-            kern<<<grid, LEVEL_THREADS, 0, st>>>(g, l, tm, py.valid[l - 1], py.valid[l], const_cast<float*>(py.pooled[l]),
+            kern<<<grid, LEVEL_THREADS, 0, st>>>(g, l, tm, py.kids, const_cast<float*>(py.pooled[l]),
                                                  const_cast<unsigned char*>(py.amax[l]), lam, status);
         } else {
             int n = g.dw[l] * g.dh[l];
