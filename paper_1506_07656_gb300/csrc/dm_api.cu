@@ -132,7 +132,6 @@ void fill_pyramid(dm_pyramid* p, const DmGeom& g, int precision, int compensated
         p->amax[l] = (const unsigned char*)(base + pl.amax[l]);
     }
     p->top = (const float*)(base + pl.top);
-    p->kids = (int4*)(base + pl.kids);
 }
 
 dm_status run_descriptors(dm_ctx* c, const float* img, int W, int H, float* desc, char* tmp, cudaStream_t st) {
@@ -217,7 +216,6 @@ void dm_pyr_layout(const DmGeom& g, int precision, DmPyrLayout* o) {
     }
     o->top = off; off = dm_align(off + (size_t)g.npatch(g.L) * (size_t)g.dsize(g.L) * 4);
     if (precision != DM_FP32) { o->a16 = off; off = dm_align(off + dm_corr0_tc_a_bytes(g, precision)); }
-    o->kids = off; off = dm_align(off + (size_t)g.npatch(1) * sizeof(int4));
     o->bytes = off;
 }
 

@@ -138,7 +138,6 @@ struct DmPyrLayout {
     size_t amax[DM_MAXL];         // u8 same shape
     size_t top;                   // f32 [npatch(L)][dh[L]][dw[L]]
     size_t a16;                   // packed patch operand tiles of the tensor-core forms (BF16, E4M3 + scales)
-    size_t kids;                  // int4 [npatch(1)]: existing children of each lattice patch (-1 absent), current level
     size_t bytes;
 };
 
@@ -168,6 +167,11 @@ void dm_grad_layout(const DmGeom& g, DmGradLayout* o);
 void dm_bt_layout(const DmGeom& g, DmBtLayout* o);
 size_t dm_desc_tmp_bytes(int W, int H);
 
+// Suspend-time hint of the kernels' mbarrier waits: a waiting thread sleeps
+// until the phase completes (or this many ns pass) instead of spinning and
+// taking issue slots from the warps that do the work.
+constexpr unsigned WAIT_HINT_NS = 1000000u;
+
 // Launch shapes the autotuner chooses among (every choice computes identical
 // results): M-tiles of 128 patches per work unit of the tensor-core level-0
 // kernel, pooled rows per CTA tile of the level kernel (8 or 16), CTAs per SM
@@ -185,7 +189,6 @@ struct dm_pyramid {
     int precision;
     int compensated;              // child sums of Eq. 12: TwoSum-compensated (1) or plain (0)
     DmTune tune;                  // launch shapes for this pair's size
-    int4* kids;                   // scratch: per-level child table of the level kernels
     const unsigned char* valid[DM_MAXL + 1];
     const float* pooled[DM_MAXL];
     const unsigned char* amax[DM_MAXL];

@@ -112,8 +112,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     long long t0 = clock64();
     while (true) {
         uint32_t ok;
-        asm volatile("{.reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p;}"
-                     : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+        asm volatile("{.reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p;}"
+                     : "=r"(ok) : "r"(bar), "r"(parity), "n"(WAIT_HINT_NS) : "memory");
         if (ok) return true;
         if (*abort_flag) return false;
         if (clock64() - t0 > WAIT_CYCLES) {

@@ -10,39 +10,36 @@
 // divided by n; pooling is on the unrectified average and the power is
 // applied to the pooled value (x -> x^lambda is increasing on [0,1]).
 //
-// This pass streams the pooled maps of the level below (bandwidth) and does
-// a fixed amount of arithmetic per stored output (~4 averages of 4 values,
-// a 9-way max with argmax, one power): it is bound by instruction issue.  A CTA owns one patch and a tile of
-// 32 x 16 pooled outputs (two per thread): one thread stages the 4 child-map
-// windows it needs (72 x 33 floats each) in shared memory with 3-D TMA tensor
-// loads (rows of the pooled maps are padded to 16 floats and the window's
-// first column is a multiple of 4, so every load starts 16-byte aligned; the
-// tensor map zero-fills whatever lies outside the domain), the CTA forms the
-// 65 x 33 averages once, then pools them.  Patches vary fastest in the grid,
-// so the (up to 4) parents that read the same child window run at about the
-// same time and the repeat reads hit L2.  Algorithmic bytes per stored
-// output: 16 B of child values read (each child value is shared by 4
+// This pass streams the pooled maps of the level below and does a fixed
+// amount of arithmetic per stored output (~4 averages of 4 values, a 9-way
+// max with argmax, one power).  A CTA owns a tile of 32 x TH pooled outputs
+// (TH = 16 or 8, autotuned) of a run of up to 8 lattice patches on one row,
+// spaced so that the right child column of one patch is the left child column
+// of the next: the child windows (72 x (2 TH + 1) floats, which cover both
+// shifts +-1 of a shared column) are staged in shared memory by 3-D TMA tensor
+// loads into a ring of three columns, the column after next loading while the
+// current patch is averaged, pooled and rectified.  Each child window reaches
+// shared memory about twice per (up to) four parents instead of four times.
+// (Rows of the pooled maps are padded to 16 floats and the window's first
+// column is a multiple of 4, so every load starts 16-byte aligned; the tensor
+// map zero-fills whatever lies outside the domain.)  Algorithmic bytes per
+// stored output: 16 B of child values read (each child value is shared by 4
 // parents), 4 + 1 B written.
 #include "dm_internal.cuh"
 
 namespace {
 
-// valid[l][p] = 1 iff some child exists (Eq. 7 with the boundary rule), and
-// kids[p] = the existing children (index into level l-1, -1 where absent).
-__global__ void k_valid(DmGeom g, int l, const unsigned char* __restrict__ vprev, unsigned char* __restrict__ v,
-                        int4* __restrict__ kids) {
+// valid[l][p] = 1 iff some child exists (Eq. 7 with the boundary rule).
+__global__ void k_valid(DmGeom g, int l, const unsigned char* __restrict__ vprev, unsigned char* __restrict__ v) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= g.Lx * g.Ly) return;
     int ix = p % g.Lx, iy = p / g.Lx;
-    int c[4];
     unsigned char any = 0;
     for (int i = 0; i < 4; i++) {
-        c[i] = dm_child(g, l, ix, iy, i);
-        if (c[i] >= 0 && !vprev[c[i]]) c[i] = -1;
-        if (c[i] >= 0) any = 1;
+        int c = dm_child(g, l, ix, iy, i);
+        if (c >= 0 && vprev[c]) any = 1;
     }
     v[p] = any;
-    kids[p] = make_int4(c[0], c[1], c[2], c[3]);
 }
 
 __global__ void k_fill_u8(unsigned char* p, int n, unsigned char val) {
@@ -131,20 +128,21 @@ __device__ __forceinline__ float div_n(float x, int n) {
 }
 
 // Averages at staged row ay, columns ax .. ax+3 of child 0's frame, from the
-// four child windows: child i contributes kid[i][ay][ax + ox_i + 3].
-template <int KIDF, bool COMP, bool ALL4>
-__device__ __forceinline__ float4 avg4(const float* kid, int ay, int ax, const int* ci, int n) {
-    // children with ox = -1 (i = 0, 1) read columns ax+2 .. ax+5 (8-byte aligned),
-    // children with ox = +1 (i = 2, 3) read columns ax+4 .. ax+7 (16-byte aligned)
+// four child windows: child i contributes kb[i][ay][ax + ox_i + 3].
+template <bool COMP, bool ALL4>
+__device__ __forceinline__ float4 avg4(const float* const* kb, int ay, int ax, const int* ci, int n) {
+    // children with ox = -1 (i = 0, 1) read columns ax+2 .. ax+5 (two aligned
+    // float4 loads, which unlike 8-byte loads at a 16-byte stride are free of
+    // bank conflicts), children with ox = +1 (i = 2, 3) columns ax+4 .. ax+7
     float v[4][4];
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         if (!ALL4 && ci[i] < 0) continue;
-        const float* row = kid + i * KIDF + ay * KW;
+        const float* row = kb[i] + ay * KW;
         if (i < 2) {
-            const float2 a = *reinterpret_cast<const float2*>(row + ax + 2);
-            const float2 b = *reinterpret_cast<const float2*>(row + ax + 4);
-            v[i][0] = a.x; v[i][1] = a.y; v[i][2] = b.x; v[i][3] = b.y;
+            const float4 a = *reinterpret_cast<const float4*>(row + ax);
+            const float4 b = *reinterpret_cast<const float4*>(row + ax + 4);
+            v[i][0] = a.z; v[i][1] = a.w; v[i][2] = b.x; v[i][3] = b.y;
         } else {
             const float4 a = *reinterpret_cast<const float4*>(row + ax + 4);
             v[i][0] = a.x; v[i][1] = a.y; v[i][2] = a.z; v[i][3] = a.w;
@@ -170,135 +168,211 @@ __device__ __forceinline__ float4 avg4(const float* kid, int ay, int ax, const i
     return make_float4(r[0], r[1], r[2], r[3]);
 }
 
-template <int KIDF, bool COMP>
-__device__ __forceinline__ float avg1(const float* kid, int ay, int ax, const int* ci, int n) {
+template <bool COMP>
+__device__ __forceinline__ float avg1(const float* const* kb, int ay, int ax, const int* ci, int n) {
     float s = 0.0f, comp = 0.0f;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         if (ci[i] < 0) continue;
-        child_add<COMP>(s, comp, kid[i * KIDF + ay * KW + ax + ((i >= 2) ? 1 : -1) + 3]);
+        child_add<COMP>(s, comp, kb[i][ay * KW + ax + ((i >= 2) ? 1 : -1) + 3]);
     }
     return div_n(COMP ? __fadd_rn(s, comp) : s, n);
 }
 
-// Level l in [1, L-1]: grid (patch, tile).  `tmap` maps the pooled maps of
+// Sweep geometry of level l: a CTA owns one tile of TW x TH pooled outputs of a
+// run of RUN lattice patches on one row iy, ix = r + (k0 + k) * S.  Patch ix
+// has its children in the lattice (or atomic-grid) columns ix - d and ix + d'
+// of level l-1 (level 1: ix - 1 and ix; level l >= 2: ix -+ 2^(l-2)), rows
+// iy - e, iy + e' likewise; the stride S = 2^(l-1) (1 at level 1) makes the
+// right column of one patch the left column of the next, so the run needs
+// RUN + 1 columns of two child windows each instead of 4 windows per patch.
+constexpr int RUN = 8;
+
+__device__ __forceinline__ void child_col_row(const DmGeom& g, int l, int ix, int iy, int* cx_left, int* cy_top, int* step) {
+    if (l == 1) { *cx_left = ix - 1; *cy_top = iy - 1; *step = 1; }
+    else { const int s = 1 << (l - 2); *cx_left = ix - s; *cy_top = iy - s; *step = 2 * s; }
+}
+
+// Index at level l-1 of the child at column cx, row cy, or -1 (outside the
+// grid, or not existing).
+__device__ __forceinline__ int child_at(const DmGeom& g, int l, int cx, int cy, const unsigned char* __restrict__ vprev) {
+    const int gx = l == 1 ? g.P0x : g.Lx, gy = l == 1 ? g.P0y : g.Ly;
+    if (cx < 0 || cy < 0 || cx >= gx || cy >= gy) return -1;
+    const int c = cy * gx + cx;
+    return vprev[c] ? c : -1;
+}
+
+// Level l in [1, L-1].  Work item = (tile, row iy, residue r, run k0) with the
+// residue and run fastest, so the patches of neighbouring rows that share
+// child windows run close together in time.  `tmap` maps the pooled maps of
 // level l-1 as a 3-D array (columns dw[l], rows dh[l], patches) with a
-// 72 x 33 x 1 box.
+// 72 x (2 TH + 1) x 1 box.  Dynamic shared memory: a ring of 3 columns x 2
+// child windows, then the averages.  Per patch of the run: wait for the next
+// column, form the averages, release the oldest column (thread 0 starts the
+// loads of the column after next into it), pool, power, store.
 template <bool COMP, int TH>
-__global__ void __launch_bounds__(LEVEL_THREADS) k_level_pool_tiled(DmGeom g, int l, const __grid_constant__ CUtensorMap tmap,
-                                                                    const int4* __restrict__ kids,
-                                                                    float* __restrict__ out,
-                                                                    unsigned char* __restrict__ amax, float lam,
-                                                                    int* __restrict__ err) {
+__global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, const __grid_constant__ CUtensorMap tmap,
+                                                               const unsigned char* __restrict__ vprev,
+                                                               int runs_per_res, float* __restrict__ out,
+                                                               unsigned char* __restrict__ amax, float lam,
+                                                               int* __restrict__ err) {
     using T = LevelTile<TH>;
     constexpr int AH = T::AH, KIDF = T::KIDF;
-    __shared__ __align__(128) float kid[4 * KIDF];
-    __shared__ __align__(16) float avg[AH][AWP];
-    __shared__ __align__(8) uint64_t bar;
+    extern __shared__ __align__(128) unsigned char lsm_raw[];
+    // TMA destinations must be 128-byte aligned: round the dynamic base up (128 bytes are reserved for this)
+    float* lsm = reinterpret_cast<float*>(lsm_raw + ((128u - ((uint32_t)__cvta_generic_to_shared(lsm_raw) & 127u)) & 127u));
+    float* ring = lsm;                                       // [3][2][KIDF]
+    float (*avg)[AWP] = reinterpret_cast<float (*)[AWP]>(lsm + 6 * KIDF);
+    __shared__ __align__(8) uint64_t bars[3];
+    __shared__ int colc[3][2];                               // child index per ring slot (top, bottom), -1 absent
     __shared__ int abort_s;
-    const int p = blockIdx.x;
-    // the patch's existing children (one broadcast load); none: the patch does not exist
-    const int4 kc = __ldg(kids + p);
-    const int ci[4] = {kc.x, kc.y, kc.z, kc.w};
-    const int n = (ci[0] >= 0) + (ci[1] >= 0) + (ci[2] >= 0) + (ci[3] >= 0);
-    if (n == 0) return;
+
     const int ow = g.dw[l + 1], oh = g.dh[l + 1], opitch = g.pitch(l + 1);
     const int mw = g.dw[l], mh = g.dh[l];
     const int tiles_x = (ow + TW - 1) / TW;
-    const int rx0 = (blockIdx.y % tiles_x) * TW, ry0 = (blockIdx.y / tiles_x) * TH;
+    int cx0, cy0, S;
+    child_col_row(g, l, 0, 0, &cx0, &cy0, &S);
+    const int per_row = S * runs_per_res;
+    const int item = blockIdx.x;
+    const int tile = item / (g.Ly * per_row);
+    const int rem = item - tile * (g.Ly * per_row);
+    const int iy = rem / per_row;
+    const int rr = rem - iy * per_row;
+    const int r = rr / runs_per_res, k0 = (rr - r * runs_per_res) * RUN;
+    const int ix0 = r + k0 * S;                              // first patch of the run
+    if (ix0 >= g.Lx) return;
+    const int nrun = min(RUN, (g.Lx - 1 - ix0) / S + 1);    // patches in this run
+    const int rx0 = (tile % tiles_x) * TW, ry0 = (tile / tiles_x) * TH;
     const int qx0 = 2 * rx0 - 1, qy0 = 2 * ry0 - 1;
-    const int xa = 2 * rx0 - 4;                      // first staged child column (multiple of 4: 16-byte aligned)
+    const int xa = 2 * rx0 - 4;                              // first staged child column (multiple of 4 floats)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t bar_s = (uint32_t)__cvta_generic_to_shared(&bar);
-    // stage: child i, window rows qy0 + oy_i + [0, AH), columns xa + [0, KW)
+    int cxl, cyt, st;
+    child_col_row(g, l, ix0, iy, &cxl, &cyt, &st);
+    const int cyb = cyt + (l == 1 ? 1 : S);                  // bottom child row
+
+    // thread 0: start the loads of column j (child column cxl + j*S) into slot j % 3
+    auto stage = [&](int j) {
+        const int slot = j % 3;
+        const int cx = cxl + j * S;
+        const int ct = child_at(g, l, cx, cyt, vprev), cb = child_at(g, l, cx, cyb, vprev);
+        colc[slot][0] = ct;
+        colc[slot][1] = cb;
+        const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&bars[slot]);
+        const unsigned bytes = T::KID_BYTES * ((ct >= 0) + (cb >= 0));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(ring + slot * 2 * KIDF);
+        if (ct >= 0)
+            asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                         :: "r"(dst), "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(xa), "r"(qy0 - 1), "r"(ct), "r"(bar)
+                         : "memory");
+        if (cb >= 0)
+            asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                         :: "r"(dst + KIDF * 4), "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(xa), "r"(qy0 + 1), "r"(cb), "r"(bar)
+                         : "memory");
+    };
+    // wait for column j (the (j / 3)-th use of its slot); false on timeout
+    auto wait_col = [&](int j) -> bool {
+        const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&bars[j % 3]);
+        const uint32_t parity = (uint32_t)((j / 3) & 1);
+        const long long t0 = clock64();
+        while (true) {
+            uint32_t done;
+            asm volatile("{.reg .pred q; mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2, %3; selp.u32 %0, 1, 0, q;}"
+                         : "=r"(done) : "r"(bar), "r"(parity), "n"(WAIT_HINT_NS) : "memory");
+            if (done) return true;
+            if (clock64() - t0 > LEVEL_WAIT_CYCLES) return false;
+        }
+    };
+
     if (tid == 0) {
         abort_s = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar_s) : "memory");
+        for (int b = 0; b < 3; b++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"((uint32_t)__cvta_generic_to_shared(&bars[b])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar_s), "r"(T::KID_BYTES * n) : "memory");
-        const uint32_t kid_s = (uint32_t)__cvta_generic_to_shared(kid);
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-            if (ci[i] < 0) continue;
-            const int oy = (i & 1) ? 1 : -1;
-            asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-                         :: "r"(kid_s + (uint32_t)(i * KIDF * 4)), "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(xa),
-                            "r"(qy0 + oy), "r"(ci[i]), "r"(bar_s)
-                         : "memory");
-        }
-    }
-    __syncthreads();                                 // barrier initialised
-    {
-        const long long t0 = clock64();
-        uint32_t done = 0;
-        while (!done) {
-            asm volatile("{.reg .pred q; mbarrier.try_wait.parity.shared::cta.b64 q, [%1], 0; selp.u32 %0, 1, 0, q;}"
-                         : "=r"(done) : "r"(bar_s) : "memory");
-            if (!done && clock64() - t0 > LEVEL_WAIT_CYCLES) {
-                atomicOr(err, 1);
-                abort_s = 1;
-                break;
-            }
-        }
+        stage(0);
+        stage(1);
     }
     __syncthreads();
-    if (abort_s) return;
-    // averages: sum over existing children in order i = 0..3, then / n; four
-    // adjacent columns per item.
-    constexpr int G4 = (AW - 1) / 4;                 // 16 groups of 4 columns, then column 64
-    for (int e = tid; e < AH * G4; e += LEVEL_THREADS) {
-        const int ay = e / G4, ax = 4 * (e - ay * G4);
-        const float4 a = (n == 4) ? avg4<KIDF, COMP, true>(kid, ay, ax, ci, n) : avg4<KIDF, COMP, false>(kid, ay, ax, ci, n);
-        *reinterpret_cast<float4*>(&avg[ay][ax]) = a;
-    }
-    for (int ay = tid; ay < AH; ay += LEVEL_THREADS) avg[ay][AW - 1] = avg1<KIDF, COMP>(kid, ay, AW - 1, ci, n);
-    __syncthreads();
-    // 3x3 / 2 max-pool over in-domain averages, first strict maximum, power.
-    // A thread owns R = TH/8 vertically adjacent outputs (rows R*warp ..), so
-    // the horizontal 3-maxima of the 2R+1 average rows it reads are formed once
-    // (a row shared by two outputs serves both); rows are then merged in scan
-    // order m_y = -1, 0, 1, which keeps the first strict maximum.
-    constexpr int R = TH / 8;
-    const int rx = rx0 + lane;
-    if (rx >= ow) return;
     const bool interior = qx0 >= 0 && qy0 >= 0 && qx0 + AW <= mw && qy0 + AH <= mh;
-    const int ty0 = R * warp;
-    float hv[2 * R + 1];
-    int hc[2 * R + 1];
+    for (int k = 0; k < nrun; k++) {
+        if (tid == 0 && k + 2 <= nrun) stage(k + 2);         // slot of column k - 1, released last iteration
+        if (!wait_col(k) || !wait_col(k + 1)) { atomicOr(err, 1); abort_s = 1; }
+        __syncthreads();                                     // colc of columns k, k+1 visible; abort agreed
+        if (abort_s) {
+            // let the loads already started finish (each wait bounded) before the CTA exits
+            if (tid == 0)
+                for (int j = k; j <= min(k + 2, nrun); j++) wait_col(j);
+            return;
+        }
+        const int sl = k % 3, sr = (k + 1) % 3;
+        const int ci[4] = {colc[sl][0], colc[sl][1], colc[sr][0], colc[sr][1]};
+        const int n = (ci[0] >= 0) + (ci[1] >= 0) + (ci[2] >= 0) + (ci[3] >= 0);
+        const int ix = ix0 + k * S;
+        const int p = iy * g.Lx + ix;
+        if (n > 0) {
+            const float* kb[4] = {ring + (sl * 2) * KIDF, ring + (sl * 2 + 1) * KIDF, ring + (sr * 2) * KIDF,
+                                  ring + (sr * 2 + 1) * KIDF};
+            // averages: sum over existing children in order i = 0..3, then / n;
+            // four adjacent columns per work item
+            constexpr int G4 = (AW - 1) / 4;                 // 16 groups of 4 columns, then column 64
+            for (int e = tid; e < AH * G4; e += LEVEL_THREADS) {
+                const int ay = e / G4, ax = 4 * (e - ay * G4);
+                const float4 a = (n == 4) ? avg4<COMP, true>(kb, ay, ax, ci, n) : avg4<COMP, false>(kb, ay, ax, ci, n);
+                *reinterpret_cast<float4*>(&avg[ay][ax]) = a;
+            }
+            for (int ay = tid; ay < AH; ay += LEVEL_THREADS) avg[ay][AW - 1] = avg1<COMP>(kb, ay, AW - 1, ci, n);
+        }
+        __syncthreads();                                     // averages ready; column k no longer needed
+        if (n > 0) {
+            // 3x3 / 2 max-pool over in-domain averages, first strict maximum, power.
+            // A thread owns R = TH/8 vertically adjacent outputs (rows R*warp ..), so
+            // the horizontal 3-maxima of the 2R+1 average rows it reads are formed
+            // once (a row shared by two outputs serves both); rows are then merged in
+            // scan order m_y = -1, 0, 1, which keeps the first strict maximum.
+            constexpr int R = TH / 8;
+            const int rx = rx0 + lane;
+            const int ty0 = R * warp;
+            if (rx < ow) {
+                float hv[2 * R + 1];
+                int hc[2 * R + 1];
 #pragma unroll
-    for (int k = 0; k < 2 * R + 1; k++) {
-        const int ay = 2 * ty0 + k;                  // average row; map row qy0 + ay
-        const int qy = qy0 + ay;
-        float best = -INFINITY;
-        int code = 0;
-        if (interior || (qy >= 0 && qy < mh)) {
+                for (int kk = 0; kk < 2 * R + 1; kk++) {
+                    const int ay = 2 * ty0 + kk;             // average row; map row qy0 + ay
+                    const int qy = qy0 + ay;
+                    float best = -INFINITY;
+                    int code = 0;
+                    if (interior || (qy >= 0 && qy < mh)) {
 #pragma unroll
-            for (int mx = -1; mx <= 1; mx++) {
-                if (!interior) {
-                    const int qx = 2 * rx + mx;
-                    if (qx < 0 || qx >= mw) continue;
+                        for (int mx = -1; mx <= 1; mx++) {
+                            if (!interior) {
+                                const int qx = 2 * rx + mx;
+                                if (qx < 0 || qx >= mw) continue;
+                            }
+                            const float a = avg[ay][2 * lane + 1 + mx];
+                            if (a > best) { best = a; code = mx + 1; }
+                        }
+                    }
+                    hv[kk] = best;
+                    hc[kk] = code;
                 }
-                const float a = avg[ay][2 * lane + 1 + mx];
-                if (a > best) { best = a; code = mx + 1; }
+#pragma unroll
+                for (int j = 0; j < R; j++) {
+                    const int ry = ry0 + ty0 + j;
+                    if (ry >= oh) break;
+                    float best = -INFINITY;
+                    int code = 4;
+#pragma unroll
+                    for (int my = 0; my < 3; my++) {
+                        const float v = hv[2 * j + my];
+                        if (v > best) { best = v; code = my * 3 + hc[2 * j + my]; }
+                    }
+                    const long long o = ((long long)p * oh + ry) * opitch + rx;
+                    out[o] = dm_powf(best, lam);
+                    amax[o] = (unsigned char)code;
+                }
             }
         }
-        hv[k] = best;
-        hc[k] = code;
-    }
-#pragma unroll
-    for (int j = 0; j < R; j++) {
-        const int ry = ry0 + ty0 + j;
-        if (ry >= oh) break;
-        float best = -INFINITY;
-        int code = 4;
-#pragma unroll
-        for (int my = 0; my < 3; my++) {
-            const float v = hv[2 * j + my];
-            if (v > best) { best = v; code = my * 3 + hc[2 * j + my]; }
-        }
-        long long o = ((long long)p * oh + ry) * opitch + rx;
-        out[o] = dm_powf(best, lam);
-        amax[o] = (unsigned char)code;
+        __syncthreads();                                     // averages consumed
     }
 }
 
@@ -318,6 +392,26 @@ __global__ void k_level_top(DmGeom g, int l, const unsigned char* __restrict__ v
     top[(long long)p * mw * mh + q] = dm_powf(a, lam);
 }
 
+template <bool COMP, int TH>
+cudaError_t launch_sweep(const DmGeom& g, int l, const CUtensorMap& tm, const dm_pyramid& py, int per_res, long long items,
+                         float lam, int* status, cudaStream_t st) {
+    const size_t smem = (size_t)(6 * LevelTile<TH>::KIDF + LevelTile<TH>::AH * AWP) * sizeof(float) + 128;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    static unsigned long long attr_set = 0;
+    if (dev < 64 && !(attr_set & (1ull << dev))) {
+        cudaError_t e = cudaFuncSetAttribute(k_level_sweep<COMP, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set |= 1ull << dev;
+    }
+    if (items <= 0) return cudaSuccess;
+    if (items > 0x7fffffffLL) return cudaErrorInvalidValue;
+    k_level_sweep<COMP, TH><<<(unsigned)items, LEVEL_THREADS, smem, st>>>(g, l, tm, py.valid[l - 1], per_res,
+                                                                          const_cast<float*>(py.pooled[l]),
+                                                                          const_cast<unsigned char*>(py.amax[l]), lam, status);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& py, float lam, int* status, cudaStream_t st) {
@@ -325,7 +419,7 @@ cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& py, float lam, i
     int n0 = g.npatch(0), np = g.npatch(1);
     k_fill_u8<<<(n0 + 255) / 256, 256, 0, st>>>(const_cast<unsigned char*>(py.valid[0]), n0, 1);
     for (int l = 1; l <= g.L; l++) {
-        k_valid<<<(np + 255) / 256, 256, 0, st>>>(g, l, py.valid[l - 1], const_cast<unsigned char*>(py.valid[l]), py.kids);
+        k_valid<<<(np + 255) / 256, 256, 0, st>>>(g, l, py.valid[l - 1], const_cast<unsigned char*>(py.valid[l]));
         if (l < g.L) {
             // pooled maps of level l-1: [npatch(l-1)][dh[l]][pitch(l)] floats
             const int th = py.tune.level_th == 8 ? 8 : 16;
@@ -336,12 +430,18 @@ cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& py, float lam, i
             if (!dm_encode_tiled(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(py.pooled[l - 1]), dims,
                                  strides, box))
                 return cudaErrorNotSupported;
-            int tiles = ((g.dw[l + 1] + TW - 1) / TW) * ((g.dh[l + 1] + th - 1) / th);
-            dim3 grid(np, tiles);
-            auto kern = th == 8 ? (py.compensated ? k_level_pool_tiled<true, 8> : k_level_pool_tiled<false, 8>)
-                                : (py.compensated ? k_level_pool_tiled<true, 16> : k_level_pool_tiled<false, 16>);
-            kern<<<grid, LEVEL_THREADS, 0, st>>>(g, l, tm, py.kids, const_cast<float*>(py.pooled[l]),
-                                                 const_cast<unsigned char*>(py.amax[l]), lam, status);
+            const int tiles = ((g.dw[l + 1] + TW - 1) / TW) * ((g.dh[l + 1] + th - 1) / th);
+            const int S = l == 1 ? 1 : 1 << (l - 1);
+            const int per_res = ((g.Lx + S - 1) / S + RUN - 1) / RUN;    // runs per residue class
+            const long long items = (long long)tiles * g.Ly * S * per_res;
+            cudaError_t e;
+            if (th == 8)
+                e = py.compensated ? launch_sweep<true, 8>(g, l, tm, py, per_res, items, lam, status, st)
+                                   : launch_sweep<false, 8>(g, l, tm, py, per_res, items, lam, status, st);
+            else
+                e = py.compensated ? launch_sweep<true, 16>(g, l, tm, py, per_res, items, lam, status, st)
+                                   : launch_sweep<false, 16>(g, l, tm, py, per_res, items, lam, status, st);
+            if (e != cudaSuccess) return e;
         } else {
             int n = g.dw[l] * g.dh[l];
             dim3 grid((n + B - 1) / B, np);
