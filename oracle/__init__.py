@@ -156,12 +156,14 @@ class Pyramid:
     argmax: list = field(default_factory=list)   # same shapes, uint8 codes (my+1)*3 + (mx+1)
     top: np.ndarray | None = None                # [npatch(L)][dh[L]][dw[L]]
     valid: list = field(default_factory=list)    # l = 0..L: [npatch(l)] uint8
+    gap: list | None = None                      # optional, like pooled: relative top-two gap of each argmax
 
 
 def pyramid(d1: np.ndarray, d2: np.ndarray, prec: str = "f64", lam: float = DEFAULT_CFG["lam"],
-            compensated: bool = True) -> Pyramid:
+            compensated: bool = True, gaps: bool = False) -> Pyramid:
     """Level maps of Algorithm 1.  `compensated` selects the FP32 mirror's
-    child sum (TwoSum-compensated or plain, both in child order); FP64 ignores it."""
+    child sum (TwoSum-compensated or plain, both in child order); FP64 ignores it.
+    `gaps`: also the relative top-two gap of every pooling decision."""
     dt = _dtype(prec)
     d1 = np.ascontiguousarray(d1, dtype=dt)
     d2 = np.ascontiguousarray(d2, dtype=dt)
@@ -178,11 +180,15 @@ def pyramid(d1: np.ndarray, d2: np.ndarray, prec: str = "f64", lam: float = DEFA
     pp = (C.c_void_p * g.L)(*[a.ctypes.data for a in pyr.pooled])
     aa = (C.c_void_p * g.L)(*[a.ctypes.data for a in pyr.argmax])
     vv = (C.c_void_p * (g.L + 1))(*[a.ctypes.data for a in pyr.valid])
+    gg = None
+    if gaps:
+        pyr.gap = [np.zeros(a.shape, dtype=np.float64) for a in pyr.pooled]
+        gg = (C.c_void_p * g.L)(*[a.ctypes.data for a in pyr.gap])
     lib = _lib(prec)
     lib.orc_pyramid.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int,
-                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     rc = lib.orc_pyramid(_ptr(d1), W1, H1, _ptr(d2), W2, H2, float(lam), int(bool(compensated)), pp, aa,
-                         _ptr(pyr.top), vv)
+                         _ptr(pyr.top), vv, gg)
     if rc != 0:
         raise ValueError("pyramid oracle failed")
     return pyr
@@ -196,6 +202,7 @@ class Backtrack:
     bestQ_i: np.ndarray    # [cells] its (patch*16 + offset in cell)
     leaf: np.ndarray | None  # [P0][H2][W2] merged atomic scores (optional)
     reached: np.ndarray    # [L+1] distinct tuples per level
+    gap: np.ndarray | None = None   # [P0] smallest relative top-two gap of the decisions behind BestAt(p)
 
 
 def backtrack(pyr: Pyramid, dense_leaf: bool = False) -> Backtrack:
@@ -208,11 +215,16 @@ def backtrack(pyr: Pyramid, dense_leaf: bool = False) -> Backtrack:
     pp = (C.c_void_p * g.L)(*[a.ctypes.data for a in pyr.pooled])
     aa = (C.c_void_p * g.L)(*[a.ctypes.data for a in pyr.argmax])
     vv = (C.c_void_p * (g.L + 1))(*[a.ctypes.data for a in pyr.valid])
+    gg = None
+    if pyr.gap is not None:
+        bt.gap = np.zeros(n0, np.float64)
+        gg = (C.c_void_p * g.L)(*[a.ctypes.data for a in pyr.gap])
     lib = _lib(pyr.prec)
-    lib.orc_backtrack.argtypes = [C.c_int] * 4 + [C.c_void_p] * 10
+    lib.orc_backtrack.argtypes = [C.c_int] * 4 + [C.c_void_p] * 12
     rc = lib.orc_backtrack(g.W1, g.H1, g.W2, g.H2, pp, aa, _ptr(pyr.top), vv,
                            _ptr(bt.bestP_s), _ptr(bt.bestP_i), _ptr(bt.bestQ_s), _ptr(bt.bestQ_i),
-                           _ptr(bt.leaf) if dense_leaf else None, _ptr(bt.reached))
+                           _ptr(bt.leaf) if dense_leaf else None, _ptr(bt.reached), gg,
+                           _ptr(bt.gap) if bt.gap is not None else None)
     if rc != 0:
         raise ValueError("backtrack oracle failed")
     return bt
@@ -231,13 +243,15 @@ def reciprocal(pyr: Pyramid, bt: Backtrack) -> np.ndarray:
     return out[:n]
 
 
-def match(img1: np.ndarray, img2: np.ndarray, prec: str = "f64", compensated: bool = True, **cfg):
-    """Descriptors -> pyramid -> backtracking -> reciprocal matches."""
+def match(img1: np.ndarray, img2: np.ndarray, prec: str = "f64", compensated: bool = True, gaps: bool = False,
+          **cfg):
+    """Descriptors -> pyramid -> backtracking -> reciprocal matches (with the
+    per-patch decision gaps in bt.gap when `gaps`)."""
     c = dict(DEFAULT_CFG, **cfg)
     lam = c.pop("lam")
     d1 = descriptors(img1, prec, **c)
     d2 = descriptors(img2, prec, **c)
-    pyr = pyramid(d1, d2, prec, lam, compensated)
+    pyr = pyramid(d1, d2, prec, lam, compensated, gaps)
     bt = backtrack(pyr)
     return reciprocal(pyr, bt), pyr, bt
 

@@ -352,7 +352,12 @@ int orc_level0(const real* d1, int W1, int H1, const real* d2, int W2, int H2, i
 /* Max-pooling + subsampling (Eq. 8-9) of one map: dst(r) = max over the      */
 /* in-domain positions 2r+m, m in {-1,0,1}^2; argmax code (my+1)*3 + (mx+1).  */
 /* ------------------------------------------------------------------------- */
-static void pool_map(const real* src, int sw, int sh, real* dst, uint8_t* am, int dw, int dh, int rectify_after, real lam) {
+/* 3x3 / 2 max-pooling of one map with its argmax; optionally the relative
+ * gap (best - second best) / best between the winner and the largest other
+ * in-domain candidate of each window (0 on a tie, 1 with a single candidate):
+ * how close the argmax decision is to changing. */
+static void pool_map(const real* src, int sw, int sh, real* dst, uint8_t* am, double* gap, int dw, int dh,
+                     int rectify_after, real lam) {
     for (int ry = 0; ry < dh; ry++)
         for (int rx = 0; rx < dw; rx++) {
             real best = RNEG_INF;
@@ -366,6 +371,19 @@ static void pool_map(const real* src, int sw, int sh, real* dst, uint8_t* am, in
                 }
             dst[(size_t)ry * dw + rx] = rectify_after ? RPOW(best, lam) : best;
             am[(size_t)ry * dw + rx] = (uint8_t)code;
+            if (gap) {
+                real second = RNEG_INF;
+                for (int my = -1; my <= 1; my++)
+                    for (int mx = -1; mx <= 1; mx++) {
+                        int x = 2 * rx + mx, y = 2 * ry + my;
+                        if (x < 0 || y < 0 || x >= sw || y >= sh || (my + 1) * 3 + (mx + 1) == code) continue;
+                        real v = src[(size_t)y * sw + x];
+                        if (v > second) second = v;
+                    }
+                double gp = 1.0;
+                if (second != RNEG_INF) gp = best > 0 ? (double)(best - second) / (double)best : 0.0;
+                gap[(size_t)ry * dw + rx] = gp;
+            }
         }
 }
 
@@ -374,11 +392,12 @@ static void pool_map(const real* src, int sw, int sh, real* dst, uint8_t* am, in
 /*                                                                            */
 /* pooled[l] : [npatch(l)][dh[l+1]][dw[l+1]]  = (S o P)(C_l), l = 0..L-1      */
 /* amax[l]   : same shape, argmax codes                                       */
+/* pgap[l]   : same shape, optional (NULL): relative top-two gap of the argmax */
 /* top       : [npatch(L)][dh[L]][dw[L]]       = C_L                          */
 /* valid[l]  : [npatch(l)] patch membership of G_{4*2^l}, l = 0..L            */
 /* ------------------------------------------------------------------------- */
 int orc_pyramid(const real* d1, int W1, int H1, const real* d2, int W2, int H2, double lambda, int compensated,
-                real** pooled, uint8_t** amax, real* top, uint8_t** valid) {
+                real** pooled, uint8_t** amax, real* top, uint8_t** valid, double** pgap) {
     geom g;
     if (make_geom(W1, H1, W2, H2, &g)) return -1;
     const real lam = (real)lambda;
@@ -399,7 +418,8 @@ int orc_pyramid(const real* d1, int W1, int H1, const real* d2, int W2, int H2, 
                     map[(size_t)ty * W2 + tx] = ORC_F32 ? c : RPOW(c, lam);
                 }
             size_t off = (size_t)p * g.dw[1] * g.dh[1];
-            pool_map(map, W2, H2, pooled[0] + off, amax[0] + off, g.dw[1], g.dh[1], ORC_F32, lam);
+            pool_map(map, W2, H2, pooled[0] + off, amax[0] + off, pgap ? pgap[0] + off : NULL, g.dw[1], g.dh[1],
+                     ORC_F32, lam);
         }
         free(map);
     }
@@ -467,7 +487,8 @@ int orc_pyramid(const real* d1, int W1, int H1, const real* d2, int W2, int H2, 
                     }
                 if (l < L) {
                     size_t off = (size_t)p * g.dw[l + 1] * g.dh[l + 1];
-                    pool_map(map, mw, mh, pooled[l] + off, amax[l] + off, g.dw[l + 1], g.dh[l + 1], ORC_F32, lam);
+                    pool_map(map, mw, mh, pooled[l] + off, amax[l] + off, pgap ? pgap[l] + off : NULL, g.dw[l + 1],
+                             g.dh[l + 1], ORC_F32, lam);
                 } else {
                     real* dst = top + (size_t)p * mw * mh;
                     for (size_t k = 0; k < (size_t)mw * mh; k++) dst[k] = ORC_F32 ? RPOW(map[k], lam) : map[k];
@@ -499,7 +520,7 @@ int orc_level0_pooled(const real* d1, int W1, int H1, const real* d2, int W2, in
                     map[(size_t)ty * W2 + tx] = ORC_F32 ? c : RPOW(c, lam);
                 }
             size_t off = (size_t)k * g.dw[1] * g.dh[1];
-            pool_map(map, W2, H2, out + off, am + off, g.dw[1], g.dh[1], ORC_F32, lam);
+            pool_map(map, W2, H2, out + off, am + off, NULL, g.dw[1], g.dh[1], ORC_F32, lam);
         }
         free(map);
     }
@@ -546,7 +567,8 @@ static int better(pscore s, long long idx, pscore bs, long long bidx) {
 }
 
 int orc_backtrack(int W1, int H1, int W2, int H2, real** pooled, uint8_t** amax, const real* top, uint8_t** valid,
-                  real* bestP_s, long long* bestP_i, real* bestQ_s, long long* bestQ_i, real* leaf, long long* reached) {
+                  real* bestP_s, long long* bestP_i, real* bestQ_s, long long* bestQ_i, real* leaf, long long* reached,
+                  double** pgap, double* gap) {
     geom g;
     if (make_geom(W1, H1, W2, H2, &g)) return -1;
     const int L = g.L;
@@ -558,10 +580,21 @@ int orc_backtrack(int W1, int H1, int W2, int H2, real** pooled, uint8_t** amax,
     for (int p = 0; p < n0; p++) { bP[p] = PS_NONE; bestP_i[p] = -1; }
     for (int c = 0; c < CW * CH; c++) { bQ[c] = PS_NONE; bestQ_i[c] = -1; }
     pscore* lf = NULL;
-    if (leaf) {
+    if (leaf || gap) {
         lf = (pscore*)malloc((size_t)n0 * W2 * H2 * sizeof(pscore));
         if (!lf) { free(bP); free(bQ); return -2; }
         for (size_t k = 0; k < (size_t)n0 * W2 * H2; k++) lf[k] = PS_NONE;
+    }
+    /* winning arrival of every merged tuple (decision gaps only): per level l < L,
+     * parent flat index at level l + 1 times 4 plus the child index i */
+    long long* par[ORC_MAXL + 1];
+    for (int l = 0; l <= L; l++) par[l] = NULL;
+    if (gap) {
+        for (int l = 0; l < L; l++) {
+            size_t n = l == 0 ? (size_t)n0 * W2 * H2 : (size_t)npatch(&g, l) * g.dw[l] * g.dh[l];
+            par[l] = (long long*)malloc(n * sizeof(long long));
+            if (!par[l]) { for (int k = 0; k < l; k++) free(par[k]); free(bP); free(bQ); free(lf); return -2; }
+        }
     }
     for (int l = 0; l <= L; l++) reached[l] = 0;
 
@@ -604,14 +637,23 @@ int orc_backtrack(int W1, int H1, int W2, int H2, real** pooled, uint8_t** amax,
                         int code = amax[l - 1][ro];
                         int tx = 2 * rx + (code % 3 - 1), ty = 2 * ry + (code / 3 - 1);
                         pscore s2 = s + ps_term(pooled[l - 1][ro]);   /* Eq. 14: s + C_{N/2,p_i}(p'_i) */
+                        const long long arrival = ((long long)p * mw * mh + (long long)qy * mw + qx) * 4 + i;
                         if (l - 1 >= 1) {
-                            pscore* d = &nxt[(size_t)c * tw * th + (size_t)ty * tw + tx];
-                            if (ps_greater(s2, *d)) *d = s2;
+                            size_t di = (size_t)c * tw * th + (size_t)ty * tw + tx;
+                            pscore* d = &nxt[di];
+                            if (ps_greater(s2, *d)) {
+                                *d = s2;
+                                if (par[l - 1]) par[l - 1][di] = arrival;
+                            }
                         } else {
                             long long tidx = (long long)ty * W2 + tx;
                             if (lf) {
-                                pscore* d = &lf[(size_t)c * W2 * H2 + tidx];
-                                if (ps_greater(s2, *d)) *d = s2;
+                                size_t di = (size_t)c * W2 * H2 + tidx;
+                                pscore* d = &lf[di];
+                                if (ps_greater(s2, *d)) {
+                                    *d = s2;
+                                    if (par[0]) par[0][di] = arrival;
+                                }
                             }
                             if (better(s2, tidx, bP[c], bestP_i[c])) { bP[c] = s2; bestP_i[c] = tidx; }
                             int cell = (ty / 4) * CW + tx / 4;
@@ -629,6 +671,63 @@ int orc_backtrack(int W1, int H1, int W2, int H2, real** pooled, uint8_t** amax,
             reached[l - 1] = cnt;
         }
     }
+    /* decision gaps (reading of the tolerance rule): for the best tuple of each
+     * atomic patch, the smallest relative top-two gap among the decisions that
+     * made it the output -- BestAt(p) over the patch's tuples, BestAt' over the
+     * tuples of its cell of I', and the 3x3 argmax at every level of the path
+     * that merged into it (winning arrival at each level) */
+    if (gap) {
+        for (int p = 0; p < n0; p++) {
+            gap[p] = 1.0;
+            if (bestP_i[p] < 0) continue;
+            const long long ts = bestP_i[p];
+            double g1 = 1.0;
+            pscore b1 = bP[p], b2 = PS_NONE;
+            for (long long t = 0; t < (long long)W2 * H2; t++) {
+                pscore v = lf[(size_t)p * W2 * H2 + t];
+                if (t == ts || v == PS_NONE) continue;
+                if (b2 == PS_NONE || v > b2) b2 = v;
+            }
+            if (b2 != PS_NONE) g1 = (double)(ps_value(b1) - ps_value(b2)) / (double)ps_value(b1);
+            /* BestAt' of the cell of t */
+            const int tx = (int)(ts % W2), ty = (int)(ts / W2);
+            pscore c2 = PS_NONE;
+            for (int c = 0; c < n0; c++)
+                for (int yy = (ty / 4) * 4; yy < (ty / 4) * 4 + 4 && yy < H2; yy++)
+                    for (int xx = (tx / 4) * 4; xx < (tx / 4) * 4 + 4 && xx < W2; xx++) {
+                        if (c == p && yy == ty && xx == tx) continue;
+                        pscore v = lf[(size_t)c * W2 * H2 + (size_t)yy * W2 + xx];
+                        if (v == PS_NONE) continue;
+                        if (c2 == PS_NONE || v > c2) c2 = v;
+                    }
+            double g2 = 1.0;
+            if (c2 != PS_NONE) g2 = fabs((double)(ps_value(b1) - ps_value(c2))) / (double)ps_value(b1);
+            double gm = g1 < g2 ? g1 : g2;
+            /* the path: level-m tuple (c, t) came from the level-(m+1) tuple `arrival` via child i,
+             * through the argmax of P_m(c, r), r = q + o_i */
+            long long idx = (long long)p * W2 * H2 + ts;
+            int c = p;
+            for (int m = 0; m < L; m++) {
+                const long long a = par[m][idx];
+                const long long pf = a / 4;
+                const int i = (int)(a % 4);
+                const int mw = g.dw[m + 1], mh = g.dh[m + 1];
+                const int pp = (int)(pf / ((long long)mw * mh));
+                const long long q = pf % ((long long)mw * mh);
+                const int ox = (i >= 2) ? 1 : -1, oy = (i & 1) ? 1 : -1;
+                const int rx = (int)(q % mw) + ox, ry = (int)(q / mw) + oy;
+                if (pgap && pgap[m]) {
+                    const double d = pgap[m][(size_t)c * mw * mh + (size_t)ry * mw + rx];
+                    if (d < gm) gm = d;
+                }
+                idx = pf;
+                c = pp;
+            }
+            gap[p] = gm;
+        }
+    }
+    for (int l = 0; l <= L; l++) free(par[l]);
+
     /* scores out, rounded once */
     for (int p = 0; p < n0; p++) bestP_s[p] = bP[p] == PS_NONE ? RNEG_INF : ps_value(bP[p]);
     for (int c = 0; c < CW * CH; c++) bestQ_s[c] = bQ[c] == PS_NONE ? RNEG_INF : ps_value(bQ[c]);
@@ -636,7 +735,7 @@ int orc_backtrack(int W1, int H1, int W2, int H2, real** pooled, uint8_t** amax,
         long long cnt = 0;
         for (size_t k = 0; k < (size_t)n0 * W2 * H2; k++) {
             cnt += (lf[k] != PS_NONE);
-            leaf[k] = lf[k] == PS_NONE ? RNEG_INF : ps_value(lf[k]);
+            if (leaf) leaf[k] = lf[k] == PS_NONE ? RNEG_INF : ps_value(lf[k]);
         }
         reached[0] = cnt;
     } else {

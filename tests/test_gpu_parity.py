@@ -13,10 +13,10 @@ from paper_1506_07656_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-# FP64 agreement: a patch may differ from the FP64 oracle only if its FP64
-# best score is within this relative gap of another candidate (see the
-# near-tie rule in the design notes); at most this fraction may differ.
-FP64_MAX_DISAGREE = 0.02
+# FP64 agreement: a patch may differ from the FP64 oracle only where one of the
+# decisions behind the oracle's output for it (BestAt, BestAt', a 3x3 argmax on
+# its winning path) has a relative top-two gap below this tolerance.
+FP64_GAP_TOL = 1e-3
 
 
 @pytest.fixture(scope="module")
@@ -159,12 +159,26 @@ def test_match_end_to_end_config1(torch_cuda, ctx, oracle_mod):
     got = ctx.match(pr.img1, pr.img2).cpu().numpy().astype(np.float64)
     want32, _, _ = oracle_mod.match(pr.img1, pr.img2, "f32")
     np.testing.assert_array_equal(got, want32)
-    want64, _, _ = oracle_mod.match(pr.img1, pr.img2, "f64")
-    agree = _agreement(got, want64)
-    assert agree >= 1.0 - FP64_MAX_DISAGREE, agree
+    want64, pyr64, bt64 = oracle_mod.match(pr.img1, pr.img2, "f64", gaps=True)
+    bad = _disagreeing_patches(got, want64, pyr64.geom)
+    excused = [p for p in bad if bt64.gap[p] < FP64_GAP_TOL]
+    print(f"FP64 agreement: {1 - len(bad) / pyr64.geom.npatch(0):.4f}, {len(bad)} differing patches, "
+          f"{len(excused)} excused by a near tie")
+    assert len(excused) == len(bad), [(p, bt64.gap[p]) for p in bad if p not in excused]
     assert synth.accuracy_at(got, pr.flow, 10.0) >= 0.95
     st, reached = ctx.status(64, 48, 64, 48)
     assert st == 0
+
+
+def _disagreeing_patches(a, b, geom):
+    """Atomic patches whose match (or absence of one) differs between two lists."""
+    ka = {(int(r[0]), int(r[1])): (r[2], r[3]) for r in a}
+    kb = {(int(r[0]), int(r[1])): (r[2], r[3]) for r in b}
+    out = []
+    for (x1, y1) in set(ka) | set(kb):
+        if ka.get((x1, y1)) != kb.get((x1, y1)):
+            out.append(((y1 - 2) // 4) * geom.P0x + (x1 - 2) // 4)
+    return sorted(out)
 
 
 def _agreement(a, b):

@@ -211,8 +211,9 @@ def _enumerate_paths(pyr):
     term = (lambda v: np.rint(v.astype(np.float32) * np.float32(2.0 ** 28)).astype(np.int64)) if fixed else (lambda v: v)
     S = term(pyr.top[P, QY, QX])
     EP, EQX, EQY = P.copy(), QX.copy(), QY.copy()
+    G = np.ones(len(P))                        # smallest pooling-decision gap along the path
     for l in range(L, 0, -1):
-        nP, nX, nY, nS, nE, nEX, nEY = [], [], [], [], [], [], []
+        nP, nX, nY, nS, nE, nEX, nEY, nG = [], [], [], [], [], [], [], []
         mw, mh = g.dw[l], g.dh[l]
         for i in range(4):
             ox = 1 if i >= 2 else -1
@@ -237,12 +238,17 @@ def _enumerate_paths(pyr):
             tx = 2 * rx + code % 3 - 1
             ty = 2 * ry + code // 3 - 1
             s2 = S + term(pyr.pooled[l - 1][c, ry, rx])
+            g2 = np.minimum(G, pyr.gap[l - 1][c, ry, rx]) if pyr.gap is not None else G
+            nG.append(g2[ok])
             nP.append(c[ok]); nX.append(tx[ok]); nY.append(ty[ok]); nS.append(s2[ok])
             nE.append(EP[ok]); nEX.append(EQX[ok]); nEY.append(EQY[ok])
         P, QX, QY, S = np.concatenate(nP), np.concatenate(nX), np.concatenate(nY), np.concatenate(nS)
         EP, EQX, EQY = np.concatenate(nE), np.concatenate(nEX), np.concatenate(nEY)
+        G = np.concatenate(nG)
     if fixed:
         S = (S.astype(np.float32) * np.float32(2.0 ** -28)).astype(np.float32)   # rounded once
+    if pyr.gap is not None:
+        return P, QX, QY, S, EP, EQX, EQY, G
     return P, QX, QY, S, EP, EQX, EQY
 
 
@@ -278,6 +284,56 @@ def test_p3_backtrack_vs_enumeration(oracle_mod, prec, W, H, seed):
     devx = TX - (ax + (1 << L) * EQX - epx)
     devy = TY - (ay + (1 << L) * EQY - epy)
     assert np.abs(devx).max() <= (1 << L) - 1 and np.abs(devy).max() <= (1 << L) - 1
+
+
+# --------------------------------------------------------------------------- #
+# P13: decision gaps (tolerance rule for FP64 agreement)                      #
+# --------------------------------------------------------------------------- #
+def test_p13_decision_gaps(oracle_mod):
+    """The FP64 oracle's per-patch decision gap: the smallest relative top-two
+    gap among BestAt(p), BestAt' of the winner's cell of I', and the 3x3 argmax
+    of every level on the winning path.  Checked against (a) level-0 pooling
+    gaps recomputed from the unpooled correlation maps, and (b) the exhaustive
+    path enumeration of P3 carrying the smallest gap along each path."""
+    W, H = 40, 32
+    pr = synth.make_pair_smooth(W, H, seed=21)
+    d1 = oracle_mod.descriptors(pr.img1, "f64")
+    d2 = oracle_mod.descriptors(pr.img2, "f64")
+    lam = 1.4
+    pyr = oracle_mod.pyramid(d1, d2, "f64", gaps=True)
+    g = pyr.geom
+    # (a) level 0: windows of the rectified unpooled maps (Algorithm 1 order)
+    c0 = oracle_mod.level0(d1, d2)                      # [P0][H2][W2], unrectified
+    r0 = np.power(c0, lam)
+    for p in range(0, g.npatch(0), 7):
+        for ry in range(g.dh[1]):
+            for rx in range(g.dw[1]):
+                vals = [r0[p, 2 * ry + my, 2 * rx + mx] for my in (-1, 0, 1) for mx in (-1, 0, 1)
+                        if 0 <= 2 * rx + mx < W and 0 <= 2 * ry + my < H]
+                vals.sort(reverse=True)
+                want = 1.0 if len(vals) == 1 else (vals[0] - vals[1]) / vals[0]
+                assert abs(pyr.gap[0][p, ry, rx] - want) <= 1e-12
+    # (b) paths
+    bt = oracle_mod.backtrack(pyr, dense_leaf=True)
+    P, TX, TY, S, EP, EQX, EQY, G = _enumerate_paths(pyr)
+    CW = (W + 3) // 4
+    leaf = bt.leaf
+    for p in range(g.npatch(0)):
+        t = bt.bestP_i[p]
+        if t < 0:
+            continue
+        tx, ty = t % W, t // W
+        row = np.sort(leaf[p].ravel()[np.isfinite(leaf[p].ravel())])[::-1]
+        gp = 1.0 if len(row) < 2 else (row[0] - row[1]) / row[0]
+        cell = leaf[:, (ty // 4) * 4:(ty // 4) * 4 + 4, (tx // 4) * 4:(tx // 4) * 4 + 4].copy()
+        cell[p, ty - (ty // 4) * 4, tx - (tx // 4) * 4] = -np.inf
+        others = cell[np.isfinite(cell)]
+        gq = 1.0 if len(others) == 0 else abs(row[0] - others.max()) / row[0]
+        sel = (P == p) & (TX == tx) & (TY == ty)
+        best = S[sel].max()
+        cands = {min(gp, gq, gpath) for gpath in G[sel][S[sel] == best]}
+        assert any(abs(bt.gap[p] - c) <= 1e-12 for c in cands), (p, bt.gap[p], cands)
+    assert (bt.gap >= 0).all() and (bt.gap <= 1).all()
 
 
 # --------------------------------------------------------------------------- #
