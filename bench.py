@@ -43,6 +43,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (CUDA graph) measurement")
     ap.add_argument("--batch-replays", type=int, default=3)
+    ap.add_argument("--batch-lanes", type=int, default=2, help="concurrent lanes of the batched form (1..4)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default launch shapes instead of autotuning them first")
     return ap.parse_args()
@@ -268,6 +269,7 @@ def _measure_batch(dm, torch, ctx, a, rank):
                       torch.empty((n0, 5), dtype=torch.float32, device="cuda"),
                       torch.zeros(1, dtype=torch.int32, device="cuda")))
     pairs = dm.make_pairs(items)
+    dm.dm_set_batch_lanes(ctx.ctx, a.batch_lanes)
     ws = torch.empty(dm.dm_batch_workspace_bytes(ctx.ctx, pairs), dtype=torch.uint8, device="cuda")
     # autotune the launch shapes once per size, on the first pair of that size (before capture)
     tuned = {}
@@ -295,7 +297,8 @@ def _measure_batch(dm, torch, ctx, a, rank):
     del graph, ws
     return {"pairs": 48, "sizes": [f"{w}x{h}" for w, h in BATCH_SIZES], "per_size": 12,
             "pairs_per_s": 48 / (ms / 1e3), "ms_per_batch": ms, "replays": a.batch_replays,
-            "graph": "one CUDA graph of dm_match_batch (all 48 pairs), replayed", "matches": n_match,
+            "graph": f"one CUDA graph of dm_match_batch (all 48 pairs, {a.batch_lanes} concurrent lanes), replayed",
+            "lanes": a.batch_lanes, "matches": n_match,
             "autotuned": tuned}
 
 

@@ -216,15 +216,27 @@ typedef struct {
     int* d_count;
 } dm_pair;
 
-/* Batched form.  Matches n pairs, of possibly different sizes, one after the
- * other on `stream` with one shared workspace (d_ws >= the largest
- * match_bytes over the pairs, from dm_batch_workspace_bytes).  Nothing in the
- * sequence synchronises with the host, so the whole batch can be captured in
- * a CUDA graph and replayed (make one uncaptured call first so that one-time
- * per-device set-up does not happen inside the capture).  Arguments of every
- * pair are checked before anything is launched. */
+/* Batched form.  Matches n pairs of possibly different sizes.  The pairs are
+ * spread over the context's concurrent lanes (internal streams; 2 by
+ * default, dm_set_batch_lanes): pair k runs on lane k % lanes, each lane in
+ * its own slice of d_ws (slice j at offset j * lane_bytes, lane_bytes = the
+ * largest match_bytes over the pairs rounded up to 256), so that the
+ * latency-bound phases of one pair (backtracking, the small top levels)
+ * overlap the compute of another.  The lanes fork from and join back into
+ * `stream` with events: all of the work is ordered after what was already on
+ * `stream`, and work queued on `stream` later waits for every pair.
+ * dm_batch_workspace_bytes gives lanes * lane_bytes; a smaller d_ws (at least
+ * lane_bytes) runs fewer lanes.  Nothing synchronises with the host, so the
+ * whole batch can be captured in a CUDA graph and replayed (make one
+ * uncaptured call first so that one-time per-device set-up does not happen
+ * inside the capture).  Arguments of every pair are checked before anything
+ * is launched.  Each lane's device status word is in the header of its slice
+ * (dm_read_status on d_ws + j * lane_bytes reads the last pair of lane j). */
 dm_status dm_batch_workspace_bytes(const dm_ctx* ctx, int n, const dm_pair* pairs, size_t* bytes);
 dm_status dm_match_batch(dm_ctx* ctx, int n, const dm_pair* pairs, void* d_ws, size_t ws_bytes, void* stream);
+/* Number of concurrent lanes of dm_match_batch, 1..4 (1: one pair after the
+ * other on `stream`). */
+dm_status dm_set_batch_lanes(dm_ctx* ctx, int lanes);
 
 /* Autotuner of the batched form.  Runs the launch-shape candidates of three
  * kernels on the given pair and keeps, for pairs of exactly these sizes in

@@ -27,6 +27,10 @@ struct dm_ctx {
     // autotuner results per pair size (W1, H1, W2, H2)
     std::mutex tune_mu;
     std::map<std::array<int, 4>, DmTune> tuned;
+    // batched form: concurrent lanes (internal streams), fork / join events
+    int lanes = 2;
+    cudaStream_t lane_st[DM_MAX_LANES] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[DM_MAX_LANES] = {};
 };
 
 namespace {
@@ -275,6 +279,17 @@ dm_status dm_create(const dm_config* cfg, int device, dm_ctx** out) {
     dm_ctx* x = new dm_ctx();
     x->cfg = c;
     x->device = device;
+    {
+        DevGuard dg(device);
+        bool ok = cudaEventCreateWithFlags(&x->fork_ev, cudaEventDisableTiming) == cudaSuccess;
+        for (int k = 0; ok && k < DM_MAX_LANES; k++)
+            ok = cudaStreamCreateWithFlags(&x->lane_st[k], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&x->join_ev[k], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            dm_destroy(x);
+            return DM_ECUDA;
+        }
+    }
     x->desc.t1 = make_taps(c.nu1);
     x->desc.t2 = make_taps(c.nu2);
     x->desc.t3 = make_taps(c.nu3);
@@ -289,6 +304,11 @@ dm_status dm_destroy(dm_ctx* ctx) {
     if (ctx) {
         DevGuard dg(ctx->device);
         for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+        if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+        for (int k = 0; k < DM_MAX_LANES; k++) {
+            if (ctx->join_ev[k]) cudaEventDestroy(ctx->join_ev[k]);
+            if (ctx->lane_st[k]) cudaStreamDestroy(ctx->lane_st[k]);
+        }
     }
     delete ctx;
     return DM_OK;
@@ -558,8 +578,9 @@ dm_status dm_loss_grad(dm_ctx* ctx, const dm_pyramid* pyr, const float* d_desc1,
     return DM_OK;
 }
 
-dm_status dm_batch_workspace_bytes(const dm_ctx* ctx, int n, const dm_pair* pairs, size_t* bytes) {
-    if (!ctx || n < 0 || (n > 0 && !pairs) || !bytes) return DM_EINVAL;
+namespace {
+// workspace of one lane: the largest match workspace over the pairs (256-byte multiple)
+dm_status batch_lane_bytes(dm_ctx* ctx, int n, const dm_pair* pairs, size_t* bytes) {
     size_t best = 256;
     for (int k = 0; k < n; k++) {
         size_t mb = 0;
@@ -568,13 +589,33 @@ dm_status dm_batch_workspace_bytes(const dm_ctx* ctx, int n, const dm_pair* pair
         if (s != DM_OK) return s;
         if (mb > best) best = mb;
     }
-    *bytes = best;
+    *bytes = dm_align(best);
+    return DM_OK;
+}
+}  // namespace
+
+dm_status dm_set_batch_lanes(dm_ctx* ctx, int lanes) {
+    if (!ctx) return DM_EINVAL;
+    if (lanes < 1 || lanes > DM_MAX_LANES) return fail(ctx, DM_EINVAL, "dm_set_batch_lanes: lanes must be 1..%d", DM_MAX_LANES);
+    ctx->lanes = lanes;
+    return DM_OK;
+}
+
+dm_status dm_batch_workspace_bytes(const dm_ctx* ctx, int n, const dm_pair* pairs, size_t* bytes) {
+    if (!ctx || n < 0 || (n > 0 && !pairs) || !bytes) return DM_EINVAL;
+    size_t lane = 0;
+    dm_status s = batch_lane_bytes(const_cast<dm_ctx*>(ctx), n, pairs, &lane);
+    if (s != DM_OK) return s;
+    const int lanes = n < ctx->lanes ? (n > 0 ? n : 1) : ctx->lanes;
+    *bytes = lane * (size_t)lanes;
     return DM_OK;
 }
 
 dm_status dm_match_batch(dm_ctx* ctx, int n, const dm_pair* pairs, void* d_ws, size_t ws_bytes, void* stream) {
     if (!ctx) return DM_EINVAL;
     if (n < 0 || (n > 0 && !pairs) || !d_ws) return fail(ctx, DM_EINVAL, "dm_match_batch: bad arguments");
+    if (!aligned256(d_ws)) return fail(ctx, DM_EINVAL, "workspace must be 256-byte aligned");
+    size_t lane_bytes = 0;
     for (int k = 0; k < n; k++) {     // validate everything before launching anything
         const dm_pair& q = pairs[k];
         if (!q.d_img1 || !q.d_img2 || !q.d_out || !q.d_count || q.capacity < 0)
@@ -582,16 +623,42 @@ dm_status dm_match_batch(dm_ctx* ctx, int n, const dm_pair* pairs, void* d_ws, s
         DmGeom g;
         dm_status s = check_geom(ctx, q.W1, q.H1, q.W2, q.H2, &g);
         if (s != DM_OK) return s;
-        MatchLayout ml;
-        match_layout(g, ctx->cfg.precision, &ml);
-        if (ws_bytes < ml.bytes) return fail(ctx, DM_ENOMEM, "dm_match_batch: pair %d needs %zu workspace bytes", k, ml.bytes);
     }
+    dm_status s = batch_lane_bytes(ctx, n, pairs, &lane_bytes);
+    if (s != DM_OK) return s;
+    if (ws_bytes < lane_bytes) return fail(ctx, DM_ENOMEM, "dm_match_batch: needs at least %zu workspace bytes", lane_bytes);
+    if (n == 0) return DM_OK;
+    int lanes = (int)(ws_bytes / lane_bytes);
+    if (lanes > ctx->lanes) lanes = ctx->lanes;
+    if (lanes > n) lanes = n;
+    DevGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (lanes == 1) {
+        for (int k = 0; k < n; k++) {
+            const dm_pair& q = pairs[k];
+            s = dm_match(ctx, q.d_img1, q.W1, q.H1, q.d_img2, q.W2, q.H2, d_ws, lane_bytes, q.d_out, q.capacity,
+                         q.d_count, stream);
+            if (s != DM_OK) return s;
+        }
+        return DM_OK;
+    }
+    // fork: every lane stream waits for the work already on `stream`; pair k
+    // runs on lane k % lanes in its own workspace slice; join back into `stream`
+    cudaError_t e = cudaEventRecord(ctx->fork_ev, st);
+    for (int j = 0; e == cudaSuccess && j < lanes; j++) e = cudaStreamWaitEvent(ctx->lane_st[j], ctx->fork_ev, 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "dm_match_batch: fork");
     for (int k = 0; k < n; k++) {
         const dm_pair& q = pairs[k];
-        dm_status s = dm_match(ctx, q.d_img1, q.W1, q.H1, q.d_img2, q.W2, q.H2, d_ws, ws_bytes, q.d_out, q.capacity,
-                               q.d_count, stream);
+        const int j = k % lanes;
+        s = dm_match(ctx, q.d_img1, q.W1, q.H1, q.d_img2, q.W2, q.H2, (char*)d_ws + (size_t)j * lane_bytes, lane_bytes,
+                     q.d_out, q.capacity, q.d_count, ctx->lane_st[j]);
         if (s != DM_OK) return s;
     }
+    for (int j = 0; e == cudaSuccess && j < lanes; j++) {
+        e = cudaEventRecord(ctx->join_ev[j], ctx->lane_st[j]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->join_ev[j], 0);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "dm_match_batch: join");
     return DM_OK;
 }
 

@@ -8,6 +8,7 @@
 #include "../../include/dm.h"
 
 #define DM_MAXL 30
+#define DM_MAX_LANES 4   // concurrent lanes (internal streams) of the batched form
 
 // Geometry of one image pair (Sec. 3.2 "Bottom level", Eq. 7, Algorithm 1).
 struct DmGeom {

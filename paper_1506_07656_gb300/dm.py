@@ -70,6 +70,7 @@ _SIGS = {
     "dm_loss_grad": (C.c_int, [C.c_void_p] * 5 + [C.c_size_t] + [C.c_void_p] * 5),
     "dm_batch_workspace_bytes": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_size_t)]),
     "dm_match_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "dm_set_batch_lanes": (C.c_int, [C.c_void_p, C.c_int]),
     "dm_backtrack_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "dm_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                               C.c_size_t, C.POINTER(C.c_int), C.c_void_p]),
@@ -286,6 +287,10 @@ def dm_match_batch(ctx, pairs, d_ws, stream=None):
     st = load().dm_match_batch(ctx, len(pairs), pairs, _dptr(d_ws), d_ws.numel() * d_ws.element_size(),
                                _stream_ptr(stream))
     _check(ctx, st, "dm_match_batch")
+
+
+def dm_set_batch_lanes(ctx, lanes: int) -> None:
+    _check(ctx, load().dm_set_batch_lanes(ctx, int(lanes)), "dm_set_batch_lanes")
 
 
 def dm_backtrack_noalloc(ctx, pyr, d_out, d_count, stream=None):

@@ -97,3 +97,29 @@ def test_batch_rejects_bad_pair_before_launch(env):
     assert e.value.status == dm.DM_EINVAL
     torch.cuda.synchronize()
     assert int(items[0][3].item()) == -7        # nothing ran for the valid first pair either
+
+
+@pytest.mark.parametrize("lanes", [1, 3, 4])
+def test_batch_lanes_give_identical_matches(env, lanes):
+    """Any number of concurrent lanes, and a workspace too small for all of
+    them (fewer lanes run), gives the matches of the single-pair calls."""
+    torch, dm, ctx = env
+    items, host = _alloc(torch, dm, SIZES, 140)
+    pairs = dm.make_pairs(items)
+    try:
+        dm.dm_set_batch_lanes(ctx.ctx, lanes)
+        full = dm.dm_batch_workspace_bytes(ctx.ctx, pairs)
+        for nbytes in (full, full // lanes + 256):
+            ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            for it in items:
+                it[2].zero_()
+                it[3].zero_()
+            dm.dm_match_batch(ctx.ctx, pairs, ws)
+            torch.cuda.synchronize()
+            for (i1, i2, out, cnt), pr in zip(items, host):
+                n = int(cnt.item())
+                np.testing.assert_array_equal(out[:n].cpu().numpy(), _single(ctx, pr))
+    finally:
+        dm.dm_set_batch_lanes(ctx.ctx, 2)
+    with pytest.raises(dm.DmError):
+        dm.dm_set_batch_lanes(ctx.ctx, 5)
