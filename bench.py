@@ -303,10 +303,12 @@ def _measure_batch(dm, torch, ctx, a, rank):
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
-# ncu captures summarised in profiles/, scaled from the 512x224 capture to the
-# 1024x436 workload by the number of pooled outputs (x15.1).  None where no
-# capture of the current kernel version exists.
-TRAFFIC_1024x436 = {"level0_bf16": 16.7e9, "level0_fp32": None, "levels": None}
+# ncu captures summarised in profiles/ (512x224, the full workload is too large
+# to capture), scaled to the 1024x436 workload: level 0 by the number of pooled
+# outputs (x15.1); the level pass from its level-1 launch by the algorithmic
+# bytes of the whole launch set (same traffic/algorithmic ratio, 1.60).  None
+# where no capture of the current kernel version exists.
+TRAFFIC_1024x436 = {"level0_bf16": 16.7e9, "level0_fp8": None, "level0_fp32": None, "levels": 34.9e9}
 
 
 def _prec_code(dm, name):
@@ -348,7 +350,7 @@ def _rooflines(r, prec, W, H, peaks, nsm):
     gbs = (rd + wr) / (lev_ms / 1e3) / 1e9
     lev = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
            "traffic": TRAFFIC_1024x436["levels"] if (W, H) == (1024, 436) else None,
-           "kernel": "k_level_pool_tiled + k_level_top (pyramid levels >= 1)",
+           "kernel": "k_level_sweep + k_level_top (pyramid levels >= 1)",
            "peak_source": "hbm_gbs of measured" if "hbm_gbs" in peaks else "fallback 6.8 TB/s",
            "algorithmic_bytes_per_launch_set": rd + wr, "launch_ms": lev_ms}
     return corr, lev
