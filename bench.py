@@ -197,6 +197,20 @@ def run_reference(a):
 # --------------------------------------------------------------------------- #
 # Our arm                                                                    #
 # --------------------------------------------------------------------------- #
+def _max_over_ranks(torch, dist, x, world, device):
+    """The largest value of x over all ranks (x itself when there is one rank)."""
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_throughput(world, steps, seconds):
+    """Whole-job pairs/s: each of `world` replicas matches `steps` pairs; the
+    slowest rank's time counts."""
+    return world * steps / seconds
+
+
 def _measure(dm, torch, dist, ctx, pair, a, world, local, stream):
     """Time K dm_match steps on device-resident images, then K dm_match_host steps."""
     W, H = a.width, a.height
@@ -228,10 +242,7 @@ def _measure(dm, torch, dist, ctx, pair, a, world, local, stream):
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
     stages, ncalls, launches = dm.dm_timing_read(ctx.ctx)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = _max_over_ranks(torch, dist, ms, world, "cuda")
     # end to end through the public API with host buffers (copies inside)
     h1 = torch.from_numpy(pair.img1).pin_memory()
     h2 = torch.from_numpy(pair.img2).pin_memory()
@@ -243,12 +254,10 @@ def _measure(dm, torch, dist, ctx, pair, a, world, local, stream):
     t0 = time.perf_counter()
     for _ in range(a.steps):
         dm.dm_match_host(ctx.ctx, h1, h2, ws, hout, stream)
-    e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    return dict(ms=ms_max, value=world * a.steps / (ms_max / 1e3), stages={k: v / max(ncalls, 1) for k, v in stages.items()},
-                launches=launches, e2e=world * a.steps / float(te.item()), status=status, reached=reached,
+    e2e_s = _max_over_ranks(torch, dist, time.perf_counter() - t0, world, "cuda")
+    return dict(ms=ms_max, value=_job_throughput(world, a.steps, ms_max / 1e3),
+                stages={k: v / max(ncalls, 1) for k, v in stages.items()},
+                launches=launches, e2e=_job_throughput(world, a.steps, e2e_s), status=status, reached=reached,
                 matches=n_matches, clocks=clk.summary(), geo=geo, tuned=tuned)
 
 
