@@ -132,6 +132,13 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(bar) : "memory");
 }
 
+// Three-input maximum (one PTX max with three operands).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 __device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, %0;" :: "n"(EPI_THREADS) : "memory"); }
 
 // Pack the patch vectors of I into BF16 M-tiles (zero rows past the last patch).
@@ -248,12 +255,12 @@ __device__ __forceinline__ void epilogue_tile(const EpiArgs& e, uint32_t b, uint
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     mbar_arrive(bar_empty);
 
-    float best[PY][4];
-    int code[PY][4];
-#pragma unroll
-    for (int y = 0; y < PY; y++)
-#pragma unroll
-        for (int x = 0; x < 4; x++) { best[y][x] = -INFINITY; code[y][x] = 4; }
+    // separable 3x3 / 2 pooling: per C0 row the 3-maxima of column triples
+    // (2k, 2k+1, 2k+2) with the first column holding it, then per pooled row
+    // the maximum of the three row maxima (C0 rows 2y, 2y+1, 2y+2 = m_y -1, 0,
+    // +1) with the first row holding it: the first maximum in scan order
+    float h[CY][4];
+    int hc[CY][4];
     const int tx0 = e.cx0 + 8 * e.part;
 #pragma unroll
     for (int ly = 0; ly < CY; ly++) {
@@ -271,27 +278,21 @@ __device__ __forceinline__ void epilogue_tile(const EpiArgs& e, uint32_t b, uint
         }
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            float h = v[2 * k];
-            int hc = 0;
-            if (v[2 * k + 1] > h) { h = v[2 * k + 1]; hc = 1; }
-            if (v[2 * k + 2] > h) { h = v[2 * k + 2]; hc = 2; }
-            // C0 row ly is m_y = -1 of pooled row ly/2 (even ly), m_y = 0 of (ly-1)/2 (odd),
-            // m_y = +1 of ly/2 - 1 (even ly); rows arrive in scan order
-            if ((ly & 1) == 0) {
-                if (ly >= 2) {
-                    const int jj = ly / 2 - 1;
-                    if (h > best[jj][k]) { best[jj][k] = h; code[jj][k] = 6 + hc; }
-                }
-                if (ly / 2 < PY) {
-                    const int jj = ly / 2;
-                    if (h > best[jj][k]) { best[jj][k] = h; code[jj][k] = hc; }
-                }
-            } else {
-                const int jj = (ly - 1) / 2;
-                if (h > best[jj][k]) { best[jj][k] = h; code[jj][k] = 3 + hc; }
-            }
+            const float m = fmax3(v[2 * k], v[2 * k + 1], v[2 * k + 2]);
+            h[ly][k] = m;
+            hc[ly][k] = v[2 * k] == m ? 0 : (v[2 * k + 1] == m ? 1 : 2);
         }
     }
+    float best[PY][4];
+    int code[PY][4];
+#pragma unroll
+    for (int y = 0; y < PY; y++)
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const float m = fmax3(h[2 * y][k], h[2 * y + 1][k], h[2 * y + 2][k]);
+            best[y][k] = m;
+            code[y][k] = h[2 * y][k] == m ? hc[2 * y][k] : (h[2 * y + 1][k] == m ? 3 + hc[2 * y + 1][k] : 6 + hc[2 * y + 2][k]);
+        }
     // staging layout = the TMA box [patch][row][16 columns]
 #pragma unroll
     for (int y = 0; y < PY; y++) {
