@@ -52,6 +52,13 @@ struct Kids {
     int n;
 };
 
+// Three-input maximum (one PTX max with three operands).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // Knuth TwoSum step of the compensated child sum.
 __device__ __forceinline__ void two_sum_add(float& s, float& comp, float v) {
     const float t = __fadd_rn(s, v);
@@ -338,34 +345,26 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
 #pragma unroll
                 for (int kk = 0; kk < 2 * R + 1; kk++) {
                     const int ay = 2 * ty0 + kk;             // average row; map row qy0 + ay
-                    const int qy = qy0 + ay;
-                    float best = -INFINITY;
-                    int code = 0;
-                    if (interior || (qy >= 0 && qy < mh)) {
-#pragma unroll
-                        for (int mx = -1; mx <= 1; mx++) {
-                            if (!interior) {
-                                const int qx = 2 * rx + mx;
-                                if (qx < 0 || qx >= mw) continue;
-                            }
-                            const float a = avg[ay][2 * lane + 1 + mx];
-                            if (a > best) { best = a; code = mx + 1; }
-                        }
+                    float a0 = avg[ay][2 * lane], a1 = avg[ay][2 * lane + 1], a2 = avg[ay][2 * lane + 2];
+                    if (!interior) {
+                        const int qy = qy0 + ay, qx = 2 * rx;
+                        const bool rin = qy >= 0 && qy < mh;
+                        if (!rin || qx - 1 < 0) a0 = -INFINITY;
+                        if (!rin) a1 = -INFINITY;
+                        if (!rin || qx + 1 >= mw) a2 = -INFINITY;
                     }
-                    hv[kk] = best;
-                    hc[kk] = code;
+                    // first column holding the row maximum (columns in scan order m_x = -1, 0, 1)
+                    const float m = fmax3(a0, a1, a2);
+                    hv[kk] = m;
+                    hc[kk] = a0 == m ? 0 : (a1 == m ? 1 : 2);
                 }
 #pragma unroll
                 for (int j = 0; j < R; j++) {
                     const int ry = ry0 + ty0 + j;
                     if (ry >= oh) break;
-                    float best = -INFINITY;
-                    int code = 4;
-#pragma unroll
-                    for (int my = 0; my < 3; my++) {
-                        const float v = hv[2 * j + my];
-                        if (v > best) { best = v; code = my * 3 + hc[2 * j + my]; }
-                    }
+                    // first row holding the maximum (m_y = -1, 0, 1): the first maximum in scan order
+                    const float best = fmax3(hv[2 * j], hv[2 * j + 1], hv[2 * j + 2]);
+                    const int code = hv[2 * j] == best ? hc[2 * j] : (hv[2 * j + 1] == best ? 3 + hc[2 * j + 1] : 6 + hc[2 * j + 2]);
                     const long long o = ((long long)p * oh + ry) * opitch + rx;
                     out[o] = dm_powf(best, lam);
                     amax[o] = (unsigned char)code;
