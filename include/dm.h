@@ -246,22 +246,23 @@ dm_status dm_set_batch_lanes(dm_ctx* ctx, int lanes);
  *              M-tiles; candidates split the patches into 1, 2, 3, 4, 6 or 8
  *              chunks; unused by DM_FP32);
  *   chosen[1]  pooled rows per CTA tile of the level kernel (16 or 8);
- *   chosen[2]  CTAs per SM of the backtracking expansion kernels (2..32).
+ *   chosen[2]  CTAs per SM of the backtracking expansion kernels (2..32);
+ *   chosen[3]  child-window columns in the level kernel's ring (3 or 2).
  * Every candidate computes identical results; only the time differs.  Each
  * candidate runs twice, timed with CUDA events; a candidate replaces the
  * current choice only when it is at least 2% faster.  Later
  * dm_correlate_pyramid / dm_match / dm_match_batch calls on pairs of these
  * sizes use the choice.  d_img1, d_img2, d_ws as for dm_match (d_ws is used as
  * scratch).  Synchronises `stream` (cannot be captured: tune before capturing
- * a graph).  chosen: 3 ints out, or NULL.  The paper has no counterpart. */
+ * a graph).  chosen: 4 ints out, or NULL.  The paper has no counterpart. */
 dm_status dm_autotune(dm_ctx* ctx, const float* d_img1, int W1, int H1, const float* d_img2, int W2, int H2,
                       void* d_ws, size_t ws_bytes, int* chosen, void* stream);
-/* The launch shapes used for pairs of these sizes (the defaults 110, 16, 8
- * until dm_autotune has run on them): 3 ints as for dm_autotune. */
+/* The launch shapes used for pairs of these sizes (the defaults 110, 16, 8, 2
+ * until dm_autotune has run on them): 4 ints as for dm_autotune. */
 dm_status dm_tuned_config(dm_ctx* ctx, int W1, int H1, int W2, int H2, int* chosen);
 /* Set the launch shapes for pairs of these sizes (e.g. a choice saved from an
  * earlier dm_autotune): chosen[0] >= 1, chosen[1] in {8, 16}, chosen[2] in
- * 1..64; DM_EINVAL otherwise. */
+ * 1..64, chosen[3] in {2, 3}; DM_EINVAL otherwise. */
 dm_status dm_set_tuned_config(dm_ctx* ctx, int W1, int H1, int W2, int H2, const int* chosen);
 
 /* Backtracking without any caller workspace.

@@ -734,12 +734,17 @@ dm_status dm_autotune(dm_ctx* ctx, const float* d_img1, int W1, int H1, const fl
         }
         py.tune.m_chunk = best.m_chunk;
     }
-    // levels: pooled rows per CTA tile
+    // levels: pooled rows per CTA tile x ring columns
     auto levels = [&]() { return dm_launch_levels(g, py, ctx->cfg.lambda, d_status, st); };
     cur = timed(levels);
-    py.tune.level_th = 8;
-    if (pick(timed(levels), cur)) best.level_th = 8;
+    const int lshapes[3][2] = {{16, 3}, {8, 2}, {8, 3}};
+    for (const auto& sh : lshapes) {
+        py.tune.level_th = sh[0];
+        py.tune.level_ring = sh[1];
+        if (pick(timed(levels), cur)) { best.level_th = sh[0]; best.level_ring = sh[1]; }
+    }
     py.tune.level_th = best.level_th;
+    py.tune.level_ring = best.level_ring;
     // backtracking: CTAs per SM of the expansion kernels
     auto backtrack = [&]() { return dm_launch_backtrack(g, py, ml.bt, base, dout, g.npatch(0), dcnt, st); };
     cur = timed(backtrack);
@@ -759,7 +764,7 @@ dm_status dm_autotune(dm_ctx* ctx, const float* d_img1, int W1, int H1, const fl
         std::lock_guard<std::mutex> lk(ctx->tune_mu);
         ctx->tuned[{W1, H1, W2, H2}] = best;
     }
-    if (chosen) { chosen[0] = best.m_chunk; chosen[1] = best.level_th; chosen[2] = best.bt_mult; }
+    if (chosen) { chosen[0] = best.m_chunk; chosen[1] = best.level_th; chosen[2] = best.bt_mult; chosen[3] = best.level_ring; }
     return DM_OK;
 }
 
@@ -772,18 +777,21 @@ dm_status dm_tuned_config(dm_ctx* ctx, int W1, int H1, int W2, int H2, int* chos
     chosen[0] = t.m_chunk;
     chosen[1] = t.level_th;
     chosen[2] = t.bt_mult;
+    chosen[3] = t.level_ring;
     return DM_OK;
 }
 
 dm_status dm_set_tuned_config(dm_ctx* ctx, int W1, int H1, int W2, int H2, const int* chosen) {
     if (!ctx || !chosen) return DM_EINVAL;
-    if (chosen[0] < 1 || (chosen[1] != 8 && chosen[1] != 16) || chosen[2] < 1 || chosen[2] > 64)
-        return fail(ctx, DM_EINVAL, "dm_set_tuned_config: invalid launch shapes %d %d %d", chosen[0], chosen[1], chosen[2]);
+    if (chosen[0] < 1 || (chosen[1] != 8 && chosen[1] != 16) || chosen[2] < 1 || chosen[2] > 64 ||
+        (chosen[3] != 2 && chosen[3] != 3))
+        return fail(ctx, DM_EINVAL, "dm_set_tuned_config: invalid launch shapes %d %d %d %d", chosen[0], chosen[1],
+                    chosen[2], chosen[3]);
     DmGeom g;
     dm_status s = check_geom(ctx, W1, H1, W2, H2, &g);
     if (s != DM_OK) return s;
     std::lock_guard<std::mutex> lk(ctx->tune_mu);
-    ctx->tuned[{W1, H1, W2, H2}] = DmTune{chosen[0], chosen[1], chosen[2]};
+    ctx->tuned[{W1, H1, W2, H2}] = DmTune{chosen[0], chosen[1], chosen[2], chosen[3]};
     return DM_OK;
 }
 

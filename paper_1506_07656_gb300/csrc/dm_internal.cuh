@@ -176,13 +176,15 @@ constexpr unsigned WAIT_HINT_NS = 1000000u;
 // Launch shapes the autotuner chooses among (every choice computes identical
 // results): M-tiles of 128 patches per work unit of the tensor-core level-0
 // kernel, pooled rows per CTA tile of the level kernel (8 or 16), CTAs per SM
-// of the backtracking expansion kernels.
+// of the backtracking expansion kernels, child-window columns in the level
+// kernel's ring (3 or 2: prefetch depth against shared memory per CTA).
 struct DmTune {
     int m_chunk;
     int level_th;
     int bt_mult;
+    int level_ring;
 };
-constexpr DmTune DM_TUNE_DEFAULT = {110, 16, 8};
+constexpr DmTune DM_TUNE_DEFAULT = {110, 16, 8, 2};
 
 // Pyramid handle (host side).
 struct dm_pyramid {

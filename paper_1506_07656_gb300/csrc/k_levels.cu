@@ -17,8 +17,9 @@
 // spaced so that the right child column of one patch is the left child column
 // of the next: the child windows (72 x (2 TH + 1) floats, which cover both
 // shifts +-1 of a shared column) are staged in shared memory by 3-D TMA tensor
-// loads into a ring of three columns, the column after next loading while the
-// current patch is averaged, pooled and rectified.  Each child window reaches
+// loads into a ring of NR = 2 (or 3, autotuned) columns; as soon as a patch's
+// averages are formed its left column is released and thread 0 starts the
+// loads of the column NR ahead, which overlap the pooling and rectification.  Each child window reaches
 // shared memory about twice per (up to) four parents instead of four times.
 // (Rows of the pooled maps are padded to 16 floats and the window's first
 // column is a multiple of 4, so every load starts 16-byte aligned; the tensor
@@ -213,11 +214,11 @@ __device__ __forceinline__ int child_at(const DmGeom& g, int l, int cx, int cy, 
 // residue and run fastest, so the patches of neighbouring rows that share
 // child windows run close together in time.  `tmap` maps the pooled maps of
 // level l-1 as a 3-D array (columns dw[l], rows dh[l], patches) with a
-// 72 x (2 TH + 1) x 1 box.  Dynamic shared memory: a ring of 3 columns x 2
-// child windows, then the averages.  Per patch of the run: wait for the next
-// column, form the averages, release the oldest column (thread 0 starts the
-// loads of the column after next into it), pool, power, store.
-template <bool COMP, int TH>
+// 72 x (2 TH + 1) x 1 box.  Dynamic shared memory: a ring of NR columns x 2
+// child windows, then the averages.  Per patch of the run: wait for its two
+// columns, form the averages, release the left column (thread 0 starts the
+// loads of the column NR ahead into it), pool, power, store.
+template <bool COMP, int TH, int NR>
 __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, const __grid_constant__ CUtensorMap tmap,
                                                                const unsigned char* __restrict__ vprev,
                                                                int runs_per_res, float* __restrict__ out,
@@ -228,10 +229,10 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
     extern __shared__ __align__(128) unsigned char lsm_raw[];
     // TMA destinations must be 128-byte aligned: round the dynamic base up (128 bytes are reserved for this)
     float* lsm = reinterpret_cast<float*>(lsm_raw + ((128u - ((uint32_t)__cvta_generic_to_shared(lsm_raw) & 127u)) & 127u));
-    float* ring = lsm;                                       // [3][2][KIDF]
-    float (*avg)[AWP] = reinterpret_cast<float (*)[AWP]>(lsm + 6 * KIDF);
-    __shared__ __align__(8) uint64_t bars[3];
-    __shared__ int colc[3][2];                               // child index per ring slot (top, bottom), -1 absent
+    float* ring = lsm;                                       // [NR][2][KIDF]
+    float (*avg)[AWP] = reinterpret_cast<float (*)[AWP]>(lsm + NR * 2 * KIDF);
+    __shared__ __align__(8) uint64_t bars[NR];
+    __shared__ int colc[NR][2];                              // child index per ring slot (top, bottom), -1 absent
     __shared__ int abort_s;
 
     const int ow = g.dw[l + 1], oh = g.dh[l + 1], opitch = g.pitch(l + 1);
@@ -257,9 +258,9 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
     child_col_row(g, l, ix0, iy, &cxl, &cyt, &st);
     const int cyb = cyt + (l == 1 ? 1 : S);                  // bottom child row
 
-    // thread 0: start the loads of column j (child column cxl + j*S) into slot j % 3
+    // thread 0: start the loads of column j (child column cxl + j*S) into slot j % NR
     auto stage = [&](int j) {
-        const int slot = j % 3;
+        const int slot = j % NR;
         const int cx = cxl + j * S;
         const int ct = child_at(g, l, cx, cyt, vprev), cb = child_at(g, l, cx, cyb, vprev);
         colc[slot][0] = ct;
@@ -277,10 +278,10 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
                          :: "r"(dst + KIDF * 4), "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(xa), "r"(qy0 + 1), "r"(cb), "r"(bar)
                          : "memory");
     };
-    // wait for column j (the (j / 3)-th use of its slot); false on timeout
+    // wait for column j (the (j / NR)-th use of its slot); false on timeout
     auto wait_col = [&](int j) -> bool {
-        const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&bars[j % 3]);
-        const uint32_t parity = (uint32_t)((j / 3) & 1);
+        const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&bars[j % NR]);
+        const uint32_t parity = (uint32_t)((j / NR) & 1);
         const long long t0 = clock64();
         while (true) {
             uint32_t done;
@@ -293,25 +294,23 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
 
     if (tid == 0) {
         abort_s = 0;
-        for (int b = 0; b < 3; b++)
+        for (int b = 0; b < NR; b++)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"((uint32_t)__cvta_generic_to_shared(&bars[b])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        stage(0);
-        stage(1);
+        for (int j = 0; j < NR && j <= nrun; j++) stage(j);
     }
     __syncthreads();
     const bool interior = qx0 >= 0 && qy0 >= 0 && qx0 + AW <= mw && qy0 + AH <= mh;
     for (int k = 0; k < nrun; k++) {
-        if (tid == 0 && k + 2 <= nrun) stage(k + 2);         // slot of column k - 1, released last iteration
         if (!wait_col(k) || !wait_col(k + 1)) { atomicOr(err, 1); abort_s = 1; }
         __syncthreads();                                     // colc of columns k, k+1 visible; abort agreed
         if (abort_s) {
             // let the loads already started finish (each wait bounded) before the CTA exits
             if (tid == 0)
-                for (int j = k; j <= min(k + 2, nrun); j++) wait_col(j);
+                for (int j = k; j <= min(k + NR - 1, nrun); j++) wait_col(j);
             return;
         }
-        const int sl = k % 3, sr = (k + 1) % 3;
+        const int sl = k % NR, sr = (k + 1) % NR;
         const int ci[4] = {colc[sl][0], colc[sl][1], colc[sr][0], colc[sr][1]};
         const int n = (ci[0] >= 0) + (ci[1] >= 0) + (ci[2] >= 0) + (ci[3] >= 0);
         const int ix = ix0 + k * S;
@@ -330,6 +329,7 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
             for (int ay = tid; ay < AH; ay += LEVEL_THREADS) avg[ay][AW - 1] = avg1<COMP>(kb, ay, AW - 1, ci, n);
         }
         __syncthreads();                                     // averages ready; column k no longer needed
+        if (tid == 0 && k + NR <= nrun) stage(k + NR);       // into the slot column k just released
         if (n > 0) {
             // 3x3 / 2 max-pool over in-domain averages, first strict maximum, power.
             // A thread owns R = TH/8 vertically adjacent outputs (rows R*warp ..), so
@@ -391,21 +391,21 @@ __global__ void k_level_top(DmGeom g, int l, const unsigned char* __restrict__ v
     top[(long long)p * mw * mh + q] = dm_powf(a, lam);
 }
 
-template <bool COMP, int TH>
+template <bool COMP, int TH, int NR>
 cudaError_t launch_sweep(const DmGeom& g, int l, const CUtensorMap& tm, const dm_pyramid& py, int per_res, long long items,
                          float lam, int* status, cudaStream_t st) {
-    const size_t smem = (size_t)(6 * LevelTile<TH>::KIDF + LevelTile<TH>::AH * AWP) * sizeof(float) + 128;
+    const size_t smem = (size_t)(NR * 2 * LevelTile<TH>::KIDF + LevelTile<TH>::AH * AWP) * sizeof(float) + 128;
     int dev = 0;
     cudaGetDevice(&dev);
     static unsigned long long attr_set = 0;
     if (dev < 64 && !(attr_set & (1ull << dev))) {
-        cudaError_t e = cudaFuncSetAttribute(k_level_sweep<COMP, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_level_sweep<COMP, TH, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_set |= 1ull << dev;
     }
     if (items <= 0) return cudaSuccess;
     if (items > 0x7fffffffLL) return cudaErrorInvalidValue;
-    k_level_sweep<COMP, TH><<<(unsigned)items, LEVEL_THREADS, smem, st>>>(g, l, tm, py.valid[l - 1], per_res,
+    k_level_sweep<COMP, TH, NR><<<(unsigned)items, LEVEL_THREADS, smem, st>>>(g, l, tm, py.valid[l - 1], per_res,
                                                                           const_cast<float*>(py.pooled[l]),
                                                                           const_cast<unsigned char*>(py.amax[l]), lam, status);
     return cudaGetLastError();
@@ -434,12 +434,13 @@ cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& py, float lam, i
             const int per_res = ((g.Lx + S - 1) / S + RUN - 1) / RUN;    // runs per residue class
             const long long items = (long long)tiles * g.Ly * S * per_res;
             cudaError_t e;
+            const bool r2 = py.tune.level_ring == 2;
             if (th == 8)
-                e = py.compensated ? launch_sweep<true, 8>(g, l, tm, py, per_res, items, lam, status, st)
-                                   : launch_sweep<false, 8>(g, l, tm, py, per_res, items, lam, status, st);
+                e = py.compensated ? (r2 ? launch_sweep<true, 8, 2> : launch_sweep<true, 8, 3>)(g, l, tm, py, per_res, items, lam, status, st)
+                                   : (r2 ? launch_sweep<false, 8, 2> : launch_sweep<false, 8, 3>)(g, l, tm, py, per_res, items, lam, status, st);
             else
-                e = py.compensated ? launch_sweep<true, 16>(g, l, tm, py, per_res, items, lam, status, st)
-                                   : launch_sweep<false, 16>(g, l, tm, py, per_res, items, lam, status, st);
+                e = py.compensated ? (r2 ? launch_sweep<true, 16, 2> : launch_sweep<true, 16, 3>)(g, l, tm, py, per_res, items, lam, status, st)
+                                   : (r2 ? launch_sweep<false, 16, 2> : launch_sweep<false, 16, 3>)(g, l, tm, py, per_res, items, lam, status, st);
             if (e != cudaSuccess) return e;
         } else {
             int n = g.dw[l] * g.dh[l];

@@ -302,14 +302,14 @@ def dm_backtrack_noalloc(ctx, pyr, d_out, d_count, stream=None):
 
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
-TUNE_KEYS = ("m_chunk", "level_tile_rows", "bt_ctas_per_sm")
+TUNE_KEYS = ("m_chunk", "level_tile_rows", "bt_ctas_per_sm", "level_ring")
 
 
 def dm_autotune(ctx, d_img1, d_img2, d_ws, stream=None) -> dict:
     """Time the launch-shape candidates on this pair; keep the fastest for its sizes."""
     H1, W1 = d_img1.shape
     H2, W2 = d_img2.shape
-    out = (C.c_int * 3)()
+    out = (C.c_int * 4)()
     st = load().dm_autotune(ctx, _dptr(d_img1), W1, H1, _dptr(d_img2), W2, H2, _dptr(d_ws),
                             d_ws.numel() * d_ws.element_size(), out, _stream_ptr(stream))
     _check(ctx, st, "dm_autotune")
@@ -317,13 +317,13 @@ def dm_autotune(ctx, d_img1, d_img2, d_ws, stream=None) -> dict:
 
 
 def dm_tuned_config(ctx, W1, H1, W2, H2) -> dict:
-    out = (C.c_int * 3)()
+    out = (C.c_int * 4)()
     _check(ctx, load().dm_tuned_config(ctx, W1, H1, W2, H2, out), "dm_tuned_config")
     return dict(zip(TUNE_KEYS, list(out)))
 
 
 def dm_set_tuned_config(ctx, W1, H1, W2, H2, cfg: dict) -> None:
-    arr = (C.c_int * 3)(*[int(cfg[k]) for k in TUNE_KEYS])
+    arr = (C.c_int * 4)(*[int(cfg[k]) for k in TUNE_KEYS])
     _check(ctx, load().dm_set_tuned_config(ctx, W1, H1, W2, H2, arr), "dm_set_tuned_config")
 
 

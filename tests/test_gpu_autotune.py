@@ -13,9 +13,9 @@ from paper_1506_07656_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 SHAPES = [
-    {"m_chunk": 1, "level_tile_rows": 8, "bt_ctas_per_sm": 2},
-    {"m_chunk": 3, "level_tile_rows": 16, "bt_ctas_per_sm": 32},
-    {"m_chunk": 1000, "level_tile_rows": 8, "bt_ctas_per_sm": 1},
+    {"m_chunk": 1, "level_tile_rows": 8, "bt_ctas_per_sm": 2, "level_ring": 3},
+    {"m_chunk": 3, "level_tile_rows": 16, "bt_ctas_per_sm": 32, "level_ring": 2},
+    {"m_chunk": 1000, "level_tile_rows": 8, "bt_ctas_per_sm": 1, "level_ring": 2},
 ]
 
 
@@ -72,13 +72,14 @@ def test_autotune_picks_a_candidate_and_keeps_results(dm_mod, prec):
     ctx = dm.Context(dm.DM_FP32 if prec == "fp32" else dm.DM_BF16)
     try:
         assert dm.dm_tuned_config(ctx.ctx, W, H, W, H) == {"m_chunk": 110, "level_tile_rows": 16,
-                                                            "bt_ctas_per_sm": 8}
+                                                            "bt_ctas_per_sm": 8, "level_ring": 2}
         before = ctx.match(pr.img1, pr.img2).cpu().numpy()
         chosen = ctx.autotune(pr.img1, pr.img2)
         n_mtiles = -(-dm.dm_geometry(W, H, W, H)["n_patch0"] // 128)
         assert chosen["m_chunk"] in {110} | {-(-n_mtiles // k) for k in (1, 2, 3, 4, 6, 8)}
         assert chosen["level_tile_rows"] in (8, 16)
         assert chosen["bt_ctas_per_sm"] in (2, 4, 8, 16, 32)
+        assert chosen["level_ring"] in (2, 3)
         assert dm.dm_tuned_config(ctx.ctx, W, H, W, H) == chosen
         after = ctx.match(pr.img1, pr.img2).cpu().numpy()
         np.testing.assert_array_equal(after, before)
@@ -90,9 +91,10 @@ def test_set_tuned_config_rejects_bad_shapes(dm_mod):
     dm = dm_mod
     ctx = dm.Context(dm.DM_FP32)
     try:
-        for bad in ({"m_chunk": 0, "level_tile_rows": 16, "bt_ctas_per_sm": 8},
-                    {"m_chunk": 4, "level_tile_rows": 12, "bt_ctas_per_sm": 8},
-                    {"m_chunk": 4, "level_tile_rows": 16, "bt_ctas_per_sm": 65}):
+        for bad in ({"m_chunk": 0, "level_tile_rows": 16, "bt_ctas_per_sm": 8, "level_ring": 2},
+                    {"m_chunk": 4, "level_tile_rows": 12, "bt_ctas_per_sm": 8, "level_ring": 2},
+                    {"m_chunk": 4, "level_tile_rows": 16, "bt_ctas_per_sm": 65, "level_ring": 3},
+                    {"m_chunk": 4, "level_tile_rows": 16, "bt_ctas_per_sm": 8, "level_ring": 4}):
             with pytest.raises(dm.DmError):
                 dm.dm_set_tuned_config(ctx.ctx, 64, 48, 64, 48, bad)
     finally:
