@@ -188,13 +188,15 @@ __device__ __forceinline__ float avg1(const float* const* kb, int ay, int ax, co
 }
 
 // Sweep geometry of level l: a CTA owns one tile of TW x TH pooled outputs of a
-// run of RUN lattice patches on one row iy, ix = r + (k0 + k) * S.  Patch ix
+// run of `run` lattice patches on one row iy, ix = r + (k0 + k) * S.  Patch ix
 // has its children in the lattice (or atomic-grid) columns ix - d and ix + d'
 // of level l-1 (level 1: ix - 1 and ix; level l >= 2: ix -+ 2^(l-2)), rows
 // iy - e, iy + e' likewise; the stride S = 2^(l-1) (1 at level 1) makes the
 // right column of one patch the left column of the next, so the run needs
-// RUN + 1 columns of two child windows each instead of 4 windows per patch.
-constexpr int RUN = 8;
+// run + 1 columns of two child windows each instead of 4 windows per patch.
+// Runs of 16 (measured at 1024x436: 3% faster than 8; shorter runs on the
+// small top levels gained nothing).
+__host__ __device__ inline int level_run(int) { return 16; }
 
 __device__ __forceinline__ void child_col_row(const DmGeom& g, int l, int ix, int iy, int* cx_left, int* cy_top, int* step) {
     if (l == 1) { *cx_left = ix - 1; *cy_top = iy - 1; *step = 1; }
@@ -221,7 +223,7 @@ __device__ __forceinline__ int child_at(const DmGeom& g, int l, int cx, int cy, 
 template <bool COMP, int TH, int NR>
 __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, const __grid_constant__ CUtensorMap tmap,
                                                                const unsigned char* __restrict__ vprev,
-                                                               int runs_per_res, float* __restrict__ out,
+                                                               int runs_per_res, int run, float* __restrict__ out,
                                                                unsigned char* __restrict__ amax, float lam,
                                                                int* __restrict__ err) {
     using T = LevelTile<TH>;
@@ -246,10 +248,10 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
     const int rem = item - tile * (g.Ly * per_row);
     const int iy = rem / per_row;
     const int rr = rem - iy * per_row;
-    const int r = rr / runs_per_res, k0 = (rr - r * runs_per_res) * RUN;
+    const int r = rr / runs_per_res, k0 = (rr - r * runs_per_res) * run;
     const int ix0 = r + k0 * S;                              // first patch of the run
     if (ix0 >= g.Lx) return;
-    const int nrun = min(RUN, (g.Lx - 1 - ix0) / S + 1);    // patches in this run
+    const int nrun = min(run, (g.Lx - 1 - ix0) / S + 1);    // patches in this run
     const int rx0 = (tile % tiles_x) * TW, ry0 = (tile / tiles_x) * TH;
     const int qx0 = 2 * rx0 - 1, qy0 = 2 * ry0 - 1;
     const int xa = 2 * rx0 - 4;                              // first staged child column (multiple of 4 floats)
@@ -405,7 +407,7 @@ cudaError_t launch_sweep(const DmGeom& g, int l, const CUtensorMap& tm, const dm
     }
     if (items <= 0) return cudaSuccess;
     if (items > 0x7fffffffLL) return cudaErrorInvalidValue;
-    k_level_sweep<COMP, TH, NR><<<(unsigned)items, LEVEL_THREADS, smem, st>>>(g, l, tm, py.valid[l - 1], per_res,
+    k_level_sweep<COMP, TH, NR><<<(unsigned)items, LEVEL_THREADS, smem, st>>>(g, l, tm, py.valid[l - 1], per_res, level_run(l),
                                                                           const_cast<float*>(py.pooled[l]),
                                                                           const_cast<unsigned char*>(py.amax[l]), lam, status);
     return cudaGetLastError();
@@ -431,7 +433,8 @@ cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& py, float lam, i
                 return cudaErrorNotSupported;
             const int tiles = ((g.dw[l + 1] + TW - 1) / TW) * ((g.dh[l + 1] + th - 1) / th);
             const int S = l == 1 ? 1 : 1 << (l - 1);
-            const int per_res = ((g.Lx + S - 1) / S + RUN - 1) / RUN;    // runs per residue class
+            const int run = level_run(l);
+            const int per_res = ((g.Lx + S - 1) / S + run - 1) / run;    // runs per residue class
             const long long items = (long long)tiles * g.Ly * S * per_res;
             cudaError_t e;
             const bool r2 = py.tune.level_ring == 2;
