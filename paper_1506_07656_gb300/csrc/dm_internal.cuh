@@ -5,6 +5,8 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <atomic>
+
 #include "../../include/dm.h"
 
 #define DM_MAXL 30
@@ -217,6 +219,20 @@ int dm_ctx_device(const dm_ctx* ctx);
 // advanced by each launcher).
 void dm_count_launches(long long n);
 long long dm_launches();
+
+// Opt `kernel` into `bytes` of dynamic shared memory on the current device,
+// once per device (`done` holds one bit per device below 64; other devices
+// set the attribute on every call).  Thread-safe.
+inline cudaError_t dm_smem_opt_in(const void* kernel, int bytes, std::atomic<unsigned long long>& done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
 
 // Tiled tensor map (cuTensorMapEncodeTiled, reached through the runtime's
 // driver entry point): no interleave, no swizzle, zero fill outside the

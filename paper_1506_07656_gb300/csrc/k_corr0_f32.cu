@@ -170,14 +170,9 @@ cudaError_t dm_launch_corr0_f32(const DmGeom& g, const float* d1, const float* d
     int tiles = ((g.dw[1] + PW - 1) / PW) * ((g.dh[1] + PH - 1) / PH);
     int pblocks = (g.P0x * g.P0y + PATCHES - 1) / PATCHES;
     dim3 grid(tiles, pblocks);
-    static unsigned long long attr_set = 0;   // one bit per device: >48 KB dynamic shared memory opted in
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 64 && !(attr_set & (1ull << dev))) {
-        cudaError_t e = cudaFuncSetAttribute(k_corr0_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        attr_set |= 1ull << dev;
-    }
+    static std::atomic<unsigned long long> smem_done{0};   // > 48 KB dynamic shared memory opted in, per device
+    cudaError_t e = dm_smem_opt_in(reinterpret_cast<const void*>(k_corr0_f32), (int)SMEM_BYTES, smem_done);
+    if (e != cudaSuccess) return e;
     k_corr0_f32<<<grid, 256, SMEM_BYTES, st>>>(g, d1, d2, lam, pooled0, amax0);
     dm_count_launches(1);
     return cudaGetLastError();

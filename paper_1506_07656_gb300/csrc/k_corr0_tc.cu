@@ -487,12 +487,9 @@ cudaError_t launch_tc(const DmGeom& g, const unsigned char* apack, const float* 
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    static unsigned long long attr_set = 0;
-    if (dev < 64 && !(attr_set & (1ull << dev))) {
-        cudaError_t e = cudaFuncSetAttribute(k_corr0_tc<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::SMEM);
-        if (e != cudaSuccess) return e;
-        attr_set |= 1ull << dev;
-    }
+    static std::atomic<unsigned long long> smem_done{0};
+    cudaError_t ea = dm_smem_opt_in(reinterpret_cast<const void*>(k_corr0_tc<FMT>), (int)F::SMEM, smem_done);
+    if (ea != cudaSuccess) return ea;
     const int tiles = ((g.dw[1] + PX - 1) / PX) * ((g.dh[1] + PY - 1) / PY);
     const int units = tiles * ((n_mtiles + m_chunk - 1) / m_chunk);
     const int grid = units < nsm ? units : nsm;
@@ -508,14 +505,15 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 
 bool dm_encode_tiled(CUtensorMap* m, CUtensorMapDataType dt, int rank, void* base, const cuuint64_t* dims,
                      const cuuint64_t* strides_bytes, const cuuint32_t* box) {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
+    // looked up once (thread-safe initialisation of a function-local static)
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-    }
+            return reinterpret_cast<EncodeTiledFn>(p);
+        return nullptr;
+    }();
     if (!fn) return false;
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     return fn(m, dt, (cuuint32_t)rank, base, dims, strides_bytes, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,

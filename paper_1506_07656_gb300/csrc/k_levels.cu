@@ -397,14 +397,9 @@ template <bool COMP, int TH, int NR>
 cudaError_t launch_sweep(const DmGeom& g, int l, const CUtensorMap& tm, const dm_pyramid& py, int per_res, long long items,
                          float lam, int* status, cudaStream_t st) {
     const size_t smem = (size_t)(NR * 2 * LevelTile<TH>::KIDF + LevelTile<TH>::AH * AWP) * sizeof(float) + 128;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    static unsigned long long attr_set = 0;
-    if (dev < 64 && !(attr_set & (1ull << dev))) {
-        cudaError_t e = cudaFuncSetAttribute(k_level_sweep<COMP, TH, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set |= 1ull << dev;
-    }
+    static std::atomic<unsigned long long> smem_done{0};
+    cudaError_t ea = dm_smem_opt_in(reinterpret_cast<const void*>(k_level_sweep<COMP, TH, NR>), (int)smem, smem_done);
+    if (ea != cudaSuccess) return ea;
     if (items <= 0) return cudaSuccess;
     if (items > 0x7fffffffLL) return cudaErrorInvalidValue;
     k_level_sweep<COMP, TH, NR><<<(unsigned)items, LEVEL_THREADS, smem, st>>>(g, l, tm, py.valid[l - 1], per_res, level_run(l),
