@@ -60,11 +60,14 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
     return r;
 }
 
-// Knuth TwoSum step of the compensated child sum.
-__device__ __forceinline__ void two_sum_add(float& s, float& comp, float v) {
-    const float t = __fadd_rn(s, v);
-    const float bp = __fsub_rn(t, s);
-    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
+// One step of the compensated child sum (Knuth's TwoSum gives the same bits
+// for any operands): for non-negative operands, which every map value is,
+// Dekker's Fast2Sum on (max, min) is exact, since the first operand is the
+// larger, with one operation fewer.
+__device__ __forceinline__ void fast_two_sum_add(float& s, float& comp, float v) {
+    const float hi = fmaxf(s, v), lo = fminf(s, v);
+    const float t = __fadd_rn(hi, lo);
+    const float err = __fsub_rn(lo, __fsub_rn(t, hi));
     s = t;
     comp = __fadd_rn(comp, err);
 }
@@ -73,7 +76,7 @@ __device__ __forceinline__ void two_sum_add(float& s, float& comp, float v) {
 // sum (0 + v = v exactly, the same as starting from zero).
 template <bool COMP>
 __device__ __forceinline__ void child_add(float& s, float& comp, float v) {
-    if (COMP) two_sum_add(s, comp, v);
+    if (COMP) fast_two_sum_add(s, comp, v);
     else s = __fadd_rn(s, v);
 }
 
