@@ -165,7 +165,15 @@ __device__ __forceinline__ float4 avg4(const float* const* kb, int ay, int ax, c
         float s = 0.0f, comp = 0.0f;
         if (ALL4) {
             s = v[0][c];
-            child_add<COMP>(s, comp, v[1][c]);
+            if (COMP) {
+                // first step: the compensation starts as its error term (0 + err = err;
+                // a -0 there would only meet s + (+-0) = s at the end)
+                const float hi = fmaxf(s, v[1][c]), lo = fminf(s, v[1][c]);
+                s = __fadd_rn(hi, lo);
+                comp = __fsub_rn(lo, __fsub_rn(s, hi));
+            } else {
+                s = __fadd_rn(s, v[1][c]);
+            }
             child_add<COMP>(s, comp, v[2][c]);
             child_add<COMP>(s, comp, v[3][c]);
             r[c] = __fmul_rn(COMP ? __fadd_rn(s, comp) : s, 0.25f);
