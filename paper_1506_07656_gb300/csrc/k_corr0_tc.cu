@@ -429,8 +429,16 @@ k_corr0_tc(DmGeom g, const unsigned char* __restrict__ apack, const float* __res
             const int quad = warp & 3;
             const EpiArgs ea{tmem + ((uint32_t)(quad * 32) << 16), quad * 32 + lane, (warp - 2) >> 2, cx0, cy0, W2, H2,
                              lam, cx0 >= 0 && cy0 >= 0 && cx0 + CX <= W2 && cy0 + CY <= H2};
+            // FP8: 1/16 times the inverse operand scales (powers of two, exact), the
+            // patch's scale loaded before the accumulator wait so its latency hides there
+            const float mult_b = FMT == FMT_E4M3 ? 0.0625f * (1.0f / s_b) : 0.0625f;
             for (int j = 0; j < nt; j++) {
                 const uint32_t ai = acc_it + j, b = ai & 1, aph = (ai >> 1) & 1;
+                float mult = mult_b;
+                if (FMT == FMT_E4M3) {
+                    const int p = (m0 + j) * BM + ea.row;
+                    mult = mult_b * (p < n0 ? __ldg(inv_sa + p) : 1.0f);
+                }
                 const bool ok = mbar_wait(bar_acc_full + 8 * b, aph, abort_flag, err);
                 // the staging buffer of this tile was last used two tiles ago: its
                 // TMA store must have finished reading before it is overwritten
@@ -438,11 +446,6 @@ k_corr0_tc(DmGeom g, const unsigned char* __restrict__ apack, const float* __res
                 epi_barrier();
                 if (*abort_flag || !ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                float mult = 0.0625f;
-                if (FMT == FMT_E4M3) {
-                    const int p = (m0 + j) * BM + ea.row;
-                    mult = 0.0625f * ((p < n0 ? inv_sa[p] : 1.0f) / s_b);
-                }
                 float* stf = sF + b * (OUT_F / 4);
                 unsigned char* stc = sC + b * OUT_C;
                 epilogue_tile(ea, b, bar_acc_empty + 8 * b, mult, stf, stc);
