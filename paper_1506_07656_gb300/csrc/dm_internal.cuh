@@ -115,6 +115,9 @@ __device__ __forceinline__ float dm_powf(float x, float lam) {
     p = __fmaf_rn(p, g, 6.93147181e-01f);
     p = __fmaf_rn(p, g, 1.0f);
     int nt = (int)n1 + (int)n2;
+    // p in [0.70, 1.42]: for nt >= -125 the product p 2^nt is normal, so one
+    // exact multiplication gives the same bits as the two-step scaling below
+    if (nt >= -125) return __fmul_rn(p, dm_pow2i(nt));
     if (nt < -151) return 0.0f;
     int na = nt / 2, nb = nt - na;
     return __fmul_rn(__fmul_rn(p, dm_pow2i(na)), dm_pow2i(nb));

@@ -228,9 +228,10 @@ __device__ __forceinline__ int child_at(const DmGeom& g, int l, int cx, int cy, 
 // child windows run close together in time.  `tmap` maps the pooled maps of
 // level l-1 as a 3-D array (columns dw[l], rows dh[l], patches) with a
 // 72 x (2 TH + 1) x 1 box.  Dynamic shared memory: a ring of NR columns x 2
-// child windows, then the averages.  Per patch of the run: wait for its two
-// columns, form the averages, release the left column (thread 0 starts the
-// loads of the column NR ahead into it), pool, power, store.
+// child windows, then the averages.  Per patch of the run: form the averages
+// from its two columns, release the left column (thread 0 starts the loads of
+// the column NR ahead into it), pool, power, store, wait for the next patch's
+// columns; two barriers per patch.
 template <bool COMP, int TH, int NR>
 __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, const __grid_constant__ CUtensorMap tmap,
                                                                const unsigned char* __restrict__ vprev,
@@ -314,9 +315,9 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
     }
     __syncthreads();
     const bool interior = qx0 >= 0 && qy0 >= 0 && qx0 + AW <= mw && qy0 + AH <= mh;
+    if (!wait_col(0) || !wait_col(1)) { atomicOr(err, 1); abort_s = 1; }
+    __syncthreads();                                         // colc of columns 0, 1 visible; abort agreed
     for (int k = 0; k < nrun; k++) {
-        if (!wait_col(k) || !wait_col(k + 1)) { atomicOr(err, 1); abort_s = 1; }
-        __syncthreads();                                     // colc of columns k, k+1 visible; abort agreed
         if (abort_s) {
             // let the loads already started finish (each wait bounded) before the CTA exits
             if (tid == 0)
@@ -384,7 +385,10 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
                 }
             }
         }
-        __syncthreads();                                     // averages consumed
+        // the next patch's columns k+1, k+2 (waited for by every thread), then one
+        // barrier: averages consumed, colc of those columns visible, abort agreed
+        if (k + 1 < nrun && (!wait_col(k + 1) || !wait_col(k + 2))) { atomicOr(err, 1); abort_s = 1; }
+        __syncthreads();
     }
 }
 
