@@ -237,7 +237,6 @@ void dm_bt_layout(const DmGeom& g, DmBtLayout* o) {
         if (cap > 0xfffffff0ull) cap = 0xfffffff0ull;
         o->cap[l] = (size_t)cap;
         o->table[l] = off; off = dm_align(off + (size_t)cap * 8);
-        o->list[l] = off; off = dm_align(off + (size_t)cap * 4);
     }
     o->bestP = off; off = dm_align(off + (size_t)g.npatch(0) * 8);
     o->bestQ = off; off = dm_align(off + (size_t)((g.W2 + 3) / 4) * ((g.H2 + 3) / 4) * 8);

@@ -150,7 +150,6 @@ struct DmPyrLayout {
 struct DmBtLayout {
     size_t header;                // DmWsHeader
     size_t table[DM_MAXL + 1];    // u64 merge tables, levels 1..L-1
-    size_t list[DM_MAXL + 1];     // u32 slot lists, levels 1..L-1
     size_t cap[DM_MAXL + 1];      // max slots per level
     size_t bestP, bestQ;          // u64 keys
     size_t bytes;

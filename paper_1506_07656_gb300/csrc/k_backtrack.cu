@@ -12,7 +12,7 @@
 // merged frontier is typically 1-5% of a level's pooled map below the top), so
 // the frontier is kept sparse: one open-addressing table per level keyed by
 // (patch, position) with 64-bit slots (key+1) << 32 | score, merged by 64-bit
-// atomicMax, plus a list of the slots taken, which is the next step's input.
+// atomicMax; the next step scans the table in slot order.
 // The active table size is derived on the device from the previous
 // frontier's size, so nothing waits for the host.
 //
@@ -47,7 +47,6 @@ struct BtArgs {
     const unsigned char* amax[DM_MAXL];
     const float* top;
     unsigned long long* table[DM_MAXL + 1];
-    unsigned int* list[DM_MAXL + 1];
     unsigned int capmax[DM_MAXL + 1];
     unsigned long long* bestP;
     unsigned long long* bestQ;
@@ -64,17 +63,31 @@ __device__ __forceinline__ unsigned int warp_agg_inc(unsigned int* ctr) {
     return base + __popc(mask & ((1u << lane) - 1u));
 }
 
+// Home slot of a key: keys are patch * |domain| + position, so 32 consecutive
+// keys are 32 neighbouring positions of one patch on one row.  Such a block of
+// keys keeps its 32 slots together (block index hashed, offset kept), and the
+// expansion scans the table in slot order: a warp then handles neighbouring
+// positions of one patch, whose children's map values and merge slots are
+// neighbours too, so loads and atomics coalesce instead of scattering.
+constexpr unsigned int HT_BLOCK_LOG2 = 5;           // 32 keys per block
+constexpr unsigned long long HT_SLOTS_PER_PREV = 12;  // active slots per tuple of the previous frontier
+
+__device__ __forceinline__ unsigned int ht_home(unsigned int key, unsigned int cap) {
+    const unsigned int nblk = cap >> HT_BLOCK_LOG2;
+    const unsigned int blk = (unsigned int)(((unsigned long long)((key >> HT_BLOCK_LOG2) * 2654435761u) * nblk) >> 32);
+    return (blk << HT_BLOCK_LOG2) | (key & ((1u << HT_BLOCK_LOG2) - 1u));
+}
+
 __device__ __forceinline__ void ht_insert(const BtArgs& a, int lvl, unsigned int cap, unsigned int key, unsigned int sb) {
     unsigned long long* tab = a.table[lvl];
     const unsigned long long packed = ((unsigned long long)(key + 1u) << 32) | sb;
-    unsigned int h = (unsigned int)(((unsigned long long)(key * 2654435761u) * cap) >> 32);
+    unsigned int h = ht_home(key, cap);
     for (unsigned int probe = 0; probe < cap; probe++) {
         unsigned long long cur = __ldcg(tab + h);
         if (cur == 0ull) {
             unsigned long long prev = atomicCAS(tab + h, 0ull, packed);
             if (prev == 0ull) {
-                unsigned int idx = warp_agg_inc(&a.hdr->count[lvl]);
-                a.list[lvl][idx] = h;
+                warp_agg_inc(&a.hdr->count[lvl]);
                 return;
             }
             cur = prev;
@@ -150,13 +163,15 @@ __device__ __forceinline__ void add_arrivals(const BtArgs& a, int n) {
     if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&a.hdr->count[0], (unsigned int)tot);
 }
 
-// Clear the active part of the level-`lvl` table.  Active size: 8x the
-// previous frontier (4 children per tuple, load <= 1/2), within [64, capmax].
+// Clear the active part of the level-`lvl` table.  Active size: 12x the
+// previous frontier (4 children per tuple: load <= 1/3, few collisions
+// between the 32-slot key blocks), a multiple of 32 within [64, capmax].
 __global__ void k_bt_prepare(BtArgs a, int lvl, long long n_top) {
     unsigned long long n_prev = (lvl + 1 == a.g.L) ? (unsigned long long)n_top : a.hdr->count[lvl + 1];
-    unsigned long long cap = n_prev * 8ull;
+    unsigned long long cap = (n_prev * HT_SLOTS_PER_PREV + 31ull) & ~31ull;
     if (cap < 64ull) cap = 64ull;
-    if (cap > a.capmax[lvl]) cap = a.capmax[lvl];
+    const unsigned long long cmax = (unsigned long long)a.capmax[lvl] & ~31ull;
+    if (cap > cmax) cap = cmax;
     if (blockIdx.x == 0 && threadIdx.x == 0) a.hdr->cap[lvl] = (unsigned int)cap;
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
          i += (unsigned long long)gridDim.x * blockDim.x)
@@ -185,24 +200,45 @@ __global__ void k_bt_expand_top(BtArgs a) {
     if (L == 1) add_arrivals(a, arrivals);
 }
 
-// Expansion of level l < L: the merged tuples listed for level l.
+// Expansion of level l < L: the merged tuples of level l, read by scanning the
+// active part of its table in slot order.  Each warp packs the occupied slots
+// it reads into a queue in shared memory and expands them 32 at a time, so its
+// lanes stay busy while the slot order (neighbouring positions of one patch
+// together) is kept.
 __global__ void k_bt_expand(BtArgs a, int l) {
+    __shared__ unsigned long long queue[BT_BLOCK / 32][64];
     const DmGeom& g = a.g;
-    const unsigned int n = a.hdr->count[l];
+    const unsigned int cap = a.hdr->cap[l];
     const unsigned int cap_next = (l - 1 >= 1) ? a.hdr->cap[l - 1] : 0u;
     const unsigned int ds = (unsigned int)g.dsize(l);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long* q = queue[warp];
+    int qn = 0;                                          // warp-uniform queue length
     int arrivals = 0;
-    for (unsigned int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
-        unsigned int i = i0 + threadIdx.x;
-        if (i < n) {
-            unsigned long long v = __ldcg(a.table[l] + a.list[l][i]);
-            unsigned int key = (unsigned int)(v >> 32) - 1u;
-            const unsigned int s = (unsigned int)v;
-            int p = (int)(key / ds);
-            int t = (int)(key % ds);
-            arrivals += expand(a, l, cap_next, p, t % g.dw[l], t / g.dw[l], s);
+    auto run = [&](unsigned long long v) {
+        const unsigned int key = (unsigned int)(v >> 32) - 1u;
+        const unsigned int sc = (unsigned int)v;
+        const int p = (int)(key / ds), t = (int)(key % ds);
+        arrivals += expand(a, l, cap_next, p, t % g.dw[l], t / g.dw[l], sc);
+    };
+    for (unsigned int i0 = blockIdx.x * blockDim.x; i0 < cap; i0 += gridDim.x * blockDim.x) {
+        const unsigned int i = i0 + threadIdx.x;
+        const unsigned long long v = i < cap ? __ldcg(a.table[l] + i) : 0ull;
+        const unsigned int occ = __ballot_sync(0xffffffffu, v != 0ull);
+        if (v != 0ull) q[qn + __popc(occ & ((1u << lane) - 1u))] = v;
+        qn += __popc(occ);
+        __syncwarp();
+        if (qn >= 32) {
+            const unsigned long long w = q[lane];
+            const unsigned long long rest = lane + 32 < qn ? q[lane + 32] : 0ull;
+            __syncwarp();
+            if (lane + 32 < qn) q[lane] = rest;
+            qn -= 32;
+            __syncwarp();
+            run(w);
         }
     }
+    if (lane < qn) run(q[lane]);
     if (l == 1) add_arrivals(a, arrivals);
 }
 
@@ -298,7 +334,6 @@ cudaError_t dm_launch_backtrack(const DmGeom& g, const dm_pyramid& py, const DmB
     a.top = py.top;
     for (int l = 1; l < g.L; l++) {
         a.table[l] = reinterpret_cast<unsigned long long*>(ws + bl.table[l]);
-        a.list[l] = reinterpret_cast<unsigned int*>(ws + bl.list[l]);
         a.capmax[l] = (unsigned int)bl.cap[l];
     }
     a.bestP = reinterpret_cast<unsigned long long*>(ws + bl.bestP);

@@ -5,7 +5,7 @@
 // host application which owns all device memory and forbids allocations after
 // start-up, or loops that must never call cudaMalloc because it can
 // synchronise the device.  For them the scratch of the backtracking step (the
-// per-level merge tables, their slot lists, the BestAt / BestAt' keys and the
+// per-level merge tables, the BestAt / BestAt' keys and the
 // status header) lives in one fixed, file-scope device array instead of a
 // caller workspace.  The kernels are the ones dm_backtrack launches; only the
 // memory they are given differs.
