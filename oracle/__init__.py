@@ -14,6 +14,7 @@ Two builds of one C source (``dm_oracle.c``):
 Functions and the passages they follow:
   descriptors()   Sec. 3.2 "Pixel descriptor"; defaults of Sec. 5.2
   level0()        Eq. 3-4 (unpooled, unrectified bottom-level maps)
+  level1_pooled() Eq. 3-12 for sampled lattice patches of level 1
   pyramid()       Algorithm 1 with Eq. 5-12 and the boundary rule of Sec. 3.2
   backtrack()     Eq. 13-15 (merge by highest score)
   reciprocal()    Eq. 16
@@ -146,6 +147,30 @@ def level0_pooled(d1: np.ndarray, d2: np.ndarray, patches, prec: str = "f32", la
     if rc != 0:
         raise ValueError("level0_pooled oracle failed")
     return out, am
+
+
+def level1_pooled(d1: np.ndarray, d2: np.ndarray, patches, prec: str = "f32", lam: float = DEFAULT_CFG["lam"],
+                  compensated: bool = True):
+    """Level-1 pooled, rectified maps, argmax codes and existence of the listed
+    lattice patches (for sampled checks of pairs too large for pyramid())."""
+    dt = _dtype(prec)
+    d1 = np.ascontiguousarray(d1, dtype=dt)
+    d2 = np.ascontiguousarray(d2, dtype=dt)
+    H1, W1, _ = d1.shape
+    H2, W2, _ = d2.shape
+    g = geometry(W1, H1, W2, H2)
+    pl = np.ascontiguousarray(np.asarray(patches, dtype=np.int32))
+    out = np.zeros((len(pl), g.dh[2], g.dw[2]), dtype=dt)
+    am = np.zeros((len(pl), g.dh[2], g.dw[2]), dtype=np.uint8)
+    ex = np.zeros(len(pl), dtype=np.uint8)
+    lib = _lib(prec)
+    lib.orc_level1_pooled.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int,
+                                      C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+    rc = lib.orc_level1_pooled(_ptr(d1), W1, H1, _ptr(d2), W2, H2, float(lam), int(bool(compensated)), _ptr(pl),
+                               len(pl), _ptr(out), _ptr(am), _ptr(ex))
+    if rc != 0:
+        raise ValueError("level1_pooled oracle failed")
+    return out, am, ex
 
 
 @dataclass

@@ -387,6 +387,50 @@ static void pool_map(const real* src, int sw, int sh, real* dst, uint8_t* am, do
         }
 }
 
+/* Map of one lattice patch at a level >= 1 from its children's pooled maps
+ * (Eq. 12, readings c10, c11, c21): kid[i] = child i's map on the same domain
+ * (mw x mh), NULL where child i does not exist; n = number of existing
+ * children.  FP64: the rectified average (Algorithm 1 order); FP32 mirror: the
+ * unrectified average (the power follows the pooling). */
+static void level_average(const real* const* kid, int n, int mw, int mh, int compensated, real lam, real* map) {
+    (void)lam;
+    (void)compensated;
+    for (int qy = 0; qy < mh; qy++)
+        for (int qx = 0; qx < mw; qx++) {
+#if ORC_F32
+            /* FP32 sum over valid children in order i = 0..3: Knuth TwoSum with a
+             * running compensation, rounded once at the end (compensated), or one
+             * rounding per addition (plain) */
+            float s = 0.0f, comp = 0.0f;
+#else
+            double s = 0.0;
+#endif
+            for (int i = 0; i < 4; i++) {
+                if (!kid[i]) continue;
+                int ox = (i >= 2) ? 1 : -1, oy = (i & 1) ? 1 : -1;
+                int rx = qx + ox, ry = qy + oy;
+                real v = 0;
+                if (rx >= 0 && ry >= 0 && rx < mw && ry < mh) v = kid[i][(size_t)ry * mw + rx];
+#if ORC_F32
+                float t = s + v;
+                if (compensated) {
+                    float bp = t - s;
+                    float err = (s - (t - bp)) + (v - bp);
+                    comp = comp + err;
+                }
+                s = t;
+#else
+                s += v;
+#endif
+            }
+#if ORC_F32
+            map[(size_t)qy * mw + qx] = (s + comp) / (float)n;                 /* rectified after pooling */
+#else
+            map[(size_t)qy * mw + qx] = RPOW(s / (double)n, lam);
+#endif
+        }
+}
+
 /* ------------------------------------------------------------------------- */
 /* The multi-level correlation pyramid (Algorithm 1, Eq. 12, boundary rule)   */
 /*                                                                            */
@@ -449,42 +493,9 @@ int orc_pyramid(const real* d1, int W1, int H1, const real* d2, int W2, int H2, 
                     ci[i] = (c >= 0 && valid[l - 1][c]) ? c : -1;
                     if (ci[i] >= 0) n++;
                 }
-                for (int qy = 0; qy < mh; qy++)
-                    for (int qx = 0; qx < mw; qx++) {
-#if ORC_F32
-                        /* FP32 sum over valid children in order i = 0..3: Knuth TwoSum with a
-                         * running compensation, rounded once at the end (compensated), or one
-                         * rounding per addition (plain) */
-                        float s = 0.0f, comp = 0.0f;
-#else
-                        double s = 0.0;
-#endif
-                        for (int i = 0; i < 4; i++) {
-                            if (ci[i] < 0) continue;
-                            int ox = (i >= 2) ? 1 : -1, oy = (i & 1) ? 1 : -1;
-                            int rx = qx + ox, ry = qy + oy;
-                            real v = 0;
-                            if (rx >= 0 && ry >= 0 && rx < cw && ry < ch)
-                                v = pooled[l - 1][(size_t)ci[i] * cw * ch + (size_t)ry * cw + rx];
-#if ORC_F32
-                            float t = s + v;
-                            if (compensated) {
-                                float bp = t - s;
-                                float err = (s - (t - bp)) + (v - bp);
-                                comp = comp + err;
-                            }
-                            s = t;
-#else
-                            s += v;
-#endif
-                        }
-#if ORC_F32
-                        float a = (s + comp) / (float)n;
-                        map[(size_t)qy * mw + qx] = a;                      /* rectified after pooling */
-#else
-                        map[(size_t)qy * mw + qx] = RPOW(s / (double)n, lam);
-#endif
-                    }
+                const real* kid[4];
+                for (int i = 0; i < 4; i++) kid[i] = ci[i] >= 0 ? pooled[l - 1] + (size_t)ci[i] * cw * ch : NULL;
+                level_average(kid, n, mw, mh, compensated, lam, map);
                 if (l < L) {
                     size_t off = (size_t)p * g.dw[l + 1] * g.dh[l + 1];
                     pool_map(map, mw, mh, pooled[l] + off, amax[l] + off, pgap ? pgap[l] + off : NULL, g.dw[l + 1],
@@ -525,6 +536,63 @@ int orc_level0_pooled(const real* d1, int W1, int H1, const real* d2, int W2, in
         free(map);
     }
     return 0;
+}
+
+/* Level-1 pooled maps and argmax codes of the listed lattice patches only
+ * (same arithmetic as level 1 of orc_pyramid): their children's level-0
+ * pooled maps first, then the shifted average, pooling and power.  out
+ * [n][dh[2]][dw[2]], am likewise; exists[k] = 0 for a patch with no child
+ * (its output is left zero).  For checks of large pairs on sampled patches. */
+int orc_level1_pooled(const real* d1, int W1, int H1, const real* d2, int W2, int H2, double lambda, int compensated,
+                      const int* plist, int n, real* out, uint8_t* am, uint8_t* exists) {
+    geom g;
+    if (make_geom(W1, H1, W2, H2, &g)) return -1;
+    if (g.L < 2) return -1;
+    const real lam = (real)lambda;
+    const int mw = g.dw[1], mh = g.dh[1];
+    int bad = 0;
+#pragma omp parallel
+    {
+        real* c0 = (real*)malloc((size_t)W2 * H2 * sizeof(real));
+        real* kids = (real*)malloc((size_t)4 * mw * mh * sizeof(real));
+        uint8_t* kam = (uint8_t*)malloc((size_t)mw * mh);
+        real* map = (real*)malloc((size_t)mw * mh * sizeof(real));
+        if (!c0 || !kids || !kam || !map) {
+#pragma omp atomic write
+            bad = 1;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (int k = 0; k < n; k++) {
+            if (bad) continue;
+            const int p = plist[k];
+            const real* kid[4];
+            int nk = 0;
+            for (int i = 0; i < 4; i++) {
+                const int c = child_index(&g, 1, p % g.Lx, p / g.Lx, i);
+                kid[i] = NULL;
+                if (c < 0) continue;
+                const int px = 4 * (c % g.P0x) + 2, py = 4 * (c / g.P0x) + 2;
+                for (int ty = 0; ty < H2; ty++)
+                    for (int tx = 0; tx < W2; tx++) {
+                        real v = corr0(d1, W1, H1, d2, W2, H2, px, py, tx, ty);
+                        c0[(size_t)ty * W2 + tx] = ORC_F32 ? v : RPOW(v, lam);
+                    }
+                pool_map(c0, W2, H2, kids + (size_t)i * mw * mh, kam, NULL, mw, mh, ORC_F32, lam);
+                kid[i] = kids + (size_t)i * mw * mh;
+                nk++;
+            }
+            exists[k] = (uint8_t)(nk > 0);
+            if (!nk) continue;
+            level_average(kid, nk, mw, mh, compensated, lam, map);
+            const size_t off = (size_t)k * g.dw[2] * g.dh[2];
+            pool_map(map, mw, mh, out + off, am + off, NULL, g.dw[2], g.dh[2], ORC_F32, lam);
+        }
+        free(c0);
+        free(kids);
+        free(kam);
+        free(map);
+    }
+    return bad ? -2 : 0;
 }
 
 /* ------------------------------------------------------------------------- */

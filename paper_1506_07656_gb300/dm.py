@@ -195,19 +195,25 @@ def dm_pyramid_level(pyr: int, level: int):
                 pitch=pitch.value)
 
 
-def read_level(ws, info):
-    """Copy one pyramid level (values, argmax or None, valid) to host numpy arrays, padding dropped."""
+def read_level(ws, info, patches=None):
+    """Copy one pyramid level (values, argmax or None, valid) to host numpy arrays,
+    padding dropped; `patches` (optional index list) selects patches on the device
+    first, for levels too large to copy whole."""
     import torch
     n, mw, mh, pitch = info["n"], info["mw"], info["mh"], info["pitch"]
     base = ws.data_ptr()
+    sel = None if patches is None else torch.as_tensor(patches, dtype=torch.long, device=ws.device)
     ov = info["vals"] - base
-    vals = ws[ov:ov + n * mh * pitch * 4].view(torch.float32).reshape(n, mh, pitch)[:, :, :mw].cpu().numpy()
+    v = ws[ov:ov + n * mh * pitch * 4].view(torch.float32).reshape(n, mh, pitch)
+    vals = (v if sel is None else v[sel])[:, :, :mw].cpu().numpy()
     am = None
     if info["argmax"]:
         oa = info["argmax"] - base
-        am = ws[oa:oa + n * mh * pitch].reshape(n, mh, pitch)[:, :, :mw].cpu().numpy()
+        a = ws[oa:oa + n * mh * pitch].reshape(n, mh, pitch)
+        am = (a if sel is None else a[sel])[:, :, :mw].cpu().numpy()
     ovl = info["valid"] - base
-    valid = ws[ovl:ovl + n].cpu().numpy()
+    vv = ws[ovl:ovl + n]
+    valid = (vv if sel is None else vv[sel]).cpu().numpy()
     return vals, am, valid
 
 

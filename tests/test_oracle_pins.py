@@ -664,3 +664,21 @@ def test_p12_gradient_finite_differences(oracle_mod, W1, H1, W2, H2, seed):
             assert abs(fd - g.flat[k]) <= 1e-5 * max(1.0, abs(fd)), (which, k, fd, g.flat[k])
             checked += 1
     assert checked >= 40
+
+
+def test_sampled_level1_equals_pyramid(oracle_mod):
+    """The sampled level-1 maps (used to check pairs too large for the whole
+    pyramid) are those of the full pyramid, in both precisions and both
+    child-sum modes, including patches with fewer than four children."""
+    pr = synth.make_pair_smooth(41, 29, seed=8)
+    for prec in ("f32", "f64"):
+        d1 = oracle_mod.descriptors(pr.img1, prec)
+        d2 = oracle_mod.descriptors(pr.img2, prec)
+        for comp in (True, False):
+            pyr = oracle_mod.pyramid(d1, d2, prec, compensated=comp)
+            sel = np.arange(pyr.geom.npatch(1))
+            v, a, e = oracle_mod.level1_pooled(d1, d2, sel, prec, compensated=comp)
+            np.testing.assert_array_equal(e, pyr.valid[1])
+            keep = e.astype(bool)
+            np.testing.assert_array_equal(v[keep], pyr.pooled[1][keep])
+            np.testing.assert_array_equal(a[keep], pyr.argmax[1][keep])
