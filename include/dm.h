@@ -271,14 +271,14 @@ dm_status dm_set_tuned_config(dm_ctx* ctx, int W1, int H1, int W2, int H2, const
  * host application that owns all device memory and forbids allocations after
  * start-up, or latency-critical loops that must never call cudaMalloc (it can
  * synchronise the device).  It does what dm_backtrack does, with the same
- * kernels and results, but its scratch (merge tables, slot lists, BestAt /
+ * kernels and results, but its scratch (merge tables, BestAt /
  * BestAt' keys, status header) is a fixed device array of
  * DM_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads the
  * library holds until the process exits.  The caller still passes the pyramid
  * (input) and d_out / d_count (outputs), as for dm_backtrack.
  *   - Pairs whose backtracking scratch (backtrack_bytes of dm_workspace_bytes)
  *     exceeds DM_NOALLOC_SCRATCH_BYTES are refused with DM_ENOMEM and a message
- *     (32 MiB holds pairs up to about 128 x 96 pixels).
+ *     (32 MiB holds pairs up to about 160 x 120 pixels).
  *   - It calls no cudaMalloc, cudaFree or other allocating routine.  Its first
  *     call on a device looks up the array's device address (cudaGetSymbolAddress)
  *     and caches it; make that first call before any stream capture.
