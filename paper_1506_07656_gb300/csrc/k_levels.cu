@@ -160,28 +160,47 @@ __device__ __forceinline__ float4 avg4(const float* const* kb, int ay, int ax, c
         }
     }
     float r[4];
+    if constexpr (ALL4 && COMP) {
+        // two columns per packed FP32x2 operation: Knuth's TwoSum (6 additions,
+        // bit-identical to the Fast2Sum below, every step correctly rounded per lane)
+        // costs 3.5 instructions per column and step instead of 6
 #pragma unroll
-    for (int c = 0; c < 4; c++) {
-        float s = 0.0f, comp = 0.0f;
-        if (ALL4) {
-            s = v[0][c];
-            if (COMP) {
+        for (int c = 0; c < 4; c += 2) {
+            float2 sv = make_float2(v[0][c], v[0][c + 1]);
+            float2 cp = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int i = 1; i < 4; i++) {
+                const float2 x = make_float2(v[i][c], v[i][c + 1]);
+                const float2 t = __fadd2_rn(sv, x);
+                const float2 bp = __fadd2_rn(t, make_float2(-sv.x, -sv.y));
+                const float2 tb = __fadd2_rn(t, make_float2(-bp.x, -bp.y));
+                const float2 e1 = __fadd2_rn(sv, make_float2(-tb.x, -tb.y));
+                const float2 e2 = __fadd2_rn(x, make_float2(-bp.x, -bp.y));
+                const float2 err = __fadd2_rn(e1, e2);
                 // first step: the compensation starts as its error term (0 + err = err;
                 // a -0 there would only meet s + (+-0) = s at the end)
-                const float hi = fmaxf(s, v[1][c]), lo = fminf(s, v[1][c]);
-                s = __fadd_rn(hi, lo);
-                comp = __fsub_rn(lo, __fsub_rn(s, hi));
-            } else {
-                s = __fadd_rn(s, v[1][c]);
+                cp = i == 1 ? err : __fadd2_rn(cp, err);
+                sv = t;
             }
-            child_add<COMP>(s, comp, v[2][c]);
-            child_add<COMP>(s, comp, v[3][c]);
-            r[c] = __fmul_rn(COMP ? __fadd_rn(s, comp) : s, 0.25f);
-        } else {
+            const float2 a = __fmul2_rn(__fadd2_rn(sv, cp), make_float2(0.25f, 0.25f));
+            r[c] = a.x;
+            r[c + 1] = a.y;
+        }
+    } else {
 #pragma unroll
-            for (int i = 0; i < 4; i++)
-                if (ci[i] >= 0) child_add<COMP>(s, comp, v[i][c]);
-            r[c] = div_n(COMP ? __fadd_rn(s, comp) : s, n);
+        for (int c = 0; c < 4; c++) {
+            float s = 0.0f, comp = 0.0f;
+            if (ALL4) {
+                s = __fadd_rn(v[0][c], v[1][c]);
+                s = __fadd_rn(s, v[2][c]);
+                s = __fadd_rn(s, v[3][c]);
+                r[c] = __fmul_rn(s, 0.25f);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+                    if (ci[i] >= 0) child_add<COMP>(s, comp, v[i][c]);
+                r[c] = div_n(COMP ? __fadd_rn(s, comp) : s, n);
+            }
         }
     }
     return make_float4(r[0], r[1], r[2], r[3]);
