@@ -123,6 +123,63 @@ __device__ __forceinline__ float dm_powf(float x, float lam) {
     return __fmul_rn(__fmul_rn(p, dm_pow2i(na)), dm_pow2i(nb));
 }
 
+// dm_powf on two values at once: the same operations in the same order, the
+// floating-point ones as packed FP32x2 instructions where both lanes do the
+// same thing (each lane rounds exactly as the scalar operation would), so
+// each lane's result has the bits dm_powf gives it.  No packed product feeds a
+// packed addition (see the exponent reduction below).
+__device__ __forceinline__ float2 dm_powf2(float2 x, float lam) {
+    float2 r;
+    // lanes that leave the common path (x <= 0, subnormal x, a subnormal result)
+    // take the scalar recipe
+    const bool fast = x.x >= 1.17549435e-38f && x.y >= 1.17549435e-38f;
+    if (!fast) return make_float2(dm_powf(x.x, lam), dm_powf(x.y, lam));
+    const uint32_t b0 = __float_as_uint(x.x), b1 = __float_as_uint(x.y);
+    int e0 = (int)((b0 >> 23) & 0xffu) - 127, e1 = (int)((b1 >> 23) & 0xffu) - 127;
+    float m0 = __uint_as_float((b0 & 0x7fffffu) | 0x3f800000u), m1 = __uint_as_float((b1 & 0x7fffffu) | 0x3f800000u);
+    if (m0 > 1.41421356f) { m0 = __fmul_rn(m0, 0.5f); e0 = e0 + 1; }
+    if (m1 > 1.41421356f) { m1 = __fmul_rn(m1, 0.5f); e1 = e1 + 1; }
+    const float2 m = make_float2(m0, m1);
+    const float2 num = __fadd2_rn(m, make_float2(-1.0f, -1.0f));
+    const float2 den = __fadd2_rn(m, make_float2(1.0f, 1.0f));
+    const float2 f = make_float2(__fdiv_rn(num.x, den.x), __fdiv_rn(num.y, den.y));
+    const float2 f2 = __fmul2_rn(f, f);
+    float2 s = make_float2(7.69230769e-02f, 7.69230769e-02f);
+    s = __ffma2_rn(s, f2, make_float2(9.09090909e-02f, 9.09090909e-02f));
+    s = __ffma2_rn(s, f2, make_float2(1.11111111e-01f, 1.11111111e-01f));
+    s = __ffma2_rn(s, f2, make_float2(1.42857143e-01f, 1.42857143e-01f));
+    s = __ffma2_rn(s, f2, make_float2(2.00000000e-01f, 2.00000000e-01f));
+    s = __ffma2_rn(s, f2, make_float2(3.33333333e-01f, 3.33333333e-01f));
+    s = __ffma2_rn(s, f2, make_float2(1.0f, 1.0f));
+    const float2 l2m = __fmul2_rn(__fmul2_rn(make_float2(2.88539008f, 2.88539008f), f), s);
+    const float2 fe = make_float2((float)e0, (float)e1);
+    const float2 lam2 = make_float2(lam, lam);
+    const float2 a = __fmul2_rn(lam2, fe);
+    const float2 aerr = __ffma2_rn(lam2, fe, make_float2(-a.x, -a.y));
+    const float2 n1 = make_float2(rintf(a.x), rintf(a.y));
+    // the product lam * log2 m feeds an addition: it is formed by scalar
+    // multiplications, since a packed multiplication followed by a packed
+    // addition was found fused into one rounding despite contraction being off
+    const float2 lg = make_float2(__fmul_rn(lam, l2m.x), __fmul_rn(lam, l2m.y));
+    float2 g = __fadd2_rn(__fadd2_rn(__fadd2_rn(a, make_float2(-n1.x, -n1.y)), aerr), lg);
+    const float2 n2 = make_float2(rintf(g.x), rintf(g.y));
+    g = __fadd2_rn(g, make_float2(-n2.x, -n2.y));
+    float2 p = make_float2(1.52527338e-05f, 1.52527338e-05f);
+    p = __ffma2_rn(p, g, make_float2(1.54035304e-04f, 1.54035304e-04f));
+    p = __ffma2_rn(p, g, make_float2(1.33335581e-03f, 1.33335581e-03f));
+    p = __ffma2_rn(p, g, make_float2(9.61812911e-03f, 9.61812911e-03f));
+    p = __ffma2_rn(p, g, make_float2(5.55041087e-02f, 5.55041087e-02f));
+    p = __ffma2_rn(p, g, make_float2(2.40226507e-01f, 2.40226507e-01f));
+    p = __ffma2_rn(p, g, make_float2(6.93147181e-01f, 6.93147181e-01f));
+    p = __ffma2_rn(p, g, make_float2(1.0f, 1.0f));
+    const int nt0 = (int)n1.x + (int)n2.x, nt1 = (int)n1.y + (int)n2.y;
+    if (nt0 >= -125 && nt1 >= -125) return __fmul2_rn(p, make_float2(dm_pow2i(nt0), dm_pow2i(nt1)));
+    // a result below the normal range: the scalar two-step scaling per lane
+    r.x = dm_powf(x.x, lam);
+    r.y = dm_powf(x.y, lam);
+    return r;
+}
+
 // ---------------------------------------------------------------------------
 // Workspace layouts (all offsets 256-byte aligned).
 // ---------------------------------------------------------------------------

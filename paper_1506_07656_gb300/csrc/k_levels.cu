@@ -391,16 +391,30 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
                     hv[kk] = m;
                     hc[kk] = a0 == m ? 0 : (a1 == m ? 1 : 2);
                 }
+                float best[R], pw[R];
+                int code[R];
+#pragma unroll
+                for (int j = 0; j < R; j++) {
+                    // first row holding the maximum (m_y = -1, 0, 1): the first maximum in scan order
+                    best[j] = fmax3(hv[2 * j], hv[2 * j + 1], hv[2 * j + 2]);
+                    code[j] = hv[2 * j] == best[j] ? hc[2 * j] : (hv[2 * j + 1] == best[j] ? 3 + hc[2 * j + 1] : 6 + hc[2 * j + 2]);
+                }
+                // the power of two outputs per packed evaluation (rows past the map
+                // are evaluated on whatever the tile holds there and not stored)
+#pragma unroll
+                for (int j = 0; j + 1 < R; j += 2) {
+                    const float2 v = dm_powf2(make_float2(best[j], best[j + 1]), lam);
+                    pw[j] = v.x;
+                    pw[j + 1] = v.y;
+                }
+                if constexpr (R % 2 == 1) pw[R - 1] = dm_powf(best[R - 1], lam);
 #pragma unroll
                 for (int j = 0; j < R; j++) {
                     const int ry = ry0 + ty0 + j;
                     if (ry >= oh) break;
-                    // first row holding the maximum (m_y = -1, 0, 1): the first maximum in scan order
-                    const float best = fmax3(hv[2 * j], hv[2 * j + 1], hv[2 * j + 2]);
-                    const int code = hv[2 * j] == best ? hc[2 * j] : (hv[2 * j + 1] == best ? 3 + hc[2 * j + 1] : 6 + hc[2 * j + 2]);
                     const long long o = ((long long)p * oh + ry) * opitch + rx;
-                    out[o] = dm_powf(best, lam);
-                    amax[o] = (unsigned char)code;
+                    out[o] = pw[j];
+                    amax[o] = (unsigned char)code[j];
                 }
             }
         }
