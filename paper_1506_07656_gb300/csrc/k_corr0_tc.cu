@@ -35,9 +35,10 @@
 // warp 1 allocates TMEM and one lane issues the MMAs and commits, warps 2-17
 // drain the accumulators: four warps per TMEM lane quadrant, each owning four
 // of the sixteen pooled columns (C0 columns 8w'..8w'+8) over the three pooled
-// rows: 14 tcgen05.ld, one wait, pool with the first-strict-maximum argmax
-// rule (scan my = -1..1, then mx), release the accumulator, raise to lambda
-// (MUFU-based power), stage, store through TMA.
+// rows: 14 tcgen05.ld in three batches of rows (each batch in flight while the
+// rows before it are pooled), pool with the first-strict-maximum argmax rule
+// (scan my = -1..1, then mx), release the accumulator after the last batch,
+// raise to lambda (MUFU-based power), stage, store through TMA.
 // FP8 form: the same kernel with E4M3 operands (tcgen05.mma kind::f8f6f4,
 // K padded 144 -> 160, five MMAs of K = 32).  Each patch vector is scaled by a
 // power of two that brings its largest entry into (224, 448] (E4M3's top
@@ -235,77 +236,110 @@ struct EpiArgs {
     bool interior;      // every C0 position of the N-tile lies inside I'
 };
 
+// Accumulator row ly of this thread's part (C0 columns 8 part .. 8 part + 8):
+// one 8-column and one 1-column tensor-memory load, completed by the next
+// tcgen05.wait::ld.
+__device__ __forceinline__ void tmem_row(uint32_t taddr, int ly, uint32_t (&r)[9]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr + ly * CX));
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r[8]) : "r"(taddr + ly * CX + 8));
+}
+
+// After tcgen05.wait::ld: an empty volatile statement that "rewrites" the row,
+// so no use of the loaded registers can be scheduled before the wait.
+__device__ __forceinline__ void tmem_row_ready(uint32_t (&r)[9]) {
+    asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                      "+r"(r[8]));
+}
+
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Horizontal step of the separable 3x3 / 2 pooling for C0 row ly: the
+// 3-maxima of the column triples (2k, 2k+1, 2k+2) and the first column
+// holding each (out-of-image positions are -inf).
+__device__ __forceinline__ void pool_row(const EpiArgs& e, int tx0, int ly, const uint32_t (&r)[9], float (&h)[4], int (&hc)[4]) {
+    float v[9];
+#pragma unroll
+    for (int c = 0; c < 9; c++) v[c] = __uint_as_float(r[c]);
+    if (!e.interior) {
+        const int ty = e.cy0 + ly;
+        const bool rin = ty >= 0 && ty < e.H2;
+#pragma unroll
+        for (int c = 0; c < 9; c++) {
+            const int tx = tx0 + c;
+            if (!(rin && tx >= 0 && tx < e.W2)) v[c] = -INFINITY;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const float m = fmax3(v[2 * k], v[2 * k + 1], v[2 * k + 2]);
+        h[k] = m;
+        hc[k] = v[2 * k] == m ? 0 : (v[2 * k + 1] == m ? 1 : 2);
+    }
+}
+
+// Vertical step for pooled row y (C0 rows 2y, 2y+1, 2y+2 = m_y -1, 0, +1; the
+// first row holding the maximum, so the first maximum in scan order), the
+// power, and the staging of the 4 values and codes.
+__device__ __forceinline__ void pool_out(const EpiArgs& e, int y, float mult, const float (&h)[CY][4], const int (&hc)[CY][4],
+                                         float* stage_f, unsigned char* stage_c) {
+    float f[4];
+    uint32_t codes = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const float m = fmax3(h[2 * y][k], h[2 * y + 1][k], h[2 * y + 2][k]);
+        const int code = h[2 * y][k] == m ? hc[2 * y][k] : (h[2 * y + 1][k] == m ? 3 + hc[2 * y + 1][k] : 6 + hc[2 * y + 2][k]);
+        f[k] = __powf(m * mult, e.lam);
+        codes |= (uint32_t)code << (8 * k);
+    }
+    // staging layout = the TMA box [patch][row][16 columns]
+    const int o = (e.row * PY + y) * PX + 4 * e.part;
+    *reinterpret_cast<float4*>(stage_f + o) = make_float4(f[0], f[1], f[2], f[3]);
+    *reinterpret_cast<uint32_t*>(stage_c + o) = codes;
+}
+
 // Pool this thread's 4 x 3 outputs of one accumulator, release the
 // accumulator, and write the powered values and codes to the staging buffer.
 // `mult` turns an accumulator value into C0 (1/16, times the inverse operand
 // scales of the FP8 form; positive, so pooling on raw accumulators is exact).
+// The seven accumulator rows are read in three batches (rows 0-2, 3-4, 5-6):
+// each batch's loads are in flight while the rows before it are pooled, and
+// pooled row y is finished as soon as its C0 rows 2y .. 2y+2 are in.
 __device__ __forceinline__ void epilogue_tile(const EpiArgs& e, uint32_t b, uint32_t bar_empty, float mult,
                                               float* stage_f, unsigned char* stage_c) {
     uint32_t r[CY][9];
-    const uint32_t taddr = e.taddr + b * 256 + 8 * e.part;
-#pragma unroll
-    for (int ly = 0; ly < CY; ly++) {
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                     : "=r"(r[ly][0]), "=r"(r[ly][1]), "=r"(r[ly][2]), "=r"(r[ly][3]), "=r"(r[ly][4]), "=r"(r[ly][5]),
-                       "=r"(r[ly][6]), "=r"(r[ly][7])
-                     : "r"(taddr + ly * CX));
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r[ly][8]) : "r"(taddr + ly * CX + 8));
-    }
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    mbar_arrive(bar_empty);
-
-    // separable 3x3 / 2 pooling: per C0 row the 3-maxima of column triples
-    // (2k, 2k+1, 2k+2) with the first column holding it, then per pooled row
-    // the maximum of the three row maxima (C0 rows 2y, 2y+1, 2y+2 = m_y -1, 0,
-    // +1) with the first row holding it: the first maximum in scan order
     float h[CY][4];
     int hc[CY][4];
+    const uint32_t taddr = e.taddr + b * 256 + 8 * e.part;
     const int tx0 = e.cx0 + 8 * e.part;
 #pragma unroll
-    for (int ly = 0; ly < CY; ly++) {
-        float v[9];
+    for (int ly = 0; ly < 3; ly++) tmem_row(taddr, ly, r[ly]);
+    tmem_wait();
 #pragma unroll
-        for (int c = 0; c < 9; c++) v[c] = __uint_as_float(r[ly][c]);
-        if (!e.interior) {
-            const int ty = e.cy0 + ly;
-            const bool rin = ty >= 0 && ty < e.H2;
+    for (int ly = 0; ly < 3; ly++) tmem_row_ready(r[ly]);
 #pragma unroll
-            for (int c = 0; c < 9; c++) {
-                const int tx = tx0 + c;
-                if (!(rin && tx >= 0 && tx < e.W2)) v[c] = -INFINITY;
-            }
-        }
+    for (int ly = 3; ly < 5; ly++) tmem_row(taddr, ly, r[ly]);
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const float m = fmax3(v[2 * k], v[2 * k + 1], v[2 * k + 2]);
-            h[ly][k] = m;
-            hc[ly][k] = v[2 * k] == m ? 0 : (v[2 * k + 1] == m ? 1 : 2);
-        }
-    }
-    float best[PY][4];
-    int code[PY][4];
+    for (int ly = 0; ly < 3; ly++) pool_row(e, tx0, ly, r[ly], h[ly], hc[ly]);
+    pool_out(e, 0, mult, h, hc, stage_f, stage_c);
+    tmem_wait();
 #pragma unroll
-    for (int y = 0; y < PY; y++)
+    for (int ly = 3; ly < 5; ly++) tmem_row_ready(r[ly]);
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const float m = fmax3(h[2 * y][k], h[2 * y + 1][k], h[2 * y + 2][k]);
-            best[y][k] = m;
-            code[y][k] = h[2 * y][k] == m ? hc[2 * y][k] : (h[2 * y + 1][k] == m ? 3 + hc[2 * y + 1][k] : 6 + hc[2 * y + 2][k]);
-        }
-    // staging layout = the TMA box [patch][row][16 columns]
+    for (int ly = 5; ly < 7; ly++) tmem_row(taddr, ly, r[ly]);
 #pragma unroll
-    for (int y = 0; y < PY; y++) {
-        float4 f;
-        f.x = __powf(best[y][0] * mult, e.lam);
-        f.y = __powf(best[y][1] * mult, e.lam);
-        f.z = __powf(best[y][2] * mult, e.lam);
-        f.w = __powf(best[y][3] * mult, e.lam);
-        const int o = (e.row * PY + y) * PX + 4 * e.part;
-        *reinterpret_cast<float4*>(stage_f + o) = f;
-        *reinterpret_cast<uint32_t*>(stage_c + o) =
-            (uint32_t)code[y][0] | ((uint32_t)code[y][1] << 8) | ((uint32_t)code[y][2] << 16) | ((uint32_t)code[y][3] << 24);
-    }
+    for (int ly = 3; ly < 5; ly++) pool_row(e, tx0, ly, r[ly], h[ly], hc[ly]);
+    pool_out(e, 1, mult, h, hc, stage_f, stage_c);
+    tmem_wait();
+#pragma unroll
+    for (int ly = 5; ly < 7; ly++) tmem_row_ready(r[ly]);
+    // every load of this accumulator is complete: hand it back to the MMA warp
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    mbar_arrive(bar_empty);
+#pragma unroll
+    for (int ly = 5; ly < 7; ly++) pool_row(e, tx0, ly, r[ly], h[ly], hc[ly]);
+    pool_out(e, 2, mult, h, hc, stage_f, stage_c);
 }
 
 template <int FMT>
