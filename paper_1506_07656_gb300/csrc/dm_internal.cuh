@@ -294,11 +294,13 @@ inline cudaError_t dm_smem_opt_in(const void* kernel, int bytes, std::atomic<uns
 }
 
 // Tiled tensor map (cuTensorMapEncodeTiled, reached through the runtime's
-// driver entry point): no interleave, no swizzle, zero fill outside the
-// extent, element strides 1.  False if the entry point is unavailable or the
-// map is rejected (base not 16-byte aligned, stride not a multiple of 16 B, ...).
+// driver entry point): no interleave, the given shared-memory swizzle (none by
+// default), zero fill outside the extent, element strides 1.  False if the
+// entry point is unavailable or the map is rejected (base not 16-byte aligned,
+// stride not a multiple of 16 B, box row wider than the swizzle span, ...).
 bool dm_encode_tiled(CUtensorMap* m, CUtensorMapDataType dt, int rank, void* base, const cuuint64_t* dims,
-                     const cuuint64_t* strides_bytes, const cuuint32_t* box);
+                     const cuuint64_t* strides_bytes, const cuuint32_t* box,
+                     CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_NONE);
 
 // Kernel launchers (return cudaGetLastError()).
 cudaError_t dm_launch_descriptors(const DmDescParams& prm, const float* img, int W, int H, float* desc,

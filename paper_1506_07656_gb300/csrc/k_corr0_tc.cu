@@ -293,10 +293,17 @@ __device__ __forceinline__ void pool_out(const EpiArgs& e, int y, float mult, co
         f[k] = __powf(m * mult, e.lam);
         codes |= (uint32_t)code << (8 * k);
     }
-    // staging layout = the TMA box [patch][row][16 columns]
-    const int o = (e.row * PY + y) * PX + 4 * e.part;
-    *reinterpret_cast<float4*>(stage_f + o) = make_float4(f[0], f[1], f[2], f[3]);
-    *reinterpret_cast<uint32_t*>(stage_c + o) = codes;
+    // staging layout = the TMA box [patch][row][16 columns].  The values' box
+    // rows (64 bytes, four 16-byte chunks) are staged with the tensor map's
+    // 64-byte swizzle: the 16-byte chunk index (shared address bits 4-5) is
+    // XORed with address bits 7-8 of the row.  Lanes hold consecutive patches,
+    // box rows 3 apart, so without it the 16-byte stores of a quarter warp
+    // would hit the same four banks four times.
+    const int R = e.row * PY + y;
+    const uint32_t row_addr = smem_u32(stage_f) + (uint32_t)R * (PX * 4);
+    const int chunk = e.part ^ (int)((row_addr >> 7) & 3u);
+    *reinterpret_cast<float4*>(stage_f + R * PX + 4 * chunk) = make_float4(f[0], f[1], f[2], f[3]);
+    *reinterpret_cast<uint32_t*>(stage_c + R * PX + 4 * e.part) = codes;
 }
 
 // Pool this thread's 4 x 3 outputs of one accumulator, release the
@@ -473,18 +480,21 @@ k_corr0_tc(DmGeom g, const unsigned char* __restrict__ apack, const float* __res
                     const int p = (m0 + j) * BM + ea.row;
                     mult = mult_b * (p < n0 ? __ldg(inv_sa + p) : 1.0f);
                 }
-                const bool ok = mbar_wait(bar_acc_full + 8 * b, aph, abort_flag, err);
-                // the staging buffer of this tile was last used two tiles ago: its
-                // TMA store must have finished reading before it is overwritten
-                if (store_leader) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                // a failed (bounded) wait has set the abort flag: this thread skips the
+                // tile but still meets the barrier, after which every thread sees the flag
+                if (mbar_wait(bar_acc_full + 8 * b, aph, abort_flag, err)) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    epilogue_tile(ea, b, bar_acc_empty + 8 * b, mult, sF + b * (OUT_F / 4), sC + b * OUT_C);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                }
+                // one barrier per tile: before it the leader also waits until the store
+                // of the previous tile has read its staging buffer, which the next tile
+                // fills (the staging is double-buffered)
+                if (store_leader) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
                 epi_barrier();
-                if (*abort_flag || !ok) break;
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                if (*abort_flag) break;
                 float* stf = sF + b * (OUT_F / 4);
                 unsigned char* stc = sC + b * OUT_C;
-                epilogue_tile(ea, b, bar_acc_empty + 8 * b, mult, stf, stc);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                epi_barrier();
                 if (store_leader) {
                     const int z = (m0 + j) * BM;
                     asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"
@@ -508,12 +518,12 @@ k_corr0_tc(DmGeom g, const unsigned char* __restrict__ apack, const float* __res
 }
 
 // 3-D map of a pooled level-0 array [n0][mh][pitch] (elements of `esize` bytes),
-// logical extent mw x mh x n0, box 16 x 3 x 128.
-bool make_map(CUtensorMap* m, void* base, CUtensorMapDataType dt, int esize, const DmGeom& g) {
+// logical extent mw x mh x n0, box 16 x 3 x 128, staged with the given swizzle.
+bool make_map(CUtensorMap* m, void* base, CUtensorMapDataType dt, int esize, const DmGeom& g, CUtensorMapSwizzle sw) {
     const cuuint64_t dims[3] = {(cuuint64_t)g.dw[1], (cuuint64_t)g.dh[1], (cuuint64_t)g.npatch(0)};
     const cuuint64_t strides[2] = {(cuuint64_t)g.pitch(1) * esize, (cuuint64_t)g.pitch(1) * g.dh[1] * esize};
     const cuuint32_t box[3] = {PX, PY, BM};
-    return dm_encode_tiled(m, dt, 3, base, dims, strides, box);
+    return dm_encode_tiled(m, dt, 3, base, dims, strides, box, sw);
 }
 
 template <int FMT>
@@ -541,7 +551,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 bool dm_encode_tiled(CUtensorMap* m, CUtensorMapDataType dt, int rank, void* base, const cuuint64_t* dims,
-                     const cuuint64_t* strides_bytes, const cuuint32_t* box) {
+                     const cuuint64_t* strides_bytes, const cuuint32_t* box, CUtensorMapSwizzle swizzle) {
     // looked up once (thread-safe initialisation of a function-local static)
     static const EncodeTiledFn fn = []() -> EncodeTiledFn {
         void* p = nullptr;
@@ -554,7 +564,7 @@ bool dm_encode_tiled(CUtensorMap* m, CUtensorMapDataType dt, int rank, void* bas
     if (!fn) return false;
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     return fn(m, dt, (cuuint32_t)rank, base, dims, strides_bytes, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+              swizzle, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // Packed-operand buffer: A tiles; FP8 form also the per-patch inverse scales
@@ -572,8 +582,9 @@ cudaError_t dm_launch_corr0_tc(const DmGeom& g, int precision, const float* d1, 
     const int n_mtiles = (n0 + BM - 1) / BM;
     if (m_chunk < 1) m_chunk = 1;
     CUtensorMap mf, mc;
-    if (!make_map(&mf, pooled0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g) ||
-        !make_map(&mc, amax0, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, g))
+    // values: 64-byte box rows staged with the 64-byte swizzle (see pool_out)
+    if (!make_map(&mf, pooled0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, CU_TENSOR_MAP_SWIZZLE_64B) ||
+        !make_map(&mc, amax0, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, g, CU_TENSOR_MAP_SWIZZLE_NONE))
         return cudaErrorNotSupported;
     unsigned char* apack = reinterpret_cast<unsigned char*>(abuf);
     cudaError_t e;
