@@ -257,8 +257,9 @@ dm_status dm_set_batch_lanes(dm_ctx* ctx, int lanes);
  * a graph).  chosen: 4 ints out, or NULL.  The paper has no counterpart. */
 dm_status dm_autotune(dm_ctx* ctx, const float* d_img1, int W1, int H1, const float* d_img2, int W2, int H2,
                       void* d_ws, size_t ws_bytes, int* chosen, void* stream);
-/* The launch shapes used for pairs of these sizes (the defaults 110, 16, 8, 2
- * until dm_autotune has run on them): 4 ints as for dm_autotune. */
+/* The launch shapes used for pairs of these sizes (until dm_autotune has run
+ * on them the defaults: all M-tiles in one work unit, 16, 8, 2): 4 ints as
+ * for dm_autotune. */
 dm_status dm_tuned_config(dm_ctx* ctx, int W1, int H1, int W2, int H2, int* chosen);
 /* Set the launch shapes for pairs of these sizes (e.g. a choice saved from an
  * earlier dm_autotune): chosen[0] >= 1, chosen[1] in {8, 16}, chosen[2] in

@@ -245,7 +245,10 @@ struct DmTune {
     int bt_mult;
     int level_ring;
 };
-constexpr DmTune DM_TUNE_DEFAULT = {110, 16, 8, 2};
+// Defaults until tuned: all M-tiles of the pair in one work unit (the N-tiles
+// are the units; measured at 1024x436 the most robust choice for BF16), tile
+// rows 16, 8 CTAs per SM, a ring of 2.
+inline DmTune dm_tune_default(const DmGeom& g) { return DmTune{(g.npatch(0) + 127) / 128, 16, 8, 2}; }
 
 // Pyramid handle (host side).
 struct dm_pyramid {
