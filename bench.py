@@ -31,7 +31,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "pairs/s at 1024x436"
+
+def metric_name(W: int, H: int) -> str:
+    """The metric: image pairs matched per second at the bench's pair size."""
+    return f"pairs/s at {W}x{H}"
 
 
 def _args():
@@ -186,7 +189,7 @@ def run_reference(a):
     sample = (f"each step: FP32 oracle level-0 correlation+pooling of {k} random atomic patches of {n0} "
               f"(one {a.width}x{a.height} pair), scaled to the whole pair")
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": a.gpus,
+        "impl": "reference", "metric": metric_name(a.width, a.height), "value": value, "unit": "pairs/s", "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": per_pair * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"one {a.width}x{a.height} pair, value noise + smooth warp (max 120 px)",
@@ -401,11 +404,11 @@ def _measure_batch_uniform(dm, torch, dist, ctx, a, world, local, rank, W, H, np
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
 # ncu captures summarised in profiles/ (the full workload is too large to
 # capture), scaled to the 1024x436 workload: level 0 from a 512x224 launch by the
-# number of pooled outputs (1.111 GB x 15.1); the level pass from its level-1
+# number of pooled outputs (BF16 1.111 GB, FP8 1.071 GB, x 15.1); the level pass from its level-1
 # launch at 640x272 by the algorithmic bytes of the whole launch set (same
 # traffic/algorithmic ratio, 4.316 / 2.498 GB = 1.73).  None where no capture of
 # the current kernel version exists.
-TRAFFIC_1024x436 = {"level0_bf16": 16.8e9, "level0_fp8": None, "level0_fp32": None, "levels": 37.7e9}
+TRAFFIC_1024x436 = {"level0_bf16": 16.8e9, "level0_fp8": 16.2e9, "level0_fp32": None, "levels": 37.7e9}
 
 
 def _prec_code(dm, name):
@@ -532,7 +535,7 @@ def run_ours(a):
                         f"pyramid and backtracking in FP32")
             status, matches, shapes = r["status"], r["matches"], r["tuned"]
         line = {
-            "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": a.steps,
+            "metric": metric_name(W, H), "value": value, "unit": "pairs/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"bf16": "bf16", "fp8": "fp8_e4m3", "fp32": "f32"}[head], "data": "synthetic",
             "config": {"workload": workload, "width": W, "height": H, "precision": head, "L": geo["L"],
