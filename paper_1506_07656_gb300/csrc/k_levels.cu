@@ -359,7 +359,10 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
                 const float4 a = (n == 4) ? avg4<COMP, true>(kb, ay, ax, ci, n) : avg4<COMP, false>(kb, ay, ax, ci, n);
                 *reinterpret_cast<float4*>(&avg[ay][ax]) = a;
             }
-            for (int ay = tid; ay < AH; ay += LEVEL_THREADS) avg[ay][AW - 1] = avg1<COMP>(kb, ay, AW - 1, ci, n);
+            // the last column's averages go to warps 2-3: warp 0 already forms the
+            // 4-column groups of the last row (AH * G4 = 256 * k + 16)
+            for (int ay = (tid + LEVEL_THREADS - 64) % LEVEL_THREADS; ay < AH; ay += LEVEL_THREADS)
+                avg[ay][AW - 1] = avg1<COMP>(kb, ay, AW - 1, ci, n);
         }
         __syncthreads();                                     // averages ready; column k no longer needed
         if (tid == 0 && k + NR <= nrun) stage(k + NR);       // into the slot column k just released
