@@ -152,13 +152,25 @@ k_corr0_f32(DmGeom g, const float* __restrict__ d1, const float* __restrict__ d2
     }
     __syncthreads();
     const int mw = g.dw[1], mh = g.dh[1], pitch = g.pitch(1);
-    for (int e = tid; e < PATCHES * PH * PW; e += 256) {
+    auto store = [&](int e, float v) {
         int kk = e % PW, i = (e / PW) % PH, pl = e / (PW * PH);
         int p = p_base + pl, rx = rx0 + kk, ry = ry0 + i;
         if (p < n0 && rx < mw && ry < mh) {
             long long o = ((long long)p * mh + ry) * pitch + rx;
-            pooled0[o] = dm_powf(best_s[e], lam);
+            pooled0[o] = v;
             amax0[o] = code_s[e];
+        }
+    };
+    // the power of two staged maxima (entries e and e + 256) per packed
+    // evaluation, bit-identical to dm_powf lane by lane
+    constexpr int NOUT = PATCHES * PH * PW;
+    for (int e = tid; e < NOUT; e += 512) {
+        if (e + 256 < NOUT) {
+            const float2 v = dm_powf2(make_float2(best_s[e], best_s[e + 256]), lam);
+            store(e, v.x);
+            store(e + 256, v.y);
+        } else {
+            store(e, dm_powf(best_s[e], lam));
         }
     }
 }
