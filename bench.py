@@ -404,11 +404,11 @@ def _measure_batch_uniform(dm, torch, dist, ctx, a, world, local, rank, W, H, np
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
 # ncu captures summarised in profiles/ (the full workload is too large to
 # capture), scaled to the 1024x436 workload: level 0 from a 512x224 launch by the
-# number of pooled outputs (BF16 1.111 GB, FP8 1.071 GB, x 15.1); the level pass from its level-1
+# number of pooled outputs (BF16 1.111 GB, FP8 1.071 GB, FP32 0.980 GB, x 15.1); the level pass from its level-1
 # launch at 640x272 by the algorithmic bytes of the whole launch set (same
 # traffic/algorithmic ratio, 4.316 / 2.498 GB = 1.73).  None where no capture of
 # the current kernel version exists.
-TRAFFIC_1024x436 = {"level0_bf16": 16.8e9, "level0_fp8": 16.2e9, "level0_fp32": None, "levels": 37.7e9}
+TRAFFIC_1024x436 = {"level0_bf16": 16.8e9, "level0_fp8": 16.2e9, "level0_fp32": 14.8e9, "levels": 37.7e9}
 
 
 def _prec_code(dm, name):
