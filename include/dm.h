@@ -258,8 +258,8 @@ dm_status dm_set_batch_lanes(dm_ctx* ctx, int lanes);
 dm_status dm_autotune(dm_ctx* ctx, const float* d_img1, int W1, int H1, const float* d_img2, int W2, int H2,
                       void* d_ws, size_t ws_bytes, int* chosen, void* stream);
 /* The launch shapes used for pairs of these sizes (until dm_autotune has run
- * on them the defaults: all M-tiles in one work unit, 16, 8, 2): 4 ints as
- * for dm_autotune. */
+ * on them the defaults: all M-tiles in one work unit -- half of them for
+ * DM_FP8_E4M3 --, 16, 8, 2): 4 ints as for dm_autotune. */
 dm_status dm_tuned_config(dm_ctx* ctx, int W1, int H1, int W2, int H2, int* chosen);
 /* Set the launch shapes for pairs of these sizes (e.g. a choice saved from an
  * earlier dm_autotune): chosen[0] >= 1, chosen[1] in {8, 16}, chosen[2] in

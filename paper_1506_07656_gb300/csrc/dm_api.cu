@@ -37,7 +37,7 @@ namespace {
 DmTune tune_for(dm_ctx* c, const DmGeom& g) {
     std::lock_guard<std::mutex> lk(c->tune_mu);
     auto it = c->tuned.find({g.W1, g.H1, g.W2, g.H2});
-    return it == c->tuned.end() ? dm_tune_default(g) : it->second;
+    return it == c->tuned.end() ? dm_tune_default(g, c->cfg.precision) : it->second;
 }
 }  // namespace
 
@@ -683,7 +683,7 @@ dm_status dm_autotune(dm_ctx* ctx, const float* d_img1, int W1, int H1, const fl
     float* desc2 = (float*)(base + ml.desc2);
     if ((s = run_descriptors(ctx, d_img1, W1, H1, desc1, base + ml.tmp, st)) != DM_OK) return s;
     if ((s = run_descriptors(ctx, d_img2, W2, H2, desc2, base + ml.tmp, st)) != DM_OK) return s;
-    DmTune best = dm_tune_default(g);
+    DmTune best = dm_tune_default(g, ctx->cfg.precision);
     dm_pyramid py;
     fill_pyramid(&py, g, ctx->cfg.precision, ctx->cfg.compensated, best, ml.py, base + ml.pyr);
     int* d_status = &reinterpret_cast<DmWsHeader*>(base + ml.bt.header)->pyr_status;
@@ -727,7 +727,7 @@ dm_status dm_autotune(dm_ctx* ctx, const float* d_img1, int W1, int H1, const fl
         const int splits[] = {1, 2, 3, 4, 6, 8};
         for (int k : splits) {
             const int mc = (n_mtiles + k - 1) / k;
-            if (mc == dm_tune_default(g).m_chunk) continue;   // the default, timed above
+            if (mc == best.m_chunk) continue;   // the default, timed above
             py.tune.m_chunk = mc;
             if (pick(timed(level0), cur)) best.m_chunk = mc;
         }

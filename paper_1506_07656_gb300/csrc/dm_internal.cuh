@@ -245,10 +245,14 @@ struct DmTune {
     int bt_mult;
     int level_ring;
 };
-// Defaults until tuned: all M-tiles of the pair in one work unit (the N-tiles
-// are the units; measured at 1024x436 the most robust choice for BF16), tile
+// Defaults until tuned: the level-0 work unit holds all M-tiles of the pair
+// (the N-tiles are the units; measured at 1024x436 the most robust choice for
+// BF16) or, for the FP8 form, half of them (its best measured split); tile
 // rows 16, 8 CTAs per SM, a ring of 2.
-inline DmTune dm_tune_default(const DmGeom& g) { return DmTune{(g.npatch(0) + 127) / 128, 16, 8, 2}; }
+inline DmTune dm_tune_default(const DmGeom& g, int precision) {
+    const int n_mtiles = (g.npatch(0) + 127) / 128;
+    return DmTune{precision == DM_FP8_E4M3 ? (n_mtiles + 1) / 2 : n_mtiles, 16, 8, 2};
+}
 
 // Pyramid handle (host side).
 struct dm_pyramid {
