@@ -19,6 +19,11 @@ Functions and the passages they follow:
   backtrack()     Eq. 13-15 (merge by highest score)
   reciprocal()    Eq. 16
   match()         the whole chain
+  patch_vectors() the atomic patches of image 1 as 144-vectors (Eq. 3-4 window)
+  kmeans_sphere() Sec. 4.1: k-means of the atomic patches with the centroids
+                  projected back on the hypersphere after every update
+  approx_match()  Sec. 4.1: the chain with every atomic patch replaced by its
+                  closest prototype
 """
 from __future__ import annotations
 
@@ -185,10 +190,12 @@ class Pyramid:
 
 
 def pyramid(d1: np.ndarray, d2: np.ndarray, prec: str = "f64", lam: float = DEFAULT_CFG["lam"],
-            compensated: bool = True, gaps: bool = False) -> Pyramid:
+            compensated: bool = True, gaps: bool = False, patches: np.ndarray | None = None) -> Pyramid:
     """Level maps of Algorithm 1.  `compensated` selects the FP32 mirror's
     child sum (TwoSum-compensated or plain, both in child order); FP64 ignores it.
-    `gaps`: also the relative top-two gap of every pooling decision."""
+    `gaps`: also the relative top-two gap of every pooling decision.
+    `patches`: [P0][144] vectors that replace image 1's atomic patches (the
+    approximate form, Sec. 4.1); d1 then only gives the size of image 1."""
     dt = _dtype(prec)
     d1 = np.ascontiguousarray(d1, dtype=dt)
     d2 = np.ascontiguousarray(d2, dtype=dt)
@@ -210,10 +217,16 @@ def pyramid(d1: np.ndarray, d2: np.ndarray, prec: str = "f64", lam: float = DEFA
         pyr.gap = [np.zeros(a.shape, dtype=np.float64) for a in pyr.pooled]
         gg = (C.c_void_p * g.L)(*[a.ctypes.data for a in pyr.gap])
     lib = _lib(prec)
-    lib.orc_pyramid.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int,
-                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
-    rc = lib.orc_pyramid(_ptr(d1), W1, H1, _ptr(d2), W2, H2, float(lam), int(bool(compensated)), pp, aa,
-                         _ptr(pyr.top), vv, gg)
+    fn = lib.orc_pyramid if patches is None else lib.orc_pyramid_vec
+    fn.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int,
+                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    if patches is not None:
+        src = np.ascontiguousarray(patches, dtype=dt)
+        if src.shape != (g.npatch(0), 144):
+            raise ValueError(f"patches must be [{g.npatch(0)}][144]")
+    else:
+        src = d1
+    rc = fn(_ptr(src), W1, H1, _ptr(d2), W2, H2, float(lam), int(bool(compensated)), pp, aa, _ptr(pyr.top), vv, gg)
     if rc != 0:
         raise ValueError("pyramid oracle failed")
     return pyr
@@ -277,6 +290,63 @@ def match(img1: np.ndarray, img2: np.ndarray, prec: str = "f64", compensated: bo
     d1 = descriptors(img1, prec, **c)
     d2 = descriptors(img2, prec, **c)
     pyr = pyramid(d1, d2, prec, lam, compensated, gaps)
+    bt = backtrack(pyr)
+    return reciprocal(pyr, bt), pyr, bt
+
+
+def patch_vectors(d1: np.ndarray) -> np.ndarray:
+    """Image 1's atomic patches as vectors [P0][144] in d1's dtype: patch p
+    (centre (4 (p % P0x) + 2, 4 (p // P0x) + 2), Eq. 3-4 window [x-2, x+1] x
+    [y-2, y+1]) has a[(dy*4 + dx)*9 + c] = d1[y-2+dy][x-2+dx][c], zero for
+    pixels outside image 1 (partial patches)."""
+    H1, W1, _ = d1.shape
+    P0x, P0y = (W1 + 1) // 4, (H1 + 1) // 4
+    g = geometry(W1, H1, W1, H1)
+    assert (g.P0x, g.P0y) == (P0x, P0y)
+    pad = np.zeros((4 * P0y, 4 * P0x, 9), dtype=d1.dtype)
+    h, w = min(H1, 4 * P0y), min(W1, 4 * P0x)
+    pad[:h, :w] = d1[:h, :w]
+    # [P0y][dy][P0x][dx][c] -> [P0y][P0x][dy][dx][c]
+    a = pad.reshape(P0y, 4, P0x, 4, 9).transpose(0, 2, 1, 3, 4)
+    return np.ascontiguousarray(a.reshape(P0y * P0x, 144))
+
+
+def kmeans_sphere(A: np.ndarray, init: np.ndarray, iters: int, radius: float = 4.0):
+    """Sec. 4.1 in FP64: Lloyd's k-means of the rows of A ([P0][144]) from the
+    initial centroids `init` ([D][144]), each centroid rescaled to norm
+    `radius` (the norm of a full atomic patch: 16 unit pixel descriptors)
+    after every update.  One iteration = assignment to the closest centroid
+    (the largest dot product, as all centroids have the same norm; ties to the
+    lower index), then each centroid = the mean of its members projected on
+    the sphere (a centroid without members keeps its value).  Returns the
+    centroids and the assignment to them."""
+    A = np.asarray(A, dtype=np.float64)
+
+    def project(C):
+        n = np.linalg.norm(C, axis=1, keepdims=True)
+        return np.where(n > 0, C * (radius / np.where(n > 0, n, 1.0)), C)
+
+    C = project(np.array(init, dtype=np.float64, copy=True))
+    for _ in range(iters):
+        assign = np.argmax(A @ C.T, axis=1)
+        for d in range(C.shape[0]):
+            members = A[assign == d]
+            if len(members):
+                C[d] = members.sum(axis=0)
+        C = project(C)
+    return C, np.argmax(A @ C.T, axis=1).astype(np.int32)
+
+
+def approx_match(img1: np.ndarray, img2: np.ndarray, protos: np.ndarray, assign: np.ndarray, prec: str = "f64",
+                 compensated: bool = True, **cfg):
+    """Sec. 4.1: the chain with atomic patch p of image 1 replaced by the
+    prototype protos[assign[p]] (given, e.g. from kmeans_sphere)."""
+    c = dict(DEFAULT_CFG, **cfg)
+    lam = c.pop("lam")
+    d1 = descriptors(img1, prec, **c)
+    d2 = descriptors(img2, prec, **c)
+    q = np.asarray(protos, dtype=_dtype(prec))[np.asarray(assign)]
+    pyr = pyramid(d1, d2, prec, lam, compensated, patches=q)
     bt = backtrack(pyr)
     return reciprocal(pyr, bt), pyr, bt
 

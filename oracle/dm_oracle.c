@@ -334,6 +334,23 @@ static real corr0(const real* d1, int W1, int H1, const real* d2, int W2, int H2
     return acc * (real)0.0625;
 }
 
+/* The same C_0 for an atomic patch given as its 144-vector a[(dy*4 + dx)*9 + c]
+ * (the pixels of a partial patch outside I already zero: their terms add an
+ * exact zero, as the skipped terms of corr0 do): same terms, same order.  The
+ * approximate form (Sec. 4.1) passes the prototype that replaces the patch. */
+static real corr0_vec(const real* a, const real* d2, int W2, int H2, int tx, int ty) {
+    real acc = 0;
+    for (int dx = 0; dx < 4; dx++)
+        for (int c = 0; c < 9; c++)
+            for (int dy = 0; dy < 4; dy++) {
+                int x2 = tx - 2 + dx, y2 = ty - 2 + dy;
+                if (x2 < 0 || y2 < 0 || x2 >= W2 || y2 >= H2) continue;   /* zero term */
+                real b = d2[((size_t)y2 * W2 + x2) * 9 + c];
+                acc = RFMA(a[(dy * 4 + dx) * 9 + c], b, acc);
+            }
+    return acc * (real)0.0625;
+}
+
 /* Unpooled, unrectified C_0 for patches [p0, p1): out [p1-p0][H2][W2]. */
 int orc_level0(const real* d1, int W1, int H1, const real* d2, int W2, int H2, int p0, int p1, real* out) {
     geom g;
@@ -440,8 +457,26 @@ static void level_average(const real* const* kid, int n, int mw, int mh, int com
 /* top       : [npatch(L)][dh[L]][dw[L]]       = C_L                          */
 /* valid[l]  : [npatch(l)] patch membership of G_{4*2^l}, l = 0..L            */
 /* ------------------------------------------------------------------------- */
+static int pyramid_impl(const real* d1, const real* amat, int W1, int H1, const real* d2, int W2, int H2,
+                        double lambda, int compensated, real** pooled, uint8_t** amax, real* top, uint8_t** valid,
+                        double** pgap);
+
 int orc_pyramid(const real* d1, int W1, int H1, const real* d2, int W2, int H2, double lambda, int compensated,
                 real** pooled, uint8_t** amax, real* top, uint8_t** valid, double** pgap) {
+    return pyramid_impl(d1, NULL, W1, H1, d2, W2, H2, lambda, compensated, pooled, amax, top, valid, pgap);
+}
+
+/* The pyramid with image 1's atomic patches given as vectors: amat
+ * [P0][144] (k = (dy*4 + dx)*9 + c), e.g. each patch replaced by its
+ * prototype (approximate form, Sec. 4.1).  W1, H1 fix the geometry. */
+int orc_pyramid_vec(const real* amat, int W1, int H1, const real* d2, int W2, int H2, double lambda, int compensated,
+                    real** pooled, uint8_t** amax, real* top, uint8_t** valid, double** pgap) {
+    return pyramid_impl(NULL, amat, W1, H1, d2, W2, H2, lambda, compensated, pooled, amax, top, valid, pgap);
+}
+
+static int pyramid_impl(const real* d1, const real* amat, int W1, int H1, const real* d2, int W2, int H2,
+                        double lambda, int compensated, real** pooled, uint8_t** amax, real* top, uint8_t** valid,
+                        double** pgap) {
     geom g;
     if (make_geom(W1, H1, W2, H2, &g)) return -1;
     const real lam = (real)lambda;
@@ -458,7 +493,8 @@ int orc_pyramid(const real* d1, int W1, int H1, const real* d2, int W2, int H2, 
             int px = 4 * (p % g.P0x) + 2, py = 4 * (p / g.P0x) + 2;
             for (int ty = 0; ty < H2; ty++)
                 for (int tx = 0; tx < W2; tx++) {
-                    real c = corr0(d1, W1, H1, d2, W2, H2, px, py, tx, ty);
+                    real c = amat ? corr0_vec(amat + (size_t)p * 144, d2, W2, H2, tx, ty)
+                                  : corr0(d1, W1, H1, d2, W2, H2, px, py, tx, ty);
                     map[(size_t)ty * W2 + tx] = ORC_F32 ? c : RPOW(c, lam);
                 }
             size_t off = (size_t)p * g.dw[1] * g.dh[1];
