@@ -144,6 +144,42 @@ dm_status dm_descriptors(dm_ctx* ctx, const float* d_img, int W, int H, float* d
 dm_status dm_correlate_pyramid(dm_ctx* ctx, const float* d_desc1, int W1, int H1, const float* d_desc2, int W2,
                                int H2, void* d_ws, size_t ws_bytes, dm_pyramid** out, void* stream);
 
+/* Approximate DeepMatching (Sec. 4.1): image 1's atomic patches replaced by
+ * their closest prototype from a dictionary of D learned per pair.
+ *
+ * dm_prototypes: the dictionary, by k-means of the atomic patches of image 1
+ * (their 144-vectors a[(dy*4 + dx)*9 + c] over the Eq. 3-4 window, zero
+ * outside I) with every centroid projected back on the hypersphere of the
+ * patches (norm 4) after each update.  Start: centroid d = patch h_init[d]
+ * projected (h_init: D host ints in [0, P0); NULL = patches floor(d P0 / D)).
+ * One iteration: assign every patch to the closest centroid (largest dot
+ * product, ties to the lower index), then replace each centroid by the sum of
+ * its members projected to norm 4 (a centroid without members is kept).
+ * After `iters` iterations (>= 0) a last assignment is made.  Out: d_protos
+ * [D][144] (FP32) and d_assign [P0] (prototype of each atomic patch, int32).
+ * The member sums are exact fixed-point sums, so the result does not depend
+ * on the order of the atomic updates.  D in [1, P0] (P0 = dm_geometry's
+ * n_patch0); d_ws >= dm_prototypes_workspace_bytes; waits for `stream` once,
+ * after copying h_init (not capturable).
+ *
+ * dm_correlate_pyramid_approx: the pyramid of dm_correlate_pyramid with atomic
+ * patch p of image 1 replaced by d_protos[d_assign[p]]: level 0 is computed
+ * and stored once per prototype (D maps instead of P0), and the level-1 and
+ * backtracking steps read the map of each atomic child through d_assign.
+ * W1, H1 give image 1's size (its descriptors are not needed).  d_protos and
+ * d_assign stay caller-owned and must stay unchanged while the pyramid is used
+ * (dm_backtrack reads d_assign); entries of d_assign outside [0, D) are
+ * clamped to that range.  Same workspace as dm_correlate_pyramid;
+ * dm_pyramid_level reports n_patches = D for level 0.  Results equal those of
+ * dm_correlate_pyramid on descriptors whose atomic patches are the assigned
+ * prototypes.  dm_loss_grad refuses such a pyramid (DM_EUNSUPPORTED). */
+dm_status dm_prototypes_workspace_bytes(dm_ctx* ctx, int W1, int H1, int D, size_t* bytes);
+dm_status dm_prototypes(dm_ctx* ctx, const float* d_desc1, int W1, int H1, int D, int iters, const int* h_init,
+                        float* d_protos, int* d_assign, void* d_ws, size_t ws_bytes, void* stream);
+dm_status dm_correlate_pyramid_approx(dm_ctx* ctx, const float* d_protos, int D, const int* d_assign, int W1, int H1,
+                                      const float* d_desc2, int W2, int H2, void* d_ws, size_t ws_bytes,
+                                      dm_pyramid** out, void* stream);
+
 /* Device views of one level of a pyramid (valid after the producing stream
  * work completes).  level in [0, L]; for level < L: d_vals = P_l
  * [n_patches][mh][pitch] (columns mw..pitch-1 are row padding, not data) and

@@ -136,6 +136,8 @@ void fill_pyramid(dm_pyramid* p, const DmGeom& g, int precision, int compensated
         p->amax[l] = (const unsigned char*)(base + pl.amax[l]);
     }
     p->top = (const float*)(base + pl.top);
+    p->proto_of = nullptr;
+    p->n0_maps = g.npatch(0);
 }
 
 dm_status run_descriptors(dm_ctx* c, const float* img, int W, int H, float* desc, char* tmp, cudaStream_t st) {
@@ -146,18 +148,26 @@ dm_status run_descriptors(dm_ctx* c, const float* img, int W, int H, float* desc
     return DM_OK;
 }
 
+// Pyramid of one pair.  Approximate form (protos != nullptr): level 0 holds
+// one map per prototype (n_protos rows of protos) and atomic patch c reads map
+// proto_of[c].
 dm_status run_pyramid(dm_ctx* c, const DmGeom& g, const float* d1, const float* d2, char* base, const DmPyrLayout& pl,
-                      dm_pyramid* py, int* d_status, cudaStream_t st) {
+                      dm_pyramid* py, int* d_status, cudaStream_t st, const float* protos = nullptr, int n_protos = -1,
+                      const int* proto_of = nullptr) {
     fill_pyramid(py, g, c->cfg.precision, c->cfg.compensated, tune_for(c, g), pl, base);
+    if (protos) {
+        py->proto_of = proto_of;
+        py->n0_maps = n_protos;
+    }
     cudaError_t e;
     if ((e = cudaMemsetAsync(d_status, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(c, e, "clear status");
     if (c->cfg.precision != DM_FP32) {
         e = dm_launch_corr0_tc(g, c->cfg.precision, d1, d2, c->cfg.lambda, base + pl.a16, d_status,
                                const_cast<float*>(py->pooled[0]), const_cast<unsigned char*>(py->amax[0]),
-                               py->tune.m_chunk, st);
+                               py->tune.m_chunk, st, protos, py->n0_maps);
     } else {
         e = dm_launch_corr0_f32(g, d1, d2, c->cfg.lambda, const_cast<float*>(py->pooled[0]),
-                                const_cast<unsigned char*>(py->amax[0]), st);
+                                const_cast<unsigned char*>(py->amax[0]), st, protos, py->n0_maps);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "level-0 correlation");
     e = dm_launch_levels(g, *py, c->cfg.lambda, d_status, st);
@@ -427,6 +437,80 @@ dm_status dm_correlate_pyramid(dm_ctx* ctx, const float* d_desc1, int W1, int H1
     return DM_OK;
 }
 
+dm_status dm_prototypes_workspace_bytes(dm_ctx* ctx, int W1, int H1, int D, size_t* bytes) {
+    if (!ctx) return DM_EINVAL;
+    if (!bytes) return fail(ctx, DM_EINVAL, "dm_prototypes_workspace_bytes: null pointer");
+    DmGeom g;
+    dm_status s = check_geom(ctx, W1, H1, W1, H1, &g);
+    if (s != DM_OK) return s;
+    if (D < 1 || D > g.npatch(0)) return fail(ctx, DM_EINVAL, "D = %d outside [1, %d atomic patches]", D, g.npatch(0));
+    *bytes = dm_kmeans_ws_bytes(g, D);
+    return DM_OK;
+}
+
+dm_status dm_prototypes(dm_ctx* ctx, const float* d_desc1, int W1, int H1, int D, int iters, const int* h_init,
+                        float* d_protos, int* d_assign, void* d_ws, size_t ws_bytes, void* stream) {
+    if (!ctx) return DM_EINVAL;
+    if (!d_desc1 || !d_protos || !d_assign || !d_ws || iters < 0) return fail(ctx, DM_EINVAL, "dm_prototypes: bad arguments");
+    if (!aligned256(d_ws)) return fail(ctx, DM_EINVAL, "workspace must be 256-byte aligned");
+    DmGeom g;
+    dm_status s = check_geom(ctx, W1, H1, W1, H1, &g);
+    if (s != DM_OK) return s;
+    const int P0 = g.npatch(0);
+    if (D < 1 || D > P0) return fail(ctx, DM_EINVAL, "D = %d outside [1, %d atomic patches]", D, P0);
+    const size_t need = dm_kmeans_ws_bytes(g, D);
+    if (ws_bytes < need) return fail(ctx, DM_ENOMEM, "prototype workspace %zu < %zu bytes", ws_bytes, need);
+    std::vector<int> init(D);
+    for (int d = 0; d < D; d++) {
+        init[d] = h_init ? h_init[d] : (int)(((long long)d * P0) / D);
+        if (init[d] < 0 || init[d] >= P0) return fail(ctx, DM_EINVAL, "init[%d] = %d outside [0, %d)", d, init[d], P0);
+    }
+    DevGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int* d_init = reinterpret_cast<int*>((char*)d_ws + dm_kmeans_init_offset(g, D));
+    cudaError_t e = cudaMemcpyAsync(d_init, init.data(), (size_t)D * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy init");
+    // the pageable source must stay valid until the copy has read it
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(ctx, e, "copy init");
+    e = dm_launch_kmeans(g, d_desc1, D, iters, d_init, d_protos, d_assign, (char*)d_ws, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "k-means kernels");
+    return DM_OK;
+}
+
+dm_status dm_correlate_pyramid_approx(dm_ctx* ctx, const float* d_protos, int D, const int* d_assign, int W1, int H1,
+                                      const float* d_desc2, int W2, int H2, void* d_ws, size_t ws_bytes,
+                                      dm_pyramid** out, void* stream) {
+    if (!ctx) return DM_EINVAL;
+    if (!out || !d_protos || !d_assign || !d_desc2 || !d_ws)
+        return fail(ctx, DM_EINVAL, "dm_correlate_pyramid_approx: null pointer");
+    *out = nullptr;
+    if (!aligned256(d_ws)) return fail(ctx, DM_EINVAL, "workspace must be 256-byte aligned");
+    DmGeom g;
+    dm_status s = check_geom(ctx, W1, H1, W2, H2, &g);
+    if (s != DM_OK) return s;
+    if (D < 1 || D > g.npatch(0)) return fail(ctx, DM_EINVAL, "D = %d outside [1, %d atomic patches]", D, g.npatch(0));
+    DmPyrLayout pl;
+    dm_pyr_layout(g, ctx->cfg.precision, &pl);
+    if (ws_bytes < pl.bytes) return fail(ctx, DM_ENOMEM, "pyramid workspace %zu < %zu bytes", ws_bytes, pl.bytes);
+    DevGuard dg(ctx->device);
+    dm_pyramid* py = (dm_pyramid*)malloc(sizeof(dm_pyramid));
+    if (!py) return fail(ctx, DM_EINVAL, "host allocation failed");
+    DmWsHeader* hdr = reinterpret_cast<DmWsHeader*>((char*)d_ws + pl.header);
+    cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(DmWsHeader), (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        free(py);
+        return cuda_fail(ctx, e, "clear header");
+    }
+    s = run_pyramid(ctx, g, nullptr, d_desc2, (char*)d_ws, pl, py, &hdr->pyr_status, (cudaStream_t)stream, d_protos, D,
+                    d_assign);
+    if (s != DM_OK) {
+        free(py);
+        return s;
+    }
+    *out = py;
+    return DM_OK;
+}
+
 dm_status dm_pyramid_level(const dm_pyramid* pyr, int level, const float** d_vals, const unsigned char** d_argmax,
                            const unsigned char** d_valid, int* n_patches, int* mw, int* mh, int* pitch) {
     if (!pyr || level < 0 || level > pyr->g.L) return DM_EINVAL;
@@ -434,7 +518,7 @@ dm_status dm_pyramid_level(const dm_pyramid* pyr, int level, const float** d_val
     if (d_vals) *d_vals = level < g.L ? pyr->pooled[level] : pyr->top;
     if (d_argmax) *d_argmax = level < g.L ? pyr->amax[level] : nullptr;
     if (d_valid) *d_valid = pyr->valid[level];
-    if (n_patches) *n_patches = g.npatch(level);
+    if (n_patches) *n_patches = level == 0 ? pyr->n0_maps : g.npatch(level);
     if (mw) *mw = level < g.L ? g.dw[level + 1] : g.dw[level];
     if (mh) *mh = level < g.L ? g.dh[level + 1] : g.dh[level];
     if (pitch) *pitch = level < g.L ? g.pitch(level + 1) : g.dw[level];
@@ -562,6 +646,7 @@ dm_status dm_loss_grad(dm_ctx* ctx, const dm_pyramid* pyr, const float* d_desc1,
                        size_t ws_bytes, float* d_loss, float* d_parts, float* d_g1, float* d_g2, void* stream) {
     if (!ctx) return DM_EINVAL;
     if (!pyr || !d_desc1 || !d_desc2 || !d_ws || !d_loss) return fail(ctx, DM_EINVAL, "dm_loss_grad: bad arguments");
+    if (pyr->proto_of) return fail(ctx, DM_EUNSUPPORTED, "dm_loss_grad: the approximate form has no adjoint");
     if (!aligned256(d_ws)) return fail(ctx, DM_EINVAL, "workspace must be 256-byte aligned");
     DmGradLayout gl;
     dm_grad_layout(pyr->g, &gl);

@@ -264,6 +264,11 @@ struct dm_pyramid {
     const float* pooled[DM_MAXL];
     const unsigned char* amax[DM_MAXL];
     const float* top;
+    // approximate form (Sec. 4.1): level 0 holds one map per prototype and
+    // atomic patch c reads map proto_of[c] (caller-owned device array);
+    // exact form: proto_of = nullptr, n0_maps = npatch(0)
+    const int* proto_of;
+    int n0_maps;
 };
 
 // Smoothing taps passed by value to kernels.
@@ -312,12 +317,22 @@ bool dm_encode_tiled(CUtensorMap* m, CUtensorMapDataType dt, int rank, void* bas
 // Kernel launchers (return cudaGetLastError()).
 cudaError_t dm_launch_descriptors(const DmDescParams& prm, const float* img, int W, int H, float* desc,
                                   float* tmpA, float* tmpB, cudaStream_t st);
+// Level-0 launchers.  The rows of the correlation are image 1's atomic
+// patches taken from d1, or, when amat is given, the n_rows vectors
+// amat[n_rows][144] (k = (dy*4 + dx)*9 + c; the prototypes of the approximate
+// form), whose maps then fill rows 0 .. n_rows-1 of the level-0 arrays.
 cudaError_t dm_launch_corr0_f32(const DmGeom& g, const float* d1, const float* d2, float lam, float* pooled0,
-                                unsigned char* amax0, cudaStream_t st);
+                                unsigned char* amax0, cudaStream_t st, const float* amat = nullptr, int n_rows = -1);
 // tcgen05 level-0 correlation, precision DM_BF16 or DM_FP8_E4M3; abuf holds
 // dm_corr0_tc_a_bytes(g, precision) bytes of packed operands.
 cudaError_t dm_launch_corr0_tc(const DmGeom& g, int precision, const float* d1, const float* d2, float lam, void* abuf,
-                               void* status, float* pooled0, unsigned char* amax0, int m_chunk, cudaStream_t st);
+                               void* status, float* pooled0, unsigned char* amax0, int m_chunk, cudaStream_t st,
+                               const float* amat = nullptr, int n_rows = -1);
+// Spherical k-means of image 1's atomic patches (Sec. 4.1), see k_approx.cu.
+size_t dm_kmeans_ws_bytes(const DmGeom& g, int D);
+size_t dm_kmeans_init_offset(const DmGeom& g, int D);
+cudaError_t dm_launch_kmeans(const DmGeom& g, const float* d1, int D, int iters, const int* init, float* protos,
+                             int* assign, char* ws, cudaStream_t st);
 size_t dm_corr0_tc_a_bytes(const DmGeom& g, int precision);
 cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& p, float lam, int* status, cudaStream_t st);
 cudaError_t dm_launch_loss_grad(const DmGeom& g, const dm_pyramid& py, const float* d1, const float* d2, float lam,

@@ -51,6 +51,8 @@ struct BtArgs {
     unsigned long long* bestP;
     unsigned long long* bestQ;
     DmWsHeader* hdr;
+    const int* proto_of;          // approximate form: level-0 map of atomic patch c is proto_of[c]; else null
+    int n0_maps;                  // level-0 maps (entries of proto_of are clamped to [0, n0_maps))
 };
 
 __device__ __forceinline__ unsigned int warp_agg_inc(unsigned int* ctr) {
@@ -134,7 +136,8 @@ __device__ __forceinline__ int expand(const BtArgs& a, int l, unsigned int cap_n
             cc[i] = c;
             rxs[i] = rx;
             rys[i] = ry;
-            long long ro = ((long long)c * mh + ry) * pitch + rx;
+            const int cm = (l == 1 && a.proto_of) ? min(max(__ldg(a.proto_of + c), 0), a.n0_maps - 1) : c;   // its map
+            long long ro = ((long long)cm * mh + ry) * pitch + rx;
             code[i] = a.amax[l - 1][ro];
             val[i] = a.pooled[l - 1][ro];
         }
@@ -326,6 +329,8 @@ cudaError_t dm_launch_backtrack(const DmGeom& g, const dm_pyramid& py, const DmB
     BtArgs a;
     memset(&a, 0, sizeof(a));
     a.g = g;
+    a.proto_of = py.proto_of;
+    a.n0_maps = py.n0_maps;
     for (int l = 0; l <= g.L; l++) a.valid[l] = py.valid[l];
     for (int l = 0; l < g.L; l++) {
         a.pooled[l] = py.pooled[l];

@@ -43,7 +43,7 @@ constexpr size_t SMEM_BYTES = (size_t)HALO_N * 8 + (size_t)144 * PATCHES * 4;
 
 __global__ void __launch_bounds__(256, 2)
 k_corr0_f32(DmGeom g, const float* __restrict__ d1, const float* __restrict__ d2, float lam,
-            float* __restrict__ pooled0, unsigned char* __restrict__ amax0) {
+            float* __restrict__ pooled0, unsigned char* __restrict__ amax0, const float* __restrict__ amat, int n0) {
     extern __shared__ __align__(16) unsigned char smem[];
     float2* halo = reinterpret_cast<float2*>(smem);                       // [HROWS][HCOLS][9] (h, h)
     float* a_s = reinterpret_cast<float*>(smem + (size_t)HALO_N * 8);     // [(dx*9+c)*4+dy][patch]
@@ -51,8 +51,7 @@ k_corr0_f32(DmGeom g, const float* __restrict__ d1, const float* __restrict__ d2
     const int tiles_x = (g.dw[1] + PW - 1) / PW;
     const int rx0 = (blockIdx.x % tiles_x) * PW;
     const int ry0 = (blockIdx.x / tiles_x) * PH;
-    const int p_base = blockIdx.y * PATCHES;
-    const int n0 = g.P0x * g.P0y;
+    const int p_base = blockIdx.y * PATCHES;      // rows: atomic patches, or the n0 vectors of amat
     const int W2 = g.W2, H2 = g.H2;
     const int cx0 = 2 * rx0 - 1, cy0 = 2 * ry0 - 1;     // C0 tile origin (may be -1)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -69,16 +68,21 @@ k_corr0_f32(DmGeom g, const float* __restrict__ d1, const float* __restrict__ d2
             halo[pix * 9 + c] = make_float2(v, v);
         }
     }
-    // patch vectors: window [p-2, p+1]^2 of I, zero outside I (partial patches)
+    // patch vectors: window [p-2, p+1]^2 of I, zero outside I (partial
+    // patches), or row p of amat (element (dy*4 + dx)*9 + c)
     for (int k = tid; k < 144 * PATCHES; k += 256) {
         int pl = k % PATCHES, kk = k / PATCHES;
         int dy = kk % 4, c = (kk / 4) % 9, dx = kk / 36;
         int p = p_base + pl;
         float v = 0.0f;
         if (p < n0) {
-            int px = 4 * (p % g.P0x) + 2, py = 4 * (p / g.P0x) + 2;
-            int x = px - 2 + dx, y = py - 2 + dy;
-            if (x < g.W1 && y < g.H1) v = __ldg(d1 + ((long long)y * g.W1 + x) * 9 + c);
+            if (amat) {
+                v = __ldg(amat + (long long)p * 144 + (dy * 4 + dx) * 9 + c);
+            } else {
+                int px = 4 * (p % g.P0x) + 2, py = 4 * (p / g.P0x) + 2;
+                int x = px - 2 + dx, y = py - 2 + dy;
+                if (x < g.W1 && y < g.H1) v = __ldg(d1 + ((long long)y * g.W1 + x) * 9 + c);
+            }
         }
         a_s[k] = v;
     }
@@ -178,14 +182,15 @@ k_corr0_f32(DmGeom g, const float* __restrict__ d1, const float* __restrict__ d2
 }  // namespace
 
 cudaError_t dm_launch_corr0_f32(const DmGeom& g, const float* d1, const float* d2, float lam, float* pooled0,
-                                unsigned char* amax0, cudaStream_t st) {
+                                unsigned char* amax0, cudaStream_t st, const float* amat, int n_rows) {
+    if (n_rows < 0) n_rows = g.P0x * g.P0y;
     int tiles = ((g.dw[1] + PW - 1) / PW) * ((g.dh[1] + PH - 1) / PH);
-    int pblocks = (g.P0x * g.P0y + PATCHES - 1) / PATCHES;
+    int pblocks = (n_rows + PATCHES - 1) / PATCHES;
     dim3 grid(tiles, pblocks);
     static std::atomic<unsigned long long> smem_done{0};   // > 48 KB dynamic shared memory opted in, per device
     cudaError_t e = dm_smem_opt_in(reinterpret_cast<const void*>(k_corr0_f32), (int)SMEM_BYTES, smem_done);
     if (e != cudaSuccess) return e;
-    k_corr0_f32<<<grid, 256, SMEM_BYTES, st>>>(g, d1, d2, lam, pooled0, amax0);
+    k_corr0_f32<<<grid, 256, SMEM_BYTES, st>>>(g, d1, d2, lam, pooled0, amax0, amat, n_rows);
     dm_count_launches(1);
     return cudaGetLastError();
 }

@@ -143,14 +143,16 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
 __device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, %0;" :: "n"(EPI_THREADS) : "memory"); }
 
 // Pack the patch vectors of I into BF16 M-tiles (zero rows past the last patch).
-__global__ void k_pack_a(DmGeom g, const float* __restrict__ d1, __nv_bfloat16* __restrict__ a16, int n_mtiles) {
+// Rows: image 1's atomic patches (from d1), or the n0 vectors of amat
+// (element (dy*4 + dx)*9 + c), zero past the last row.
+__global__ void k_pack_a(DmGeom g, const float* __restrict__ d1, __nv_bfloat16* __restrict__ a16, int n_mtiles,
+                         const float* __restrict__ amat, int n0) {
     using F = Fmt<FMT_BF16>;
     const long long total = (long long)n_mtiles * BM * F::CHUNKS;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
     const int kc = (int)(idx % F::CHUNKS);
     const int pm = (int)(idx / F::CHUNKS);
-    const int n0 = g.P0x * g.P0y;
     __align__(16) __nv_bfloat16 v[8];
     const int px = 4 * (pm % g.P0x) + 2, py = 4 * (pm / g.P0x) + 2;
 #pragma unroll
@@ -158,7 +160,8 @@ __global__ void k_pack_a(DmGeom g, const float* __restrict__ d1, __nv_bfloat16* 
         int k = kc * 8 + e;
         int dy = k / 36, dx = (k / 9) % 4, c = k % 9;
         int x = px - 2 + dx, y = py - 2 + dy;
-        float f = (pm < n0 && x < g.W1 && y < g.H1) ? __ldg(d1 + ((long long)y * g.W1 + x) * 9 + c) : 0.0f;
+        float f = amat ? (pm < n0 ? __ldg(amat + (long long)pm * KD + k) : 0.0f)
+                       : ((pm < n0 && x < g.W1 && y < g.H1) ? __ldg(d1 + ((long long)y * g.W1 + x) * 9 + c) : 0.0f);
         v[e] = __float2bfloat16_rn(f);
     }
     const int t = pm / BM, r = pm % BM;
@@ -195,11 +198,10 @@ __global__ void k_absmax(const float* __restrict__ d, long long n, unsigned int*
 // Pack the patch vectors into E4M3 M-tiles with a per-patch power-of-two scale
 // s_p bringing the largest entry into [224, 448]; inv_scale[p] = 1 / s_p.
 __global__ void k_pack_a8(DmGeom g, const float* __restrict__ d1, unsigned char* __restrict__ a8,
-                          float* __restrict__ inv_scale, int n_mtiles) {
+                          float* __restrict__ inv_scale, int n_mtiles, const float* __restrict__ amat, int n0) {
     using F = Fmt<FMT_E4M3>;
     const int pm = blockIdx.x * blockDim.x + threadIdx.x;
     if (pm >= n_mtiles * BM) return;
-    const int n0 = g.P0x * g.P0y;
     const int px = 4 * (pm % g.P0x) + 2, py = 4 * (pm / g.P0x) + 2;
     float vals[KD];
     float m = 0.0f;
@@ -207,7 +209,8 @@ __global__ void k_pack_a8(DmGeom g, const float* __restrict__ d1, unsigned char*
     for (int k = 0; k < KD; k++) {
         int dy = k / 36, dx = (k / 9) % 4, c = k % 9;
         int x = px - 2 + dx, y = py - 2 + dy;
-        float f = (pm < n0 && x < g.W1 && y < g.H1) ? __ldg(d1 + ((long long)y * g.W1 + x) * 9 + c) : 0.0f;
+        float f = amat ? (pm < n0 ? __ldg(amat + (long long)pm * KD + k) : 0.0f)
+                       : ((pm < n0 && x < g.W1 && y < g.H1) ? __ldg(d1 + ((long long)y * g.W1 + x) * 9 + c) : 0.0f);
         vals[k] = f;
         m = fmaxf(m, fabsf(f));
     }
@@ -391,7 +394,6 @@ k_corr0_tc(DmGeom g, const unsigned char* __restrict__ apack, const float* __res
     const uint32_t tmem = *tmem_holder;
 
     const int W2 = g.W2, H2 = g.H2, mw = g.dw[1], mh = g.dh[1];
-    const int n0 = g.P0x * g.P0y;
     const int tiles_x = (mw + PX - 1) / PX, tiles_y = (mh + PY - 1) / PY;
     const int mchunks = (n_mtiles + m_chunk - 1) / m_chunk;
     const int n_units = tiles_x * tiles_y * mchunks;
@@ -478,7 +480,7 @@ k_corr0_tc(DmGeom g, const unsigned char* __restrict__ apack, const float* __res
                 float mult = mult_b;
                 if (FMT == FMT_E4M3) {
                     const int p = (m0 + j) * BM + ea.row;
-                    mult = mult_b * (p < n0 ? __ldg(inv_sa + p) : 1.0f);
+                    mult = mult_b * __ldg(inv_sa + p);       // inv_sa covers every row of every M-tile
                 }
                 // a failed (bounded) wait has set the abort flag: this thread skips the
                 // tile but still meets the barrier, after which every thread sees the flag
@@ -519,8 +521,8 @@ k_corr0_tc(DmGeom g, const unsigned char* __restrict__ apack, const float* __res
 
 // 3-D map of a pooled level-0 array [n0][mh][pitch] (elements of `esize` bytes),
 // logical extent mw x mh x n0, box 16 x 3 x 128, staged with the given swizzle.
-bool make_map(CUtensorMap* m, void* base, CUtensorMapDataType dt, int esize, const DmGeom& g, CUtensorMapSwizzle sw) {
-    const cuuint64_t dims[3] = {(cuuint64_t)g.dw[1], (cuuint64_t)g.dh[1], (cuuint64_t)g.npatch(0)};
+bool make_map(CUtensorMap* m, void* base, CUtensorMapDataType dt, int esize, const DmGeom& g, int n0, CUtensorMapSwizzle sw) {
+    const cuuint64_t dims[3] = {(cuuint64_t)g.dw[1], (cuuint64_t)g.dh[1], (cuuint64_t)n0};
     const cuuint64_t strides[2] = {(cuuint64_t)g.pitch(1) * esize, (cuuint64_t)g.pitch(1) * g.dh[1] * esize};
     const cuuint32_t box[3] = {PX, PY, BM};
     return dm_encode_tiled(m, dt, 3, base, dims, strides, box, sw);
@@ -577,14 +579,15 @@ size_t dm_corr0_tc_a_bytes(const DmGeom& g, int precision) {
 }
 
 cudaError_t dm_launch_corr0_tc(const DmGeom& g, int precision, const float* d1, const float* d2, float lam, void* abuf,
-                               void* status, float* pooled0, unsigned char* amax0, int m_chunk, cudaStream_t st) {
-    const int n0 = g.npatch(0);
+                               void* status, float* pooled0, unsigned char* amax0, int m_chunk, cudaStream_t st,
+                               const float* amat, int n_rows) {
+    const int n0 = n_rows < 0 ? g.npatch(0) : n_rows;
     const int n_mtiles = (n0 + BM - 1) / BM;
     if (m_chunk < 1) m_chunk = 1;
     CUtensorMap mf, mc;
     // values: 64-byte box rows staged with the 64-byte swizzle (see pool_out)
-    if (!make_map(&mf, pooled0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, CU_TENSOR_MAP_SWIZZLE_64B) ||
-        !make_map(&mc, amax0, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, g, CU_TENSOR_MAP_SWIZZLE_NONE))
+    if (!make_map(&mf, pooled0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, n0, CU_TENSOR_MAP_SWIZZLE_64B) ||
+        !make_map(&mc, amax0, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, g, n0, CU_TENSOR_MAP_SWIZZLE_NONE))
         return cudaErrorNotSupported;
     unsigned char* apack = reinterpret_cast<unsigned char*>(abuf);
     cudaError_t e;
@@ -596,12 +599,13 @@ cudaError_t dm_launch_corr0_tc(const DmGeom& g, int precision, const float* d1, 
         const long long n2 = (long long)g.W2 * g.H2 * 9;
         const long long blocks = (n2 / 4 + 255) / 256;
         k_absmax<<<(unsigned)(blocks < 1216 ? (blocks > 0 ? blocks : 1) : 1216), 256, 0, st>>>(d2, n2, bmax);
-        k_pack_a8<<<(unsigned)((n_mtiles * BM + 127) / 128), 128, 0, st>>>(g, d1, apack, inv_sa, n_mtiles);
+        k_pack_a8<<<(unsigned)((n_mtiles * BM + 127) / 128), 128, 0, st>>>(g, d1, apack, inv_sa, n_mtiles, amat, n0);
         e = launch_tc<FMT_E4M3>(g, apack, inv_sa, bmax, d2, lam, mf, mc, n_mtiles, m_chunk, reinterpret_cast<int*>(status), st);
         dm_count_launches(3);
     } else {
         long long total = (long long)n_mtiles * BM * Fmt<FMT_BF16>::CHUNKS;
-        k_pack_a<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(g, d1, reinterpret_cast<__nv_bfloat16*>(apack), n_mtiles);
+        k_pack_a<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(g, d1, reinterpret_cast<__nv_bfloat16*>(apack), n_mtiles,
+                                                                   amat, n0);
         e = launch_tc<FMT_BF16>(g, apack, nullptr, nullptr, d2, lam, mf, mc, n_mtiles, m_chunk, reinterpret_cast<int*>(status), st);
         dm_count_launches(2);
     }

@@ -96,8 +96,11 @@ __device__ __forceinline__ float child_mean(const Kids& k, int qx, int qy, int m
 }
 
 
+// (proto_of: the map of atomic child c is map proto_of[c], clamped to
+// [0, n_maps) -- approximate form, l = 1)
 __device__ __forceinline__ bool load_kids(const DmGeom& g, int l, int p, const unsigned char* __restrict__ vprev,
-                                          const float* __restrict__ prev, Kids& k) {
+                                          const float* __restrict__ prev, Kids& k, const int* __restrict__ proto_of,
+                                          int n_maps) {
     int ix = p % g.Lx, iy = p / g.Lx;
     long long cs = g.psize(l);     // child pooled map size (domain of level l, padded rows)
     k.n = 0;
@@ -105,7 +108,7 @@ __device__ __forceinline__ bool load_kids(const DmGeom& g, int l, int p, const u
     for (int i = 0; i < 4; i++) {
         int c = dm_child(g, l, ix, iy, i);
         if (c >= 0 && vprev[c]) {
-            k.base[i] = prev + (long long)c * cs;
+            k.base[i] = prev + (long long)(proto_of ? min(max(proto_of[c], 0), n_maps - 1) : c) * cs;
             k.n++;
         } else {
             k.base[i] = nullptr;
@@ -251,12 +254,13 @@ __device__ __forceinline__ int child_at(const DmGeom& g, int l, int cx, int cy, 
 // from its two columns, release the left column (thread 0 starts the loads of
 // the column NR ahead into it), pool, power, store, wait for the next patch's
 // columns; two barriers per patch.
-template <bool COMP, int TH, int NR>
+template <bool COMP, int TH, int NR, bool APPROX = false>
 __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, const __grid_constant__ CUtensorMap tmap,
                                                                const unsigned char* __restrict__ vprev,
                                                                int runs_per_res, int run, float* __restrict__ out,
                                                                unsigned char* __restrict__ amax, float lam,
-                                                               int* __restrict__ err) {
+                                                               int* __restrict__ err, const int* __restrict__ proto_of,
+                                                               int n_maps) {
     using T = LevelTile<TH>;
     constexpr int AH = T::AH, KIDF = T::KIDF;
     extern __shared__ __align__(128) unsigned char lsm_raw[];
@@ -302,13 +306,21 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
         const unsigned bytes = T::KID_BYTES * ((ct >= 0) + (cb >= 0));
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
         const uint32_t dst = (uint32_t)__cvta_generic_to_shared(ring + slot * 2 * KIDF);
+        // the map of an atomic child is its prototype's in the approximate form
+        int zt = ct, zb = cb;
+        if constexpr (APPROX) {
+            // (an entry outside [0, maps) would only read the zero fill; it is
+            // clamped like everywhere else)
+            if (ct >= 0) zt = min(max(__ldg(proto_of + ct), 0), n_maps - 1);
+            if (cb >= 0) zb = min(max(__ldg(proto_of + cb), 0), n_maps - 1);
+        }
         if (ct >= 0)
             asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-                         :: "r"(dst), "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(xa), "r"(qy0 - 1), "r"(ct), "r"(bar)
+                         :: "r"(dst), "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(xa), "r"(qy0 - 1), "r"(zt), "r"(bar)
                          : "memory");
         if (cb >= 0)
             asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-                         :: "r"(dst + KIDF * 4), "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(xa), "r"(qy0 + 1), "r"(cb), "r"(bar)
+                         :: "r"(dst + KIDF * 4), "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(xa), "r"(qy0 + 1), "r"(zb), "r"(bar)
                          : "memory");
     };
     // wait for column j (the (j / NR)-th use of its slot); false on timeout
@@ -432,30 +444,31 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
 template <bool COMP>
 __global__ void k_level_top(DmGeom g, int l, const unsigned char* __restrict__ vprev,
                             const unsigned char* __restrict__ vcur, const float* __restrict__ prev,
-                            float* __restrict__ top, float lam) {
+                            float* __restrict__ top, float lam, const int* __restrict__ proto_of, int n_maps) {
     const int p = blockIdx.y;
     if (!vcur[p]) return;
     const int mw = g.dw[l], mh = g.dh[l];
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= mw * mh) return;
     Kids k;
-    load_kids(g, l, p, vprev, prev, k);
+    load_kids(g, l, p, vprev, prev, k, proto_of, n_maps);
     float a = child_mean<COMP>(k, q % mw, q / mw, mw, mh, g.pitch(l));
     top[(long long)p * mw * mh + q] = dm_powf(a, lam);
 }
 
-template <bool COMP, int TH, int NR>
+template <bool COMP, int TH, int NR, bool APPROX = false>
 cudaError_t launch_sweep(const DmGeom& g, int l, const CUtensorMap& tm, const dm_pyramid& py, int per_res, long long items,
                          float lam, int* status, cudaStream_t st) {
     const size_t smem = (size_t)(NR * 2 * LevelTile<TH>::KIDF + LevelTile<TH>::AH * AWP) * sizeof(float) + 128;
     static std::atomic<unsigned long long> smem_done{0};
-    cudaError_t ea = dm_smem_opt_in(reinterpret_cast<const void*>(k_level_sweep<COMP, TH, NR>), (int)smem, smem_done);
+    cudaError_t ea = dm_smem_opt_in(reinterpret_cast<const void*>(k_level_sweep<COMP, TH, NR, APPROX>), (int)smem, smem_done);
     if (ea != cudaSuccess) return ea;
     if (items <= 0) return cudaSuccess;
     if (items > 0x7fffffffLL) return cudaErrorInvalidValue;
-    k_level_sweep<COMP, TH, NR><<<(unsigned)items, LEVEL_THREADS, smem, st>>>(g, l, tm, py.valid[l - 1], per_res, level_run(l),
+    k_level_sweep<COMP, TH, NR, APPROX><<<(unsigned)items, LEVEL_THREADS, smem, st>>>(g, l, tm, py.valid[l - 1], per_res, level_run(l),
                                                                           const_cast<float*>(py.pooled[l]),
-                                                                          const_cast<unsigned char*>(py.amax[l]), lam, status);
+                                                                          const_cast<unsigned char*>(py.amax[l]), lam, status,
+                                                                          APPROX ? py.proto_of : nullptr, py.n0_maps);
     return cudaGetLastError();
 }
 
@@ -469,9 +482,14 @@ cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& py, float lam, i
         k_valid<<<(np + 255) / 256, 256, 0, st>>>(g, l, py.valid[l - 1], const_cast<unsigned char*>(py.valid[l]));
         if (l < g.L) {
             // pooled maps of level l-1: [npatch(l-1)][dh[l]][pitch(l)] floats
-            const int th = py.tune.level_th == 8 ? 8 : 16;
+            // level 1 of an approximate pyramid reads the level-0 maps through the
+            // prototype index: its own kernel instance, 16-row tiles, ring of 2
+            const bool approx = l == 1 && py.proto_of != nullptr;
+            const int th = approx ? 16 : (py.tune.level_th == 8 ? 8 : 16);
             CUtensorMap tm;
-            const cuuint64_t dims[3] = {(cuuint64_t)g.dw[l], (cuuint64_t)g.dh[l], (cuuint64_t)g.npatch(l - 1)};
+            // (level 0 holds n0_maps maps: one per atomic patch, or per prototype)
+            const cuuint64_t dims[3] = {(cuuint64_t)g.dw[l], (cuuint64_t)g.dh[l],
+                                        (cuuint64_t)(l == 1 ? py.n0_maps : g.npatch(l - 1))};
             const cuuint64_t strides[2] = {(cuuint64_t)g.pitch(l) * 4, (cuuint64_t)g.psize(l) * 4};
             const cuuint32_t box[3] = {KW, (cuuint32_t)(2 * th + 1), 1};
             if (!dm_encode_tiled(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(py.pooled[l - 1]), dims,
@@ -484,7 +502,10 @@ cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& py, float lam, i
             const long long items = (long long)tiles * g.Ly * S * per_res;
             cudaError_t e;
             const bool r2 = py.tune.level_ring == 2;
-            if (th == 8)
+            if (approx)
+                e = py.compensated ? launch_sweep<true, 16, 2, true>(g, l, tm, py, per_res, items, lam, status, st)
+                                   : launch_sweep<false, 16, 2, true>(g, l, tm, py, per_res, items, lam, status, st);
+            else if (th == 8)
                 e = py.compensated ? (r2 ? launch_sweep<true, 8, 2> : launch_sweep<true, 8, 3>)(g, l, tm, py, per_res, items, lam, status, st)
                                    : (r2 ? launch_sweep<false, 8, 2> : launch_sweep<false, 8, 3>)(g, l, tm, py, per_res, items, lam, status, st);
             else
@@ -495,7 +516,8 @@ cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& py, float lam, i
             int n = g.dw[l] * g.dh[l];
             dim3 grid((n + B - 1) / B, np);
             auto kern = py.compensated ? k_level_top<true> : k_level_top<false>;
-            kern<<<grid, B, 0, st>>>(g, l, py.valid[l - 1], py.valid[l], py.pooled[l - 1], const_cast<float*>(py.top), lam);
+            kern<<<grid, B, 0, st>>>(g, l, py.valid[l - 1], py.valid[l], py.pooled[l - 1], const_cast<float*>(py.top), lam,
+                                     l == 1 ? py.proto_of : nullptr, py.n0_maps);
         }
     }
     dm_count_launches(1 + 2 * g.L);

@@ -78,6 +78,12 @@ _SIGS = {
     "dm_set_tuned_config": (C.c_int, [C.c_void_p] + [C.c_int] * 4 + [C.POINTER(C.c_int)]),
     "dm_timing_start": (C.c_int, [C.c_void_p, C.c_int]),
     "dm_timing_read": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
+    "dm_prototypes_workspace_bytes": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
+    "dm_prototypes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "dm_correlate_pyramid_approx": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int,
+                                              C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t,
+                                              C.POINTER(C.c_void_p), C.c_void_p]),
 }
 NSTAGES = 4
 STAGES = ("descriptors", "level0_correlation", "levels", "backtracking")
@@ -181,6 +187,40 @@ def dm_correlate_pyramid(ctx, d_desc1, d_desc2, d_ws, stream=None) -> int:
     st = load().dm_correlate_pyramid(ctx, _dptr(d_desc1), W1, H1, _dptr(d_desc2), W2, H2, _dptr(d_ws),
                                      d_ws.numel() * d_ws.element_size(), C.byref(h), _stream_ptr(stream))
     _check(ctx, st, "dm_correlate_pyramid")
+    return h.value
+
+
+def dm_prototypes_workspace_bytes(ctx, W1, H1, D) -> int:
+    n = C.c_size_t()
+    _check(ctx, load().dm_prototypes_workspace_bytes(ctx, W1, H1, D, C.byref(n)), "dm_prototypes_workspace_bytes")
+    return n.value
+
+
+def dm_prototypes(ctx, d_desc1, D, iters, d_protos, d_assign, d_ws, init=None, stream=None):
+    """Approximate form (Sec. 4.1): the D-prototype dictionary of image 1's
+    atomic patches (spherical k-means) into d_protos [D][144] and the
+    prototype of every atomic patch into d_assign [P0] (int32).  `init`: D
+    patch indices (a host sequence) or None for evenly spaced patches."""
+    H1, W1, _ = d_desc1.shape
+    h_init = None
+    if init is not None:
+        arr = (C.c_int * D)(*[int(v) for v in init])
+        h_init = C.cast(arr, C.c_void_p)
+    st = load().dm_prototypes(ctx, _dptr(d_desc1), W1, H1, D, iters, h_init, _dptr(d_protos), _dptr(d_assign),
+                              _dptr(d_ws), d_ws.numel() * d_ws.element_size(), _stream_ptr(stream))
+    _check(ctx, st, "dm_prototypes")
+
+
+def dm_correlate_pyramid_approx(ctx, d_protos, d_assign, W1, H1, d_desc2, d_ws, stream=None) -> int:
+    """Approximate form (Sec. 4.1): the pyramid with every atomic patch of
+    image 1 replaced by its prototype (level 0 computed once per prototype)."""
+    D = d_protos.shape[0]
+    H2, W2, _ = d_desc2.shape
+    h = C.c_void_p()
+    st = load().dm_correlate_pyramid_approx(ctx, _dptr(d_protos), D, _dptr(d_assign), W1, H1, _dptr(d_desc2), W2, H2,
+                                            _dptr(d_ws), d_ws.numel() * d_ws.element_size(), C.byref(h),
+                                            _stream_ptr(stream))
+    _check(ctx, st, "dm_correlate_pyramid_approx")
     return h.value
 
 
