@@ -51,6 +51,7 @@ def _args():
     ap.add_argument("--batch-replays", type=int, default=3)
     ap.add_argument("--batch-lanes", type=int, default=2, help="concurrent lanes of the batched form (1..4)")
     ap.add_argument("--batch-pairs", type=int, default=8, help="pairs per step of the headline batched measurement")
+    ap.add_argument("--no-approx", action="store_true", help="skip the approximate-form (Sec. 4.1) measurement")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default launch shapes instead of autotuning them first")
     return ap.parse_args()
@@ -266,6 +267,73 @@ def _measure(dm, torch, dist, ctx, pair, a, world, local, stream):
                 stages={k: v / max(ncalls, 1) for k, v in stages.items()},
                 launches=launches, e2e=_job_throughput(world, a.steps, e2e_s), status=status, reached=reached,
                 matches=n_matches, clocks=clk.summary(), geo=geo, tuned=tuned)
+
+
+def _measure_approx(dm, torch, a, pair, stream, D=1024, iters=10):
+    """Approximate form (Sec. 4.1) with BF16 level 0 over the prototypes.  One
+    step = descriptors of both images, the spherical k-means (D prototypes,
+    `iters` iterations, evenly spaced start), the approximate pyramid and
+    backtracking; K steps timed with CUDA events on the library's stream, per
+    stage.  Also: how many of its matches land within 10 px of the exact BF16
+    path's match for the same atomic patch."""
+    import numpy as np
+    W, H = a.width, a.height
+    ctx = dm.Context(dm.DM_BF16)
+    try:
+        geo = dm.dm_geometry(W, H, W, H)
+        P0 = geo["n_patch0"]
+        D = min(D, P0)
+        i1, i2 = torch.from_numpy(pair.img1).cuda(), torch.from_numpy(pair.img2).cuda()
+        sizes = dm.dm_workspace_bytes(ctx.ctx, W, H, W, H)
+        dws = torch.empty(sizes["desc"], dtype=torch.uint8, device="cuda")
+        pws = torch.empty(sizes["pyramid"], dtype=torch.uint8, device="cuda")
+        bws = torch.empty(sizes["backtrack"], dtype=torch.uint8, device="cuda")
+        kws = torch.empty(dm.dm_prototypes_workspace_bytes(ctx.ctx, W, H, D), dtype=torch.uint8, device="cuda")
+        d1 = torch.empty((H, W, 9), dtype=torch.float32, device="cuda")
+        d2 = torch.empty((H, W, 9), dtype=torch.float32, device="cuda")
+        protos = torch.empty((D, 144), dtype=torch.float32, device="cuda")
+        assign = torch.empty(P0, dtype=torch.int32, device="cuda")
+        out = torch.empty((P0, 5), dtype=torch.float32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+        names = ("descriptors", "kmeans", "pyramid", "backtracking")
+
+        def step(ev=None):
+            if ev: ev[0].record(stream)
+            dm.dm_descriptors(ctx.ctx, i1, d1, dws, stream)
+            dm.dm_descriptors(ctx.ctx, i2, d2, dws, stream)
+            if ev: ev[1].record(stream)
+            dm.dm_prototypes(ctx.ctx, d1, D, iters, protos, assign, kws, stream=stream)
+            if ev: ev[2].record(stream)
+            h = dm.dm_correlate_pyramid_approx(ctx.ctx, protos, assign, W, H, d2, pws, stream)
+            if ev: ev[3].record(stream)
+            dm.dm_backtrack(ctx.ctx, h, bws, out, cnt, stream)
+            if ev: ev[4].record(stream)
+            dm.dm_pyramid_free(h)
+
+        for _ in range(a.warmup):
+            step()
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(a.steps)]
+        for k in range(a.steps):
+            step(evs[k])
+        torch.cuda.synchronize()
+        stages = {n: sum(e[i].elapsed_time(e[i + 1]) for e in evs) / a.steps for i, n in enumerate(names)}
+        ms = sum(e[0].elapsed_time(e[4]) for e in evs) / a.steps
+        approx_m = out[:int(cnt.item())].cpu().numpy()
+        # the exact BF16 matches of the same pair, for the agreement figure
+        ws = ctx.workspace("match", W, H, W, H)
+        dm.dm_match(ctx.ctx, i1, i2, ws, out, cnt, stream)
+        torch.cuda.synchronize()
+        exact_m = out[:int(cnt.item())].cpu().numpy()
+    finally:
+        ctx.close()
+    ex = {(float(m[0]), float(m[1])): (float(m[2]), float(m[3])) for m in exact_m}
+    close = [max(abs(m[2] - ex[k][0]), abs(m[3] - ex[k][1])) <= 10.0
+             for m in approx_m for k in [(float(m[0]), float(m[1]))] if k in ex]
+    return {"D": D, "kmeans_iterations": iters, "precision": "bf16", "pairs_per_s": 1000.0 / ms,
+            "ms_per_step": ms, "stages_ms": stages, "matches": int(len(approx_m)), "exact_matches": int(len(exact_m)),
+            "within_10px_of_exact": float(np.mean(close)) if close else None,
+            "note": "one pair per step; the prototype dictionary is learned on every step"}
 
 
 BATCH_SIZES = [(320, 240), (640, 480), (1024, 436), (1242, 375)]
@@ -496,6 +564,11 @@ def run_ours(a):
         del ctx
         torch.cuda.empty_cache()
 
+    approx = None
+    if not a.no_approx and world == 1:
+        approx = _measure_approx(dm, torch, a, pair, stream)
+        torch.cuda.empty_cache()
+
     if rank == 0:
         peaks = {}
         pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -549,6 +622,7 @@ def run_ours(a):
             "single_pair": {"pairs_per_s": r["value"], "ms_per_step": r["ms"] / a.steps, "e2e_pairs_per_s": r["e2e"],
                             "note": "one pair per step, no graph; stage times and rooflines come from these steps"},
             "batched": batch,
+            "approx": approx,
             "stages_ms": r["stages"],
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_v, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -159,8 +159,8 @@ dm_status dm_correlate_pyramid(dm_ctx* ctx, const float* d_desc1, int W1, int H1
  * [D][144] (FP32) and d_assign [P0] (prototype of each atomic patch, int32).
  * The member sums are exact fixed-point sums, so the result does not depend
  * on the order of the atomic updates.  D in [1, P0] (P0 = dm_geometry's
- * n_patch0); d_ws >= dm_prototypes_workspace_bytes; waits for `stream` once,
- * after copying h_init (not capturable).
+ * n_patch0); d_ws >= dm_prototypes_workspace_bytes.  h_init is copied from
+ * pageable memory on `stream` (not capturable in a CUDA graph).
  *
  * dm_correlate_pyramid_approx: the pyramid of dm_correlate_pyramid with atomic
  * patch p of image 1 replaced by d_protos[d_assign[p]]: level 0 is computed

@@ -468,10 +468,10 @@ dm_status dm_prototypes(dm_ctx* ctx, const float* d_desc1, int W1, int H1, int D
     DevGuard dg(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     int* d_init = reinterpret_cast<int*>((char*)d_ws + dm_kmeans_init_offset(g, D));
+    // a copy from pageable memory returns once the source has been staged, so
+    // `init` may go out of scope right after it
     cudaError_t e = cudaMemcpyAsync(d_init, init.data(), (size_t)D * sizeof(int), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "copy init");
-    // the pageable source must stay valid until the copy has read it
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(ctx, e, "copy init");
     e = dm_launch_kmeans(g, d_desc1, D, iters, d_init, d_protos, d_assign, (char*)d_ws, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "k-means kernels");
     return DM_OK;

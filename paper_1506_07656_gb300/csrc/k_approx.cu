@@ -10,8 +10,8 @@
 // One iteration = assignment, then update:
 //   assignment: the closest centroid = the largest dot product (all centroids
 //     have the same norm), ties to the lower index.  k_km_assign fuses the
-//     P0 x D x 144 product with the running argmax: a CTA stages 64 patch
-//     vectors in shared memory once and streams the centroids in tiles of 48;
+//     P0 x D x 144 product with the running argmax: a CTA stages 128 patch
+//     vectors in shared memory once and streams the centroids in tiles of 64;
 //     each dot product is one fma chain over k = 0..143 in FP32.
 //   update: each centroid = the sum of its members projected to norm 4 (a
 //     centroid without members keeps its value).  The member sums are exact
@@ -24,8 +24,10 @@
 
 namespace {
 
-constexpr int KM_BM = 64;      // patches per CTA of the assignment
-constexpr int KM_BN = 48;      // centroids per tile
+constexpr int KM_BM = 128;     // patches per CTA of the assignment
+constexpr int KM_BN = 64;      // centroids per tile
+constexpr int ASTR = KM_BM + 4;   // shared row strides (16-byte multiples, fewer bank conflicts on the transposing stores)
+constexpr int CSTR = KM_BN + 4;
 constexpr int KD = 144;
 constexpr double FIX = 1099511627776.0;   // 2^40
 
@@ -63,58 +65,64 @@ __global__ void k_km_init(const float* __restrict__ A, const int* __restrict__ i
 
 __device__ __forceinline__ bool better(float s, int i, float bs, int bi) { return s > bs || (s == bs && i < bi); }
 
-// assign[p] = argmax_d <A_p, C_d> (first maximum).  Dynamic shared memory:
-// As[144][64] patch vectors, Cs[144][48] centroids.
+// The best centroid of chunk blockIdx.y (centroids [y*chunk, (y+1)*chunk))
+// for each patch: (score, index) into part_s / part_i [gridDim.y][P0].  A
+// CTA holds 128 patch vectors (As[144][132]) and streams its centroids in
+// tiles of 64 (Cs[144][68]); a thread owns 8 patches x 4 centroids of each
+// tile (vector shared loads, 32 fmas per 3 loads) and keeps its patches'
+// running best.
 __global__ void __launch_bounds__(256) k_km_assign(const float* __restrict__ A, int P0, const float* __restrict__ C, int D,
-                                                   int* __restrict__ assign) {
+                                                   int chunk, float* __restrict__ part_s, int* __restrict__ part_i) {
     extern __shared__ __align__(16) float kms[];
-    float* As = kms;                       // [KD][KM_BM]
-    float* Cs = kms + KD * KM_BM;          // [KD][KM_BN]
+    float* As = kms;                       // [KD][ASTR]
+    float* Cs = kms + KD * ASTR;           // [KD][CSTR]
     const int tid = threadIdx.x, p0 = blockIdx.x * KM_BM;
+    // staged transposed; the global reads run along k (coalesced)
     for (int e = tid; e < KD * KM_BM; e += 256) {
-        const int m = e % KM_BM, k = e / KM_BM;
-        As[e] = p0 + m < P0 ? A[(long long)(p0 + m) * KD + k] : 0.0f;
+        const int m = e / KD, k = e - m * KD;
+        As[k * ASTR + m] = p0 + m < P0 ? A[(long long)(p0 + m) * KD + k] : 0.0f;
     }
-    const int tm = (tid % 16) * 4, tn = (tid / 16) * 3;
-    float best[4];
-    int bidx[4];
+    const int tm = (tid % 16) * 8, tn = (tid / 16) * 4;
+    float best[8];
+    int bidx[8];
 #pragma unroll
-    for (int i = 0; i < 4; i++) { best[i] = -INFINITY; bidx[i] = 0x7fffffff; }
-    for (int n0 = 0; n0 < D; n0 += KM_BN) {
+    for (int i = 0; i < 8; i++) { best[i] = -INFINITY; bidx[i] = 0x7fffffff; }
+    const int nb = blockIdx.y * chunk, ne = min(D, nb + chunk);
+    for (int n0 = nb; n0 < ne; n0 += KM_BN) {
         __syncthreads();
         for (int e = tid; e < KD * KM_BN; e += 256) {
-            const int n = e % KM_BN, k = e / KM_BN;
-            Cs[e] = n0 + n < D ? C[(long long)(n0 + n) * KD + k] : 0.0f;
+            const int n = e / KD, k = e - n * KD;
+            Cs[k * CSTR + n] = n0 + n < ne ? C[(long long)(n0 + n) * KD + k] : 0.0f;
         }
         __syncthreads();
-        float acc[4][3] = {};
-#pragma unroll 4
+        float acc[8][4] = {};
+#pragma unroll 2
         for (int k = 0; k < KD; k++) {
-            float a[4], b[3];
+            const float4 a0 = *reinterpret_cast<const float4*>(As + k * ASTR + tm);
+            const float4 a1 = *reinterpret_cast<const float4*>(As + k * ASTR + tm + 4);
+            const float4 b = *reinterpret_cast<const float4*>(Cs + k * CSTR + tn);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-            for (int i = 0; i < 4; i++) a[i] = As[k * KM_BM + tm + i];
+            for (int i = 0; i < 8; i++)
 #pragma unroll
-            for (int j = 0; j < 3; j++) b[j] = Cs[k * KM_BN + tn + j];
-#pragma unroll
-            for (int i = 0; i < 4; i++)
-#pragma unroll
-                for (int j = 0; j < 3; j++) acc[i][j] = __fmaf_rn(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < 4; j++) acc[i][j] = __fmaf_rn(av[i], bv[j], acc[i][j]);
         }
 #pragma unroll
-        for (int j = 0; j < 3; j++) {
+        for (int j = 0; j < 4; j++) {
             const int d = n0 + tn + j;
-            if (d >= D) continue;
+            if (d >= ne) continue;
 #pragma unroll
-            for (int i = 0; i < 4; i++)
+            for (int i = 0; i < 8; i++)
                 if (better(acc[i][j], d, best[i], bidx[i])) { best[i] = acc[i][j]; bidx[i] = d; }
         }
     }
-    // the 16 threads holding the same 4 patches (different centroid columns) agree
+    // the 16 threads holding the same 8 patches (different centroid columns) agree
     __syncthreads();
     float* rs = Cs;                                          // [16][KM_BM]
     int* ri = reinterpret_cast<int*>(Cs + 16 * KM_BM);       // [16][KM_BM]
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
+    for (int i = 0; i < 8; i++) {
         rs[(tid / 16) * KM_BM + tm + i] = best[i];
         ri[(tid / 16) * KM_BM + tm + i] = bidx[i];
     }
@@ -124,8 +132,25 @@ __global__ void __launch_bounds__(256) k_km_assign(const float* __restrict__ A, 
         int bi = ri[tid];
         for (int j = 1; j < 16; j++)
             if (better(rs[j * KM_BM + tid], ri[j * KM_BM + tid], bs, bi)) { bs = rs[j * KM_BM + tid]; bi = ri[j * KM_BM + tid]; }
-        assign[p0 + tid] = bi < D ? bi : 0;                  // (no finite score at all: prototype 0)
+        part_s[(long long)blockIdx.y * P0 + p0 + tid] = bs;
+        part_i[(long long)blockIdx.y * P0 + p0 + tid] = bi;
     }
+}
+
+// assign[p] = the best of the chunks' candidates (same order rule: the larger
+// score, then the lower index), so the split does not change the result.
+__global__ void k_km_merge(const float* __restrict__ part_s, const int* __restrict__ part_i, int P0, int nchunk, int D,
+                           int* __restrict__ assign) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P0) return;
+    float bs = part_s[p];
+    int bi = part_i[p];
+    for (int y = 1; y < nchunk; y++)
+        if (better(part_s[(long long)y * P0 + p], part_i[(long long)y * P0 + p], bs, bi)) {
+            bs = part_s[(long long)y * P0 + p];
+            bi = part_i[(long long)y * P0 + p];
+        }
+    assign[p] = bi < D ? bi : 0;                             // (no finite score at all: prototype 0)
 }
 
 // S[d][k] += A[p][k] in 2^-40 fixed point, cnt[d] += 1, for d = assign[p].
@@ -152,7 +177,8 @@ __global__ void k_km_finish(const unsigned long long* __restrict__ S, const unsi
 }
 
 struct KmLayout {
-    size_t A, S, cnt, init, bytes;
+    size_t A, S, cnt, init, part_s, part_i, bytes;
+    int nchunk, chunk;
 };
 
 KmLayout km_layout(const DmGeom& g, int D) {
@@ -162,6 +188,16 @@ KmLayout km_layout(const DmGeom& g, int D) {
     l.S = o;    o += dm_align((size_t)D * KD * sizeof(unsigned long long));
     l.cnt = o;  o += dm_align((size_t)D * sizeof(unsigned int));
     l.init = o; o += dm_align((size_t)D * sizeof(int));
+    // centroid chunks: enough CTAs for about three waves of two per SM on 152 SMs
+    const int P0 = g.P0x * g.P0y;
+    const int mblocks = (P0 + KM_BM - 1) / KM_BM;
+    const int want = (912 + mblocks - 1) / mblocks;
+    const int maxc = (D + KM_BN - 1) / KM_BN;
+    const int nsplit = want < 1 ? 1 : (want > maxc ? maxc : want);
+    l.chunk = (((D + nsplit - 1) / nsplit) + KM_BN - 1) / KM_BN * KM_BN;
+    l.nchunk = (D + l.chunk - 1) / l.chunk;
+    l.part_s = o; o += dm_align((size_t)l.nchunk * P0 * sizeof(float));
+    l.part_i = o; o += dm_align((size_t)l.nchunk * P0 * sizeof(int));
     l.bytes = o;
     return l;
 }
@@ -179,24 +215,30 @@ cudaError_t dm_launch_kmeans(const DmGeom& g, const float* d1, int D, int iters,
     unsigned int* cnt = reinterpret_cast<unsigned int*>(ws + l.cnt);
     const int P0 = g.P0x * g.P0y;
     const long long n = (long long)P0 * KD;
-    const size_t smem = (size_t)KD * (KM_BM + KM_BN) * sizeof(float);
+    const size_t smem = (size_t)KD * (ASTR + CSTR) * sizeof(float);
     static std::atomic<unsigned long long> smem_done{0};
     cudaError_t e = dm_smem_opt_in(reinterpret_cast<const void*>(k_km_assign), (int)smem, smem_done);
     if (e != cudaSuccess) return e;
-    const unsigned nb = (unsigned)((n + 255) / 256), ab = (unsigned)((P0 + KM_BM - 1) / KM_BM);
+    float* part_s = reinterpret_cast<float*>(ws + l.part_s);
+    int* part_i = reinterpret_cast<int*>(ws + l.part_i);
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    const dim3 ag((unsigned)((P0 + KM_BM - 1) / KM_BM), (unsigned)l.nchunk);
+    const unsigned mb = (unsigned)((P0 + 255) / 256);
     k_patch_vectors<<<nb, 256, 0, st>>>(g, d1, A);
     k_km_init<<<D, 160, 0, st>>>(A, init, protos);
     long long launches = 2;
     for (int it = 0; it < iters; it++) {
-        k_km_assign<<<ab, 256, smem, st>>>(A, P0, protos, D, assign);
+        k_km_assign<<<ag, 256, smem, st>>>(A, P0, protos, D, l.chunk, part_s, part_i);
+        k_km_merge<<<mb, 256, 0, st>>>(part_s, part_i, P0, l.nchunk, D, assign);
         if ((e = cudaMemsetAsync(S, 0, (size_t)D * KD * sizeof(unsigned long long), st)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(cnt, 0, (size_t)D * sizeof(unsigned int), st)) != cudaSuccess) return e;
         k_km_accum<<<nb, 256, 0, st>>>(A, n, assign, S, cnt);
         k_km_finish<<<D, 160, 0, st>>>(S, cnt, protos);
-        launches += 3;
+        launches += 4;
     }
-    k_km_assign<<<ab, 256, smem, st>>>(A, P0, protos, D, assign);
-    dm_count_launches(launches + 1);
+    k_km_assign<<<ag, 256, smem, st>>>(A, P0, protos, D, l.chunk, part_s, part_i);
+    k_km_merge<<<mb, 256, 0, st>>>(part_s, part_i, P0, l.nchunk, D, assign);
+    dm_count_launches(launches + 2);
     return cudaGetLastError();
 }
 
