@@ -24,6 +24,9 @@ Functions and the passages they follow:
                   projected back on the hypersphere after every update
   approx_match()  Sec. 4.1: the chain with every atomic patch replaced by its
                   closest prototype
+  warp()          Algorithm 2: image downsized by sigma and rotated by -k pi/4
+  invariant_match() Algorithm 2: the chain over 9 scales x 8 rotations, the
+                  atomic correspondences mapped back and pooled, then Eq. 16
 """
 from __future__ import annotations
 
@@ -241,9 +244,10 @@ class Backtrack:
     leaf: np.ndarray | None  # [P0][H2][W2] merged atomic scores (optional)
     reached: np.ndarray    # [L+1] distinct tuples per level
     gap: np.ndarray | None = None   # [P0] smallest relative top-two gap of the decisions behind BestAt(p)
+    leaf_raw: np.ndarray | None = None   # [P0][H2][W2] unrounded merged scores (FP32: fixed-point integers), -1 = none
 
 
-def backtrack(pyr: Pyramid, dense_leaf: bool = False) -> Backtrack:
+def backtrack(pyr: Pyramid, dense_leaf: bool = False, leaf_raw: bool = False) -> Backtrack:
     g = pyr.geom
     dt = _dtype(pyr.prec)
     n0 = g.npatch(0)
@@ -257,12 +261,15 @@ def backtrack(pyr: Pyramid, dense_leaf: bool = False) -> Backtrack:
     if pyr.gap is not None:
         bt.gap = np.zeros(n0, np.float64)
         gg = (C.c_void_p * g.L)(*[a.ctypes.data for a in pyr.gap])
+    if leaf_raw:
+        bt.leaf_raw = np.zeros((n0, g.H2, g.W2), np.float64)
     lib = _lib(pyr.prec)
-    lib.orc_backtrack.argtypes = [C.c_int] * 4 + [C.c_void_p] * 12
+    lib.orc_backtrack.argtypes = [C.c_int] * 4 + [C.c_void_p] * 13
     rc = lib.orc_backtrack(g.W1, g.H1, g.W2, g.H2, pp, aa, _ptr(pyr.top), vv,
                            _ptr(bt.bestP_s), _ptr(bt.bestP_i), _ptr(bt.bestQ_s), _ptr(bt.bestQ_i),
                            _ptr(bt.leaf) if dense_leaf else None, _ptr(bt.reached), gg,
-                           _ptr(bt.gap) if bt.gap is not None else None)
+                           _ptr(bt.gap) if bt.gap is not None else None,
+                           _ptr(bt.leaf_raw) if leaf_raw else None)
     if rc != 0:
         raise ValueError("backtrack oracle failed")
     return bt
@@ -349,6 +356,156 @@ def approx_match(img1: np.ndarray, img2: np.ndarray, protos: np.ndarray, assign:
     pyr = pyramid(d1, d2, prec, lam, compensated, patches=q)
     bt = backtrack(pyr)
     return reciprocal(pyr, bt), pyr, bt
+
+
+# --------------------------------------------------------------------------- #
+# Scale and rotation invariant form (Algorithm 2)                              #
+# --------------------------------------------------------------------------- #
+# Scale factors 2^(|sigma|) for sigma = 0, 0.5, .., 2 and the rotation table
+# cos / sin of k pi/4 (k = 0..7): definitions, rounded to the working precision.
+INV_SCALES = (1.0, 1.4142135623730951, 2.0, 2.8284271247461903, 4.0)
+_H = 0.70710678118654752440
+ROT_C = (1.0, _H, 0.0, -_H, -1.0, -_H, 0.0, _H)
+ROT_S = (0.0, _H, 1.0, _H, 0.0, -_H, -1.0, -_H)
+
+
+def invariant_transforms():
+    """Algorithm 2's loop order: sigma = -2, -1.5, .., 2 (outer), theta = k pi/4,
+    k = 0..7 (inner); sigma1 = max(1, 2^sigma) downsizes image 1, sigma2 =
+    max(1, 2^-sigma) image 2.  Entries (sigma1, sigma2, k)."""
+    out = []
+    for j in range(9):
+        a = abs(j - 4)
+        s1 = INV_SCALES[a] if j >= 4 else 1.0
+        s2 = INV_SCALES[a] if j < 4 else 1.0
+        for k in range(8):
+            out.append((s1, s2, k))
+    return out
+
+
+def canvas_size(W: int, H: int, sigma: float, k: int):
+    """Size of image W x H downsized by sigma and rotated by k pi/4 (the
+    bounding box, so nothing is cropped), computed in double precision."""
+    c, s = abs(ROT_C[k]), abs(ROT_S[k])
+    Wr = max(1, int(np.floor((W * c + H * s) / sigma + 0.5)))
+    Hr = max(1, int(np.floor((W * s + H * c) / sigma + 0.5)))
+    return Wr, Hr
+
+
+def _to_source(u, v, W, H, Wr, Hr, sigma, k, dt):
+    """Canvas pixel (u, v) -> point of the original W x H image: the offset from
+    the canvas centre rotated by +k pi/4 and scaled by sigma, about the image
+    centre (fixed order of rounded operations in dtype dt)."""
+    c, s, sg = dt(ROT_C[k]), dt(ROT_S[k]), dt(sigma)
+    cu, cv = dt((Wr - 1) * 0.5), dt((Hr - 1) * 0.5)
+    cx, cy = dt((W - 1) * 0.5), dt((H - 1) * 0.5)
+    du = np.asarray(u, dtype=dt) - cu
+    dv = np.asarray(v, dtype=dt) - cv
+    rx = (c * du) - (s * dv)
+    ry = (s * du) + (c * dv)
+    return cx + sg * rx, cy + sg * ry
+
+
+def warp(img: np.ndarray, sigma: float, k: int, prec: str = "f64") -> np.ndarray:
+    """Algorithm 2's R_{-theta} * I_sigma: image downsized by sigma and rotated
+    by -k pi/4 on the canvas of canvas_size(); bilinear interpolation (reading:
+    the paper does not state the resampling; no prefilter -- the descriptor's
+    own smoothing follows), zero outside the image."""
+    dt = np.float32 if prec == "f32" else np.float64
+    H, W = img.shape
+    Wr, Hr = canvas_size(W, H, sigma, k)
+    v, u = np.mgrid[0:Hr, 0:Wr]
+    x, y = _to_source(u, v, W, H, Wr, Hr, sigma, k, dt)
+    x0, y0 = np.floor(x), np.floor(y)
+    fx, fy = x - x0, y - y0
+    I = np.asarray(img, dtype=dt)
+    xi, yi = x0.astype(np.int64), y0.astype(np.int64)
+
+    def px(yy, xx):
+        ok = (xx >= 0) & (yy >= 0) & (xx < W) & (yy < H)
+        return np.where(ok, I[np.clip(yy, 0, H - 1), np.clip(xx, 0, W - 1)], dt(0))
+
+    p00, p10, p01, p11 = px(yi, xi), px(yi, xi + 1), px(yi + 1, xi), px(yi + 1, xi + 1)
+    top = p00 + fx * (p10 - p00)
+    bot = p01 + fx * (p11 - p01)
+    return (top + fy * (bot - top)).astype(dt)
+
+
+def _round_px(x, n):
+    """Nearest pixel index (floor(x + 1/2)) clamped to [0, n)."""
+    return np.clip(np.floor(x + x.dtype.type(0.5)).astype(np.int64), 0, n - 1)
+
+
+def invariant_match(img1: np.ndarray, img2: np.ndarray, prec: str = "f64", transforms=None, **cfg):
+    """Algorithm 2: DeepMatching of I downsized by sigma1 against I' downsized by
+    sigma2 and rotated by -theta, for every transform; every atomic
+    correspondence (the merged leaf tuples, Eq. 15) is mapped back to the input
+    images (p -> sigma1 p, p' -> sigma2 R_theta p', here about the image
+    centres, rounded to the nearest pixel) and pooled; Eq. 16 then keeps the
+    tuples that are the best of their 4x4 cell of I (an atomic patch of I) and
+    of I' (readings c17, c24-c26).  Transforms whose images are too small for
+    the pyramid are skipped.  Rows (x1, y1, x2, y2, score) in patch order."""
+    c = dict(DEFAULT_CFG, **cfg)
+    lam = c.pop("lam")
+    dt = np.float32 if prec == "f32" else np.float64
+    H1, W1 = img1.shape
+    H2, W2 = img2.shape
+    go = geometry(W1, H1, W2, H2)
+    P0x, P0y = go.P0x, go.P0y
+    CW2 = (W2 + 3) // 4
+    cells1, tpix, qloc, scores = [], [], [], []
+    for (s1, s2, k) in (transforms or invariant_transforms()):
+        i1 = warp(img1, s1, 0, prec)
+        i2 = warp(img2, s2, k, prec)
+        h1, w1 = i1.shape
+        h2, w2 = i2.shape
+        if min(w1, h1) < 4 or max(w1, h1) < 5 or min(w2, h2) < 1:
+            continue
+        d1 = descriptors(i1, prec, **c)
+        d2 = descriptors(i2, prec, **c)
+        pyr = pyramid(d1, d2, prec, lam)
+        bt = backtrack(pyr, leaf_raw=True)
+        p, ty, tx = np.nonzero(bt.leaf_raw >= 0)
+        if len(p) == 0:
+            continue
+        sc = bt.leaf_raw[p, ty, tx]
+        g = pyr.geom
+        # image 1: patch centre (rotation 0) -> original cell (atomic patch)
+        x1, y1 = _to_source(4 * (p % g.P0x) + 2, 4 * (p // g.P0x) + 2, W1, H1, w1, h1, s1, 0, dt)
+        X1, Y1 = _round_px(x1, W1), _round_px(y1, H1)
+        C1 = np.minimum(Y1 >> 2, P0y - 1) * P0x + np.minimum(X1 >> 2, P0x - 1)
+        # image 2: canvas pixel -> original pixel
+        x2, y2 = _to_source(tx, ty, W2, H2, w2, h2, s2, k, dt)
+        X2, Y2 = _round_px(x2, W2), _round_px(y2, H2)
+        cells1.append(C1)
+        tpix.append(Y2 * W2 + X2)
+        qloc.append((Y2 & 3) * 4 + (X2 & 3))
+        scores.append(sc)
+    out = []
+    if cells1:
+        C1 = np.concatenate(cells1)
+        T = np.concatenate(tpix)
+        Q = C1 * 16 + np.concatenate(qloc)
+        S = np.concatenate(scores)
+        cell2 = (T // W2 >> 2) * CW2 + (T % W2 >> 2)
+        # BestAt: per cell of I the larger score, then the lower pixel index of I'
+        o = np.lexsort((T, -S, C1))
+        first = np.ones(len(o), bool)
+        first[1:] = C1[o][1:] != C1[o][:-1]
+        bestP = {int(C1[i]): (S[i], int(T[i])) for i in o[first]}
+        # BestAt': per cell of I' the larger score, then the lower (patch, offset) index
+        o = np.lexsort((Q, -S, cell2))
+        first = np.ones(len(o), bool)
+        first[1:] = cell2[o][1:] != cell2[o][:-1]
+        bestQ = {int(cell2[i]): (S[i], int(Q[i])) for i in o[first]}
+        for c1 in sorted(bestP):
+            s, t = bestP[c1]
+            tx_, ty_ = t % W2, t // W2
+            q = bestQ.get((ty_ >> 2) * CW2 + (tx_ >> 2))
+            if q is not None and q[0] == s and q[1] == c1 * 16 + (ty_ & 3) * 4 + (tx_ & 3):
+                score = float(np.float32(s) * np.float32(1.0 / 268435456.0)) if prec == "f32" else float(s)
+                out.append((4 * (c1 % P0x) + 2, 4 * (c1 // P0x) + 2, tx_, ty_, score))
+    return np.array(out, dtype=np.float64).reshape(-1, 5)
 
 
 def loss_grad(d1: np.ndarray, d2: np.ndarray, prec: str = "f64", lam: float = DEFAULT_CFG["lam"]):

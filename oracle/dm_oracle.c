@@ -643,6 +643,8 @@ int orc_level1_pooled(const real* d1, int W1, int H1, const real* d2, int W2, in
 /*   BestAt(p)   : best tuple of atomic patch p (its own 4x4 cell of I),       */
 /*   BestAt'(c)  : best tuple whose t lies in the 4x4 cell c of I'.            */
 /* leaf (optional, [P0][H2][W2]): the merged atomic scores themselves.        */
+/* leaf_raw (optional, same shape): the same scores unrounded -- the FP32      */
+/* mirror's fixed-point integers, exact as doubles -- or -1 where absent.     */
 /* reached[l]   : number of distinct tuples at level l (l = 0..L).            */
 /* ------------------------------------------------------------------------- */
 
@@ -672,7 +674,7 @@ static int better(pscore s, long long idx, pscore bs, long long bidx) {
 
 int orc_backtrack(int W1, int H1, int W2, int H2, real** pooled, uint8_t** amax, const real* top, uint8_t** valid,
                   real* bestP_s, long long* bestP_i, real* bestQ_s, long long* bestQ_i, real* leaf, long long* reached,
-                  double** pgap, double* gap) {
+                  double** pgap, double* gap, double* leaf_raw) {
     geom g;
     if (make_geom(W1, H1, W2, H2, &g)) return -1;
     const int L = g.L;
@@ -684,7 +686,7 @@ int orc_backtrack(int W1, int H1, int W2, int H2, real** pooled, uint8_t** amax,
     for (int p = 0; p < n0; p++) { bP[p] = PS_NONE; bestP_i[p] = -1; }
     for (int c = 0; c < CW * CH; c++) { bQ[c] = PS_NONE; bestQ_i[c] = -1; }
     pscore* lf = NULL;
-    if (leaf || gap) {
+    if (leaf || gap || leaf_raw) {
         lf = (pscore*)malloc((size_t)n0 * W2 * H2 * sizeof(pscore));
         if (!lf) { free(bP); free(bQ); return -2; }
         for (size_t k = 0; k < (size_t)n0 * W2 * H2; k++) lf[k] = PS_NONE;
@@ -840,6 +842,7 @@ int orc_backtrack(int W1, int H1, int W2, int H2, real** pooled, uint8_t** amax,
         for (size_t k = 0; k < (size_t)n0 * W2 * H2; k++) {
             cnt += (lf[k] != PS_NONE);
             if (leaf) leaf[k] = lf[k] == PS_NONE ? RNEG_INF : ps_value(lf[k]);
+            if (leaf_raw) leaf_raw[k] = lf[k] == PS_NONE ? -1.0 : (double)lf[k];
         }
         reached[0] = cnt;
     } else {
