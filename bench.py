@@ -52,6 +52,8 @@ def _args():
     ap.add_argument("--batch-lanes", type=int, default=2, help="concurrent lanes of the batched form (1..4)")
     ap.add_argument("--batch-pairs", type=int, default=8, help="pairs per step of the headline batched measurement")
     ap.add_argument("--no-approx", action="store_true", help="skip the approximate-form (Sec. 4.1) measurement")
+    ap.add_argument("--no-invariant", action="store_true",
+                    help="skip the scale and rotation invariant form (Sec. 4.2) measurement")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default launch shapes instead of autotuning them first")
     return ap.parse_args()
@@ -336,6 +338,61 @@ def _measure_approx(dm, torch, a, pair, stream, D=1024, iters=10):
             "note": "one pair per step; the prototype dictionary is learned on every step"}
 
 
+def _measure_invariant(dm, torch, a, stream, W=512, H=224, prec="bf16"):
+    """Scale and rotation invariant form (Sec. 4.2, Algorithm 2): 72 runs of the
+    method (9 scales x 8 rotations) on image 1 against image 2 = image 1 turned
+    by a quarter, pooled and verified once.  W x H is the largest size whose
+    45-degree canvases keep the merge keys within 32 bits at this aspect ratio.
+    One step = one dm_match_invariant call; K steps timed with CUDA events on
+    the library's stream.  Also: the fraction of matches consistent (3 px) with
+    the quarter turn, and the same figure for the exact form."""
+    import numpy as np
+    from paper_1506_07656_gb300 import synth
+    img1 = synth.make_pair_smooth(W, H, seed=2, max_disp=1.0).img1.astype(np.float32)
+    img2 = np.ascontiguousarray(np.rot90(img1, 1))
+    ctx = dm.Context(dm.DM_BF16 if prec == "bf16" else dm.DM_FP32)
+    try:
+        i1 = torch.from_numpy(img1).cuda()
+        i2 = torch.from_numpy(img2).cuda()
+        H2, W2 = img2.shape
+        ws = torch.empty(dm.dm_invariant_workspace_bytes(ctx.ctx, W, H, W2, H2), dtype=torch.uint8, device="cuda")
+        P0 = dm.dm_geometry(W, H, W2, H2)["n_patch0"]
+        out = torch.empty((P0, 5), dtype=torch.float32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+        launches0 = dm.dm_timing_read(ctx.ctx)[2]
+        dm.dm_match_invariant(ctx.ctx, i1, i2, ws, out, cnt, stream)
+        launches = dm.dm_timing_read(ctx.ctx)[2] - launches0
+        for _ in range(max(a.warmup - 1, 1)):
+            dm.dm_match_invariant(ctx.ctx, i1, i2, ws, out, cnt, stream)
+        torch.cuda.synchronize()
+        steps = max(min(a.steps, 5), 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            dm.dm_match_invariant(ctx.ctx, i1, i2, ws, out, cnt, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        status, _ = dm.dm_read_status(ctx.ctx, ws, 1)
+        inv = out[:int(cnt.item())].cpu().numpy().astype(np.float64)
+        mws = ctx.workspace("match", W, H, W2, H2)
+        dm.dm_match(ctx.ctx, i1, i2, mws, out, cnt, stream)
+        torch.cuda.synchronize()
+        exact = out[:int(cnt.item())].cpu().numpy().astype(np.float64)
+    finally:
+        ctx.close()
+
+    def turn(m):
+        if len(m) == 0:
+            return None
+        return float(np.mean((np.abs(m[:, 2] - m[:, 1]) <= 3) & (np.abs(m[:, 3] - (W - 1 - m[:, 0])) <= 3)))
+
+    return {"workload": f"{W}x{H} against its quarter turn", "transforms": 72, "precision": prec,
+            "pairs_per_s": 1000.0 / ms, "ms_per_step": ms, "kernel_launches_per_step": int(launches),
+            "status": int(status), "matches": int(len(inv)), "consistent_with_turn": turn(inv),
+            "exact_form_matches": int(len(exact)), "exact_form_consistent_with_turn": turn(exact)}
+
+
 BATCH_SIZES = [(320, 240), (640, 480), (1024, 436), (1242, 375)]
 
 
@@ -568,6 +625,10 @@ def run_ours(a):
     if not a.no_approx and world == 1:
         approx = _measure_approx(dm, torch, a, pair, stream)
         torch.cuda.empty_cache()
+    invariant = None
+    if not a.no_invariant and world == 1:
+        invariant = _measure_invariant(dm, torch, a, stream)
+        torch.cuda.empty_cache()
 
     if rank == 0:
         peaks = {}
@@ -623,6 +684,7 @@ def run_ours(a):
                             "note": "one pair per step, no graph; stage times and rooflines come from these steps"},
             "batched": batch,
             "approx": approx,
+            "invariant": invariant,
             "stages_ms": r["stages"],
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_v, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -215,8 +215,33 @@ dm_status dm_match(dm_ctx* ctx, const float* d_img1, int W1, int H1, const float
 dm_status dm_match_host(dm_ctx* ctx, const float* h_img1, int W1, int H1, const float* h_img2, int W2, int H2,
                         void* d_ws, size_t ws_bytes, dm_match_t* h_out, int capacity, int* h_count, void* stream);
 
+/* Scale and rotation invariant form (Sec. 4.2, Algorithm 2), device buffers.
+ * For sigma = -2, -1.5, .., 2 and theta = k pi/4 (k = 0..7) the method runs on
+ * image 1 downsized by sigma1 = max(1, 2^sigma) against image 2 downsized by
+ * sigma2 = max(1, 2^-sigma) and rotated by -theta.  A warped image lies on the
+ * bounding box of the scaled, rotated image (sizes rounded to the nearest
+ * integer), sampled bilinearly about the image centres, zero outside.  Every
+ * atomic correspondence of every run (Eq. 15) is rectified to the input pair
+ * (sigma1 p, sigma2 R_theta p' about the image centres, rounded to the
+ * nearest pixel; p's atomic patch of I is the 4x4 cell holding that pixel)
+ * and reduced into BestAt / BestAt' of the input pair; one reciprocal
+ * verification (Eq. 16) then writes the matches as dm_match does: up to
+ * `capacity` in atomic-patch order of image 1, *d_count (device int) the
+ * number found.  Transforms that leave an image below 4 pixels, or with no
+ * aggregation level, are skipped; DM_EUNSUPPORTED if a transform's warped
+ * pair exceeds the 32-bit merge keys (the 45-degree canvases are the
+ * largest).  The precision and parameters are the context's.  Runs entirely
+ * on `stream` with no host synchronisation.  Status words of all runs are
+ * OR-ed into the header at offset 0 of d_ws (dm_read_status; reached[] sums
+ * the runs).  d_ws >= *bytes of dm_invariant_workspace_bytes, 256-byte
+ * aligned; it is reused by each run in turn. */
+dm_status dm_invariant_workspace_bytes(dm_ctx* ctx, int W1, int H1, int W2, int H2, size_t* bytes);
+dm_status dm_match_invariant(dm_ctx* ctx, const float* d_img1, int W1, int H1, const float* d_img2, int W2, int H2,
+                             void* d_ws, size_t ws_bytes, dm_match_t* d_out, int capacity, int* d_count,
+                             void* stream);
+
 /* Synchronise `stream` and read the header at offset 0 of a pyramid,
- * backtracking or dm_match workspace: *status = DM_DEV_* bits (0 = fine;
+ * backtracking, dm_match or dm_match_invariant workspace: *status = DM_DEV_* bits (0 = fine;
  * DM_DEV_TIMEOUT if a bounded device-side wait of the pyramid step gave up);
  * reached[l] (l = 0..n_reached-1, may be NULL) = number of distinct merged
  * tuples at level l during the last backtracking (level 0: atomic tuples

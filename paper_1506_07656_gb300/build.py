@@ -3,8 +3,9 @@
 Each translation unit under ``csrc/`` is compiled in parallel with
 ``-gencode arch=compute_103a,code=sm_103a`` and linked into
 ``paper_1506_07656_gb300/libdm.so``.  Contraction of floating-point multiply
-and add is turned off (``-fmad=false``): kernels that want fused operations
-spell them out, so FP32 results are reproducible bit for bit.
+and add is turned off in device and host code (``-fmad=false``,
+``-ffp-contract=off``): code that wants fused operations spells them out, so
+FP32 results are reproducible bit for bit, on x86-64 and Arm hosts alike.
 """
 from __future__ import annotations
 
@@ -21,7 +22,8 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_objs")
 LIB = os.path.join(HERE, "libdm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing",
+         "-Xcompiler", "-ffp-contract=off"]
 
 
 def _nvcc() -> str:

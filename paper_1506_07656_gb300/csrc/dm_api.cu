@@ -175,6 +175,46 @@ dm_status run_pyramid(dm_ctx* c, const DmGeom& g, const float* d1, const float* 
     return DM_OK;
 }
 
+// Invariant form (Algorithm 2): the transforms whose warped pair the method
+// accepts -- a transform that leaves an image too small for one aggregation
+// level is skipped -- and the workspace: the call's header, the input pair's
+// BestAt / BestAt' arrays, then one dm_match workspace sized for the largest
+// transform, reused by each transform in turn (warped images in its image
+// slots).
+struct InvLayout {
+    size_t header, bestP, bestQ, match, bytes;
+};
+
+struct InvStep {
+    DmInvTransform t;
+    DmGeom g;
+    MatchLayout ml;
+};
+
+dm_status inv_plan(dm_ctx* c, const DmGeom& go, std::vector<InvStep>* steps, InvLayout* o) {
+    steps->clear();
+    size_t mbytes = 0;
+    for (int i = 0; i < DM_INV_TRANSFORMS; i++) {
+        InvStep s;
+        dm_invariant_transform(i, go.W1, go.H1, go.W2, go.H2, &s.t);
+        const int r = dm_make_geom(s.t.w1, s.t.h1, s.t.w2, s.t.h2, &s.g);
+        if (r == -1) continue;
+        if (r != 0)
+            return fail(c, DM_EUNSUPPORTED, "invariant form: transform %d (%dx%d / %dx%d) exceeds the 32-bit merge keys", i,
+                        s.t.w1, s.t.h1, s.t.w2, s.t.h2);
+        match_layout(s.g, c->cfg.precision, &s.ml);
+        if (s.ml.bytes > mbytes) mbytes = s.ml.bytes;
+        steps->push_back(s);
+    }
+    size_t off = 0;
+    o->header = off; off = dm_align(off + sizeof(DmWsHeader));
+    o->bestP = off; off = dm_align(off + (size_t)go.npatch(0) * 8);
+    o->bestQ = off; off = dm_align(off + (size_t)((go.W2 + 3) / 4) * ((go.H2 + 3) / 4) * 8);
+    o->match = off; off = dm_align(off + mbytes);
+    o->bytes = off;
+    return DM_OK;
+}
+
 dm_status check_geom(dm_ctx* c, int W1, int H1, int W2, int H2, DmGeom* g) {
     int r = dm_make_geom(W1, H1, W2, H2, g);
     if (r == -1) return fail(c, DM_EINVAL, "invalid sizes %dx%d / %dx%d (need W1,H1 >= 4, max(W1,H1) >= 5, W2,H2 >= 1)", W1, H1, W2, H2);
@@ -876,6 +916,76 @@ dm_status dm_set_tuned_config(dm_ctx* ctx, int W1, int H1, int W2, int H2, const
     if (s != DM_OK) return s;
     std::lock_guard<std::mutex> lk(ctx->tune_mu);
     ctx->tuned[{W1, H1, W2, H2}] = DmTune{chosen[0], chosen[1], chosen[2], chosen[3]};
+    return DM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Scale and rotation invariant form (Sec. 4.2, Algorithm 2)
+// ---------------------------------------------------------------------------
+dm_status dm_invariant_workspace_bytes(dm_ctx* ctx, int W1, int H1, int W2, int H2, size_t* bytes) {
+    if (!ctx) return DM_EINVAL;
+    if (!bytes) return fail(ctx, DM_EINVAL, "dm_invariant_workspace_bytes: bytes is NULL");
+    DmGeom go;
+    dm_status s = check_geom(ctx, W1, H1, W2, H2, &go);
+    if (s != DM_OK) return s;
+    std::vector<InvStep> steps;
+    InvLayout il;
+    if ((s = inv_plan(ctx, go, &steps, &il)) != DM_OK) return s;
+    *bytes = il.bytes;
+    return DM_OK;
+}
+
+dm_status dm_match_invariant(dm_ctx* ctx, const float* d_img1, int W1, int H1, const float* d_img2, int W2, int H2,
+                             void* d_ws, size_t ws_bytes, dm_match_t* d_out, int capacity, int* d_count, void* stream) {
+    if (!ctx) return DM_EINVAL;
+    if (!d_img1 || !d_img2 || !d_ws || !d_out || !d_count || capacity < 0)
+        return fail(ctx, DM_EINVAL, "dm_match_invariant: bad arguments");
+    if (!aligned256(d_ws)) return fail(ctx, DM_EINVAL, "workspace must be 256-byte aligned");
+    DmGeom go;
+    dm_status s = check_geom(ctx, W1, H1, W2, H2, &go);
+    if (s != DM_OK) return s;
+    std::vector<InvStep> steps;
+    InvLayout il;
+    if ((s = inv_plan(ctx, go, &steps, &il)) != DM_OK) return s;
+    if (ws_bytes < il.bytes) return fail(ctx, DM_ENOMEM, "invariant workspace %zu < %zu bytes", ws_bytes, il.bytes);
+    DevGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    char* base = (char*)d_ws;
+    DmWsHeader* hdr = reinterpret_cast<DmWsHeader*>(base + il.header);
+    unsigned long long* bestP = reinterpret_cast<unsigned long long*>(base + il.bestP);
+    unsigned long long* bestQ = reinterpret_cast<unsigned long long*>(base + il.bestQ);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(hdr, 0, sizeof(DmWsHeader), st)) != cudaSuccess) return cuda_fail(ctx, e, "clear header");
+    if ((e = cudaMemsetAsync(bestP, 0, il.bestQ - il.bestP, st)) != cudaSuccess) return cuda_fail(ctx, e, "clear BestAt");
+    if ((e = cudaMemsetAsync(bestQ, 0, il.match - il.bestQ, st)) != cudaSuccess) return cuda_fail(ctx, e, "clear BestAt'");
+    char* mb = base + il.match;
+    for (const InvStep& sp : steps) {
+        const DmInvTransform& t = sp.t;
+        const MatchLayout& ml = sp.ml;
+        float* w1 = (float*)(mb + ml.img1);
+        float* w2 = (float*)(mb + ml.img2);
+        DmRect rect;
+        rect.t1 = dm_make_xform(W1, H1, t.w1, t.h1, t.s1, 0);
+        rect.t2 = dm_make_xform(W2, H2, t.w2, t.h2, t.s2, t.k);
+        rect.W1 = W1; rect.H1 = H1; rect.W2 = W2; rect.H2 = H2;
+        rect.P0x = go.P0x; rect.P0y = go.P0y;
+        rect.bestP = bestP;
+        rect.bestQ = bestQ;
+        if ((e = dm_launch_warp(d_img1, W1, H1, w1, t.w1, t.h1, rect.t1, st)) != cudaSuccess) return cuda_fail(ctx, e, "warp");
+        if ((e = dm_launch_warp(d_img2, W2, H2, w2, t.w2, t.h2, rect.t2, st)) != cudaSuccess) return cuda_fail(ctx, e, "warp");
+        float* desc1 = (float*)(mb + ml.desc1);
+        float* desc2 = (float*)(mb + ml.desc2);
+        if ((s = run_descriptors(ctx, w1, t.w1, t.h1, desc1, mb + ml.tmp, st)) != DM_OK) return s;
+        if ((s = run_descriptors(ctx, w2, t.w2, t.h2, desc2, mb + ml.tmp, st)) != DM_OK) return s;
+        DmWsHeader* th = reinterpret_cast<DmWsHeader*>(mb + ml.bt.header);
+        dm_pyramid py;
+        if ((s = run_pyramid(ctx, sp.g, desc1, desc2, mb + ml.pyr, ml.py, &py, &th->pyr_status, st)) != DM_OK) return s;
+        e = dm_launch_backtrack(sp.g, py, ml.bt, mb, nullptr, 0, nullptr, st, &rect);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "backtracking kernels");
+        if ((e = dm_launch_inv_fold(hdr, th, st)) != cudaSuccess) return cuda_fail(ctx, e, "status fold");
+    }
+    e = dm_launch_reciprocal(go, bestP, bestQ, hdr, d_out, capacity, d_count, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reciprocal verification");
     return DM_OK;
 }
 

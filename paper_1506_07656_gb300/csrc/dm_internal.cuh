@@ -271,6 +271,61 @@ struct dm_pyramid {
     int n0_maps;
 };
 
+// ---------------------------------------------------------------------------
+// Scale and rotation invariant form (Sec. 4.2, Algorithm 2).
+//
+// A warped canvas Wr x Hr holds an image W x H downsized by sigma and rotated
+// by -theta.  Canvas pixel (u, v) samples the image at
+//   (x, y) = image centre + sigma * R_theta * ((u, v) - canvas centre);
+// the same map takes a canvas position back to the image when the atomic
+// correspondences are rectified.  The order of the rounded FP32 operations is
+// part of the definition: the warp and the rectification use this one
+// function.
+struct DmXform {
+    float cu, cv;      // canvas centre ((Wr - 1) / 2, (Hr - 1) / 2)
+    float cx, cy;      // image centre ((W - 1) / 2, (H - 1) / 2)
+    float sg, c, s;    // sigma, cos theta, sin theta
+};
+
+__device__ __forceinline__ void dm_to_source(const DmXform& t, float u, float v, float& x, float& y) {
+    const float du = __fsub_rn(u, t.cu), dv = __fsub_rn(v, t.cv);
+    const float rx = __fsub_rn(__fmul_rn(t.c, du), __fmul_rn(t.s, dv));
+    const float ry = __fadd_rn(__fmul_rn(t.s, du), __fmul_rn(t.c, dv));
+    x = __fadd_rn(t.cx, __fmul_rn(t.sg, rx));
+    y = __fadd_rn(t.cy, __fmul_rn(t.sg, ry));
+}
+
+// Rectification of one transform's atomic correspondences to the input pair:
+// a correspondence (patch c of the warped image 1, canvas pixel t of the warped
+// image 2, score s) becomes (the atomic patch of I holding sigma1 * centre(c),
+// the pixel of I' nearest sigma2 R_theta t) and is reduced into the input
+// pair's BestAt / BestAt' arrays.
+struct DmRect {
+    DmXform t1, t2;               // warped image 1 (theta = 0) and warped image 2
+    int W1, H1, W2, H2;           // input sizes
+    int P0x, P0y;                 // atomic lattice of the input image 1
+    unsigned long long* bestP;    // BestAt of the input pair  [P0x * P0y]
+    unsigned long long* bestQ;    // BestAt' of the input pair [ceil(W2/4) * ceil(H2/4)]
+};
+
+// Transform i (0..71) of Algorithm 2's list: sigma = -2 + 0.5 (i / 8) (outer),
+// theta = (i % 8) pi/4 (inner); sigma1 = max(1, 2^sigma) downsizes image 1,
+// sigma2 = max(1, 2^-sigma) image 2; (w1, h1), (w2, h2) are the canvas sizes.
+struct DmInvTransform {
+    double s1, s2;
+    int k;
+    int w1, h1, w2, h2;
+};
+constexpr int DM_INV_TRANSFORMS = 72;
+void dm_invariant_transform(int i, int W1, int H1, int W2, int H2, DmInvTransform* t);
+DmXform dm_make_xform(int W, int H, int Wr, int Hr, double sigma, int k);
+cudaError_t dm_launch_warp(const float* img, int W, int H, float* out, int Wr, int Hr, const DmXform& t,
+                           cudaStream_t st);
+// dst->status |= src->status, dst->pyr_status |= src->pyr_status and the
+// per-level counts added (saturating): one transform's outcome folded into the
+// invariant call's header.
+cudaError_t dm_launch_inv_fold(DmWsHeader* dst, const DmWsHeader* src, cudaStream_t st);
+
 // Smoothing taps passed by value to kernels.
 struct DmTaps {
     int R;
@@ -337,5 +392,12 @@ size_t dm_corr0_tc_a_bytes(const DmGeom& g, int precision);
 cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& p, float lam, int* status, cudaStream_t st);
 cudaError_t dm_launch_loss_grad(const DmGeom& g, const dm_pyramid& py, const float* d1, const float* d2, float lam,
                                 const DmGradLayout& gl, char* ws, float* d_loss, float* g1, float* g2, cudaStream_t st);
+// With rect != nullptr the atomic correspondences are rectified into
+// rect->bestP / rect->bestQ (which the caller clears once) and no reciprocal
+// step runs: out, capacity and d_count are unused.
 cudaError_t dm_launch_backtrack(const DmGeom& g, const dm_pyramid& p, const DmBtLayout& bl, char* ws,
-                                dm_match_t* out, int capacity, int* d_count, cudaStream_t st);
+                                dm_match_t* out, int capacity, int* d_count, cudaStream_t st,
+                                const DmRect* rect = nullptr);
+// Reciprocal verification (Eq. 16) of BestAt / BestAt' arrays of geometry g.
+cudaError_t dm_launch_reciprocal(const DmGeom& g, unsigned long long* bestP, unsigned long long* bestQ, DmWsHeader* hdr,
+                                 dm_match_t* out, int capacity, int* d_count, cudaStream_t st);

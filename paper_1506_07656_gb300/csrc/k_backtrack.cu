@@ -53,6 +53,7 @@ struct BtArgs {
     DmWsHeader* hdr;
     const int* proto_of;          // approximate form: level-0 map of atomic patch c is proto_of[c]; else null
     int n0_maps;                  // level-0 maps (entries of proto_of are clamped to [0, n0_maps))
+    DmRect rect;                  // invariant form: rectification of the atomic tuples (RECT kernels only)
 };
 
 __device__ __forceinline__ unsigned int warp_agg_inc(unsigned int* ctr) {
@@ -116,9 +117,40 @@ __device__ __forceinline__ void leaf_update(const BtArgs& a, int c, int tx, int 
     if (__ldcg(a.bestQ + cell) < kq) atomicMax(a.bestQ + cell, kq);
 }
 
+// Nearest pixel index floor(x + 1/2), clamped to [0, n).
+__device__ __forceinline__ int round_px(float x, int n) {
+    const float f = floorf(__fadd_rn(x, 0.5f));
+    if (!(f > 0.0f)) return 0;
+    return f >= (float)(n - 1) ? n - 1 : (int)f;
+}
+
+// Invariant form (Algorithm 2): the atomic tuple (c, t, s) of one transform
+// rectified to the input pair -- the centre of warped patch c taken back to
+// image 1 and rounded to a pixel, whose atomic patch (4x4 cell) becomes the
+// tuple's patch; canvas pixel t taken back to image 2 and rounded -- and
+// reduced into the input pair's BestAt / BestAt' with the same keys as above.
+__device__ __forceinline__ void leaf_update_rect(const BtArgs& a, int c, int tx, int ty, unsigned int s) {
+    const DmRect& r = a.rect;
+    const int gx = a.g.P0x;
+    float x1, y1, x2, y2;
+    dm_to_source(r.t1, (float)(4 * (c % gx) + 2), (float)(4 * (c / gx) + 2), x1, y1);
+    dm_to_source(r.t2, (float)tx, (float)ty, x2, y2);
+    const int X1 = round_px(x1, r.W1), Y1 = round_px(y1, r.H1);
+    const int X2 = round_px(x2, r.W2), Y2 = round_px(y2, r.H2);
+    const int C1 = min(Y1 >> 2, r.P0y - 1) * r.P0x + min(X1 >> 2, r.P0x - 1);
+    const unsigned long long sb = (unsigned long long)s << 32;
+    const unsigned long long kp = sb | (0xffffffffu - (unsigned int)(Y2 * r.W2 + X2));
+    if (__ldcg(r.bestP + C1) < kp) atomicMax(r.bestP + C1, kp);
+    const int cell = (Y2 >> 2) * ((r.W2 + 3) >> 2) + (X2 >> 2);
+    const unsigned int qidx = (unsigned int)C1 * 16u + (unsigned int)((Y2 & 3) * 4 + (X2 & 3));
+    const unsigned long long kq = sb | (0xffffffffu - qidx);
+    if (__ldcg(r.bestQ + cell) < kq) atomicMax(r.bestQ + cell, kq);
+}
+
 // Children of tuple (l, p, q, s); returns the number of atomic arrivals.
 // The (up to 4) children's pooled values and argmax codes are loaded first,
 // all independent, so their memory latencies overlap; the merges follow.
+template <bool RECT>
 __device__ __forceinline__ int expand(const BtArgs& a, int l, unsigned int cap_next, int p, int qx, int qy, unsigned int s) {
     const DmGeom& g = a.g;
     const int mw = g.dw[l], mh = g.dh[l], pitch = g.pitch(l);    // pooled map P_{l-1} lives on domain l
@@ -153,7 +185,8 @@ __device__ __forceinline__ int expand(const BtArgs& a, int l, unsigned int cap_n
             unsigned int key = (unsigned int)cc[i] * (unsigned int)g.dsize(l - 1) + (unsigned int)(ty * g.dw[l - 1] + tx);
             ht_insert(a, l - 1, cap_next, key, s2);
         } else {
-            leaf_update(a, cc[i], tx, ty, s2);
+            if constexpr (RECT) leaf_update_rect(a, cc[i], tx, ty, s2);
+            else leaf_update(a, cc[i], tx, ty, s2);
             arrivals++;
         }
     }
@@ -182,6 +215,7 @@ __global__ void k_bt_prepare(BtArgs a, int lvl, long long n_top) {
 }
 
 // Expansion of the top level: every position of every existing top patch.
+template <bool RECT>
 __global__ void k_bt_expand_top(BtArgs a) {
     const DmGeom& g = a.g;
     const int L = g.L;
@@ -196,7 +230,7 @@ __global__ void k_bt_expand_top(BtArgs a) {
             int q = (int)(e % ds);
             if (a.valid[L][p]) {
                 if (q == 0) atomicAdd(&a.hdr->count[L], (unsigned int)ds);
-                arrivals += expand(a, L, cap_next, p, q % g.dw[L], q / g.dw[L], ps_term(a.top[e]));
+                arrivals += expand<RECT>(a, L, cap_next, p, q % g.dw[L], q / g.dw[L], ps_term(a.top[e]));
             }
         }
     }
@@ -208,6 +242,7 @@ __global__ void k_bt_expand_top(BtArgs a) {
 // it reads into a queue in shared memory and expands them 32 at a time, so its
 // lanes stay busy while the slot order (neighbouring positions of one patch
 // together) is kept.
+template <bool RECT>
 __global__ void k_bt_expand(BtArgs a, int l) {
     __shared__ unsigned long long queue[BT_BLOCK / 32][64];
     const DmGeom& g = a.g;
@@ -222,7 +257,7 @@ __global__ void k_bt_expand(BtArgs a, int l) {
         const unsigned int key = (unsigned int)(v >> 32) - 1u;
         const unsigned int sc = (unsigned int)v;
         const int p = (int)(key / ds), t = (int)(key % ds);
-        arrivals += expand(a, l, cap_next, p, t % g.dw[l], t / g.dw[l], sc);
+        arrivals += expand<RECT>(a, l, cap_next, p, t % g.dw[l], t / g.dw[l], sc);
     };
     for (unsigned int i0 = blockIdx.x * blockDim.x; i0 < cap; i0 += gridDim.x * blockDim.x) {
         const unsigned int i = i0 + threadIdx.x;
@@ -322,10 +357,25 @@ __global__ void __launch_bounds__(1024) k_reciprocal(BtArgs a, dm_match_t* __res
     }
 }
 
+template <bool RECT>
+void launch_steps(const BtArgs& a, int grid, cudaStream_t st) {
+    const DmGeom& g = a.g;
+    const long long n_top = (long long)g.npatch(g.L) * g.dsize(g.L);
+    for (int l = g.L; l >= 1; l--) {
+        if (l - 1 >= 1) k_bt_prepare<<<grid, BT_BLOCK, 0, st>>>(a, l - 1, n_top);
+        if (l == g.L) {
+            long long nb = (n_top + BT_BLOCK - 1) / BT_BLOCK;
+            k_bt_expand_top<RECT><<<(unsigned)(nb < grid ? nb : grid), BT_BLOCK, 0, st>>>(a);
+        } else {
+            k_bt_expand<RECT><<<grid, BT_BLOCK, 0, st>>>(a, l);
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t dm_launch_backtrack(const DmGeom& g, const dm_pyramid& py, const DmBtLayout& bl, char* ws,
-                                dm_match_t* out, int capacity, int* d_count, cudaStream_t st) {
+                                dm_match_t* out, int capacity, int* d_count, cudaStream_t st, const DmRect* rect) {
     BtArgs a;
     memset(&a, 0, sizeof(a));
     a.g = g;
@@ -344,31 +394,43 @@ cudaError_t dm_launch_backtrack(const DmGeom& g, const dm_pyramid& py, const DmB
     a.bestP = reinterpret_cast<unsigned long long*>(ws + bl.bestP);
     a.bestQ = reinterpret_cast<unsigned long long*>(ws + bl.bestQ);
     a.hdr = reinterpret_cast<DmWsHeader*>(ws + bl.header);
+    if (rect) a.rect = *rect;
 
     cudaError_t e;
     // clear the backtracking part of the header (status word, counts, table sizes);
     // pyr_status belongs to the pyramid step that ran before
     if ((e = cudaMemsetAsync(&a.hdr->status, 0, sizeof(int), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(a.hdr->count, 0, sizeof(a.hdr->count) + sizeof(a.hdr->cap), st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(a.bestP, 0, sizeof(unsigned long long) * g.npatch(0), st)) != cudaSuccess) return e;
-    size_t ncell = (size_t)((g.W2 + 3) / 4) * ((g.H2 + 3) / 4);
-    if ((e = cudaMemsetAsync(a.bestQ, 0, sizeof(unsigned long long) * ncell, st)) != cudaSuccess) return e;
+    if (!rect) {
+        if ((e = cudaMemsetAsync(a.bestP, 0, sizeof(unsigned long long) * g.npatch(0), st)) != cudaSuccess) return e;
+        size_t ncell = (size_t)((g.W2 + 3) / 4) * ((g.H2 + 3) / 4);
+        if ((e = cudaMemsetAsync(a.bestQ, 0, sizeof(unsigned long long) * ncell, st)) != cudaSuccess) return e;
+    }
 
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int grid = nsm * (py.tune.bt_mult > 0 ? py.tune.bt_mult : 8);
-    const long long n_top = (long long)g.npatch(g.L) * g.dsize(g.L);
-    for (int l = g.L; l >= 1; l--) {
-        if (l - 1 >= 1) k_bt_prepare<<<grid, BT_BLOCK, 0, st>>>(a, l - 1, n_top);
-        if (l == g.L) {
-            long long nb = (n_top + BT_BLOCK - 1) / BT_BLOCK;
-            k_bt_expand_top<<<(unsigned)(nb < grid ? nb : grid), BT_BLOCK, 0, st>>>(a);
-        } else {
-            k_bt_expand<<<grid, BT_BLOCK, 0, st>>>(a, l);
-        }
+    if (rect) {
+        launch_steps<true>(a, grid, st);
+        dm_count_launches(2 * g.L - 1);
+        return cudaGetLastError();
     }
+    launch_steps<false>(a, grid, st);
     k_reciprocal<<<1, 1024, 0, st>>>(a, out, capacity, d_count);
     dm_count_launches(2 * g.L);
+    return cudaGetLastError();
+}
+
+cudaError_t dm_launch_reciprocal(const DmGeom& g, unsigned long long* bestP, unsigned long long* bestQ, DmWsHeader* hdr,
+                                 dm_match_t* out, int capacity, int* d_count, cudaStream_t st) {
+    BtArgs a;
+    memset(&a, 0, sizeof(a));
+    a.g = g;
+    a.bestP = bestP;
+    a.bestQ = bestQ;
+    a.hdr = hdr;
+    k_reciprocal<<<1, 1024, 0, st>>>(a, out, capacity, d_count);
+    dm_count_launches(1);
     return cudaGetLastError();
 }

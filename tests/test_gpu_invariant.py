@@ -1,0 +1,157 @@
+"""Scale and rotation invariant form (Sec. 4.2, Algorithm 2) on the GPU,
+through the C ABI (dm_match_invariant).
+
+* FP32: the matches equal, bit for bit, the oracle's FP32 invariant chain (the
+  same warp, rectification, keys and final reciprocal verification; the GPU
+  runs the 72 transforms through its kernels and reduces the rectified
+  correspondences on the device) -- on a pair with a smooth displacement, a
+  quarter-turned pair, a pair at half scale and ragged sizes where the
+  smallest scales are skipped.
+* BF16: the matches agree with the oracle's FP32 invariant matches on most
+  patches, and the quarter turn is still recovered.
+* The status header of the invariant workspace reports the runs; argument and
+  workspace checks fail with the documented codes; a size whose 45-degree
+  canvas exceeds the 32-bit merge keys is refused (DM_EUNSUPPORTED).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1506_07656_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1506_07656_gb300 import build
+    build.build()
+    return torch
+
+
+def _ctx(prec):
+    from paper_1506_07656_gb300 import dm
+    return dm.Context({"fp32": dm.DM_FP32, "bf16": dm.DM_BF16}[prec])
+
+
+def _block_mean(img):
+    H, W = img.shape
+    return img[:H // 2 * 2, :W // 2 * 2].reshape(H // 2, 2, W // 2, 2).mean(axis=(1, 3))
+
+
+def _case(name):
+    if name == "smooth_40x32":
+        pr = synth.make_pair_smooth(40, 32, seed=5, max_disp=3.0)
+        return pr.img1, pr.img2
+    if name == "quarter_turn_48x40":
+        img1 = synth.make_pair_smooth(48, 40, seed=9, max_disp=1.0).img1
+        return img1, np.ascontiguousarray(np.rot90(img1, 1))
+    if name == "half_scale_64x48":
+        img1 = synth.make_pair_smooth(64, 48, seed=13, max_disp=1.0).img1
+        return img1, _block_mean(img1)
+    if name == "ragged_37x29_33x41":
+        a = synth.make_pair_smooth(37, 29, seed=17, max_disp=2.0).img1
+        b = synth.make_pair_smooth(33, 41, seed=19, max_disp=2.0).img2
+        return a, b
+    raise KeyError(name)
+
+
+def _run(torch, ctx, img1, img2):
+    from paper_1506_07656_gb300 import dm
+    t = ctx.match_invariant(np.ascontiguousarray(img1, dtype=np.float32), np.ascontiguousarray(img2, dtype=np.float32))
+    torch.cuda.synchronize()
+    return t.cpu().numpy().astype(np.float64)
+
+
+def _quarter_turn_consistent(m, W1, tol=3.0):
+    if len(m) == 0:
+        return 0.0
+    return float(np.mean((np.abs(m[:, 2] - m[:, 1]) <= tol) & (np.abs(m[:, 3] - (W1 - 1 - m[:, 0])) <= tol)))
+
+
+@pytest.mark.parametrize("case", ["smooth_40x32", "quarter_turn_48x40", "half_scale_64x48", "ragged_37x29_33x41"])
+def test_fp32_matches_equal_oracle(torch_cuda, case):
+    img1, img2 = _case(case)
+    want = oracle.invariant_match(img1.astype(np.float32), img2.astype(np.float32), "f32")
+    ctx = _ctx("fp32")
+    got = _run(torch_cuda, ctx, img1, img2)
+    assert len(want) > 0
+    np.testing.assert_array_equal(got[:, :4], want[:, :4])
+    np.testing.assert_array_equal(got[:, 4], want[:, 4])
+
+
+def test_fp32_repeatable_and_status(torch_cuda):
+    from paper_1506_07656_gb300 import dm
+    img1, img2 = _case("quarter_turn_48x40")
+    ctx = _ctx("fp32")
+    a = _run(torch_cuda, ctx, img1, img2)
+    b = _run(torch_cuda, ctx, img1, img2)
+    np.testing.assert_array_equal(a, b)
+    ws = ctx._ws[("invariant", 48, 40, 40, 48)]
+    status, reached = dm.dm_read_status(ctx.ctx, ws, 3)
+    assert status == 0
+    assert reached[0] > 0          # atomic arrivals summed over the transforms
+
+
+def test_bf16_agrees_with_fp32_oracle(torch_cuda):
+    img1, img2 = _case("quarter_turn_48x40")
+    want = oracle.invariant_match(img1.astype(np.float32), img2.astype(np.float32), "f32")
+    got = _run(torch_cuda, _ctx("bf16"), img1, img2)
+    key = {(r[0], r[1]): (r[2], r[3]) for r in want}
+    agree = np.mean([key.get((r[0], r[1])) == (r[2], r[3]) for r in got]) if len(got) else 0.0
+    assert agree >= 0.8, agree
+    assert abs(len(got) - len(want)) <= 0.2 * len(want)
+    assert _quarter_turn_consistent(got, 48) >= 0.7
+
+
+def test_argument_and_workspace_checks(torch_cuda):
+    from paper_1506_07656_gb300 import dm
+    torch = torch_cuda
+    ctx = _ctx("fp32")
+    img1, img2 = _case("smooth_40x32")
+    i1 = torch.as_tensor(img1, dtype=torch.float32, device="cuda")
+    i2 = torch.as_tensor(img2, dtype=torch.float32, device="cuda")
+    need = dm.dm_invariant_workspace_bytes(ctx.ctx, 40, 32, 40, 32)
+    single = dm.dm_workspace_bytes(ctx.ctx, 40, 32, 40, 32)["match"]
+    assert need > single            # the 45-degree canvases are larger than the input pair
+    out = torch.empty((100, 5), dtype=torch.float32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    small = torch.empty(need - 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(dm.DmError) as e:
+        dm.dm_match_invariant(ctx.ctx, i1, i2, small, out, cnt)
+    assert e.value.status == dm.DM_ENOMEM
+    ws = torch.empty(need + 512, dtype=torch.uint8, device="cuda")
+    with pytest.raises(dm.DmError) as e:
+        dm.dm_match_invariant(ctx.ctx, i1, i2, ws[16:], out, cnt)
+    assert e.value.status == dm.DM_EINVAL
+    tiny = torch.zeros((3, 40), dtype=torch.float32, device="cuda")
+    with pytest.raises(dm.DmError) as e:
+        dm.dm_match_invariant(ctx.ctx, tiny, i2, ws, out, cnt)
+    assert e.value.status == dm.DM_EINVAL
+    # 1024 x 436: the 45-degree canvas of image 2 (1032 x 1032) overflows the merge keys
+    with pytest.raises(dm.DmError) as e:
+        dm.dm_invariant_workspace_bytes(ctx.ctx, 1024, 436, 1024, 436)
+    assert e.value.status == dm.DM_EUNSUPPORTED
+
+
+def test_output_capacity_overflow_is_reported(torch_cuda):
+    from paper_1506_07656_gb300 import dm
+    torch = torch_cuda
+    ctx = _ctx("fp32")
+    img1, img2 = _case("smooth_40x32")
+    want = oracle.invariant_match(img1.astype(np.float32), img2.astype(np.float32), "f32")
+    i1 = torch.as_tensor(img1, dtype=torch.float32, device="cuda")
+    i2 = torch.as_tensor(img2, dtype=torch.float32, device="cuda")
+    ws = torch.empty(dm.dm_invariant_workspace_bytes(ctx.ctx, 40, 32, 40, 32), dtype=torch.uint8, device="cuda")
+    cap = len(want) // 2
+    out = torch.zeros((cap, 5), dtype=torch.float32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    dm.dm_match_invariant(ctx.ctx, i1, i2, ws, out, cnt)
+    torch.cuda.synchronize()
+    assert int(cnt.item()) == len(want)
+    status, _ = dm.dm_read_status(ctx.ctx, ws, 1)
+    assert status & dm.DM_DEV_OUTPUT_OVERFLOW
+    np.testing.assert_array_equal(out.cpu().numpy().astype(np.float64), want[:cap].astype(np.float32).astype(np.float64))
