@@ -355,6 +355,7 @@ def _measure_invariant(dm, torch, a, stream, W=512, H=224, prec="bf16"):
         i1 = torch.from_numpy(img1).cuda()
         i2 = torch.from_numpy(img2).cuda()
         H2, W2 = img2.shape
+        dm.dm_set_batch_lanes(ctx.ctx, 4)
         ws = torch.empty(dm.dm_invariant_workspace_bytes(ctx.ctx, W, H, W2, H2), dtype=torch.uint8, device="cuda")
         P0 = dm.dm_geometry(W, H, W2, H2)["n_patch0"]
         out = torch.empty((P0, 5), dtype=torch.float32, device="cuda")
@@ -362,17 +363,22 @@ def _measure_invariant(dm, torch, a, stream, W=512, H=224, prec="bf16"):
         launches0 = dm.dm_timing_read(ctx.ctx)[2]
         dm.dm_match_invariant(ctx.ctx, i1, i2, ws, out, cnt, stream)
         launches = dm.dm_timing_read(ctx.ctx)[2] - launches0
-        for _ in range(max(a.warmup - 1, 1)):
-            dm.dm_match_invariant(ctx.ctx, i1, i2, ws, out, cnt, stream)
-        torch.cuda.synchronize()
         steps = max(min(a.steps, 5), 1)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            dm.dm_match_invariant(ctx.ctx, i1, i2, ws, out, cnt, stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / steps
+        by_lanes = {}
+        for lanes in (1, 2, 4):                 # the transforms on 1, 2 or 4 concurrent lanes
+            dm.dm_set_batch_lanes(ctx.ctx, lanes)
+            for _ in range(max(a.warmup - 1, 1)):
+                dm.dm_match_invariant(ctx.ctx, i1, i2, ws, out, cnt, stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                dm.dm_match_invariant(ctx.ctx, i1, i2, ws, out, cnt, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            by_lanes[lanes] = e0.elapsed_time(e1) / steps
+        best = min(by_lanes, key=by_lanes.get)
+        ms = by_lanes[best]
         status, _ = dm.dm_read_status(ctx.ctx, ws, 1)
         inv = out[:int(cnt.item())].cpu().numpy().astype(np.float64)
         mws = ctx.workspace("match", W, H, W2, H2)
@@ -388,7 +394,8 @@ def _measure_invariant(dm, torch, a, stream, W=512, H=224, prec="bf16"):
         return float(np.mean((np.abs(m[:, 2] - m[:, 1]) <= 3) & (np.abs(m[:, 3] - (W - 1 - m[:, 0])) <= 3)))
 
     return {"workload": f"{W}x{H} against its quarter turn", "transforms": 72, "precision": prec,
-            "pairs_per_s": 1000.0 / ms, "ms_per_step": ms, "kernel_launches_per_step": int(launches),
+            "pairs_per_s": 1000.0 / ms, "ms_per_step": ms, "lanes": best,
+            "ms_per_step_by_lanes": {str(k): v for k, v in by_lanes.items()}, "kernel_launches_per_step": int(launches),
             "status": int(status), "matches": int(len(inv)), "consistent_with_turn": turn(inv),
             "exact_form_matches": int(len(exact)), "exact_form_consistent_with_turn": turn(exact)}
 

@@ -230,11 +230,16 @@ dm_status dm_match_host(dm_ctx* ctx, const float* h_img1, int W1, int H1, const 
  * number found.  Transforms that leave an image below 4 pixels, or with no
  * aggregation level, are skipped; DM_EUNSUPPORTED if a transform's warped
  * pair exceeds the 32-bit merge keys (the 45-degree canvases are the
- * largest).  The precision and parameters are the context's.  Runs entirely
- * on `stream` with no host synchronisation.  Status words of all runs are
- * OR-ed into the header at offset 0 of d_ws (dm_read_status; reached[] sums
- * the runs).  d_ws >= *bytes of dm_invariant_workspace_bytes, 256-byte
- * aligned; it is reused by each run in turn. */
+ * largest).  The precision and parameters are the context's.  The runs are
+ * independent (their reductions are order-independent), so they are spread
+ * over the context's concurrent lanes (dm_set_batch_lanes; longest run first,
+ * each to the least loaded lane) that fork from and join back into `stream`;
+ * the result does not depend on the number of lanes.  No host
+ * synchronisation.  Status words of all runs are OR-ed into the header at
+ * offset 0 of d_ws (dm_read_status; reached[] sums the runs).  d_ws is
+ * 256-byte aligned and >= *bytes of dm_invariant_workspace_bytes (the size for
+ * the context's lanes); a smaller workspace holding at least one lane's
+ * region runs on fewer lanes, each lane's region reused by its runs in turn. */
 dm_status dm_invariant_workspace_bytes(dm_ctx* ctx, int W1, int H1, int W2, int H2, size_t* bytes);
 dm_status dm_match_invariant(dm_ctx* ctx, const float* d_img1, int W1, int H1, const float* d_img2, int W2, int H2,
                              void* d_ws, size_t ws_bytes, dm_match_t* d_out, int capacity, int* d_count,
@@ -295,8 +300,8 @@ typedef struct {
  * (dm_read_status on d_ws + j * lane_bytes reads the last pair of lane j). */
 dm_status dm_batch_workspace_bytes(const dm_ctx* ctx, int n, const dm_pair* pairs, size_t* bytes);
 dm_status dm_match_batch(dm_ctx* ctx, int n, const dm_pair* pairs, void* d_ws, size_t ws_bytes, void* stream);
-/* Number of concurrent lanes of dm_match_batch, 1..4 (1: one pair after the
- * other on `stream`). */
+/* Number of concurrent lanes of dm_match_batch and dm_match_invariant, 1..4
+ * (1: one pair, or one transform, after the other on `stream`). */
 dm_status dm_set_batch_lanes(dm_ctx* ctx, int lanes);
 
 /* Autotuner of the batched form.  Runs the launch-shape candidates of three

@@ -6,6 +6,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <array>
 #include <atomic>
 #include <map>
@@ -178,17 +179,19 @@ dm_status run_pyramid(dm_ctx* c, const DmGeom& g, const float* d1, const float* 
 // Invariant form (Algorithm 2): the transforms whose warped pair the method
 // accepts -- a transform that leaves an image too small for one aggregation
 // level is skipped -- and the workspace: the call's header, the input pair's
-// BestAt / BestAt' arrays, then one dm_match workspace sized for the largest
-// transform, reused by each transform in turn (warped images in its image
-// slots).
+// BestAt / BestAt' arrays, then one dm_match workspace ("region") per lane,
+// sized for the largest transform and reused by the transforms of its lane in
+// turn (warped images in its image slots).
 struct InvLayout {
-    size_t header, bestP, bestQ, match, bytes;
+    size_t header, bestP, bestQ, match, region;
+    size_t bytes(int lanes) const { return match + region * (size_t)lanes; }
 };
 
 struct InvStep {
     DmInvTransform t;
     DmGeom g;
     MatchLayout ml;
+    double cost;          // level-0 products (patches x positions) + a fixed share per transform
 };
 
 dm_status inv_plan(dm_ctx* c, const DmGeom& go, std::vector<InvStep>* steps, InvLayout* o) {
@@ -204,15 +207,35 @@ dm_status inv_plan(dm_ctx* c, const DmGeom& go, std::vector<InvStep>* steps, Inv
                         s.t.w1, s.t.h1, s.t.w2, s.t.h2);
         match_layout(s.g, c->cfg.precision, &s.ml);
         if (s.ml.bytes > mbytes) mbytes = s.ml.bytes;
+        s.cost = (double)s.g.npatch(0) * (double)s.t.w2 * (double)s.t.h2 + 2.0e7;
         steps->push_back(s);
     }
     size_t off = 0;
     o->header = off; off = dm_align(off + sizeof(DmWsHeader));
     o->bestP = off; off = dm_align(off + (size_t)go.npatch(0) * 8);
     o->bestQ = off; off = dm_align(off + (size_t)((go.W2 + 3) / 4) * ((go.H2 + 3) / 4) * 8);
-    o->match = off; off = dm_align(off + mbytes);
-    o->bytes = off;
+    o->match = off;
+    o->region = dm_align(mbytes);
     return DM_OK;
+}
+
+// Lane of each transform: longest first, each to the least loaded lane.  The
+// results do not depend on it (the reductions into BestAt / BestAt' and the
+// header are order-independent).
+std::vector<int> inv_schedule(const std::vector<InvStep>& steps, int lanes, std::vector<int>* order) {
+    order->resize(steps.size());
+    for (size_t i = 0; i < steps.size(); i++) (*order)[i] = (int)i;
+    std::sort(order->begin(), order->end(), [&](int a, int b) { return steps[a].cost > steps[b].cost; });
+    std::vector<int> lane(steps.size(), 0);
+    std::vector<double> load((size_t)lanes, 0.0);
+    for (int i : *order) {
+        int j = 0;
+        for (int k = 1; k < lanes; k++)
+            if (load[k] < load[j]) j = k;
+        lane[i] = j;
+        load[j] += steps[i].cost;
+    }
+    return lane;
 }
 
 dm_status check_geom(dm_ctx* c, int W1, int H1, int W2, int H2, DmGeom* g) {
@@ -931,7 +954,8 @@ dm_status dm_invariant_workspace_bytes(dm_ctx* ctx, int W1, int H1, int W2, int 
     std::vector<InvStep> steps;
     InvLayout il;
     if ((s = inv_plan(ctx, go, &steps, &il)) != DM_OK) return s;
-    *bytes = il.bytes;
+    const int lanes = (int)steps.size() < ctx->lanes ? (int)steps.size() : ctx->lanes;
+    *bytes = il.bytes(lanes > 0 ? lanes : 1);
     return DM_OK;
 }
 
@@ -947,7 +971,10 @@ dm_status dm_match_invariant(dm_ctx* ctx, const float* d_img1, int W1, int H1, c
     std::vector<InvStep> steps;
     InvLayout il;
     if ((s = inv_plan(ctx, go, &steps, &il)) != DM_OK) return s;
-    if (ws_bytes < il.bytes) return fail(ctx, DM_ENOMEM, "invariant workspace %zu < %zu bytes", ws_bytes, il.bytes);
+    if (ws_bytes < il.bytes(1)) return fail(ctx, DM_ENOMEM, "invariant workspace %zu < %zu bytes", ws_bytes, il.bytes(1));
+    // lanes: the context's count, as many as the workspace holds, at most one per transform
+    int lanes = ctx->lanes < (int)steps.size() ? ctx->lanes : (int)steps.size();
+    while (lanes > 1 && ws_bytes < il.bytes(lanes)) lanes--;
     DevGuard dg(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     char* base = (char*)d_ws;
@@ -958,10 +985,21 @@ dm_status dm_match_invariant(dm_ctx* ctx, const float* d_img1, int W1, int H1, c
     if ((e = cudaMemsetAsync(hdr, 0, sizeof(DmWsHeader), st)) != cudaSuccess) return cuda_fail(ctx, e, "clear header");
     if ((e = cudaMemsetAsync(bestP, 0, il.bestQ - il.bestP, st)) != cudaSuccess) return cuda_fail(ctx, e, "clear BestAt");
     if ((e = cudaMemsetAsync(bestQ, 0, il.match - il.bestQ, st)) != cudaSuccess) return cuda_fail(ctx, e, "clear BestAt'");
-    char* mb = base + il.match;
-    for (const InvStep& sp : steps) {
+    std::vector<int> order;
+    const std::vector<int> lane_of = inv_schedule(steps, lanes, &order);
+    // fork: with several lanes every lane stream waits for the work already on `stream`
+    if (lanes > 1) {
+        e = cudaEventRecord(ctx->fork_ev, st);
+        for (int j = 0; e == cudaSuccess && j < lanes; j++) e = cudaStreamWaitEvent(ctx->lane_st[j], ctx->fork_ev, 0);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "dm_match_invariant: fork");
+    }
+    for (int i : order) {
+        const InvStep& sp = steps[i];
         const DmInvTransform& t = sp.t;
         const MatchLayout& ml = sp.ml;
+        const int j = lane_of[i];
+        cudaStream_t ls = lanes > 1 ? ctx->lane_st[j] : st;
+        char* mb = base + il.match + il.region * (size_t)j;
         float* w1 = (float*)(mb + ml.img1);
         float* w2 = (float*)(mb + ml.img2);
         DmRect rect;
@@ -971,18 +1009,25 @@ dm_status dm_match_invariant(dm_ctx* ctx, const float* d_img1, int W1, int H1, c
         rect.P0x = go.P0x; rect.P0y = go.P0y;
         rect.bestP = bestP;
         rect.bestQ = bestQ;
-        if ((e = dm_launch_warp(d_img1, W1, H1, w1, t.w1, t.h1, rect.t1, st)) != cudaSuccess) return cuda_fail(ctx, e, "warp");
-        if ((e = dm_launch_warp(d_img2, W2, H2, w2, t.w2, t.h2, rect.t2, st)) != cudaSuccess) return cuda_fail(ctx, e, "warp");
+        if ((e = dm_launch_warp(d_img1, W1, H1, w1, t.w1, t.h1, rect.t1, ls)) != cudaSuccess) return cuda_fail(ctx, e, "warp");
+        if ((e = dm_launch_warp(d_img2, W2, H2, w2, t.w2, t.h2, rect.t2, ls)) != cudaSuccess) return cuda_fail(ctx, e, "warp");
         float* desc1 = (float*)(mb + ml.desc1);
         float* desc2 = (float*)(mb + ml.desc2);
-        if ((s = run_descriptors(ctx, w1, t.w1, t.h1, desc1, mb + ml.tmp, st)) != DM_OK) return s;
-        if ((s = run_descriptors(ctx, w2, t.w2, t.h2, desc2, mb + ml.tmp, st)) != DM_OK) return s;
+        if ((s = run_descriptors(ctx, w1, t.w1, t.h1, desc1, mb + ml.tmp, ls)) != DM_OK) return s;
+        if ((s = run_descriptors(ctx, w2, t.w2, t.h2, desc2, mb + ml.tmp, ls)) != DM_OK) return s;
         DmWsHeader* th = reinterpret_cast<DmWsHeader*>(mb + ml.bt.header);
         dm_pyramid py;
-        if ((s = run_pyramid(ctx, sp.g, desc1, desc2, mb + ml.pyr, ml.py, &py, &th->pyr_status, st)) != DM_OK) return s;
-        e = dm_launch_backtrack(sp.g, py, ml.bt, mb, nullptr, 0, nullptr, st, &rect);
+        if ((s = run_pyramid(ctx, sp.g, desc1, desc2, mb + ml.pyr, ml.py, &py, &th->pyr_status, ls)) != DM_OK) return s;
+        e = dm_launch_backtrack(sp.g, py, ml.bt, mb, nullptr, 0, nullptr, ls, &rect);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "backtracking kernels");
-        if ((e = dm_launch_inv_fold(hdr, th, st)) != cudaSuccess) return cuda_fail(ctx, e, "status fold");
+        if ((e = dm_launch_inv_fold(hdr, th, ls)) != cudaSuccess) return cuda_fail(ctx, e, "status fold");
+    }
+    if (lanes > 1) {
+        for (int j = 0; e == cudaSuccess && j < lanes; j++) {
+            e = cudaEventRecord(ctx->join_ev[j], ctx->lane_st[j]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->join_ev[j], 0);
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "dm_match_invariant: join");
     }
     e = dm_launch_reciprocal(go, bestP, bestQ, hdr, d_out, capacity, d_count, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "reciprocal verification");

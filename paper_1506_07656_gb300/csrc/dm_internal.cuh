@@ -322,8 +322,8 @@ DmXform dm_make_xform(int W, int H, int Wr, int Hr, double sigma, int k);
 cudaError_t dm_launch_warp(const float* img, int W, int H, float* out, int Wr, int Hr, const DmXform& t,
                            cudaStream_t st);
 // dst->status |= src->status, dst->pyr_status |= src->pyr_status and the
-// per-level counts added (saturating): one transform's outcome folded into the
-// invariant call's header.
+// per-level counts added (saturating), all atomically: one transform's outcome
+// folded into the invariant call's header (transforms may run concurrently).
 cudaError_t dm_launch_inv_fold(DmWsHeader* dst, const DmWsHeader* src, cudaStream_t st);
 
 // Smoothing taps passed by value to kernels.

@@ -57,15 +57,18 @@ __global__ void k_warp(const float* __restrict__ img, int W, int H, float* __res
     }
 }
 
+// Transforms may run on concurrent streams: every update of the call's header
+// is atomic.  A count that wraps is set to the maximum (saturation).
 __global__ void k_inv_fold(DmWsHeader* __restrict__ dst, const DmWsHeader* __restrict__ src) {
     const int i = threadIdx.x;
     if (i == 0) {
-        dst->status |= src->status;
-        dst->pyr_status |= src->pyr_status;
+        if (src->status) atomicOr(&dst->status, src->status);
+        if (src->pyr_status) atomicOr(&dst->pyr_status, src->pyr_status);
     }
     if (i < DM_MAXL + 2) {
-        const unsigned long long v = (unsigned long long)dst->count[i] + src->count[i];
-        dst->count[i] = v > 0xffffffffull ? 0xffffffffu : (unsigned int)v;
+        const unsigned int v = src->count[i];
+        const unsigned int old = atomicAdd(&dst->count[i], v);
+        if (old + v < old) atomicExch(&dst->count[i], 0xffffffffu);
     }
 }
 

@@ -114,6 +114,7 @@ def test_argument_and_workspace_checks(torch_cuda):
     img1, img2 = _case("smooth_40x32")
     i1 = torch.as_tensor(img1, dtype=torch.float32, device="cuda")
     i2 = torch.as_tensor(img2, dtype=torch.float32, device="cuda")
+    dm.dm_set_batch_lanes(ctx.ctx, 1)            # one lane: below this size nothing can run
     need = dm.dm_invariant_workspace_bytes(ctx.ctx, 40, 32, 40, 32)
     single = dm.dm_workspace_bytes(ctx.ctx, 40, 32, 40, 32)["match"]
     assert need > single            # the 45-degree canvases are larger than the input pair
@@ -155,3 +156,40 @@ def test_output_capacity_overflow_is_reported(torch_cuda):
     status, _ = dm.dm_read_status(ctx.ctx, ws, 1)
     assert status & dm.DM_DEV_OUTPUT_OVERFLOW
     np.testing.assert_array_equal(out.cpu().numpy().astype(np.float64), want[:cap].astype(np.float32).astype(np.float64))
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4])
+def test_lanes_give_the_oracle_matches(torch_cuda, lanes):
+    """The transforms spread over 1, 2 or 4 concurrent lanes: the reductions are
+    order-independent, so the matches are the oracle's in every case."""
+    from paper_1506_07656_gb300 import dm
+    img1, img2 = _case("ragged_37x29_33x41")
+    want = oracle.invariant_match(img1.astype(np.float32), img2.astype(np.float32), "f32")
+    ctx = _ctx("fp32")
+    dm.dm_set_batch_lanes(ctx.ctx, lanes)
+    got = _run(torch_cuda, ctx, img1, img2)
+    np.testing.assert_array_equal(got, want.astype(np.float32).astype(np.float64))
+
+
+def test_workspace_for_fewer_lanes(torch_cuda):
+    """A workspace sized for one lane runs the transforms one after the other
+    although the context asks for four lanes."""
+    from paper_1506_07656_gb300 import dm
+    torch = torch_cuda
+    img1, img2 = _case("smooth_40x32")
+    want = oracle.invariant_match(img1.astype(np.float32), img2.astype(np.float32), "f32")
+    ctx = _ctx("fp32")
+    dm.dm_set_batch_lanes(ctx.ctx, 1)
+    one = dm.dm_invariant_workspace_bytes(ctx.ctx, 40, 32, 40, 32)
+    dm.dm_set_batch_lanes(ctx.ctx, 4)
+    four = dm.dm_invariant_workspace_bytes(ctx.ctx, 40, 32, 40, 32)
+    assert four > one
+    i1 = torch.as_tensor(img1, dtype=torch.float32, device="cuda")
+    i2 = torch.as_tensor(img2, dtype=torch.float32, device="cuda")
+    ws = torch.empty(one, dtype=torch.uint8, device="cuda")
+    out = torch.zeros((dm.dm_geometry(40, 32, 40, 32)["n_patch0"], 5), dtype=torch.float32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    dm.dm_match_invariant(ctx.ctx, i1, i2, ws, out, cnt)
+    torch.cuda.synchronize()
+    got = out[:int(cnt.item())].cpu().numpy().astype(np.float64)
+    np.testing.assert_array_equal(got, want.astype(np.float32).astype(np.float64))
