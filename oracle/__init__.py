@@ -443,7 +443,7 @@ def invariant_match(img1: np.ndarray, img2: np.ndarray, prec: str = "f64", trans
     images (p -> sigma1 p, p' -> sigma2 R_theta p', here about the image
     centres, rounded to the nearest pixel) and pooled; Eq. 16 then keeps the
     tuples that are the best of their 4x4 cell of I (an atomic patch of I) and
-    of I' (readings c17, c24-c26).  Transforms whose images are too small for
+    of I'.  Transforms whose images are too small for
     the pyramid are skipped.  Rows (x1, y1, x2, y2, score) in patch order."""
     c = dict(DEFAULT_CFG, **cfg)
     lam = c.pop("lam")

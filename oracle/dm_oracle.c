@@ -81,10 +81,10 @@ int orc_real_size(void) { return (int)sizeof(real); }
 
 typedef struct {
     int W1, H1, W2, H2;
-    int L;            /* number of aggregation iterations (c14) */
-    int P0x, P0y;     /* atomic grid G_4: centres 4k+2 (c7) */
+    int L;            /* number of aggregation iterations */
+    int P0x, P0y;     /* atomic grid G_4: centres 4k+2 */
     int Lx, Ly;       /* lattice 4Z^2 inside image 1, patches of levels >= 1 */
-    int dw[ORC_MAXL + 2], dh[ORC_MAXL + 2]; /* map domain of level l (c11) */
+    int dw[ORC_MAXL + 2], dh[ORC_MAXL + 2]; /* map domain of level l */
 } geom;
 
 static int ceil_half(int v) { return (v + 1) / 2; }
@@ -225,7 +225,7 @@ double orc_exp_r(double z) { return (double)REXP((real)z); }
 /* Pixel descriptors (Sec. 3.2 "Pixel descriptor"; parameters of Sec. 5.2)    */
 /* ------------------------------------------------------------------------- */
 
-/* Gaussian taps of standard deviation nu (reading c1), computed in double and
+/* Gaussian taps of standard deviation nu, computed in double and
  * rounded once to the working precision.  Returns the radius R (0 = identity). */
 static int gauss_taps(double nu, real* w, int cap) {
     if (!(nu > 0.0)) { w[0] = (real)1.0; return 0; }
@@ -274,7 +274,7 @@ int orc_descriptors(const float* img, int W, int H, const double* cfg, real* out
     if (!s || !o || !tmp) { free(s); free(o); free(tmp); return -2; }
     for (size_t i = 0; i < n; i++) s[i] = (real)img[i] * scale;          /* c3 */
     smooth(s, W, H, 1, 0, 1, w1, R1, tmp);                                 /* nu1 */
-    /* 8 orientations (c4): exact direction table, r = sqrt(1/2) */
+    /* 8 orientations: exact direction table, r = sqrt(1/2) */
     const real r = (real)0.70710678118654752;
     const real dc[8] = {1, r, 0, -r, -1, -r, 0, r};
     const real ds[8] = {0, r, 1, r, 0, -r, -1, -r};
@@ -295,7 +295,7 @@ int orc_descriptors(const float* img, int W, int H, const double* cfg, real* out
         o[i] = (real)2 / d - (real)1;
     }
     smooth(o, W, H, 8, 0, 8, w3, R3, tmp);                                 /* nu3 */
-    for (size_t i = 0; i < n; i++) {                                       /* [8 channels, mu] / norm (c5) */
+    for (size_t i = 0; i < n; i++) {                                       /* [8 channels, mu] / norm */
         real acc = 0;
         for (int k = 0; k < 8; k++) acc = RFMA(o[i * 8 + k], o[i * 8 + k], acc);
         acc = RFMA(mu, mu, acc);
@@ -313,9 +313,9 @@ int orc_descriptors(const float* img, int W, int H, const double* cfg, real* out
 
 /* sim of the atomic patch p (grid index) of I with the 4x4 window of I' at
  * pixel (tx, ty): (1/16) sum over the 16 pixels of the 9-D dot products.
- * Window convention (c6): centre 2 <-> pixels 0..3, i.e. [t-2, t+1]^2;
+ * Window convention: centre 2 <-> pixels 0..3, i.e. [t-2, t+1]^2;
  * descriptors of I' are zero outside the image, and so are those of the
- * pixels of a partial atomic patch that fall outside I (c7).
+ * pixels of a partial atomic patch that fall outside I.
  * Order: dx = 0..3 (outer), channel c = 0..8, dy = 0..3 (inner), one fma per
  * term from acc = 0, then one multiplication by 1/16. */
 static real corr0(const real* d1, int W1, int H1, const real* d2, int W2, int H2, int px, int py, int tx, int ty) {
@@ -326,7 +326,7 @@ static real corr0(const real* d1, int W1, int H1, const real* d2, int W2, int H2
                 int x2 = tx - 2 + dx, y2 = ty - 2 + dy;
                 int x1 = px - 2 + dx, y1 = py - 2 + dy;
                 if (x2 < 0 || y2 < 0 || x2 >= W2 || y2 >= H2) continue;   /* zero term */
-                if (x1 >= W1 || y1 >= H1) continue;   /* partial atomic patch (c7): zero term */
+                if (x1 >= W1 || y1 >= H1) continue;   /* partial atomic patch: zero term */
                 real a = d1[((size_t)y1 * W1 + x1) * 9 + c];
                 real b = d2[((size_t)y2 * W2 + x2) * 9 + c];
                 acc = RFMA(a, b, acc);
@@ -405,7 +405,7 @@ static void pool_map(const real* src, int sw, int sh, real* dst, uint8_t* am, do
 }
 
 /* Map of one lattice patch at a level >= 1 from its children's pooled maps
- * (Eq. 12, readings c10, c11, c21): kid[i] = child i's map on the same domain
+ * (Eq. 12): kid[i] = child i's map on the same domain
  * (mw x mh), NULL where child i does not exist; n = number of existing
  * children.  FP64: the rectified average (Algorithm 1 order); FP32 mirror: the
  * unrectified average (the power follows the pooling). */
@@ -648,7 +648,7 @@ int orc_level1_pooled(const real* d1, int W1, int H1, const real* d2, int W2, in
 /* reached[l]   : number of distinct tuples at level l (l = 0..L).            */
 /* ------------------------------------------------------------------------- */
 
-/* Path scores (reading c15).  FP64: plain double sums.  FP32 mirror: unsigned
+/* Path scores.  FP64: plain double sums.  FP32 mirror: unsigned
  * fixed point with 28 fractional bits; every term (a map value in [0, 1]) is
  * rounded to the nearest multiple of 2^-28 (ties to even) and the sum of the
  * L + 1 terms (< 16) is exact, hence independent of order and of the merging;
@@ -855,7 +855,7 @@ int orc_backtrack(int W1, int H1, int W2, int H2, real** pooled, uint8_t** amax,
     return 0;
 }
 
-/* Reciprocal verification (Eq. 16, reading c17): keep the best tuple of each
+/* Reciprocal verification (Eq. 16): keep the best tuple of each
  * atomic patch iff it is also the best tuple of its 4x4 cell of I'.  Output in
  * patch order: out[k] = {x1, y1, x2, y2, score}.  Returns the count. */
 int orc_reciprocal(int W1, int H1, int W2, int H2, const real* bestP_s, const long long* bestP_i,
