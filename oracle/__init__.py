@@ -190,13 +190,17 @@ class Pyramid:
     top: np.ndarray | None = None                # [npatch(L)][dh[L]][dw[L]]
     valid: list = field(default_factory=list)    # l = 0..L: [npatch(l)] uint8
     gap: list | None = None                      # optional, like pooled: relative top-two gap of each argmax
+    cmaps: list | None = None                    # optional, l = 1..L: [npatch(l)][dh[l]][dw[l]] maps before pooling
 
 
 def pyramid(d1: np.ndarray, d2: np.ndarray, prec: str = "f64", lam: float = DEFAULT_CFG["lam"],
-            compensated: bool = True, gaps: bool = False, patches: np.ndarray | None = None) -> Pyramid:
+            compensated: bool = True, gaps: bool = False, patches: np.ndarray | None = None,
+            maps: bool = False) -> Pyramid:
     """Level maps of Algorithm 1.  `compensated` selects the FP32 mirror's
     child sum (TwoSum-compensated or plain, both in child order); FP64 ignores it.
     `gaps`: also the relative top-two gap of every pooling decision.
+    `maps`: also each level's maps before pooling (pyr.cmaps[l], l = 1..L):
+    FP64 the rectified C_l; FP32 the unrectified averages (C_l is their power).
     `patches`: [P0][144] vectors that replace image 1's atomic patches (the
     approximate form, Sec. 4.1); d1 then only gives the size of image 1."""
     dt = _dtype(prec)
@@ -219,17 +223,22 @@ def pyramid(d1: np.ndarray, d2: np.ndarray, prec: str = "f64", lam: float = DEFA
     if gaps:
         pyr.gap = [np.zeros(a.shape, dtype=np.float64) for a in pyr.pooled]
         gg = (C.c_void_p * g.L)(*[a.ctypes.data for a in pyr.gap])
+    cc = None
+    if maps:
+        pyr.cmaps = [None] + [np.zeros((g.npatch(l), g.dh[l], g.dw[l]), dtype=dt) for l in range(1, g.L + 1)]
+        cc = (C.c_void_p * (g.L + 1))(None, *[a.ctypes.data for a in pyr.cmaps[1:]])
     lib = _lib(prec)
     fn = lib.orc_pyramid if patches is None else lib.orc_pyramid_vec
     fn.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int,
-                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     if patches is not None:
         src = np.ascontiguousarray(patches, dtype=dt)
         if src.shape != (g.npatch(0), 144):
             raise ValueError(f"patches must be [{g.npatch(0)}][144]")
     else:
         src = d1
-    rc = fn(_ptr(src), W1, H1, _ptr(d2), W2, H2, float(lam), int(bool(compensated)), pp, aa, _ptr(pyr.top), vv, gg)
+    rc = fn(_ptr(src), W1, H1, _ptr(d2), W2, H2, float(lam), int(bool(compensated)), pp, aa, _ptr(pyr.top), vv, gg,
+            cc)
     if rc != 0:
         raise ValueError("pyramid oracle failed")
     return pyr
@@ -436,6 +445,39 @@ def _round_px(x, n):
     return np.clip(np.floor(x + x.dtype.type(0.5)).astype(np.int64), 0, n - 1)
 
 
+def _reciprocal_union(C1, T, S, W2: int, H2: int, P0x: int, prec: str) -> np.ndarray:
+    """Eq. 16 over a set of atomic tuples (patch C1 of I, pixel T = y*W2 + x of
+    I', raw score S; a tuple may appear several times): BestAt per patch of I
+    (higher score, then lower T), BestAt' per 4x4 cell of I' (higher score,
+    then lower C1*16 + offset in the cell); a patch's best tuple is kept iff it
+    also wins its cell.  FP32: raw scores are fixed-point integers, rounded to
+    FP32 once here.  Rows (x1, y1, x2, y2, score) in patch order."""
+    C1 = np.asarray(C1, dtype=np.int64)
+    T = np.asarray(T, dtype=np.int64)
+    S = np.asarray(S, dtype=np.float64)
+    CW2 = (W2 + 3) // 4
+    tx, ty = T % W2, T // W2
+    Q = C1 * 16 + (ty & 3) * 4 + (tx & 3)
+    cell2 = (ty >> 2) * CW2 + (tx >> 2)
+    o = np.lexsort((T, -S, C1))
+    first = np.ones(len(o), bool)
+    first[1:] = C1[o][1:] != C1[o][:-1]
+    bestP = {int(C1[i]): (S[i], int(T[i])) for i in o[first]}
+    o = np.lexsort((Q, -S, cell2))
+    first = np.ones(len(o), bool)
+    first[1:] = cell2[o][1:] != cell2[o][:-1]
+    bestQ = {int(cell2[i]): (S[i], int(Q[i])) for i in o[first]}
+    out = []
+    for c1 in sorted(bestP):
+        s, t = bestP[c1]
+        tx_, ty_ = t % W2, t // W2
+        q = bestQ.get((ty_ >> 2) * CW2 + (tx_ >> 2))
+        if q is not None and q[0] == s and q[1] == c1 * 16 + (ty_ & 3) * 4 + (tx_ & 3):
+            score = float(np.float32(s) * np.float32(1.0 / 268435456.0)) if prec == "f32" else float(s)
+            out.append((4 * (c1 % P0x) + 2, 4 * (c1 // P0x) + 2, tx_, ty_, score))
+    return np.array(out, dtype=np.float64).reshape(-1, 5)
+
+
 def invariant_match(img1: np.ndarray, img2: np.ndarray, prec: str = "f64", transforms=None, **cfg):
     """Algorithm 2: DeepMatching of I downsized by sigma1 against I' downsized by
     sigma2 and rotated by -theta, for every transform; every atomic
@@ -452,8 +494,7 @@ def invariant_match(img1: np.ndarray, img2: np.ndarray, prec: str = "f64", trans
     H2, W2 = img2.shape
     go = geometry(W1, H1, W2, H2)
     P0x, P0y = go.P0x, go.P0y
-    CW2 = (W2 + 3) // 4
-    cells1, tpix, qloc, scores = [], [], [], []
+    cells1, tpix, scores = [], [], []
     for (s1, s2, k) in (transforms or invariant_transforms()):
         i1 = warp(img1, s1, 0, prec)
         i2 = warp(img2, s2, k, prec)
@@ -479,33 +520,151 @@ def invariant_match(img1: np.ndarray, img2: np.ndarray, prec: str = "f64", trans
         X2, Y2 = _round_px(x2, W2), _round_px(y2, H2)
         cells1.append(C1)
         tpix.append(Y2 * W2 + X2)
-        qloc.append((Y2 & 3) * 4 + (X2 & 3))
         scores.append(sc)
-    out = []
-    if cells1:
-        C1 = np.concatenate(cells1)
-        T = np.concatenate(tpix)
-        Q = C1 * 16 + np.concatenate(qloc)
-        S = np.concatenate(scores)
-        cell2 = (T // W2 >> 2) * CW2 + (T % W2 >> 2)
-        # BestAt: per cell of I the larger score, then the lower pixel index of I'
-        o = np.lexsort((T, -S, C1))
-        first = np.ones(len(o), bool)
-        first[1:] = C1[o][1:] != C1[o][:-1]
-        bestP = {int(C1[i]): (S[i], int(T[i])) for i in o[first]}
-        # BestAt': per cell of I' the larger score, then the lower (patch, offset) index
-        o = np.lexsort((Q, -S, cell2))
-        first = np.ones(len(o), bool)
-        first[1:] = cell2[o][1:] != cell2[o][:-1]
-        bestQ = {int(cell2[i]): (S[i], int(Q[i])) for i in o[first]}
-        for c1 in sorted(bestP):
-            s, t = bestP[c1]
-            tx_, ty_ = t % W2, t // W2
-            q = bestQ.get((ty_ >> 2) * CW2 + (tx_ >> 2))
-            if q is not None and q[0] == s and q[1] == c1 * 16 + (ty_ & 3) * 4 + (tx_ & 3):
-                score = float(np.float32(s) * np.float32(1.0 / 268435456.0)) if prec == "f32" else float(s)
-                out.append((4 * (c1 % P0x) + 2, 4 * (c1 // P0x) + 2, tx_, ty_, score))
-    return np.array(out, dtype=np.float64).reshape(-1, 5)
+    if not cells1:
+        return np.zeros((0, 5), dtype=np.float64)
+    return _reciprocal_union(np.concatenate(cells1), np.concatenate(tpix), np.concatenate(scores), W2, H2, P0x, prec)
+
+
+# --------------------------------------------------------------------------- #
+# DM*: the earlier backtracking variant (Sec. 5.3, Table "oldvsnew")           #
+# --------------------------------------------------------------------------- #
+def local_maxima(m: np.ndarray) -> np.ndarray:
+    """Mask of the local maxima of one correlation map (reading: the paper
+    names them without a tie rule): q is one iff m[q] > 0 and, over its 8
+    neighbours r inside the map, m[q] > m[r] for r before q in row-major order
+    and m[q] >= m[r] for r after q -- so a plateau gives its first point and
+    two maxima are never neighbours."""
+    m = np.asarray(m)
+    H, W = m.shape
+    pad = np.full((H + 2, W + 2), -np.inf)
+    pad[1:-1, 1:-1] = m
+    mask = m > 0
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            if dy == 0 and dx == 0:
+                continue
+            nb = pad[1 + dy:H + 1 + dy, 1 + dx:W + 1 + dx]
+            mask &= (m > nb) if (dy < 0 or (dy == 0 and dx < 0)) else (m >= nb)
+    return mask
+
+
+def pow_vec(x: np.ndarray, lam: float, prec: str) -> np.ndarray:
+    """x^lam element by element in the working precision (Eq. 11)."""
+    dt = _dtype(prec)
+    x = np.ascontiguousarray(x, dtype=dt)
+    out = np.empty_like(x)
+    lib = _lib(prec)
+    lib.orc_pow_vec.argtypes = [C.c_void_p, C.c_longlong, C.c_double, C.c_void_p]
+    lib.orc_pow_vec(_ptr(x), x.size, float(lam), _ptr(out))
+    return out
+
+
+def _child(g: Geometry, l: int, ix: int, iy: int, i: int) -> int:
+    """Child i of lattice patch (ix, iy) at level l (Eq. 5: offsets o_i =
+    (-1,-1), (-1,+1), (+1,-1), (+1,+1) as (x, y), 2^l o_i pixels), as an index
+    at level l-1, or -1 outside the grid."""
+    ox = 1 if i >= 2 else -1
+    oy = 1 if i & 1 else -1
+    if l == 1:
+        cx, cy = ix + (ox - 1) // 2, iy + (oy - 1) // 2
+        return cy * g.P0x + cx if 0 <= cx < g.P0x and 0 <= cy < g.P0y else -1
+    st = 1 << (l - 2)
+    cx, cy = ix + ox * st, iy + oy * st
+    return cy * g.Lx + cx if 0 <= cx < g.Lx and 0 <= cy < g.Ly else -1
+
+
+def _ps_term(prec: str):
+    """Score term of a map value: FP64 the value; FP32 the nearest multiple of
+    2^-28 as a fixed-point integer (ties to even), as for the path scores."""
+    if prec == "f32":
+        return lambda v: int(np.rint(np.float32(v) * np.float32(268435456.0)))
+    return float
+
+
+def dmstar_entries(pyr: Pyramid, l: int, lam: float = DEFAULT_CFG["lam"]) -> dict:
+    """Entry points of DM* at level l >= 1: the local maxima of the maps C_l of
+    the existing patches, {(p, qy, qx): score term of C_l(p, q)} (needs
+    pyramid(..., maps=True); FP32 detects on the unrectified averages, whose
+    order is C_l's, and raises the value to lam for the score)."""
+    g = pyr.geom
+    term = _ps_term(pyr.prec)
+    out = {}
+    for p in range(g.npatch(l)):
+        if not pyr.valid[l][p]:
+            continue
+        m = pyr.cmaps[l][p]
+        ys, xs = np.nonzero(local_maxima(m))
+        if len(ys) == 0:
+            continue
+        v = m[ys, xs]
+        if pyr.prec == "f32":
+            v = pow_vec(v, lam, "f32")
+        for y, x, val in zip(ys.tolist(), xs.tolist(), v.tolist()):
+            out[(p, y, x)] = term(val)
+    return out
+
+
+def dmstar_backtrack(pyr: Pyramid, lam: float = DEFAULT_CFG["lam"], entries: str = "maxima") -> dict:
+    """DM*'s backtracking: tuples (l, p, q, s) start at the entry points of every
+    level (entries="maxima") -- or, for comparison, at every position of the
+    top level with the new form's entry set (entries="top") -- and carry their
+    start score unchanged down the path (Eq. 13 children, merged by the highest
+    start); an atomic tuple's score is its start plus the rectified atomic
+    correlation at its end, P_0 at the last step (reading: "start and end
+    point").  Returns {(c, ty, tx): raw score} of the atomic tuples."""
+    g = pyr.geom
+    L = g.L
+    term = _ps_term(pyr.prec)
+    if entries == "maxima":
+        F = dmstar_entries(pyr, L, lam)
+    else:
+        F = {}
+        for p in range(g.npatch(L)):
+            if pyr.valid[L][p]:
+                for (y, x), v in np.ndenumerate(pyr.top[p]):
+                    F[(p, y, x)] = term(v)
+    leaves = {}
+    for l in range(L, 0, -1):
+        nxt = dmstar_entries(pyr, l - 1, lam) if (l - 1 >= 1 and entries == "maxima") else {}
+        P, A = pyr.pooled[l - 1], pyr.argmax[l - 1]
+        mw, mh = g.dw[l], g.dh[l]
+        for (p, qy, qx), s in F.items():
+            ix, iy = p % g.Lx, p // g.Lx
+            for i in range(4):
+                c = _child(g, l, ix, iy, i)
+                if c < 0 or not pyr.valid[l - 1][c]:
+                    continue
+                rx, ry = qx + (1 if i >= 2 else -1), qy + (1 if i & 1 else -1)
+                if not (0 <= rx < mw and 0 <= ry < mh):
+                    continue
+                code = int(A[c, ry, rx])
+                key = (c, 2 * ry + code // 3 - 1, 2 * rx + code % 3 - 1)
+                v = s if l - 1 >= 1 else s + term(P[c, ry, rx])
+                tgt = nxt if l - 1 >= 1 else leaves
+                if key not in tgt or v > tgt[key]:
+                    tgt[key] = v
+        F = nxt
+    return leaves
+
+
+def dmstar_match(img1: np.ndarray, img2: np.ndarray, prec: str = "f64", entries: str = "maxima", **cfg) -> np.ndarray:
+    """DM* (Sec. 5.3): entry points at the local maxima of every level >= 1,
+    start + end scoring, then Eq. 16 as in the new form.  Rows (x1, y1, x2,
+    y2, score) in patch order."""
+    c = dict(DEFAULT_CFG, **cfg)
+    lam = c.pop("lam")
+    compensated = c.pop("compensated", True)
+    d1 = descriptors(img1, prec, **c)
+    d2 = descriptors(img2, prec, **c)
+    pyr = pyramid(d1, d2, prec, lam, compensated=compensated, maps=True)
+    leaves = dmstar_backtrack(pyr, lam, entries)
+    g = pyr.geom
+    if not leaves:
+        return np.zeros((0, 5), dtype=np.float64)
+    keys = np.array(list(leaves.keys()), dtype=np.int64)
+    S = np.array(list(leaves.values()), dtype=np.float64)
+    return _reciprocal_union(keys[:, 0], keys[:, 1] * g.W2 + keys[:, 2], S, g.W2, g.H2, g.P0x, prec)
 
 
 def loss_grad(d1: np.ndarray, d2: np.ndarray, prec: str = "f64", lam: float = DEFAULT_CFG["lam"]):

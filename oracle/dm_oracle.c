@@ -219,6 +219,10 @@ static float orc_powf(float x, float lam) {
 
 /* exported for the accuracy pin of the FP32 routines */
 double orc_pow_r(double x, double lam) { return (double)RPOW((real)x, (real)lam); }
+/* out[i] = x[i]^lam in the working precision (the rectification of Eq. 11). */
+void orc_pow_vec(const real* x, long long n, double lam, real* out) {
+    for (long long i = 0; i < n; i++) out[i] = RPOW(x[i], (real)lam);
+}
 double orc_exp_r(double z) { return (double)REXP((real)z); }
 
 /* ------------------------------------------------------------------------- */
@@ -456,27 +460,31 @@ static void level_average(const real* const* kid, int n, int mw, int mh, int com
 /* pgap[l]   : same shape, optional (NULL): relative top-two gap of the argmax */
 /* top       : [npatch(L)][dh[L]][dw[L]]       = C_L                          */
 /* valid[l]  : [npatch(l)] patch membership of G_{4*2^l}, l = 0..L            */
+/* cmaps[l]  : optional (NULL, or NULL entries): [npatch(l)][dh[l]][dw[l]],   */
+/*             l = 1..L, the level's maps before pooling -- FP64: C_l        */
+/*             (rectified); FP32 mirror: the unrectified averages, whose     */
+/*             power is C_l                                                    */
 /* ------------------------------------------------------------------------- */
 static int pyramid_impl(const real* d1, const real* amat, int W1, int H1, const real* d2, int W2, int H2,
                         double lambda, int compensated, real** pooled, uint8_t** amax, real* top, uint8_t** valid,
-                        double** pgap);
+                        double** pgap, real** cmaps);
 
 int orc_pyramid(const real* d1, int W1, int H1, const real* d2, int W2, int H2, double lambda, int compensated,
-                real** pooled, uint8_t** amax, real* top, uint8_t** valid, double** pgap) {
-    return pyramid_impl(d1, NULL, W1, H1, d2, W2, H2, lambda, compensated, pooled, amax, top, valid, pgap);
+                real** pooled, uint8_t** amax, real* top, uint8_t** valid, double** pgap, real** cmaps) {
+    return pyramid_impl(d1, NULL, W1, H1, d2, W2, H2, lambda, compensated, pooled, amax, top, valid, pgap, cmaps);
 }
 
 /* The pyramid with image 1's atomic patches given as vectors: amat
  * [P0][144] (k = (dy*4 + dx)*9 + c), e.g. each patch replaced by its
  * prototype (approximate form, Sec. 4.1).  W1, H1 fix the geometry. */
 int orc_pyramid_vec(const real* amat, int W1, int H1, const real* d2, int W2, int H2, double lambda, int compensated,
-                    real** pooled, uint8_t** amax, real* top, uint8_t** valid, double** pgap) {
-    return pyramid_impl(NULL, amat, W1, H1, d2, W2, H2, lambda, compensated, pooled, amax, top, valid, pgap);
+                    real** pooled, uint8_t** amax, real* top, uint8_t** valid, double** pgap, real** cmaps) {
+    return pyramid_impl(NULL, amat, W1, H1, d2, W2, H2, lambda, compensated, pooled, amax, top, valid, pgap, cmaps);
 }
 
 static int pyramid_impl(const real* d1, const real* amat, int W1, int H1, const real* d2, int W2, int H2,
                         double lambda, int compensated, real** pooled, uint8_t** amax, real* top, uint8_t** valid,
-                        double** pgap) {
+                        double** pgap, real** cmaps) {
     geom g;
     if (make_geom(W1, H1, W2, H2, &g)) return -1;
     const real lam = (real)lambda;
@@ -532,6 +540,7 @@ static int pyramid_impl(const real* d1, const real* amat, int W1, int H1, const 
                 const real* kid[4];
                 for (int i = 0; i < 4; i++) kid[i] = ci[i] >= 0 ? pooled[l - 1] + (size_t)ci[i] * cw * ch : NULL;
                 level_average(kid, n, mw, mh, compensated, lam, map);
+                if (cmaps && cmaps[l]) memcpy(cmaps[l] + (size_t)p * mw * mh, map, (size_t)mw * mh * sizeof(real));
                 if (l < L) {
                     size_t off = (size_t)p * g.dw[l + 1] * g.dh[l + 1];
                     pool_map(map, mw, mh, pooled[l] + off, amax[l] + off, pgap ? pgap[l] + off : NULL, g.dw[l + 1],
