@@ -52,6 +52,7 @@ def _args():
     ap.add_argument("--batch-lanes", type=int, default=2, help="concurrent lanes of the batched form (1..4)")
     ap.add_argument("--batch-pairs", type=int, default=8, help="pairs per step of the headline batched measurement")
     ap.add_argument("--no-approx", action="store_true", help="skip the approximate-form (Sec. 4.1) measurement")
+    ap.add_argument("--no-star", action="store_true", help="skip the DM* (Sec. 5.3) measurement")
     ap.add_argument("--no-invariant", action="store_true",
                     help="skip the scale and rotation invariant form (Sec. 4.2) measurement")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
@@ -336,6 +337,52 @@ def _measure_approx(dm, torch, a, pair, stream, D=1024, iters=10):
             "ms_per_step": ms, "stages_ms": stages, "matches": int(len(approx_m)), "exact_matches": int(len(exact_m)),
             "within_10px_of_exact": float(np.mean(close)) if close else None,
             "note": "one pair per step; the prototype dictionary is learned on every step"}
+
+
+def _measure_star(dm, torch, a, pair, stream, prec="bf16"):
+    """DM* (Sec. 5.3) on the bench pair: one dm_match_star per step (descriptors,
+    pyramid, the local-maximum search at every level, backtracking with start
+    + end scores), K steps timed with CUDA events.  Also: its matches against
+    the new form's on the same pair."""
+    import numpy as np
+    W, H = a.width, a.height
+    ctx = dm.Context(dm.DM_BF16 if prec == "bf16" else dm.DM_FP32)
+    try:
+        i1, i2 = torch.from_numpy(pair.img1).cuda(), torch.from_numpy(pair.img2).cuda()
+        ws = torch.empty(dm.dm_star_workspace_bytes(ctx.ctx, W, H, W, H)["match"], dtype=torch.uint8, device="cuda")
+        P0 = dm.dm_geometry(W, H, W, H)["n_patch0"]
+        out = torch.empty((P0, 5), dtype=torch.float32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+        launches0 = dm.dm_timing_read(ctx.ctx)[2]
+        dm.dm_match_star(ctx.ctx, i1, i2, ws, out, cnt, stream)
+        launches = dm.dm_timing_read(ctx.ctx)[2] - launches0
+        for _ in range(max(a.warmup - 1, 1)):
+            dm.dm_match_star(ctx.ctx, i1, i2, ws, out, cnt, stream)
+        torch.cuda.synchronize()
+        steps = max(min(a.steps, 10), 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            dm.dm_match_star(ctx.ctx, i1, i2, ws, out, cnt, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        status, reached = dm.dm_read_status(ctx.ctx, ws, 1)
+        star = out[:int(cnt.item())].cpu().numpy().astype(np.float64)
+        del ws
+        torch.cuda.empty_cache()
+        mws = ctx.workspace("match", W, H, W, H)
+        dm.dm_match(ctx.ctx, i1, i2, mws, out, cnt, stream)
+        torch.cuda.synchronize()
+        new = out[:int(cnt.item())].cpu().numpy().astype(np.float64)
+    finally:
+        ctx.close()
+    key = {(float(m[0]), float(m[1])): (float(m[2]), float(m[3])) for m in new}
+    same = [key.get((float(m[0]), float(m[1]))) == (float(m[2]), float(m[3])) for m in star]
+    return {"workload": f"{W}x{H}", "precision": prec, "pairs_per_s": 1000.0 / ms, "ms_per_step": ms,
+            "kernel_launches_per_step": int(launches), "status": int(status), "atomic_arrivals": int(reached[0]),
+            "matches": int(len(star)), "new_form_matches": int(len(new)),
+            "same_match_as_new_form": float(np.mean(same)) if same else None}
 
 
 def _measure_invariant(dm, torch, a, stream, W=512, H=224, prec="bf16"):
@@ -632,6 +679,10 @@ def run_ours(a):
     if not a.no_approx and world == 1:
         approx = _measure_approx(dm, torch, a, pair, stream)
         torch.cuda.empty_cache()
+    star = None
+    if not a.no_star and world == 1:
+        star = _measure_star(dm, torch, a, pair, stream)
+        torch.cuda.empty_cache()
     invariant = None
     if not a.no_invariant and world == 1:
         invariant = _measure_invariant(dm, torch, a, stream)
@@ -691,6 +742,7 @@ def run_ours(a):
                             "note": "one pair per step, no graph; stage times and rooflines come from these steps"},
             "batched": batch,
             "approx": approx,
+            "star": star,
             "invariant": invariant,
             "stages_ms": r["stages"],
             "cpu_baseline": cpu,

@@ -215,6 +215,27 @@ dm_status dm_match(dm_ctx* ctx, const float* d_img1, int W1, int H1, const float
 dm_status dm_match_host(dm_ctx* ctx, const float* h_img1, int W1, int H1, const float* h_img2, int W2, int H2,
                         void* d_ws, size_t ws_bytes, dm_match_t* h_out, int capacity, int* h_count, void* stream);
 
+/* DM*, the earlier backtracking variant compared in Sec. 5.3 (Table
+ * "oldvsnew"): entry points are the local maxima of the maps C_l(p, .) of every
+ * level l = 1..L (q is one iff C_l(p, q) > 0, C_l(p, q) > C_l(p, r) for its
+ * in-domain 8-neighbours r before q in row-major order and >= for those
+ * after it), each with start score C_l(p, q); a tuple carries its start score
+ * down unchanged (Eq. 13 children, merged by the highest start), and an
+ * atomic correspondence scores start + the rectified atomic correlation at
+ * its end (P_0 at the last step).  Reciprocal verification and output as
+ * dm_backtrack / dm_match.  dm_backtrack_star takes a pyramid built by a
+ * context with the same parameters as ctx (lambda is the context's);
+ * d_ws >= backtrack_bytes of dm_star_workspace_bytes.  dm_match_star runs the
+ * whole chain; d_ws >= match_bytes.  The tables of DM* also hold the entry
+ * points, so its workspaces are larger than dm_backtrack's / dm_match's.
+ * dm_read_status works on both workspaces. */
+dm_status dm_star_workspace_bytes(const dm_ctx* ctx, int W1, int H1, int W2, int H2, size_t* backtrack_bytes,
+                                  size_t* match_bytes);
+dm_status dm_backtrack_star(dm_ctx* ctx, const dm_pyramid* pyr, void* d_ws, size_t ws_bytes, dm_match_t* d_out,
+                            int capacity, int* d_count, void* stream);
+dm_status dm_match_star(dm_ctx* ctx, const float* d_img1, int W1, int H1, const float* d_img2, int W2, int H2,
+                        void* d_ws, size_t ws_bytes, dm_match_t* d_out, int capacity, int* d_count, void* stream);
+
 /* Scale and rotation invariant form (Sec. 4.2, Algorithm 2), device buffers.
  * For sigma = -2, -1.5, .., 2 and theta = k pi/4 (k = 0..7) the method runs on
  * image 1 downsized by sigma1 = max(1, 2^sigma) against image 2 downsized by

@@ -108,8 +108,8 @@ struct MatchLayout {
     size_t bytes;
 };
 
-void match_layout(const DmGeom& g, int precision, MatchLayout* m) {
-    dm_bt_layout(g, &m->bt);
+void match_layout(const DmGeom& g, int precision, MatchLayout* m, bool star = false) {
+    dm_bt_layout(g, &m->bt, star);
     size_t o = m->bt.bytes;
     m->desc1 = o; o = dm_align(o + (size_t)g.W1 * g.H1 * 9 * 4);
     m->desc2 = o; o = dm_align(o + (size_t)g.W2 * g.H2 * 9 * 4);
@@ -296,15 +296,22 @@ void dm_pyr_layout(const DmGeom& g, int precision, DmPyrLayout* o) {
     o->bytes = off;
 }
 
-void dm_bt_layout(const DmGeom& g, DmBtLayout* o) {
+void dm_bt_layout(const DmGeom& g, DmBtLayout* o, bool star) {
     memset(o, 0, sizeof(*o));
     size_t off = 0;
     o->header = off; off = dm_align(off + sizeof(DmWsHeader));
-    // bound on merged tuples per level: B_L = entries; B_l = min(4 B_{l+1}, |P_l|)
+    // bound on merged tuples per level: B_L = entries; B_l = min(4 B_{l+1}, |P_l|).
+    // DM*: level l also receives its local maxima, which are never neighbours,
+    // so at most one per 2x2 block of the domain (|P_l| per level, with
+    // P_L's size taken as npatch(L) x dsize(L+1)): B_L = that, B_l =
+    // min(4 B_{l+1} + |P_l|, 2 |P_l|), and level L has a table too.
     unsigned long long B = (unsigned long long)g.npatch(g.L) * (unsigned long long)g.dsize(g.L);
-    for (int l = g.L - 1; l >= 1; l--) {
+    const int top = star ? g.L : g.L - 1;
+    if (star) B = 0;
+    for (int l = top; l >= 1; l--) {
         unsigned long long pooled = (unsigned long long)g.npatch(l) * (unsigned long long)g.dsize(l + 1);
-        B = 4ull * B < pooled ? 4ull * B : pooled;
+        if (star) B = 4ull * B + pooled < 2ull * pooled ? 4ull * B + pooled : 2ull * pooled;
+        else B = 4ull * B < pooled ? 4ull * B : pooled;
         unsigned long long cap = 2ull * B;
         if (cap < 64ull) cap = 64ull;
         if (cap > 0xfffffff0ull) cap = 0xfffffff0ull;
@@ -939,6 +946,70 @@ dm_status dm_set_tuned_config(dm_ctx* ctx, int W1, int H1, int W2, int H2, const
     if (s != DM_OK) return s;
     std::lock_guard<std::mutex> lk(ctx->tune_mu);
     ctx->tuned[{W1, H1, W2, H2}] = DmTune{chosen[0], chosen[1], chosen[2], chosen[3]};
+    return DM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// DM* (Sec. 5.3): local-maximum entry points at every level, start + end scores
+// ---------------------------------------------------------------------------
+dm_status dm_star_workspace_bytes(const dm_ctx* ctx, int W1, int H1, int W2, int H2, size_t* backtrack_bytes,
+                                  size_t* match_bytes) {
+    if (!ctx) return DM_EINVAL;
+    DmGeom g;
+    dm_status s = check_geom(const_cast<dm_ctx*>(ctx), W1, H1, W2, H2, &g);
+    if (s != DM_OK) return s;
+    DmBtLayout bl;
+    dm_bt_layout(g, &bl, true);
+    MatchLayout ml;
+    match_layout(g, ctx->cfg.precision, &ml, true);
+    if (backtrack_bytes) *backtrack_bytes = bl.bytes;
+    if (match_bytes) *match_bytes = ml.bytes;
+    return DM_OK;
+}
+
+dm_status dm_backtrack_star(dm_ctx* ctx, const dm_pyramid* pyr, void* d_ws, size_t ws_bytes, dm_match_t* d_out,
+                            int capacity, int* d_count, void* stream) {
+    if (!ctx) return DM_EINVAL;
+    if (!pyr || !d_ws || !d_out || !d_count || capacity < 0)
+        return fail(ctx, DM_EINVAL, "dm_backtrack_star: bad arguments");
+    if (!aligned256(d_ws)) return fail(ctx, DM_EINVAL, "workspace must be 256-byte aligned");
+    DmBtLayout bl;
+    dm_bt_layout(pyr->g, &bl, true);
+    if (ws_bytes < bl.bytes) return fail(ctx, DM_ENOMEM, "DM* backtrack workspace %zu < %zu bytes", ws_bytes, bl.bytes);
+    DevGuard dg(ctx->device);
+    cudaError_t e = cudaMemsetAsync(&reinterpret_cast<DmWsHeader*>((char*)d_ws + bl.header)->pyr_status, 0, sizeof(int),
+                                    (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "clear status");
+    e = dm_launch_backtrack_star(pyr->g, *pyr, bl, (char*)d_ws, ctx->cfg.lambda, d_out, capacity, d_count,
+                                 (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "DM* backtracking kernels");
+    return DM_OK;
+}
+
+dm_status dm_match_star(dm_ctx* ctx, const float* d_img1, int W1, int H1, const float* d_img2, int W2, int H2,
+                        void* d_ws, size_t ws_bytes, dm_match_t* d_out, int capacity, int* d_count, void* stream) {
+    if (!ctx) return DM_EINVAL;
+    if (!d_img1 || !d_img2 || !d_ws || !d_out || !d_count || capacity < 0)
+        return fail(ctx, DM_EINVAL, "dm_match_star: bad arguments");
+    if (!aligned256(d_ws)) return fail(ctx, DM_EINVAL, "workspace must be 256-byte aligned");
+    DmGeom g;
+    dm_status s = check_geom(ctx, W1, H1, W2, H2, &g);
+    if (s != DM_OK) return s;
+    MatchLayout ml;
+    match_layout(g, ctx->cfg.precision, &ml, true);
+    if (ws_bytes < ml.bytes) return fail(ctx, DM_ENOMEM, "DM* match workspace %zu < %zu bytes", ws_bytes, ml.bytes);
+    DevGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    char* base = (char*)d_ws;
+    float* desc1 = (float*)(base + ml.desc1);
+    float* desc2 = (float*)(base + ml.desc2);
+    if ((s = run_descriptors(ctx, d_img1, W1, H1, desc1, base + ml.tmp, st)) != DM_OK) return s;
+    if ((s = run_descriptors(ctx, d_img2, W2, H2, desc2, base + ml.tmp, st)) != DM_OK) return s;
+    dm_pyramid py;
+    int* d_status = &reinterpret_cast<DmWsHeader*>(base + ml.bt.header)->pyr_status;
+    if ((s = run_pyramid(ctx, g, desc1, desc2, base + ml.pyr, ml.py, &py, d_status, st)) != DM_OK) return s;
+    cudaError_t e = dm_launch_backtrack_star(g, py, ml.bt, base, ctx->cfg.lambda, d_out, capacity, d_count, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "DM* backtracking kernels");
     return DM_OK;
 }
 

@@ -192,6 +192,7 @@ struct DmWsHeader {
     int pad0[14];
     unsigned int count[DM_MAXL + 2];   // merged tuples per level (level 0: arrivals)
     unsigned int cap[DM_MAXL + 2];     // active merge-table capacity per level
+    unsigned int entries[DM_MAXL + 2]; // DM*: local-maximum entry points per level
 };
 
 struct DmPyrLayout {
@@ -226,7 +227,8 @@ struct DmGradLayout {
 
 void dm_pyr_layout(const DmGeom& g, int precision, DmPyrLayout* o);
 void dm_grad_layout(const DmGeom& g, DmGradLayout* o);
-void dm_bt_layout(const DmGeom& g, DmBtLayout* o);
+// star: the DM* variant's tables (levels 1..L, room for the entry points too)
+void dm_bt_layout(const DmGeom& g, DmBtLayout* o, bool star = false);
 size_t dm_desc_tmp_bytes(int W, int H);
 
 // Suspend-time hint of the kernels' mbarrier waits: a waiting thread sleeps
@@ -270,6 +272,75 @@ struct dm_pyramid {
     const int* proto_of;
     int n0_maps;
 };
+
+// ---------------------------------------------------------------------------
+// Average of a lattice patch's children at one position (Eq. 12, boundary
+// rule): C_l(p, q) before rectification = (1/n) sum over the n existing
+// children c_i of P_{l-1}(c_i, q + o_i), 0 outside the domain.  Shared by the
+// top level and the local-maximum search of DM*, so that both produce the
+// averages of the level pass bit for bit.
+// ---------------------------------------------------------------------------
+struct Kids {
+    const float* base[4];
+    int n;
+};
+
+// One step of the compensated child sum (Knuth's TwoSum gives the same bits
+// for any operands): for non-negative operands, which every map value is,
+// Dekker's Fast2Sum on (max, min) is exact, since the first operand is the
+// larger, with one operation fewer.
+__device__ __forceinline__ void fast_two_sum_add(float& s, float& comp, float v) {
+    const float hi = fmaxf(s, v), lo = fminf(s, v);
+    const float t = __fadd_rn(hi, lo);
+    const float err = __fsub_rn(lo, __fsub_rn(t, hi));
+    s = t;
+    comp = __fadd_rn(comp, err);
+}
+
+// Child sum step: compensated or plain.  The first existing child starts the
+// sum (0 + v = v exactly, the same as starting from zero).
+template <bool COMP>
+__device__ __forceinline__ void child_add(float& s, float& comp, float v) {
+    if (COMP) fast_two_sum_add(s, comp, v);
+    else s = __fadd_rn(s, v);
+}
+
+template <bool COMP>
+__device__ __forceinline__ float child_mean(const Kids& k, int qx, int qy, int mw, int mh, int pitch) {
+    float s = 0.0f, comp = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        if (k.base[i] == nullptr) continue;
+        int ox = (i >= 2) ? 1 : -1, oy = (i & 1) ? 1 : -1;
+        int rx = qx + ox, ry = qy + oy;
+        float v = 0.0f;
+        if (rx >= 0 && ry >= 0 && rx < mw && ry < mh) v = __ldg(k.base[i] + (long long)ry * pitch + rx);
+        child_add<COMP>(s, comp, v);
+    }
+    return __fdiv_rn(__fadd_rn(s, comp), (float)k.n);
+}
+
+
+// (proto_of: the map of atomic child c is map proto_of[c], clamped to
+// [0, n_maps) -- approximate form, l = 1)
+__device__ __forceinline__ bool load_kids(const DmGeom& g, int l, int p, const unsigned char* __restrict__ vprev,
+                                          const float* __restrict__ prev, Kids& k, const int* __restrict__ proto_of,
+                                          int n_maps) {
+    int ix = p % g.Lx, iy = p / g.Lx;
+    long long cs = g.psize(l);     // child pooled map size (domain of level l, padded rows)
+    k.n = 0;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        int c = dm_child(g, l, ix, iy, i);
+        if (c >= 0 && vprev[c]) {
+            k.base[i] = prev + (long long)(proto_of ? min(max(proto_of[c], 0), n_maps - 1) : c) * cs;
+            k.n++;
+        } else {
+            k.base[i] = nullptr;
+        }
+    }
+    return k.n > 0;
+}
 
 // ---------------------------------------------------------------------------
 // Scale and rotation invariant form (Sec. 4.2, Algorithm 2).
@@ -398,6 +469,10 @@ cudaError_t dm_launch_loss_grad(const DmGeom& g, const dm_pyramid& py, const flo
 cudaError_t dm_launch_backtrack(const DmGeom& g, const dm_pyramid& p, const DmBtLayout& bl, char* ws,
                                 dm_match_t* out, int capacity, int* d_count, cudaStream_t st,
                                 const DmRect* rect = nullptr);
+// DM* (Sec. 5.3): entry points at the local maxima of every level's maps,
+// start + end scoring; bl from dm_bt_layout(g, &bl, true).
+cudaError_t dm_launch_backtrack_star(const DmGeom& g, const dm_pyramid& p, const DmBtLayout& bl, char* ws, float lam,
+                                     dm_match_t* out, int capacity, int* d_count, cudaStream_t st);
 // Reciprocal verification (Eq. 16) of BestAt / BestAt' arrays of geometry g.
 cudaError_t dm_launch_reciprocal(const DmGeom& g, unsigned long long* bestP, unsigned long long* bestQ, DmWsHeader* hdr,
                                  dm_match_t* out, int capacity, int* d_count, cudaStream_t st);

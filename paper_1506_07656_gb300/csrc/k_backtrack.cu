@@ -150,7 +150,12 @@ __device__ __forceinline__ void leaf_update_rect(const BtArgs& a, int c, int tx,
 // Children of tuple (l, p, q, s); returns the number of atomic arrivals.
 // The (up to 4) children's pooled values and argmax codes are loaded first,
 // all independent, so their memory latencies overlap; the merges follow.
-template <bool RECT>
+// Variants of the expansion: the new form, the invariant form's rectified
+// leaves, and DM* (start score carried down unchanged, the end value added at
+// the leaf).
+constexpr int BT_EXACT = 0, BT_RECT = 1, BT_STAR = 2;
+
+template <int MODE>
 __device__ __forceinline__ int expand(const BtArgs& a, int l, unsigned int cap_next, int p, int qx, int qy, unsigned int s) {
     const DmGeom& g = a.g;
     const int mw = g.dw[l], mh = g.dh[l], pitch = g.pitch(l);    // pooled map P_{l-1} lives on domain l
@@ -180,12 +185,12 @@ __device__ __forceinline__ int expand(const BtArgs& a, int l, unsigned int cap_n
         if (cc[i] < 0) continue;
         const int rx = rxs[i], ry = rys[i];
         const int tx = 2 * rx + code[i] % 3 - 1, ty = 2 * ry + code[i] / 3 - 1;
-        const unsigned int s2 = s + ps_term(val[i]);
+        const unsigned int s2 = (MODE == BT_STAR && l - 1 >= 1) ? s : s + ps_term(val[i]);
         if (l - 1 >= 1) {
             unsigned int key = (unsigned int)cc[i] * (unsigned int)g.dsize(l - 1) + (unsigned int)(ty * g.dw[l - 1] + tx);
             ht_insert(a, l - 1, cap_next, key, s2);
         } else {
-            if constexpr (RECT) leaf_update_rect(a, cc[i], tx, ty, s2);
+            if constexpr (MODE == BT_RECT) leaf_update_rect(a, cc[i], tx, ty, s2);
             else leaf_update(a, cc[i], tx, ty, s2);
             arrivals++;
         }
@@ -202,6 +207,24 @@ __device__ __forceinline__ void add_arrivals(const BtArgs& a, int n) {
 // Clear the active part of the level-`lvl` table.  Active size: 12x the
 // previous frontier (4 children per tuple: load <= 1/3, few collisions
 // between the 32-slot key blocks), a multiple of 32 within [64, capmax].
+__device__ __forceinline__ void clear_table(const BtArgs& a, int lvl, unsigned long long cap) {
+    if (cap < 64ull) cap = 64ull;
+    const unsigned long long cmax = (unsigned long long)a.capmax[lvl] & ~31ull;
+    if (cap > cmax) cap = cmax;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.hdr->cap[lvl] = (unsigned int)cap;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        a.table[lvl][i] = 0ull;
+}
+
+// DM*: the level-`lvl` table also receives that level's entry points (counted
+// before the backtracking starts); 3 slots per entry (load <= 1/3, like the
+// children's 12 per tuple of 4 children).
+__global__ void k_star_prepare(BtArgs a, int lvl) {
+    const unsigned long long n_prev = lvl == a.g.L ? 0ull : a.hdr->count[lvl + 1];
+    clear_table(a, lvl, (n_prev * HT_SLOTS_PER_PREV + 3ull * a.hdr->entries[lvl] + 31ull) & ~31ull);
+}
+
 __global__ void k_bt_prepare(BtArgs a, int lvl, long long n_top) {
     unsigned long long n_prev = (lvl + 1 == a.g.L) ? (unsigned long long)n_top : a.hdr->count[lvl + 1];
     unsigned long long cap = (n_prev * HT_SLOTS_PER_PREV + 31ull) & ~31ull;
@@ -215,7 +238,7 @@ __global__ void k_bt_prepare(BtArgs a, int lvl, long long n_top) {
 }
 
 // Expansion of the top level: every position of every existing top patch.
-template <bool RECT>
+template <int MODE>
 __global__ void k_bt_expand_top(BtArgs a) {
     const DmGeom& g = a.g;
     const int L = g.L;
@@ -230,7 +253,7 @@ __global__ void k_bt_expand_top(BtArgs a) {
             int q = (int)(e % ds);
             if (a.valid[L][p]) {
                 if (q == 0) atomicAdd(&a.hdr->count[L], (unsigned int)ds);
-                arrivals += expand<RECT>(a, L, cap_next, p, q % g.dw[L], q / g.dw[L], ps_term(a.top[e]));
+                arrivals += expand<MODE>(a, L, cap_next, p, q % g.dw[L], q / g.dw[L], ps_term(a.top[e]));
             }
         }
     }
@@ -242,7 +265,7 @@ __global__ void k_bt_expand_top(BtArgs a) {
 // it reads into a queue in shared memory and expands them 32 at a time, so its
 // lanes stay busy while the slot order (neighbouring positions of one patch
 // together) is kept.
-template <bool RECT>
+template <int MODE>
 __global__ void k_bt_expand(BtArgs a, int l) {
     __shared__ unsigned long long queue[BT_BLOCK / 32][64];
     const DmGeom& g = a.g;
@@ -257,7 +280,7 @@ __global__ void k_bt_expand(BtArgs a, int l) {
         const unsigned int key = (unsigned int)(v >> 32) - 1u;
         const unsigned int sc = (unsigned int)v;
         const int p = (int)(key / ds), t = (int)(key % ds);
-        arrivals += expand<RECT>(a, l, cap_next, p, t % g.dw[l], t / g.dw[l], sc);
+        arrivals += expand<MODE>(a, l, cap_next, p, t % g.dw[l], t / g.dw[l], sc);
     };
     for (unsigned int i0 = blockIdx.x * blockDim.x; i0 < cap; i0 += gridDim.x * blockDim.x) {
         const unsigned int i = i0 + threadIdx.x;
@@ -357,7 +380,59 @@ __global__ void __launch_bounds__(1024) k_reciprocal(BtArgs a, dm_match_t* __res
     }
 }
 
-template <bool RECT>
+// DM* entry points at level l (1..L): the local maxima of the maps C_l(p, .)
+// of the existing patches.  q is one iff A(q) > 0 and, over its in-domain
+// 8-neighbours r, A(q) > A(r) for r before q in row-major order and
+// A(q) >= A(r) for r after it, A being the unrectified average of the level
+// pass (same arithmetic, hence the same order as C_l = A^lambda).  A CTA takes
+// a 32 x 8 tile of positions of one patch and forms the averages of the tile
+// and its one-position halo in shared memory.  COUNT pass: the number of
+// entries per level (sizes the tables); INSERT pass: tuple (l, p, q) with
+// score C_l(p, q) merged into the level-l table.
+constexpr int ST_W = 32, ST_H = 8;
+
+template <bool COMP, bool INSERT>
+__global__ void __launch_bounds__(256) k_star_entries(BtArgs a, int l, float lam, long long n_items) {
+    __shared__ float A[ST_H + 2][ST_W + 2];
+    const DmGeom& g = a.g;
+    const int mw = g.dw[l], mh = g.dh[l];
+    const int tiles_x = (mw + ST_W - 1) / ST_W, tiles = tiles_x * ((mh + ST_H - 1) / ST_H);
+    const unsigned int cap = INSERT ? a.hdr->cap[l] : 0u;
+    const unsigned int ds = (unsigned int)g.dsize(l);
+    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+    unsigned int found = 0;
+    for (long long it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int p = (int)(it / tiles), t = (int)(it % tiles);
+        if (!a.valid[l][p]) continue;                  // the same for the whole CTA
+        Kids k;
+        load_kids(g, l, p, a.valid[l - 1], a.pooled[l - 1], k, l == 1 ? a.proto_of : nullptr, a.n0_maps);
+        const int x0 = (t % tiles_x) * ST_W, y0 = (t / tiles_x) * ST_H;
+        for (int i = threadIdx.x; i < (ST_H + 2) * (ST_W + 2); i += blockDim.x) {
+            const int hy = i / (ST_W + 2), hx = i % (ST_W + 2);
+            const int qx = x0 - 1 + hx, qy = y0 - 1 + hy;
+            A[hy][hx] = (qx >= 0 && qy >= 0 && qx < mw && qy < mh) ? child_mean<COMP>(k, qx, qy, mw, mh, g.pitch(l))
+                                                                   : -INFINITY;
+        }
+        __syncthreads();
+        const int qx = x0 + lx, qy = y0 + ly;
+        if (qx < mw && qy < mh) {
+            const float v = A[ly + 1][lx + 1];
+            const bool m = v > 0.0f && v > A[ly][lx] && v > A[ly][lx + 1] && v > A[ly][lx + 2] && v > A[ly + 1][lx] &&
+                           v >= A[ly + 1][lx + 2] && v >= A[ly + 2][lx] && v >= A[ly + 2][lx + 1] && v >= A[ly + 2][lx + 2];
+            if (m) {
+                if (INSERT) ht_insert(a, l, cap, (unsigned int)p * ds + (unsigned int)(qy * mw + qx), ps_term(dm_powf(v, lam)));
+                else found++;
+            }
+        }
+        __syncthreads();
+    }
+    if (!INSERT) {
+        const unsigned int tot = __reduce_add_sync(0xffffffffu, found);
+        if (lx == 0 && tot) atomicAdd(&a.hdr->entries[l], tot);
+    }
+}
+
+template <int MODE>
 void launch_steps(const BtArgs& a, int grid, cudaStream_t st) {
     const DmGeom& g = a.g;
     const long long n_top = (long long)g.npatch(g.L) * g.dsize(g.L);
@@ -365,9 +440,9 @@ void launch_steps(const BtArgs& a, int grid, cudaStream_t st) {
         if (l - 1 >= 1) k_bt_prepare<<<grid, BT_BLOCK, 0, st>>>(a, l - 1, n_top);
         if (l == g.L) {
             long long nb = (n_top + BT_BLOCK - 1) / BT_BLOCK;
-            k_bt_expand_top<RECT><<<(unsigned)(nb < grid ? nb : grid), BT_BLOCK, 0, st>>>(a);
+            k_bt_expand_top<MODE><<<(unsigned)(nb < grid ? nb : grid), BT_BLOCK, 0, st>>>(a);
         } else {
-            k_bt_expand<RECT><<<grid, BT_BLOCK, 0, st>>>(a, l);
+            k_bt_expand<MODE><<<grid, BT_BLOCK, 0, st>>>(a, l);
         }
     }
 }
@@ -412,13 +487,76 @@ cudaError_t dm_launch_backtrack(const DmGeom& g, const dm_pyramid& py, const DmB
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int grid = nsm * (py.tune.bt_mult > 0 ? py.tune.bt_mult : 8);
     if (rect) {
-        launch_steps<true>(a, grid, st);
+        launch_steps<BT_RECT>(a, grid, st);
         dm_count_launches(2 * g.L - 1);
         return cudaGetLastError();
     }
-    launch_steps<false>(a, grid, st);
+    launch_steps<BT_EXACT>(a, grid, st);
     k_reciprocal<<<1, 1024, 0, st>>>(a, out, capacity, d_count);
     dm_count_launches(2 * g.L);
+    return cudaGetLastError();
+}
+
+cudaError_t dm_launch_backtrack_star(const DmGeom& g, const dm_pyramid& py, const DmBtLayout& bl, char* ws, float lam,
+                                     dm_match_t* out, int capacity, int* d_count, cudaStream_t st) {
+    BtArgs a;
+    memset(&a, 0, sizeof(a));
+    a.g = g;
+    a.proto_of = py.proto_of;
+    a.n0_maps = py.n0_maps;
+    for (int l = 0; l <= g.L; l++) a.valid[l] = py.valid[l];
+    for (int l = 0; l < g.L; l++) {
+        a.pooled[l] = py.pooled[l];
+        a.amax[l] = py.amax[l];
+    }
+    a.top = py.top;
+    for (int l = 1; l <= g.L; l++) {
+        a.table[l] = reinterpret_cast<unsigned long long*>(ws + bl.table[l]);
+        a.capmax[l] = (unsigned int)bl.cap[l];
+    }
+    a.bestP = reinterpret_cast<unsigned long long*>(ws + bl.bestP);
+    a.bestQ = reinterpret_cast<unsigned long long*>(ws + bl.bestQ);
+    a.hdr = reinterpret_cast<DmWsHeader*>(ws + bl.header);
+
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(&a.hdr->status, 0, sizeof(int), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(a.hdr->count, 0, sizeof(a.hdr->count) + sizeof(a.hdr->cap) + sizeof(a.hdr->entries), st)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaMemsetAsync(a.bestP, 0, sizeof(unsigned long long) * g.npatch(0), st)) != cudaSuccess) return e;
+    const size_t ncell = (size_t)((g.W2 + 3) / 4) * ((g.H2 + 3) / 4);
+    if ((e = cudaMemsetAsync(a.bestQ, 0, sizeof(unsigned long long) * ncell, st)) != cudaSuccess) return e;
+
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = nsm * (py.tune.bt_mult > 0 ? py.tune.bt_mult : 8);
+    auto items = [&](int l) -> long long {
+        return (long long)g.npatch(l) * ((g.dw[l] + ST_W - 1) / ST_W) * ((g.dh[l] + ST_H - 1) / ST_H);
+    };
+    auto entries = [&](int l, bool insert) {
+        const long long n = items(l);
+        const unsigned gb = (unsigned)(n < 8LL * nsm ? n : 8LL * nsm);
+        if (py.compensated) {
+            if (insert) k_star_entries<true, true><<<gb, 256, 0, st>>>(a, l, lam, n);
+            else k_star_entries<true, false><<<gb, 256, 0, st>>>(a, l, lam, n);
+        } else {
+            if (insert) k_star_entries<false, true><<<gb, 256, 0, st>>>(a, l, lam, n);
+            else k_star_entries<false, false><<<gb, 256, 0, st>>>(a, l, lam, n);
+        }
+    };
+    for (int l = 1; l <= g.L; l++) entries(l, false);
+    k_star_prepare<<<grid, BT_BLOCK, 0, st>>>(a, g.L);
+    entries(g.L, true);
+    for (int l = g.L; l >= 1; l--) {
+        if (l - 1 >= 1) {
+            k_star_prepare<<<grid, BT_BLOCK, 0, st>>>(a, l - 1);
+            entries(l - 1, true);
+        }
+        k_bt_expand<BT_STAR><<<grid, BT_BLOCK, 0, st>>>(a, l);
+    }
+    k_reciprocal<<<1, 1024, 0, st>>>(a, out, capacity, d_count);
+    dm_count_launches(4 * g.L + 1);
     return cudaGetLastError();
 }
 

@@ -48,73 +48,11 @@ __global__ void k_fill_u8(unsigned char* p, int n, unsigned char val) {
     if (i < n) p[i] = val;
 }
 
-struct Kids {
-    const float* base[4];
-    int n;
-};
-
 // Three-input maximum (one PTX max with three operands).
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
     float r;
     asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
     return r;
-}
-
-// One step of the compensated child sum (Knuth's TwoSum gives the same bits
-// for any operands): for non-negative operands, which every map value is,
-// Dekker's Fast2Sum on (max, min) is exact, since the first operand is the
-// larger, with one operation fewer.
-__device__ __forceinline__ void fast_two_sum_add(float& s, float& comp, float v) {
-    const float hi = fmaxf(s, v), lo = fminf(s, v);
-    const float t = __fadd_rn(hi, lo);
-    const float err = __fsub_rn(lo, __fsub_rn(t, hi));
-    s = t;
-    comp = __fadd_rn(comp, err);
-}
-
-// Child sum step: compensated or plain.  The first existing child starts the
-// sum (0 + v = v exactly, the same as starting from zero).
-template <bool COMP>
-__device__ __forceinline__ void child_add(float& s, float& comp, float v) {
-    if (COMP) fast_two_sum_add(s, comp, v);
-    else s = __fadd_rn(s, v);
-}
-
-template <bool COMP>
-__device__ __forceinline__ float child_mean(const Kids& k, int qx, int qy, int mw, int mh, int pitch) {
-    float s = 0.0f, comp = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 4; i++) {
-        if (k.base[i] == nullptr) continue;
-        int ox = (i >= 2) ? 1 : -1, oy = (i & 1) ? 1 : -1;
-        int rx = qx + ox, ry = qy + oy;
-        float v = 0.0f;
-        if (rx >= 0 && ry >= 0 && rx < mw && ry < mh) v = __ldg(k.base[i] + (long long)ry * pitch + rx);
-        child_add<COMP>(s, comp, v);
-    }
-    return __fdiv_rn(__fadd_rn(s, comp), (float)k.n);
-}
-
-
-// (proto_of: the map of atomic child c is map proto_of[c], clamped to
-// [0, n_maps) -- approximate form, l = 1)
-__device__ __forceinline__ bool load_kids(const DmGeom& g, int l, int p, const unsigned char* __restrict__ vprev,
-                                          const float* __restrict__ prev, Kids& k, const int* __restrict__ proto_of,
-                                          int n_maps) {
-    int ix = p % g.Lx, iy = p / g.Lx;
-    long long cs = g.psize(l);     // child pooled map size (domain of level l, padded rows)
-    k.n = 0;
-#pragma unroll
-    for (int i = 0; i < 4; i++) {
-        int c = dm_child(g, l, ix, iy, i);
-        if (c >= 0 && vprev[c]) {
-            k.base[i] = prev + (long long)(proto_of ? min(max(proto_of[c], 0), n_maps - 1) : c) * cs;
-            k.n++;
-        } else {
-            k.base[i] = nullptr;
-        }
-    }
-    return k.n > 0;
 }
 
 constexpr int TW = 32;                           // pooled columns per CTA tile (one per lane)

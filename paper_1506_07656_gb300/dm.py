@@ -84,6 +84,11 @@ _SIGS = {
     "dm_correlate_pyramid_approx": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int,
                                               C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t,
                                               C.POINTER(C.c_void_p), C.c_void_p]),
+    "dm_star_workspace_bytes": (C.c_int, [C.c_void_p] + [C.c_int] * 4 + [C.POINTER(C.c_size_t)] * 2),
+    "dm_backtrack_star": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_int, C.c_void_p,
+                                    C.c_void_p]),
+    "dm_match_star": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                                C.c_size_t, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "dm_invariant_workspace_bytes": (C.c_int, [C.c_void_p] + [C.c_int] * 4 + [C.POINTER(C.c_size_t)]),
     "dm_match_invariant": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int,
                                      C.c_void_p, C.c_size_t, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
@@ -280,6 +285,28 @@ def dm_match(ctx, d_img1, d_img2, d_ws, d_out, d_count, stream=None):
     _check(ctx, st, "dm_match")
 
 
+def dm_star_workspace_bytes(ctx, W1, H1, W2, H2) -> dict:
+    b, m = C.c_size_t(), C.c_size_t()
+    _check(ctx, load().dm_star_workspace_bytes(ctx, W1, H1, W2, H2, C.byref(b), C.byref(m)), "dm_star_workspace_bytes")
+    return {"backtrack": b.value, "match": m.value}
+
+
+def dm_backtrack_star(ctx, pyr, d_ws, d_out, d_count, stream=None):
+    cap = d_out.numel() * d_out.element_size() // MATCH_BYTES
+    st = load().dm_backtrack_star(ctx, pyr, _dptr(d_ws), d_ws.numel() * d_ws.element_size(), _dptr(d_out), cap,
+                                  _dptr(d_count), _stream_ptr(stream))
+    _check(ctx, st, "dm_backtrack_star")
+
+
+def dm_match_star(ctx, d_img1, d_img2, d_ws, d_out, d_count, stream=None):
+    H1, W1 = d_img1.shape
+    H2, W2 = d_img2.shape
+    cap = d_out.numel() * d_out.element_size() // MATCH_BYTES
+    st = load().dm_match_star(ctx, _dptr(d_img1), W1, H1, _dptr(d_img2), W2, H2, _dptr(d_ws),
+                              d_ws.numel() * d_ws.element_size(), _dptr(d_out), cap, _dptr(d_count), _stream_ptr(stream))
+    _check(ctx, st, "dm_match_star")
+
+
 def dm_invariant_workspace_bytes(ctx, W1, H1, W2, H2) -> int:
     b = C.c_size_t()
     _check(ctx, load().dm_invariant_workspace_bytes(ctx, W1, H1, W2, H2, C.byref(b)), "dm_invariant_workspace_bytes")
@@ -456,6 +483,26 @@ class Context:
         out = torch.empty((max(n0, 1), 5), dtype=torch.float32, device=dev)
         cnt = torch.zeros(1, dtype=torch.int32, device=dev)
         dm_match(self.ctx, i1, i2, ws, out, cnt, stream)
+        n = int(cnt.item())
+        return out[:n]
+
+    def match_star(self, img1, img2, stream=None):
+        """DM* matches (local-maximum entry points, start + end scores) as a
+        float32 tensor [n][5] on the device."""
+        torch = self.torch
+        dev = f"cuda:{self.device}"
+        i1 = torch.as_tensor(img1, dtype=torch.float32, device=dev).contiguous()
+        i2 = torch.as_tensor(img2, dtype=torch.float32, device=dev).contiguous()
+        H1, W1 = i1.shape
+        H2, W2 = i2.shape
+        key = ("star", W1, H1, W2, H2)
+        if key not in self._ws:
+            nbytes = dm_star_workspace_bytes(self.ctx, W1, H1, W2, H2)["match"]
+            self._ws[key] = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=dev)
+        n0 = dm_geometry(W1, H1, W2, H2)["n_patch0"]
+        out = torch.empty((max(n0, 1), 5), dtype=torch.float32, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+        dm_match_star(self.ctx, i1, i2, self._ws[key], out, cnt, stream)
         n = int(cnt.item())
         return out[:n]
 
