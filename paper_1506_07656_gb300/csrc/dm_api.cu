@@ -320,6 +320,11 @@ void dm_bt_layout(const DmGeom& g, DmBtLayout* o, bool star) {
     }
     o->bestP = off; off = dm_align(off + (size_t)g.npatch(0) * 8);
     o->bestQ = off; off = dm_align(off + (size_t)((g.W2 + 3) / 4) * ((g.H2 + 3) / 4) * 8);
+    if (star)
+        for (int l = 1; l <= g.L; l++) {     // local maxima: at most one per 2x2 block of the domain
+            o->elcap[l] = (size_t)g.npatch(l) * (size_t)g.dsize(l + 1);
+            o->elist[l] = off; off = dm_align(off + o->elcap[l] * 8);
+        }
     o->bytes = off;
 }
 

@@ -210,6 +210,8 @@ struct DmBtLayout {
     size_t table[DM_MAXL + 1];    // u64 merge tables, levels 1..L-1
     size_t cap[DM_MAXL + 1];      // max slots per level
     size_t bestP, bestQ;          // u64 keys
+    size_t elist[DM_MAXL + 1];    // DM*: entry points found per level, u64 (key << 32 | score)
+    size_t elcap[DM_MAXL + 1];    // DM*: their capacity (entries)
     size_t bytes;
 };
 

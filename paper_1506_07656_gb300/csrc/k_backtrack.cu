@@ -48,6 +48,8 @@ struct BtArgs {
     const float* top;
     unsigned long long* table[DM_MAXL + 1];
     unsigned int capmax[DM_MAXL + 1];
+    unsigned long long* elist[DM_MAXL + 1];   // DM*: entry points found per level
+    unsigned long long elcap[DM_MAXL + 1];
     unsigned long long* bestP;
     unsigned long long* bestQ;
     DmWsHeader* hdr;
@@ -384,51 +386,67 @@ __global__ void __launch_bounds__(1024) k_reciprocal(BtArgs a, dm_match_t* __res
 // of the existing patches.  q is one iff A(q) > 0 and, over its in-domain
 // 8-neighbours r, A(q) > A(r) for r before q in row-major order and
 // A(q) >= A(r) for r after it, A being the unrectified average of the level
-// pass (same arithmetic, hence the same order as C_l = A^lambda).  A CTA takes
-// a 32 x 8 tile of positions of one patch and forms the averages of the tile
-// and its one-position halo in shared memory.  COUNT pass: the number of
-// entries per level (sizes the tables); INSERT pass: tuple (l, p, q) with
-// score C_l(p, q) merged into the level-l table.
-constexpr int ST_W = 32, ST_H = 8;
+// pass (same arithmetic, hence the same order as C_l = A^lambda).
+//
+// One warp streams down a strip of 30 columns of one patch's map (lane j
+// holds column x0 - 1 + j, so lanes 0 and 31 are the halo), ST_ROWS rows per
+// work item: each step forms one new row of averages (4 coalesced child loads
+// per lane) and tests the row above it against the three rows held in
+// registers, horizontal neighbours by shuffles.  No shared memory and no
+// block barrier.  Each entry (l, p, q) with score C_l(p, q) is appended to
+// the level's list (hdr->entries[l] counts them; the merge tables are sized
+// from the counts before anything is inserted).
+constexpr int ST_COLS = 30, ST_ROWS = 32;
 
-template <bool COMP, bool INSERT>
+template <bool COMP>
 __global__ void __launch_bounds__(256) k_star_entries(BtArgs a, int l, float lam, long long n_items) {
-    __shared__ float A[ST_H + 2][ST_W + 2];
     const DmGeom& g = a.g;
-    const int mw = g.dw[l], mh = g.dh[l];
-    const int tiles_x = (mw + ST_W - 1) / ST_W, tiles = tiles_x * ((mh + ST_H - 1) / ST_H);
-    const unsigned int cap = INSERT ? a.hdr->cap[l] : 0u;
+    const int mw = g.dw[l], mh = g.dh[l], pitch = g.pitch(l);
+    const int strips = (mw + ST_COLS - 1) / ST_COLS, tiles = strips * ((mh + ST_ROWS - 1) / ST_ROWS);
     const unsigned int ds = (unsigned int)g.dsize(l);
-    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
-    unsigned int found = 0;
-    for (long long it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long it = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < n_items; it += warps) {
         const int p = (int)(it / tiles), t = (int)(it % tiles);
-        if (!a.valid[l][p]) continue;                  // the same for the whole CTA
+        if (!a.valid[l][p]) continue;                  // the same for the whole warp
         Kids k;
         load_kids(g, l, p, a.valid[l - 1], a.pooled[l - 1], k, l == 1 ? a.proto_of : nullptr, a.n0_maps);
-        const int x0 = (t % tiles_x) * ST_W, y0 = (t / tiles_x) * ST_H;
-        for (int i = threadIdx.x; i < (ST_H + 2) * (ST_W + 2); i += blockDim.x) {
-            const int hy = i / (ST_W + 2), hx = i % (ST_W + 2);
-            const int qx = x0 - 1 + hx, qy = y0 - 1 + hy;
-            A[hy][hx] = (qx >= 0 && qy >= 0 && qx < mw && qy < mh) ? child_mean<COMP>(k, qx, qy, mw, mh, g.pitch(l))
-                                                                   : -INFINITY;
-        }
-        __syncthreads();
-        const int qx = x0 + lx, qy = y0 + ly;
-        if (qx < mw && qy < mh) {
-            const float v = A[ly + 1][lx + 1];
-            const bool m = v > 0.0f && v > A[ly][lx] && v > A[ly][lx + 1] && v > A[ly][lx + 2] && v > A[ly + 1][lx] &&
-                           v >= A[ly + 1][lx + 2] && v >= A[ly + 2][lx] && v >= A[ly + 2][lx + 1] && v >= A[ly + 2][lx + 2];
+        const int x = (t % strips) * ST_COLS - 1 + lane;
+        const int y0 = (t / strips) * ST_ROWS;
+        const int y1 = min(y0 + ST_ROWS, mh);          // rows y0 .. y1-1 are tested
+        const bool col_in = x >= 0 && x < mw;
+        auto avg = [&](int y) -> float {
+            return (col_in && y >= 0 && y < mh) ? child_mean<COMP>(k, x, y, mw, mh, pitch) : -INFINITY;
+        };
+        float up = avg(y0 - 1), mid = avg(y0);
+        for (int y = y0; y < y1; y++) {
+            const float dn = avg(y + 1);
+            const float ul = __shfl_up_sync(0xffffffffu, up, 1), ur = __shfl_down_sync(0xffffffffu, up, 1);
+            const float ml = __shfl_up_sync(0xffffffffu, mid, 1), mr = __shfl_down_sync(0xffffffffu, mid, 1);
+            const float dl = __shfl_up_sync(0xffffffffu, dn, 1), dr = __shfl_down_sync(0xffffffffu, dn, 1);
+            const float v = mid;
+            const bool m = lane >= 1 && lane <= ST_COLS && col_in && v > 0.0f && v > ul && v > up && v > ur && v > ml &&
+                           v >= mr && v >= dl && v >= dn && v >= dr;
             if (m) {
-                if (INSERT) ht_insert(a, l, cap, (unsigned int)p * ds + (unsigned int)(qy * mw + qx), ps_term(dm_powf(v, lam)));
-                else found++;
+                const unsigned int pos = warp_agg_inc(&a.hdr->entries[l]);
+                const unsigned int key = (unsigned int)p * ds + (unsigned int)(y * mw + x);
+                if (pos < a.elcap[l]) a.elist[l][pos] = ((unsigned long long)key << 32) | ps_term(dm_powf(v, lam));
+                else atomicOr(&a.hdr->status, DM_DEV_FRONTIER_OVERFLOW);
             }
+            up = mid;
+            mid = dn;
         }
-        __syncthreads();
     }
-    if (!INSERT) {
-        const unsigned int tot = __reduce_add_sync(0xffffffffu, found);
-        if (lx == 0 && tot) atomicAdd(&a.hdr->entries[l], tot);
+}
+
+// DM*: the level-l entry points merged into the level-l table.
+__global__ void k_star_insert(BtArgs a, int l) {
+    const unsigned int cap = a.hdr->cap[l];
+    const unsigned long long n = min((unsigned long long)a.hdr->entries[l], a.elcap[l]);
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long e = a.elist[l][i];
+        ht_insert(a, l, cap, (unsigned int)(e >> 32), (unsigned int)e);
     }
 }
 
@@ -513,6 +531,8 @@ cudaError_t dm_launch_backtrack_star(const DmGeom& g, const dm_pyramid& py, cons
     for (int l = 1; l <= g.L; l++) {
         a.table[l] = reinterpret_cast<unsigned long long*>(ws + bl.table[l]);
         a.capmax[l] = (unsigned int)bl.cap[l];
+        a.elist[l] = reinterpret_cast<unsigned long long*>(ws + bl.elist[l]);
+        a.elcap[l] = bl.elcap[l];
     }
     a.bestP = reinterpret_cast<unsigned long long*>(ws + bl.bestP);
     a.bestQ = reinterpret_cast<unsigned long long*>(ws + bl.bestQ);
@@ -532,26 +552,21 @@ cudaError_t dm_launch_backtrack_star(const DmGeom& g, const dm_pyramid& py, cons
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int grid = nsm * (py.tune.bt_mult > 0 ? py.tune.bt_mult : 8);
     auto items = [&](int l) -> long long {
-        return (long long)g.npatch(l) * ((g.dw[l] + ST_W - 1) / ST_W) * ((g.dh[l] + ST_H - 1) / ST_H);
+        return (long long)g.npatch(l) * ((g.dw[l] + ST_COLS - 1) / ST_COLS) * ((g.dh[l] + ST_ROWS - 1) / ST_ROWS);
     };
-    auto entries = [&](int l, bool insert) {
-        const long long n = items(l);
-        const unsigned gb = (unsigned)(n < 8LL * nsm ? n : 8LL * nsm);
-        if (py.compensated) {
-            if (insert) k_star_entries<true, true><<<gb, 256, 0, st>>>(a, l, lam, n);
-            else k_star_entries<true, false><<<gb, 256, 0, st>>>(a, l, lam, n);
-        } else {
-            if (insert) k_star_entries<false, true><<<gb, 256, 0, st>>>(a, l, lam, n);
-            else k_star_entries<false, false><<<gb, 256, 0, st>>>(a, l, lam, n);
-        }
-    };
-    for (int l = 1; l <= g.L; l++) entries(l, false);
+    for (int l = 1; l <= g.L; l++) {
+        const long long n = items(l);                   // one warp per item, 8 per CTA
+        const long long nb = (n + 7) / 8;
+        const unsigned gb = (unsigned)(nb < 8LL * nsm ? nb : 8LL * nsm);
+        if (py.compensated) k_star_entries<true><<<gb, 256, 0, st>>>(a, l, lam, n);
+        else k_star_entries<false><<<gb, 256, 0, st>>>(a, l, lam, n);
+    }
     k_star_prepare<<<grid, BT_BLOCK, 0, st>>>(a, g.L);
-    entries(g.L, true);
+    k_star_insert<<<grid, BT_BLOCK, 0, st>>>(a, g.L);
     for (int l = g.L; l >= 1; l--) {
         if (l - 1 >= 1) {
             k_star_prepare<<<grid, BT_BLOCK, 0, st>>>(a, l - 1);
-            entries(l - 1, true);
+            k_star_insert<<<grid, BT_BLOCK, 0, st>>>(a, l - 1);
         }
         k_bt_expand<BT_STAR><<<grid, BT_BLOCK, 0, st>>>(a, l);
     }
