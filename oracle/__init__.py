@@ -40,6 +40,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "dm_oracle.c")
+DF_SRC = os.path.join(HERE, "df_oracle.c")      # included by dm_oracle.c
 
 DEFAULT_CFG = dict(nu1=1.0, nu2=1.0, nu3=1.0, slope=0.2, mu=0.3, image_scale=255.0, lam=1.4)
 
@@ -52,7 +53,8 @@ def build(force: bool = False) -> None:
     """Compile both oracle builds with gcc (no fp contraction; OpenMP)."""
     for prec, flag in (("f64", "0"), ("f32", "1")):
         out = _lib_path(prec)
-        if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(SRC):
+        newest = max(os.path.getmtime(SRC), os.path.getmtime(DF_SRC))
+        if not force and os.path.exists(out) and os.path.getmtime(out) >= newest:
             continue
         cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
                f"-DORC_F32={flag}", SRC, "-o", out, "-lm"]
@@ -665,6 +667,98 @@ def dmstar_match(img1: np.ndarray, img2: np.ndarray, prec: str = "f64", entries:
     keys = np.array(list(leaves.keys()), dtype=np.int64)
     S = np.array(list(leaves.values()), dtype=np.float64)
     return _reciprocal_union(keys[:, 0], keys[:, 1] * g.W2 + keys[:, 2], S, g.W2, g.H2, g.P0x, prec)
+
+
+# --------------------------------------------------------------------------- #
+# DeepFlow (Sec. 4.3): variational refinement with the matches as a term      #
+# --------------------------------------------------------------------------- #
+DF_DEFAULT = dict(sigma=0.5, eta=0.95, gamma=0.8, delta=0.0, beta=300.0, b=0.6, kappa=5.0, zeta=0.1, eps=0.001,
+                  sigma_m=50.0, omega=1.6, image_scale=255.0, n_fixed=5, n_sor=25, min_size=16)
+_DF_KEYS = ("sigma", "eta", "gamma", "delta", "beta", "b", "kappa", "zeta", "eps", "sigma_m", "omega",
+            "image_scale", "n_fixed", "n_sor", "min_size")
+
+
+def df_params(**kw) -> np.ndarray:
+    """The parameter vector of the DeepFlow oracle (defaults: the paper's
+    values, Sec. 4.3 and Sec. 5.4, plus the readings' omega and min_size)."""
+    bad = set(kw) - set(DF_DEFAULT)
+    if bad:
+        raise KeyError(f"unknown DeepFlow parameters {sorted(bad)}")
+    c = dict(DF_DEFAULT, **kw)
+    return np.array([float(c[k]) for k in _DF_KEYS], dtype=np.float64)
+
+
+def df_levels(W: int, H: int, **kw):
+    """Sizes of the coarse-to-fine pyramid, finest first."""
+    ws = np.zeros(256, np.int32)
+    hs = np.zeros(256, np.int32)
+    lib = _lib("f64")
+    lib.orc_df_levels.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+    prm = df_params(**kw)
+    n = lib.orc_df_levels(W, H, _ptr(prm), _ptr(ws), _ptr(hs), 256)
+    return list(zip(ws[:n].tolist(), hs[:n].tolist()))
+
+
+def df_resample(src: np.ndarray, Wd: int, Hd: int, s: float, down: bool, mul: float = 1.0, prec: str = "f64"):
+    dt = _dtype(prec)
+    src = np.ascontiguousarray(src, dtype=dt)
+    dst = np.zeros((Hd, Wd), dtype=dt)
+    lib = _lib(prec)
+    lib.orc_df_resample.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int,
+                                    C.c_double]
+    lib.orc_df_resample(_ptr(src), src.shape[1], src.shape[0], _ptr(dst), Wd, Hd, float(s), int(bool(down)),
+                        float(mul))
+    return dst
+
+
+def df_sor(A: np.ndarray, ps: np.ndarray, u: np.ndarray, v: np.ndarray, du: np.ndarray, dv: np.ndarray,
+           omega: float, n_sor: int, prec: str = "f64"):
+    """n_sor red-black SOR sweeps of one fixed-point step's linear system;
+    A [h][w][5] = (A11, A12, A22, b1, b2), ps [h][w] smoothness weights.
+    Returns (du, dv)."""
+    dt = _dtype(prec)
+    A, ps, u, v = (np.ascontiguousarray(a, dtype=dt) for a in (A, ps, u, v))
+    du = np.array(du, dtype=dt)
+    dv = np.array(dv, dtype=dt)
+    h, w = ps.shape
+    lib = _lib(prec)
+    lib.orc_df_sor.argtypes = [C.c_void_p] * 6 + [C.c_int, C.c_int, C.c_double, C.c_int]
+    lib.orc_df_sor(_ptr(A), _ptr(ps), _ptr(u), _ptr(v), _ptr(du), _ptr(dv), w, h, float(omega), int(n_sor))
+    return du, dv
+
+
+def df_phi(I1: np.ndarray, I2: np.ndarray, x1: int, y1: int, x2: int, y2: int, sigma_m: float = 50.0,
+           prec: str = "f64") -> float:
+    dt = _dtype(prec)
+    I1 = np.ascontiguousarray(I1, dtype=dt)
+    I2 = np.ascontiguousarray(I2, dtype=dt)
+    lib = _lib(prec)
+    lib.orc_df_phi.restype = C.c_double
+    lib.orc_df_phi.argtypes = [C.c_void_p, C.c_void_p] + [C.c_int] * 8 + [C.c_double]
+    return lib.orc_df_phi(_ptr(I1), _ptr(I2), I1.shape[1], I1.shape[0], I2.shape[1], I2.shape[0], x1, y1, x2, y2,
+                          float(sigma_m))
+
+
+def deepflow(img1: np.ndarray, img2: np.ndarray, matches: np.ndarray | None = None, prec: str = "f64", **kw):
+    """DeepFlow (Sec. 4.3) of two images in [0, 1] (H x W) with DeepMatching
+    matches rows (x1, y1, x2, y2, score) (may be empty).  Returns (u, v)."""
+    dt = _dtype(prec)
+    i1 = np.ascontiguousarray(img1, dtype=np.float32)
+    i2 = np.ascontiguousarray(img2, dtype=np.float32)
+    if i1.shape != i2.shape:
+        raise ValueError("DeepFlow needs two images of the same size")
+    H, W = i1.shape
+    m = np.ascontiguousarray(np.zeros((0, 5)) if matches is None else matches, dtype=np.float32).reshape(-1, 5)
+    u = np.zeros((H, W), dtype=dt)
+    v = np.zeros((H, W), dtype=dt)
+    prm = df_params(**kw)
+    lib = _lib(prec)
+    lib.orc_deepflow.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
+                                 C.c_void_p, C.c_void_p]
+    rc = lib.orc_deepflow(_ptr(i1), _ptr(i2), W, H, _ptr(m), len(m), _ptr(prm), _ptr(u), _ptr(v))
+    if rc != 0:
+        raise ValueError("DeepFlow oracle failed")
+    return u, v
 
 
 def loss_grad(d1: np.ndarray, d2: np.ndarray, prec: str = "f64", lam: float = DEFAULT_CFG["lam"]):

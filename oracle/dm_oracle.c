@@ -6,7 +6,8 @@
  * Matching"), written from the paper: pixel descriptors (Sec. 3.2), bottom
  * level correlation (Eq. 3-4), the bottom-up pyramid (Eq. 5-12 and
  * Algorithm 1, boundary rule of Sec. 3.2), top-down backtracking with merging
- * (Eq. 13-15) and reciprocal verification (Eq. 16).
+ * (Eq. 13-15) and reciprocal verification (Eq. 16); the DM* backtracking
+ * variant's level maps (Sec. 5.3); and DeepFlow (Sec. 4.3, df_oracle.c).
  *
  * Only the test-suite, the smoke check and the CPU-baseline leg of the bench
  * may load this file's library.  It shares no source with the CUDA path.
@@ -26,28 +27,27 @@
  *                 to FP32 once at the end).  It is the bit-exact target of
  *                 the FP32 GPU path.
  *
- * Readings of the paper where it is silent or ambiguous (numbered as in the
- * design notes):
- *   c1  Gaussian "radius" nu = standard deviation; taps on [-ceil(3nu), ceil(3nu)],
+ * Readings of the paper where it is silent or ambiguous:
+ *   - Gaussian "radius" nu = standard deviation; taps on [-ceil(3nu), ceil(3nu)],
  *       renormalised to sum 1; replicate border; nu = 0 is the identity.
- *   c2  gradient = central differences, replicate border.
- *   c3  images come in [0,1] and are multiplied by image_scale (255).
- *   c4  8 orientations k*pi/4, k = 0..7; channel = max(0, <g, dir_k>).
- *   c5  mu is appended first, then the 9-vector is L2-normalised.
- *   c6  image-2 window at pixel t covers [t-2, t+1]^2; zero descriptor outside.
- *   c7  atomic centres 4k+2 <= W-1.
- *   c8  a level-N patch exists if at least one child exists; average over valid
+ *   - gradient = central differences, replicate border.
+ *   - images come in [0,1] and are multiplied by image_scale (255).
+ *   - 8 orientations k*pi/4, k = 0..7; channel = max(0, <g, dir_k>).
+ *   - mu is appended first, then the 9-vector is L2-normalised.
+ *   - image-2 window at pixel t covers [t-2, t+1]^2; zero descriptor outside.
+ *   - atomic centres 4k+2 <= W-1.
+ *   - a level-N patch exists if at least one child exists; average over valid
  *       children (weight 1/n_valid).
- *   c9  Theta_i has radius N/8 (a 3x3 max on the child's subsampled grid).
- *   c10 child i is sampled at q + o_i (sign of Eq. 6 and Eq. 13).
- *   c11 map domain at level l is ceil(W'/2^l) x ceil(H'/2^l); pooling only over
+ *   - Theta_i has radius N/8 (a 3x3 max on the child's subsampled grid).
+ *   - child i is sampled at q + o_i (sign of Eq. 6 and Eq. 13).
+ *   - map domain at level l is ceil(W'/2^l) x ceil(H'/2^l); pooling only over
  *       in-domain positions; a child sample outside the domain contributes 0.
- *   c13 argmax = first strict maximum, scan order m_y = -1..1 then m_x = -1..1;
+ *   - argmax = first strict maximum, scan order m_y = -1..1 then m_x = -1..1;
  *       ties in BestAt/BestAt': higher score, then lower index.
- *   c14 L = min{l : 4*2^l >= max(W,H)} (image 1); entries = all top positions.
- *   c15 path score = top value + pooled values along the path, summed top-down
+ *   - L = min{l : 4*2^l >= max(W,H)} (image 1); entries = all top positions.
+ *   - path score = top value + pooled values along the path, summed top-down
  *       (FP32 mirror: exact fixed-point sum, see the path-score helpers).
- *   c17 BestAt / BestAt' over aligned 4x4 cells (the atomic patch in I, the cell
+ *   - BestAt / BestAt' over aligned 4x4 cells (the atomic patch in I, the cell
  *       floor(t/4) in I'); a tuple survives iff it is the best of both.
  */
 #include <math.h>
@@ -1057,3 +1057,6 @@ int orc_loss_grad(const real* d1, int W1, int H1, const real* d2, int W2, int H2
     }
     return 0;
 }
+
+/* DeepFlow (Sec. 4.3): the variational refinement that consumes the matches. */
+#include "df_oracle.c"
