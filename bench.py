@@ -53,6 +53,7 @@ def _args():
     ap.add_argument("--batch-pairs", type=int, default=8, help="pairs per step of the headline batched measurement")
     ap.add_argument("--no-approx", action="store_true", help="skip the approximate-form (Sec. 4.1) measurement")
     ap.add_argument("--no-star", action="store_true", help="skip the DM* (Sec. 5.3) measurement")
+    ap.add_argument("--no-deepflow", action="store_true", help="skip the DeepFlow (Sec. 4.3) measurement")
     ap.add_argument("--no-invariant", action="store_true",
                     help="skip the scale and rotation invariant form (Sec. 4.2) measurement")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
@@ -385,6 +386,51 @@ def _measure_star(dm, torch, a, pair, stream, prec="bf16"):
             "same_match_as_new_form": float(np.mean(same)) if same else None}
 
 
+def _measure_deepflow(dm, torch, a, pair, stream):
+    """DeepFlow (Sec. 4.3) on the bench pair with the BF16 DeepMatching matches
+    of the same pair as its matching term (passed on the device, count read on
+    the device).  One step = one dm_deepflow call (paper parameters: eta 0.95,
+    5 fixed-point x 25 SOR iterations per level); K steps timed with CUDA
+    events.  Also: the mean end-point distance between the flow and the
+    matches it was given, at the matched pixels."""
+    import numpy as np
+    W, H = a.width, a.height
+    ctx = dm.Context(dm.DM_BF16)
+    try:
+        i1, i2 = torch.from_numpy(pair.img1).cuda(), torch.from_numpy(pair.img2).cuda()
+        P0 = dm.dm_geometry(W, H, W, H)["n_patch0"]
+        out = torch.zeros((P0, 5), dtype=torch.float32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+        dm.dm_match(ctx.ctx, i1, i2, ctx.workspace("match", W, H, W, H), out, cnt, stream)
+        prm = dm.dm_flow_params()
+        ws = torch.empty(dm.dm_deepflow_workspace_bytes(ctx.ctx, W, H, P0, prm), dtype=torch.uint8, device="cuda")
+        u = torch.empty((H, W), dtype=torch.float32, device="cuda")
+        v = torch.empty_like(u)
+        launches0 = dm.dm_timing_read(ctx.ctx)[2]
+        dm.dm_deepflow(ctx.ctx, i1, i2, out, cnt, u, v, ws, prm, stream)
+        launches = dm.dm_timing_read(ctx.ctx)[2] - launches0
+        for _ in range(max(a.warmup - 1, 1)):
+            dm.dm_deepflow(ctx.ctx, i1, i2, out, cnt, u, v, ws, prm, stream)
+        torch.cuda.synchronize()
+        steps = max(min(a.steps, 10), 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            dm.dm_deepflow(ctx.ctx, i1, i2, out, cnt, u, v, ws, prm, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        m = out[:int(cnt.item())].cpu().numpy()
+        un, vn = u.cpu().numpy(), v.cpu().numpy()
+    finally:
+        ctx.close()
+    xs, ys = m[:, 0].astype(int), m[:, 1].astype(int)
+    epe = np.hypot(un[ys, xs] - (m[:, 2] - m[:, 0]), vn[ys, xs] - (m[:, 3] - m[:, 1]))
+    return {"workload": f"{W}x{H}, BF16 DeepMatching matches as the matching term", "precision": "fp32",
+            "pairs_per_s": 1000.0 / ms, "ms_per_step": ms, "kernel_launches_per_step": int(launches),
+            "matches": int(len(m)), "median_distance_to_matches_px": float(np.median(epe)) if len(epe) else None}
+
+
 def _measure_invariant(dm, torch, a, stream, W=512, H=224, prec="bf16"):
     """Scale and rotation invariant form (Sec. 4.2, Algorithm 2): 72 runs of the
     method (9 scales x 8 rotations) on image 1 against image 2 = image 1 turned
@@ -683,6 +729,10 @@ def run_ours(a):
     if not a.no_star and world == 1:
         star = _measure_star(dm, torch, a, pair, stream)
         torch.cuda.empty_cache()
+    deepflow = None
+    if not a.no_deepflow and world == 1:
+        deepflow = _measure_deepflow(dm, torch, a, pair, stream)
+        torch.cuda.empty_cache()
     invariant = None
     if not a.no_invariant and world == 1:
         invariant = _measure_invariant(dm, torch, a, stream)
@@ -743,6 +793,7 @@ def run_ours(a):
             "batched": batch,
             "approx": approx,
             "star": star,
+            "deepflow": deepflow,
             "invariant": invariant,
             "stages_ms": r["stages"],
             "cpu_baseline": cpu,

@@ -215,6 +215,35 @@ dm_status dm_match(dm_ctx* ctx, const float* d_img1, int W1, int H1, const float
 dm_status dm_match_host(dm_ctx* ctx, const float* h_img1, int W1, int H1, const float* h_img2, int W2, int H2,
                         void* d_ws, size_t ws_bytes, dm_match_t* h_out, int capacity, int* h_count, void* stream);
 
+/* DeepFlow (Sec. 4.3): dense flow (u, v) from I1 to I2 (same size W x H,
+ * values in [0,1]) refining the matches with a variational energy: data term
+ * delta Psi(theta0 (grad3 I . w)^2) + gamma Psi(normalised gradient
+ * constancy), smoothness alpha(x) Psi(|grad u|^2 + |grad v|^2) with alpha =
+ * exp(-kappa |grad I1|), matching term beta_k c phi Psi(|w - w'|^2) with phi
+ * from the structure tensor and the appearance difference at each match,
+ * Psi(s^2) = sqrt(s^2 + eps^2); coarse to fine (factor eta, levels down to a
+ * side of min_size) with warping, n_fixed fixed-point steps per level of
+ * n_sor red-black SOR sweeps each (relaxation omega).  Defaults
+ * (dm_flow_params_default) are the paper's: sigma 0.5, eta 0.95, gamma 0.8,
+ * delta 0, beta 300, b 0.6, kappa 5, zeta 0.1, eps 0.001, sigma_M 50, 5 x 25
+ * iterations; omega 1.6 and min_size 16 are this library's choices.
+ * d_matches: device array of `capacity` matches, of which *d_count (device
+ * int) are used -- the output of dm_match can be passed as it is, so the two
+ * calls chain on one stream without a host round trip; d_matches / d_count
+ * may be NULL (no matching term).  d_u, d_v: device [H][W] outputs.
+ * d_ws >= dm_deepflow_workspace_bytes (256-byte aligned).  No host
+ * synchronisation; the call can be captured in a CUDA graph. */
+typedef struct {
+    double sigma, eta, gamma, delta, beta, b, kappa, zeta, eps, sigma_m, omega, image_scale;
+    int n_fixed, n_sor, min_size;
+} dm_flow_params;
+void dm_flow_params_default(dm_flow_params* p);
+dm_status dm_deepflow_workspace_bytes(dm_ctx* ctx, int W, int H, int capacity, const dm_flow_params* prm,
+                                      size_t* bytes);
+dm_status dm_deepflow(dm_ctx* ctx, const float* d_img1, const float* d_img2, int W, int H, const dm_match_t* d_matches,
+                      const int* d_count, int capacity, const dm_flow_params* prm, float* d_u, float* d_v, void* d_ws,
+                      size_t ws_bytes, void* stream);
+
 /* DM*, the earlier backtracking variant compared in Sec. 5.3 (Table
  * "oldvsnew"): entry points are the local maxima of the maps C_l(p, .) of every
  * level l = 1..L (q is one iff C_l(p, q) > 0, C_l(p, q) > C_l(p, r) for its

@@ -78,10 +78,9 @@ dm_status cuda_fail(dm_ctx* c, cudaError_t e, const char* where) {
 // Gaussian taps of standard deviation nu on [-ceil(3nu), ceil(3nu)],
 // exp(-j^2/(2 nu^2)) in double, normalised by their sum (accumulated from
 // j = -R upwards), then rounded to float.  nu <= 0: identity (R = 0).
-DmTaps make_taps(float nu_f) {
+DmTaps make_taps_d(double nu) {
     DmTaps t;
     memset(&t, 0, sizeof(t));
-    double nu = (double)nu_f;
     if (!(nu > 0.0)) {
         t.R = 0;
         t.w[0] = 1.0f;
@@ -98,6 +97,8 @@ DmTaps make_taps(float nu_f) {
     t.R = R;
     return t;
 }
+
+DmTaps make_taps(float nu_f) { return make_taps_d((double)nu_f); }
 
 bool aligned256(const void* p) { return ((uintptr_t)p & 255u) == 0; }
 
@@ -951,6 +952,63 @@ dm_status dm_set_tuned_config(dm_ctx* ctx, int W1, int H1, int W2, int H2, const
     if (s != DM_OK) return s;
     std::lock_guard<std::mutex> lk(ctx->tune_mu);
     ctx->tuned[{W1, H1, W2, H2}] = DmTune{chosen[0], chosen[1], chosen[2], chosen[3]};
+    return DM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// DeepFlow (Sec. 4.3)
+// ---------------------------------------------------------------------------
+void dm_flow_params_default(dm_flow_params* p) {
+    if (!p) return;
+    p->sigma = 0.5; p->eta = 0.95; p->gamma = 0.8; p->delta = 0.0; p->beta = 300.0; p->b = 0.6; p->kappa = 5.0;
+    p->zeta = 0.1; p->eps = 0.001; p->sigma_m = 50.0; p->omega = 1.6; p->image_scale = 255.0;
+    p->n_fixed = 5; p->n_sor = 25; p->min_size = 16;
+}
+
+namespace {
+dm_status flow_check(dm_ctx* ctx, int W, int H, int capacity, const dm_flow_params* prm, dm_flow_params* q) {
+    if (prm) *q = *prm;
+    else dm_flow_params_default(q);
+    if (W < 1 || H < 1 || capacity < 0) return fail(ctx, DM_EINVAL, "DeepFlow: bad size %dx%d or capacity %d", W, H, capacity);
+    if ((long long)W * H > (1LL << 30)) return fail(ctx, DM_EUNSUPPORTED, "DeepFlow: %dx%d is too large", W, H);
+    if (!(q->eta > 0.0 && q->eta < 1.0) || q->min_size < 1 || q->n_fixed < 0 || q->n_sor < 0 || !(q->eps > 0.0) ||
+        !(q->sigma_m > 0.0) || !(q->omega > 0.0 && q->omega < 2.0) || !(q->sigma >= 0.0) || !(q->image_scale > 0.0))
+        return fail(ctx, DM_EINVAL, "DeepFlow: parameter out of range");
+    return DM_OK;
+}
+}  // namespace
+
+dm_status dm_deepflow_workspace_bytes(dm_ctx* ctx, int W, int H, int capacity, const dm_flow_params* prm, size_t* bytes) {
+    if (!ctx) return DM_EINVAL;
+    if (!bytes) return fail(ctx, DM_EINVAL, "dm_deepflow_workspace_bytes: bytes is NULL");
+    dm_flow_params q;
+    dm_status s = flow_check(ctx, W, H, capacity, prm, &q);
+    if (s != DM_OK) return s;
+    DmFlowPlan plan;
+    dm_flow_plan(W, H, capacity, q, &plan);
+    *bytes = plan.bytes;
+    return DM_OK;
+}
+
+dm_status dm_deepflow(dm_ctx* ctx, const float* d_img1, const float* d_img2, int W, int H, const dm_match_t* d_matches,
+                      const int* d_count, int capacity, const dm_flow_params* prm, float* d_u, float* d_v, void* d_ws,
+                      size_t ws_bytes, void* stream) {
+    if (!ctx) return DM_EINVAL;
+    if (!d_img1 || !d_img2 || !d_u || !d_v || !d_ws) return fail(ctx, DM_EINVAL, "dm_deepflow: bad arguments");
+    if ((d_matches == nullptr) != (d_count == nullptr))
+        return fail(ctx, DM_EINVAL, "dm_deepflow: give both d_matches and d_count, or neither");
+    if (!aligned256(d_ws)) return fail(ctx, DM_EINVAL, "workspace must be 256-byte aligned");
+    dm_flow_params q;
+    dm_status s = flow_check(ctx, W, H, d_matches ? capacity : 0, prm, &q);
+    if (s != DM_OK) return s;
+    DmFlowPlan plan;
+    dm_flow_plan(W, H, d_matches ? capacity : 0, q, &plan);
+    if (ws_bytes < plan.bytes) return fail(ctx, DM_ENOMEM, "DeepFlow workspace %zu < %zu bytes", ws_bytes, plan.bytes);
+    DevGuard dg(ctx->device);
+    const DmTaps taps = make_taps_d(q.sigma);
+    cudaError_t e = dm_launch_deepflow(plan, taps, d_img1, d_img2, d_matches, d_count, d_u, d_v, (char*)d_ws,
+                                       (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "DeepFlow kernels");
     return DM_OK;
 }
 

@@ -410,6 +410,25 @@ struct DmDescParams {
     float scale, slope, mu;
 };
 
+// DeepFlow (Sec. 4.3), see k_deepflow.cu.
+#define DM_DF_MAXLEVELS 256
+struct DmFlowPlan {
+    int nl;                                   // levels (k_max + 1), finest first
+    int ws[DM_DF_MAXLEVELS], hs[DM_DF_MAXLEVELS];
+    float beta_k[DM_DF_MAXLEVELS], sk[DM_DF_MAXLEVELS];   // matching weight and eta^k per level
+    float eta, inv_eta, scale, kappa, gamma, delta, zeta2, eps2, omega, one_m_omega, sigma_m, two_sigma_m, norm;
+    int n_fixed, n_sor, capacity;
+    size_t P1[DM_DF_MAXLEVELS], P2[DM_DF_MAXLEVELS];      // workspace offsets
+    size_t tmp, fa_u, fa_v, fb_u, fb_v, du, dv, alpha, I2w, Im, Ix, Iy, ps, mc, mu, mv, D, A, owner, phi;
+    size_t bytes;
+};
+void dm_flow_plan(int W, int H, int capacity, const dm_flow_params& p, DmFlowPlan* q);
+cudaError_t dm_launch_smooth1(const float* img, int W, int H, float scale, const DmTaps& t, float* out, float* tmp,
+                              cudaStream_t st);
+cudaError_t dm_launch_deepflow(const DmFlowPlan& q, const DmTaps& taps, const float* img1, const float* img2,
+                               const dm_match_t* m, const int* d_count, float* out_u, float* out_v, char* ws,
+                               cudaStream_t st);
+
 // Record an error message on a context and return `s`; device of a context.
 dm_status dm_set_error(dm_ctx* ctx, dm_status s, const char* msg);
 int dm_ctx_device(const dm_ctx* ctx);

@@ -155,3 +155,20 @@ cudaError_t dm_launch_descriptors(const DmDescParams& prm, const float* img, int
     dm_count_launches((prm.t1.R > 0 ? 2 : 1) + 1 + (prm.t2.R > 0 ? 2 : 1) + (prm.t3.R > 0 ? 1 : 0) + 1);
     return cudaGetLastError();
 }
+
+// One image scaled by `scale` and smoothed by taps t (horizontal pass, then
+// vertical), as the first step of the descriptors; R = 0: scaled only.
+cudaError_t dm_launch_smooth1(const float* img, int W, int H, float scale, const DmTaps& t, float* out, float* tmp,
+                              cudaStream_t st) {
+    const int B = 256;
+    const long long n1 = (long long)W * H;
+    if (t.R > 0) {
+        k_smooth_h<1><<<nblk(n1, B), B, 0, st>>>(img, tmp, W, H, t, scale, 1);
+        k_smooth_v<1, 0><<<nblk(n1, B), B, 0, st>>>(tmp, out, W, H, t, 0.f, 0.f);
+        dm_count_launches(2);
+    } else {
+        k_scale<<<nblk(n1, B), B, 0, st>>>(img, out, n1, scale);
+        dm_count_launches(1);
+    }
+    return cudaGetLastError();
+}

@@ -43,6 +43,12 @@ class DmPair(C.Structure):
     _fields_ = [("d_img1", C.c_void_p), ("W1", C.c_int), ("H1", C.c_int), ("d_img2", C.c_void_p), ("W2", C.c_int),
                 ("H2", C.c_int), ("d_out", C.c_void_p), ("capacity", C.c_int), ("d_count", C.c_void_p)]
 
+class DmFlowParams(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("sigma", "eta", "gamma", "delta", "beta", "b", "kappa", "zeta", "eps",
+                                          "sigma_m", "omega", "image_scale")] + \
+               [(k, C.c_int) for k in ("n_fixed", "n_sor", "min_size")]
+
+
 # Exported symbols and their signatures (restype dm_status = c_int unless noted).
 _SIGS = {
     "dm_config_default": (None, [C.POINTER(DmConfig)]),
@@ -84,6 +90,11 @@ _SIGS = {
     "dm_correlate_pyramid_approx": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int,
                                               C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t,
                                               C.POINTER(C.c_void_p), C.c_void_p]),
+    "dm_flow_params_default": (None, [C.POINTER(DmFlowParams)]),
+    "dm_deepflow_workspace_bytes": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(DmFlowParams),
+                                              C.POINTER(C.c_size_t)]),
+    "dm_deepflow": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
+                              C.POINTER(DmFlowParams), C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "dm_star_workspace_bytes": (C.c_int, [C.c_void_p] + [C.c_int] * 4 + [C.POINTER(C.c_size_t)] * 2),
     "dm_backtrack_star": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_int, C.c_void_p,
                                     C.c_void_p]),
@@ -283,6 +294,38 @@ def dm_match(ctx, d_img1, d_img2, d_ws, d_out, d_count, stream=None):
     st = load().dm_match(ctx, _dptr(d_img1), W1, H1, _dptr(d_img2), W2, H2, _dptr(d_ws),
                          d_ws.numel() * d_ws.element_size(), _dptr(d_out), cap, _dptr(d_count), _stream_ptr(stream))
     _check(ctx, st, "dm_match")
+
+
+def dm_flow_params(**kw) -> DmFlowParams:
+    """DeepFlow parameters: the library defaults (the paper's values) with the
+    given fields replaced."""
+    p = DmFlowParams()
+    load().dm_flow_params_default(C.byref(p))
+    for k, v in kw.items():
+        if k not in dict(DmFlowParams._fields_):
+            raise KeyError(f"unknown DeepFlow parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+def dm_deepflow_workspace_bytes(ctx, W, H, capacity, prm: DmFlowParams | None = None) -> int:
+    b = C.c_size_t()
+    st = load().dm_deepflow_workspace_bytes(ctx, W, H, capacity, C.byref(prm) if prm is not None else None, C.byref(b))
+    _check(ctx, st, "dm_deepflow_workspace_bytes")
+    return b.value
+
+
+def dm_deepflow(ctx, d_img1, d_img2, d_matches, d_count, d_u, d_v, d_ws, prm: DmFlowParams | None = None,
+                stream=None):
+    """d_matches: device float32 tensor [capacity][5] (or None), d_count: device
+    int32 [1] (or None); d_u, d_v: device float32 [H][W] outputs."""
+    H, W = d_img1.shape
+    cap = 0 if d_matches is None else d_matches.numel() * d_matches.element_size() // MATCH_BYTES
+    st = load().dm_deepflow(ctx, _dptr(d_img1), _dptr(d_img2), W, H, None if d_matches is None else _dptr(d_matches),
+                            None if d_count is None else _dptr(d_count), cap,
+                            C.byref(prm) if prm is not None else None, _dptr(d_u), _dptr(d_v), _dptr(d_ws),
+                            d_ws.numel() * d_ws.element_size(), _stream_ptr(stream))
+    _check(ctx, st, "dm_deepflow")
 
 
 def dm_star_workspace_bytes(ctx, W1, H1, W2, H2) -> dict:
@@ -485,6 +528,30 @@ class Context:
         dm_match(self.ctx, i1, i2, ws, out, cnt, stream)
         n = int(cnt.item())
         return out[:n]
+
+    def deepflow(self, img1, img2, matches=None, stream=None, **params):
+        """DeepFlow (Sec. 4.3) of two same-size images with optional matches
+        (rows x1, y1, x2, y2, score); returns device tensors (u, v)."""
+        torch = self.torch
+        dev = f"cuda:{self.device}"
+        i1 = torch.as_tensor(img1, dtype=torch.float32, device=dev).contiguous()
+        i2 = torch.as_tensor(img2, dtype=torch.float32, device=dev).contiguous()
+        H, W = i1.shape
+        prm = dm_flow_params(**params)
+        dm_m = cnt = None
+        cap = 0
+        if matches is not None:
+            dm_m = torch.as_tensor(matches, dtype=torch.float32, device=dev).reshape(-1, 5).contiguous()
+            cap = dm_m.shape[0]
+            cnt = torch.full((1,), cap, dtype=torch.int32, device=dev)
+            if cap == 0:
+                dm_m = torch.zeros((1, 5), dtype=torch.float32, device=dev)
+        ws = torch.empty(max(dm_deepflow_workspace_bytes(self.ctx, W, H, max(cap, 1) if dm_m is not None else 0, prm), 256),
+                         dtype=torch.uint8, device=dev)
+        u = torch.empty((H, W), dtype=torch.float32, device=dev)
+        v = torch.empty((H, W), dtype=torch.float32, device=dev)
+        dm_deepflow(self.ctx, i1, i2, dm_m, cnt, u, v, ws, prm, stream)
+        return u, v
 
     def match_star(self, img1, img2, stream=None):
         """DM* matches (local-maximum entry points, start + end scores) as a
