@@ -419,7 +419,7 @@ struct DmFlowPlan {
     float eta, inv_eta, scale, kappa, gamma, delta, zeta2, eps2, omega, one_m_omega, sigma_m, two_sigma_m, norm;
     int n_fixed, n_sor, capacity;
     size_t P1[DM_DF_MAXLEVELS], P2[DM_DF_MAXLEVELS];      // workspace offsets
-    size_t tmp, fa_u, fa_v, fb_u, fb_v, du, dv, alpha, I2w, Im, Ix, Iy, ps, mc, mu, mv, D, A, owner, phi;
+    size_t tmp, fa_u, fa_v, fb_u, fb_v, du, dv, du2, dv2, alpha, I2w, Im, Ix, Iy, ps, mc, mu, mv, D, A, owner, phi;
     size_t bytes;
 };
 void dm_flow_plan(int W, int H, int capacity, const dm_flow_params& p, DmFlowPlan* q);

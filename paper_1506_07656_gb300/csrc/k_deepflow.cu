@@ -12,10 +12,13 @@
 // choices the paper leaves open (resampling, stencils, border rules, where a
 // match lands on a coarse level, SOR ordering) are stated at each kernel.
 //
-// Levels whose pixels fit one CTA's sweep (small levels, most of the 60-odd
-// levels of a VGA-sized pair) run all their fixed-point steps and SOR sweeps
-// in one kernel with block barriers between sweeps; larger levels launch one
-// kernel per step and colour.
+// The SOR sweeps are sequential in time (each half-sweep needs the other
+// colour's previous values), so the launch count, not the arithmetic, bounds
+// the solver: levels of up to 5120 pixels (about half of the 60-odd levels of
+// a 1024 x 436 pair) run entirely in one CTA with their state in shared
+// memory; larger levels run 8 half-sweeps per launch, temporally blocked in
+// shared memory (a tile plus an 8-pixel halo), which gives the same bits as
+// 8 global half-sweeps.
 #include <math.h>
 
 #include "dm_internal.cuh"
@@ -223,25 +226,33 @@ struct DfLevel {
     float* ps;
 };
 
-__device__ __forceinline__ void df_weights_at(const DfLevel& L, const DfConst& k, long long o) {
-    const int x = (int)(o % L.w), y = (int)(o / L.w);
-    const long long n = L.n;
-    const float* D = L.D;
-    const float du = L.du[o], dv = L.dv[o];
-    const float U = __fadd_rn(L.u[o], du), V = __fadd_rn(L.v[o], dv);
+// The fixed-point step's arithmetic for one pixel, on values: the
+// smoothness weight from the forward differences of u + du, v + dv (has_r /
+// has_d: the right / lower neighbour exists), the data and matching weights
+// and the 2x2 system (A11, A12, A22, b1, b2).
+struct DfPix {
+    float ps, a11, a12, a22, b1, b2;
+};
+
+__device__ __forceinline__ DfPix df_weights_vals(float u, float du, float v, float dv, bool has_r, float ur, float dur,
+                                                 float vr, float dvr, bool has_d, float ud, float dud, float vd, float dvd,
+                                                 const float* d, float alpha, float mc, float mu, float mv,
+                                                 const DfConst& k) {
+    const float U = __fadd_rn(u, du), V = __fadd_rn(v, dv);
     float ux = 0.0f, uy = 0.0f, vx = 0.0f, vy = 0.0f;
-    if (x + 1 < L.w) {
-        ux = __fsub_rn(__fadd_rn(L.u[o + 1], L.du[o + 1]), U);
-        vx = __fsub_rn(__fadd_rn(L.v[o + 1], L.dv[o + 1]), V);
+    if (has_r) {
+        ux = __fsub_rn(__fadd_rn(ur, dur), U);
+        vx = __fsub_rn(__fadd_rn(vr, dvr), V);
     }
-    if (y + 1 < L.h) {
-        uy = __fsub_rn(__fadd_rn(L.u[o + L.w], L.du[o + L.w]), U);
-        vy = __fsub_rn(__fadd_rn(L.v[o + L.w], L.dv[o + L.w]), V);
+    if (has_d) {
+        uy = __fsub_rn(__fadd_rn(ud, dud), U);
+        vy = __fsub_rn(__fadd_rn(vd, dvd), V);
     }
+    DfPix r;
     const float s2 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(ux, ux), __fmul_rn(uy, uy)), __fmul_rn(vx, vx)), __fmul_rn(vy, vy));
-    L.ps[o] = __fmul_rn(L.alpha[o], df_dpsi(s2, k.eps2));
-    const float d0 = D[o], d1 = D[n + o], d2 = D[2 * n + o], d3 = D[3 * n + o], d4 = D[4 * n + o], d5 = D[5 * n + o];
-    const float d6 = D[6 * n + o], d7 = D[7 * n + o], d8 = D[8 * n + o], d9 = D[9 * n + o], d10 = D[10 * n + o];
+    r.ps = __fmul_rn(alpha, df_dpsi(s2, k.eps2));
+    const float d0 = d[0], d1 = d[1], d2 = d[2], d3 = d[3], d4 = d[4], d5 = d[5], d6 = d[6], d7 = d[7], d8 = d[8];
+    const float d9 = d[9], d10 = d[10];
     float a0 = 0.0f;
     if (k.delta > 0.0f) {
         const float r0 = __fadd_rn(__fadd_rn(__fmul_rn(d0, du), __fmul_rn(d1, dv)), d2);
@@ -251,53 +262,65 @@ __device__ __forceinline__ void df_weights_at(const DfLevel& L, const DfConst& k
     const float ry = __fadd_rn(__fadd_rn(__fmul_rn(d4, du), __fmul_rn(d5, dv)), d7);
     const float ag = __fmul_rn(k.gamma, df_dpsi(__fadd_rn(__fmul_rn(d9, __fmul_rn(rx, rx)), __fmul_rn(d10, __fmul_rn(ry, ry))), k.eps2));
     float mw = 0.0f;
-    const float mc = L.mc[o], mu = L.mu[o], mv = L.mv[o];
     if (mc > 0.0f) {
         const float eu = __fsub_rn(U, mu), ev = __fsub_rn(V, mv);
         mw = __fmul_rn(mc, df_dpsi(__fadd_rn(__fmul_rn(eu, eu), __fmul_rn(ev, ev)), k.eps2));
     }
     const float gx = __fmul_rn(ag, d9), gy = __fmul_rn(ag, d10);
     const float a0x = __fmul_rn(a0, d0), a0y = __fmul_rn(a0, d1);
-    float* A = L.A;
-    A[o] = __fadd_rn(__fadd_rn(__fmul_rn(a0x, d0), __fadd_rn(__fmul_rn(__fmul_rn(gx, d3), d3), __fmul_rn(__fmul_rn(gy, d4), d4))), mw);
-    A[n + o] = __fadd_rn(__fmul_rn(a0x, d1), __fadd_rn(__fmul_rn(__fmul_rn(gx, d3), d4), __fmul_rn(__fmul_rn(gy, d4), d5)));
-    A[2 * n + o] = __fadd_rn(__fadd_rn(__fmul_rn(a0y, d1), __fadd_rn(__fmul_rn(__fmul_rn(gx, d4), d4), __fmul_rn(__fmul_rn(gy, d5), d5))), mw);
-    A[3 * n + o] = __fsub_rn(-__fadd_rn(__fmul_rn(a0x, d2), __fadd_rn(__fmul_rn(__fmul_rn(gx, d3), d6), __fmul_rn(__fmul_rn(gy, d4), d7))),
-                             __fmul_rn(mw, __fsub_rn(L.u[o], mu)));
-    A[4 * n + o] = __fsub_rn(-__fadd_rn(__fmul_rn(a0y, d2), __fadd_rn(__fmul_rn(__fmul_rn(gx, d4), d6), __fmul_rn(__fmul_rn(gy, d5), d7))),
-                             __fmul_rn(mw, __fsub_rn(L.v[o], mv)));
+    r.a11 = __fadd_rn(__fadd_rn(__fmul_rn(a0x, d0), __fadd_rn(__fmul_rn(__fmul_rn(gx, d3), d3), __fmul_rn(__fmul_rn(gy, d4), d4))), mw);
+    r.a12 = __fadd_rn(__fmul_rn(a0x, d1), __fadd_rn(__fmul_rn(__fmul_rn(gx, d3), d4), __fmul_rn(__fmul_rn(gy, d4), d5)));
+    r.a22 = __fadd_rn(__fadd_rn(__fmul_rn(a0y, d1), __fadd_rn(__fmul_rn(__fmul_rn(gx, d4), d4), __fmul_rn(__fmul_rn(gy, d5), d5))), mw);
+    r.b1 = __fsub_rn(-__fadd_rn(__fmul_rn(a0x, d2), __fadd_rn(__fmul_rn(__fmul_rn(gx, d3), d6), __fmul_rn(__fmul_rn(gy, d4), d7))),
+                     __fmul_rn(mw, __fsub_rn(u, mu)));
+    r.b2 = __fsub_rn(-__fadd_rn(__fmul_rn(a0y, d2), __fadd_rn(__fmul_rn(__fmul_rn(gx, d4), d6), __fmul_rn(__fmul_rn(gy, d5), d7))),
+                     __fmul_rn(mw, __fsub_rn(v, mv)));
+    return r;
 }
 
-// One SOR relaxation of pixel o (red-black: its 4-neighbours have the other
-// colour, so the pixels of one colour are independent): neighbours in the
-// order left, right, up, down, edge weight (ps_o + ps_p) / 2;
-//   du = (1 - omega) du + omega (b1 + sum w (du_p + u_p - u_o) - A12 dv) / (A11 + sum w),
-// then dv the same way with the new du.
-__device__ __forceinline__ void df_sor_at(const DfLevel& L, const DfConst& k, long long o) {
+__device__ __forceinline__ void df_load_d(const float* D, long long n, long long o, float* d) {
+#pragma unroll
+    for (int j = 0; j < 11; j++) d[j] = D[j * n + o];
+}
+
+__device__ __forceinline__ void df_weights_at(const DfLevel& L, const DfConst& k, long long o) {
     const int x = (int)(o % L.w), y = (int)(o / L.w);
+    const bool hr = x + 1 < L.w, hd = y + 1 < L.h;
+    const long long r = hr ? o + 1 : o, dn = hd ? o + L.w : o;
+    float d[11];
+    df_load_d(L.D, L.n, o, d);
+    const DfPix q = df_weights_vals(L.u[o], L.du[o], L.v[o], L.dv[o], hr, L.u[r], L.du[r], L.v[r], L.dv[r], hd, L.u[dn],
+                                    L.du[dn], L.v[dn], L.dv[dn], d, L.alpha[o], L.mc[o], L.mu[o], L.mv[o], k);
     const long long n = L.n;
-    const float pso = L.ps[o], uo = L.u[o], vo = L.v[o];
+    L.ps[o] = q.ps;
+    L.A[o] = q.a11;
+    L.A[n + o] = q.a12;
+    L.A[2 * n + o] = q.a22;
+    L.A[3 * n + o] = q.b1;
+    L.A[4 * n + o] = q.b2;
+}
+
+// One SOR relaxation of a pixel from its existing 4-neighbours (left, right,
+// up, down, compacted into nb[0..nn)): edge weight (ps_o + ps_p) / 2,
+//   du = (1 - omega) du + omega (b1 + sum w (du_p + u_p - u_o) - A12 dv) / (A11 + sum w),
+// then dv the same way with the new du.  Get(p, ps, du, u, dv, v) reads a neighbour.
+template <class Get>
+__device__ __forceinline__ void df_sor_vals(int nn, const int* nb, Get get, float pso, float uo, float vo, float a11,
+                                            float a12, float a22, float b1, float b2, const DfConst& k, float& du,
+                                            float& dv) {
     float sw = 0.0f, su = 0.0f, sv = 0.0f;
-    long long nb[4];
-    int nn = 0;
-    if (x > 0) nb[nn++] = o - 1;
-    if (x + 1 < L.w) nb[nn++] = o + 1;
-    if (y > 0) nb[nn++] = o - L.w;
-    if (y + 1 < L.h) nb[nn++] = o + L.w;
     for (int j = 0; j < nn; j++) {
-        const long long p = nb[j];
-        const float we = __fmul_rn(0.5f, __fadd_rn(pso, L.ps[p]));
+        float psp, dup, up, dvp, vp;
+        get(nb[j], psp, dup, up, dvp, vp);
+        const float we = __fmul_rn(0.5f, __fadd_rn(pso, psp));
         sw = __fadd_rn(sw, we);
-        su = __fadd_rn(su, __fmul_rn(we, __fsub_rn(__fadd_rn(L.du[p], L.u[p]), uo)));
-        sv = __fadd_rn(sv, __fmul_rn(we, __fsub_rn(__fadd_rn(L.dv[p], L.v[p]), vo)));
+        su = __fadd_rn(su, __fmul_rn(we, __fsub_rn(__fadd_rn(dup, up), uo)));
+        sv = __fadd_rn(sv, __fmul_rn(we, __fsub_rn(__fadd_rn(dvp, vp), vo)));
     }
-    const float* A = L.A;
-    const float a12 = A[n + o];
-    const float nu = __fsub_rn(__fadd_rn(A[3 * n + o], su), __fmul_rn(a12, L.dv[o]));
-    const float du = __fadd_rn(__fmul_rn(k.one_m_omega, L.du[o]), __fmul_rn(k.omega, __fdiv_rn(nu, __fadd_rn(A[o], sw))));
-    L.du[o] = du;
-    const float nv = __fsub_rn(__fadd_rn(A[4 * n + o], sv), __fmul_rn(a12, du));
-    L.dv[o] = __fadd_rn(__fmul_rn(k.one_m_omega, L.dv[o]), __fmul_rn(k.omega, __fdiv_rn(nv, __fadd_rn(A[2 * n + o], sw))));
+    const float nu = __fsub_rn(__fadd_rn(b1, su), __fmul_rn(a12, dv));
+    du = __fadd_rn(__fmul_rn(k.one_m_omega, du), __fmul_rn(k.omega, __fdiv_rn(nu, __fadd_rn(a11, sw))));
+    const float nv = __fsub_rn(__fadd_rn(b2, sv), __fmul_rn(a12, du));
+    dv = __fadd_rn(__fmul_rn(k.one_m_omega, dv), __fmul_rn(k.omega, __fdiv_rn(nv, __fadd_rn(a22, sw))));
 }
 
 __global__ void k_df_weights(DfLevel L, DfConst k) {
@@ -305,15 +328,84 @@ __global__ void k_df_weights(DfLevel L, DfConst k) {
         df_weights_at(L, k, o);
 }
 
-// Pixels of one colour ((x + y) & 1 == color), indexed densely: row y holds
-// ceil((w - start) / 2) of them, start = (y + color) & 1.
-__global__ void k_df_sor(DfLevel L, DfConst k, int color) {
-    const int half = (L.w + 1) / 2;
-    const long long n = (long long)half * L.h;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(i / half), j = (int)(i % half);
-        const int x = 2 * j + ((y + color) & 1);
-        if (x < L.w) df_sor_at(L, k, (long long)y * L.w + x);
+// Temporally blocked red-black SOR: a CTA owns a TB_W x TB_H tile and stages
+// it with a halo of S pixels (S = the half-sweeps of this launch, <= TB_S) in
+// shared memory, then runs S half-sweeps there, colour start, start + 1, ...
+// Half-sweep j updates the pixels of its colour in the staged region shrunk by
+// j + 1 on every side that is not the image border: their neighbours then
+// hold exactly the values the global sweep would give them, so after S
+// half-sweeps the tile itself is exact and is written back -- the same bits
+// as S global half-sweeps, with one launch and no global barrier between them.
+// The halos of other CTAs overlap this tile, so the increments are read from
+// L.du / L.dv and written to a second pair of buffers (ping-pong between
+// launches): no CTA ever sees another's updates of the same launch.
+constexpr int TB_W = 32, TB_H = 16, TB_S = 8;
+constexpr int TB_LW = TB_W + 2 * TB_S, TB_LH = TB_H + 2 * TB_S, TB_LN = TB_LW * TB_LH;
+constexpr size_t TB_SMEM = (size_t)TB_LN * 10 * sizeof(float);
+
+__global__ void __launch_bounds__(256) k_df_sor_tb(DfLevel L, DfConst k, int start_color, int S, float* __restrict__ out_du,
+                                                   float* __restrict__ out_dv) {
+    extern __shared__ __align__(16) float sm[];
+    float* sdu = sm;
+    float* sdv = sm + TB_LN;
+    float* su_ = sm + 2 * TB_LN;
+    float* sv_ = sm + 3 * TB_LN;
+    float* sps = sm + 4 * TB_LN;
+    float* sA = sm + 5 * TB_LN;          // [5][TB_LN]
+    const int tiles_x = (L.w + TB_W - 1) / TB_W;
+    const int tx0 = (blockIdx.x % tiles_x) * TB_W, ty0 = (blockIdx.x / tiles_x) * TB_H;
+    const int tx1 = min(tx0 + TB_W, L.w), ty1 = min(ty0 + TB_H, L.h);
+    const int lx0 = max(tx0 - S, 0), ly0 = max(ty0 - S, 0);
+    const int lx1 = min(tx1 + S, L.w), ly1 = min(ty1 + S, L.h);
+    const int lw = lx1 - lx0, lh = ly1 - ly0, ln = lw * lh;
+    const long long n = L.n;
+    for (int i = threadIdx.x; i < ln; i += blockDim.x) {
+        const long long o = (long long)(ly0 + i / lw) * L.w + (lx0 + i % lw);
+        sdu[i] = L.du[o];
+        sdv[i] = L.dv[o];
+        su_[i] = L.u[o];
+        sv_[i] = L.v[o];
+        sps[i] = L.ps[o];
+#pragma unroll
+        for (int j = 0; j < 5; j++) sA[j * TB_LN + i] = L.A[j * n + o];
+    }
+    __syncthreads();
+    auto get = [&](int p, float& ps, float& du, float& u, float& dv, float& v) {
+        ps = sps[p]; du = sdu[p]; u = su_[p]; dv = sdv[p]; v = sv_[p];
+    };
+    for (int j = 0; j < S; j++) {
+        const int color = (start_color + j) & 1;
+        const int ax0 = lx0 > 0 ? lx0 + j + 1 : lx0, ay0 = ly0 > 0 ? ly0 + j + 1 : ly0;
+        const int ax1 = lx1 < L.w ? lx1 - j - 1 : lx1, ay1 = ly1 < L.h ? ly1 - j - 1 : ly1;
+        const int aw = ax1 - ax0, ah = ay1 - ay0;
+        if (aw > 0 && ah > 0) {
+            const int half = (aw + 1) / 2;
+            for (int i = threadIdx.x; i < half * ah; i += blockDim.x) {
+                const int gy = ay0 + i / half;
+                const int gx = ax0 + 2 * (i % half) + ((gy + ax0 + color) & 1);
+                if (gx >= ax1) continue;
+                const int p = (gy - ly0) * lw + (gx - lx0);
+                int nb[4], nn = 0;
+                if (gx > 0) nb[nn++] = p - 1;
+                if (gx + 1 < L.w) nb[nn++] = p + 1;
+                if (gy > 0) nb[nn++] = p - lw;
+                if (gy + 1 < L.h) nb[nn++] = p + lw;
+                float du = sdu[p], dv = sdv[p];
+                df_sor_vals(nn, nb, get, sps[p], su_[p], sv_[p], sA[p], sA[TB_LN + p], sA[2 * TB_LN + p],
+                            sA[3 * TB_LN + p], sA[4 * TB_LN + p], k, du, dv);
+                sdu[p] = du;
+                sdv[p] = dv;
+            }
+        }
+        __syncthreads();
+    }
+    const int ow = tx1 - tx0;
+    for (int i = threadIdx.x; i < ow * (ty1 - ty0); i += blockDim.x) {
+        const int gx = tx0 + i % ow, gy = ty0 + i / ow;
+        const int p = (gy - ly0) * lw + (gx - lx0);
+        const long long o = (long long)gy * L.w + gx;
+        out_du[o] = sdu[p];
+        out_dv[o] = sdv[p];
     }
 }
 
@@ -325,32 +417,77 @@ __global__ void k_df_update(float* __restrict__ u, float* __restrict__ v, const 
     }
 }
 
-// A whole small level in one CTA: n_fixed x (weights, then n_sor red-black
-// sweeps), block barriers between the passes, then w += dw.  The same
-// per-pixel operations as the multi-launch path.
+// A whole small level in one CTA with its state in shared memory: u, v, du,
+// dv, ps and the system (10 floats per pixel); n_fixed x (weights, then
+// n_sor red-black sweeps) with block barriers between the passes, then
+// w += dw.  The same per-pixel arithmetic as the multi-launch path.
 constexpr int DF_SMALL_THREADS = 1024;
+constexpr int DF_SMALL_MAX = 5120;              // pixels: 10 x 4 B x 5120 = 200 KB of shared memory
+constexpr size_t DF_SMALL_SMEM = (size_t)DF_SMALL_MAX * 10 * sizeof(float);
 
 __global__ void __launch_bounds__(DF_SMALL_THREADS) k_df_level_small(DfLevel L, DfConst k, int n_fixed, int n_sor) {
-    const int half = (L.w + 1) / 2;
-    const long long nc = (long long)half * L.h;
+    extern __shared__ __align__(16) float sm[];
+    const int n = (int)L.n, w = L.w, h = L.h;
+    float* su_ = sm;
+    float* sv_ = sm + n;
+    float* sdu = sm + 2 * n;
+    float* sdv = sm + 3 * n;
+    float* sps = sm + 4 * n;
+    float* sA = sm + 5 * n;              // [5][n]
+    for (int o = threadIdx.x; o < n; o += blockDim.x) {
+        su_[o] = L.u[o];
+        sv_[o] = L.v[o];
+        sdu[o] = 0.0f;
+        sdv[o] = 0.0f;
+    }
+    __syncthreads();
+    auto get = [&](int p, float& ps, float& du, float& u, float& dv, float& v) {
+        ps = sps[p]; du = sdu[p]; u = su_[p]; dv = sdv[p]; v = sv_[p];
+    };
+    const int half = (w + 1) / 2;
     for (int it = 0; it < n_fixed; it++) {
-        for (long long o = threadIdx.x; o < L.n; o += blockDim.x) df_weights_at(L, k, o);
+        for (int o = threadIdx.x; o < n; o += blockDim.x) {
+            const int x = o % w, y = o / w;
+            const bool hr = x + 1 < w, hd = y + 1 < h;
+            const int r = hr ? o + 1 : o, dn = hd ? o + w : o;
+            float d[11];
+            df_load_d(L.D, L.n, o, d);
+            const DfPix q = df_weights_vals(su_[o], sdu[o], sv_[o], sdv[o], hr, su_[r], sdu[r], sv_[r], sdv[r], hd, su_[dn],
+                                            sdu[dn], sv_[dn], sdv[dn], d, L.alpha[o], L.mc[o], L.mu[o], L.mv[o], k);
+            sps[o] = q.ps;
+            sA[o] = q.a11;
+            sA[n + o] = q.a12;
+            sA[2 * n + o] = q.a22;
+            sA[3 * n + o] = q.b1;
+            sA[4 * n + o] = q.b2;
+        }
         __syncthreads();
         for (int s = 0; s < n_sor; s++)
             for (int color = 0; color < 2; color++) {
-                for (long long i = threadIdx.x; i < nc; i += blockDim.x) {
-                    const int y = (int)(i / half), j = (int)(i % half);
-                    const int x = 2 * j + ((y + color) & 1);
-                    if (x < L.w) df_sor_at(L, k, (long long)y * L.w + x);
+                for (int i = threadIdx.x; i < half * h; i += blockDim.x) {
+                    const int y = i / half;
+                    const int x = 2 * (i % half) + ((y + color) & 1);
+                    if (x >= w) continue;
+                    const int p = y * w + x;
+                    int nb[4], nn = 0;
+                    if (x > 0) nb[nn++] = p - 1;
+                    if (x + 1 < w) nb[nn++] = p + 1;
+                    if (y > 0) nb[nn++] = p - w;
+                    if (y + 1 < h) nb[nn++] = p + w;
+                    float du = sdu[p], dv = sdv[p];
+                    df_sor_vals(nn, nb, get, sps[p], su_[p], sv_[p], sA[p], sA[n + p], sA[2 * n + p], sA[3 * n + p],
+                                sA[4 * n + p], k, du, dv);
+                    sdu[p] = du;
+                    sdv[p] = dv;
                 }
                 __syncthreads();
             }
     }
     float* u = const_cast<float*>(L.u);
     float* v = const_cast<float*>(L.v);
-    for (long long o = threadIdx.x; o < L.n; o += blockDim.x) {
-        u[o] = __fadd_rn(u[o], L.du[o]);
-        v[o] = __fadd_rn(v[o], L.dv[o]);
+    for (int o = threadIdx.x; o < n; o += blockDim.x) {
+        u[o] = __fadd_rn(su_[o], sdu[o]);
+        v[o] = __fadd_rn(sv_[o], sdv[o]);
     }
 }
 
@@ -361,7 +498,6 @@ __global__ void __launch_bounds__(DF_SMALL_THREADS) k_df_level_small(DfLevel L, 
 // ---------------------------------------------------------------------------
 namespace {
 constexpr double kPi = 3.14159265358979323846;
-constexpr long long DF_SMALL_MAX = 65536;      // pixels of a level solved by one CTA
 inline unsigned df_blocks(long long n) {
     const long long b = (n + 255) / 256;
     return (unsigned)(b < 4096 ? (b > 0 ? b : 1) : 4096);
@@ -410,7 +546,7 @@ void dm_flow_plan(int W, int H, int capacity, const dm_flow_params& p, DmFlowPla
         q->P1[k] = off; off = dm_align(off + Nk * 4);
         q->P2[k] = off; off = dm_align(off + Nk * 4);
     }
-    size_t* one[] = {&q->tmp, &q->fa_u, &q->fa_v, &q->fb_u, &q->fb_v, &q->du, &q->dv, &q->alpha, &q->I2w, &q->Im,
+    size_t* one[] = {&q->tmp, &q->fa_u, &q->fa_v, &q->fb_u, &q->fb_v, &q->du, &q->dv, &q->du2, &q->dv2, &q->alpha, &q->I2w, &q->Im,
                      &q->Ix, &q->Iy, &q->ps, &q->mc, &q->mu, &q->mv};
     for (size_t* f : one) { *f = off; off = dm_align(off + N0 * 4); }
     q->D = off; off = dm_align(off + N0 * 11 * 4);
@@ -431,6 +567,10 @@ cudaError_t dm_launch_deepflow(const DmFlowPlan& q, const DmTaps& taps, const fl
     const int W = q.ws[0], H = q.hs[0];
     long long launches = 0;
     cudaError_t e;
+    static std::atomic<unsigned long long> tb_done{0}, small_done{0};
+    if ((e = dm_smem_opt_in(reinterpret_cast<const void*>(k_df_sor_tb), (int)TB_SMEM, tb_done)) != cudaSuccess) return e;
+    if ((e = dm_smem_opt_in(reinterpret_cast<const void*>(k_df_level_small), (int)DF_SMALL_SMEM, small_done)) != cudaSuccess)
+        return e;
     if ((e = dm_launch_smooth1(img1, W, H, q.scale, taps, F(q.P1[0]), F(q.tmp), st)) != cudaSuccess) return e;
     if ((e = dm_launch_smooth1(img2, W, H, q.scale, taps, F(q.P2[0]), F(q.tmp), st)) != cudaSuccess) return e;
     for (int l = 1; l < q.nl; l++) {
@@ -484,19 +624,24 @@ cudaError_t dm_launch_deepflow(const DmFlowPlan& q, const DmTaps& taps, const fl
         L.D = F(q.D); L.alpha = F(q.alpha); L.mc = F(q.mc); L.mu = F(q.mu); L.mv = F(q.mv);
         L.u = cu; L.v = cv; L.du = F(q.du); L.dv = F(q.dv); L.A = F(q.A); L.ps = F(q.ps);
         if (n <= DF_SMALL_MAX) {
-            k_df_level_small<<<1, DF_SMALL_THREADS, 0, st>>>(L, k, q.n_fixed, q.n_sor);
+            k_df_level_small<<<1, DF_SMALL_THREADS, DF_SMALL_SMEM, st>>>(L, k, q.n_fixed, q.n_sor);
             launches++;
         } else {
-            const long long nc = (long long)((w + 1) / 2) * h;
+            const unsigned tiles = (unsigned)(((w + TB_W - 1) / TB_W) * ((h + TB_H - 1) / TB_H));
+            float* alt_u = F(q.du2);
+            float* alt_v = F(q.dv2);
             for (int it = 0; it < q.n_fixed; it++) {
                 k_df_weights<<<df_blocks(n), 256, 0, st>>>(L, k);
-                for (int s = 0; s < q.n_sor; s++) {
-                    k_df_sor<<<df_blocks(nc), 256, 0, st>>>(L, k, 0);
-                    k_df_sor<<<df_blocks(nc), 256, 0, st>>>(L, k, 1);
+                launches++;
+                for (int j = 0; j < 2 * q.n_sor; j += TB_S) {
+                    const int S = 2 * q.n_sor - j < TB_S ? 2 * q.n_sor - j : TB_S;
+                    k_df_sor_tb<<<tiles, 256, TB_SMEM, st>>>(L, k, j & 1, S, alt_u, alt_v);
+                    launches++;
+                    float* t = L.du; L.du = alt_u; alt_u = t;
+                    t = L.dv; L.dv = alt_v; alt_v = t;
                 }
-                launches += 1 + 2LL * q.n_sor;
             }
-            k_df_update<<<df_blocks(n), 256, 0, st>>>(cu, cv, F(q.du), F(q.dv), n);
+            k_df_update<<<df_blocks(n), 256, 0, st>>>(cu, cv, L.du, L.dv, n);
             launches++;
         }
     }

@@ -2,8 +2,11 @@
 
 * FP32: the flow equals, bit for bit, the oracle's FP32 DeepFlow -- without
   matches, with the oracle's own DeepMatching matches as the matching term,
-  on ragged sizes, with the brightness term switched on, and on a size whose
-  finest levels take the multi-launch path (more pixels than one CTA's sweep).
+  on ragged sizes, with the brightness term switched on, and on sizes whose
+  finest levels take the temporally blocked multi-launch path (more pixels
+  than one CTA holds), with partial and full blocks of half-sweeps, and with
+  more tiles than resident CTAs (the halos of later waves must not see the
+  updates of earlier ones).
 * identical images: zero flow.
 * chaining: the matches of dm_match passed on the device (its count read on
   the device) give the same flow as the same matches passed from the host.
@@ -45,7 +48,8 @@ def _flow(torch, ctx, i1, i2, m=None, **kw):
     return u.cpu().numpy(), v.cpu().numpy()
 
 
-CASES = ["translation_64x48", "dm_matches_64x48", "ragged_37x29", "brightness_term_48x40", "multi_launch_320x240"]
+CASES = ["translation_64x48", "dm_matches_64x48", "ragged_37x29", "brightness_term_48x40", "multi_launch_320x240",
+         "blocked_sor_97x75", "many_tiles_1024x436"]
 
 
 def _case(name):
@@ -67,6 +71,13 @@ def _case(name):
         xs, ys = rng.integers(0, 320, 400), rng.integers(0, 240, 400)
         m = np.stack([xs, ys, np.clip(xs + 2, 0, 319), np.clip(ys - 1, 0, 239), rng.random(400)], 1)
         return pr.img1.astype(np.float32), pr.img2.astype(np.float32), m, {"n_fixed": 2, "n_sor": 5}
+    if name == "blocked_sor_97x75":                   # default parameters, finest levels above one CTA's size
+        pr = synth.make_pair_smooth(97, 75, seed=12, max_disp=4.0)
+        m, _, _ = oracle.match(pr.img1, pr.img2, "f32")
+        return pr.img1.astype(np.float32), pr.img2.astype(np.float32), m, {}
+    if name == "many_tiles_1024x436":                 # more SOR tiles than resident CTAs (several waves), 2 levels
+        pr = synth.make_pair_smooth(1024, 436, seed=21, max_disp=8.0)
+        return pr.img1.astype(np.float32), pr.img2.astype(np.float32), None, {"min_size": 400}
     raise KeyError(name)
 
 
