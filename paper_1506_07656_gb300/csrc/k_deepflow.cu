@@ -14,9 +14,8 @@
 //
 // The SOR sweeps are sequential in time (each half-sweep needs the other
 // colour's previous values), so the launch count, not the arithmetic, bounds
-// the solver: levels of up to 5120 pixels (about half of the 60-odd levels of
-// a 1024 x 436 pair) run entirely in one CTA with their state in shared
-// memory; larger levels run 8 half-sweeps per launch, temporally blocked in
+// the solver: the smallest levels (up to 1024 pixels) run entirely in one
+// CTA with their state in shared memory; larger levels run 8 half-sweeps per launch, temporally blocked in
 // shared memory (a tile plus an 8-pixel halo), which gives the same bits as
 // 8 global half-sweeps.
 #include <math.h>
@@ -343,7 +342,9 @@ constexpr int TB_W = 32, TB_H = 16, TB_S = 8;
 constexpr int TB_LW = TB_W + 2 * TB_S, TB_LH = TB_H + 2 * TB_S, TB_LN = TB_LW * TB_LH;
 constexpr size_t TB_SMEM = (size_t)TB_LN * 10 * sizeof(float);
 
-__global__ void __launch_bounds__(256) k_df_sor_tb(DfLevel L, DfConst k, int start_color, int S, float* __restrict__ out_du,
+constexpr int TB_THREADS = 1024;                  // a tile's half-sweep is short: many threads, short latency
+
+__global__ void __launch_bounds__(TB_THREADS) k_df_sor_tb(DfLevel L, DfConst k, int start_color, int S, float* __restrict__ out_du,
                                                    float* __restrict__ out_dv) {
     extern __shared__ __align__(16) float sm[];
     float* sdu = sm;
@@ -422,8 +423,13 @@ __global__ void k_df_update(float* __restrict__ u, float* __restrict__ v, const 
 // n_sor red-black sweeps) with block barriers between the passes, then
 // w += dw.  The same per-pixel arithmetic as the multi-launch path.
 constexpr int DF_SMALL_THREADS = 1024;
-constexpr int DF_SMALL_MAX = 5120;              // pixels: 10 x 4 B x 5120 = 200 KB of shared memory
+// Pixels of a level solved by one CTA: above about a thousand pixels a single
+// SM is slower than the blocked launches (1024x436 pair: 43.0 ms with 5120
+// and 256-thread blocked CTAs, 39.4 ms with 1024 and 1024 threads).  At most
+// 5120 (200 KB of shared memory).
+constexpr int DF_SMALL_MAX = 1024;
 constexpr size_t DF_SMALL_SMEM = (size_t)DF_SMALL_MAX * 10 * sizeof(float);
+static_assert(DF_SMALL_MAX <= 5120, "small-level state must fit shared memory");
 
 __global__ void __launch_bounds__(DF_SMALL_THREADS) k_df_level_small(DfLevel L, DfConst k, int n_fixed, int n_sor) {
     extern __shared__ __align__(16) float sm[];
@@ -635,7 +641,7 @@ cudaError_t dm_launch_deepflow(const DmFlowPlan& q, const DmTaps& taps, const fl
                 launches++;
                 for (int j = 0; j < 2 * q.n_sor; j += TB_S) {
                     const int S = 2 * q.n_sor - j < TB_S ? 2 * q.n_sor - j : TB_S;
-                    k_df_sor_tb<<<tiles, 256, TB_SMEM, st>>>(L, k, j & 1, S, alt_u, alt_v);
+                    k_df_sor_tb<<<tiles, TB_THREADS, TB_SMEM, st>>>(L, k, j & 1, S, alt_u, alt_v);
                     launches++;
                     float* t = L.du; L.du = alt_u; alt_u = t;
                     t = L.dv; L.dv = alt_v; alt_v = t;
