@@ -14,6 +14,15 @@
  *                         verification (Eq. 16)
  *   dm_match              all of the above
  *
+ * and the paper's extensions built on them:
+ *
+ *   dm_prototypes, dm_correlate_pyramid_approx   approximate form (Sec. 4.1)
+ *   dm_match_invariant    scale and rotation invariant form (Sec. 4.2, Algorithm 2)
+ *   dm_match_star, dm_backtrack_star             DM*, the earlier backtracking (Sec. 5.3)
+ *   dm_deepflow           DeepFlow, the variational flow fed by the matches (Sec. 4.3)
+ *   dm_loss_grad          differentiable form (a loss the paper does not define)
+ *   dm_match_batch        many pairs in concurrent lanes (CUDA-graph capturable)
+ *
  * Conventions shared by every call:
  *   - Pointers named d_* are CUDA device pointers on the context's device;
  *     h_* are host pointers.  The caller owns every buffer and the stream; the
