@@ -313,7 +313,7 @@ dm_status dm_match_invariant(dm_ctx* ctx, const float* d_img1, int W1, int H1, c
 dm_status dm_read_status(dm_ctx* ctx, const void* d_ws, int* status, long long* reached, int n_reached,
                          void* stream);
 
-/* Differentiable form (the paper defines no loss; see the design notes).
+/* Differentiable form (the paper defines no loss; this one is the sum of the top-level maxima).
  * loss = sum over the existing top-level patches p of max_q C_L(p, q) (first
  * maximum), for the pyramid `pyr` built by dm_correlate_pyramid from d_desc1 /
  * d_desc2 (which must be unchanged).  Writes *d_loss (device float; summed in

@@ -1,8 +1,8 @@
 """Pins of the CPU oracle against what the paper and the mathematics fix.
 
 Each test checks the oracle against something other than itself: brute force
-on tiny inputs, closed forms, invariants, special cases.  Numbering follows the
-pin list in the design notes (P1..P11).
+on tiny inputs, closed forms, invariants, special cases (numbered P1..P11 in
+the test names).
 """
 import math
 
