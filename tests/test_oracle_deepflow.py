@@ -158,3 +158,13 @@ def test_pyramid_sizes_and_affine_resampling():
     # d is affine where its own samples were not clamped: columns <= 46, rows <= 36
     inner = inside & (xs <= 45) & (ys <= 35)
     np.testing.assert_allclose(up[inner], want[inner], rtol=0, atol=1e-9)
+
+
+def test_fp32_mirror_close_to_fp64():
+    """The FP32 mirror follows the FP64 definition closely on a translated texture
+    (the two differ only by rounding)."""
+    x, y = _grid(48, 40)
+    I1, I2 = _tex(x, y), _tex(x - 0.8, y + 0.4)
+    u64, v64 = oracle.deepflow(I1, I2, None, "f64")
+    u32, v32 = oracle.deepflow(I1, I2, None, "f32")
+    assert np.abs(u64 - u32).max() < 1e-3 and np.abs(v64 - v32).max() < 1e-3

@@ -166,3 +166,16 @@ def test_end_term_is_the_rectified_atomic_correlation(prec):
         st = np.array(sorted(starts))
         for (c, ty, tx), e in zip(keys, ends):
             assert np.min(np.abs(st - (leaves[(c, ty, tx)] - e))) <= 1e-12
+
+
+def test_fp32_mirror_agrees_with_fp64():
+    """DM* in the FP32 mirror and in FP64 choose the same matches on most patches
+    (they differ only where rounding flips a decision) with close scores."""
+    pr = synth.make_pair_smooth(48, 40, seed=17, max_disp=3.0)
+    m64 = oracle.dmstar_match(pr.img1, pr.img2, "f64")
+    m32 = oracle.dmstar_match(pr.img1, pr.img2, "f32")
+    k64 = {(r[0], r[1]): r for r in m64}
+    same = [r for r in m32 if (r[0], r[1]) in k64 and tuple(k64[(r[0], r[1])][2:4]) == tuple(r[2:4])]
+    assert len(same) >= 0.9 * len(m64)
+    for r in same:
+        assert abs(r[4] - k64[(r[0], r[1])][4]) < 1e-5
