@@ -69,3 +69,17 @@ def test_quarter_turn_is_recovered():
     inv = oracle.invariant_match(img1, img2, "f32")
     assert _consistent_with_quarter_turn(inv, W) >= 0.7
     assert _consistent_with_quarter_turn(exact, W) <= 0.3
+
+
+def test_fp32_mirror_agrees_with_fp64():
+    """The invariant chain in the FP32 mirror and in FP64 choose the same matches
+    on most patches (FP32 rounds the warp coordinates, so a few rectified pixels
+    may move by one)."""
+    W, H = 40, 32
+    img1 = synth.make_pair_smooth(W, H, seed=23, max_disp=1.0).img1
+    img2 = np.ascontiguousarray(np.rot90(img1, 1))
+    m64 = oracle.invariant_match(img1, img2, "f64")
+    m32 = oracle.invariant_match(img1, img2, "f32")
+    k64 = {(r[0], r[1]): tuple(r[2:4]) for r in m64}
+    agree = np.mean([k64.get((r[0], r[1])) == tuple(r[2:4]) for r in m32])
+    assert agree >= 0.85, agree
