@@ -587,6 +587,95 @@ def test_p11_descriptor_closed_forms(oracle_mod):
 
 
 # --------------------------------------------------------------------------- #
+# P11b: the three Gaussian smoothings of the descriptor (Sec. 3.2, "radius"   #
+# nu read as the standard deviation), pinned by the moments of a Gaussian      #
+# --------------------------------------------------------------------------- #
+# A vertical step edge isolates one smoothing.  With only nu1 active, channel 0
+# (direction (1, 0)) before the sigmoid is max(0, gx) of the smoothed step:
+# the central difference turns the step into two equal impulses at x0 - 1 and
+# x0, so the profile along x is (h * 255 / 2) (w * [1, 1]) for the smoothing
+# kernel w.  With only nu2 active the same two impulses are smoothed after the
+# projection; with only nu3 active they pass the sigmoid first, then are
+# smoothed.  The descriptor's ratio d_0 / d_8 = o_0 / mu gives o_0 back, and
+# the sigmoid 2 / (1 + exp(-s x)) - 1 = tanh(s x / 2) is inverted where it
+# comes first.  Normalised to unit mass, the profile of a Gaussian of std nu
+# convolved with the two-tap box has mean x0 - 1/2 and variance nu^2 + 1/4;
+# truncation of a Gaussian at z standard deviations (renormalised) lowers its
+# variance by the factor 1 - 2 z phi(z) / (2 Phi(z) - 1), at most 2.7 % for
+# z >= 3.  Two smoothings in a row are one of std sqrt(2) nu.
+def _gauss_trunc_var_deficit(z):
+    phi = math.exp(-0.5 * z * z) / math.sqrt(2 * math.pi)
+    Phi2 = math.erf(z / math.sqrt(2))                  # 2 Phi(z) - 1
+    return 2 * z * phi / Phi2
+
+
+def _edge_profile(oracle_mod, which, nu, x0=40, W=96, H=9, h=0.2, slope=0.2, mu=0.3):
+    img = np.zeros((H, W), np.float32)
+    img[:, x0:] = h
+    h = float(np.float32(h))                          # the step the oracle sees
+    cfg = dict(nu1=0.0, nu2=0.0, nu3=0.0, slope=slope, mu=mu)
+    for k in which:
+        cfg[k] = nu
+    d = oracle_mod.descriptors(img, "f64", **cfg)
+    o0 = mu * d[H // 2, :, 0] / d[H // 2, :, 8]
+    if "nu3" in which:                                # sigmoid before this smoothing
+        prof = o0 / (2.0 * math.tanh(slope * 255.0 * h / 4.0))
+    else:
+        prof = (2.0 * np.arctanh(o0) / slope) / (255.0 * h)
+    return prof
+
+
+@pytest.mark.parametrize("which", [("nu1",), ("nu2",), ("nu3",)])
+@pytest.mark.parametrize("nu", [1.0, 1.5, 2.3])
+def test_p11b_descriptor_smoothing_is_gaussian(oracle_mod, which, nu):
+    x0 = 40
+    prof = _edge_profile(oracle_mod, which, nu, x0=x0)
+    x = np.arange(len(prof), dtype=np.float64)
+    R = math.ceil(3 * nu)
+    # support: the kernel reaches exactly ceil(3 nu) pixels (the box adds one)
+    inside = (x >= x0 - 1 - R) & (x <= x0 + R)
+    assert np.all(prof[inside] > 0), prof[inside]
+    assert np.all(prof[~inside] == 0.0)
+    # unit mass, symmetric about the edge
+    np.testing.assert_allclose(prof.sum(), 1.0, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(prof[x0:x0 + R + 1], prof[x0 - 1 - R:x0][::-1], rtol=0, atol=1e-13)
+    mean = float((x * prof).sum())
+    assert abs(mean - (x0 - 0.5)) < 1e-12
+    # second moment: nu^2 (std nu) within the truncation deficit, plus the box's 1/4
+    var = float(((x - mean) ** 2 * prof).sum()) - 0.25
+    deficit = _gauss_trunc_var_deficit(3.0)
+    assert nu * nu * (1 - deficit) - 1e-9 <= var <= nu * nu * (1 + 1e-6), (var, nu * nu)
+    # the two readings this excludes: sigma = nu / 2, or taps cut at +-nu
+    assert abs(var - nu * nu / 4) > 0.3 * nu * nu
+    assert abs(var - nu * nu * (1 - _gauss_trunc_var_deficit(1.0))) > 0.3 * nu * nu
+
+
+@pytest.mark.parametrize("nu", [1.0, 1.5])
+def test_p11b_two_smoothings_compose(oracle_mod, nu):
+    """nu1 then nu2 on the edge: one Gaussian of std sqrt(2) nu (up to truncation)."""
+    x0 = 40
+    prof = _edge_profile(oracle_mod, ("nu1", "nu2"), nu, x0=x0)
+    x = np.arange(len(prof), dtype=np.float64)
+    R = math.ceil(3 * nu)
+    assert np.all(prof[x0 - 1 - 2 * R:x0 + 2 * R + 1] > 0)
+    assert np.all(prof[:x0 - 1 - 2 * R] == 0.0) and np.all(prof[x0 + 2 * R + 1:] == 0.0)
+    np.testing.assert_allclose(prof.sum(), 1.0, rtol=0, atol=1e-12)
+    mean = float((x * prof).sum())
+    var = float(((x - mean) ** 2 * prof).sum()) - 0.25
+    deficit = _gauss_trunc_var_deficit(3.0)
+    assert 2 * nu * nu * (1 - deficit) - 1e-9 <= var <= 2 * nu * nu * (1 + 1e-6), (var, 2 * nu * nu)
+    # and the profile is close to the single smoothing of std sqrt(2) nu convolved with the box
+    t = np.arange(-4 * R, 4 * R + 1, dtype=np.float64)
+    g = np.exp(-t * t / (4 * nu * nu))
+    g /= g.sum()
+    want = np.zeros_like(prof)
+    for off in (0, -1):
+        idx = (x0 + off + t).astype(int)
+        want[idx] += 0.5 * g
+    assert np.abs(prof - want).sum() < 0.02
+
+
+# --------------------------------------------------------------------------- #
 # Own FP32 elementary functions: accuracy against FP64                         #
 # --------------------------------------------------------------------------- #
 def test_own_pow_exp_accuracy(oracle_mod):
