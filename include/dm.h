@@ -407,7 +407,13 @@ dm_status dm_set_tuned_config(dm_ctx* ctx, int W1, int H1, int W2, int H2, const
  *     (32 MiB holds pairs up to about 160 x 120 pixels).
  *   - It calls no cudaMalloc, cudaFree or other allocating routine.  Its first
  *     call on a device looks up the array's device address (cudaGetSymbolAddress)
- *     and caches it; make that first call before any stream capture.
+ *     and caches it; make that first call before any stream capture.  Under
+ *     CUDA's lazy module loading (the default) that first look-up is also when
+ *     the driver loads this part of the library and reserves the array, which
+ *     can synchronise the device and fails (DM_ECUDA) if the application has
+ *     already taken all device memory: make the first call at start-up, before
+ *     the application claims the rest of the memory.  A context whose device
+ *     cannot be made current gets DM_ECUDA before anything is looked up.
  *   - Every call uses the same array and leaves its contents behind; each call
  *     clears what must start empty.  Calls that overlap on the GPU (other
  *     streams, other threads) race on the array: serialise them.

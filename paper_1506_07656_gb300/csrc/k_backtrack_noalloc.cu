@@ -41,12 +41,20 @@ cudaError_t scratch_address(int device, void** out) {
     return cudaSuccess;
 }
 
+// Makes `d` the current device for the scope of one call and restores the
+// previous one; ok() is false when `d` could not be made current.
 struct DeviceScope {
     int prev = -1;
     bool changed = false;
+    cudaError_t err = cudaSuccess;
     explicit DeviceScope(int d) {
-        if (cudaGetDevice(&prev) == cudaSuccess && prev != d) changed = (cudaSetDevice(d) == cudaSuccess);
+        err = cudaGetDevice(&prev);
+        if (err == cudaSuccess && prev != d) {
+            err = cudaSetDevice(d);
+            changed = err == cudaSuccess;
+        }
     }
+    bool ok() const { return err == cudaSuccess; }
     ~DeviceScope() {
         if (changed) cudaSetDevice(prev);
     }
@@ -68,6 +76,12 @@ extern "C" dm_status dm_backtrack_noalloc(dm_ctx* ctx, const dm_pyramid* pyr, dm
         return dm_set_error(ctx, DM_ENOMEM, msg.c_str());
     }
     DeviceScope scope(dm_ctx_device(ctx));
+    if (!scope.ok()) {
+        // the array's address must be taken with the context's device current
+        std::string msg = std::string("dm_backtrack_noalloc: cannot make the context's device current: ") +
+                          cudaGetErrorString(scope.err);
+        return dm_set_error(ctx, DM_ECUDA, msg.c_str());
+    }
     void* scratch = nullptr;
     cudaError_t e = scratch_address(dm_ctx_device(ctx), &scratch);
     if (e != cudaSuccess) {

@@ -13,7 +13,7 @@
 // This pass streams the pooled maps of the level below and does a fixed
 // amount of arithmetic per stored output (~4 averages of 4 values, a 9-way
 // max with argmax, one power).  A CTA owns a tile of 32 x TH pooled outputs
-// (TH = 16 or 8, autotuned) of a run of up to 8 lattice patches on one row,
+// (TH = 16 or 8, autotuned) of a run of up to 16 lattice patches on one row,
 // spaced so that the right child column of one patch is the left child column
 // of the next: the child windows (72 x (2 TH + 1) floats, which cover both
 // shifts +-1 of a shared column) are staged in shared memory by 3-D TMA tensor
