@@ -111,7 +111,9 @@ dm_status dm_destroy(dm_ctx* ctx);
 const char* dm_last_error(const dm_ctx* ctx);
 
 /* Geometry of the method for a pair of sizes (Sec. 3.2 and Algorithm 1):
- *   *L        number of aggregation iterations, min{l : 4*2^l >= max(W1,H1)}
+ *   *L        top level: min{l : 4*2^l >= max(W1,H1)} (where Algorithm 1 stops),
+ *             lowered to the highest level at which image 1 has a patch (a wide,
+ *             low image has none at that level: e.g. 1242 x 375 gives 8, not 9)
  *   *n_patch0 atomic patches (centres 4k+2 inside I)
  *   *n_patch  lattice patches of levels >= 1 (centres in 4Z^2 inside I)
  *   dw, dh    (may be NULL) map domain of level l = 0..L+1: ceil(W2/2^l) x ceil(H2/2^l)

@@ -15,6 +15,8 @@ Functions and the passages they follow:
   descriptors()   Sec. 3.2 "Pixel descriptor"; defaults of Sec. 5.2
   level0()        Eq. 3-4 (unpooled, unrectified bottom-level maps)
   level1_pooled() Eq. 3-12 for sampled lattice patches of level 1
+  levels_sampled() Eq. 3-12 for sampled patches of any level below the top
+  valid_flags()   Eq. 7 with the boundary rule: patch existence per level
   pyramid()       Algorithm 1 with Eq. 5-12 and the boundary rule of Sec. 3.2
   backtrack()     Eq. 13-15 (merge by highest score)
   reciprocal()    Eq. 16
@@ -180,6 +182,45 @@ def level1_pooled(d1: np.ndarray, d2: np.ndarray, patches, prec: str = "f32", la
                                len(pl), _ptr(out), _ptr(am), _ptr(ex))
     if rc != 0:
         raise ValueError("level1_pooled oracle failed")
+    return out, am, ex
+
+
+def valid_flags(W1: int, H1: int, W2: int, H2: int) -> list:
+    """Existence of every patch at every level l = 0..L (Eq. 7 with the
+    boundary rule of Sec. 3.2): a list of uint8 arrays [npatch(l)]."""
+    g = geometry(W1, H1, W2, H2)
+    out = [np.zeros(g.npatch(l), dtype=np.uint8) for l in range(g.L + 1)]
+    vv = (C.c_void_p * (g.L + 1))(*[a.ctypes.data for a in out])
+    lib = _lib("f64")
+    lib.orc_valid.argtypes = [C.c_int] * 4 + [C.c_void_p]
+    if lib.orc_valid(W1, H1, W2, H2, vv) != 0:
+        raise ValueError("valid oracle failed")
+    return out
+
+
+def levels_sampled(d1: np.ndarray, d2: np.ndarray, level: int, patches, prec: str = "f32",
+                   lam: float = DEFAULT_CFG["lam"], compensated: bool = True):
+    """Pooled, rectified maps, argmax codes and existence of the listed
+    patches of one level l < L, computed from their atomic descendants only
+    (the same arithmetic as pyramid(); for sampled checks of pairs too large
+    for the whole pyramid).  Returns (maps [n][dh[l+1]][dw[l+1]], codes, exists)."""
+    dt = _dtype(prec)
+    d1 = np.ascontiguousarray(d1, dtype=dt)
+    d2 = np.ascontiguousarray(d2, dtype=dt)
+    H1, W1, _ = d1.shape
+    H2, W2, _ = d2.shape
+    g = geometry(W1, H1, W2, H2)
+    pl = np.ascontiguousarray(np.asarray(patches, dtype=np.int32))
+    out = np.zeros((len(pl), g.dh[level + 1], g.dw[level + 1]), dtype=dt)
+    am = np.zeros(out.shape, dtype=np.uint8)
+    ex = np.zeros(len(pl), dtype=np.uint8)
+    lib = _lib(prec)
+    lib.orc_levels_sampled.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_double,
+                                       C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+    rc = lib.orc_levels_sampled(_ptr(d1), W1, H1, _ptr(d2), W2, H2, float(lam), int(bool(compensated)), int(level),
+                                _ptr(pl), len(pl), _ptr(out), _ptr(am), _ptr(ex))
+    if rc != 0:
+        raise ValueError("levels_sampled oracle failed")
     return out, am, ex
 
 

@@ -44,7 +44,11 @@
  *       in-domain positions; a child sample outside the domain contributes 0.
  *   - argmax = first strict maximum, scan order m_y = -1..1 then m_x = -1..1;
  *       ties in BestAt/BestAt': higher score, then lower index.
- *   - L = min{l : 4*2^l >= max(W,H)} (image 1); entries = all top positions.
+ *   - L = min{l : 4*2^l >= max(W,H)} (image 1), the level at which Algorithm 1's
+ *       loop stops; when image 1 has no patch at that level (a wide, low image:
+ *       every child of level l lies 2^l px away, above and below), the top is
+ *       the highest level that has a patch, the top of the pyramid the loop
+ *       returns; entries = all top positions.
  *   - path score = top value + pooled values along the path, summed top-down
  *       (FP32 mirror: exact fixed-point sum, see the path-score helpers).
  *   - BestAt / BestAt' over aligned 4x4 cells (the atomic patch in I, the cell
@@ -89,6 +93,28 @@ typedef struct {
 
 static int ceil_half(int v) { return (v + 1) / 2; }
 
+/* Along one axis: does some lattice column (row) hold a patch of level l?
+ * n0 atomic columns (all exist), n lattice columns; the children of lattice
+ * column i are atomic columns i-1, i at level 1 and lattice columns i -+
+ * 2^(l-2) at level l >= 2. */
+static int axis_has_patch(int n0, int n, int l) {
+    uint8_t* a = (uint8_t*)malloc((size_t)n);
+    uint8_t* b = (uint8_t*)malloc((size_t)n);
+    int any = 0;
+    if (a && b) {
+        for (int i = 0; i < n; i++) a[i] = (uint8_t)((i - 1 >= 0 && i - 1 < n0) || i < n0);
+        for (int k = 2; k <= l; k++) {
+            int s = 1 << (k - 2);
+            for (int i = 0; i < n; i++) b[i] = (uint8_t)((i - s >= 0 && a[i - s]) || (i + s < n && a[i + s]));
+            memcpy(a, b, (size_t)n);
+        }
+        for (int i = 0; i < n; i++) any |= a[i];
+    }
+    free(a);
+    free(b);
+    return any;
+}
+
 static int make_geom(int W1, int H1, int W2, int H2, geom* g) {
     memset(g, 0, sizeof(*g));
     if (W1 < 4 || H1 < 4 || W2 < 1 || H2 < 1) return -1;
@@ -98,11 +124,17 @@ static int make_geom(int W1, int H1, int W2, int H2, geom* g) {
     long N = 4;
     while (N < mx) { N *= 2; L++; }
     if (L < 1 || L > ORC_MAXL) return -1;
-    g->L = L;
     g->P0x = (W1 - 3) / 4 + 1;
     g->P0y = (H1 - 3) / 4 + 1;
     g->Lx = (W1 - 1) / 4 + 1;
     g->Ly = (H1 - 1) / 4 + 1;
+    /* the highest level <= L with a patch: a patch exists iff one of its
+     * children does (Eq. 7, boundary rule), and since the four children are
+     * the combinations of two columns and two rows, existence is a column
+     * condition times a row condition -- check each axis on its own */
+    int top = L;
+    while (top > 1 && !(axis_has_patch(g->P0x, g->Lx, top) && axis_has_patch(g->P0y, g->Ly, top))) top--;
+    g->L = top;
     g->dw[0] = W2; g->dh[0] = H2;
     for (int l = 1; l <= L + 1; l++) { g->dw[l] = ceil_half(g->dw[l - 1]); g->dh[l] = ceil_half(g->dh[l - 1]); }
     return 0;
@@ -638,6 +670,167 @@ int orc_level1_pooled(const real* d1, int W1, int H1, const real* d2, int W2, in
         free(map);
     }
     return bad ? -2 : 0;
+}
+
+/* Existence of every patch at every level (Eq. 7 with the boundary rule of
+ * Sec. 3.2): valid[0] = all atomic patches; a lattice patch of level l exists
+ * iff one of its children exists.  valid[l]: [npatch(l)], l = 0..L. */
+int orc_valid(int W1, int H1, int W2, int H2, uint8_t** valid) {
+    geom g;
+    if (make_geom(W1, H1, W2, H2, &g)) return -1;
+    memset(valid[0], 1, (size_t)npatch(&g, 0));
+    for (int l = 1; l <= g.L; l++)
+        for (int p = 0; p < npatch(&g, l); p++) {
+            int any = 0;
+            for (int i = 0; i < 4; i++) {
+                int c = child_index(&g, l, p % g.Lx, p / g.Lx, i);
+                if (c >= 0 && valid[l - 1][c]) any = 1;
+            }
+            valid[l][p] = (uint8_t)any;
+        }
+    return 0;
+}
+
+/* Pooled maps and argmax codes at one level l (0 <= l < L) of the listed
+ * patches only, for checks of pairs too large for the whole pyramid: the
+ * level-0 maps of their atomic descendants (up to 4^l patches each), then
+ * levels 1..l for the descendants only, with the same arithmetic as
+ * orc_pyramid (level_average, pool_map).  out [n][dh[l+1]][dw[l+1]], am
+ * likewise; exists[k] = valid[l][plist[k]] (a patch that does not exist keeps
+ * a zero output). */
+int orc_levels_sampled(const real* d1, int W1, int H1, const real* d2, int W2, int H2, double lambda,
+                       int compensated, int l, const int* plist, int n, real* out, uint8_t* am, uint8_t* exists) {
+    geom g;
+    if (make_geom(W1, H1, W2, H2, &g)) return -1;
+    if (l < 0 || l >= g.L) return -1;
+    const real lam = (real)lambda;
+    int rc = 0;
+    uint8_t* valid[ORC_MAXL + 1];
+    uint8_t* need[ORC_MAXL + 1];
+    real** maps[ORC_MAXL + 1];
+    for (int k = 0; k <= l; k++) {
+        valid[k] = (uint8_t*)calloc((size_t)npatch(&g, k), 1);
+        need[k] = (uint8_t*)calloc((size_t)npatch(&g, k), 1);
+        maps[k] = (real**)calloc((size_t)npatch(&g, k), sizeof(real*));
+        if (!valid[k] || !need[k] || !maps[k]) rc = -2;
+    }
+    if (rc == 0) {
+        /* existence up to level l */
+        memset(valid[0], 1, (size_t)npatch(&g, 0));
+        for (int k = 1; k <= l; k++)
+            for (int p = 0; p < npatch(&g, k); p++) {
+                int any = 0;
+                for (int i = 0; i < 4; i++) {
+                    int c = child_index(&g, k, p % g.Lx, p / g.Lx, i);
+                    if (c >= 0 && valid[k - 1][c]) any = 1;
+                }
+                valid[k][p] = (uint8_t)any;
+            }
+        /* the descendants the listed patches need, level by level downwards */
+        for (int j = 0; j < n; j++) {
+            if (plist[j] < 0 || plist[j] >= npatch(&g, l)) { rc = -1; break; }
+            exists[j] = valid[l][plist[j]];
+            if (exists[j]) need[l][plist[j]] = 1;
+        }
+        for (int k = l; k >= 1 && rc == 0; k--)
+            for (int p = 0; p < npatch(&g, k); p++) {
+                if (!need[k][p]) continue;
+                for (int i = 0; i < 4; i++) {
+                    int c = child_index(&g, k, p % g.Lx, p / g.Lx, i);
+                    if (c >= 0 && valid[k - 1][c]) need[k - 1][c] = 1;
+                }
+            }
+    }
+    /* level 0: correlate, pool (and rectify) the needed atomic patches */
+    if (rc == 0) {
+        const int n0 = npatch(&g, 0);
+        const size_t sz = (size_t)g.dw[1] * g.dh[1];
+        for (int p = 0; p < n0; p++)
+            if (need[0][p]) {
+                maps[0][p] = (real*)malloc(sz * sizeof(real));
+                if (!maps[0][p]) rc = -2;
+            }
+        if (rc == 0) {
+#pragma omp parallel
+            {
+                real* map = (real*)malloc((size_t)W2 * H2 * sizeof(real));
+                uint8_t* am0 = (uint8_t*)malloc(sz);
+#pragma omp for schedule(dynamic, 1)
+                for (int p = 0; p < n0; p++) {
+                    if (!need[0][p] || !map || !am0) continue;
+                    int px = 4 * (p % g.P0x) + 2, py = 4 * (p / g.P0x) + 2;
+                    for (int ty = 0; ty < H2; ty++)
+                        for (int tx = 0; tx < W2; tx++) {
+                            real c = corr0(d1, W1, H1, d2, W2, H2, px, py, tx, ty);
+                            map[(size_t)ty * W2 + tx] = ORC_F32 ? c : RPOW(c, lam);
+                        }
+                    uint8_t* dst_am = (l == 0) ? NULL : am0;
+                    if (l == 0)
+                        for (int j = 0; j < n; j++)
+                            if (plist[j] == p) dst_am = am + (size_t)j * sz;
+                    pool_map(map, W2, H2, maps[0][p], dst_am ? dst_am : am0, NULL, g.dw[1], g.dh[1], ORC_F32, lam);
+                }
+                if (!map || !am0) {
+#pragma omp atomic write
+                    rc = -2;
+                }
+                free(map);
+                free(am0);
+            }
+        }
+    }
+    /* levels 1..l: shift-average of the children's pooled maps, pool, power */
+    for (int k = 1; k <= l && rc == 0; k++) {
+        const int mw = g.dw[k], mh = g.dh[k];
+        const size_t sz = (size_t)g.dw[k + 1] * g.dh[k + 1];
+        for (int p = 0; p < npatch(&g, k); p++)
+            if (need[k][p]) {
+                maps[k][p] = (real*)malloc(sz * sizeof(real));
+                if (!maps[k][p]) rc = -2;
+            }
+        if (rc) break;
+#pragma omp parallel
+        {
+            real* map = (real*)malloc((size_t)mw * mh * sizeof(real));
+            uint8_t* amk = (uint8_t*)malloc(sz);
+#pragma omp for schedule(dynamic, 1)
+            for (int p = 0; p < npatch(&g, k); p++) {
+                if (!need[k][p] || !map || !amk) continue;
+                int nk = 0;
+                const real* kid[4];
+                for (int i = 0; i < 4; i++) {
+                    int c = child_index(&g, k, p % g.Lx, p / g.Lx, i);
+                    kid[i] = (c >= 0 && valid[k - 1][c]) ? maps[k - 1][c] : NULL;
+                    if (kid[i]) nk++;
+                }
+                level_average(kid, nk, mw, mh, compensated, lam, map);
+                uint8_t* dst_am = amk;
+                if (k == l)
+                    for (int j = 0; j < n; j++)
+                        if (plist[j] == p) dst_am = am + (size_t)j * sz;
+                pool_map(map, mw, mh, maps[k][p], dst_am, NULL, g.dw[k + 1], g.dh[k + 1], ORC_F32, lam);
+            }
+            if (!map || !amk) {
+#pragma omp atomic write
+                rc = -2;
+            }
+            free(map);
+            free(amk);
+        }
+    }
+    if (rc == 0) {
+        const size_t sz = (size_t)g.dw[l + 1] * g.dh[l + 1];
+        for (int j = 0; j < n; j++)
+            if (exists[j]) memcpy(out + (size_t)j * sz, maps[l][plist[j]], sz * sizeof(real));
+    }
+    for (int k = 0; k <= l; k++) {
+        if (maps[k])
+            for (int p = 0; p < npatch(&g, k); p++) free(maps[k][p]);
+        free(maps[k]);
+        free(valid[k]);
+        free(need[k]);
+    }
+    return rc;
 }
 
 /* ------------------------------------------------------------------------- */

@@ -254,6 +254,24 @@ int dm_ctx_device(const dm_ctx* ctx) { return ctx->device; }
 // ---------------------------------------------------------------------------
 // Geometry and layouts
 // ---------------------------------------------------------------------------
+// Along one axis of image 1 (n_atomic atomic columns, n_lattice lattice
+// columns): does some lattice column hold a patch of level l?  Level-1 column c
+// has the atomic children c - 1 and c; level l >= 2 column c the level-(l-1)
+// children c - 2^(l-2) and c + 2^(l-2).
+static bool dm_axis_level_exists(int n_atomic, int n_lattice, int l) {
+    std::vector<char> cur(n_lattice), nxt(n_lattice);
+    for (int c = 0; c < n_lattice; c++) cur[c] = (c < n_atomic) || (c >= 1 && c - 1 < n_atomic);
+    for (int k = 2; k <= l; k++) {
+        const int d = 1 << (k - 2);
+        for (int c = 0; c < n_lattice; c++)
+            nxt[c] = (c >= d && cur[c - d]) || (c + d < n_lattice && cur[c + d]);
+        cur.swap(nxt);
+    }
+    for (char v : cur)
+        if (v) return true;
+    return false;
+}
+
 int dm_make_geom(int W1, int H1, int W2, int H2, DmGeom* g) {
     memset(g, 0, sizeof(*g));
     if (W1 < 4 || H1 < 4 || W2 < 1 || H2 < 1) return -1;
@@ -264,13 +282,20 @@ int dm_make_geom(int W1, int H1, int W2, int H2, DmGeom* g) {
     long long N = 4;
     while (N < mx) { N *= 2; L++; }
     if (L < 1) return -1;
-    if (L > DM_MAXL) return -2;
-    if (L > 14) return -2;   // fixed-point path scores: L + 1 terms below 2^28 each fit 32 bits
-    g->L = L;
     g->P0x = (W1 - 3) / 4 + 1;
     g->P0y = (H1 - 3) / 4 + 1;
     g->Lx = (W1 - 1) / 4 + 1;
     g->Ly = (H1 - 1) / 4 + 1;
+    // Algorithm 1 stops at the first N = 4 * 2^L >= max(W1, H1); if image 1 has
+    // no patch at that level (a wide, low image whose level-L children all lie
+    // 2^L px above and below every lattice point), the pyramid's top is the
+    // highest level that has one.  A patch exists iff a child does (Eq. 7 with
+    // the boundary rule); the children are two columns times two rows, so a
+    // level has a patch iff some column and some row qualify on their own.
+    while (L > 1 && !(dm_axis_level_exists(g->P0x, g->Lx, L) && dm_axis_level_exists(g->P0y, g->Ly, L))) L--;
+    if (L > DM_MAXL) return -2;
+    if (L > 14) return -2;   // fixed-point path scores: L + 1 terms below 2^28 each fit 32 bits
+    g->L = L;
     g->dw[0] = W2; g->dh[0] = H2;
     for (int l = 1; l <= L + 1; l++) { g->dw[l] = (g->dw[l - 1] + 1) / 2; g->dh[l] = (g->dh[l - 1] + 1) / 2; }
     // merge keys patch * |domain| + position must fit 32 bits (levels 1..L-1);

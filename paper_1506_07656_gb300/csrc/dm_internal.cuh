@@ -15,7 +15,7 @@
 // Geometry of one image pair (Sec. 3.2 "Bottom level", Eq. 7, Algorithm 1).
 struct DmGeom {
     int W1, H1, W2, H2;
-    int L;              // aggregation iterations: min{l : 4*2^l >= max(W1,H1)}
+    int L;              // top level: min{l : 4*2^l >= max(W1,H1)}, lowered to the highest level with a patch
     int P0x, P0y;       // atomic grid: centres 4k+2 <= W1-1
     int Lx, Ly;         // lattice 4Z^2 inside I: patches of levels >= 1
     int dw[DM_MAXL + 2], dh[DM_MAXL + 2];  // map domain of level l

@@ -40,7 +40,9 @@ def test_library_exports_every_declared_symbol(lib):
 def test_geometry_matches_oracle(lib, oracle_mod):
     from paper_1506_07656_gb300 import dm
     for (W1, H1, W2, H2) in [(64, 48, 64, 48), (37, 29, 41, 23), (1024, 436, 1024, 436), (1242, 375, 1242, 375),
-                             (512, 224, 512, 224), (5, 4, 1, 1), (320, 240, 320, 240), (7, 5, 3, 2)]:
+                             (512, 224, 512, 224), (5, 4, 1, 1), (320, 240, 320, 240), (7, 5, 3, 2),
+                             (621, 188, 621, 188), (80, 20, 80, 20), (20, 80, 20, 80), (256, 112, 300, 90),
+                             (5, 100, 5, 100), (130, 70, 130, 70)]:
         a = dm.dm_geometry(W1, H1, W2, H2)
         b = oracle_mod.geometry(W1, H1, W2, H2)
         assert a["L"] == b.L and a["n_patch0"] == b.P0x * b.P0y and a["n_patch"] == b.Lx * b.Ly

@@ -4,8 +4,11 @@ bench times.  The oracle cannot produce the whole pyramid of such a pair in
 seconds, so sampled outputs are checked one by one and the rest by properties
 that hold at any size.
 
-FP32 path: the level-0 and level-1 pooled maps and argmax codes of sampled
-patches are bit-exact with the FP32 oracle; every stored level value lies in
+FP32 path: the pooled maps and argmax codes of sampled patches of levels 0
+to 3 are bit-exact with the FP32 oracle (which builds a level-l map from the
+4^l atomic descendants of the patch); the existence of every patch at every
+level, including the top-level patches that drop out for lack of a child
+(reading c8), equals the oracle's; every stored level value lies in
 [0, 1]; the matches are well formed (at most one per atomic patch, centres on
 the atomic grid, targets inside I', scores in (0, L+1]).  BF16 path: the same
 sampled level-0 maps are within the BF16 tolerance of the FP32 oracle, and its
@@ -33,7 +36,7 @@ def env(oracle_mod):
     return torch, dm, pr, d1, d2
 
 
-def _run(torch, dm, precision, d1, d2, patches0, patches1, pr):
+def _run(torch, dm, precision, d1, d2, samples, pr):
     ctx = dm.Context(precision)
     vmax = 1.0 + (1e-6 if precision == dm.DM_FP32 else 2e-2)   # BF16/FP8 operands can push C0 a little past 1
     try:
@@ -45,15 +48,16 @@ def _run(torch, dm, precision, d1, d2, patches0, patches1, pr):
         h = dm.dm_correlate_pyramid(ctx.ctx, t1, t2, ws)
         torch.cuda.synchronize()
         g = dm.dm_geometry(W, H, W, H)
-        lv0 = dm.read_level(ws, dm.dm_pyramid_level(h, 0), patches0)
-        lv1 = dm.read_level(ws, dm.dm_pyramid_level(h, 1), patches1)
-        # every stored level value in [0, 1] (sampled rows of every level, on the device)
+        lv = {l: dm.read_level(ws, dm.dm_pyramid_level(h, l), sel) for l, sel in samples.items()}
+        valid = []
+        # every stored level value in [0, 1] (all rows of every level, on the device)
         for l in range(g["L"] + 1):
             info = dm.dm_pyramid_level(h, l)
             base = ws.data_ptr()
             n, mh, pitch = info["n"], info["mh"], info["pitch"]
             v = ws[info["vals"] - base:info["vals"] - base + n * mh * pitch * 4].view(torch.float32)
             assert float(v.min()) >= 0.0 and float(v.max()) <= vmax, l
+            valid.append(ws[info["valid"] - base:info["valid"] - base + n].cpu().numpy())
         wsb = torch.empty(sizes["backtrack"], dtype=torch.uint8, device="cuda")
         out = torch.zeros((g["n_patch0"], 5), dtype=torch.float32, device="cuda")
         cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
@@ -61,17 +65,23 @@ def _run(torch, dm, precision, d1, d2, patches0, patches1, pr):
         st, _ = dm.dm_read_status(ctx.ctx, wsb, 1)
         n = int(cnt.item())
         dm.dm_pyramid_free(h)
-        return lv0, lv1, out[:n].cpu().numpy().astype(np.float64), st, g
+        return lv, valid, out[:n].cpu().numpy().astype(np.float64), st, g
     finally:
         ctx.close()
         torch.cuda.empty_cache()
 
 
 def _samples(g):
+    """Sampled patches per level: 12 atomic patches, 5 of level 1, and two each
+    of levels 2 and 3 (16 and 64 atomic descendants), one of them at the right
+    border of the lattice."""
     rng = np.random.default_rng(3)
-    p0 = np.sort(rng.choice(g["n_patch0"], size=12, replace=False))
-    p1 = np.sort(rng.choice(g["n_patch"], size=5, replace=False))
-    return p0, p1
+    s = {0: np.sort(rng.choice(g["n_patch0"], size=12, replace=False)),
+         1: np.sort(rng.choice(g["n_patch"], size=5, replace=False))}
+    Lx = (W - 1) // 4 + 1
+    s[2] = np.sort(np.append(rng.choice(g["n_patch"], size=1), 37 * Lx + Lx - 1))
+    s[3] = np.sort(rng.choice(g["n_patch"], size=2, replace=False))
+    return s
 
 
 def _check_matches(m, g):
@@ -86,16 +96,19 @@ def _check_matches(m, g):
 def test_fp32_full_size_sampled_bit_exact(env, oracle_mod):
     torch, dm, pr, d1, d2 = env
     g = dm.dm_geometry(W, H, W, H)
-    p0, p1 = _samples(g)
-    (v0, a0, _), (v1, a1, e1), m, st, _ = _run(torch, dm, dm.DM_FP32, d1, d2, p0, p1, pr)
-    w0, b0 = oracle_mod.level0_pooled(d1, d2, p0, "f32")
-    np.testing.assert_array_equal(v0, w0)
-    np.testing.assert_array_equal(a0, b0)
-    w1, b1, x1 = oracle_mod.level1_pooled(d1, d2, p1, "f32")
-    np.testing.assert_array_equal(e1, x1)
-    keep = x1.astype(bool)
-    np.testing.assert_array_equal(v1[keep], w1[keep])
-    np.testing.assert_array_equal(a1[keep], b1[keep])
+    samples = _samples(g)
+    lv, valid, m, st, _ = _run(torch, dm, dm.DM_FP32, d1, d2, samples, pr)
+    vf = oracle_mod.valid_flags(W, H, W, H)
+    for l in range(g["L"] + 1):
+        np.testing.assert_array_equal(valid[l], vf[l], err_msg=f"existence, level {l}")
+    assert not vf[g["L"]].all()                                 # some top-level patches drop out (c8)
+    for l, sel in samples.items():
+        want, codes, ex = oracle_mod.levels_sampled(d1, d2, l, sel, "f32")
+        v, a, e = lv[l]
+        np.testing.assert_array_equal(e, ex)
+        keep = ex.astype(bool)
+        np.testing.assert_array_equal(v[keep], want[keep], err_msg=f"level {l} values")
+        np.testing.assert_array_equal(a[keep], codes[keep], err_msg=f"level {l} codes")
     assert st == 0
     _check_matches(m, g)
 
@@ -103,15 +116,16 @@ def test_fp32_full_size_sampled_bit_exact(env, oracle_mod):
 def test_bf16_full_size_sampled_within_tolerance(env, oracle_mod):
     torch, dm, pr, d1, d2 = env
     g = dm.dm_geometry(W, H, W, H)
-    p0, p1 = _samples(g)
-    (v0, a0, _), _, m16, st, _ = _run(torch, dm, dm.DM_BF16, d1, d2, p0, p1, pr)
-    w0, b0 = oracle_mod.level0_pooled(d1, d2, p0, "f32")
+    s = _samples(g)
+    lv, _, m16, st, _ = _run(torch, dm, dm.DM_BF16, d1, d2, {0: s[0]}, pr)
+    v0, a0, _ = lv[0]
+    w0, b0 = oracle_mod.level0_pooled(d1, d2, s[0], "f32")
     rel = np.abs(v0 - w0) / np.maximum(np.abs(w0), 1e-30)
     assert rel.max() <= 1e-2, rel.max()
     assert np.mean(a0 == b0) >= 0.9
     assert st == 0
     _check_matches(m16, g)
-    _, _, m32, _, _ = _run(torch, dm, dm.DM_FP32, d1, d2, p0[:1], p1[:1], pr)
+    _, _, m32, _, _ = _run(torch, dm, dm.DM_FP32, d1, d2, {0: s[0][:1]}, pr)
     k32 = {(r[0], r[1]): (r[2], r[3]) for r in m32}
     k16 = {(r[0], r[1]): (r[2], r[3]) for r in m16}
     keys = set(k32) | set(k16)

@@ -771,3 +771,74 @@ def test_sampled_level1_equals_pyramid(oracle_mod):
             keep = e.astype(bool)
             np.testing.assert_array_equal(v[keep], pyr.pooled[1][keep])
             np.testing.assert_array_equal(a[keep], pyr.argmax[1][keep])
+
+
+@pytest.mark.parametrize("W1,H1,W2,H2,seed", [(70, 54, 61, 47, 9), (83, 37, 90, 41, 10)])
+def test_sampled_levels_equal_pyramid(oracle_mod, W1, H1, W2, H2, seed):
+    """The sampled maps of any level below the top (computed from the atomic
+    descendants only, for checks of pairs too large for the whole pyramid) and
+    the existence flags are those of the full pyramid, in both precisions and
+    both child-sum modes; patches that do not exist are reported as such."""
+    rng = np.random.default_rng(seed)
+    a = synth.value_noise(W1, H1, rng).astype(np.float32)
+    b = synth.value_noise(W2, H2, rng).astype(np.float32)
+    for prec in ("f32", "f64"):
+        d1 = oracle_mod.descriptors(a, prec)
+        d2 = oracle_mod.descriptors(b, prec)
+        for comp in ((True, False) if prec == "f32" else (True,)):
+            pyr = oracle_mod.pyramid(d1, d2, prec, compensated=comp)
+            g = pyr.geom
+            vf = oracle_mod.valid_flags(W1, H1, W2, H2)
+            for l in range(g.L + 1):
+                np.testing.assert_array_equal(vf[l], pyr.valid[l])
+            for l in range(g.L):
+                sel = np.sort(rng.choice(g.npatch(l), size=min(9, g.npatch(l)), replace=False))
+                if l > 0:                               # include a patch that does not exist, if any
+                    gone = np.flatnonzero(pyr.valid[l] == 0)
+                    if len(gone):
+                        sel = np.unique(np.append(sel, gone[0]))
+                v, am, e = oracle_mod.levels_sampled(d1, d2, l, sel, prec, compensated=comp)
+                np.testing.assert_array_equal(e, pyr.valid[l][sel])
+                keep = e.astype(bool)
+                np.testing.assert_array_equal(v[keep], pyr.pooled[l][sel][keep])
+                np.testing.assert_array_equal(am[keep], pyr.argmax[l][sel][keep])
+                assert np.all(v[~keep] == 0)
+
+
+def _existence_brute(W, H, lmax):
+    """Patch existence per level straight from Eq. 7 with the boundary rule, on
+    the 2-D grids: atomic centres 4k + 2 <= W - 1 all exist; a lattice point
+    (4x, 4y) of image 1 holds a level-l patch iff one of its four children
+    (centres 2^l px away diagonally) holds a level-(l-1) patch."""
+    atom = {(4 * kx + 2, 4 * ky + 2) for kx in range((W - 3) // 4 + 1) for ky in range((H - 3) // 4 + 1)}
+    levels = [atom]
+    lattice = [(4 * x, 4 * y) for x in range((W - 1) // 4 + 1) for y in range((H - 1) // 4 + 1)]
+    for l in range(1, lmax + 1):
+        prev = levels[-1]
+        s = 1 << l
+        levels.append({(x, y) for (x, y) in lattice if any((x + ox * s, y + oy * s) in prev
+                                                              for ox in (-1, 1) for oy in (-1, 1))})
+    return levels
+
+
+@pytest.mark.parametrize("W,H", [(80, 20), (20, 80), (100, 30), (64, 48), (61, 17), (130, 70), (155, 46),
+                                 (9, 40), (48, 13), (37, 29), (70, 6)])
+def test_top_level_is_the_highest_with_a_patch(oracle_mod, W, H):
+    """Algorithm 1 runs until N = 4 * 2^l >= max(W, H); a wide, low image has no
+    patch at that level (its children lie 2^l px above and below every lattice
+    point), and the pyramid's top is then the highest level that has one."""
+    l_alg = 0
+    while 4 * 2 ** l_alg < max(W, H):
+        l_alg += 1
+    ex = _existence_brute(W, H, l_alg)
+    want = max(l for l in range(1, l_alg + 1) if ex[l])
+    g = oracle_mod.geometry(W, H, W, H)
+    assert g.L == want
+    vf = oracle_mod.valid_flags(W, H, W, H)
+    for l in range(1, g.L + 1):
+        got = {(4 * (p % g.Lx), 4 * (p // g.Lx)) for p in np.flatnonzero(vf[l])}
+        assert got == ex[l], l
+    # and the matches of such a pair are not empty
+    pr = synth.make_pair_smooth(W, H, seed=5, max_disp=2.0)
+    m, _, _ = oracle_mod.match(pr.img1, pr.img2, "f32")
+    assert len(m) > 0
