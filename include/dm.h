@@ -315,6 +315,40 @@ dm_status dm_match_invariant(dm_ctx* ctx, const float* d_img1, int W1, int H1, c
 dm_status dm_read_status(dm_ctx* ctx, const void* d_ws, int* status, long long* reached, int n_reached,
                          void* stream);
 
+/* Fault injection (no counterpart in the paper): test hooks that drive the
+ * library's failure paths on the host or through bounded device waits, never
+ * through a GPU fault.  Each hook stays armed until it fires or is reset.
+ *   DM_FAULT_NONE      reset every hook of ctx and the process-wide one.
+ *   DM_FAULT_LAUNCH    the arg-th next launch site of ctx (level-0
+ *                      correlation, pyramid levels, backtracking of
+ *                      dm_correlate_pyramid, dm_backtrack and dm_match) reports a
+ *                      launch failure: the call returns DM_ECUDA with a message
+ *                      naming the stage and "injected"; the stages before it
+ *                      have been queued, the rest is not; later calls run
+ *                      normally.  arg = 0: off.
+ *   DM_FAULT_CAPACITY  the merge tables of dm_backtrack and dm_match hold at
+ *                      most arg slots per level (rounded up to a multiple of
+ *                      64): a pair with more merged tuples sets
+ *                      DM_DEV_FRONTIER_OVERFLOW (dm_read_status) and returns
+ *                      the matches of the tuples that fitted.  arg = 0: off.
+ *   DM_FAULT_WAIT      every CTA of the level kernel (levels 1..L-1) first
+ *                      waits arg clock cycles on a barrier nothing completes;
+ *                      the bounded wait runs out, the CTA waits for the loads
+ *                      it has started and exits, and dm_read_status on the
+ *                      pyramid (or dm_match) workspace reports DM_DEV_TIMEOUT;
+ *                      the pyramid's contents are then undefined.  arg = 0: off.
+ *   DM_FAULT_ALLOC     process-wide (ctx may be NULL): the arg-th next resource
+ *                      creation (dm_create's context, dm_timing_start's events)
+ *                      fails with DM_ENOMEM and leaves nothing behind.
+ * Not covered: a run-out of the tensor-core level-0 kernel's waits (its abort
+ * path does not wait for the copies and MMAs already issued). */
+#define DM_FAULT_NONE 0
+#define DM_FAULT_LAUNCH 1
+#define DM_FAULT_CAPACITY 2
+#define DM_FAULT_WAIT 3
+#define DM_FAULT_ALLOC 4
+dm_status dm_inject_fault(dm_ctx* ctx, int kind, long long arg);
+
 /* Differentiable form (the paper defines no loss; this one is the sum of the top-level maxima).
  * loss = sum over the existing top-level patches p of max_q C_L(p, q) (first
  * maximum), for the pyramid `pyr` built by dm_correlate_pyramid from d_desc1 /

@@ -11,6 +11,7 @@
 #include <atomic>
 #include <map>
 #include <mutex>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -32,7 +33,14 @@ struct dm_ctx {
     int lanes = 2;
     cudaStream_t lane_st[DM_MAX_LANES] = {};
     cudaEvent_t fork_ev = nullptr, join_ev[DM_MAX_LANES] = {};
+    // fault injection (dm_inject_fault): test hooks that drive the failure paths
+    long long inj_launch = 0;         // > 0: the inj_launch-th next launch site reports a launch failure
+    unsigned int inj_table_cap = 0;   // > 0: merge tables of the backtracking capped at this many slots
+    long long inj_wait = 0;           // > 0: level-kernel CTAs first wait this many cycles on a barrier nothing completes
 };
+
+// process-wide: > 0, the g_inj_alloc-th next resource creation of the library fails
+static std::atomic<long long> g_inj_alloc{0};
 
 namespace {
 DmTune tune_for(dm_ctx* c, const DmGeom& g) {
@@ -73,6 +81,32 @@ dm_status fail(dm_ctx* c, dm_status s, const char* fmt, ...) {
 
 dm_status cuda_fail(dm_ctx* c, cudaError_t e, const char* where) {
     return fail(c, DM_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// Fault injection: true when this launch site is the one dm_inject_fault
+// asked to fail (the count runs down over the sites the context reaches).
+bool inject_launch(dm_ctx* c) { return c->inj_launch > 0 && --c->inj_launch == 0; }
+
+dm_status injected_launch_failure(dm_ctx* c, const char* where) {
+    return fail(c, DM_ECUDA, "%s: injected launch failure", where);
+}
+
+// true when this resource creation is the one dm_inject_fault(NULL, DM_FAULT_ALLOC, n) asked to fail
+bool inject_alloc() {
+    long long v = g_inj_alloc.load();
+    while (v > 0)
+        if (g_inj_alloc.compare_exchange_weak(v, v - 1)) return v == 1;
+    return false;
+}
+
+// The backtracking layout with the merge tables capped by dm_inject_fault
+// (at least 64 slots, a multiple of 64, never above the layout's own size).
+DmBtLayout capped_tables(const dm_ctx* c, const DmBtLayout& bl) {
+    DmBtLayout o = bl;
+    if (c->inj_table_cap > 0)
+        for (size_t l = 0; l < sizeof(o.cap) / sizeof(o.cap[0]); l++)
+            if (o.cap[l] > c->inj_table_cap) o.cap[l] = c->inj_table_cap;
+    return o;
 }
 
 // Gaussian taps of standard deviation nu on [-ceil(3nu), ceil(3nu)],
@@ -157,12 +191,14 @@ dm_status run_pyramid(dm_ctx* c, const DmGeom& g, const float* d1, const float* 
                       dm_pyramid* py, int* d_status, cudaStream_t st, const float* protos = nullptr, int n_protos = -1,
                       const int* proto_of = nullptr) {
     fill_pyramid(py, g, c->cfg.precision, c->cfg.compensated, tune_for(c, g), pl, base);
+    py->inject_wait = c->inj_wait;
     if (protos) {
         py->proto_of = proto_of;
         py->n0_maps = n_protos;
     }
     cudaError_t e;
     if ((e = cudaMemsetAsync(d_status, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(c, e, "clear status");
+    if (inject_launch(c)) return injected_launch_failure(c, "level-0 correlation");
     if (c->cfg.precision != DM_FP32) {
         e = dm_launch_corr0_tc(g, c->cfg.precision, d1, d2, c->cfg.lambda, base + pl.a16, d_status,
                                const_cast<float*>(py->pooled[0]), const_cast<unsigned char*>(py->amax[0]),
@@ -172,6 +208,7 @@ dm_status run_pyramid(dm_ctx* c, const DmGeom& g, const float* d1, const float* 
                                 const_cast<unsigned char*>(py->amax[0]), st, protos, py->n0_maps);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "level-0 correlation");
+    if (inject_launch(c)) return injected_launch_failure(c, "pyramid levels");
     e = dm_launch_levels(g, *py, c->cfg.lambda, d_status, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "pyramid levels");
     return DM_OK;
@@ -386,7 +423,9 @@ dm_status dm_create(const dm_config* cfg, int device, dm_ctx** out) {
     if (c.compensated != 0 && c.compensated != 1) return DM_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return DM_EINVAL;
-    dm_ctx* x = new dm_ctx();
+    if (inject_alloc()) return DM_ENOMEM;          // fault injection: the context cannot be created
+    dm_ctx* x = new (std::nothrow) dm_ctx();
+    if (!x) return DM_ENOMEM;
     x->cfg = c;
     x->device = device;
     {
@@ -429,6 +468,7 @@ dm_status dm_timing_start(dm_ctx* ctx, int max_calls) {
     DevGuard dg(ctx->device);
     size_t need = (size_t)max_calls * (DM_NSTAGES + 1);
     while (ctx->ev.size() < need) {
+        if (inject_alloc()) return fail(ctx, DM_ENOMEM, "dm_timing_start: injected allocation failure");
         cudaEvent_t e;
         cudaError_t r = cudaEventCreate(&e);
         if (r != cudaSuccess) return cuda_fail(ctx, r, "cudaEventCreate");
@@ -645,7 +685,9 @@ dm_status dm_backtrack(dm_ctx* ctx, const dm_pyramid* pyr, void* d_ws, size_t ws
     cudaError_t e = cudaMemsetAsync(&reinterpret_cast<DmWsHeader*>((char*)d_ws + bl.header)->pyr_status, 0, sizeof(int),
                                     (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "clear status");
-    e = dm_launch_backtrack(pyr->g, *pyr, bl, (char*)d_ws, d_out, capacity, d_count, (cudaStream_t)stream);
+    if (inject_launch(ctx)) return injected_launch_failure(ctx, "backtracking kernels");
+    e = dm_launch_backtrack(pyr->g, *pyr, capped_tables(ctx, bl), (char*)d_ws, d_out, capacity, d_count,
+                            (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "backtracking kernels");
     return DM_OK;
 }
@@ -675,9 +717,11 @@ dm_status dm_match(dm_ctx* ctx, const float* d_img1, int W1, int H1, const float
     if (ev) cudaEventRecord(ev[1], st);
     dm_pyramid py;
     fill_pyramid(&py, g, ctx->cfg.precision, ctx->cfg.compensated, tune_for(ctx, g), ml.py, base + ml.pyr);
+    py.inject_wait = ctx->inj_wait;
     cudaError_t e;
     int* d_status = &reinterpret_cast<DmWsHeader*>(base + ml.bt.header)->pyr_status;
     if ((e = cudaMemsetAsync(d_status, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(ctx, e, "clear status");
+    if (inject_launch(ctx)) return injected_launch_failure(ctx, "level-0 correlation");
     if (ctx->cfg.precision != DM_FP32)
         e = dm_launch_corr0_tc(g, ctx->cfg.precision, desc1, desc2, ctx->cfg.lambda, base + ml.pyr + ml.py.a16,
                                d_status, const_cast<float*>(py.pooled[0]), const_cast<unsigned char*>(py.amax[0]),
@@ -687,10 +731,12 @@ dm_status dm_match(dm_ctx* ctx, const float* d_img1, int W1, int H1, const float
                                 const_cast<unsigned char*>(py.amax[0]), st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "level-0 correlation");
     if (ev) cudaEventRecord(ev[2], st);
+    if (inject_launch(ctx)) return injected_launch_failure(ctx, "pyramid levels");
     e = dm_launch_levels(g, py, ctx->cfg.lambda, d_status, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "pyramid levels");
     if (ev) cudaEventRecord(ev[3], st);
-    e = dm_launch_backtrack(g, py, ml.bt, base, d_out, capacity, d_count, st);
+    if (inject_launch(ctx)) return injected_launch_failure(ctx, "backtracking kernels");
+    e = dm_launch_backtrack(g, py, capped_tables(ctx, ml.bt), base, d_out, capacity, d_count, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "backtracking kernels");
     if (ev) cudaEventRecord(ev[4], st);
     return DM_OK;
@@ -1191,6 +1237,36 @@ dm_status dm_match_invariant(dm_ctx* ctx, const float* d_img1, int W1, int H1, c
     e = dm_launch_reciprocal(go, bestP, bestQ, hdr, d_out, capacity, d_count, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "reciprocal verification");
     return DM_OK;
+}
+
+dm_status dm_inject_fault(dm_ctx* ctx, int kind, long long arg) {
+    if (arg < 0) return fail(ctx, DM_EINVAL, "dm_inject_fault: negative argument");
+    if (kind == DM_FAULT_ALLOC) {
+        g_inj_alloc.store(arg);
+        return DM_OK;
+    }
+    if (!ctx) return DM_EINVAL;
+    switch (kind) {
+        case DM_FAULT_NONE:
+            ctx->inj_launch = 0;
+            ctx->inj_table_cap = 0;
+            ctx->inj_wait = 0;
+            g_inj_alloc.store(0);
+            return DM_OK;
+        case DM_FAULT_LAUNCH:
+            ctx->inj_launch = arg;
+            return DM_OK;
+        case DM_FAULT_CAPACITY:
+            if (arg > 0xffffffffLL) return fail(ctx, DM_EINVAL, "dm_inject_fault: capacity too large");
+            // whole blocks of 64 slots (the hashing keeps blocks of 32 keys together)
+            ctx->inj_table_cap = arg == 0 ? 0u : (unsigned int)(((arg + 63) / 64) * 64);
+            return DM_OK;
+        case DM_FAULT_WAIT:
+            ctx->inj_wait = arg;
+            return DM_OK;
+        default:
+            return fail(ctx, DM_EINVAL, "dm_inject_fault: unknown kind %d", kind);
+    }
 }
 
 dm_status dm_read_status(dm_ctx* ctx, const void* d_ws, int* status, long long* reached, int n_reached, void* stream) {

@@ -273,6 +273,10 @@ struct dm_pyramid {
     // exact form: proto_of = nullptr, n0_maps = npatch(0)
     const int* proto_of;
     int n0_maps;
+    // fault injection (dm_inject_fault): > 0, every CTA of the level kernel
+    // first waits this many cycles on a barrier nothing completes, so its
+    // bounded wait runs out and the pyramid status reports it; 0 otherwise
+    long long inject_wait;
 };
 
 // ---------------------------------------------------------------------------

@@ -184,7 +184,10 @@ __device__ __forceinline__ int expand(const BtArgs& a, int l, unsigned int cap_n
     int arrivals = 0;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
-        if (cc[i] < 0) continue;
+        // a code above 8 never comes from the pooling (first in-domain maximum of
+        // 9); it can only be left by a level kernel whose bounded wait gave up
+        // (status DM_DEV_TIMEOUT): skipping it keeps every position in its domain
+        if (cc[i] < 0 || code[i] > 8) continue;
         const int rx = rxs[i], ry = rys[i];
         const int tx = 2 * rx + code[i] % 3 - 1, ty = 2 * ry + code[i] / 3 - 1;
         const unsigned int s2 = (MODE == BT_STAR && l - 1 >= 1) ? s : s + ps_term(val[i]);

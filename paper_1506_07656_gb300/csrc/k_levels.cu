@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
                                                                int runs_per_res, int run, float* __restrict__ out,
                                                                unsigned char* __restrict__ amax, float lam,
                                                                int* __restrict__ err, const int* __restrict__ proto_of,
-                                                               int n_maps) {
+                                                               int n_maps, long long inject_wait) {
     using T = LevelTile<TH>;
     constexpr int AH = T::AH, KIDF = T::KIDF;
     extern __shared__ __align__(128) unsigned char lsm_raw[];
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
     float* lsm = reinterpret_cast<float*>(lsm_raw + ((128u - ((uint32_t)__cvta_generic_to_shared(lsm_raw) & 127u)) & 127u));
     float* ring = lsm;                                       // [NR][2][KIDF]
     float (*avg)[AWP] = reinterpret_cast<float (*)[AWP]>(lsm + NR * 2 * KIDF);
-    __shared__ __align__(8) uint64_t bars[NR];
+    __shared__ __align__(8) uint64_t bars[NR + 1];          // ring slots, then one barrier nothing completes
     __shared__ int colc[NR][2];                              // child index per ring slot (top, bottom), -1 absent
     __shared__ int abort_s;
 
@@ -277,10 +277,23 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
 
     if (tid == 0) {
         abort_s = 0;
-        for (int b = 0; b < NR; b++)
+        for (int b = 0; b <= NR; b++)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"((uint32_t)__cvta_generic_to_shared(&bars[b])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         for (int j = 0; j < NR && j <= nrun; j++) stage(j);
+        if (inject_wait > 0) {
+            // fault injection: a bounded wait on a barrier nothing completes runs
+            // out after inject_wait cycles, exactly like a wait for a load that
+            // never lands; the CTA then takes its abort path below (which still
+            // waits, with the normal limit, for the loads it has started)
+            const uint32_t never = (uint32_t)__cvta_generic_to_shared(&bars[NR]);
+            const long long t0 = clock64();
+            uint32_t done = 0;
+            while (!done && clock64() - t0 <= inject_wait)
+                asm volatile("{.reg .pred q; mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2, %3; selp.u32 %0, 1, 0, q;}"
+                             : "=r"(done) : "r"(never), "r"(0u), "n"(WAIT_HINT_NS) : "memory");
+            if (!done) { atomicOr(err, 1); abort_s = 1; }
+        }
     }
     __syncthreads();
     const bool interior = qx0 >= 0 && qy0 >= 0 && qx0 + AW <= mw && qy0 + AH <= mh;
@@ -406,7 +419,8 @@ cudaError_t launch_sweep(const DmGeom& g, int l, const CUtensorMap& tm, const dm
     k_level_sweep<COMP, TH, NR, APPROX><<<(unsigned)items, LEVEL_THREADS, smem, st>>>(g, l, tm, py.valid[l - 1], per_res, level_run(l),
                                                                           const_cast<float*>(py.pooled[l]),
                                                                           const_cast<unsigned char*>(py.amax[l]), lam, status,
-                                                                          APPROX ? py.proto_of : nullptr, py.n0_maps);
+                                                                          APPROX ? py.proto_of : nullptr, py.n0_maps,
+                                                                          py.inject_wait);
     return cudaGetLastError();
 }
 

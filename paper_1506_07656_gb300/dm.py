@@ -72,6 +72,7 @@ _SIGS = {
     "dm_match_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                 C.c_size_t, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_void_p]),
     "dm_read_status": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.c_void_p, C.c_int, C.c_void_p]),
+    "dm_inject_fault": (C.c_int, [C.c_void_p, C.c_int, C.c_longlong]),
     "dm_grad_workspace_bytes": (C.c_int, [C.c_void_p] + [C.c_int] * 4 + [C.POINTER(C.c_size_t)]),
     "dm_loss_grad": (C.c_int, [C.c_void_p] * 5 + [C.c_size_t] + [C.c_void_p] * 5),
     "dm_batch_workspace_bytes": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_size_t)]),
@@ -385,6 +386,15 @@ def dm_read_status(ctx, d_ws, n_levels: int, stream=None):
     st = load().dm_read_status(ctx, _dptr(d_ws), C.byref(status), reached, n_levels, _stream_ptr(stream))
     _check(ctx, st, "dm_read_status")
     return status.value, list(reached)
+
+
+DM_FAULT_NONE, DM_FAULT_LAUNCH, DM_FAULT_CAPACITY, DM_FAULT_WAIT, DM_FAULT_ALLOC = 0, 1, 2, 3, 4
+
+
+def dm_inject_fault(ctx, kind: int, arg: int = 0) -> None:
+    """Arm a fault-injection hook (test use): see dm_inject_fault in dm.h.
+    ctx may be None for DM_FAULT_ALLOC."""
+    _check(ctx, load().dm_inject_fault(ctx, int(kind), int(arg)), "dm_inject_fault")
 
 
 def dm_grad_workspace_bytes(ctx, W1, H1, W2, H2) -> int:

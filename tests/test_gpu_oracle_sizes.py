@@ -15,54 +15,19 @@
 
 Derived tolerances (config 3).  Both sides start from the same descriptors
 (the FP32 oracle's, which the GPU reproduces bit for bit), so the comparison
-isolates the pyramid's arithmetic.  A non-negative sum of products whose
-operands carry a relative rounding error <= u_op each, accumulated in FP32
-(<= 144 terms, u_acc = 2^-16 covers their roundings and the few ulp of the
-power), has relative error <= r_0 = (1 + u_op)^2 (1 + u_acc) - 1.  Pooling and
-averaging non-negative values keep a relative error bound, and x -> x^lambda
-turns a factor (1 + r) into (1 + r)^lambda, so the unrectified values of level
-l carry at most r_l = (1 + r_0)^(lambda^l) - 1 and the stored (rectified)
-maps eps_l = (1 + r_0)^(lambda^(l+1)) - 1; u_op = 0 (FP32), 2^-9 (BF16),
-2^-4 (E4M3).  An argmax between two candidates x1 > x2 can only change if
-x2 / x1 > (1 - r_l) / (1 + r_l), i.e. if the FP64 gap of the rectified values
-(reading c23) is below 1 - ((1 - r_l) / (1 + r_l))^lambda.  BestAt and
-BestAt' compare path scores (sums of terms each within eps_L), which can only
-change below a gap of 2 eps_L / (1 - eps_L).  A patch's match can only differ
-where one of its decisions is that close; for FP32 the spec rule (gap
-< 1e-3) is asserted on top.  The share of patches the strict 1e-3 rule does
-not excuse is printed for BF16 and FP8.
+isolates the pyramid's arithmetic; the per-level map error bounds and the
+decision tolerances follow from the operand rounding of each precision
+(precision_bounds.py).  For FP32 the spec rule (gap < 1e-3) is asserted
+on top; the share of patches that rule does not excuse is printed for BF16
+and FP8.
 """
 import numpy as np
 import pytest
 
 from paper_1506_07656_gb300 import synth
+from precision_bounds import argmax_tol, eps_level, match_tol
 
 pytestmark = pytest.mark.gpu
-
-LAM = 1.4
-U_OP = {"fp32": 0.0, "bf16": 2.0 ** -9, "fp8": 2.0 ** -4}
-U_ACC = 2.0 ** -16
-
-
-def _r(prec, l):
-    """Bound on the relative error of the unrectified values of level l."""
-    return ((1 + U_OP[prec]) ** 2 * (1 + U_ACC)) ** (LAM ** l) - 1.0
-
-
-def eps_level(prec, l):
-    """Bound on the relative error of the stored (rectified) maps of level l."""
-    return (1.0 + _r(prec, l)) ** LAM - 1.0
-
-
-def argmax_tol(prec, l):
-    r = _r(prec, l)
-    return 1.0 - ((1.0 - r) / (1.0 + r)) ** LAM if r < 1 else 1.0
-
-
-def match_tol(prec, L):
-    e = eps_level(prec, L)
-    return max(argmax_tol(prec, L - 1), 2 * e / (1 - e) if e < 1 else np.inf)
-
 
 @pytest.fixture(scope="module")
 def env():
