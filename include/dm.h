@@ -406,7 +406,9 @@ dm_status dm_set_batch_lanes(dm_ctx* ctx, int lanes);
  *              level-0 kernel (the work unit is one N-tile x that many
  *              M-tiles; candidates split the patches into 1, 2, 3, 4, 6 or 8
  *              chunks; unused by DM_FP32);
- *   chosen[1]  pooled rows per CTA tile of the level kernel (16 or 8);
+ *   chosen[1]  level kernel: pooled rows per CTA tile of the tiled kernel (16
+ *              or 8), or 0 for the row-streaming kernel (one warp per patch
+ *              and 31-column strip, no shared memory);
  *   chosen[2]  CTAs per SM of the backtracking expansion kernels (2..32);
  *   chosen[3]  child-window columns in the level kernel's ring (3 or 2).
  * Every candidate computes identical results; only the time differs.  Each
@@ -423,7 +425,7 @@ dm_status dm_autotune(dm_ctx* ctx, const float* d_img1, int W1, int H1, const fl
  * DM_FP8_E4M3 --, 16, 8, 2): 4 ints as for dm_autotune. */
 dm_status dm_tuned_config(dm_ctx* ctx, int W1, int H1, int W2, int H2, int* chosen);
 /* Set the launch shapes for pairs of these sizes (e.g. a choice saved from an
- * earlier dm_autotune): chosen[0] >= 1, chosen[1] in {8, 16}, chosen[2] in
+ * earlier dm_autotune): chosen[0] >= 1, chosen[1] in {0, 8, 16}, chosen[2] in
  * 1..64, chosen[3] in {2, 3}; DM_EINVAL otherwise. */
 dm_status dm_set_tuned_config(dm_ctx* ctx, int W1, int H1, int W2, int H2, const int* chosen);
 

@@ -16,6 +16,7 @@ SHAPES = [
     {"m_chunk": 1, "level_tile_rows": 8, "bt_ctas_per_sm": 2, "level_ring": 3},
     {"m_chunk": 3, "level_tile_rows": 16, "bt_ctas_per_sm": 32, "level_ring": 2},
     {"m_chunk": 1000, "level_tile_rows": 8, "bt_ctas_per_sm": 1, "level_ring": 2},
+    {"m_chunk": 2, "level_tile_rows": 0, "bt_ctas_per_sm": 8, "level_ring": 2},      # row-streaming level kernel
 ]
 
 
@@ -77,7 +78,7 @@ def test_autotune_picks_a_candidate_and_keeps_results(dm_mod, prec):
         before = ctx.match(pr.img1, pr.img2).cpu().numpy()
         chosen = ctx.autotune(pr.img1, pr.img2)
         assert chosen["m_chunk"] in {-(-n_mtiles // k) for k in (1, 2, 3, 4, 6, 8)}
-        assert chosen["level_tile_rows"] in (8, 16)
+        assert chosen["level_tile_rows"] in (0, 8, 16)
         assert chosen["bt_ctas_per_sm"] in (2, 4, 8, 16, 32)
         assert chosen["level_ring"] in (2, 3)
         assert dm.dm_tuned_config(ctx.ctx, W, H, W, H) == chosen
@@ -97,5 +98,44 @@ def test_set_tuned_config_rejects_bad_shapes(dm_mod):
                     {"m_chunk": 4, "level_tile_rows": 16, "bt_ctas_per_sm": 8, "level_ring": 4}):
             with pytest.raises(dm.DmError):
                 dm.dm_set_tuned_config(ctx.ctx, 64, 48, 64, 48, bad)
+    finally:
+        ctx.close()
+
+
+STREAM = {"m_chunk": 1, "level_tile_rows": 0, "bt_ctas_per_sm": 8, "level_ring": 2}
+
+
+@pytest.mark.parametrize("compensated", [True, False])
+@pytest.mark.parametrize("W1,H1,W2,H2,seed", [(64, 48, 64, 48, 1), (37, 29, 37, 29, 2), (41, 23, 53, 35, 3),
+                                              (96, 61, 71, 80, 4), (130, 70, 130, 70, 5), (300, 90, 257, 131, 6)])
+def test_row_streaming_level_kernel_bit_exact(dm_mod, oracle_mod, W1, H1, W2, H2, seed, compensated):
+    """The row-streaming level kernel: every level (values, argmax codes,
+    existence) bit-exact with the FP32 oracle, in both child-sum modes, on
+    equal, ragged and unequal sizes (strips that end inside the map, patches
+    with fewer than four children, odd map sizes)."""
+    import torch
+    dm = dm_mod
+    rng = np.random.default_rng(seed)
+    a = synth.value_noise(W1, H1, rng).astype(np.float32)
+    b = synth.value_noise(W2, H2, rng).astype(np.float32)
+    d1 = oracle_mod.descriptors(a, "f32")
+    d2 = oracle_mod.descriptors(b, "f32")
+    pyr = oracle_mod.pyramid(d1, d2, "f32", compensated=compensated)
+    ctx = dm.Context(dm.DM_FP32, compensated=int(compensated))
+    try:
+        dm.dm_set_tuned_config(ctx.ctx, W1, H1, W2, H2, STREAM)
+        ws = torch.empty(dm.dm_workspace_bytes(ctx.ctx, W1, H1, W2, H2)["pyramid"], dtype=torch.uint8, device="cuda")
+        h = dm.dm_correlate_pyramid(ctx.ctx, torch.from_numpy(d1).cuda(), torch.from_numpy(d2).cuda(), ws)
+        try:
+            for l in range(pyr.geom.L + 1):
+                vals, am, valid = dm.read_level(ws, dm.dm_pyramid_level(h, l))
+                np.testing.assert_array_equal(valid, pyr.valid[l])
+                keep = valid.astype(bool)
+                want = pyr.pooled[l] if l < pyr.geom.L else pyr.top
+                np.testing.assert_array_equal(vals[keep], want[keep], err_msg=f"level {l}")
+                if l < pyr.geom.L:
+                    np.testing.assert_array_equal(am[keep], pyr.argmax[l][keep], err_msg=f"level {l} codes")
+        finally:
+            dm.dm_pyramid_free(h)
     finally:
         ctx.close()
