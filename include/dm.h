@@ -408,7 +408,8 @@ dm_status dm_set_batch_lanes(dm_ctx* ctx, int lanes);
  *              chunks; unused by DM_FP32);
  *   chosen[1]  level kernel: pooled rows per CTA tile of the tiled kernel (16
  *              or 8), or 0 for the row-streaming kernel (one warp per patch
- *              and 31-column strip, no shared memory);
+ *              and 31-column strip, no shared memory); levels whose stored
+ *              maps are at most 16 columns wide always take the latter;
  *   chosen[2]  CTAs per SM of the backtracking expansion kernels (2..32);
  *   chosen[3]  child-window columns in the level kernel's ring (3 or 2).
  * Every candidate computes identical results; only the time differs.  Each

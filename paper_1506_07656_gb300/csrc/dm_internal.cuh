@@ -291,6 +291,30 @@ struct Kids {
     int n;
 };
 
+// a - b for two lanes at once, each lane rounded as the scalar subtraction
+// (the packed add has no negated operand, so a - b written as a + (-b) would
+// need the negations as separate instructions)
+__device__ __forceinline__ float2 dm_fsub2(float2 a, float2 b) {
+    unsigned long long ra, rb, rd;
+    memcpy(&ra, &a, 8);
+    memcpy(&rb, &b, 8);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    float2 d;
+    memcpy(&d, &rd, 8);
+    return d;
+}
+
+// One packed step of Knuth's TwoSum (s, x) -> (s + x, its rounding error),
+// two lanes at once; every operation rounded as the scalar one.
+__device__ __forceinline__ void dm_two_sum2(float2& s, float2 x, float2& err) {
+    const float2 t = __fadd2_rn(s, x);
+    const float2 bp = dm_fsub2(t, s);
+    const float2 e1 = dm_fsub2(s, dm_fsub2(t, bp));
+    const float2 e2 = dm_fsub2(x, bp);
+    err = __fadd2_rn(e1, e2);
+    s = t;
+}
+
 // One step of the compensated child sum (Knuth's TwoSum gives the same bits
 // for any operands): for non-negative operands, which every map value is,
 // Dekker's Fast2Sum on (max, min) is exact, since the first operand is the

@@ -112,16 +112,11 @@ __device__ __forceinline__ float4 avg4(const float* const* kb, int ay, int ax, c
 #pragma unroll
             for (int i = 1; i < 4; i++) {
                 const float2 x = make_float2(v[i][c], v[i][c + 1]);
-                const float2 t = __fadd2_rn(sv, x);
-                const float2 bp = __fadd2_rn(t, make_float2(-sv.x, -sv.y));
-                const float2 tb = __fadd2_rn(t, make_float2(-bp.x, -bp.y));
-                const float2 e1 = __fadd2_rn(sv, make_float2(-tb.x, -tb.y));
-                const float2 e2 = __fadd2_rn(x, make_float2(-bp.x, -bp.y));
-                const float2 err = __fadd2_rn(e1, e2);
+                float2 err;
+                dm_two_sum2(sv, x, err);
                 // first step: the compensation starts as its error term (0 + err = err;
                 // a -0 there would only meet s + (+-0) = s at the end)
                 cp = i == 1 ? err : __fadd2_rn(cp, err);
-                sv = t;
             }
             const float2 a = __fmul2_rn(__fadd2_rn(sv, cp), make_float2(0.25f, 0.25f));
             r[c] = a.x;
@@ -397,30 +392,24 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
 // One warp owns one lattice patch p and a strip of STREAM_W = 31 pooled columns
 // [r0, r0 + 31) of its stored map, and walks down every row of it: no shared
 // memory, no barrier.  For a row y of averages, lane t forms A(2(r0+t) - 1, y)
-// and A(2(r0+t), y), two columns at once with the packed child sum: child i
-// contributes its values at columns 2(r0+t) - 1 + o_x,i - ... which for the
-// children with o_x = -1 are columns 2(r0+t) - 2 and - 1, for those with
-// o_x = +1 columns 2(r0+t) and + 1 -- one aligned 8-byte load per child, rows
-// y - 1 (o_y = -1) and y + 1 (o_y = +1).  A(2(r0+t) + 1, y) is lane t+1's first
-// average (one shuffle); lane 31 only supplies it.  The horizontal 3-maxima of
-// the rows are kept in registers and merged over three rows into the pooled
-// output, two output rows per step (one packed power).  Missing children and
-// samples outside the domain read as 0, which leaves both child sums unchanged
-// (s + 0 = s exactly, with a zero TwoSum error), so every patch runs the
-// four-child code and divides by its number of children.  The warps of a CTA
-// take neighbouring patches that share children (stride S along the row), so
-// most child rows a warp loads were just loaded by its neighbour (L1 hits).
+// and A(2(r0+t), y), two columns at once with the packed child sum: the
+// children with o_x = -1 contribute their columns 2(r0+t) - 2 and - 1, those
+// with o_x = +1 their columns 2(r0+t) and + 1 -- one aligned 8-byte load per
+// child, from row y - 1 (o_y = -1) or y + 1 (o_y = +1).  A(2(r0+t) + 1, y) is
+// lane t+1's first average (one shuffle); lane 31 only supplies it.  The
+// horizontal 3-maxima of the rows stay in registers and merge over three rows
+// into the pooled output, two output rows per step (one packed power).
+// Missing children and samples outside the domain read as 0, which leaves both
+// child sums unchanged (s + 0 = s exactly, with a zero TwoSum error), so every
+// patch runs the four-child arithmetic and divides by its number of children;
+// warps whose strip and children lie wholly inside take loads without any
+// masks, and only the first and last steps check rows.  The 8 warps of a CTA
+// take a 4 x 2 block of patches spaced S apart, which share child maps: each
+// child row a CTA needs comes from L2 once and is reused from L1.
 // ---------------------------------------------------------------------------
 constexpr int STREAM_W = 31;        // pooled columns per warp strip
-constexpr int STREAM_WARPS = 8;
-
-// Two map values at columns x, x+1 of one stored row; mode 3 = both columns in
-// the domain, 1 = only x, 0 = none (zeros).
-__device__ __forceinline__ float2 ld_pair(const float* __restrict__ row, int x, int mode) {
-    if (mode == 3) return __ldg(reinterpret_cast<const float2*>(row + x));
-    if (mode == 1) return make_float2(__ldg(row + x), 0.0f);
-    return make_float2(0.0f, 0.0f);
-}
+constexpr int STREAM_BX = 4, STREAM_BY = 2;   // patches per CTA along x and y
+constexpr int STREAM_WARPS = STREAM_BX * STREAM_BY;
 
 // Average of the four children (child order i = 0..3, zeros for missing ones)
 // for two columns at once, then times 1/n (n = 3 divides).
@@ -431,125 +420,163 @@ __device__ __forceinline__ float2 avg_pair(const float2* v, int n) {
         float2 cp = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int i = 1; i < 4; i++) {
-            const float2 x = v[i];
-            const float2 t = __fadd2_rn(sv, x);
-            const float2 bp = __fadd2_rn(t, make_float2(-sv.x, -sv.y));
-            const float2 tb = __fadd2_rn(t, make_float2(-bp.x, -bp.y));
-            const float2 e1 = __fadd2_rn(sv, make_float2(-tb.x, -tb.y));
-            const float2 e2 = __fadd2_rn(x, make_float2(-bp.x, -bp.y));
-            const float2 err = __fadd2_rn(e1, e2);
+            float2 err;
+            dm_two_sum2(sv, v[i], err);
             cp = i == 1 ? err : __fadd2_rn(cp, err);
-            sv = t;
         }
         sv = __fadd2_rn(sv, cp);
     } else {
 #pragma unroll
         for (int i = 1; i < 4; i++) sv = __fadd2_rn(sv, v[i]);
     }
+    if (n == 4) return __fmul2_rn(sv, make_float2(0.25f, 0.25f));
     if (n == 3) return make_float2(__fdiv_rn(sv.x, 3.0f), __fdiv_rn(sv.y, 3.0f));
-    const float w = n == 4 ? 0.25f : (n == 2 ? 0.5f : 1.0f);
+    const float w = n == 2 ? 0.5f : 1.0f;
     return __fmul2_rn(sv, make_float2(w, w));
 }
 
+// Per-warp state of the row-streaming kernel.
+struct StreamWarp {
+    const float* kid[4];   // child maps (nullptr: missing)
+    int n;                 // existing children
+    int mw, mh, pitch;     // child map domain and row pitch (level l)
+    int xl, xr;            // first column of this lane's left / right child pairs
+    int ml, mr;            // their load modes: 3 both columns in the domain, 1 only the first, 0 none
+    bool has_a0, has_a2;   // A(2rx - 1) and A(2rx + 1) in the domain
+};
+
+// The four children's pairs of A row y.  CHECK: rows outside the domain, missing
+// children and columns outside the domain read as zeros; otherwise every load is
+// known to be inside.
+template <bool CHECK>
+__device__ __forceinline__ void stream_load_row(const StreamWarp& w, float2* v, int y) {
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const int cy = y + ((i & 1) ? 1 : -1);
+        const int x = i < 2 ? w.xl : w.xr;
+        if constexpr (!CHECK) {
+            v[i] = __ldg(reinterpret_cast<const float2*>(w.kid[i] + (cy * w.pitch + x)));
+        } else {
+            const int mode = i < 2 ? w.ml : w.mr;
+            const bool ok = w.kid[i] != nullptr && cy >= 0 && cy < w.mh;
+            float2 t = make_float2(0.0f, 0.0f);
+            if (ok && mode == 3) t = __ldg(reinterpret_cast<const float2*>(w.kid[i] + (cy * w.pitch + x)));
+            else if (ok && mode == 1) t.x = __ldg(w.kid[i] + (cy * w.pitch + x));
+            v[i] = t;
+        }
+    }
+}
+
+// Horizontal 3-max (first column equal to the maximum) of A row y; -inf outside the domain.
+template <bool COMP>
+__device__ __forceinline__ void stream_hrow(const StreamWarp& w, const float2* v, int y, float& h, int& hc) {
+    const float2 a = avg_pair<COMP>(v, w.n);
+    const float a2s = __shfl_down_sync(0xffffffffu, a.x, 1);
+    const float a0 = w.has_a0 ? a.x : -INFINITY, a1 = a.y, a2 = w.has_a2 ? a2s : -INFINITY;
+    const float m = fmax3(a0, a1, a2);
+    h = y < w.mh ? m : -INFINITY;
+    hc = a0 == m ? 0 : (a1 == m ? 1 : 2);
+}
+
+// One step: output rows ry and ry + 1 from A rows 2ry - 1 (carried in hp, cp)
+// to 2ry + 3.
+template <bool COMP, bool CHECK>
+__device__ __forceinline__ void stream_step(const StreamWarp& w, int ry, int oh, float& hp, int& cp, float lam,
+                                            bool store, float* __restrict__ orow, unsigned char* __restrict__ arow,
+                                            int opitch) {
+    float2 v[4][4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) stream_load_row<CHECK>(w, v[k], 2 * ry + k);
+    float h[4];
+    int hc[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) stream_hrow<COMP>(w, v[k], 2 * ry + k, h[k], hc[k]);
+    const float b0 = fmax3(hp, h[0], h[1]);
+    const int c0 = hp == b0 ? cp : (h[0] == b0 ? 3 + hc[0] : 6 + hc[1]);
+    const float b1 = fmax3(h[1], h[2], h[3]);
+    const int c1 = h[1] == b1 ? hc[1] : (h[2] == b1 ? 3 + hc[2] : 6 + hc[3]);
+    hp = h[3];
+    cp = hc[3];
+    const bool two = ry + 1 < oh;
+    // (with one output row left, the second lane of the pair repeats the first and is not stored)
+    const float2 pw = dm_powf2(make_float2(b0, two ? b1 : b0), lam);
+    if (store) {
+        orow[(long long)ry * opitch] = pw.x;
+        arow[(long long)ry * opitch] = (unsigned char)c0;
+        if (two) {
+            orow[(long long)(ry + 1) * opitch] = pw.y;
+            arow[(long long)(ry + 1) * opitch] = (unsigned char)c1;
+        }
+    }
+}
+
 template <bool COMP, bool APPROX = false>
-__global__ void __launch_bounds__(STREAM_WARPS * 32) k_level_stream(DmGeom g, int l, const float* __restrict__ prev,
+__global__ void __launch_bounds__(STREAM_WARPS * 32, 4) k_level_stream(DmGeom g, int l, const float* __restrict__ prev,
                                                                    const unsigned char* __restrict__ vprev,
                                                                    const unsigned char* __restrict__ vcur,
-                                                                   int runs_per_res, float* __restrict__ out,
+                                                                   int bx_per_res, int by_per_res, float* __restrict__ out,
                                                                    unsigned char* __restrict__ amax, float lam,
                                                                    const int* __restrict__ proto_of, int n_maps) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int cx0, cy0, S;
     child_col_row(g, l, 0, 0, &cx0, &cy0, &S);
-    // block = ((strip * Ly + iy) * S + residue) * runs_per_res + run
+    // block = (((strip * S + res_y) * by_per_res + by) * S + res_x) * bx_per_res + bx: a block holds
+    // patches (res_x + (bx * 4 + wx) S, res_y + (by * 2 + wy) S), wx < 4, wy < 2
     long long item = blockIdx.x;
-    const int run = (int)(item % runs_per_res);
-    item /= runs_per_res;
-    const int res = (int)(item % S);
+    const int bx = (int)(item % bx_per_res);
+    item /= bx_per_res;
+    const int res_x = (int)(item % S);
     item /= S;
-    const int iy = (int)(item % g.Ly);
-    const int strip = (int)(item / g.Ly);
-    const int ix = res + (run * STREAM_WARPS + warp) * S;
-    if (ix >= g.Lx) return;
+    const int by = (int)(item % by_per_res);
+    item /= by_per_res;
+    const int res_y = (int)(item % S);
+    const int strip = (int)(item / S);
+    const int ix = res_x + (bx * STREAM_BX + (warp % STREAM_BX)) * S;
+    const int iy = res_y + (by * STREAM_BY + (warp / STREAM_BX)) * S;
+    if (ix >= g.Lx || iy >= g.Ly) return;
     const int p = iy * g.Lx + ix;
     if (!vcur[p]) return;
 
-    const int mw = g.dw[l], mh = g.dh[l], pitch = g.pitch(l);
+    StreamWarp w;
+    w.mw = g.dw[l];
+    w.mh = g.dh[l];
+    w.pitch = g.pitch(l);
     const int ow = g.dw[l + 1], oh = g.dh[l + 1], opitch = g.pitch(l + 1);
     const long long csize = g.psize(l);
-    const float* kid[4];
-    int n = 0;
+    w.n = 0;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         const int c = dm_child(g, l, ix, iy, i);
-        kid[i] = nullptr;
+        w.kid[i] = nullptr;
         if (c >= 0 && vprev[c]) {
             const int cm = APPROX ? min(max(__ldg(proto_of + c), 0), n_maps - 1) : c;
-            kid[i] = prev + (long long)cm * csize;
-            n++;
+            w.kid[i] = prev + (long long)cm * csize;
+            w.n++;
         }
     }
     const int r0 = strip * STREAM_W, rx = r0 + lane;
-    const int xl = 2 * rx - 2, xr = 2 * rx;                 // first column of the left / right children's pairs
-    auto mode_of = [&](int x) { return (x >= 0 && x < mw) ? ((x + 1 < mw) ? 3 : 1) : 0; };
-    const int ml = mode_of(xl), mr = mode_of(xr);
-    const bool has_a0 = rx >= 1;                            // A(2rx - 1) in the domain
-    const bool has_a2 = 2 * rx + 1 < mw;                    // A(2rx + 1) in the domain
+    w.xl = 2 * rx - 2;
+    w.xr = 2 * rx;
+    auto mode_of = [&](int x) { return (x >= 0 && x < w.mw) ? ((x + 1 < w.mw) ? 3 : 1) : 0; };
+    w.ml = mode_of(w.xl);
+    w.mr = mode_of(w.xr);
+    w.has_a0 = rx >= 1;
+    w.has_a2 = 2 * rx + 1 < w.mw;
     const bool store = lane < STREAM_W && rx < ow;
-
-    // horizontal 3-max (first column equal to the maximum) of A row y; -inf outside the domain
-    auto hrow = [&](const float2* v, int y, float& h, int& hc) {
-        const float2 a = avg_pair<COMP>(v, n);
-        const float a2s = __shfl_down_sync(0xffffffffu, a.x, 1);
-        const float a0 = has_a0 ? a.x : -INFINITY, a1 = a.y, a2 = has_a2 ? a2s : -INFINITY;
-        const float m = fmax3(a0, a1, a2);
-        h = y < mh ? m : -INFINITY;
-        hc = a0 == m ? 0 : (a1 == m ? 1 : 2);
-    };
-    // the four children's pairs of A row y
-    auto load_row = [&](float2* v, int y) {
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-            const int cy = y + ((i & 1) ? 1 : -1);
-            const bool ok = kid[i] != nullptr && cy >= 0 && cy < mh;
-            v[i] = ok ? ld_pair(kid[i] + (long long)cy * pitch, i < 2 ? xl : xr, i < 2 ? ml : mr)
-                      : make_float2(0.0f, 0.0f);
-        }
-    };
+    // every lane's pairs inside the domain and all four children present
+    const bool inside = w.n == 4 && 2 * r0 - 2 >= 0 && 2 * (r0 + 31) + 1 < w.mw;
 
     float* orow = out + (long long)p * oh * opitch + rx;
     unsigned char* arow = amax + (long long)p * oh * opitch + rx;
-    float hp = -INFINITY;                                   // row 2ry - 1 (none for ry = 0)
+    float hp = -INFINITY;                                   // A row 2ry - 1 (none for ry = 0)
     int cp = 0;
-    for (int ry = 0; ry < oh; ry += 2) {
-        // A rows 2ry .. 2ry + 3: every load first, then the arithmetic
-        float2 v[4][4];
-#pragma unroll
-        for (int k = 0; k < 4; k++) load_row(v[k], 2 * ry + k);
-        float h[4];
-        int hc[4];
-#pragma unroll
-        for (int k = 0; k < 4; k++) hrow(v[k], 2 * ry + k, h[k], hc[k]);
-        // output ry: rows 2ry-1, 2ry, 2ry+1; output ry+1: rows 2ry+1, 2ry+2, 2ry+3
-        const float b0 = fmax3(hp, h[0], h[1]);
-        const int c0 = hp == b0 ? cp : (h[0] == b0 ? 3 + hc[0] : 6 + hc[1]);
-        const float b1 = fmax3(h[1], h[2], h[3]);
-        const int c1 = h[1] == b1 ? hc[1] : (h[2] == b1 ? 3 + hc[2] : 6 + hc[3]);
-        hp = h[3];
-        cp = hc[3];
-        const bool two = ry + 1 < oh;
-        // (when only one output row is left, the second lane of the pair is
-        // evaluated on the first's value and not stored)
-        const float2 pw = dm_powf2(make_float2(b0, two ? b1 : b0), lam);
-        if (store) {
-            orow[(long long)ry * opitch] = pw.x;
-            arow[(long long)ry * opitch] = (unsigned char)c0;
-            if (two) {
-                orow[(long long)(ry + 1) * opitch] = pw.y;
-                arow[(long long)(ry + 1) * opitch] = (unsigned char)c1;
-            }
-        }
+    int ry = 0;
+    if (inside) {
+        // step ry reads child rows 2ry - 1 .. 2ry + 4: unchecked while they lie in the domain
+        stream_step<COMP, true>(w, 0, oh, hp, cp, lam, store, orow, arow, opitch);
+        for (ry = 2; 2 * ry + 4 < w.mh; ry += 2) stream_step<COMP, false>(w, ry, oh, hp, cp, lam, store, orow, arow, opitch);
     }
+    for (; ry < oh; ry += 2) stream_step<COMP, true>(w, ry, oh, hp, cp, lam, store, orow, arow, opitch);
 }
 
 // Top level L: C_L = (mean of children)^lambda over the domain of level L.
@@ -588,13 +615,14 @@ cudaError_t launch_sweep(const DmGeom& g, int l, const CUtensorMap& tm, const dm
 template <bool COMP, bool APPROX = false>
 cudaError_t launch_stream(const DmGeom& g, int l, const dm_pyramid& py, float lam, cudaStream_t st) {
     const int S = l == 1 ? 1 : 1 << (l - 1);
-    const int per_res = ((g.Lx + S - 1) / S + STREAM_WARPS - 1) / STREAM_WARPS;   // runs of 8 patches per residue
+    const int bx_per_res = ((g.Lx + S - 1) / S + STREAM_BX - 1) / STREAM_BX;
+    const int by_per_res = ((g.Ly + S - 1) / S + STREAM_BY - 1) / STREAM_BY;
     const int strips = (g.dw[l + 1] + STREAM_W - 1) / STREAM_W;
-    const long long blocks = (long long)strips * g.Ly * S * per_res;
+    const long long blocks = (long long)strips * S * by_per_res * S * bx_per_res;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     k_level_stream<COMP, APPROX><<<(unsigned)blocks, STREAM_WARPS * 32, 0, st>>>(
-        g, l, py.pooled[l - 1], py.valid[l - 1], py.valid[l], per_res, const_cast<float*>(py.pooled[l]),
+        g, l, py.pooled[l - 1], py.valid[l - 1], py.valid[l], bx_per_res, by_per_res, const_cast<float*>(py.pooled[l]),
         const_cast<unsigned char*>(py.amax[l]), lam, APPROX ? py.proto_of : nullptr, py.n0_maps);
     return cudaGetLastError();
 }
@@ -607,9 +635,13 @@ cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& py, float lam, i
     k_fill_u8<<<(n0 + 255) / 256, 256, 0, st>>>(const_cast<unsigned char*>(py.valid[0]), n0, 1);
     for (int l = 1; l <= g.L; l++) {
         k_valid<<<(np + 255) / 256, 256, 0, st>>>(g, l, py.valid[l - 1], const_cast<unsigned char*>(py.valid[l]));
-        if (l < g.L && py.tune.level_th == 0 && py.inject_wait == 0) {
-            // row-streaming kernel (a fault-injection run takes the tiled kernel,
-            // which holds the bounded waits)
+        // the row-streaming kernel: as the tuned shape, and always for the levels
+        // whose stored maps are at most 16 columns wide, where the tiled kernel's
+        // per-patch pipeline is latency-bound (1024x436: levels 5-7 take 0.18
+        // instead of 0.38 ms); a fault-injection run takes the tiled kernel,
+        // which holds the bounded waits
+        const bool stream = py.tune.level_th == 0 || g.dw[l + 1] <= 16;
+        if (l < g.L && stream && py.inject_wait == 0) {
             const bool approx = l == 1 && py.proto_of != nullptr;
             cudaError_t e;
             if (approx)
