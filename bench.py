@@ -54,6 +54,7 @@ def _args():
     ap.add_argument("--no-approx", action="store_true", help="skip the approximate-form (Sec. 4.1) measurement")
     ap.add_argument("--no-star", action="store_true", help="skip the DM* (Sec. 5.3) measurement")
     ap.add_argument("--no-deepflow", action="store_true", help="skip the DeepFlow (Sec. 4.3) measurement")
+    ap.add_argument("--no-grad", action="store_true", help="skip the differentiable-form (8 x 256x256) measurement")
     ap.add_argument("--no-invariant", action="store_true",
                     help="skip the scale and rotation invariant form (Sec. 4.2) measurement")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
@@ -496,6 +497,79 @@ def _measure_invariant(dm, torch, a, stream, W=512, H=224, prec="bf16"):
 BATCH_SIZES = [(320, 240), (640, 480), (1024, 436), (1242, 375)]
 
 
+def _measure_grad(dm, torch, a, stream, W=256, H=256, npairs=8):
+    """Differentiable form (config 5): a batch of 8 pairs of 256x256 with the
+    FP32 descriptor fields resident on the device as the leaves; one step = for
+    every pair, the forward pyramid (dm_correlate_pyramid), the loss (sum of the
+    top-level maxima) and its gradient with respect to both fields
+    (dm_loss_grad: the adjoint through rectification, shifted averages,
+    max-pool argmax and the level-0 correlation, the level-0 maps recomputed).
+    K steps timed with CUDA events; the loss-and-gradient calls alone are timed
+    the same way to split the step."""
+    from paper_1506_07656_gb300 import synth
+    ctx = dm.Context(dm.DM_FP32)
+    try:
+        descs = []
+        wsd = ctx.workspace("desc", W, H, W, H)
+        for k in range(npairs):
+            pr = synth.make_pair_smooth(W, H, seed=5000 + k, max_disp=16.0, with_flow=False)
+            pair = []
+            for img in (pr.img1, pr.img2):
+                d = torch.empty((H, W, 9), dtype=torch.float32, device="cuda")
+                dm.dm_descriptors(ctx.ctx, torch.from_numpy(img).cuda(), d, wsd, stream)
+                pair.append(d)
+            descs.append(pair)
+        wsp = torch.empty(dm.dm_workspace_bytes(ctx.ctx, W, H, W, H)["pyramid"], dtype=torch.uint8, device="cuda")
+        wsg = torch.empty(dm.dm_grad_workspace_bytes(ctx.ctx, W, H, W, H), dtype=torch.uint8, device="cuda")
+        loss = torch.zeros(npairs, dtype=torch.float32, device="cuda")
+        grads = [(torch.empty_like(d1), torch.empty_like(d2)) for d1, d2 in descs]
+
+        def step():
+            for k, (d1, d2) in enumerate(descs):
+                h = dm.dm_correlate_pyramid(ctx.ctx, d1, d2, wsp, stream)
+                dm.dm_loss_grad(ctx.ctx, h, d1, d2, wsg, loss[k:k + 1], None, grads[k][0], grads[k][1], stream)
+                dm.dm_pyramid_free(h)
+
+        launches0 = dm.dm_timing_read(ctx.ctx)[2]
+        step()
+        launches = dm.dm_timing_read(ctx.ctx)[2] - launches0
+        for _ in range(max(a.warmup - 1, 1)):
+            step()
+        torch.cuda.synchronize()
+        steps = max(min(a.steps, 10), 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        # the adjoint alone (pyramids of the last pair kept; loss + gradient repeated)
+        d1, d2 = descs[-1]
+        h = dm.dm_correlate_pyramid(ctx.ctx, d1, d2, wsp, stream)
+        e0.record(stream)
+        for _ in range(steps):
+            dm.dm_loss_grad(ctx.ctx, h, d1, d2, wsg, loss[-1:], None, grads[-1][0], grads[-1][1], stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        grad_ms = e0.elapsed_time(e1) / steps
+        dm.dm_pyramid_free(h)
+        g = dm.dm_geometry(W, H, W, H)
+        gnorm = float(sum(float(torch.linalg.vector_norm(x)) ** 2 + float(torch.linalg.vector_norm(y)) ** 2
+                          for x, y in grads)) ** 0.5
+        # level-0 backward as dense products: two (1/16) dC0-weighted GEMMs of P0 x W2H2 x 144
+        flop_l0 = 2 * 2.0 * g["n_patch0"] * W * H * 144
+    finally:
+        ctx.close()
+    return {"workload": f"{npairs} pairs of {W}x{H}, FP32 descriptor fields as leaves; loss = sum of the top-level "
+                        f"maxima; forward pyramid + loss + gradient w.r.t. both fields per pair",
+            "precision": "fp32", "pairs_per_s": npairs * 1000.0 / ms, "ms_per_step": ms,
+            "loss_grad_ms_per_pair": grad_ms, "forward_ms_per_pair": ms / npairs - grad_ms,
+            "kernel_launches_per_step": int(launches), "loss": [float(x) for x in loss.cpu()],
+            "grad_l2_norm": gnorm, "level0_backward_flop_per_pair": flop_l0,
+            "level0_backward_tflops_lower_bound": flop_l0 / (grad_ms * 1e-3) / 1e12}
+
+
 def _measure_batch(dm, torch, ctx, a, rank):
     """Batched form: 48 pairs, 12 of each size, value noise + smooth warp with
     per-pair seeds, matched by dm_match_batch inside one captured CUDA graph;
@@ -737,6 +811,10 @@ def run_ours(a):
     if not a.no_invariant and world == 1:
         invariant = _measure_invariant(dm, torch, a, stream)
         torch.cuda.empty_cache()
+    grad = None
+    if not a.no_grad and world == 1:
+        grad = _measure_grad(dm, torch, a, stream)
+        torch.cuda.empty_cache()
 
     if rank == 0:
         peaks = {}
@@ -795,6 +873,7 @@ def run_ours(a):
             "star": star,
             "deepflow": deepflow,
             "invariant": invariant,
+            "differentiable": grad,
             "stages_ms": r["stages"],
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_v, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

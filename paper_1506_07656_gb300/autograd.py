@@ -12,6 +12,29 @@ import torch
 from . import dm
 
 
+class _PyramidHandle:
+    """Owns a pyramid handle of dm_correlate_pyramid (host-side views into the
+    caller's workspace) and frees it exactly once: at release() after the
+    backward, or when the autograd graph holding it is dropped without one."""
+    live = 0                     # handles not yet freed (for tests)
+
+    def __init__(self, handle: int):
+        self.handle = handle
+        _PyramidHandle.live += 1
+
+    def release(self) -> None:
+        if self.handle:
+            dm.dm_pyramid_free(self.handle)
+            self.handle = 0
+            _PyramidHandle.live -= 1
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:        # interpreter shutdown: the library may be gone
+            pass
+
+
 class _TopMaxLoss(torch.autograd.Function):
     @staticmethod
     def forward(ctx, desc1, desc2, context):
@@ -27,7 +50,7 @@ class _TopMaxLoss(torch.autograd.Function):
         loss = torch.zeros(1, dtype=torch.float32, device=d1.device)
         dm.dm_loss_grad(context.ctx, pyr, d1, d2, ws_grad, loss)
         ctx.save_for_backward(d1, d2)
-        ctx.state = (context, pyr, ws_pyr, ws_grad)
+        ctx.state = (context, _PyramidHandle(pyr), ws_pyr, ws_grad)
         return loss[0]
 
     @staticmethod
@@ -37,8 +60,8 @@ class _TopMaxLoss(torch.autograd.Function):
         g1 = torch.empty_like(d1)
         g2 = torch.empty_like(d2)
         loss = torch.zeros(1, dtype=torch.float32, device=d1.device)
-        dm.dm_loss_grad(context.ctx, pyr, d1, d2, ws_grad, loss, None, g1, g2)
-        dm.dm_pyramid_free(pyr)
+        dm.dm_loss_grad(context.ctx, pyr.handle, d1, d2, ws_grad, loss, None, g1, g2)
+        pyr.release()
         ctx.state = None
         return grad * g1, grad * g2, None
 
