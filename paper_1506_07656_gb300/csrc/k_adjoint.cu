@@ -10,11 +10,13 @@
 // deterministic.  Per level two dense arrays are used: dA_l on the map
 // domain of level l (unrectified averages) and dP_l in the pooled layout.
 // Level 0 is recomputed rather than stored: the unrectified C0 at an argmax
-// position is one 144-term dot product, and the two level-0 products
+// position is one 144-term dot product.  Of the two level-0 products
 //   G1[p][k] = (1/16) sum_t dC0(p,t) b_t[k],   Gim[t][k] = (1/16) sum_p dC0(p,t) a_p[k]
-// are dense FP32 GEMMs over chunks of patches (the dense dC0 block of a chunk
-// is the only large temporary), followed by the scatter of G1 onto the
-// atomic windows of I and the col2im gather of Gim onto the pixels of I'.
+// G1 is a gather over the nonzeros of dC0 (at most one per pooled output),
+// one warp per patch; Gim is a dense FP32 GEMM over chunks of patches (the
+// dense dC0 block of a chunk is the only large temporary).  Then G1 is
+// scattered onto the atomic windows of I and Gim gathered (col2im) onto the
+// pixels of I'.
 #include "dm_internal.cuh"
 
 namespace {
@@ -181,88 +183,154 @@ __global__ void k_adj_im2col(DmGeom g, const float* __restrict__ d1, const float
     }
 }
 
-// dC0 for patches [p0, p0 + pc): dense [pc][W2*H2]; nonzero only at argmax
-// positions of the pooled level-0 map, where dC0 = sum dP0 * lam C0^(lam-1)
-// with C0 recomputed as the 144-term dot product.
-__global__ void k_adj_dc0(DmGeom g, int p0, int pc, const float* __restrict__ dP0, const unsigned char* __restrict__ amax0,
-                          const float* __restrict__ Am, const float* __restrict__ Bm, float lam, float* __restrict__ dC) {
-    const int pl = blockIdx.y;
+// G1[p][k] = (1/16) sum over the pooled positions r of patch p (row-major order)
+// with dP0(p, r) != 0 of dP0(p, r) * lam C0(p, t_r)^(lam-1) * b_{t_r}[k], t_r the
+// argmax position of r -- the level-0 product dC0 * B restricted to its
+// nonzeros (at most one per pooled output; dC0 is zero elsewhere).  One warp
+// per patch: lanes scan 32 pooled positions at a time, the warp takes their
+// nonzeros in order; lane j holds k = j + 32 i (i < 5) of the accumulator and
+// of the dot product C0 = (1/16) a_p . b_t (lane partials, then a fixed
+// butterfly sum).  Deterministic: a fixed order throughout.
+// It also writes the same coefficients into row p - p0 of the dense dC0 block
+// of patches [p0, p0 + pc) (zeroed before), added in the same order where two
+// pooled positions share an argmax position, for the other product.
+__global__ void __launch_bounds__(256) k_adj_g1_sparse(DmGeom g, int p0, int pc, const float* __restrict__ dP0,
+                                                      const unsigned char* __restrict__ amax0,
+                                                      const float* __restrict__ Am, const float* __restrict__ Bm,
+                                                      float lam, float* __restrict__ G1, float* __restrict__ dC) {
+    const int lane = threadIdx.x & 31;
+    const int pl = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (pl >= pc) return;
     const int p = p0 + pl;
-    const int W2 = g.W2, H2 = g.H2;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= W2 * H2 || pl >= pc) return;
-    const int tx = t % W2, ty = t / W2;
-    const int pw = g.dw[1], ph = g.dh[1], pitch = g.pitch(1);
-    float dsum = 0.0f;
-    for (int ry = ty >> 1; ry <= (ty + 1) >> 1; ry++) {
-        if (ry >= ph) continue;
-        for (int rx = tx >> 1; rx <= (tx + 1) >> 1; rx++) {
-            if (rx >= pw) continue;
-            const long long o = (long long)p * g.psize(1) + (long long)ry * pitch + rx;
-            const int code = amax0[o];
-            if (2 * rx + code % 3 - 1 != tx || 2 * ry + code / 3 - 1 != ty) continue;
-            dsum = __fadd_rn(dsum, dP0[o]);
-        }
+    float* dcrow = dC + (long long)pl * g.W2 * g.H2;
+    const int pw = g.dw[1], ph = g.dh[1], pitch = g.pitch(1), W2 = g.W2;
+    const float* dp = dP0 + (long long)p * g.psize(1);
+    const unsigned char* am = amax0 + (long long)p * g.psize(1);
+    float a[5], acc[5];
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        const int k = lane + 32 * i;
+        a[i] = k < 144 ? __ldg(Am + (long long)p * 144 + k) : 0.0f;
+        acc[i] = 0.0f;
     }
-    float out = 0.0f;
-    if (dsum != 0.0f) {
-        const float* a = Am + (long long)p * 144;
-        const float* b = Bm + (long long)t * 144;
-        float acc = 0.0f;
-        for (int k = 0; k < 144; k++) acc = __fmaf_rn(a[k], b[k], acc);
-        out = __fmul_rn(dsum, dpow(__fmul_rn(acc, 0.0625f), lam));
-    }
-    dC[(long long)pl * W2 * H2 + t] = out;
-}
-
-// C[m][n] (+)= alpha * sum_k A(m,k) B[k][n], A(m,k) = TRANS_A ? A[k*lda + m] : A[m*lda + k];
-// 64 x 48 tiles, K steps of 16, 256 threads, 4 x 3 outputs per thread.
-template <bool TRANS_A, bool ACCUM>
-__global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, float alpha, const float* __restrict__ A, long long lda,
-                                               const float* __restrict__ B, int ldb, float* __restrict__ C, int ldc) {
-    constexpr int BM = 64, BN = 48, BK = 16;
-    __shared__ float As[BK][BM + 4];
-    __shared__ float Bs[BK][BN];
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-    const int tid = threadIdx.x;
-    const int tm = (tid % 16) * 4, tn = (tid / 16) * 3;
-    float acc[4][3] = {};
-    for (int k0 = 0; k0 < K; k0 += BK) {
-        for (int e = tid; e < BM * BK; e += 256) {
-            int mm, kk;
-            if (TRANS_A) { mm = e % BM; kk = e / BM; }
-            else { kk = e % BK; mm = e / BK; }
-            const int gm = m0 + mm, gk = k0 + kk;
-            float v = 0.0f;
-            if (gm < M && gk < K) v = TRANS_A ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
-            As[kk][mm] = v;
-        }
-        for (int e = tid; e < BK * BN; e += 256) {
-            const int nn = e % BN, kk = e / BN;
-            const int gn = n0 + nn, gk = k0 + kk;
-            Bs[kk][nn] = (gn < N && gk < K) ? B[(long long)gk * ldb + gn] : 0.0f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; kk++) {
-#pragma unroll
-            for (int i = 0; i < 4; i++)
-#pragma unroll
-                for (int j = 0; j < 3; j++) acc[i][j] = __fmaf_rn(As[kk][tm + i], Bs[kk][tn + j], acc[i][j]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            const int gm = m0 + tm + i, gn = n0 + tn + j;
-            if (gm < M && gn < N) {
-                float* o = C + (long long)gm * ldc + gn;
-                const float v = __fmul_rn(alpha, acc[i][j]);
-                *o = ACCUM ? __fadd_rn(*o, v) : v;
+    const int n = pw * ph;
+    for (int r0 = 0; r0 < n; r0 += 32) {
+        const int r = r0 + lane;
+        float d = 0.0f;
+        int t = 0;
+        if (r < n) {
+            const int rx = r % pw, ry = r / pw;
+            d = dp[(long long)ry * pitch + rx];
+            if (d != 0.0f) {
+                const int code = am[(long long)ry * pitch + rx];
+                const int tx = 2 * rx + code % 3 - 1, ty = 2 * ry + code / 3 - 1;
+                // (the forward's pooling only ever points inside I')
+                if (code <= 8 && tx >= 0 && ty >= 0 && tx < W2 && ty < g.H2) t = ty * W2 + tx;
+                else d = 0.0f;
             }
         }
+        unsigned int nz = __ballot_sync(0xffffffffu, d != 0.0f);
+        while (nz) {
+            const int src = __ffs(nz) - 1;
+            nz &= nz - 1;
+            const float dv = __shfl_sync(0xffffffffu, d, src);
+            const int tv = __shfl_sync(0xffffffffu, t, src);
+            const float* b = Bm + (long long)tv * 144;
+            float bk[5], part = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 5; i++) {
+                const int k = lane + 32 * i;
+                bk[i] = k < 144 ? __ldg(b + k) : 0.0f;
+                part = __fmaf_rn(a[i], bk[i], part);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part = __fadd_rn(part, __shfl_xor_sync(0xffffffffu, part, o));
+            const float c = __fmul_rn(dv, dpow(__fmul_rn(part, 0.0625f), lam));   // this r's share of dC0(p, t)
+            const float w = __fmul_rn(c, 0.0625f);
+#pragma unroll
+            for (int i = 0; i < 5; i++) acc[i] = __fmaf_rn(w, bk[i], acc[i]);
+            if (lane == 0) dcrow[tv] = __fadd_rn(dcrow[tv], c);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        const int k = lane + 32 * i;
+        if (k < 144) G1[(long long)p * 144 + k] = acc[i];
+    }
+}
+
+// C[m][n] (+)= alpha * sum_k A[k][m] B[k][n] for n < 144: the transposed
+// product of the level-0 backward (m = position of I', k = patch, n = the 144
+// window entries).  128 x 144 tiles, K steps of 16, 256 threads, each 8 rows
+// (m = 8 tm ..) x 9 columns (n = tn + 16 j) of the tile, the next K step's
+// tiles prefetched into registers while the current one is multiplied.
+__global__ void __launch_bounds__(256, 2) k_sgemm_tn144(int M, int K, float alpha, const float* __restrict__ A, long long lda,
+                                                    const float* __restrict__ B, float* __restrict__ C, int accum) {
+    constexpr int BM = 128, BN = 144, BK = 16;
+    __shared__ __align__(16) float As[BK][BM];
+    __shared__ float Bs[BK][BN];
+    const int m0 = blockIdx.x * BM;
+    const int tid = threadIdx.x;
+    const int tm = tid >> 4, tn = tid & 15;
+    float acc[8][9] = {};
+    float ra[8], rb[9];
+    auto fetch = [&](int k0) {
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+            const int idx = tid + 256 * e, kk = idx >> 7, mm = idx & 127;
+            const int gm = m0 + mm, gk = k0 + kk;
+            ra[e] = (gm < M && gk < K) ? __ldg(A + (long long)gk * lda + gm) : 0.0f;
+        }
+#pragma unroll
+        for (int e = 0; e < 9; e++) {
+            const int idx = tid + 256 * e, kk = idx / BN, nn = idx % BN;
+            const int gk = k0 + kk;
+            rb[e] = gk < K ? __ldg(B + (long long)gk * BN + nn) : 0.0f;
+        }
+    };
+    auto stash = [&]() {
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+            const int idx = tid + 256 * e;
+            As[idx >> 7][idx & 127] = ra[e];
+        }
+#pragma unroll
+        for (int e = 0; e < 9; e++) {
+            const int idx = tid + 256 * e;
+            Bs[idx / BN][idx % BN] = rb[e];
+        }
+    };
+    fetch(0);
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        stash();
+        __syncthreads();
+        if (k0 + BK < K) fetch(k0 + BK);
+#pragma unroll
+        for (int kk = 0; kk < BK; kk++) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][8 * tm]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][8 * tm + 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            float bv[9];
+#pragma unroll
+            for (int j = 0; j < 9; j++) bv[j] = Bs[kk][tn + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 8; i++)
+#pragma unroll
+                for (int j = 0; j < 9; j++) acc[i][j] = __fmaf_rn(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const int gm = m0 + 8 * tm + i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 9; j++) {
+            float* o = C + (long long)gm * BN + tn + 16 * j;
+            const float v = __fmul_rn(alpha, acc[i][j]);
+            *o = accum ? __fadd_rn(*o, v) : v;
+        }
+    }
 }
 
 // g1[y][x][c] = G1[patch of (x, y)][(y%4*4 + x%4)*9 + c] (0 outside every atomic window).
@@ -357,19 +425,14 @@ cudaError_t dm_launch_loss_grad(const DmGeom& g, const dm_pyramid& py, const flo
     launches++;
     for (long long p0 = 0; p0 < n0; p0 += gl.chunk) {
         const int pc = (int)(n0 - p0 < gl.chunk ? n0 - p0 : gl.chunk);
-        dim3 gd(nb(T, 128), pc);
-        k_adj_dc0<<<gd, 128, 0, st>>>(g, (int)p0, pc, reinterpret_cast<const float*>(ws + gl.dP[0]), py.amax[0], Am, Bm,
-                                      lam, dC);
-        // G1[p0 .. p0+pc) = (1/16) dC [pc x T] * Bm [T x 144]
-        dim3 gg1(nb(pc, 64), nb(144, 48));
-        k_sgemm<false, false><<<gg1, 256, 0, st>>>(pc, 144, (int)T, 0.0625f, dC, T, Bm, 144, G1 + p0 * 144, 144);
+        // the chunk's dC0 rows and G1 rows from the nonzeros of dC0
+        cudaError_t e = cudaMemsetAsync(dC, 0, (size_t)pc * T * sizeof(float), st);
+        if (e != cudaSuccess) return e;
+        k_adj_g1_sparse<<<nb(pc, 8), 256, 0, st>>>(g, (int)p0, pc, reinterpret_cast<const float*>(ws + gl.dP[0]),
+                                                   py.amax[0], Am, Bm, lam, G1, dC);
         // Gim (+)= (1/16) dC^T [T x pc] * Am[p0 .. p0+pc) [pc x 144]
-        dim3 gg2(nb(T, 64), nb(144, 48));
-        if (p0 == 0)
-            k_sgemm<true, false><<<gg2, 256, 0, st>>>((int)T, 144, pc, 0.0625f, dC, T, Am + p0 * 144, 144, Gim, 144);
-        else
-            k_sgemm<true, true><<<gg2, 256, 0, st>>>((int)T, 144, pc, 0.0625f, dC, T, Am + p0 * 144, 144, Gim, 144);
-        launches += 3;
+        k_sgemm_tn144<<<nb(T, 128), 256, 0, st>>>((int)T, pc, 0.0625f, dC, T, Am + p0 * 144, Gim, p0 != 0);
+        launches += 2;
     }
     k_adj_g1<<<nb((long long)g.W1 * g.H1 * 9, 256), 256, 0, st>>>(g, G1, g1);
     k_adj_g2<<<nb(T * 9, 256), 256, 0, st>>>(g, Gim, g2);
