@@ -36,8 +36,8 @@
 // drain the accumulators: four warps per TMEM lane quadrant, each owning four
 // of the sixteen pooled columns (C0 columns 8w'..8w'+8) over the three pooled
 // rows: 14 tcgen05.ld in three batches of rows (each batch in flight while the
-// rows before it are pooled), pool with the first-strict-maximum argmax rule
-// (scan my = -1..1, then mx), release the accumulator after the last batch,
+// rows before it are pooled), pool on order-preserving keys that carry the
+// position (first maximum in scan order), release the accumulator after the last batch,
 // raise to lambda (MUFU-based power), stage, store through TMA.
 // FP8 form: the same kernel with E4M3 operands (tcgen05.mma kind::f8f6f4,
 // K padded 144 -> 160, five MMAs of K = 32).  Each patch vector is scaled by a
@@ -258,13 +258,21 @@ __device__ __forceinline__ void tmem_row_ready(uint32_t (&r)[9]) {
 
 __device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Horizontal step of the separable 3x3 / 2 pooling for C0 row ly: the
-// 3-maxima of the column triples (2k, 2k+1, 2k+2) and the first column
-// holding each (out-of-image positions are -inf).
-__device__ __forceinline__ void pool_row(const EpiArgs& e, int tx0, int ly, const uint32_t (&r)[9], float (&h)[4], int (&hc)[4]) {
+// Pooling on order-preserving keys.  An accumulator value is non-negative, so
+// its bits order like the value; replacing its 7 low mantissa bits by 127 -
+// (16 ly + c), ly the C0 row (0..6) and c the column (0..8) of this thread's
+// block, makes every key distinct and, among values equal above those bits, the
+// key of the position first in scan order (rows, then columns) the largest.
+// The 3x3 maximum of the keys then gives the pooled value (within 127 units of
+// its last place: 2^-16 relative, far below the BF16 / E4M3 operand rounding)
+// and, from its low bits, the argmax code, with no comparisons.
+//
+// Horizontal step for C0 row ly: the key maxima of the column triples (2k,
+// 2k+1, 2k+2); positions outside I' are -inf.
+__device__ __forceinline__ void pool_row(const EpiArgs& e, int tx0, int ly, const uint32_t (&r)[9], float (&h)[4]) {
     float v[9];
 #pragma unroll
-    for (int c = 0; c < 9; c++) v[c] = __uint_as_float(r[c]);
+    for (int c = 0; c < 9; c++) v[c] = __uint_as_float((r[c] & ~0x7Fu) | (uint32_t)(127 - (16 * ly + c)));
     if (!e.interior) {
         const int ty = e.cy0 + ly;
         const bool rin = ty >= 0 && ty < e.H2;
@@ -275,24 +283,21 @@ __device__ __forceinline__ void pool_row(const EpiArgs& e, int tx0, int ly, cons
         }
     }
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const float m = fmax3(v[2 * k], v[2 * k + 1], v[2 * k + 2]);
-        h[k] = m;
-        hc[k] = v[2 * k] == m ? 0 : (v[2 * k + 1] == m ? 1 : 2);
-    }
+    for (int k = 0; k < 4; k++) h[k] = fmax3(v[2 * k], v[2 * k + 1], v[2 * k + 2]);
 }
 
-// Vertical step for pooled row y (C0 rows 2y, 2y+1, 2y+2 = m_y -1, 0, +1; the
-// first row holding the maximum, so the first maximum in scan order), the
-// power, and the staging of the 4 values and codes.
-__device__ __forceinline__ void pool_out(const EpiArgs& e, int y, float mult, const float (&h)[CY][4], const int (&hc)[CY][4],
+// Vertical step for pooled row y (C0 rows 2y, 2y+1, 2y+2 = m_y -1, 0, +1): the
+// key maximum, its code 3 (row - 2y) + (c - 2k) from the low bits, the power,
+// and the staging of the 4 values and codes.
+__device__ __forceinline__ void pool_out(const EpiArgs& e, int y, float mult, const float (&h)[CY][4],
                                          float* stage_f, unsigned char* stage_c) {
     float f[4];
     uint32_t codes = 0;
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         const float m = fmax3(h[2 * y][k], h[2 * y + 1][k], h[2 * y + 2][k]);
-        const int code = h[2 * y][k] == m ? hc[2 * y][k] : (h[2 * y + 1][k] == m ? 3 + hc[2 * y + 1][k] : 6 + hc[2 * y + 2][k]);
+        const int idx = (int)(~__float_as_uint(m) & 0x7Fu);          // 16 row + c of the winner
+        const int code = idx - 13 * (idx >> 4) - (6 * y + 2 * k);     // 3 row + c - (6 y + 2 k)
         f[k] = __powf(m * mult, e.lam);
         codes |= (uint32_t)code << (8 * k);
     }
@@ -320,7 +325,6 @@ __device__ __forceinline__ void epilogue_tile(const EpiArgs& e, uint32_t b, uint
                                               float* stage_f, unsigned char* stage_c) {
     uint32_t r[CY][9];
     float h[CY][4];
-    int hc[CY][4];
     const uint32_t taddr = e.taddr + b * 256 + 8 * e.part;
     const int tx0 = e.cx0 + 8 * e.part;
 #pragma unroll
@@ -331,16 +335,16 @@ __device__ __forceinline__ void epilogue_tile(const EpiArgs& e, uint32_t b, uint
 #pragma unroll
     for (int ly = 3; ly < 5; ly++) tmem_row(taddr, ly, r[ly]);
 #pragma unroll
-    for (int ly = 0; ly < 3; ly++) pool_row(e, tx0, ly, r[ly], h[ly], hc[ly]);
-    pool_out(e, 0, mult, h, hc, stage_f, stage_c);
+    for (int ly = 0; ly < 3; ly++) pool_row(e, tx0, ly, r[ly], h[ly]);
+    pool_out(e, 0, mult, h, stage_f, stage_c);
     tmem_wait();
 #pragma unroll
     for (int ly = 3; ly < 5; ly++) tmem_row_ready(r[ly]);
 #pragma unroll
     for (int ly = 5; ly < 7; ly++) tmem_row(taddr, ly, r[ly]);
 #pragma unroll
-    for (int ly = 3; ly < 5; ly++) pool_row(e, tx0, ly, r[ly], h[ly], hc[ly]);
-    pool_out(e, 1, mult, h, hc, stage_f, stage_c);
+    for (int ly = 3; ly < 5; ly++) pool_row(e, tx0, ly, r[ly], h[ly]);
+    pool_out(e, 1, mult, h, stage_f, stage_c);
     tmem_wait();
 #pragma unroll
     for (int ly = 5; ly < 7; ly++) tmem_row_ready(r[ly]);
@@ -348,8 +352,8 @@ __device__ __forceinline__ void epilogue_tile(const EpiArgs& e, uint32_t b, uint
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     mbar_arrive(bar_empty);
 #pragma unroll
-    for (int ly = 5; ly < 7; ly++) pool_row(e, tx0, ly, r[ly], h[ly], hc[ly]);
-    pool_out(e, 2, mult, h, hc, stage_f, stage_c);
+    for (int ly = 5; ly < 7; ly++) pool_row(e, tx0, ly, r[ly], h[ly]);
+    pool_out(e, 2, mult, h, stage_f, stage_c);
 }
 
 template <int FMT>
