@@ -620,9 +620,10 @@ def _measure_batch(dm, torch, ctx, a, rank):
 def _measure_batch_uniform(dm, torch, dist, ctx, a, world, local, rank, W, H, npairs):
     """BF16 batched form at one size: `npairs` pairs per step in the concurrent
     lanes of dm_match_batch, captured once in a CUDA graph; K timed replays
-    (device-resident inputs), then K end-to-end steps that also copy every
-    pair's images from pinned host memory and the match counts and matches
-    back, inside the timed region."""
+    (device-resident inputs), then K end-to-end steps through
+    dm_match_batch_host (also one graph): every pair's images copied in from
+    page-locked host memory and its matches and count copied back, inside the
+    timed region."""
     from paper_1506_07656_gb300 import synth
     items, host = [], []
     n0 = dm.dm_geometry(W, H, W, H)["n_patch0"]
@@ -669,33 +670,38 @@ def _measure_batch_uniform(dm, torch, dist, ctx, a, world, local, rank, W, H, np
         st, _ = dm.dm_read_status(ctx.ctx, ws[j * lane_bytes:], 1)
         statuses.append(st)
     n_match = [int(it[3].item()) for it in items]
-    # end to end: host images in, counts and matches out, every step
-    hout = [torch.empty((n0, 5), dtype=torch.float32).pin_memory() for _ in range(npairs)]
-    hcnt = torch.empty(npairs, dtype=torch.int32).pin_memory()
-
-    def e2e_step():
-        with torch.cuda.stream(side):
-            for (i1, i2, _, _), (h1, h2) in zip(items, host):
-                i1.copy_(h1, non_blocking=True)
-                i2.copy_(h2, non_blocking=True)
-            graph.replay()
-            for k, (_, _, out, cnt) in enumerate(items):
-                hcnt[k:k + 1].copy_(cnt, non_blocking=True)
-                hout[k].copy_(out, non_blocking=True)
-        side.synchronize()
-
+    del graph
+    # end to end through the library's host-buffer entry point: every step, each
+    # pair's images are copied in from page-locked host memory and its matches
+    # and count copied back, inside the lanes (dm_match_batch_host, one graph)
+    hitems = [(h1, h2, torch.empty((n0, 5), dtype=torch.float32).pin_memory(),
+               torch.zeros(1, dtype=torch.int32).pin_memory()) for (h1, h2) in host]
+    hpairs = dm.make_pairs_host(hitems)
+    del ws
+    torch.cuda.empty_cache()
+    hws = torch.empty(dm.dm_batch_host_workspace_bytes(ctx.ctx, hpairs), dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(side):
+        dm.dm_match_batch_host(ctx.ctx, hpairs, hws, side)
+    torch.cuda.synchronize()
+    hgraph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(hgraph, stream=side):
+        dm.dm_match_batch_host(ctx.ctx, hpairs, hws, side)
     for _ in range(max(1, a.warmup)):
-        e2e_step()
+        hgraph.replay()
+    torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(a.steps):
-        e2e_step()
+        hgraph.replay()
+    torch.cuda.synchronize()
     e2e_s = _max_over_ranks(torch, dist, time.perf_counter() - t0, world, "cuda")
-    del graph
+    e2e_matches = [int(h[3].item()) for h in hitems]
+    del hgraph, hws
     return {"value": _job_throughput(world, a.steps * npairs, ms / 1e3), "ms": ms, "pairs_per_step": npairs,
             "e2e": _job_throughput(world, a.steps * npairs, e2e_s), "launches": launches_per_step * a.steps,
             "clocks": clk.summary(), "status": max(statuses) if statuses else 0, "matches": n_match,
+            "e2e_matches_equal": e2e_matches == n_match,
             "tuned": tuned, "h2d_bytes_per_step": npairs * 2 * W * H * 4,
             "d2h_bytes_per_step": npairs * (n0 * 20 + 4)}
 

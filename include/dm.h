@@ -395,6 +395,33 @@ typedef struct {
  * (dm_read_status on d_ws + j * lane_bytes reads the last pair of lane j). */
 dm_status dm_batch_workspace_bytes(const dm_ctx* ctx, int n, const dm_pair* pairs, size_t* bytes);
 dm_status dm_match_batch(dm_ctx* ctx, int n, const dm_pair* pairs, void* d_ws, size_t ws_bytes, void* stream);
+/* One image pair of a host-buffer batch: images and outputs in host memory. */
+typedef struct {
+    const float* h_img1;
+    int W1, H1;
+    const float* h_img2;
+    int W2, H2;
+    dm_match_t* h_out;    /* first min(capacity, number of atomic patches) rows are written */
+    int capacity;
+    int* h_count;         /* number of matches (may exceed capacity: then only capacity rows) */
+} dm_pair_host;
+
+/* Batched form with host buffers (the whole chain as one call from host
+ * memory: no counterpart in the paper).  As dm_match_batch, but every pair's
+ * images are copied from host memory into its lane's workspace slice, and its
+ * matches and count copied back to host memory, inside the lane: the copies of
+ * one pair overlap the compute of the pairs in the other lanes.  Everything is
+ * asynchronous on the lanes and `stream`; the host buffers must stay valid,
+ * and the results are there, once `stream` has completed.  With page-locked
+ * host buffers the copies are truly asynchronous and the whole call can be
+ * captured in a CUDA graph (make one uncaptured call first); with pageable
+ * buffers the copies are staged synchronously by the CUDA runtime and the call
+ * cannot be captured.  A count above the capacity is reported only through
+ * *h_count.  dm_batch_host_workspace_bytes gives lanes * lane_bytes as for
+ * dm_match_batch (lane_bytes = the largest match_bytes over the pairs). */
+dm_status dm_batch_host_workspace_bytes(const dm_ctx* ctx, int n, const dm_pair_host* pairs, size_t* bytes);
+dm_status dm_match_batch_host(dm_ctx* ctx, int n, const dm_pair_host* pairs, void* d_ws, size_t ws_bytes, void* stream);
+
 /* Number of concurrent lanes of dm_match_batch and dm_match_invariant, 1..4
  * (1: one pair, or one transform, after the other on `stream`). */
 dm_status dm_set_batch_lanes(dm_ctx* ctx, int lanes);

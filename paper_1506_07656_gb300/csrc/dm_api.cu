@@ -893,6 +893,104 @@ dm_status dm_match_batch(dm_ctx* ctx, int n, const dm_pair* pairs, void* d_ws, s
     return DM_OK;
 }
 
+namespace {
+// One pair of a host-buffer batch on stream `st` in the workspace slice `base`:
+// its images copied into the slice's image slots, matched, and the matches and
+// the count copied back (all asynchronous).
+dm_status run_host_pair(dm_ctx* ctx, const dm_pair_host& q, char* base, size_t bytes, cudaStream_t st) {
+    DmGeom g;
+    dm_status s = check_geom(ctx, q.W1, q.H1, q.W2, q.H2, &g);
+    if (s != DM_OK) return s;
+    MatchLayout ml;
+    match_layout(g, ctx->cfg.precision, &ml);
+    float* i1 = (float*)(base + ml.img1);
+    float* i2 = (float*)(base + ml.img2);
+    dm_match_t* dout = (dm_match_t*)(base + ml.out);
+    int* dcnt = (int*)(base + ml.count);
+    const int cap_dev = g.npatch(0);   // at most one match per atomic patch
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(i1, q.h_img1, (size_t)q.W1 * q.H1 * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(ctx, e, "dm_match_batch_host: copy image 1");
+    if ((e = cudaMemcpyAsync(i2, q.h_img2, (size_t)q.W2 * q.H2 * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(ctx, e, "dm_match_batch_host: copy image 2");
+    if ((s = dm_match(ctx, i1, q.W1, q.H1, i2, q.W2, q.H2, base, bytes, dout, cap_dev, dcnt, st)) != DM_OK) return s;
+    const int ncopy = q.capacity < cap_dev ? q.capacity : cap_dev;
+    if (ncopy > 0 &&
+        (e = cudaMemcpyAsync(q.h_out, dout, (size_t)ncopy * sizeof(dm_match_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(ctx, e, "dm_match_batch_host: copy matches");
+    if ((e = cudaMemcpyAsync(q.h_count, dcnt, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(ctx, e, "dm_match_batch_host: copy count");
+    return DM_OK;
+}
+
+dm_status batch_host_lane_bytes(dm_ctx* ctx, int n, const dm_pair_host* pairs, size_t* bytes) {
+    size_t best = 256;
+    for (int k = 0; k < n; k++) {
+        size_t mb = 0;
+        dm_status s = dm_workspace_bytes(ctx, pairs[k].W1, pairs[k].H1, pairs[k].W2, pairs[k].H2, nullptr, nullptr,
+                                         nullptr, &mb);
+        if (s != DM_OK) return s;
+        if (mb > best) best = mb;
+    }
+    *bytes = dm_align(best);
+    return DM_OK;
+}
+}  // namespace
+
+dm_status dm_batch_host_workspace_bytes(const dm_ctx* ctx, int n, const dm_pair_host* pairs, size_t* bytes) {
+    if (!ctx || n < 0 || (n > 0 && !pairs) || !bytes) return DM_EINVAL;
+    size_t lane = 0;
+    dm_status s = batch_host_lane_bytes(const_cast<dm_ctx*>(ctx), n, pairs, &lane);
+    if (s != DM_OK) return s;
+    const int lanes = n < ctx->lanes ? (n > 0 ? n : 1) : ctx->lanes;
+    *bytes = lane * (size_t)lanes;
+    return DM_OK;
+}
+
+dm_status dm_match_batch_host(dm_ctx* ctx, int n, const dm_pair_host* pairs, void* d_ws, size_t ws_bytes, void* stream) {
+    if (!ctx) return DM_EINVAL;
+    if (n < 0 || (n > 0 && !pairs) || !d_ws) return fail(ctx, DM_EINVAL, "dm_match_batch_host: bad arguments");
+    if (!aligned256(d_ws)) return fail(ctx, DM_EINVAL, "workspace must be 256-byte aligned");
+    for (int k = 0; k < n; k++) {     // validate everything before copying or launching anything
+        const dm_pair_host& q = pairs[k];
+        if (!q.h_img1 || !q.h_img2 || !q.h_out || !q.h_count || q.capacity < 0)
+            return fail(ctx, DM_EINVAL, "dm_match_batch_host: pair %d: null pointer or negative capacity", k);
+        DmGeom g;
+        dm_status s = check_geom(ctx, q.W1, q.H1, q.W2, q.H2, &g);
+        if (s != DM_OK) return s;
+    }
+    size_t lane_bytes = 0;
+    dm_status s = batch_host_lane_bytes(ctx, n, pairs, &lane_bytes);
+    if (s != DM_OK) return s;
+    if (ws_bytes < lane_bytes)
+        return fail(ctx, DM_ENOMEM, "dm_match_batch_host: needs at least %zu workspace bytes", lane_bytes);
+    if (n == 0) return DM_OK;
+    int lanes = (int)(ws_bytes / lane_bytes);
+    if (lanes > ctx->lanes) lanes = ctx->lanes;
+    if (lanes > n) lanes = n;
+    DevGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (lanes == 1) {
+        for (int k = 0; k < n; k++)
+            if ((s = run_host_pair(ctx, pairs[k], (char*)d_ws, lane_bytes, st)) != DM_OK) return s;
+        return DM_OK;
+    }
+    cudaError_t e = cudaEventRecord(ctx->fork_ev, st);
+    for (int j = 0; e == cudaSuccess && j < lanes; j++) e = cudaStreamWaitEvent(ctx->lane_st[j], ctx->fork_ev, 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "dm_match_batch_host: fork");
+    for (int k = 0; k < n; k++) {
+        const int j = k % lanes;
+        if ((s = run_host_pair(ctx, pairs[k], (char*)d_ws + (size_t)j * lane_bytes, lane_bytes, ctx->lane_st[j])) != DM_OK)
+            return s;
+    }
+    for (int j = 0; e == cudaSuccess && j < lanes; j++) {
+        e = cudaEventRecord(ctx->join_ev[j], ctx->lane_st[j]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->join_ev[j], 0);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "dm_match_batch_host: join");
+    return DM_OK;
+}
+
 // Autotuner.  Each stage's candidates run back to back on the caller's pair,
 // each timed twice with CUDA events (the faster run counts); a candidate
 // replaces the current choice only if it is at least 2% faster, so timing

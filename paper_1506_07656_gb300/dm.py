@@ -43,6 +43,11 @@ class DmPair(C.Structure):
     _fields_ = [("d_img1", C.c_void_p), ("W1", C.c_int), ("H1", C.c_int), ("d_img2", C.c_void_p), ("W2", C.c_int),
                 ("H2", C.c_int), ("d_out", C.c_void_p), ("capacity", C.c_int), ("d_count", C.c_void_p)]
 
+class DmPairHost(C.Structure):
+    _fields_ = [("h_img1", C.c_void_p), ("W1", C.c_int), ("H1", C.c_int), ("h_img2", C.c_void_p),
+                ("W2", C.c_int), ("H2", C.c_int), ("h_out", C.c_void_p), ("capacity", C.c_int), ("h_count", C.c_void_p)]
+
+
 class DmFlowParams(C.Structure):
     _fields_ = [(k, C.c_double) for k in ("sigma", "eta", "gamma", "delta", "beta", "b", "kappa", "zeta", "eps",
                                           "sigma_m", "omega", "image_scale")] + \
@@ -78,6 +83,8 @@ _SIGS = {
     "dm_batch_workspace_bytes": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_size_t)]),
     "dm_match_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "dm_set_batch_lanes": (C.c_int, [C.c_void_p, C.c_int]),
+    "dm_batch_host_workspace_bytes": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_size_t)]),
+    "dm_match_batch_host": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "dm_backtrack_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "dm_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                               C.c_size_t, C.POINTER(C.c_int), C.c_void_p]),
@@ -432,6 +439,31 @@ def dm_match_batch(ctx, pairs, d_ws, stream=None):
     st = load().dm_match_batch(ctx, len(pairs), pairs, _dptr(d_ws), d_ws.numel() * d_ws.element_size(),
                                _stream_ptr(stream))
     _check(ctx, st, "dm_match_batch")
+
+
+def make_pairs_host(items):
+    """items: list of (h_img1, h_img2, h_out, h_count) CPU tensors (page-locked for
+    asynchronous, capturable copies) -> ctypes array of DmPairHost."""
+    arr = (DmPairHost * len(items))()
+    for k, (i1, i2, out, cnt) in enumerate(items):
+        H1, W1 = i1.shape
+        H2, W2 = i2.shape
+        arr[k] = DmPairHost(i1.data_ptr(), W1, H1, i2.data_ptr(), W2, H2, out.data_ptr(),
+                            out.numel() * out.element_size() // MATCH_BYTES, cnt.data_ptr())
+    return arr
+
+
+def dm_batch_host_workspace_bytes(ctx, pairs) -> int:
+    b = C.c_size_t()
+    _check(ctx, load().dm_batch_host_workspace_bytes(ctx, len(pairs), pairs, C.byref(b)),
+           "dm_batch_host_workspace_bytes")
+    return b.value
+
+
+def dm_match_batch_host(ctx, pairs, d_ws, stream=None):
+    st = load().dm_match_batch_host(ctx, len(pairs), pairs, _dptr(d_ws), d_ws.numel() * d_ws.element_size(),
+                                    _stream_ptr(stream))
+    _check(ctx, st, "dm_match_batch_host")
 
 
 def dm_set_batch_lanes(ctx, lanes: int) -> None:

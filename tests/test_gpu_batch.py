@@ -123,3 +123,63 @@ def test_batch_lanes_give_identical_matches(env, lanes):
         dm.dm_set_batch_lanes(ctx.ctx, 2)
     with pytest.raises(dm.DmError):
         dm.dm_set_batch_lanes(ctx.ctx, 5)
+
+
+def _host_items(torch, dm, sizes, seed0):
+    items, host = [], []
+    for k, (W, H) in enumerate(sizes):
+        pr = synth.make_pair_smooth(W, H, seed=seed0 + k)
+        n0 = dm.dm_geometry(W, H, W, H)["n_patch0"]
+        items.append((torch.from_numpy(pr.img1).pin_memory(), torch.from_numpy(pr.img2).pin_memory(),
+                      torch.full((n0, 5), -1.0, dtype=torch.float32).pin_memory(),
+                      torch.full((1,), -1, dtype=torch.int32).pin_memory()))
+        host.append(pr)
+    return items, host
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4])
+def test_host_batch_equals_single_pairs(env, lanes):
+    """dm_match_batch_host: images from (page-locked) host memory, matches and
+    counts back to host memory, inside the lanes; every pair equals dm_match."""
+    torch, dm, ctx = env
+    items, host = _host_items(torch, dm, SIZES, 200)
+    pairs = dm.make_pairs_host(items)
+    try:
+        dm.dm_set_batch_lanes(ctx.ctx, lanes)
+        ws = torch.empty(dm.dm_batch_host_workspace_bytes(ctx.ctx, pairs), dtype=torch.uint8, device="cuda")
+        dm.dm_match_batch_host(ctx.ctx, pairs, ws)
+        torch.cuda.synchronize()
+    finally:
+        dm.dm_set_batch_lanes(ctx.ctx, 2)
+    for (h1, h2, out, cnt), pr in zip(items, host):
+        n = int(cnt.item())
+        np.testing.assert_array_equal(out[:n].numpy(), _single(ctx, pr))
+
+
+def test_host_batch_graph_replay(env):
+    """The host-buffer batch captured in a CUDA graph (copies included) and
+    replayed on new image contents written into the same host buffers."""
+    torch, dm, ctx = env
+    items, _ = _host_items(torch, dm, SIZES, 220)
+    pairs = dm.make_pairs_host(items)
+    ws = torch.empty(dm.dm_batch_host_workspace_bytes(ctx.ctx, pairs), dtype=torch.uint8, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        dm.dm_match_batch_host(ctx.ctx, pairs, ws, side)      # uncaptured first call
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        dm.dm_match_batch_host(ctx.ctx, pairs, ws, side)
+    for seed0 in (240, 260):
+        new = [synth.make_pair_smooth(W, H, seed=seed0 + k) for k, (W, H) in enumerate(SIZES)]
+        for (h1, h2, out, cnt), pr in zip(items, new):
+            h1.copy_(torch.from_numpy(pr.img1))
+            h2.copy_(torch.from_numpy(pr.img2))
+            cnt.fill_(-1)
+        graph.replay()
+        torch.cuda.synchronize()
+        for (h1, h2, out, cnt), pr in zip(items, new):
+            n = int(cnt.item())
+            assert n >= 0
+            np.testing.assert_array_equal(out[:n].numpy(), _single(ctx, pr))
