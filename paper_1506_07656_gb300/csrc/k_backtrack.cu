@@ -83,7 +83,10 @@ __device__ __forceinline__ unsigned int ht_home(unsigned int key, unsigned int c
     return (blk << HT_BLOCK_LOG2) | (key & ((1u << HT_BLOCK_LOG2) - 1u));
 }
 
-__device__ __forceinline__ void ht_insert(const BtArgs& a, int lvl, unsigned int cap, unsigned int key, unsigned int sb) {
+// Merge (key, score) into the level-`lvl` table; returns 1 if the key is new.
+// (New keys are counted by the caller and added to the level's count once per
+// block: a shared counter bumped by every warp serialised the whole pass.)
+__device__ __forceinline__ int ht_insert(const BtArgs& a, int lvl, unsigned int cap, unsigned int key, unsigned int sb) {
     unsigned long long* tab = a.table[lvl];
     const unsigned long long packed = ((unsigned long long)(key + 1u) << 32) | sb;
     unsigned int h = ht_home(key, cap);
@@ -91,19 +94,17 @@ __device__ __forceinline__ void ht_insert(const BtArgs& a, int lvl, unsigned int
         unsigned long long cur = __ldcg(tab + h);
         if (cur == 0ull) {
             unsigned long long prev = atomicCAS(tab + h, 0ull, packed);
-            if (prev == 0ull) {
-                warp_agg_inc(&a.hdr->count[lvl]);
-                return;
-            }
+            if (prev == 0ull) return 1;
             cur = prev;
         }
         if ((unsigned int)(cur >> 32) == key + 1u) {
             if ((unsigned int)cur < sb) atomicMax(tab + h, packed);
-            return;
+            return 0;
         }
         h = (h + 1u == cap) ? 0u : h + 1u;
     }
     atomicOr(&a.hdr->status, DM_DEV_FRONTIER_OVERFLOW);
+    return 0;
 }
 
 __device__ __forceinline__ void leaf_update(const BtArgs& a, int c, int tx, int ty, unsigned int s) {
@@ -193,7 +194,7 @@ __device__ __forceinline__ int expand(const BtArgs& a, int l, unsigned int cap_n
         const unsigned int s2 = (MODE == BT_STAR && l - 1 >= 1) ? s : s + ps_term(val[i]);
         if (l - 1 >= 1) {
             unsigned int key = (unsigned int)cc[i] * (unsigned int)g.dsize(l - 1) + (unsigned int)(ty * g.dw[l - 1] + tx);
-            ht_insert(a, l - 1, cap_next, key, s2);
+            arrivals += ht_insert(a, l - 1, cap_next, key, s2);
         } else {
             if constexpr (MODE == BT_RECT) leaf_update_rect(a, cc[i], tx, ty, s2);
             else leaf_update(a, cc[i], tx, ty, s2);
@@ -203,10 +204,16 @@ __device__ __forceinline__ int expand(const BtArgs& a, int l, unsigned int cap_n
     return arrivals;
 }
 
-__device__ __forceinline__ void add_arrivals(const BtArgs& a, int n) {
-    // every lane of every warp reaches this point
-    int tot = __reduce_add_sync(0xffffffffu, n);
-    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&a.hdr->count[0], (unsigned int)tot);
+// Add the block's count to count[lvl]: a warp sum, a shared-memory sum, one
+// global atomic per block.  Every thread of the block reaches this point.
+__device__ __forceinline__ void add_count(const BtArgs& a, int lvl, int n) {
+    __shared__ unsigned int blk;
+    if (threadIdx.x == 0) blk = 0u;
+    __syncthreads();
+    const int tot = __reduce_add_sync(0xffffffffu, n);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&blk, (unsigned int)tot);
+    __syncthreads();
+    if (threadIdx.x == 0 && blk) atomicAdd(&a.hdr->count[lvl], blk);
 }
 
 // Clear the active part of the level-`lvl` table.  Active size: 12x the
@@ -262,7 +269,7 @@ __global__ void k_bt_expand_top(BtArgs a) {
             }
         }
     }
-    if (L == 1) add_arrivals(a, arrivals);
+    add_count(a, L - 1, arrivals);
 }
 
 // Expansion of level l < L: the merged tuples of level l, read by scanning the
@@ -305,7 +312,7 @@ __global__ void k_bt_expand(BtArgs a, int l) {
         }
     }
     if (lane < qn) run(q[lane]);
-    if (l == 1) add_arrivals(a, arrivals);
+    add_count(a, l - 1, arrivals);
 }
 
 // Reciprocal verification and compaction in atomic-patch order (one block).
@@ -446,11 +453,13 @@ __global__ void __launch_bounds__(256) k_star_entries(BtArgs a, int l, float lam
 __global__ void k_star_insert(BtArgs a, int l) {
     const unsigned int cap = a.hdr->cap[l];
     const unsigned long long n = min((unsigned long long)a.hdr->entries[l], a.elcap[l]);
+    int fresh = 0;
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         const unsigned long long e = a.elist[l][i];
-        ht_insert(a, l, cap, (unsigned int)(e >> 32), (unsigned int)e);
+        fresh += ht_insert(a, l, cap, (unsigned int)(e >> 32), (unsigned int)e);
     }
+    add_count(a, l, fresh);
 }
 
 template <int MODE>
