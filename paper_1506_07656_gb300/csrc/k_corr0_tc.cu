@@ -259,20 +259,26 @@ __device__ __forceinline__ void tmem_row_ready(uint32_t (&r)[9]) {
 __device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Pooling on order-preserving keys.  An accumulator value is non-negative, so
-// its bits order like the value; replacing its 7 low mantissa bits by 127 -
-// (16 ly + c), ly the C0 row (0..6) and c the column (0..8) of this thread's
-// block, makes every key distinct and, among values equal above those bits, the
-// key of the position first in scan order (rows, then columns) the largest.
-// The 3x3 maximum of the keys then gives the pooled value (within 127 units of
-// its last place: 2^-16 relative, far below the BF16 / E4M3 operand rounding)
-// and, from its low bits, the argmax code, with no comparisons.
+// its bits order like the value; its 5 low mantissa bits are replaced by 31 -
+// (3 ly + c), ly the C0 row (0..6) and c the column (0..8) of this thread's
+// block.  Within any 3x3 window (rows 2y..2y+2, columns 2k..2k+2) 3 ly + c is
+// the scan-order rank plus the constant 6y + 2k (a column step of at most 2 never
+// reaches a row step of 3), so among values equal above those bits the key of
+// the position first in scan order is the largest, and the winner's rank is
+// (31 - low bits) - (6y + 2k).  The 3x3 maximum of the keys thus gives the
+// pooled value (within 31 units of its last place: 2^-18 relative, far below
+// the BF16 / E4M3 operand rounding) and its argmax code, with no comparisons.
 //
 // Horizontal step for C0 row ly: the key maxima of the column triples (2k,
 // 2k+1, 2k+2); positions outside I' are -inf.
 __device__ __forceinline__ void pool_row(const EpiArgs& e, int tx0, int ly, const uint32_t (&r)[9], float (&h)[4]) {
+    // the mask lives in a register, so each key is one logic operation with the
+    // position as its immediate
+    uint32_t keep;
+    asm("mov.b32 %0, %1;" : "=r"(keep) : "n"(0xFFFFFFE0u));
     float v[9];
 #pragma unroll
-    for (int c = 0; c < 9; c++) v[c] = __uint_as_float((r[c] & ~0x7Fu) | (uint32_t)(127 - (16 * ly + c)));
+    for (int c = 0; c < 9; c++) v[c] = __uint_as_float((r[c] & keep) | (uint32_t)(31 - (3 * ly + c)));
     if (!e.interior) {
         const int ty = e.cy0 + ly;
         const bool rin = ty >= 0 && ty < e.H2;
@@ -286,6 +292,15 @@ __device__ __forceinline__ void pool_row(const EpiArgs& e, int tx0, int ly, cons
     for (int k = 0; k < 4; k++) h[k] = fmax3(v[2 * k], v[2 * k + 1], v[2 * k + 2]);
 }
 
+// x^lam = 2^(lam log2 x) with the hardware's approximate base-2 logarithm and
+// exponential (x in (0, 1]: pooled C0 values, never subnormal; 0 gives 0).
+__device__ __forceinline__ float pow_hw(float x, float lam) {
+    float l, r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(x));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(__fmul_rn(l, lam)));
+    return r;
+}
+
 // Vertical step for pooled row y (C0 rows 2y, 2y+1, 2y+2 = m_y -1, 0, +1): the
 // key maximum, its code 3 (row - 2y) + (c - 2k) from the low bits, the power,
 // and the staging of the 4 values and codes.
@@ -296,9 +311,8 @@ __device__ __forceinline__ void pool_out(const EpiArgs& e, int y, float mult, co
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         const float m = fmax3(h[2 * y][k], h[2 * y + 1][k], h[2 * y + 2][k]);
-        const int idx = (int)(~__float_as_uint(m) & 0x7Fu);          // 16 row + c of the winner
-        const int code = idx - 13 * (idx >> 4) - (6 * y + 2 * k);     // 3 row + c - (6 y + 2 k)
-        f[k] = __powf(m * mult, e.lam);
+        const int code = (int)(~__float_as_uint(m) & 0x1Fu) - (6 * y + 2 * k);   // 3 row + c - (6 y + 2 k)
+        f[k] = pow_hw(m * mult, e.lam);
         codes |= (uint32_t)code << (8 * k);
     }
     // staging layout = the TMA box [patch][row][16 columns].  The values' box

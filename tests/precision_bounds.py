@@ -3,7 +3,7 @@
 A non-negative sum of products whose operands carry a relative rounding error
 <= u_op each, accumulated in FP32 (<= 144 terms; u_acc = 2^-16 covers their
 roundings and the few ulp of the power; 2^-15 in the tensor-core forms, whose
-pooling keys also round the maximum's last 7 bits), has relative error <= r_0 = (1 +
+hardware power and pooling keys (the maximum's last 5 bits) add to that), has relative error <= r_0 = (1 +
 u_op)^2 (1 + u_acc) - 1.  Pooling and averaging non-negative values keep a
 relative error bound, and x -> x^lambda turns a factor (1 + r) into (1 +
 r)^lambda, so the unrectified values of level l carry at most r_l = (1 +
@@ -24,8 +24,9 @@ import numpy as np
 LAM = 1.4
 U_OP = {"fp32": 0.0, "bf16": 2.0 ** -9, "fp8": 2.0 ** -4}
 # FP32 arithmetic of the level-0 value: the FP32 path's fma chain and power;
-# the tensor-core forms also carry the hardware power and the pooling keys,
-# which keep the maximum to within 127 units of its last place (2^-16)
+# the tensor-core forms also carry the hardware power (lg2 / ex2 approximations)
+# and the pooling keys, which keep the maximum to within 31 units of its last
+# place (2^-18)
 U_ACC = {"fp32": 2.0 ** -16, "bf16": 2.0 ** -15, "fp8": 2.0 ** -15}
 
 
