@@ -58,16 +58,6 @@ struct BtArgs {
     DmRect rect;                  // invariant form: rectification of the atomic tuples (RECT kernels only)
 };
 
-__device__ __forceinline__ unsigned int warp_agg_inc(unsigned int* ctr) {
-    unsigned int mask = __activemask();
-    int lane = threadIdx.x & 31;
-    int leader = __ffs(mask) - 1;
-    unsigned int base = 0;
-    if (lane == leader) base = atomicAdd(ctr, (unsigned int)__popc(mask));
-    base = __shfl_sync(mask, base, leader);
-    return base + __popc(mask & ((1u << lane) - 1u));
-}
-
 // Home slot of a key: keys are patch * |domain| + position, so 32 consecutive
 // keys are 32 neighbouring positions of one patch on one row.  Such a block of
 // keys keeps its 32 slots together (block index hashed, offset kept), and the
@@ -408,6 +398,26 @@ __global__ void __launch_bounds__(1024) k_reciprocal(BtArgs a, dm_match_t* __res
 // from the counts before anything is inserted).
 constexpr int ST_COLS = 30, ST_ROWS = 32;
 
+// Each warp gathers the entry points it finds in a shared-memory buffer of
+// STAR_BUF and appends a full buffer to the level's list with one global
+// atomic for the whole buffer (instead of one per group of maxima found, all
+// on one counter), so the list stays dense.
+constexpr unsigned int STAR_BUF = 256;
+
+__device__ __forceinline__ void star_flush(const BtArgs& a, int l, const unsigned long long* buf, unsigned int n, int lane) {
+    __syncwarp();
+    unsigned int base = 0u;
+    if (lane == 0 && n) base = atomicAdd(&a.hdr->entries[l], n);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    bool over = false;
+    for (unsigned int j = (unsigned int)lane; j < n; j += 32u) {
+        if (base + j < a.elcap[l]) a.elist[l][base + j] = buf[j];
+        else over = true;
+    }
+    if (over) atomicOr(&a.hdr->status, DM_DEV_FRONTIER_OVERFLOW);
+    __syncwarp();
+}
+
 template <bool COMP>
 __global__ void __launch_bounds__(256) k_star_entries(BtArgs a, int l, float lam, long long n_items) {
     const DmGeom& g = a.g;
@@ -416,6 +426,9 @@ __global__ void __launch_bounds__(256) k_star_entries(BtArgs a, int l, float lam
     const unsigned int ds = (unsigned int)g.dsize(l);
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    __shared__ unsigned long long sbuf[8][STAR_BUF];    // (blocks of 8 warps)
+    unsigned long long* buf = sbuf[threadIdx.x >> 5];
+    unsigned int nbuf = 0u;                             // entries in this warp's buffer
     for (long long it = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < n_items; it += warps) {
         const int p = (int)(it / tiles), t = (int)(it % tiles);
         if (!a.valid[l][p]) continue;                  // the same for the whole warp
@@ -437,16 +450,25 @@ __global__ void __launch_bounds__(256) k_star_entries(BtArgs a, int l, float lam
             const float v = mid;
             const bool m = lane >= 1 && lane <= ST_COLS && col_in && v > 0.0f && v > ul && v > up && v > ur && v > ml &&
                            v >= mr && v >= dl && v >= dn && v >= dr;
-            if (m) {
-                const unsigned int pos = warp_agg_inc(&a.hdr->entries[l]);
-                const unsigned int key = (unsigned int)p * ds + (unsigned int)(y * mw + x);
-                if (pos < a.elcap[l]) a.elist[l][pos] = ((unsigned long long)key << 32) | ps_term(dm_powf(v, lam));
-                else atomicOr(&a.hdr->status, DM_DEV_FRONTIER_OVERFLOW);
+            const unsigned int found = __ballot_sync(0xffffffffu, m);
+            if (found) {
+                const unsigned int cnt = (unsigned int)__popc(found);
+                if (nbuf + cnt > STAR_BUF) {
+                    star_flush(a, l, buf, nbuf, lane);
+                    nbuf = 0u;
+                }
+                if (m) {
+                    const unsigned int key = (unsigned int)p * ds + (unsigned int)(y * mw + x);
+                    buf[nbuf + (unsigned int)__popc(found & ((1u << lane) - 1u))] =
+                        ((unsigned long long)key << 32) | ps_term(dm_powf(v, lam));
+                }
+                nbuf += cnt;
             }
             up = mid;
             mid = dn;
         }
     }
+    star_flush(a, l, buf, nbuf, lane);
 }
 
 // DM*: the level-l entry points merged into the level-l table.
