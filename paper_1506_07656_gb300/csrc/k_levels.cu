@@ -60,6 +60,7 @@ constexpr int AW = 2 * TW + 1;                   // average columns per CTA (65)
 constexpr int KW = 72;                           // staged child columns (TMA box width)
 constexpr int AWP = 68;                          // padded row of the averages (16-byte aligned rows)
 constexpr int LEVEL_THREADS = 256;
+constexpr int AG = AWP / 4;                      // groups of 4 averages per row (17)
 
 // CTA tile of TW x TH pooled outputs (TH = 8 or 16, chosen by the autotuner):
 // AH rows of averages, child windows of KW x AH floats (KIDF with padding to
@@ -73,84 +74,47 @@ struct LevelTile {
 };
 constexpr long long LEVEL_WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 
-// x / n rounded once, for n in 1..4: multiplications by 1, 1/2, 1/4 are exact,
-// so they equal the correctly rounded quotient; n = 3 divides.
-__device__ __forceinline__ float div_n(float x, int n) {
-    return n == 3 ? __fdiv_rn(x, 3.0f) : __fmul_rn(x, n == 4 ? 0.25f : (n == 2 ? 0.5f : 1.0f));
-}
-
 // Averages at staged row ay, columns ax .. ax+3 of child 0's frame, from the
-// four child windows: child i contributes kb[i][ay][ax + ox_i + 3].
-template <bool COMP, bool ALL4>
-__device__ __forceinline__ float4 avg4(const float* const* kb, int ay, int ax, const int* ci, int n) {
-    // children with ox = -1 (i = 0, 1) read columns ax+2 .. ax+5 (two aligned
-    // float4 loads, which unlike 8-byte loads at a 16-byte stride are free of
-    // bank conflicts), children with ox = +1 (i = 2, 3) columns ax+4 .. ax+7
-    float v[4][4];
+// four child windows (a missing child's window holds zeros, which leave both
+// the plain and the compensated sum of the others unchanged: s + 0 = s exactly,
+// with a zero TwoSum error): child i contributes its column ax + o_x,i + 3.
+// Children with o_x = -1 (left, windows lt / lb) read columns ax+2 .. ax+5 (two
+// aligned float4 loads, which unlike 8-byte loads at a 16-byte stride are free
+// of bank conflicts), children with o_x = +1 (right, rt / rb) columns
+// ax+4 .. ax+7.  Then times w (1/n for n = 1, 2, 4, exact) or, for n = 3,
+// divided by 3.  Two columns per packed FP32x2 operation: Knuth's TwoSum (6
+// additions, every step correctly rounded per lane) costs 3 instructions per
+// column and step.
+template <bool COMP, bool DIV3>
+__device__ __forceinline__ float4 avg_group(const float* lt, const float* lb, const float* rt, const float* rb, float w) {
+    const float4 a0 = *reinterpret_cast<const float4*>(lt), b0 = *reinterpret_cast<const float4*>(lt + 4);
+    const float4 a1 = *reinterpret_cast<const float4*>(lb), b1 = *reinterpret_cast<const float4*>(lb + 4);
+    const float4 v2 = *reinterpret_cast<const float4*>(rt + 4);
+    const float4 v3 = *reinterpret_cast<const float4*>(rb + 4);
+    const float2 x[2][4] = {{make_float2(a0.z, a0.w), make_float2(a1.z, a1.w), make_float2(v2.x, v2.y), make_float2(v3.x, v3.y)},
+                            {make_float2(b0.x, b0.y), make_float2(b1.x, b1.y), make_float2(v2.z, v2.w), make_float2(v3.z, v3.w)}};
+    float2 r[2];
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-        if (!ALL4 && ci[i] < 0) continue;
-        const float* row = kb[i] + ay * KW;
-        if (i < 2) {
-            const float4 a = *reinterpret_cast<const float4*>(row + ax);
-            const float4 b = *reinterpret_cast<const float4*>(row + ax + 4);
-            v[i][0] = a.z; v[i][1] = a.w; v[i][2] = b.x; v[i][3] = b.y;
-        } else {
-            const float4 a = *reinterpret_cast<const float4*>(row + ax + 4);
-            v[i][0] = a.x; v[i][1] = a.y; v[i][2] = a.z; v[i][3] = a.w;
-        }
-    }
-    float r[4];
-    if constexpr (ALL4 && COMP) {
-        // two columns per packed FP32x2 operation: Knuth's TwoSum (6 additions,
-        // bit-identical to the Fast2Sum below, every step correctly rounded per lane)
-        // costs 3.5 instructions per column and step instead of 6
-#pragma unroll
-        for (int c = 0; c < 4; c += 2) {
-            float2 sv = make_float2(v[0][c], v[0][c + 1]);
-            float2 cp = make_float2(0.0f, 0.0f);
+    for (int h = 0; h < 2; h++) {
+        float2 sv = x[h][0];
+        if constexpr (COMP) {
+            float2 cp;
 #pragma unroll
             for (int i = 1; i < 4; i++) {
-                const float2 x = make_float2(v[i][c], v[i][c + 1]);
                 float2 err;
-                dm_two_sum2(sv, x, err);
+                dm_two_sum2(sv, x[h][i], err);
                 // first step: the compensation starts as its error term (0 + err = err;
                 // a -0 there would only meet s + (+-0) = s at the end)
                 cp = i == 1 ? err : __fadd2_rn(cp, err);
             }
-            const float2 a = __fmul2_rn(__fadd2_rn(sv, cp), make_float2(0.25f, 0.25f));
-            r[c] = a.x;
-            r[c + 1] = a.y;
+            sv = __fadd2_rn(sv, cp);
+        } else {
+#pragma unroll
+            for (int i = 1; i < 4; i++) sv = __fadd2_rn(sv, x[h][i]);
         }
-    } else {
-#pragma unroll
-        for (int c = 0; c < 4; c++) {
-            float s = 0.0f, comp = 0.0f;
-            if (ALL4) {
-                s = __fadd_rn(v[0][c], v[1][c]);
-                s = __fadd_rn(s, v[2][c]);
-                s = __fadd_rn(s, v[3][c]);
-                r[c] = __fmul_rn(s, 0.25f);
-            } else {
-#pragma unroll
-                for (int i = 0; i < 4; i++)
-                    if (ci[i] >= 0) child_add<COMP>(s, comp, v[i][c]);
-                r[c] = div_n(COMP ? __fadd_rn(s, comp) : s, n);
-            }
-        }
+        r[h] = DIV3 ? make_float2(__fdiv_rn(sv.x, 3.0f), __fdiv_rn(sv.y, 3.0f)) : __fmul2_rn(sv, make_float2(w, w));
     }
-    return make_float4(r[0], r[1], r[2], r[3]);
-}
-
-template <bool COMP>
-__device__ __forceinline__ float avg1(const float* const* kb, int ay, int ax, const int* ci, int n) {
-    float s = 0.0f, comp = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 4; i++) {
-        if (ci[i] < 0) continue;
-        child_add<COMP>(s, comp, kb[i][ay * KW + ax + ((i >= 2) ? 1 : -1) + 3]);
-    }
-    return div_n(COMP ? __fadd_rn(s, comp) : s, n);
+    return make_float4(r[0].x, r[0].y, r[1].x, r[1].y);
 }
 
 // Sweep geometry of level l: a CTA owns one tile of TW x TH pooled outputs of a
@@ -178,9 +142,10 @@ __device__ __forceinline__ int child_at(const DmGeom& g, int l, int cx, int cy, 
     return vprev[c] ? c : -1;
 }
 
-// Level l in [1, L-1].  Work item = (tile, row iy, residue r, run k0) with the
-// residue and run fastest, so the patches of neighbouring rows that share
-// child windows run close together in time.  `tmap` maps the pooled maps of
+// Level l in [1, L-1].  Work item = (row iy, tile, residue r, run k0) with the
+// residue and run fastest, then the tile, so the CTAs whose windows overlap
+// (neighbouring tiles, neighbouring runs, and -- one row of patches later --
+// the rows that share child windows) run close together in time.  `tmap` maps the pooled maps of
 // level l-1 as a 3-D array (columns dw[l], rows dh[l], patches) with a
 // 72 x (2 TH + 1) x 1 box.  Dynamic shared memory: a ring of NR columns x 2
 // child windows, then the averages.  Per patch of the run: form the averages
@@ -196,6 +161,7 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
                                                                int n_maps, long long inject_wait) {
     using T = LevelTile<TH>;
     constexpr int AH = T::AH, KIDF = T::KIDF;
+    constexpr int AGPT = (AH * AG + LEVEL_THREADS - 1) / LEVEL_THREADS;   // average groups per thread
     extern __shared__ __align__(128) unsigned char lsm_raw[];
     // TMA destinations must be 128-byte aligned: round the dynamic base up (128 bytes are reserved for this)
     float* lsm = reinterpret_cast<float*>(lsm_raw + ((128u - ((uint32_t)__cvta_generic_to_shared(lsm_raw) & 127u)) & 127u));
@@ -211,11 +177,17 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
     int cx0, cy0, S;
     child_col_row(g, l, 0, 0, &cx0, &cy0, &S);
     const int per_row = S * runs_per_res;
+    // work item = ((lattice row iy, tile), run): all tiles of one row of
+    // patches run together, so the window edges that neighbouring tiles share
+    // (64-byte memory granules at their x edges, rows at their y edges) come
+    // from DRAM once (at 512x224, level 1: 1.03x the maps read instead of 1.83x
+    // with the tile as the slowest index)
+    const int ntiles = tiles_x * ((oh + TH - 1) / TH);
     const int item = blockIdx.x;
-    const int tile = item / (g.Ly * per_row);
-    const int rem = item - tile * (g.Ly * per_row);
-    const int iy = rem / per_row;
-    const int rr = rem - iy * per_row;
+    const int rr = item % per_row;
+    const int t1 = item / per_row;
+    const int tile = t1 % ntiles;
+    const int iy = t1 / ntiles;
     const int r = rr / runs_per_res, k0 = (rr - r * runs_per_res) * run;
     const int ix0 = r + k0 * S;                              // first patch of the run
     if (ix0 >= g.Lx) return;
@@ -228,7 +200,9 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
     child_col_row(g, l, ix0, iy, &cxl, &cyt, &st);
     const int cyb = cyt + (l == 1 ? 1 : S);                  // bottom child row
 
-    // thread 0: start the loads of column j (child column cxl + j*S) into slot j % NR
+    // thread 0: start the loads of column j (child column cxl + j*S) into slot j % NR;
+    // a missing child's window is loaded from map index -1, outside the tensor,
+    // which the TMA unit fills with zeros without reading memory
     auto stage = [&](int j) {
         const int slot = j % NR;
         const int cx = cxl + j * S;
@@ -236,8 +210,7 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
         colc[slot][0] = ct;
         colc[slot][1] = cb;
         const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&bars[slot]);
-        const unsigned bytes = T::KID_BYTES * ((ct >= 0) + (cb >= 0));
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(2u * T::KID_BYTES) : "memory");
         const uint32_t dst = (uint32_t)__cvta_generic_to_shared(ring + slot * 2 * KIDF);
         // the map of an atomic child is its prototype's in the approximate form
         int zt = ct, zb = cb;
@@ -247,14 +220,12 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
             if (ct >= 0) zt = min(max(__ldg(proto_of + ct), 0), n_maps - 1);
             if (cb >= 0) zb = min(max(__ldg(proto_of + cb), 0), n_maps - 1);
         }
-        if (ct >= 0)
-            asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-                         :: "r"(dst), "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(xa), "r"(qy0 - 1), "r"(zt), "r"(bar)
-                         : "memory");
-        if (cb >= 0)
-            asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-                         :: "r"(dst + KIDF * 4), "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(xa), "r"(qy0 + 1), "r"(zb), "r"(bar)
-                         : "memory");
+        asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                     :: "r"(dst), "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(xa), "r"(qy0 - 1), "r"(zt), "r"(bar)
+                     : "memory");
+        asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                     :: "r"(dst + KIDF * 4), "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(xa), "r"(qy0 + 1), "r"(zb), "r"(bar)
+                     : "memory");
     };
     // wait for column j (the (j / NR)-th use of its slot); false on timeout
     auto wait_col = [&](int j) -> bool {
@@ -292,8 +263,10 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
     }
     __syncthreads();
     const bool interior = qx0 >= 0 && qy0 >= 0 && qx0 + AW <= mw && qy0 + AH <= mh;
-    if (!wait_col(0) || !wait_col(1)) { atomicOr(err, 1); abort_s = 1; }
-    __syncthreads();                                         // colc of columns 0, 1 visible; abort agreed
+    // thread 0 waits for the loads; the barrier after its wait passes their
+    // data on to every thread of the CTA
+    if (tid == 0 && (!wait_col(0) || !wait_col(1))) { atomicOr(err, 1); abort_s = 1; }
+    __syncthreads();                                         // columns 0, 1 and their colc visible; abort agreed
     for (int k = 0; k < nrun; k++) {
         if (abort_s) {
             // let the loads already started finish (each wait bounded) before the CTA exits
@@ -307,20 +280,31 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
         const int ix = ix0 + k * S;
         const int p = iy * g.Lx + ix;
         if (n > 0) {
-            const float* kb[4] = {ring + (sl * 2) * KIDF, ring + (sl * 2 + 1) * KIDF, ring + (sr * 2) * KIDF,
-                                  ring + (sr * 2 + 1) * KIDF};
-            // averages: sum over existing children in order i = 0..3, then / n;
-            // four adjacent columns per work item
-            constexpr int G4 = (AW - 1) / 4;                 // 16 groups of 4 columns, then column 64
-            for (int e = tid; e < AH * G4; e += LEVEL_THREADS) {
-                const int ay = e / G4, ax = 4 * (e - ay * G4);
-                const float4 a = (n == 4) ? avg4<COMP, true>(kb, ay, ax, ci, n) : avg4<COMP, false>(kb, ay, ax, ci, n);
+            // averages of the tile: 17 groups of 4 columns per row (columns 0 .. 67;
+            // the pooling reads 0 .. 64), group e = tid + 256 u
+            const float* lt = ring + (sl * 2) * KIDF;
+            const float* rt = ring + (sr * 2) * KIDF;
+            const float w = n == 4 ? 0.25f : (n == 2 ? 0.5f : 1.0f);
+#pragma unroll
+            for (int u = 0; u < AGPT; u++) {
+                const int e = tid + u * LEVEL_THREADS;
+                if (u == AGPT - 1 && e >= AH * AG) break;
+                const int ay = e / AG, ax = 4 * (e - ay * AG);
+                const int o = ay * KW + ax;
+                float4 a = n == 3 ? avg_group<COMP, true>(lt + o, lt + KIDF + o, rt + o, rt + KIDF + o, w)
+                                  : avg_group<COMP, false>(lt + o, lt + KIDF + o, rt + o, rt + KIDF + o, w);
+                if (!interior) {
+                    // a tile that reaches past the map holds -inf at the positions outside
+                    // the domain, which the pooling then never selects
+                    const int qy = qy0 + ay, qx = qx0 + ax;
+                    const bool rin = qy >= 0 && qy < mh;
+                    if (!rin || qx < 0 || qx >= mw) a.x = -INFINITY;
+                    if (!rin || qx + 1 < 0 || qx + 1 >= mw) a.y = -INFINITY;
+                    if (!rin || qx + 2 < 0 || qx + 2 >= mw) a.z = -INFINITY;
+                    if (!rin || qx + 3 < 0 || qx + 3 >= mw) a.w = -INFINITY;
+                }
                 *reinterpret_cast<float4*>(&avg[ay][ax]) = a;
             }
-            // the last column's averages go to warps 2-3: warp 0 already forms the
-            // 4-column groups of the last row (AH * G4 = 256 * k + 16)
-            for (int ay = (tid + LEVEL_THREADS - 64) % LEVEL_THREADS; ay < AH; ay += LEVEL_THREADS)
-                avg[ay][AW - 1] = avg1<COMP>(kb, ay, AW - 1, ci, n);
         }
         __syncthreads();                                     // averages ready; column k no longer needed
         if (tid == 0 && k + NR <= nrun) stage(k + NR);       // into the slot column k just released
@@ -339,14 +323,7 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
 #pragma unroll
                 for (int kk = 0; kk < 2 * R + 1; kk++) {
                     const int ay = 2 * ty0 + kk;             // average row; map row qy0 + ay
-                    float a0 = avg[ay][2 * lane], a1 = avg[ay][2 * lane + 1], a2 = avg[ay][2 * lane + 2];
-                    if (!interior) {
-                        const int qy = qy0 + ay, qx = 2 * rx;
-                        const bool rin = qy >= 0 && qy < mh;
-                        if (!rin || qx - 1 < 0) a0 = -INFINITY;
-                        if (!rin) a1 = -INFINITY;
-                        if (!rin || qx + 1 >= mw) a2 = -INFINITY;
-                    }
+                    const float a0 = avg[ay][2 * lane], a1 = avg[ay][2 * lane + 1], a2 = avg[ay][2 * lane + 2];
                     // first column holding the row maximum (columns in scan order m_x = -1, 0, 1)
                     const float m = fmax3(a0, a1, a2);
                     hv[kk] = m;
@@ -379,9 +356,9 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
                 }
             }
         }
-        // the next patch's columns k+1, k+2 (waited for by every thread), then one
-        // barrier: averages consumed, colc of those columns visible, abort agreed
-        if (k + 1 < nrun && (!wait_col(k + 1) || !wait_col(k + 2))) { atomicOr(err, 1); abort_s = 1; }
+        // the next patch's columns k+1, k+2 (waited for by thread 0), then one
+        // barrier: averages consumed, those columns and their colc visible, abort agreed
+        if (tid == 0 && k + 1 < nrun && (!wait_col(k + 1) || !wait_col(k + 2))) { atomicOr(err, 1); abort_s = 1; }
         __syncthreads();
     }
 }
