@@ -118,7 +118,10 @@ const char* dm_last_error(const dm_ctx* ctx);
  *   *n_patch  lattice patches of levels >= 1 (centres in 4Z^2 inside I)
  *   dw, dh    (may be NULL) map domain of level l = 0..L+1: ceil(W2/2^l) x ceil(H2/2^l)
  * Requires W1, H1 >= 4, max(W1, H1) >= 5, W2, H2 >= 1; DM_EUNSUPPORTED when
- * a level's node count does not fit the 32-bit merge keys. */
+ * L > 14 (the fixed-point path scores hold L + 1 terms in 32 bits) or the
+ * atomic indices (pixel of I', patch * 16 + offset) exceed 32 bits.  Sizes
+ * whose merge keys patch * |domain| + position exceed 32 bits are supported
+ * with 64-bit keys (dm_set_merge_keys). */
 dm_status dm_geometry(int W1, int H1, int W2, int H2, int* L, int* n_patch0, int* n_patch, int* dw, int* dh);
 
 /* Workspace bytes for a pair of sizes:
@@ -289,9 +292,9 @@ dm_status dm_match_star(dm_ctx* ctx, const float* d_img1, int W1, int H1, const 
  * verification (Eq. 16) then writes the matches as dm_match does: up to
  * `capacity` in atomic-patch order of image 1, *d_count (device int) the
  * number found.  Transforms that leave an image below 4 pixels, or with no
- * aggregation level, are skipped; DM_EUNSUPPORTED if a transform's warped
- * pair exceeds the 32-bit merge keys (the 45-degree canvases are the
- * largest).  The precision and parameters are the context's.  The runs are
+ * aggregation level, are skipped; a transform whose warped pair needs
+ * 64-bit merge keys (the 45-degree canvases are the largest) gets them
+ * (dm_set_merge_keys).  The precision and parameters are the context's.  The runs are
  * independent (their reductions are order-independent), so they are spread
  * over the context's concurrent lanes (dm_set_batch_lanes; longest run first,
  * each to the least loaded lane) that fork from and join back into `stream`;
@@ -367,6 +370,20 @@ dm_status dm_loss_grad(dm_ctx* ctx, const dm_pyramid* pyr, const float* d_desc1,
                        size_t ws_bytes, float* d_loss, float* d_parts, float* d_g1, float* d_g2, void* stream);
 
 /* One image pair of a batch (device buffers, as for dm_match). */
+/* Width of the backtracking's merge keys (Sec. 3.3 "Merging correspondences":
+ * tuples equal in (level, patch, position) are merged).  The key of a tuple
+ * of level l is patch * |domain of l| + position; bits = 0 (default) takes
+ * 32-bit keys in 8-byte table slots where every level's keys fit 32 bits and
+ * 64-bit keys in 16-byte slots elsewhere (e.g. images of about 1024 x 512 and
+ * more, and the rotated canvases of dm_match_invariant); bits = 64 takes
+ * 64-bit keys at every size (the results are the same; used to test the wide
+ * form on small pairs).  It applies to the calls made afterwards, workspace
+ * queries included (64-bit keys double the tables' bytes): set it before
+ * sizing workspaces.  DM* (dm_match_star, dm_backtrack_star) keeps 32-bit keys
+ * and returns DM_EUNSUPPORTED for sizes that need 64.  DM_EINVAL for other
+ * values of bits. */
+dm_status dm_set_merge_keys(dm_ctx* ctx, int bits);
+
 typedef struct {
     const float* d_img1;
     int W1, H1;

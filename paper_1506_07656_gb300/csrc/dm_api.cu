@@ -37,6 +37,7 @@ struct dm_ctx {
     long long inj_launch = 0;         // > 0: the inj_launch-th next launch site reports a launch failure
     unsigned int inj_table_cap = 0;   // > 0: merge tables of the backtracking capped at this many slots
     long long inj_wait = 0;           // > 0: level-kernel CTAs first wait this many cycles on a barrier nothing completes
+    int force_key64 = 0;              // dm_set_merge_keys(64): 64-bit merge keys at every size
 };
 
 // process-wide: > 0, the g_inj_alloc-th next resource creation of the library fails
@@ -241,8 +242,9 @@ dm_status inv_plan(dm_ctx* c, const DmGeom& go, std::vector<InvStep>* steps, Inv
         const int r = dm_make_geom(s.t.w1, s.t.h1, s.t.w2, s.t.h2, &s.g);
         if (r == -1) continue;
         if (r != 0)
-            return fail(c, DM_EUNSUPPORTED, "invariant form: transform %d (%dx%d / %dx%d) exceeds the 32-bit merge keys", i,
+            return fail(c, DM_EUNSUPPORTED, "invariant form: transform %d (%dx%d / %dx%d) exceeds the supported sizes", i,
                         s.t.w1, s.t.h1, s.t.w2, s.t.h2);
+        if (c->force_key64) s.g.key64 = 1;
         match_layout(s.g, c->cfg.precision, &s.ml);
         if (s.ml.bytes > mbytes) mbytes = s.ml.bytes;
         s.cost = (double)s.g.npatch(0) * (double)s.t.w2 * (double)s.t.h2 + 2.0e7;
@@ -279,7 +281,18 @@ std::vector<int> inv_schedule(const std::vector<InvStep>& steps, int lanes, std:
 dm_status check_geom(dm_ctx* c, int W1, int H1, int W2, int H2, DmGeom* g) {
     int r = dm_make_geom(W1, H1, W2, H2, g);
     if (r == -1) return fail(c, DM_EINVAL, "invalid sizes %dx%d / %dx%d (need W1,H1 >= 4, max(W1,H1) >= 5, W2,H2 >= 1)", W1, H1, W2, H2);
-    if (r == -2) return fail(c, DM_EUNSUPPORTED, "sizes %dx%d / %dx%d exceed the 32-bit merge keys", W1, H1, W2, H2);
+    if (r == -2)
+        return fail(c, DM_EUNSUPPORTED, "sizes %dx%d / %dx%d exceed the supported sizes (fixed-point path scores, 32-bit "
+                                        "atomic indices)", W1, H1, W2, H2);
+    if (c->force_key64) g->key64 = 1;
+    return DM_OK;
+}
+
+// DM* keeps 32-bit merge keys (its entry lists pack key and score in 64 bits).
+dm_status star_keys(dm_ctx* c, const DmGeom& g) {
+    if (g.key64)
+        return fail(c, DM_EUNSUPPORTED, "DM*: sizes %dx%d / %dx%d need 64-bit merge keys, which DM* does not take", g.W1,
+                    g.H1, g.W2, g.H2);
     return DM_OK;
 }
 
@@ -335,10 +348,10 @@ int dm_make_geom(int W1, int H1, int W2, int H2, DmGeom* g) {
     g->L = L;
     g->dw[0] = W2; g->dh[0] = H2;
     for (int l = 1; l <= L + 1; l++) { g->dw[l] = (g->dw[l - 1] + 1) / 2; g->dh[l] = (g->dh[l - 1] + 1) / 2; }
-    // merge keys patch * |domain| + position must fit 32 bits (levels 1..L-1);
-    // atomic indices (pixel of I', patch*16 + offset) too.
+    // merge keys patch * |domain| + position (levels 1..L-1): 32 bits where they
+    // fit, else 64; the atomic indices (pixel of I', patch*16 + offset) must fit 32.
     for (int l = 1; l <= L; l++)
-        if ((unsigned long long)g->npatch(l) * (unsigned long long)g->dsize(l) >= 0xffffffffull) return -2;
+        if ((unsigned long long)g->npatch(l) * (unsigned long long)g->dsize(l) >= 0xffffffffull) g->key64 = 1;
     if ((unsigned long long)g->npatch(0) * 16ull >= 0xffffffffull) return -2;
     if ((unsigned long long)W2 * H2 >= 0xffffffffull) return -2;
     return 0;
@@ -379,7 +392,7 @@ void dm_bt_layout(const DmGeom& g, DmBtLayout* o, bool star) {
         if (cap < 64ull) cap = 64ull;
         if (cap > 0xfffffff0ull) cap = 0xfffffff0ull;
         o->cap[l] = (size_t)cap;
-        o->table[l] = off; off = dm_align(off + (size_t)cap * 8);
+        o->table[l] = off; off = dm_align(off + (size_t)cap * (g.key64 ? 16 : 8));
     }
     o->bestP = off; off = dm_align(off + (size_t)g.npatch(0) * 8);
     o->bestQ = off; off = dm_align(off + (size_t)((g.W2 + 3) / 4) * ((g.H2 + 3) / 4) * 8);
@@ -825,6 +838,13 @@ dm_status batch_lane_bytes(dm_ctx* ctx, int n, const dm_pair* pairs, size_t* byt
 }
 }  // namespace
 
+dm_status dm_set_merge_keys(dm_ctx* ctx, int bits) {
+    if (!ctx) return DM_EINVAL;
+    if (bits != 0 && bits != 64) return fail(ctx, DM_EINVAL, "dm_set_merge_keys: bits must be 0 or 64");
+    ctx->force_key64 = bits == 64;
+    return DM_OK;
+}
+
 dm_status dm_set_batch_lanes(dm_ctx* ctx, int lanes) {
     if (!ctx) return DM_EINVAL;
     if (lanes < 1 || lanes > DM_MAX_LANES) return fail(ctx, DM_EINVAL, "dm_set_batch_lanes: lanes must be 1..%d", DM_MAX_LANES);
@@ -1189,6 +1209,7 @@ dm_status dm_star_workspace_bytes(const dm_ctx* ctx, int W1, int H1, int W2, int
     if (!ctx) return DM_EINVAL;
     DmGeom g;
     dm_status s = check_geom(const_cast<dm_ctx*>(ctx), W1, H1, W2, H2, &g);
+    if (s == DM_OK) s = star_keys(const_cast<dm_ctx*>(ctx), g);
     if (s != DM_OK) return s;
     DmBtLayout bl;
     dm_bt_layout(g, &bl, true);
@@ -1205,6 +1226,8 @@ dm_status dm_backtrack_star(dm_ctx* ctx, const dm_pyramid* pyr, void* d_ws, size
     if (!pyr || !d_ws || !d_out || !d_count || capacity < 0)
         return fail(ctx, DM_EINVAL, "dm_backtrack_star: bad arguments");
     if (!aligned256(d_ws)) return fail(ctx, DM_EINVAL, "workspace must be 256-byte aligned");
+    dm_status s = star_keys(ctx, pyr->g);
+    if (s != DM_OK) return s;
     DmBtLayout bl;
     dm_bt_layout(pyr->g, &bl, true);
     if (ws_bytes < bl.bytes) return fail(ctx, DM_ENOMEM, "DM* backtrack workspace %zu < %zu bytes", ws_bytes, bl.bytes);
@@ -1226,6 +1249,7 @@ dm_status dm_match_star(dm_ctx* ctx, const float* d_img1, int W1, int H1, const 
     if (!aligned256(d_ws)) return fail(ctx, DM_EINVAL, "workspace must be 256-byte aligned");
     DmGeom g;
     dm_status s = check_geom(ctx, W1, H1, W2, H2, &g);
+    if (s == DM_OK) s = star_keys(ctx, g);
     if (s != DM_OK) return s;
     MatchLayout ml;
     match_layout(g, ctx->cfg.precision, &ml, true);

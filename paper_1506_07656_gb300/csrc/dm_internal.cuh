@@ -19,6 +19,7 @@ struct DmGeom {
     int P0x, P0y;       // atomic grid: centres 4k+2 <= W1-1
     int Lx, Ly;         // lattice 4Z^2 inside I: patches of levels >= 1
     int dw[DM_MAXL + 2], dh[DM_MAXL + 2];  // map domain of level l
+    int key64;          // merge keys patch * |domain| + position need 64 bits (16-byte table slots)
     __host__ __device__ int npatch(int l) const { return l == 0 ? P0x * P0y : Lx * Ly; }
     __host__ __device__ int gx(int l) const { return l == 0 ? P0x : Lx; }
     __host__ __device__ long long dsize(int l) const { return (long long)dw[l] * dh[l]; }

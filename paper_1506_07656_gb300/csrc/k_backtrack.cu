@@ -12,7 +12,12 @@
 // merged frontier is typically 1-5% of a level's pooled map below the top), so
 // the frontier is kept sparse: one open-addressing table per level keyed by
 // (patch, position) with 64-bit slots (key+1) << 32 | score, merged by 64-bit
-// atomicMax; the next step scans the table in slot order.
+// atomicMax; the next step scans the table in slot order.  Where the keys
+// patch * |domain| + position do not fit 32 bits (large or rotated images:
+// the canvases of the invariant form), the slots are 16 bytes, {key + 1,
+// score}: the key word is claimed by a 64-bit compare-and-swap and the score
+// merged by atomicMax in its own word (the next step reads both after the
+// kernel has ended).
 // The active table size is derived on the device from the previous
 // frontier's size, so nothing waits for the host.
 //
@@ -71,6 +76,39 @@ __device__ __forceinline__ unsigned int ht_home(unsigned int key, unsigned int c
     const unsigned int nblk = cap >> HT_BLOCK_LOG2;
     const unsigned int blk = (unsigned int)(((unsigned long long)((key >> HT_BLOCK_LOG2) * 2654435761u) * nblk) >> 32);
     return (blk << HT_BLOCK_LOG2) | (key & ((1u << HT_BLOCK_LOG2) - 1u));
+}
+
+// 64-bit keys: the block index is hashed from the 64-bit block number.
+__device__ __forceinline__ unsigned int ht_home64(unsigned long long key, unsigned int cap) {
+    const unsigned long long nblk = cap >> HT_BLOCK_LOG2;
+    const unsigned long long hb = ((key >> HT_BLOCK_LOG2) * 0x9E3779B97F4A7C15ull) >> 32;
+    const unsigned int blk = (unsigned int)((hb * nblk) >> 32);
+    return (blk << HT_BLOCK_LOG2) | (unsigned int)(key & ((1u << HT_BLOCK_LOG2) - 1u));
+}
+
+// Merge (key, score) into a level table of 16-byte slots; returns 1 if the key is new.
+__device__ __forceinline__ int ht_insert64(const BtArgs& a, int lvl, unsigned int cap, unsigned long long key, unsigned int sb) {
+    ulonglong2* tab = reinterpret_cast<ulonglong2*>(a.table[lvl]);
+    const unsigned long long kw = key + 1ull;
+    unsigned int h = ht_home64(key, cap);
+    for (unsigned int probe = 0; probe < cap; probe++) {
+        unsigned long long cur = __ldcg(&tab[h].x);
+        if (cur == 0ull) {
+            const unsigned long long prev = atomicCAS(&tab[h].x, 0ull, kw);
+            if (prev == 0ull) {
+                atomicMax(&tab[h].y, (unsigned long long)sb);
+                return 1;
+            }
+            cur = prev;
+        }
+        if (cur == kw) {
+            if (__ldcg(&tab[h].y) < (unsigned long long)sb) atomicMax(&tab[h].y, (unsigned long long)sb);
+            return 0;
+        }
+        h = (h + 1u == cap) ? 0u : h + 1u;
+    }
+    atomicOr(&a.hdr->status, DM_DEV_FRONTIER_OVERFLOW);
+    return 0;
 }
 
 // Merge (key, score) into the level-`lvl` table; returns 1 if the key is new.
@@ -148,7 +186,7 @@ __device__ __forceinline__ void leaf_update_rect(const BtArgs& a, int c, int tx,
 // the leaf).
 constexpr int BT_EXACT = 0, BT_RECT = 1, BT_STAR = 2;
 
-template <int MODE>
+template <int MODE, bool K64>
 __device__ __forceinline__ int expand(const BtArgs& a, int l, unsigned int cap_next, int p, int qx, int qy, unsigned int s) {
     const DmGeom& g = a.g;
     const int mw = g.dw[l], mh = g.dh[l], pitch = g.pitch(l);    // pooled map P_{l-1} lives on domain l
@@ -183,8 +221,14 @@ __device__ __forceinline__ int expand(const BtArgs& a, int l, unsigned int cap_n
         const int tx = 2 * rx + code[i] % 3 - 1, ty = 2 * ry + code[i] / 3 - 1;
         const unsigned int s2 = (MODE == BT_STAR && l - 1 >= 1) ? s : s + ps_term(val[i]);
         if (l - 1 >= 1) {
-            unsigned int key = (unsigned int)cc[i] * (unsigned int)g.dsize(l - 1) + (unsigned int)(ty * g.dw[l - 1] + tx);
-            arrivals += ht_insert(a, l - 1, cap_next, key, s2);
+            if constexpr (K64) {
+                const unsigned long long key = (unsigned long long)cc[i] * (unsigned long long)g.dsize(l - 1) +
+                                               (unsigned long long)(ty * g.dw[l - 1] + tx);
+                arrivals += ht_insert64(a, l - 1, cap_next, key, s2);
+            } else {
+                const unsigned int key = (unsigned int)cc[i] * (unsigned int)g.dsize(l - 1) + (unsigned int)(ty * g.dw[l - 1] + tx);
+                arrivals += ht_insert(a, l - 1, cap_next, key, s2);
+            }
         } else {
             if constexpr (MODE == BT_RECT) leaf_update_rect(a, cc[i], tx, ty, s2);
             else leaf_update(a, cc[i], tx, ty, s2);
@@ -209,12 +253,14 @@ __device__ __forceinline__ void add_count(const BtArgs& a, int lvl, int n) {
 // Clear the active part of the level-`lvl` table.  Active size: 12x the
 // previous frontier (4 children per tuple: load <= 1/3, few collisions
 // between the 32-slot key blocks), a multiple of 32 within [64, capmax].
+template <bool K64 = false>
 __device__ __forceinline__ void clear_table(const BtArgs& a, int lvl, unsigned long long cap) {
     if (cap < 64ull) cap = 64ull;
     const unsigned long long cmax = (unsigned long long)a.capmax[lvl] & ~31ull;
     if (cap > cmax) cap = cmax;
     if (blockIdx.x == 0 && threadIdx.x == 0) a.hdr->cap[lvl] = (unsigned int)cap;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
+    const unsigned long long words = K64 ? 2ull * cap : cap;     // 16-byte slots hold two words
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < words;
          i += (unsigned long long)gridDim.x * blockDim.x)
         a.table[lvl][i] = 0ull;
 }
@@ -227,20 +273,14 @@ __global__ void k_star_prepare(BtArgs a, int lvl) {
     clear_table(a, lvl, (n_prev * HT_SLOTS_PER_PREV + 3ull * a.hdr->entries[lvl] + 31ull) & ~31ull);
 }
 
+template <bool K64>
 __global__ void k_bt_prepare(BtArgs a, int lvl, long long n_top) {
-    unsigned long long n_prev = (lvl + 1 == a.g.L) ? (unsigned long long)n_top : a.hdr->count[lvl + 1];
-    unsigned long long cap = (n_prev * HT_SLOTS_PER_PREV + 31ull) & ~31ull;
-    if (cap < 64ull) cap = 64ull;
-    const unsigned long long cmax = (unsigned long long)a.capmax[lvl] & ~31ull;
-    if (cap > cmax) cap = cmax;
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.hdr->cap[lvl] = (unsigned int)cap;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
-         i += (unsigned long long)gridDim.x * blockDim.x)
-        a.table[lvl][i] = 0ull;
+    const unsigned long long n_prev = (lvl + 1 == a.g.L) ? (unsigned long long)n_top : a.hdr->count[lvl + 1];
+    clear_table<K64>(a, lvl, (n_prev * HT_SLOTS_PER_PREV + 31ull) & ~31ull);
 }
 
 // Expansion of the top level: every position of every existing top patch.
-template <int MODE>
+template <int MODE, bool K64>
 __global__ void k_bt_expand_top(BtArgs a) {
     const DmGeom& g = a.g;
     const int L = g.L;
@@ -255,7 +295,7 @@ __global__ void k_bt_expand_top(BtArgs a) {
             int q = (int)(e % ds);
             if (a.valid[L][p]) {
                 if (q == 0) atomicAdd(&a.hdr->count[L], (unsigned int)ds);
-                arrivals += expand<MODE>(a, L, cap_next, p, q % g.dw[L], q / g.dw[L], ps_term(a.top[e]));
+                arrivals += expand<MODE, K64>(a, L, cap_next, p, q % g.dw[L], q / g.dw[L], ps_term(a.top[e]));
             }
         }
     }
@@ -267,41 +307,73 @@ __global__ void k_bt_expand_top(BtArgs a) {
 // it reads into a queue in shared memory and expands them 32 at a time, so its
 // lanes stay busy while the slot order (neighbouring positions of one patch
 // together) is kept.
-template <int MODE>
+template <int MODE, bool K64>
 __global__ void k_bt_expand(BtArgs a, int l) {
+    // queued slots: the packed slot (32-bit keys), or key + 1 and score
     __shared__ unsigned long long queue[BT_BLOCK / 32][64];
+    __shared__ unsigned int qscore[K64 ? BT_BLOCK / 32 : 1][64];
     const DmGeom& g = a.g;
     const unsigned int cap = a.hdr->cap[l];
     const unsigned int cap_next = (l - 1 >= 1) ? a.hdr->cap[l - 1] : 0u;
     const unsigned int ds = (unsigned int)g.dsize(l);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long* q = queue[warp];
+    unsigned int* qs = qscore[K64 ? warp : 0];
     int qn = 0;                                          // warp-uniform queue length
     int arrivals = 0;
-    auto run = [&](unsigned long long v) {
-        const unsigned int key = (unsigned int)(v >> 32) - 1u;
-        const unsigned int sc = (unsigned int)v;
-        const int p = (int)(key / ds), t = (int)(key % ds);
-        arrivals += expand<MODE>(a, l, cap_next, p, t % g.dw[l], t / g.dw[l], sc);
+    auto run = [&](unsigned long long v, unsigned int sc64) {
+        int p, t;
+        unsigned int sc;
+        if constexpr (K64) {
+            const unsigned long long key = v - 1ull;
+            p = (int)(key / ds);
+            t = (int)(key - (unsigned long long)p * ds);
+            sc = sc64;
+        } else {
+            const unsigned int key = (unsigned int)(v >> 32) - 1u;
+            sc = (unsigned int)v;
+            p = (int)(key / ds);
+            t = (int)(key % ds);
+        }
+        arrivals += expand<MODE, K64>(a, l, cap_next, p, t % g.dw[l], t / g.dw[l], sc);
     };
     for (unsigned int i0 = blockIdx.x * blockDim.x; i0 < cap; i0 += gridDim.x * blockDim.x) {
         const unsigned int i = i0 + threadIdx.x;
-        const unsigned long long v = i < cap ? __ldcg(a.table[l] + i) : 0ull;
+        unsigned long long v = 0ull;
+        unsigned int sc = 0u;
+        if constexpr (K64) {
+            if (i < cap) {
+                const ulonglong2 w = __ldcg(reinterpret_cast<const ulonglong2*>(a.table[l]) + i);
+                v = w.x;
+                sc = (unsigned int)w.y;
+            }
+        } else {
+            v = i < cap ? __ldcg(a.table[l] + i) : 0ull;
+        }
         const unsigned int occ = __ballot_sync(0xffffffffu, v != 0ull);
-        if (v != 0ull) q[qn + __popc(occ & ((1u << lane) - 1u))] = v;
+        if (v != 0ull) {
+            const int at = qn + __popc(occ & ((1u << lane) - 1u));
+            q[at] = v;
+            if constexpr (K64) qs[at] = sc;
+        }
         qn += __popc(occ);
         __syncwarp();
         if (qn >= 32) {
             const unsigned long long w = q[lane];
+            const unsigned int ws = K64 ? qs[lane] : 0u;
             const unsigned long long rest = lane + 32 < qn ? q[lane + 32] : 0ull;
+            const unsigned int rests = (K64 && lane + 32 < qn) ? qs[lane + 32] : 0u;
             __syncwarp();
-            if (lane + 32 < qn) q[lane] = rest;
+            if (lane + 32 < qn) {
+                q[lane] = rest;
+                if constexpr (K64) qs[lane] = rests;
+            }
             qn -= 32;
             __syncwarp();
-            run(w);
+            run(w, ws);
         }
     }
-    if (lane < qn) run(q[lane]);
+    if (lane < qn) run(q[lane], K64 ? qs[lane] : 0u);
     add_count(a, l - 1, arrivals);
 }
 
@@ -484,19 +556,25 @@ __global__ void k_star_insert(BtArgs a, int l) {
     add_count(a, l, fresh);
 }
 
-template <int MODE>
-void launch_steps(const BtArgs& a, int grid, cudaStream_t st) {
+template <int MODE, bool K64>
+void launch_steps_k(const BtArgs& a, int grid, cudaStream_t st) {
     const DmGeom& g = a.g;
     const long long n_top = (long long)g.npatch(g.L) * g.dsize(g.L);
     for (int l = g.L; l >= 1; l--) {
-        if (l - 1 >= 1) k_bt_prepare<<<grid, BT_BLOCK, 0, st>>>(a, l - 1, n_top);
+        if (l - 1 >= 1) k_bt_prepare<K64><<<grid, BT_BLOCK, 0, st>>>(a, l - 1, n_top);
         if (l == g.L) {
             long long nb = (n_top + BT_BLOCK - 1) / BT_BLOCK;
-            k_bt_expand_top<MODE><<<(unsigned)(nb < grid ? nb : grid), BT_BLOCK, 0, st>>>(a);
+            k_bt_expand_top<MODE, K64><<<(unsigned)(nb < grid ? nb : grid), BT_BLOCK, 0, st>>>(a);
         } else {
-            k_bt_expand<MODE><<<grid, BT_BLOCK, 0, st>>>(a, l);
+            k_bt_expand<MODE, K64><<<grid, BT_BLOCK, 0, st>>>(a, l);
         }
     }
+}
+
+template <int MODE>
+void launch_steps(const BtArgs& a, int grid, cudaStream_t st) {
+    if (a.g.key64) launch_steps_k<MODE, true>(a, grid, st);
+    else launch_steps_k<MODE, false>(a, grid, st);
 }
 
 }  // namespace
@@ -602,7 +680,7 @@ cudaError_t dm_launch_backtrack_star(const DmGeom& g, const dm_pyramid& py, cons
             k_star_prepare<<<grid, BT_BLOCK, 0, st>>>(a, l - 1);
             k_star_insert<<<grid, BT_BLOCK, 0, st>>>(a, l - 1);
         }
-        k_bt_expand<BT_STAR><<<grid, BT_BLOCK, 0, st>>>(a, l);
+        k_bt_expand<BT_STAR, false><<<grid, BT_BLOCK, 0, st>>>(a, l);
     }
     k_reciprocal<<<1, 1024, 0, st>>>(a, out, capacity, d_count);
     dm_count_launches(4 * g.L + 1);

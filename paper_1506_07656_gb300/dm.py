@@ -83,6 +83,7 @@ _SIGS = {
     "dm_batch_workspace_bytes": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_size_t)]),
     "dm_match_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "dm_set_batch_lanes": (C.c_int, [C.c_void_p, C.c_int]),
+    "dm_set_merge_keys": (C.c_int, [C.c_void_p, C.c_int]),
     "dm_batch_host_workspace_bytes": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_size_t)]),
     "dm_match_batch_host": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "dm_backtrack_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
@@ -470,6 +471,11 @@ def dm_set_batch_lanes(ctx, lanes: int) -> None:
     _check(ctx, load().dm_set_batch_lanes(ctx, int(lanes)), "dm_set_batch_lanes")
 
 
+def dm_set_merge_keys(ctx, bits: int) -> None:
+    """0: 32-bit merge keys where they fit (else 64); 64: 64-bit keys at every size."""
+    _check(ctx, load().dm_set_merge_keys(ctx, int(bits)), "dm_set_merge_keys")
+
+
 def dm_backtrack_noalloc(ctx, pyr, d_out, d_count, stream=None):
     """Backtracking with the library's fixed internal scratch (no workspace argument)."""
     cap = d_out.numel() * d_out.element_size() // MATCH_BYTES
@@ -547,6 +553,11 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def set_merge_keys(self, bits: int):
+        """dm_set_merge_keys; drops the cached workspaces (their sizes depend on it)."""
+        dm_set_merge_keys(self.ctx, bits)
+        self._ws.clear()
 
     def workspace(self, kind: str, W1, H1, W2, H2):
         key = (kind, W1, H1, W2, H2)

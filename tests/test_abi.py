@@ -55,10 +55,14 @@ def test_geometry_rejects_degenerate_sizes(lib):
         with pytest.raises(dm.DmError) as e:
             dm.dm_geometry(*bad)
         assert e.value.status == dm.DM_EINVAL
-    # keys of the sparse merge tables are 32-bit: very large pairs are refused
-    with pytest.raises(dm.DmError) as e:
-        dm.dm_geometry(4096, 4096, 4096, 4096)
-    assert e.value.status == dm.DM_EUNSUPPORTED
+    # merge keys beyond 32 bits take 64-bit keys: a 4096 x 4096 pair is accepted;
+    # atomic indices (patch * 16 + offset) beyond 32 bits and more than 14
+    # levels (fixed-point path scores) are refused
+    assert dm.dm_geometry(4096, 4096, 4096, 4096)["L"] == 10
+    for big in [(70000, 70000, 8, 8), (8, 8, 70000, 70000)]:
+        with pytest.raises(dm.DmError) as e:
+            dm.dm_geometry(*big)
+        assert e.value.status == dm.DM_EUNSUPPORTED
 
 
 def test_create_without_gpu_fails_cleanly(lib):

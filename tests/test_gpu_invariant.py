@@ -11,7 +11,8 @@ through the C ABI (dm_match_invariant).
   patches, and the quarter turn is still recovered.
 * The status header of the invariant workspace reports the runs; argument and
   workspace checks fail with the documented codes; a size whose 45-degree
-  canvas exceeds the 32-bit merge keys is refused (DM_EUNSUPPORTED).
+  canvas needs 64-bit merge keys is sized with them (the 1024 x 436 run itself
+  is in test_gpu_key64.py).
 """
 import numpy as np
 import pytest
@@ -132,10 +133,10 @@ def test_argument_and_workspace_checks(torch_cuda):
     with pytest.raises(dm.DmError) as e:
         dm.dm_match_invariant(ctx.ctx, tiny, i2, ws, out, cnt)
     assert e.value.status == dm.DM_EINVAL
-    # 1024 x 436: the 45-degree canvas of image 2 (1032 x 1032) overflows the merge keys
-    with pytest.raises(dm.DmError) as e:
-        dm.dm_invariant_workspace_bytes(ctx.ctx, 1024, 436, 1024, 436)
-    assert e.value.status == dm.DM_EUNSUPPORTED
+    # 1024 x 436: the 45-degree canvas of image 2 (1032 x 1032) needs 64-bit
+    # merge keys, whose 16-byte slots the workspace includes
+    big = dm.dm_invariant_workspace_bytes(ctx.ctx, 1024, 436, 1024, 436)
+    assert big > dm.dm_workspace_bytes(ctx.ctx, 1024, 436, 1024, 436)["match"]
 
 
 def test_output_capacity_overflow_is_reported(torch_cuda):
