@@ -570,6 +570,27 @@ def _measure_grad(dm, torch, a, stream, W=256, H=256, npairs=8):
             "level0_backward_tflops_lower_bound": flop_l0 / (grad_ms * 1e-3) / 1e12}
 
 
+def _batch_shape(dm, torch, ctx, a, pairs, tune_pairs=None):
+    """Workspace and shape (wave width, lanes) of the batched form: as many
+    per-pair slices as fit the device's free memory (16 GB kept back) up to 8,
+    then dm_autotune_batch picks the fastest shape within them (with
+    --no-autotune: each pair its own launches on --batch-lanes lanes)."""
+    dm.dm_set_batch_wave(ctx.ctx, 1)
+    dm.dm_set_batch_lanes(ctx.ctx, 1)
+    lane = dm.dm_batch_workspace_bytes(ctx.ctx, pairs)
+    torch.cuda.empty_cache()
+    free = torch.cuda.mem_get_info()[0]
+    slices = int(max(1, min(8, (free - 16e9) // lane)))
+    if not a.autotune:
+        k = max(1, min(a.batch_lanes, slices))
+        dm.dm_set_batch_lanes(ctx.ctx, k)
+        return torch.empty(k * lane, dtype=torch.uint8, device="cuda"), {"wave": 1, "lanes": k, "slices": k}
+    ws = torch.empty(slices * lane, dtype=torch.uint8, device="cuda")
+    shape = dm.dm_autotune_batch(ctx.ctx, tune_pairs if tune_pairs is not None else pairs, ws)
+    shape["slices"] = slices
+    return ws, shape
+
+
 def _measure_batch(dm, torch, ctx, a, rank):
     """Batched form: 48 pairs, 12 of each size, value noise + smooth warp with
     per-pair seeds, matched by dm_match_batch inside one captured CUDA graph;
@@ -584,13 +605,18 @@ def _measure_batch(dm, torch, ctx, a, rank):
                       torch.empty((n0, 5), dtype=torch.float32, device="cuda"),
                       torch.zeros(1, dtype=torch.int32, device="cuda")))
     pairs = dm.make_pairs(items)
-    dm.dm_set_batch_lanes(ctx.ctx, a.batch_lanes)
+    # autotune the launch shapes once per size, on the first pair of that size
+    # (before capture), then the batch shape on the 48 pairs
+    dm.dm_set_batch_wave(ctx.ctx, 1)
+    dm.dm_set_batch_lanes(ctx.ctx, 1)
     ws = torch.empty(dm.dm_batch_workspace_bytes(ctx.ctx, pairs), dtype=torch.uint8, device="cuda")
-    # autotune the launch shapes once per size, on the first pair of that size (before capture)
     tuned = {}
     for k in range(4):
         W, H = BATCH_SIZES[k]
-        tuned[f"{W}x{H}"] = dm.dm_autotune(ctx.ctx, items[k][0], items[k][1], ws)
+        tuned[f"{W}x{H}"] = dm.dm_autotune(ctx.ctx, items[k][0], items[k][1], ws) if a.autotune else \
+            dm.dm_tuned_config(ctx.ctx, W, H, W, H)
+    del ws
+    ws, shape = _batch_shape(dm, torch, ctx, a, pairs)
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(side):
@@ -612,8 +638,9 @@ def _measure_batch(dm, torch, ctx, a, rank):
     del graph, ws
     return {"pairs": 48, "sizes": [f"{w}x{h}" for w, h in BATCH_SIZES], "per_size": 12,
             "pairs_per_s": 48 / (ms / 1e3), "ms_per_batch": ms, "replays": a.batch_replays,
-            "graph": f"one CUDA graph of dm_match_batch (all 48 pairs, {a.batch_lanes} concurrent lanes), replayed",
-            "lanes": a.batch_lanes, "matches": n_match,
+            "graph": (f"one CUDA graph of dm_match_batch (all 48 pairs, waves of {shape['wave']} pairs on "
+                      f"{shape['lanes']} concurrent lanes), replayed"),
+            "batch_shape": shape, "matches": n_match,
             "autotuned": tuned}
 
 
@@ -634,9 +661,12 @@ def _measure_batch_uniform(dm, torch, dist, ctx, a, world, local, rank, W, H, np
                       torch.zeros(1, dtype=torch.int32, device="cuda")))
         host.append((torch.from_numpy(pr.img1).pin_memory(), torch.from_numpy(pr.img2).pin_memory()))
     pairs = dm.make_pairs(items)
-    dm.dm_set_batch_lanes(ctx.ctx, a.batch_lanes)
+    dm.dm_set_batch_wave(ctx.ctx, 1)
+    dm.dm_set_batch_lanes(ctx.ctx, 1)
     ws = torch.empty(dm.dm_batch_workspace_bytes(ctx.ctx, pairs), dtype=torch.uint8, device="cuda")
     tuned = dm.dm_autotune(ctx.ctx, items[0][0], items[0][1], ws) if a.autotune else dm.dm_tuned_config(ctx.ctx, W, H, W, H)
+    del ws
+    ws, shape = _batch_shape(dm, torch, ctx, a, pairs)
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     dm.dm_timing_start(ctx.ctx, npairs)               # one uncaptured batch: counts the kernels of a step
@@ -665,8 +695,8 @@ def _measure_batch_uniform(dm, torch, dist, ctx, a, world, local, rank, W, H, np
         dist.barrier()
     ms = _max_over_ranks(torch, dist, e0.elapsed_time(e1), world, "cuda")
     statuses = []
-    lane_bytes = ws.numel() // min(a.batch_lanes, npairs)
-    for j in range(min(a.batch_lanes, npairs)):
+    lane_bytes = ws.numel() // shape["slices"]
+    for j in range(min(shape["wave"] * shape["lanes"], npairs)):
         st, _ = dm.dm_read_status(ctx.ctx, ws[j * lane_bytes:], 1)
         statuses.append(st)
     n_match = [int(it[3].item()) for it in items]
@@ -702,7 +732,7 @@ def _measure_batch_uniform(dm, torch, dist, ctx, a, world, local, rank, W, H, np
             "e2e": _job_throughput(world, a.steps * npairs, e2e_s), "launches": launches_per_step * a.steps,
             "clocks": clk.summary(), "status": max(statuses) if statuses else 0, "matches": n_match,
             "e2e_matches_equal": e2e_matches == n_match,
-            "tuned": tuned, "h2d_bytes_per_step": npairs * 2 * W * H * 4,
+            "tuned": tuned, "batch_shape": shape, "h2d_bytes_per_step": npairs * 2 * W * H * 4,
             "d2h_bytes_per_step": npairs * (n0 * 20 + 4)}
 
 
@@ -854,9 +884,12 @@ def run_ours(a):
             # headline: the batched form at this size (pairs of one step matched in concurrent lanes, one graph)
             value, ms_step, e2e_v = uni["value"], uni["ms"] / a.steps, uni["e2e"]
             h2d, d2h, launches, clocks = uni["h2d_bytes_per_step"], uni["d2h_bytes_per_step"], uni["launches"], uni["clocks"]
-            workload = (f"batched: {uni['pairs_per_step']} {W}x{H} pairs per GPU per step in {a.batch_lanes} concurrent "
-                        f"lanes of dm_match_batch, one CUDA graph replayed per step; {recipe}; level-0 correlation in "
-                        f"{prec_text}, pyramid and backtracking in FP32")
+            bs = uni["batch_shape"]
+            form = (f"each pair on its own launches in {bs['lanes']} concurrent lanes" if bs["wave"] == 1 else
+                    f"cross-pair waves of {bs['wave']} pairs (one launch per step for a wave) on {bs['lanes']} lanes")
+            workload = (f"batched: {uni['pairs_per_step']} {W}x{H} pairs per GPU per step, {form} of dm_match_batch "
+                        f"(shape picked by dm_autotune_batch), one CUDA graph replayed per step; {recipe}; level-0 "
+                        f"correlation in {prec_text}, pyramid and backtracking in FP32")
             status, matches, shapes = uni["status"], uni["matches"], uni["tuned"]
         else:
             value, ms_step, e2e_v = r["value"], r["ms"] / a.steps, r["e2e"]

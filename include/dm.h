@@ -394,22 +394,36 @@ typedef struct {
     int* d_count;
 } dm_pair;
 
-/* Batched form.  Matches n pairs of possibly different sizes.  The pairs are
- * spread over the context's concurrent lanes (internal streams; 2 by
- * default, dm_set_batch_lanes): pair k runs on lane k % lanes, each lane in
- * its own slice of d_ws (slice j at offset j * lane_bytes, lane_bytes = the
- * largest match_bytes over the pairs rounded up to 256), so that the
- * latency-bound phases of one pair (backtracking, the small top levels)
- * overlap the compute of another.  The lanes fork from and join back into
- * `stream` with events: all of the work is ordered after what was already on
- * `stream`, and work queued on `stream` later waits for every pair.
- * dm_batch_workspace_bytes gives lanes * lane_bytes; a smaller d_ws (at least
- * lane_bytes) runs fewer lanes.  Nothing synchronises with the host, so the
- * whole batch can be captured in a CUDA graph and replayed (make one
- * uncaptured call first so that one-time per-device set-up does not happen
- * inside the capture).  Arguments of every pair are checked before anything
- * is launched.  Each lane's device status word is in the header of its slice
- * (dm_read_status on d_ws + j * lane_bytes reads the last pair of lane j). */
+/* Batched form.  Matches n pairs of possibly different sizes, with the
+ * results of dm_match pair by pair.  The pairs run in waves of up to W pairs
+ * (dm_set_batch_wave, 1 by default; dm_autotune_batch picks W and the number
+ * of lanes for a batch and a workspace): within a wave every step of the method
+ * is one launch for all of its pairs -- the descriptor passes, the operand
+ * packing, one persistent level-0 kernel whose CTAs drain the work units of
+ * every pair of the wave in turn, one launch per kernel and level of the
+ * pyramid, one per step of the backtracking, one reciprocal verification --
+ * each kernel taking the wave's per-pair arguments in its parameters and
+ * mapping its blocks or work units onto (pair, unit), so that the small and
+ * latency-bound steps of all pairs (the top levels, the backtracking) fill
+ * the GPU together.  Waves run on the context's concurrent lanes (internal
+ * streams; 2 by default, dm_set_batch_lanes): wave i on lane i % lanes.  Each
+ * pair of a wave has its own slice of d_ws (pair j of the wave on lane k in
+ * slice k W + j, at offset (k W + j) lane_bytes, lane_bytes = the largest
+ * match_bytes over the pairs rounded up to 256); a smaller d_ws (at least
+ * lane_bytes) runs narrower waves, then fewer lanes.  With W = 1 each pair
+ * runs its own launches, pair k on lane k % lanes, so that the latency-bound
+ * phases of one pair overlap the compute of another.  The lanes fork from
+ * and join back into `stream` with events: all of the work is ordered after
+ * what was already on `stream`, and work queued on `stream` later waits for
+ * every pair.  dm_batch_workspace_bytes gives the slices of the configured
+ * waves and lanes (W' K' lane_bytes, W' = min(W, n), K' = min(lanes, number
+ * of waves)).  Nothing synchronises with the host, so the whole batch can be
+ * captured in a CUDA graph and replayed (make one uncaptured call first so
+ * that one-time per-device set-up does not happen inside the capture); the
+ * per-pair arguments of the cross-pair launches are kernel parameters, which
+ * the graph keeps.  Arguments of every pair are checked before anything is
+ * launched.  Each pair's device status word is in the header of its slice
+ * (dm_read_status on the slice reads the last pair that ran there). */
 dm_status dm_batch_workspace_bytes(const dm_ctx* ctx, int n, const dm_pair* pairs, size_t* bytes);
 dm_status dm_match_batch(dm_ctx* ctx, int n, const dm_pair* pairs, void* d_ws, size_t ws_bytes, void* stream);
 /* One image pair of a host-buffer batch: images and outputs in host memory. */
@@ -425,23 +439,44 @@ typedef struct {
 
 /* Batched form with host buffers (the whole chain as one call from host
  * memory: no counterpart in the paper).  As dm_match_batch, but every pair's
- * images are copied from host memory into its lane's workspace slice, and its
- * matches and count copied back to host memory, inside the lane: the copies of
- * one pair overlap the compute of the pairs in the other lanes.  Everything is
+ * images are copied from host memory into its workspace slice, and its
+ * matches and count copied back to host memory, inside its lane (before and
+ * after its wave): the copies of one wave overlap the compute of the waves in
+ * the other lanes.  Everything is
  * asynchronous on the lanes and `stream`; the host buffers must stay valid,
  * and the results are there, once `stream` has completed.  With page-locked
  * host buffers the copies are truly asynchronous and the whole call can be
  * captured in a CUDA graph (make one uncaptured call first); with pageable
  * buffers the copies are staged synchronously by the CUDA runtime and the call
  * cannot be captured.  A count above the capacity is reported only through
- * *h_count.  dm_batch_host_workspace_bytes gives lanes * lane_bytes as for
- * dm_match_batch (lane_bytes = the largest match_bytes over the pairs). */
+ * *h_count.  dm_batch_host_workspace_bytes gives the slices of the configured
+ * waves and lanes as for dm_match_batch (lane_bytes = the largest match_bytes
+ * over the pairs). */
 dm_status dm_batch_host_workspace_bytes(const dm_ctx* ctx, int n, const dm_pair_host* pairs, size_t* bytes);
 dm_status dm_match_batch_host(dm_ctx* ctx, int n, const dm_pair_host* pairs, void* d_ws, size_t ws_bytes, void* stream);
 
 /* Number of concurrent lanes of dm_match_batch and dm_match_invariant, 1..4
- * (1: one pair, or one transform, after the other on `stream`). */
+ * (1: one wave, pair or transform after the other on `stream`). */
 dm_status dm_set_batch_lanes(dm_ctx* ctx, int lanes);
+
+/* Pairs per wave of dm_match_batch and dm_match_batch_host, 1..8 (1, the
+ * default: every pair with its own launches). */
+dm_status dm_set_batch_wave(dm_ctx* ctx, int pairs);
+
+/* Autotuner of the batch shape: runs dm_match_batch on these pairs (twice
+ * per candidate, timed with CUDA events on `stream`) for every wave width W in
+ * {1, 2, 3, 4, 6, 8} and lanes K in 1..4 with W K slices of lane_bytes within
+ * ws_bytes (and W <= n, K <= the number of waves), and keeps the fastest
+ * (a candidate must beat the best so far by 2 %) as the context's wave width
+ * and lanes.  chosen (may be NULL) receives {W, K}.  Synchronises with the host
+ * (not capturable); the pairs' outputs hold the matches of the last run.
+ * DM_ENOMEM if ws_bytes is below one lane_bytes.  The measured choice at
+ * 1024 x 436 (8 BF16 pairs): W = 1 on 2 lanes (55.6 pairs/s) against waves of
+ * 2 on 2 lanes (53.8) and of 4 on one lane (52.0) -- there one pair's
+ * kernels already fill the GPU and two lanes overlap one pair's latency-bound
+ * steps with another's level 0; waves pay off where pairs are small. */
+dm_status dm_autotune_batch(dm_ctx* ctx, int n, const dm_pair* pairs, void* d_ws, size_t ws_bytes, int* chosen,
+                            void* stream);
 
 /* Autotuner of the batched form.  Runs the launch-shape candidates of three
  * kernels on the given pair and keeps, for pairs of exactly these sizes in

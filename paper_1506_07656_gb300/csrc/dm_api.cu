@@ -38,6 +38,7 @@ struct dm_ctx {
     unsigned int inj_table_cap = 0;   // > 0: merge tables of the backtracking capped at this many slots
     long long inj_wait = 0;           // > 0: level-kernel CTAs first wait this many cycles on a barrier nothing completes
     int force_key64 = 0;              // dm_set_merge_keys(64): 64-bit merge keys at every size
+    int wave = 1;                     // batched form: pairs per cross-pair wave (dm_set_batch_wave, dm_autotune_batch)
 };
 
 // process-wide: > 0, the g_inj_alloc-th next resource creation of the library fails
@@ -150,7 +151,7 @@ void match_layout(const DmGeom& g, int precision, MatchLayout* m, bool star = fa
     m->desc1 = o; o = dm_align(o + (size_t)g.W1 * g.H1 * 9 * 4);
     m->desc2 = o; o = dm_align(o + (size_t)g.W2 * g.H2 * 9 * 4);
     size_t big = (size_t)g.W1 * g.H1 > (size_t)g.W2 * g.H2 ? (size_t)g.W1 * g.H1 : (size_t)g.W2 * g.H2;
-    m->tmp = o; o = dm_align(o + 2 * big * 8 * 4);
+    m->tmp = o; o = dm_align(o + 4 * big * 8 * 4);   // two [H][W][8] buffers per image (both images at once in a wave)
     m->img1 = o; o = dm_align(o + (size_t)g.W1 * g.H1 * 4);
     m->img2 = o; o = dm_align(o + (size_t)g.W2 * g.H2 * 4);
     m->out = o; o = dm_align(o + (size_t)g.npatch(0) * sizeof(dm_match_t));
@@ -823,6 +824,150 @@ dm_status dm_loss_grad(dm_ctx* ctx, const dm_pyramid* pyr, const float* d_desc1,
 }
 
 namespace {
+// One pair of a wave of the batched form: device images, its workspace slice
+// (a match workspace), its output.
+struct WavePair {
+    const float* img1;
+    int W1, H1;
+    const float* img2;
+    int W2, H2;
+    char* base;
+    dm_match_t* out;
+    int capacity;
+    int* count;
+};
+
+// A wave of n <= DM_BATCH_MAX pairs in the cross-pair form: every step of the
+// method is one launch for all of them (descriptors, the operand packing and
+// the level-0 kernel, each level, each step of the backtracking, the
+// reciprocal verification) -- the exact form's results, pair by pair.
+dm_status run_wave(dm_ctx* ctx, int n, const WavePair* w, cudaStream_t st) {
+    DmGeom g[DM_BATCH_MAX];
+    MatchLayout ml[DM_BATCH_MAX];
+    dm_pyramid py[DM_BATCH_MAX];
+    const dm_pyramid* pys[DM_BATCH_MAX];
+    DmBtLayout bls[DM_BATCH_MAX];
+    const DmBtLayout* blp[DM_BATCH_MAX];
+    int* status[DM_BATCH_MAX];
+    char* bases[DM_BATCH_MAX];
+    dm_match_t* outs[DM_BATCH_MAX];
+    int caps[DM_BATCH_MAX];
+    int* counts[DM_BATCH_MAX];
+    const float* imgs[2 * DM_BATCH_MAX];
+    int Ws[2 * DM_BATCH_MAX], Hs[2 * DM_BATCH_MAX];
+    float *descs[2 * DM_BATCH_MAX], *tA[2 * DM_BATCH_MAX], *tB[2 * DM_BATCH_MAX];
+    const int prec = ctx->cfg.precision;
+    cudaError_t e;
+    for (int j = 0; j < n; j++) {
+        dm_status s = check_geom(ctx, w[j].W1, w[j].H1, w[j].W2, w[j].H2, &g[j]);
+        if (s != DM_OK) return s;
+        match_layout(g[j], prec, &ml[j]);
+        char* base = w[j].base;
+        const size_t big = std::max((size_t)g[j].W1 * g[j].H1, (size_t)g[j].W2 * g[j].H2) * 8;
+        float* tmp = (float*)(base + ml[j].tmp);
+        imgs[2 * j] = w[j].img1;
+        Ws[2 * j] = w[j].W1;
+        Hs[2 * j] = w[j].H1;
+        descs[2 * j] = (float*)(base + ml[j].desc1);
+        tA[2 * j] = tmp;
+        tB[2 * j] = tmp + big;
+        imgs[2 * j + 1] = w[j].img2;
+        Ws[2 * j + 1] = w[j].W2;
+        Hs[2 * j + 1] = w[j].H2;
+        descs[2 * j + 1] = (float*)(base + ml[j].desc2);
+        tA[2 * j + 1] = tmp + 2 * big;
+        tB[2 * j + 1] = tmp + 3 * big;
+        fill_pyramid(&py[j], g[j], prec, ctx->cfg.compensated, tune_for(ctx, g[j]), ml[j].py, base + ml[j].pyr);
+        pys[j] = &py[j];
+        bls[j] = capped_tables(ctx, ml[j].bt);
+        blp[j] = &bls[j];
+        status[j] = &reinterpret_cast<DmWsHeader*>(base + ml[j].bt.header)->pyr_status;
+        if ((e = cudaMemsetAsync(status[j], 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(ctx, e, "clear status");
+        bases[j] = base;
+        outs[j] = w[j].out;
+        caps[j] = w[j].capacity;
+        counts[j] = w[j].count;
+    }
+    if ((e = dm_launch_descriptors_batch(ctx->desc, 2 * n, imgs, Ws, Hs, descs, tA, tB, st)) != cudaSuccess)
+        return cuda_fail(ctx, e, "descriptor kernels");
+    if (inject_launch(ctx)) return injected_launch_failure(ctx, "level-0 correlation");
+    if (prec != DM_FP32) {
+        const float* d1s[DM_BATCH_MAX];
+        const float* d2s[DM_BATCH_MAX];
+        void* abufs[DM_BATCH_MAX];
+        void* sts[DM_BATCH_MAX];
+        float* p0[DM_BATCH_MAX];
+        unsigned char* a0[DM_BATCH_MAX];
+        int mch[DM_BATCH_MAX];
+        for (int j = 0; j < n; j++) {
+            d1s[j] = descs[2 * j];
+            d2s[j] = descs[2 * j + 1];
+            abufs[j] = bases[j] + ml[j].pyr + ml[j].py.a16;
+            sts[j] = status[j];
+            p0[j] = const_cast<float*>(py[j].pooled[0]);
+            a0[j] = const_cast<unsigned char*>(py[j].amax[0]);
+            mch[j] = py[j].tune.m_chunk;
+        }
+        e = dm_launch_corr0_tc_batch(n, g, prec, d1s, d2s, ctx->cfg.lambda, abufs, sts, p0, a0, mch, st);
+    } else {
+        // (the FP32 SIMT kernel runs pair by pair)
+        for (int j = 0; j < n && e == cudaSuccess; j++)
+            e = dm_launch_corr0_f32(g[j], descs[2 * j], descs[2 * j + 1], ctx->cfg.lambda, const_cast<float*>(py[j].pooled[0]),
+                                    const_cast<unsigned char*>(py[j].amax[0]), st);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "level-0 correlation");
+    if (inject_launch(ctx)) return injected_launch_failure(ctx, "pyramid levels");
+    if ((e = dm_launch_levels_batch(pys, n, ctx->cfg.lambda, status, st)) != cudaSuccess)
+        return cuda_fail(ctx, e, "pyramid levels");
+    if (inject_launch(ctx)) return injected_launch_failure(ctx, "backtracking kernels");
+    if ((e = dm_launch_backtrack_batch(pys, blp, bases, outs, caps, counts, n, st)) != cudaSuccess)
+        return cuda_fail(ctx, e, "backtracking kernels");
+    return DM_OK;
+}
+
+// Waves of the batched form over a workspace of `slices` match workspaces:
+// width W (pairs per wave) and lanes K (concurrent waves), K * W <= slices.
+void wave_shape(const dm_ctx* ctx, int n, size_t slices, int* W, int* K) {
+    int w = std::min(std::min(ctx->wave, n), (int)std::min(slices, (size_t)DM_BATCH_MAX));
+    if (w < 1) w = 1;
+    const int waves = (n + w - 1) / w;
+    int k = (int)std::min(slices / (size_t)w, (size_t)ctx->lanes);
+    if (k > waves) k = waves;
+    if (k < 1) k = 1;
+    *W = w;
+    *K = k;
+}
+
+// Runs the n pairs of a batch as waves of W pairs on K lanes (fork from and
+// join into `st`); wave i covers pairs [i W, i W + W) and runs on lane i % K in
+// the slices [lane W, lane W + W) of the workspace.  run(first, count, slice0,
+// stream) issues one wave.
+extern "C++" template <class F>
+dm_status run_waves(dm_ctx* ctx, int n, int W, int K, char* ws, size_t slice, cudaStream_t st, const char* what, F run) {
+    const int waves = (n + W - 1) / W;
+    if (K == 1) {
+        for (int i = 0; i < waves; i++) {
+            dm_status s = run(i * W, std::min(W, n - i * W), ws, st);
+            if (s != DM_OK) return s;
+        }
+        return DM_OK;
+    }
+    cudaError_t e = cudaEventRecord(ctx->fork_ev, st);
+    for (int j = 0; e == cudaSuccess && j < K; j++) e = cudaStreamWaitEvent(ctx->lane_st[j], ctx->fork_ev, 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+    for (int i = 0; i < waves; i++) {
+        const int lane = i % K;
+        dm_status s = run(i * W, std::min(W, n - i * W), ws + (size_t)lane * W * slice, ctx->lane_st[lane]);
+        if (s != DM_OK) return s;
+    }
+    for (int j = 0; e == cudaSuccess && j < K; j++) {
+        e = cudaEventRecord(ctx->join_ev[j], ctx->lane_st[j]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->join_ev[j], 0);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+    return DM_OK;
+}
+
 // workspace of one lane: the largest match workspace over the pairs (256-byte multiple)
 dm_status batch_lane_bytes(dm_ctx* ctx, int n, const dm_pair* pairs, size_t* bytes) {
     size_t best = 256;
@@ -845,6 +990,14 @@ dm_status dm_set_merge_keys(dm_ctx* ctx, int bits) {
     return DM_OK;
 }
 
+dm_status dm_set_batch_wave(dm_ctx* ctx, int pairs) {
+    if (!ctx) return DM_EINVAL;
+    if (pairs < 1 || pairs > DM_BATCH_MAX)
+        return fail(ctx, DM_EINVAL, "dm_set_batch_wave: pairs must be in [1, %d]", DM_BATCH_MAX);
+    ctx->wave = pairs;
+    return DM_OK;
+}
+
 dm_status dm_set_batch_lanes(dm_ctx* ctx, int lanes) {
     if (!ctx) return DM_EINVAL;
     if (lanes < 1 || lanes > DM_MAX_LANES) return fail(ctx, DM_EINVAL, "dm_set_batch_lanes: lanes must be 1..%d", DM_MAX_LANES);
@@ -857,8 +1010,10 @@ dm_status dm_batch_workspace_bytes(const dm_ctx* ctx, int n, const dm_pair* pair
     size_t lane = 0;
     dm_status s = batch_lane_bytes(const_cast<dm_ctx*>(ctx), n, pairs, &lane);
     if (s != DM_OK) return s;
-    const int lanes = n < ctx->lanes ? (n > 0 ? n : 1) : ctx->lanes;
-    *bytes = lane * (size_t)lanes;
+    const int W = std::max(1, std::min(ctx->wave, n));
+    const int waves = n > 0 ? (n + W - 1) / W : 1;
+    const int lanes = std::max(1, std::min(ctx->lanes, waves));
+    *bytes = lane * (size_t)W * (size_t)lanes;
     return DM_OK;
 }
 
@@ -879,11 +1034,25 @@ dm_status dm_match_batch(dm_ctx* ctx, int n, const dm_pair* pairs, void* d_ws, s
     if (s != DM_OK) return s;
     if (ws_bytes < lane_bytes) return fail(ctx, DM_ENOMEM, "dm_match_batch: needs at least %zu workspace bytes", lane_bytes);
     if (n == 0) return DM_OK;
+    DevGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int W = 1, K = 1;
+    wave_shape(ctx, n, ws_bytes / lane_bytes, &W, &K);
+    if (W > 1) {
+        return run_waves(ctx, n, W, K, (char*)d_ws, lane_bytes, st, "dm_match_batch: fork / join",
+                         [&](int first, int cnt, char* slice0, cudaStream_t ls) -> dm_status {
+                             WavePair w[DM_BATCH_MAX];
+                             for (int j = 0; j < cnt; j++) {
+                                 const dm_pair& q = pairs[first + j];
+                                 w[j] = WavePair{q.d_img1, q.W1, q.H1, q.d_img2, q.W2, q.H2, slice0 + (size_t)j * lane_bytes,
+                                                 q.d_out, q.capacity, q.d_count};
+                             }
+                             return run_wave(ctx, cnt, w, ls);
+                         });
+    }
     int lanes = (int)(ws_bytes / lane_bytes);
     if (lanes > ctx->lanes) lanes = ctx->lanes;
     if (lanes > n) lanes = n;
-    DevGuard dg(ctx->device);
-    cudaStream_t st = (cudaStream_t)stream;
     if (lanes == 1) {
         for (int k = 0; k < n; k++) {
             const dm_pair& q = pairs[k];
@@ -962,8 +1131,10 @@ dm_status dm_batch_host_workspace_bytes(const dm_ctx* ctx, int n, const dm_pair_
     size_t lane = 0;
     dm_status s = batch_host_lane_bytes(const_cast<dm_ctx*>(ctx), n, pairs, &lane);
     if (s != DM_OK) return s;
-    const int lanes = n < ctx->lanes ? (n > 0 ? n : 1) : ctx->lanes;
-    *bytes = lane * (size_t)lanes;
+    const int W = std::max(1, std::min(ctx->wave, n));
+    const int waves = n > 0 ? (n + W - 1) / W : 1;
+    const int lanes = std::max(1, std::min(ctx->lanes, waves));
+    *bytes = lane * (size_t)W * (size_t)lanes;
     return DM_OK;
 }
 
@@ -985,11 +1156,52 @@ dm_status dm_match_batch_host(dm_ctx* ctx, int n, const dm_pair_host* pairs, voi
     if (ws_bytes < lane_bytes)
         return fail(ctx, DM_ENOMEM, "dm_match_batch_host: needs at least %zu workspace bytes", lane_bytes);
     if (n == 0) return DM_OK;
+    DevGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int W = 1, K = 1;
+    wave_shape(ctx, n, ws_bytes / lane_bytes, &W, &K);
+    if (W > 1) {
+        return run_waves(ctx, n, W, K, (char*)d_ws, lane_bytes, st, "dm_match_batch_host: fork / join",
+                         [&](int first, int cnt, char* slice0, cudaStream_t ls) -> dm_status {
+                             WavePair w[DM_BATCH_MAX];
+                             MatchLayout ml[DM_BATCH_MAX];
+                             cudaError_t e;
+                             for (int j = 0; j < cnt; j++) {
+                                 const dm_pair_host& q = pairs[first + j];
+                                 DmGeom g;
+                                 dm_status s2 = check_geom(ctx, q.W1, q.H1, q.W2, q.H2, &g);
+                                 if (s2 != DM_OK) return s2;
+                                 match_layout(g, ctx->cfg.precision, &ml[j]);
+                                 char* base = slice0 + (size_t)j * lane_bytes;
+                                 float* i1 = (float*)(base + ml[j].img1);
+                                 float* i2 = (float*)(base + ml[j].img2);
+                                 if ((e = cudaMemcpyAsync(i1, q.h_img1, (size_t)q.W1 * q.H1 * 4, cudaMemcpyHostToDevice, ls)) !=
+                                     cudaSuccess)
+                                     return cuda_fail(ctx, e, "dm_match_batch_host: copy image 1");
+                                 if ((e = cudaMemcpyAsync(i2, q.h_img2, (size_t)q.W2 * q.H2 * 4, cudaMemcpyHostToDevice, ls)) !=
+                                     cudaSuccess)
+                                     return cuda_fail(ctx, e, "dm_match_batch_host: copy image 2");
+                                 w[j] = WavePair{i1, q.W1, q.H1, i2, q.W2, q.H2, base, (dm_match_t*)(base + ml[j].out),
+                                                 g.npatch(0), (int*)(base + ml[j].count)};
+                             }
+                             dm_status s2 = run_wave(ctx, cnt, w, ls);
+                             if (s2 != DM_OK) return s2;
+                             for (int j = 0; j < cnt; j++) {
+                                 const dm_pair_host& q = pairs[first + j];
+                                 const int ncopy = std::min(q.capacity, w[j].capacity);
+                                 if (ncopy > 0 && (e = cudaMemcpyAsync(q.h_out, w[j].out, (size_t)ncopy * sizeof(dm_match_t),
+                                                                       cudaMemcpyDeviceToHost, ls)) != cudaSuccess)
+                                     return cuda_fail(ctx, e, "dm_match_batch_host: copy matches");
+                                 if ((e = cudaMemcpyAsync(q.h_count, w[j].count, sizeof(int), cudaMemcpyDeviceToHost, ls)) !=
+                                     cudaSuccess)
+                                     return cuda_fail(ctx, e, "dm_match_batch_host: copy count");
+                             }
+                             return DM_OK;
+                         });
+    }
     int lanes = (int)(ws_bytes / lane_bytes);
     if (lanes > ctx->lanes) lanes = ctx->lanes;
     if (lanes > n) lanes = n;
-    DevGuard dg(ctx->device);
-    cudaStream_t st = (cudaStream_t)stream;
     if (lanes == 1) {
         for (int k = 0; k < n; k++)
             if ((s = run_host_pair(ctx, pairs[k], (char*)d_ws, lane_bytes, st)) != DM_OK) return s;
@@ -1114,6 +1326,67 @@ dm_status dm_autotune(dm_ctx* ctx, const float* d_img1, int W1, int H1, const fl
         ctx->tuned[{W1, H1, W2, H2}] = best;
     }
     if (chosen) { chosen[0] = best.m_chunk; chosen[1] = best.level_th; chosen[2] = best.bt_mult; chosen[3] = best.level_ring; }
+    return DM_OK;
+}
+
+dm_status dm_autotune_batch(dm_ctx* ctx, int n, const dm_pair* pairs, void* d_ws, size_t ws_bytes, int* chosen,
+                            void* stream) {
+    if (!ctx) return DM_EINVAL;
+    if (n < 1 || !pairs || !d_ws) return fail(ctx, DM_EINVAL, "dm_autotune_batch: bad arguments");
+    size_t lane = 0;
+    dm_status s = batch_lane_bytes(ctx, n, pairs, &lane);
+    if (s != DM_OK) return s;
+    const size_t slices = ws_bytes / lane;
+    if (slices < 1) return fail(ctx, DM_ENOMEM, "dm_autotune_batch: needs at least %zu workspace bytes", lane);
+    DevGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int wave0 = ctx->wave, lanes0 = ctx->lanes;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(ctx, cudaGetLastError(), "dm_autotune_batch: events");
+    }
+    // (wave width, lanes) within the workspace: each pair on its own launches
+    // on 1..4 lanes, and waves of 2..8 pairs on 1..4 lanes
+    int best_w = 1, best_k = 1;
+    float best_ms = -1.0f;
+    dm_status rs = DM_OK;
+    for (int w : {1, 2, 3, 4, 6, 8}) {
+        if (w > n || (size_t)w > slices || w > DM_BATCH_MAX) continue;
+        const int waves = (n + w - 1) / w;
+        for (int k = 1; k <= DM_MAX_LANES; k++) {
+            if ((size_t)(w * k) > slices || k > waves) break;
+            ctx->wave = w;
+            ctx->lanes = k;
+            float ms = -1.0f;
+            for (int r = 0; r < 2 && rs == DM_OK; r++) {     // the first run also absorbs one-time set-up
+                cudaEventRecord(e0, st);
+                rs = dm_match_batch(ctx, n, pairs, d_ws, (size_t)w * k * lane, st);
+                cudaEventRecord(e1, st);
+                if (rs == DM_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (rs != DM_OK) break;
+            if (ms >= 0.0f && (best_ms < 0.0f || ms < 0.98f * best_ms)) {
+                best_ms = ms;
+                best_w = w;
+                best_k = k;
+            }
+        }
+        if (rs != DM_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rs != DM_OK) {
+        ctx->wave = wave0;
+        ctx->lanes = lanes0;
+        return rs;
+    }
+    ctx->wave = best_w;
+    ctx->lanes = best_k;
+    if (chosen) {
+        chosen[0] = best_w;
+        chosen[1] = best_k;
+    }
     return DM_OK;
 }
 

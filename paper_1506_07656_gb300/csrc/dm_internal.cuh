@@ -11,6 +11,7 @@
 
 #define DM_MAXL 30
 #define DM_MAX_LANES 4   // concurrent lanes (internal streams) of the batched form
+#define DM_BATCH_MAX 8   // pairs per wave of the cross-pair batched form (one launch per step for the wave)
 
 // Geometry of one image pair (Sec. 3.2 "Bottom level", Eq. 7, Algorithm 1).
 struct DmGeom {
@@ -493,6 +494,10 @@ bool dm_encode_tiled(CUtensorMap* m, CUtensorMapDataType dt, int rank, void* bas
 // Kernel launchers (return cudaGetLastError()).
 cudaError_t dm_launch_descriptors(const DmDescParams& prm, const float* img, int W, int H, float* desc,
                                   float* tmpA, float* tmpB, cudaStream_t st);
+// The same for n <= 2 DM_BATCH_MAX images: one launch per pass for all of them.
+cudaError_t dm_launch_descriptors_batch(const DmDescParams& prm, int n, const float* const* imgs, const int* Ws,
+                                        const int* Hs, float* const* descs, float* const* tmpAs, float* const* tmpBs,
+                                        cudaStream_t st);
 // Level-0 launchers.  The rows of the correlation are image 1's atomic
 // patches taken from d1, or, when amat is given, the n_rows vectors
 // amat[n_rows][144] (k = (dy*4 + dx)*9 + c; the prototypes of the approximate
@@ -504,6 +509,12 @@ cudaError_t dm_launch_corr0_f32(const DmGeom& g, const float* d1, const float* d
 cudaError_t dm_launch_corr0_tc(const DmGeom& g, int precision, const float* d1, const float* d2, float lam, void* abuf,
                                void* status, float* pooled0, unsigned char* amax0, int m_chunk, cudaStream_t st,
                                const float* amat = nullptr, int n_rows = -1);
+// Level 0 of the n <= DM_BATCH_MAX pairs of a wave (exact form): their operand
+// packing, then one persistent launch that drains the work units of all pairs.
+cudaError_t dm_launch_corr0_tc_batch(int n, const DmGeom* gs, int precision, const float* const* d1s,
+                                     const float* const* d2s, float lam, void* const* abufs, void* const* statuses,
+                                     float* const* pooled0s, unsigned char* const* amax0s, const int* m_chunks,
+                                     cudaStream_t st);
 // Spherical k-means of image 1's atomic patches (Sec. 4.1), see k_approx.cu.
 size_t dm_kmeans_ws_bytes(const DmGeom& g, int D);
 size_t dm_kmeans_init_offset(const DmGeom& g, int D);
@@ -511,6 +522,9 @@ cudaError_t dm_launch_kmeans(const DmGeom& g, const float* d1, int D, int iters,
                              int* assign, char* ws, cudaStream_t st);
 size_t dm_corr0_tc_a_bytes(const DmGeom& g, int precision);
 cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& p, float lam, int* status, cudaStream_t st);
+// The same for the n <= DM_BATCH_MAX pyramids of a wave (same precision and
+// child-sum mode, level 0 computed): one launch per kernel and level for all.
+cudaError_t dm_launch_levels_batch(const dm_pyramid* const* pys, int n, float lam, int* const* status, cudaStream_t st);
 cudaError_t dm_launch_loss_grad(const DmGeom& g, const dm_pyramid& py, const float* d1, const float* d2, float lam,
                                 const DmGradLayout& gl, char* ws, float* d_loss, float* g1, float* g2, cudaStream_t st);
 // With rect != nullptr the atomic correspondences are rectified into
@@ -519,6 +533,11 @@ cudaError_t dm_launch_loss_grad(const DmGeom& g, const dm_pyramid& py, const flo
 cudaError_t dm_launch_backtrack(const DmGeom& g, const dm_pyramid& p, const DmBtLayout& bl, char* ws,
                                 dm_match_t* out, int capacity, int* d_count, cudaStream_t st,
                                 const DmRect* rect = nullptr);
+// The same for the n <= DM_BATCH_MAX pairs of a wave (pyramids computed), each
+// with its own workspace wss[j] (layout *bls[j]) and output: one launch per
+// step of the descent for all of them, then one reciprocal launch.
+cudaError_t dm_launch_backtrack_batch(const dm_pyramid* const* pys, const DmBtLayout* const* bls, char* const* wss,
+                                      dm_match_t* const* outs, const int* caps, int* const* counts, int n, cudaStream_t st);
 // DM* (Sec. 5.3): entry points at the local maxima of every level's maps,
 // start + end scoring; bl from dm_bt_layout(g, &bl, true).
 cudaError_t dm_launch_backtrack_star(const DmGeom& g, const dm_pyramid& p, const DmBtLayout& bl, char* ws, float lam,

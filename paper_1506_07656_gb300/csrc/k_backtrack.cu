@@ -35,6 +35,8 @@
 // A patch's best tuple is output iff it also wins its cell of I'.
 #include "dm_internal.cuh"
 
+#include <memory>
+
 namespace {
 
 constexpr int BT_BLOCK = 256;
@@ -274,14 +276,17 @@ __global__ void k_star_prepare(BtArgs a, int lvl) {
 }
 
 template <bool K64>
-__global__ void k_bt_prepare(BtArgs a, int lvl, long long n_top) {
+__device__ __forceinline__ void bt_prepare_body(const BtArgs& a, int lvl, long long n_top) {
     const unsigned long long n_prev = (lvl + 1 == a.g.L) ? (unsigned long long)n_top : a.hdr->count[lvl + 1];
     clear_table<K64>(a, lvl, (n_prev * HT_SLOTS_PER_PREV + 31ull) & ~31ull);
 }
 
+template <bool K64>
+__global__ void k_bt_prepare(BtArgs a, int lvl, long long n_top) { bt_prepare_body<K64>(a, lvl, n_top); }
+
 // Expansion of the top level: every position of every existing top patch.
 template <int MODE, bool K64>
-__global__ void k_bt_expand_top(BtArgs a) {
+__device__ __forceinline__ void bt_expand_top_body(const BtArgs& a) {
     const DmGeom& g = a.g;
     const int L = g.L;
     const long long ds = g.dsize(L);
@@ -302,13 +307,16 @@ __global__ void k_bt_expand_top(BtArgs a) {
     add_count(a, L - 1, arrivals);
 }
 
+template <int MODE, bool K64>
+__global__ void k_bt_expand_top(BtArgs a) { bt_expand_top_body<MODE, K64>(a); }
+
 // Expansion of level l < L: the merged tuples of level l, read by scanning the
 // active part of its table in slot order.  Each warp packs the occupied slots
 // it reads into a queue in shared memory and expands them 32 at a time, so its
 // lanes stay busy while the slot order (neighbouring positions of one patch
 // together) is kept.
 template <int MODE, bool K64>
-__global__ void k_bt_expand(BtArgs a, int l) {
+__device__ __forceinline__ void bt_expand_body(const BtArgs& a, int l) {
     // queued slots: the packed slot (32-bit keys), or key + 1 and score
     __shared__ unsigned long long queue[BT_BLOCK / 32][64];
     __shared__ unsigned int qscore[K64 ? BT_BLOCK / 32 : 1][64];
@@ -377,9 +385,12 @@ __global__ void k_bt_expand(BtArgs a, int l) {
     add_count(a, l - 1, arrivals);
 }
 
+template <int MODE, bool K64>
+__global__ void k_bt_expand(BtArgs a, int l) { bt_expand_body<MODE, K64>(a, l); }
+
 // Reciprocal verification and compaction in atomic-patch order (one block).
-__global__ void __launch_bounds__(1024) k_reciprocal(BtArgs a, dm_match_t* __restrict__ out, int capacity,
-                                                     int* __restrict__ d_count) {
+__device__ __forceinline__ void reciprocal_body(const BtArgs& a, dm_match_t* __restrict__ out, int capacity,
+                                                int* __restrict__ d_count) {
     const DmGeom& g = a.g;
     const int n0 = g.npatch(0);
     const int CW = (g.W2 + 3) >> 2;
@@ -452,6 +463,11 @@ __global__ void __launch_bounds__(1024) k_reciprocal(BtArgs a, dm_match_t* __res
         *d_count = total;
         if (total > capacity) atomicOr(&a.hdr->status, DM_DEV_OUTPUT_OVERFLOW);
     }
+}
+
+__global__ void __launch_bounds__(1024) k_reciprocal(BtArgs a, dm_match_t* __restrict__ out, int capacity,
+                                                     int* __restrict__ d_count) {
+    reciprocal_body(a, out, capacity, d_count);
 }
 
 // DM* entry points at level l (1..L): the local maxima of the maps C_l(p, .)
@@ -579,8 +595,10 @@ void launch_steps(const BtArgs& a, int grid, cudaStream_t st) {
 
 }  // namespace
 
-cudaError_t dm_launch_backtrack(const DmGeom& g, const dm_pyramid& py, const DmBtLayout& bl, char* ws,
-                                dm_match_t* out, int capacity, int* d_count, cudaStream_t st, const DmRect* rect) {
+namespace {
+
+// Arguments of one pair's backtracking over workspace ws (layout bl).
+BtArgs make_bt_args(const DmGeom& g, const dm_pyramid& py, const DmBtLayout& bl, char* ws) {
     BtArgs a;
     memset(&a, 0, sizeof(a));
     a.g = g;
@@ -599,23 +617,75 @@ cudaError_t dm_launch_backtrack(const DmGeom& g, const dm_pyramid& py, const DmB
     a.bestP = reinterpret_cast<unsigned long long*>(ws + bl.bestP);
     a.bestQ = reinterpret_cast<unsigned long long*>(ws + bl.bestQ);
     a.hdr = reinterpret_cast<DmWsHeader*>(ws + bl.header);
-    if (rect) a.rect = *rect;
+    return a;
+}
 
+// Clear the backtracking part of the header (status word, counts, table
+// sizes; pyr_status belongs to the pyramid step that ran before) and, unless
+// the tuples go to another pair's keys (rect), the BestAt / BestAt' keys.
+cudaError_t clear_bt(const BtArgs& a, bool keys, cudaStream_t st) {
+    const DmGeom& g = a.g;
     cudaError_t e;
-    // clear the backtracking part of the header (status word, counts, table sizes);
-    // pyr_status belongs to the pyramid step that ran before
     if ((e = cudaMemsetAsync(&a.hdr->status, 0, sizeof(int), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(a.hdr->count, 0, sizeof(a.hdr->count) + sizeof(a.hdr->cap), st)) != cudaSuccess) return e;
-    if (!rect) {
+    if (keys) {
         if ((e = cudaMemsetAsync(a.bestP, 0, sizeof(unsigned long long) * g.npatch(0), st)) != cudaSuccess) return e;
         size_t ncell = (size_t)((g.W2 + 3) / 4) * ((g.H2 + 3) / 4);
         if ((e = cudaMemsetAsync(a.bestQ, 0, sizeof(unsigned long long) * ncell, st)) != cudaSuccess) return e;
     }
+    return cudaSuccess;
+}
 
+int sm_count() {
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = nsm * (py.tune.bt_mult > 0 ? py.tune.bt_mult : 8);
+    return nsm;
+}
+
+// Cross-pair form: the pairs of a wave of the batched form in one launch per
+// step, pair blockIdx.y (blockIdx.x for the reciprocal step), its arguments in
+// the kernel parameters (a captured graph replays them as they were).  Step s
+// of the backtracking works on level lvl[j] = L_j - s of pair j.
+struct BtBatch {
+    BtArgs a[DM_BATCH_MAX];
+    int lvl[DM_BATCH_MAX];
+    dm_match_t* out[DM_BATCH_MAX];
+    int capacity[DM_BATCH_MAX];
+    int* count[DM_BATCH_MAX];
+    int n;
+};
+static_assert(sizeof(BtBatch) < 32000, "the kernel parameters of a wave must stay below the 32 KB limit");
+
+template <bool K64>
+__global__ void k_bt_prepare_b(const __grid_constant__ BtBatch B) {
+    const BtArgs& a = B.a[blockIdx.y];
+    bt_prepare_body<K64>(a, B.lvl[blockIdx.y] - 1, (long long)a.g.npatch(a.g.L) * a.g.dsize(a.g.L));
+}
+
+template <bool K64>
+__global__ void k_bt_expand_top_b(const __grid_constant__ BtBatch B) {
+    bt_expand_top_body<BT_EXACT, K64>(B.a[blockIdx.y]);
+}
+
+template <bool K64>
+__global__ void k_bt_expand_b(const __grid_constant__ BtBatch B) {
+    bt_expand_body<BT_EXACT, K64>(B.a[blockIdx.y], B.lvl[blockIdx.y]);
+}
+
+__global__ void __launch_bounds__(1024) k_reciprocal_b(const __grid_constant__ BtBatch B) {
+    reciprocal_body(B.a[blockIdx.x], B.out[blockIdx.x], B.capacity[blockIdx.x], B.count[blockIdx.x]);
+}
+
+}  // namespace
+
+cudaError_t dm_launch_backtrack(const DmGeom& g, const dm_pyramid& py, const DmBtLayout& bl, char* ws,
+                                dm_match_t* out, int capacity, int* d_count, cudaStream_t st, const DmRect* rect) {
+    BtArgs a = make_bt_args(g, py, bl, ws);
+    if (rect) a.rect = *rect;
+    cudaError_t e = clear_bt(a, !rect, st);
+    if (e != cudaSuccess) return e;
+    const int grid = sm_count() * (py.tune.bt_mult > 0 ? py.tune.bt_mult : 8);
     if (rect) {
         launch_steps<BT_RECT>(a, grid, st);
         dm_count_launches(2 * g.L - 1);
@@ -697,5 +767,86 @@ cudaError_t dm_launch_reciprocal(const DmGeom& g, unsigned long long* bestP, uns
     a.hdr = hdr;
     k_reciprocal<<<1, 1024, 0, st>>>(a, out, capacity, d_count);
     dm_count_launches(1);
+    return cudaGetLastError();
+}
+
+// Backtracking and reciprocal verification of the n <= DM_BATCH_MAX pairs of
+// a wave (pyramids computed): per step of the descent one launch per kernel
+// (and merge-key width in use) for every pair still descending, then one
+// reciprocal launch for all.
+cudaError_t dm_launch_backtrack_batch(const dm_pyramid* const* pys, const DmBtLayout* const* bls, char* const* wss,
+                                      dm_match_t* const* outs, const int* caps, int* const* counts, int n, cudaStream_t st) {
+    if (n < 1 || n > DM_BATCH_MAX) return cudaErrorInvalidValue;
+    // (host staging of the parameter blocks, ~20 KB each; a launch copies them)
+    std::unique_ptr<BtBatch> all_p(new BtBatch), sub_p(new BtBatch), part_p(new BtBatch);
+    BtBatch& all = *all_p;
+    memset(&all, 0, sizeof(all));
+    all.n = n;
+    int Lmax = 0, mult = 8;
+    cudaError_t e;
+    for (int j = 0; j < n; j++) {
+        all.a[j] = make_bt_args(pys[j]->g, *pys[j], *bls[j], wss[j]);
+        all.out[j] = outs[j];
+        all.capacity[j] = caps[j];
+        all.count[j] = counts[j];
+        if ((e = clear_bt(all.a[j], true, st)) != cudaSuccess) return e;
+        Lmax = max(Lmax, pys[j]->g.L);
+        if (pys[j]->tune.bt_mult > 0) mult = pys[j]->tune.bt_mult;
+    }
+    const int nsm = sm_count();
+    // blocks per pair: the single-pair grid shared by the wave, at least one per SM
+    const int per = max(nsm, nsm * mult / n);
+    long long launches = 0;
+    BtBatch& sub = *sub_p;
+    for (int step = 0; step < Lmax; step++) {
+        for (int k64 = 0; k64 < 2; k64++) {
+            // the pairs still descending at this step with this key width
+            memset(&sub, 0, sizeof(sub));
+            long long top_max = 0;
+            for (int j = 0; j < n; j++) {
+                const DmGeom& g = pys[j]->g;
+                if (step >= g.L || g.key64 != k64) continue;
+                sub.a[sub.n] = all.a[j];
+                sub.lvl[sub.n] = g.L - step;
+                sub.n++;
+                top_max = max(top_max, (long long)g.npatch(g.L) * g.dsize(g.L));
+            }
+            if (sub.n == 0) continue;
+            // tables of the next level down (for the pairs that have one)
+            BtBatch& b = sub;
+            int with_next = 0;
+            for (int j = 0; j < b.n; j++) with_next += b.lvl[j] - 1 >= 1;
+            if (with_next == b.n) {
+                if (k64) k_bt_prepare_b<true><<<dim3(per, b.n), BT_BLOCK, 0, st>>>(b);
+                else k_bt_prepare_b<false><<<dim3(per, b.n), BT_BLOCK, 0, st>>>(b);
+                launches++;
+            } else if (with_next > 0) {
+                // (pairs at level 1 have no table below: launched without them)
+                BtBatch& part = *part_p;
+                memset(&part, 0, sizeof(part));
+                for (int j = 0; j < b.n; j++)
+                    if (b.lvl[j] - 1 >= 1) {
+                        part.a[part.n] = b.a[j];
+                        part.lvl[part.n] = b.lvl[j];
+                        part.n++;
+                    }
+                if (k64) k_bt_prepare_b<true><<<dim3(per, part.n), BT_BLOCK, 0, st>>>(part);
+                else k_bt_prepare_b<false><<<dim3(per, part.n), BT_BLOCK, 0, st>>>(part);
+                launches++;
+            }
+            if (step == 0) {
+                const long long nb = (top_max + BT_BLOCK - 1) / BT_BLOCK;
+                const unsigned gx = (unsigned)(nb < per ? nb : per);
+                if (k64) k_bt_expand_top_b<true><<<dim3(gx, b.n), BT_BLOCK, 0, st>>>(b);
+                else k_bt_expand_top_b<false><<<dim3(gx, b.n), BT_BLOCK, 0, st>>>(b);
+            } else {
+                if (k64) k_bt_expand_b<true><<<dim3(per, b.n), BT_BLOCK, 0, st>>>(b);
+                else k_bt_expand_b<false><<<dim3(per, b.n), BT_BLOCK, 0, st>>>(b);
+            }
+            launches++;
+        }
+    }
+    k_reciprocal_b<<<n, 1024, 0, st>>>(all);
+    dm_count_launches(launches + 1);
     return cudaGetLastError();
 }

@@ -53,6 +53,8 @@
 
 #include "dm_internal.cuh"
 
+#include <memory>
+
 namespace {
 
 constexpr int BM = 128;                       // patches per M-tile (TMEM lanes)
@@ -370,12 +372,31 @@ __device__ __forceinline__ void epilogue_tile(const EpiArgs& e, uint32_t b, uint
     pool_out(e, 2, mult, h, stage_f, stage_c);
 }
 
+// Per-pair arguments of the level-0 kernel.  One launch serves one pair, or
+// every pair of a wave of the batched form: the persistent CTAs then drain the
+// pairs' work units one after another (pair j owns units first .. first +
+// units - 1), keeping the A-tile and accumulator pipelines running across
+// pairs; the arguments travel in the kernel parameters, so a captured graph
+// replays them as they were.
+struct L0Pair {
+    CUtensorMap tf, tc;          // pooled values and argmax codes of level 0 (TMA stores)
+    DmGeom g;
+    const unsigned char* apack;  // packed patch operand (M-tiles)
+    const float* inv_sa;         // FP8: inverse per-patch scales
+    const unsigned int* bmax;    // FP8: maximum of the image-2 field (float bits)
+    const float* d2;             // image-2 descriptors [H2][W2][9]
+    int* err;                    // the pair's status word
+    int n_mtiles, m_chunk;
+    int first, units;
+};
+struct L0Batch {
+    L0Pair p[DM_BATCH_MAX];
+    int n, total;
+};
+
 template <int FMT>
 __global__ void __launch_bounds__(THREADS, 1)
-k_corr0_tc(DmGeom g, const unsigned char* __restrict__ apack, const float* __restrict__ inv_sa,
-           const unsigned int* __restrict__ bmax, const float* __restrict__ d2,
-           float lam, const __grid_constant__ CUtensorMap tmap_f, const __grid_constant__ CUtensorMap tmap_c, int n_mtiles,
-           int m_chunk, int* __restrict__ err) {
+k_corr0_tc(const __grid_constant__ L0Batch B, float lam) {
     using F = Fmt<FMT>;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sB = smem + F::OFF_B;
@@ -389,8 +410,6 @@ k_corr0_tc(DmGeom g, const unsigned char* __restrict__ apack, const float* __res
     const uint32_t bar_acc_full = smem_u32(bars + 2 * F::STAGES), bar_acc_empty = smem_u32(bars + 2 * F::STAGES + 2);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // image-2 operand scale of the FP8 form (power of two from the field's maximum)
-    const float s_b = FMT == FMT_E4M3 ? e4m3_scale(__uint_as_float(*bmax)) : 1.0f;
     if (tid == 0) {
         for (int s = 0; s < F::STAGES; s++) {
             mbar_init(bar_full + 8 * s, 1);
@@ -411,14 +430,24 @@ k_corr0_tc(DmGeom g, const unsigned char* __restrict__ apack, const float* __res
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_holder;
 
-    const int W2 = g.W2, H2 = g.H2, mw = g.dw[1], mh = g.dh[1];
-    const int tiles_x = (mw + PX - 1) / PX, tiles_y = (mh + PY - 1) / PY;
-    const int mchunks = (n_mtiles + m_chunk - 1) / m_chunk;
-    const int n_units = tiles_x * tiles_y * mchunks;
     uint32_t a_it = 0, acc_it = 0;
     const bool store_leader = (warp == 2 && lane == 0);
 
-    for (int unit = blockIdx.x; unit < n_units; unit += gridDim.x) {
+    for (int gu = blockIdx.x; gu < B.total; gu += gridDim.x) {
+        int pj = 0;
+        while (pj + 1 < B.n && gu >= B.p[pj + 1].first) pj++;
+        const L0Pair& P = B.p[pj];
+        const unsigned char* __restrict__ apack = P.apack;
+        const float* __restrict__ inv_sa = P.inv_sa;
+        const float* __restrict__ d2 = P.d2;
+        int* __restrict__ err = P.err;
+        const int W2 = P.g.W2, H2 = P.g.H2, mw = P.g.dw[1];
+        const int tiles_x = (mw + PX - 1) / PX;
+        const int mchunks = (P.n_mtiles + P.m_chunk - 1) / P.m_chunk;
+        // image-2 operand scale of the FP8 form (power of two from the field's maximum)
+        const float s_b = FMT == FMT_E4M3 ? e4m3_scale(__uint_as_float(*P.bmax)) : 1.0f;
+        const int unit = gu - P.first;
+        const int m_chunk = P.m_chunk, n_mtiles = P.n_mtiles;
         const int ntile = unit / mchunks, mc = unit % mchunks;
         const int m0 = mc * m_chunk, m1 = min(n_mtiles, m0 + m_chunk), nt = m1 - m0;
         const int rx0 = (ntile % tiles_x) * PX, ry0 = (ntile / tiles_x) * PY;
@@ -518,10 +547,10 @@ k_corr0_tc(DmGeom g, const unsigned char* __restrict__ apack, const float* __res
                 if (store_leader) {
                     const int z = (m0 + j) * BM;
                     asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"
-                                 :: "l"(reinterpret_cast<uint64_t>(&tmap_f)), "r"(rx0), "r"(ry0), "r"(z), "r"(smem_u32(stf))
+                                 :: "l"(reinterpret_cast<uint64_t>(&P.tf)), "r"(rx0), "r"(ry0), "r"(z), "r"(smem_u32(stf))
                                  : "memory");
                     asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"
-                                 :: "l"(reinterpret_cast<uint64_t>(&tmap_c)), "r"(rx0), "r"(ry0), "r"(z), "r"(smem_u32(stc))
+                                 :: "l"(reinterpret_cast<uint64_t>(&P.tc)), "r"(rx0), "r"(ry0), "r"(z), "r"(smem_u32(stc))
                                  : "memory");
                     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
                 }
@@ -547,9 +576,7 @@ bool make_map(CUtensorMap* m, void* base, CUtensorMapDataType dt, int esize, con
 }
 
 template <int FMT>
-cudaError_t launch_tc(const DmGeom& g, const unsigned char* apack, const float* inv_sa, const unsigned int* bmax,
-                      const float* d2, float lam,
-                      const CUtensorMap& mf, const CUtensorMap& mc, int n_mtiles, int m_chunk, int* status, cudaStream_t st) {
+cudaError_t launch_tc(const L0Batch& B, float lam, cudaStream_t st) {
     using F = Fmt<FMT>;
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
@@ -557,10 +584,52 @@ cudaError_t launch_tc(const DmGeom& g, const unsigned char* apack, const float* 
     static std::atomic<unsigned long long> smem_done{0};
     cudaError_t ea = dm_smem_opt_in(reinterpret_cast<const void*>(k_corr0_tc<FMT>), (int)F::SMEM, smem_done);
     if (ea != cudaSuccess) return ea;
-    const int tiles = ((g.dw[1] + PX - 1) / PX) * ((g.dh[1] + PY - 1) / PY);
-    const int units = tiles * ((n_mtiles + m_chunk - 1) / m_chunk);
-    const int grid = units < nsm ? units : nsm;
-    k_corr0_tc<FMT><<<grid, THREADS, F::SMEM, st>>>(g, apack, inv_sa, bmax, d2, lam, mf, mc, n_mtiles, m_chunk, status);
+    if (B.total <= 0) return cudaSuccess;
+    const int grid = B.total < nsm ? B.total : nsm;
+    k_corr0_tc<FMT><<<grid, THREADS, F::SMEM, st>>>(B, lam);
+    return cudaGetLastError();
+}
+
+// One pair's entry of a level-0 launch, after its operand packing (launched
+// here on st): tensor maps of its outputs, pointers, work units.
+cudaError_t prepare_pair(const DmGeom& g, int precision, const float* d1, const float* d2, void* abuf, void* status,
+                         float* pooled0, unsigned char* amax0, int m_chunk, cudaStream_t st, const float* amat, int n_rows,
+                         L0Pair* q) {
+    memset(q, 0, sizeof(*q));
+    const int n0 = n_rows < 0 ? g.npatch(0) : n_rows;
+    const int n_mtiles = (n0 + BM - 1) / BM;
+    if (m_chunk < 1) m_chunk = 1;
+    // values: 64-byte box rows staged with the 64-byte swizzle (see pool_out)
+    if (!make_map(&q->tf, pooled0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, n0, CU_TENSOR_MAP_SWIZZLE_64B) ||
+        !make_map(&q->tc, amax0, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, g, n0, CU_TENSOR_MAP_SWIZZLE_NONE))
+        return cudaErrorNotSupported;
+    unsigned char* apack = reinterpret_cast<unsigned char*>(abuf);
+    q->g = g;
+    q->apack = apack;
+    q->d2 = d2;
+    q->err = reinterpret_cast<int*>(status);
+    q->n_mtiles = n_mtiles;
+    q->m_chunk = m_chunk;
+    q->units = ((g.dw[1] + PX - 1) / PX) * ((g.dh[1] + PY - 1) / PY) * ((n_mtiles + m_chunk - 1) / m_chunk);
+    cudaError_t e;
+    if (precision == DM_FP8_E4M3) {
+        const size_t a_bytes = dm_align((size_t)n_mtiles * Fmt<FMT_E4M3>::A_TILE);
+        float* inv_sa = reinterpret_cast<float*>(apack + a_bytes);
+        unsigned int* bmax = reinterpret_cast<unsigned int*>(apack + a_bytes + dm_align((size_t)n_mtiles * BM * sizeof(float)));
+        if ((e = cudaMemsetAsync(bmax, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
+        const long long n2 = (long long)g.W2 * g.H2 * 9;
+        const long long blocks = (n2 / 4 + 255) / 256;
+        k_absmax<<<(unsigned)(blocks < 1216 ? (blocks > 0 ? blocks : 1) : 1216), 256, 0, st>>>(d2, n2, bmax);
+        k_pack_a8<<<(unsigned)((n_mtiles * BM + 127) / 128), 128, 0, st>>>(g, d1, apack, inv_sa, n_mtiles, amat, n0);
+        q->inv_sa = inv_sa;
+        q->bmax = bmax;
+        dm_count_launches(2);
+    } else {
+        long long total = (long long)n_mtiles * BM * Fmt<FMT_BF16>::CHUNKS;
+        k_pack_a<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(g, d1, reinterpret_cast<__nv_bfloat16*>(apack), n_mtiles,
+                                                                   amat, n0);
+        dm_count_launches(1);
+    }
     return cudaGetLastError();
 }
 
@@ -599,33 +668,33 @@ size_t dm_corr0_tc_a_bytes(const DmGeom& g, int precision) {
 cudaError_t dm_launch_corr0_tc(const DmGeom& g, int precision, const float* d1, const float* d2, float lam, void* abuf,
                                void* status, float* pooled0, unsigned char* amax0, int m_chunk, cudaStream_t st,
                                const float* amat, int n_rows) {
-    const int n0 = n_rows < 0 ? g.npatch(0) : n_rows;
-    const int n_mtiles = (n0 + BM - 1) / BM;
-    if (m_chunk < 1) m_chunk = 1;
-    CUtensorMap mf, mc;
-    // values: 64-byte box rows staged with the 64-byte swizzle (see pool_out)
-    if (!make_map(&mf, pooled0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, n0, CU_TENSOR_MAP_SWIZZLE_64B) ||
-        !make_map(&mc, amax0, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, g, n0, CU_TENSOR_MAP_SWIZZLE_NONE))
-        return cudaErrorNotSupported;
-    unsigned char* apack = reinterpret_cast<unsigned char*>(abuf);
-    cudaError_t e;
-    if (precision == DM_FP8_E4M3) {
-        const size_t a_bytes = dm_align((size_t)n_mtiles * Fmt<FMT_E4M3>::A_TILE);
-        float* inv_sa = reinterpret_cast<float*>(apack + a_bytes);
-        unsigned int* bmax = reinterpret_cast<unsigned int*>(apack + a_bytes + dm_align((size_t)n_mtiles * BM * sizeof(float)));
-        if ((e = cudaMemsetAsync(bmax, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
-        const long long n2 = (long long)g.W2 * g.H2 * 9;
-        const long long blocks = (n2 / 4 + 255) / 256;
-        k_absmax<<<(unsigned)(blocks < 1216 ? (blocks > 0 ? blocks : 1) : 1216), 256, 0, st>>>(d2, n2, bmax);
-        k_pack_a8<<<(unsigned)((n_mtiles * BM + 127) / 128), 128, 0, st>>>(g, d1, apack, inv_sa, n_mtiles, amat, n0);
-        e = launch_tc<FMT_E4M3>(g, apack, inv_sa, bmax, d2, lam, mf, mc, n_mtiles, m_chunk, reinterpret_cast<int*>(status), st);
-        dm_count_launches(3);
-    } else {
-        long long total = (long long)n_mtiles * BM * Fmt<FMT_BF16>::CHUNKS;
-        k_pack_a<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(g, d1, reinterpret_cast<__nv_bfloat16*>(apack), n_mtiles,
-                                                                   amat, n0);
-        e = launch_tc<FMT_BF16>(g, apack, nullptr, nullptr, d2, lam, mf, mc, n_mtiles, m_chunk, reinterpret_cast<int*>(status), st);
-        dm_count_launches(2);
+    std::unique_ptr<L0Batch> B(new L0Batch);
+    memset(B.get(), 0, sizeof(L0Batch));
+    cudaError_t e = prepare_pair(g, precision, d1, d2, abuf, status, pooled0, amax0, m_chunk, st, amat, n_rows, &B->p[0]);
+    if (e != cudaSuccess) return e;
+    B->n = 1;
+    B->total = B->p[0].units;
+    e = precision == DM_FP8_E4M3 ? launch_tc<FMT_E4M3>(*B, lam, st) : launch_tc<FMT_BF16>(*B, lam, st);
+    dm_count_launches(1);
+    return e;
+}
+
+cudaError_t dm_launch_corr0_tc_batch(int n, const DmGeom* gs, int precision, const float* const* d1s,
+                                     const float* const* d2s, float lam, void* const* abufs, void* const* statuses,
+                                     float* const* pooled0s, unsigned char* const* amax0s, const int* m_chunks,
+                                     cudaStream_t st) {
+    if (n < 1 || n > DM_BATCH_MAX) return cudaErrorInvalidValue;
+    std::unique_ptr<L0Batch> B(new L0Batch);
+    memset(B.get(), 0, sizeof(L0Batch));
+    for (int j = 0; j < n; j++) {
+        cudaError_t e = prepare_pair(gs[j], precision, d1s[j], d2s[j], abufs[j], statuses[j], pooled0s[j], amax0s[j],
+                                     m_chunks[j], st, nullptr, -1, &B->p[j]);
+        if (e != cudaSuccess) return e;
+        B->p[j].first = B->total;
+        B->total += B->p[j].units;
     }
+    B->n = n;
+    cudaError_t e = precision == DM_FP8_E4M3 ? launch_tc<FMT_E4M3>(*B, lam, st) : launch_tc<FMT_BF16>(*B, lam, st);
+    dm_count_launches(1);
     return e;
 }

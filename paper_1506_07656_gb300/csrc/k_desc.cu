@@ -10,6 +10,9 @@
 // so the FP32 result is reproducible bit for bit.
 #include "dm_internal.cuh"
 
+#include <algorithm>
+#include <cstring>
+
 namespace {
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -17,9 +20,8 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? l
 // Horizontal pass of one channel plane set.  in: [H][W][C] (C = 1 or 8);
 // scale applied to the input value first when `scale_in` != 1 (first pass).
 template <int C>
-__global__ void k_smooth_h(const float* __restrict__ in, float* __restrict__ out, int W, int H, DmTaps t,
-                           float scale_in, int apply_scale) {
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void smooth_h(const float* __restrict__ in, float* __restrict__ out, int W, int H,
+                                         const DmTaps& t, float scale_in, int apply_scale, long long idx) {
     long long n = (long long)W * H * C;
     if (idx >= n) return;
     int c = (int)(idx % C);
@@ -37,11 +39,11 @@ __global__ void k_smooth_h(const float* __restrict__ in, float* __restrict__ out
 
 // Vertical pass; post = 0 none, 1 sigmoid, 2 normalise into [H][W][9] output.
 template <int C, int POST>
-__global__ void k_smooth_v(const float* __restrict__ in, float* __restrict__ out, int W, int H, DmTaps t,
-                           float slope, float mu) {
+__device__ __forceinline__ void smooth_v(const float* __restrict__ in, float* __restrict__ out, int W, int H,
+                                         const DmTaps& t, float slope, float mu, long long gidx) {
     if (POST == 2) {
         // one thread per pixel: smooth its C channels, then normalise
-        long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        long long pix = gidx;
         if (pix >= (long long)W * H) return;
         int x = (int)(pix % W), y = (int)(pix / W);
         float v[C];
@@ -63,7 +65,7 @@ __global__ void k_smooth_v(const float* __restrict__ in, float* __restrict__ out
         o[8] = __fdiv_rn(mu, nrm);
         return;
     }
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long idx = gidx;
     long long n = (long long)W * H * C;
     if (idx >= n) return;
     int c = (int)(idx % C);
@@ -100,8 +102,7 @@ __global__ void k_scale(const float* __restrict__ in, float* __restrict__ out, l
 // Gradient + 8 non-negative projections.  dir_k = (cos k pi/4, sin k pi/4)
 // with the exact table {1, r, 0, -r, -1, -r, 0, r} / {0, r, 1, r, 0, -r, -1, -r},
 // r = sqrt(1/2) rounded to float; v_k = fma(gx, cos_k, gy * sin_k), then max(v, 0).
-__global__ void k_grad_proj(const float* __restrict__ s, float* __restrict__ o8, int W, int H) {
-    long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void grad_proj(const float* __restrict__ s, float* __restrict__ o8, int W, int H, long long pix) {
     if (pix >= (long long)W * H) return;
     int x = (int)(pix % W), y = (int)(pix / W);
     float gx = __fmul_rn(__fsub_rn(s[(long long)y * W + clampi(x + 1, 0, W - 1)], s[(long long)y * W + clampi(x - 1, 0, W - 1)]), 0.5f);
@@ -115,6 +116,43 @@ __global__ void k_grad_proj(const float* __restrict__ s, float* __restrict__ o8,
         float v = __fmaf_rn(gx, dc[k], __fmul_rn(gy, ds[k]));
         o[k] = v > 0.0f ? v : 0.0f;
     }
+}
+
+__device__ __forceinline__ long long gtid() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
+
+template <int C>
+__global__ void k_smooth_h(const float* __restrict__ in, float* __restrict__ out, int W, int H, DmTaps t, float scale_in,
+                           int apply_scale) {
+    smooth_h<C>(in, out, W, H, t, scale_in, apply_scale, gtid());
+}
+template <int C, int POST>
+__global__ void k_smooth_v(const float* __restrict__ in, float* __restrict__ out, int W, int H, DmTaps t, float slope,
+                           float mu) {
+    smooth_v<C, POST>(in, out, W, H, t, slope, mu, gtid());
+}
+__global__ void k_grad_proj(const float* __restrict__ s, float* __restrict__ o8, int W, int H) { grad_proj(s, o8, W, H, gtid()); }
+
+// Cross-pair form: the same passes for every image of a wave of the batched
+// form in one launch each, image blockIdx.y (its buffers in the parameters).
+struct IoBatch {
+    const float* in[2 * DM_BATCH_MAX];
+    float* out[2 * DM_BATCH_MAX];
+    int W[2 * DM_BATCH_MAX], H[2 * DM_BATCH_MAX];
+    int n;
+};
+template <int C>
+__global__ void k_smooth_h_b(const __grid_constant__ IoBatch B, DmTaps t, float scale_in, int apply_scale) {
+    const int i = blockIdx.y;
+    smooth_h<C>(B.in[i], B.out[i], B.W[i], B.H[i], t, scale_in, apply_scale, gtid());
+}
+template <int C, int POST>
+__global__ void k_smooth_v_b(const __grid_constant__ IoBatch B, DmTaps t, float slope, float mu) {
+    const int i = blockIdx.y;
+    smooth_v<C, POST>(B.in[i], B.out[i], B.W[i], B.H[i], t, slope, mu, gtid());
+}
+__global__ void k_grad_proj_b(const __grid_constant__ IoBatch B) {
+    const int i = blockIdx.y;
+    grad_proj(B.in[i], B.out[i], B.W[i], B.H[i], gtid());
 }
 
 inline unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -170,5 +208,54 @@ cudaError_t dm_launch_smooth1(const float* img, int W, int H, float scale, const
         k_scale<<<nblk(n1, B), B, 0, st>>>(img, out, n1, scale);
         dm_count_launches(1);
     }
+    return cudaGetLastError();
+}
+
+// Descriptors of n <= 2 DM_BATCH_MAX images (a wave of the batched form): one
+// launch per pass for all of them.  (With a zero smoothing width the scaling
+// and sigmoid passes run image by image.)
+cudaError_t dm_launch_descriptors_batch(const DmDescParams& prm, int n, const float* const* imgs, const int* Ws,
+                                        const int* Hs, float* const* descs, float* const* tmpAs, float* const* tmpBs,
+                                        cudaStream_t st) {
+    if (n < 1 || n > 2 * DM_BATCH_MAX) return cudaErrorInvalidValue;
+    if (prm.t1.R == 0 || prm.t2.R == 0 || prm.t3.R == 0) {
+        for (int i = 0; i < n; i++) {
+            cudaError_t e = dm_launch_descriptors(prm, imgs[i], Ws[i], Hs[i], descs[i], tmpAs[i], tmpBs[i], st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    const int B = 256;
+    long long n1 = 0;
+    for (int i = 0; i < n; i++) n1 = std::max(n1, (long long)Ws[i] * Hs[i]);
+    const long long n8 = 8 * n1;
+    auto io = [&](int step) {
+        IoBatch b;
+        memset(&b, 0, sizeof(b));
+        b.n = n;
+        for (int i = 0; i < n; i++) {
+            b.W[i] = Ws[i];
+            b.H[i] = Hs[i];
+            switch (step) {
+                case 0: b.in[i] = imgs[i]; b.out[i] = tmpAs[i]; break;     // nu1, horizontal
+                case 1: b.in[i] = tmpAs[i]; b.out[i] = tmpBs[i]; break;    // nu1, vertical
+                case 2: b.in[i] = tmpBs[i]; b.out[i] = tmpAs[i]; break;    // gradient projections
+                case 3: b.in[i] = tmpAs[i]; b.out[i] = tmpBs[i]; break;    // nu2, horizontal
+                case 4: b.in[i] = tmpBs[i]; b.out[i] = tmpAs[i]; break;    // nu2, vertical + sigmoid
+                case 5: b.in[i] = tmpAs[i]; b.out[i] = tmpBs[i]; break;    // nu3, horizontal
+                default: b.in[i] = tmpBs[i]; b.out[i] = descs[i]; break;   // nu3, vertical + normalisation
+            }
+        }
+        return b;
+    };
+    const dim3 g1(nblk(n1, B), (unsigned)n), g8(nblk(n8, B), (unsigned)n);
+    k_smooth_h_b<1><<<g1, B, 0, st>>>(io(0), prm.t1, prm.scale, 1);
+    k_smooth_v_b<1, 0><<<g1, B, 0, st>>>(io(1), prm.t1, 0.f, 0.f);
+    k_grad_proj_b<<<g1, B, 0, st>>>(io(2));
+    k_smooth_h_b<8><<<g8, B, 0, st>>>(io(3), prm.t2, 1.f, 0);
+    k_smooth_v_b<8, 1><<<g8, B, 0, st>>>(io(4), prm.t2, prm.slope, 0.f);
+    k_smooth_h_b<8><<<g8, B, 0, st>>>(io(5), prm.t3, 1.f, 0);
+    k_smooth_v_b<8, 2><<<g1, B, 0, st>>>(io(6), prm.t3, 0.f, prm.mu);
+    dm_count_launches(7);
     return cudaGetLastError();
 }

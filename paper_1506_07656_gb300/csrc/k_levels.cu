@@ -152,13 +152,12 @@ __device__ __forceinline__ int child_at(const DmGeom& g, int l, int cx, int cy, 
 // from its two columns, release the left column (thread 0 starts the loads of
 // the column NR ahead into it), pool, power, store, wait for the next patch's
 // columns; two barriers per patch.
-template <bool COMP, int TH, int NR, bool APPROX = false>
-__global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, const __grid_constant__ CUtensorMap tmap,
-                                                               const unsigned char* __restrict__ vprev,
-                                                               int runs_per_res, int run, float* __restrict__ out,
-                                                               unsigned char* __restrict__ amax, float lam,
-                                                               int* __restrict__ err, const int* __restrict__ proto_of,
-                                                               int n_maps, long long inject_wait) {
+template <bool COMP, int TH, int NR, bool APPROX>
+__device__ __forceinline__ void level_sweep_body(const DmGeom& g, int l, const CUtensorMap* tmap_p,
+                                                 const unsigned char* __restrict__ vprev, int runs_per_res, int run,
+                                                 float* __restrict__ out, unsigned char* __restrict__ amax, float lam,
+                                                 int* __restrict__ err, const int* __restrict__ proto_of, int n_maps,
+                                                 long long inject_wait, int item) {
     using T = LevelTile<TH>;
     constexpr int AH = T::AH, KIDF = T::KIDF;
     constexpr int AGPT = (AH * AG + LEVEL_THREADS - 1) / LEVEL_THREADS;   // average groups per thread
@@ -183,7 +182,6 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
     // from DRAM once (at 512x224, level 1: 1.03x the maps read instead of 1.83x
     // with the tile as the slowest index)
     const int ntiles = tiles_x * ((oh + TH - 1) / TH);
-    const int item = blockIdx.x;
     const int rr = item % per_row;
     const int t1 = item / per_row;
     const int tile = t1 % ntiles;
@@ -221,10 +219,10 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
             if (cb >= 0) zb = min(max(__ldg(proto_of + cb), 0), n_maps - 1);
         }
         asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-                     :: "r"(dst), "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(xa), "r"(qy0 - 1), "r"(zt), "r"(bar)
+                     :: "r"(dst), "l"(reinterpret_cast<uint64_t>(tmap_p)), "r"(xa), "r"(qy0 - 1), "r"(zt), "r"(bar)
                      : "memory");
         asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-                     :: "r"(dst + KIDF * 4), "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(xa), "r"(qy0 + 1), "r"(zb), "r"(bar)
+                     :: "r"(dst + KIDF * 4), "l"(reinterpret_cast<uint64_t>(tmap_p)), "r"(xa), "r"(qy0 + 1), "r"(zb), "r"(bar)
                      : "memory");
     };
     // wait for column j (the (j / NR)-th use of its slot); false on timeout
@@ -363,6 +361,17 @@ __global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, 
     }
 }
 
+template <bool COMP, int TH, int NR, bool APPROX = false>
+__global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, const __grid_constant__ CUtensorMap tmap,
+                                                               const unsigned char* __restrict__ vprev,
+                                                               int runs_per_res, int run, float* __restrict__ out,
+                                                               unsigned char* __restrict__ amax, float lam,
+                                                               int* __restrict__ err, const int* __restrict__ proto_of,
+                                                               int n_maps, long long inject_wait) {
+    level_sweep_body<COMP, TH, NR, APPROX>(g, l, &tmap, vprev, runs_per_res, run, out, amax, lam, err, proto_of, n_maps,
+                                           inject_wait, (int)blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // Row-streaming form of the same pass (level_th = 0 in the tuned shapes).
 //
@@ -487,19 +496,17 @@ __device__ __forceinline__ void stream_step(const StreamWarp& w, int ry, int oh,
     }
 }
 
-template <bool COMP, bool APPROX = false>
-__global__ void __launch_bounds__(STREAM_WARPS * 32, 4) k_level_stream(DmGeom g, int l, const float* __restrict__ prev,
-                                                                   const unsigned char* __restrict__ vprev,
-                                                                   const unsigned char* __restrict__ vcur,
-                                                                   int bx_per_res, int by_per_res, float* __restrict__ out,
-                                                                   unsigned char* __restrict__ amax, float lam,
-                                                                   const int* __restrict__ proto_of, int n_maps) {
+template <bool COMP, bool APPROX>
+__device__ __forceinline__ void level_stream_body(const DmGeom& g, int l, const float* __restrict__ prev,
+                                                  const unsigned char* __restrict__ vprev,
+                                                  const unsigned char* __restrict__ vcur, int bx_per_res, int by_per_res,
+                                                  float* __restrict__ out, unsigned char* __restrict__ amax, float lam,
+                                                  const int* __restrict__ proto_of, int n_maps, long long item) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int cx0, cy0, S;
     child_col_row(g, l, 0, 0, &cx0, &cy0, &S);
     // block = (((strip * S + res_y) * by_per_res + by) * S + res_x) * bx_per_res + bx: a block holds
     // patches (res_x + (bx * 4 + wx) S, res_y + (by * 2 + wy) S), wx < 4, wy < 2
-    long long item = blockIdx.x;
     const int bx = (int)(item % bx_per_res);
     item /= bx_per_res;
     const int res_x = (int)(item % S);
@@ -556,6 +563,17 @@ __global__ void __launch_bounds__(STREAM_WARPS * 32, 4) k_level_stream(DmGeom g,
     for (; ry < oh; ry += 2) stream_step<COMP, true>(w, ry, oh, hp, cp, lam, store, orow, arow, opitch);
 }
 
+template <bool COMP, bool APPROX = false>
+__global__ void __launch_bounds__(STREAM_WARPS * 32, 4) k_level_stream(DmGeom g, int l, const float* __restrict__ prev,
+                                                                   const unsigned char* __restrict__ vprev,
+                                                                   const unsigned char* __restrict__ vcur,
+                                                                   int bx_per_res, int by_per_res, float* __restrict__ out,
+                                                                   unsigned char* __restrict__ amax, float lam,
+                                                                   const int* __restrict__ proto_of, int n_maps) {
+    level_stream_body<COMP, APPROX>(g, l, prev, vprev, vcur, bx_per_res, by_per_res, out, amax, lam, proto_of, n_maps,
+                                    (long long)blockIdx.x);
+}
+
 // Top level L: C_L = (mean of children)^lambda over the domain of level L.
 template <bool COMP>
 __global__ void k_level_top(DmGeom g, int l, const unsigned char* __restrict__ vprev,
@@ -602,6 +620,84 @@ cudaError_t launch_stream(const DmGeom& g, int l, const dm_pyramid& py, float la
         g, l, py.pooled[l - 1], py.valid[l - 1], py.valid[l], bx_per_res, by_per_res, const_cast<float*>(py.pooled[l]),
         const_cast<unsigned char*>(py.amax[l]), lam, APPROX ? py.proto_of : nullptr, py.n0_maps);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Cross-pair form: one launch per step of the pass for every pair of a wave
+// of the batched form (dm_launch_levels_batch).  The per-pair arguments travel
+// in the kernel parameters (a captured graph replays them as they were), and
+// block b of a launch belongs to the pair j with first[j] <= b < first[j+1]
+// (tiled and row-streaming kernels) or to pair blockIdx.y / blockIdx.z.
+// ---------------------------------------------------------------------------
+struct LvPair {
+    CUtensorMap tmap;          // tiled kernel: the pooled maps of level l-1
+    DmGeom g;
+    const unsigned char* vprev;
+    unsigned char* vcur;
+    const float* prev;         // pooled maps of level l-1
+    float* out;                // pooled maps of level l (or the top)
+    unsigned char* amax;
+    int* err;
+    int a, b;                  // tiled: runs per residue; row-streaming: blocks per residue in x, y
+    long long first;           // first block of this pair in the launch
+};
+struct LvBatch {
+    LvPair p[DM_BATCH_MAX];
+    int n;
+};
+
+__device__ __forceinline__ int lv_pair_of(const LvBatch& B, long long blk) {
+    int j = 0;
+    while (j + 1 < B.n && blk >= B.p[j + 1].first) j++;
+    return j;
+}
+
+template <bool COMP, int TH, int NR>
+__global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep_b(const __grid_constant__ LvBatch B, int l, float lam) {
+    const int j = lv_pair_of(B, blockIdx.x);
+    const LvPair& P = B.p[j];
+    level_sweep_body<COMP, TH, NR, false>(P.g, l, &P.tmap, P.vprev, P.a, level_run(l), P.out, P.amax, lam, P.err, nullptr,
+                                          0, 0, (int)((long long)blockIdx.x - P.first));
+}
+
+template <bool COMP>
+__global__ void __launch_bounds__(STREAM_WARPS * 32, 4) k_level_stream_b(const __grid_constant__ LvBatch B, int l, float lam) {
+    const int j = lv_pair_of(B, blockIdx.x);
+    const LvPair& P = B.p[j];
+    level_stream_body<COMP, false>(P.g, l, P.prev, P.vprev, P.vcur, P.a, P.b, P.out, P.amax, lam, nullptr, 0,
+                                   (long long)blockIdx.x - P.first);
+}
+
+__global__ void k_valid_b(const __grid_constant__ LvBatch B, int l) {
+    const LvPair& P = B.p[blockIdx.y];
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l == 0) {
+        if (p < P.g.npatch(0)) P.vcur[p] = 1;
+        return;
+    }
+    if (p >= P.g.Lx * P.g.Ly) return;
+    const int ix = p % P.g.Lx, iy = p / P.g.Lx;
+    unsigned char any = 0;
+    for (int i = 0; i < 4; i++) {
+        const int c = dm_child(P.g, l, ix, iy, i);
+        if (c >= 0 && P.vprev[c]) any = 1;
+    }
+    P.vcur[p] = any;
+}
+
+template <bool COMP>
+__global__ void k_level_top_b(const __grid_constant__ LvBatch B, int l, float lam) {
+    const LvPair& P = B.p[blockIdx.z];
+    const DmGeom& g = P.g;
+    const int p = blockIdx.y;
+    if (p >= g.npatch(l) || !P.vcur[p]) return;
+    const int mw = g.dw[l], mh = g.dh[l];
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= mw * mh) return;
+    Kids k;
+    load_kids(g, l, p, P.vprev, P.prev, k, nullptr, g.npatch(0));
+    const float a = child_mean<COMP>(k, q % mw, q / mw, mw, mh, g.pitch(l));
+    P.out[(long long)p * mw * mh + q] = dm_powf(a, lam);
 }
 
 }  // namespace
@@ -667,5 +763,129 @@ cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& py, float lam, i
         }
     }
     dm_count_launches(1 + 2 * g.L);
+    return cudaGetLastError();
+}
+
+// Levels >= 1 of the n <= DM_BATCH_MAX pyramids of a wave (level 0 computed):
+// per level, one launch of the existence flags and one launch per kernel shape
+// in use (tiled with each tuned (rows, ring), row-streaming, top) for all the
+// pairs at that level; status[j] receives pair j's bounded-wait flag.
+cudaError_t dm_launch_levels_batch(const dm_pyramid* const* pys, int n, float lam, int* const* status, cudaStream_t st) {
+    if (n < 1 || n > DM_BATCH_MAX) return cudaErrorInvalidValue;
+    const bool comp = pys[0]->compensated != 0;
+    int Lmax = 0;
+    for (int j = 0; j < n; j++) Lmax = max(Lmax, pys[j]->g.L);
+    long long launches = 0;
+    auto base_pair = [&](int j, int l) {
+        const dm_pyramid& py = *pys[j];
+        LvPair q;
+        memset(&q, 0, sizeof(q));
+        q.g = py.g;
+        q.vprev = l >= 1 ? py.valid[l - 1] : nullptr;
+        q.vcur = const_cast<unsigned char*>(py.valid[l]);
+        q.prev = l >= 1 ? py.pooled[l - 1] : nullptr;
+        q.out = l < py.g.L ? const_cast<float*>(py.pooled[l]) : const_cast<float*>(py.top);
+        q.amax = l < py.g.L ? const_cast<unsigned char*>(py.amax[l]) : nullptr;
+        q.err = status[j];
+        return q;
+    };
+    for (int l = 0; l <= Lmax; l++) {
+        // existence flags of level l (level 0: every atomic patch)
+        {
+            LvBatch B;
+            memset(&B, 0, sizeof(B));
+            int maxp = 0;
+            for (int j = 0; j < n; j++)
+                if (l <= pys[j]->g.L) {
+                    B.p[B.n++] = base_pair(j, l);
+                    maxp = max(maxp, pys[j]->g.npatch(l));
+                }
+            if (B.n == 0) break;
+            k_valid_b<<<dim3((unsigned)((maxp + 255) / 256), (unsigned)B.n), 256, 0, st>>>(B, l);
+            launches++;
+        }
+        if (l == 0) continue;
+        // the pairs whose level l is the top
+        {
+            LvBatch B;
+            memset(&B, 0, sizeof(B));
+            int maxq = 0, maxp = 0;
+            for (int j = 0; j < n; j++)
+                if (l == pys[j]->g.L) {
+                    B.p[B.n++] = base_pair(j, l);
+                    maxq = max(maxq, pys[j]->g.dw[l] * pys[j]->g.dh[l]);
+                    maxp = max(maxp, pys[j]->g.npatch(l));
+                }
+            if (B.n) {
+                const dim3 grid((unsigned)((maxq + 127) / 128), (unsigned)maxp, (unsigned)B.n);
+                if (comp) k_level_top_b<true><<<grid, 128, 0, st>>>(B, l, lam);
+                else k_level_top_b<false><<<grid, 128, 0, st>>>(B, l, lam);
+                launches++;
+            }
+        }
+        // the pairs below their top: one launch per kernel shape in use.
+        // shape 0: row-streaming; 1 + (rows == 8) + 2 (ring == 3): tiled
+        for (int shape = 0; shape < 5; shape++) {
+            LvBatch B;
+            memset(&B, 0, sizeof(B));
+            long long blocks = 0;
+            for (int j = 0; j < n; j++) {
+                const dm_pyramid& py = *pys[j];
+                const DmGeom& g = py.g;
+                if (l >= g.L) continue;
+                const bool stream = py.tune.level_th == 0 || g.dw[l + 1] <= 16;
+                const int th = py.tune.level_th == 8 ? 8 : 16, nr = py.tune.level_ring == 3 ? 3 : 2;
+                const int my = stream ? 0 : 1 + (th == 8) + 2 * (nr == 3);
+                if (my != shape) continue;
+                LvPair q = base_pair(j, l);
+                const int S = l == 1 ? 1 : 1 << (l - 1);
+                long long items;
+                if (stream) {
+                    q.a = ((g.Lx + S - 1) / S + STREAM_BX - 1) / STREAM_BX;
+                    q.b = ((g.Ly + S - 1) / S + STREAM_BY - 1) / STREAM_BY;
+                    const int strips = (g.dw[l + 1] + STREAM_W - 1) / STREAM_W;
+                    items = (long long)strips * S * q.b * S * q.a;
+                } else {
+                    const cuuint64_t dims[3] = {(cuuint64_t)g.dw[l], (cuuint64_t)g.dh[l], (cuuint64_t)g.npatch(l - 1)};
+                    const cuuint64_t strides[2] = {(cuuint64_t)g.pitch(l) * 4, (cuuint64_t)g.psize(l) * 4};
+                    const cuuint32_t box[3] = {KW, (cuuint32_t)(2 * th + 1), 1};
+                    if (!dm_encode_tiled(&q.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(py.pooled[l - 1]),
+                                         dims, strides, box))
+                        return cudaErrorNotSupported;
+                    const int tiles = ((g.dw[l + 1] + TW - 1) / TW) * ((g.dh[l + 1] + th - 1) / th);
+                    const int run = level_run(l);
+                    q.a = ((g.Lx + S - 1) / S + run - 1) / run;
+                    items = (long long)tiles * g.Ly * S * q.a;
+                }
+                q.first = blocks;
+                blocks += items;
+                B.p[B.n++] = q;
+            }
+            if (B.n == 0 || blocks == 0) continue;
+            if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+            cudaError_t e = cudaSuccess;
+            if (shape == 0) {
+                if (comp) k_level_stream_b<true><<<(unsigned)blocks, STREAM_WARPS * 32, 0, st>>>(B, l, lam);
+                else k_level_stream_b<false><<<(unsigned)blocks, STREAM_WARPS * 32, 0, st>>>(B, l, lam);
+            } else {
+                auto launch = [&](auto kern, int TH, int NR) -> cudaError_t {
+                    const int kidf = (((2 * TH + 1) * KW + 31) / 32) * 32;     // LevelTile<TH>::KIDF
+                    const size_t smem = (size_t)(NR * 2 * kidf + (2 * TH + 1) * AWP) * sizeof(float) + 128;
+                    static std::atomic<unsigned long long> done[4];
+                    cudaError_t ea = dm_smem_opt_in(reinterpret_cast<const void*>(kern), (int)smem, done[shape - 1]);
+                    if (ea != cudaSuccess) return ea;
+                    kern<<<(unsigned)blocks, LEVEL_THREADS, smem, st>>>(B, l, lam);
+                    return cudaSuccess;
+                };
+                if (shape == 1) e = comp ? launch(k_level_sweep_b<true, 16, 2>, 16, 2) : launch(k_level_sweep_b<false, 16, 2>, 16, 2);
+                else if (shape == 2) e = comp ? launch(k_level_sweep_b<true, 8, 2>, 8, 2) : launch(k_level_sweep_b<false, 8, 2>, 8, 2);
+                else if (shape == 3) e = comp ? launch(k_level_sweep_b<true, 16, 3>, 16, 3) : launch(k_level_sweep_b<false, 16, 3>, 16, 3);
+                else e = comp ? launch(k_level_sweep_b<true, 8, 3>, 8, 3) : launch(k_level_sweep_b<false, 8, 3>, 8, 3);
+            }
+            if (e != cudaSuccess) return e;
+            launches++;
+        }
+    }
+    dm_count_launches(launches);
     return cudaGetLastError();
 }

@@ -84,6 +84,9 @@ _SIGS = {
     "dm_match_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "dm_set_batch_lanes": (C.c_int, [C.c_void_p, C.c_int]),
     "dm_set_merge_keys": (C.c_int, [C.c_void_p, C.c_int]),
+    "dm_set_batch_wave": (C.c_int, [C.c_void_p, C.c_int]),
+    "dm_autotune_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_int),
+                                    C.c_void_p]),
     "dm_batch_host_workspace_bytes": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_size_t)]),
     "dm_match_batch_host": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "dm_backtrack_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
@@ -469,6 +472,19 @@ def dm_match_batch_host(ctx, pairs, d_ws, stream=None):
 
 def dm_set_batch_lanes(ctx, lanes: int) -> None:
     _check(ctx, load().dm_set_batch_lanes(ctx, int(lanes)), "dm_set_batch_lanes")
+
+
+def dm_set_batch_wave(ctx, pairs: int) -> None:
+    """Pairs per cross-pair wave of the batched form (1: each pair its own launches)."""
+    _check(ctx, load().dm_set_batch_wave(ctx, int(pairs)), "dm_set_batch_wave")
+
+
+def dm_autotune_batch(ctx, pairs, d_ws, stream=None) -> dict:
+    """Pick the batch shape (wave width, lanes) for these pairs within d_ws; returns it."""
+    ch = (C.c_int * 2)()
+    _check(ctx, load().dm_autotune_batch(ctx, len(pairs), pairs, _dptr(d_ws), d_ws.numel() * d_ws.element_size(), ch,
+                                         _stream_ptr(stream)), "dm_autotune_batch")
+    return {"wave": ch[0], "lanes": ch[1]}
 
 
 def dm_set_merge_keys(ctx, bits: int) -> None:
