@@ -60,7 +60,6 @@ constexpr int AW = 2 * TW + 1;                   // average columns per CTA (65)
 constexpr int KW = 72;                           // staged child columns (TMA box width)
 constexpr int AWP = 68;                          // padded row of the averages (16-byte aligned rows)
 constexpr int LEVEL_THREADS = 256;
-constexpr int AG = AWP / 4;                      // groups of 4 averages per row (17)
 
 // CTA tile of TW x TH pooled outputs (TH = 8 or 16, chosen by the autotuner):
 // AH rows of averages, child windows of KW x AH floats (KIDF with padding to
@@ -86,35 +85,54 @@ constexpr long long LEVEL_WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 // additions, every step correctly rounded per lane) costs 3 instructions per
 // column and step.
 template <bool COMP, bool DIV3>
+__device__ __forceinline__ float2 avg_pair4(float2 x0, float2 x1, float2 x2, float2 x3, float w) {
+    float2 sv = x0;
+    if constexpr (COMP) {
+        float2 cp, err;
+        // first step: the compensation starts as its error term (0 + err = err;
+        // a -0 there would only meet s + (+-0) = s at the end)
+        dm_two_sum2(sv, x1, cp);
+        dm_two_sum2(sv, x2, err);
+        cp = __fadd2_rn(cp, err);
+        dm_two_sum2(sv, x3, err);
+        cp = __fadd2_rn(cp, err);
+        sv = __fadd2_rn(sv, cp);
+    } else {
+        sv = __fadd2_rn(__fadd2_rn(__fadd2_rn(sv, x1), x2), x3);
+    }
+    return DIV3 ? make_float2(__fdiv_rn(sv.x, 3.0f), __fdiv_rn(sv.y, 3.0f)) : __fmul2_rn(sv, make_float2(w, w));
+}
+
+template <bool COMP, bool DIV3>
 __device__ __forceinline__ float4 avg_group(const float* lt, const float* lb, const float* rt, const float* rb, float w) {
     const float4 a0 = *reinterpret_cast<const float4*>(lt), b0 = *reinterpret_cast<const float4*>(lt + 4);
     const float4 a1 = *reinterpret_cast<const float4*>(lb), b1 = *reinterpret_cast<const float4*>(lb + 4);
     const float4 v2 = *reinterpret_cast<const float4*>(rt + 4);
     const float4 v3 = *reinterpret_cast<const float4*>(rb + 4);
-    const float2 x[2][4] = {{make_float2(a0.z, a0.w), make_float2(a1.z, a1.w), make_float2(v2.x, v2.y), make_float2(v3.x, v3.y)},
-                            {make_float2(b0.x, b0.y), make_float2(b1.x, b1.y), make_float2(v2.z, v2.w), make_float2(v3.z, v3.w)}};
-    float2 r[2];
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-        float2 sv = x[h][0];
-        if constexpr (COMP) {
-            float2 cp;
-#pragma unroll
-            for (int i = 1; i < 4; i++) {
-                float2 err;
-                dm_two_sum2(sv, x[h][i], err);
-                // first step: the compensation starts as its error term (0 + err = err;
-                // a -0 there would only meet s + (+-0) = s at the end)
-                cp = i == 1 ? err : __fadd2_rn(cp, err);
-            }
-            sv = __fadd2_rn(sv, cp);
-        } else {
-#pragma unroll
-            for (int i = 1; i < 4; i++) sv = __fadd2_rn(sv, x[h][i]);
-        }
-        r[h] = DIV3 ? make_float2(__fdiv_rn(sv.x, 3.0f), __fdiv_rn(sv.y, 3.0f)) : __fmul2_rn(sv, make_float2(w, w));
+    const float2 r0 = avg_pair4<COMP, DIV3>(make_float2(a0.z, a0.w), make_float2(a1.z, a1.w), make_float2(v2.x, v2.y),
+                                            make_float2(v3.x, v3.y), w);
+    const float2 r1 = avg_pair4<COMP, DIV3>(make_float2(b0.x, b0.y), make_float2(b1.x, b1.y), make_float2(v2.z, v2.w),
+                                            make_float2(v3.z, v3.w), w);
+    return make_float4(r0.x, r0.y, r1.x, r1.y);
+}
+
+// The same for two columns c, c+1 (c even: 8-byte loads at columns c+2 and
+// c+4), or -- ONE -- for column c alone (the second lane's result unused).
+template <bool COMP, bool DIV3, bool ONE>
+__device__ __forceinline__ float2 avg_two(const float* lt, const float* lb, const float* rt, const float* rb, float w) {
+    float2 x[4];
+    if constexpr (ONE) {
+        x[0] = make_float2(lt[2], 0.0f);
+        x[1] = make_float2(lb[2], 0.0f);
+        x[2] = make_float2(rt[4], 0.0f);
+        x[3] = make_float2(rb[4], 0.0f);
+    } else {
+        x[0] = *reinterpret_cast<const float2*>(lt + 2);
+        x[1] = *reinterpret_cast<const float2*>(lb + 2);
+        x[2] = *reinterpret_cast<const float2*>(rt + 4);
+        x[3] = *reinterpret_cast<const float2*>(rb + 4);
     }
-    return make_float4(r[0].x, r[0].y, r[1].x, r[1].y);
+    return avg_pair4<COMP, DIV3>(x[0], x[1], x[2], x[3], w);
 }
 
 // Sweep geometry of level l: a CTA owns one tile of TW x TH pooled outputs of a
@@ -160,7 +178,6 @@ __device__ __forceinline__ void level_sweep_body(const DmGeom& g, int l, const C
                                                  long long inject_wait, int item) {
     using T = LevelTile<TH>;
     constexpr int AH = T::AH, KIDF = T::KIDF;
-    constexpr int AGPT = (AH * AG + LEVEL_THREADS - 1) / LEVEL_THREADS;   // average groups per thread
     extern __shared__ __align__(128) unsigned char lsm_raw[];
     // TMA destinations must be 128-byte aligned: round the dynamic base up (128 bytes are reserved for this)
     float* lsm = reinterpret_cast<float*>(lsm_raw + ((128u - ((uint32_t)__cvta_generic_to_shared(lsm_raw) & 127u)) & 127u));
@@ -278,30 +295,53 @@ __device__ __forceinline__ void level_sweep_body(const DmGeom& g, int l, const C
         const int ix = ix0 + k * S;
         const int p = iy * g.Lx + ix;
         if (n > 0) {
-            // averages of the tile: 17 groups of 4 columns per row (columns 0 .. 67;
-            // the pooling reads 0 .. 64), group e = tid + 256 u
+            // averages of the tile: rows 0 .. 2 TH - 1 in 16 groups of 4 columns
+            // (columns 0 .. 63), TH / 8 groups per thread; then the last row's 32
+            // column pairs and column 64 of every row, one item each for threads
+            // from 64 on.  (A tile that reaches past the map holds -inf at the
+            // positions outside the domain, which the pooling then never selects.)
             const float* lt = ring + (sl * 2) * KIDF;
             const float* rt = ring + (sr * 2) * KIDF;
             const float w = n == 4 ? 0.25f : (n == 2 ? 0.5f : 1.0f);
+            auto mask = [&](float& v, int ay, int ax) {
+                const int qy = qy0 + ay, qx = qx0 + ax;
+                if (qy < 0 || qy >= mh || qx < 0 || qx >= mw) v = -INFINITY;
+            };
 #pragma unroll
-            for (int u = 0; u < AGPT; u++) {
+            for (int u = 0; u < TH / 8; u++) {
                 const int e = tid + u * LEVEL_THREADS;
-                if (u == AGPT - 1 && e >= AH * AG) break;
-                const int ay = e / AG, ax = 4 * (e - ay * AG);
+                const int ay = e >> 4, ax = 4 * (e & 15);
                 const int o = ay * KW + ax;
                 float4 a = n == 3 ? avg_group<COMP, true>(lt + o, lt + KIDF + o, rt + o, rt + KIDF + o, w)
                                   : avg_group<COMP, false>(lt + o, lt + KIDF + o, rt + o, rt + KIDF + o, w);
                 if (!interior) {
-                    // a tile that reaches past the map holds -inf at the positions outside
-                    // the domain, which the pooling then never selects
-                    const int qy = qy0 + ay, qx = qx0 + ax;
-                    const bool rin = qy >= 0 && qy < mh;
-                    if (!rin || qx < 0 || qx >= mw) a.x = -INFINITY;
-                    if (!rin || qx + 1 < 0 || qx + 1 >= mw) a.y = -INFINITY;
-                    if (!rin || qx + 2 < 0 || qx + 2 >= mw) a.z = -INFINITY;
-                    if (!rin || qx + 3 < 0 || qx + 3 >= mw) a.w = -INFINITY;
+                    mask(a.x, ay, ax);
+                    mask(a.y, ay, ax + 1);
+                    mask(a.z, ay, ax + 2);
+                    mask(a.w, ay, ax + 3);
                 }
                 *reinterpret_cast<float4*>(&avg[ay][ax]) = a;
+            }
+            const int x = tid - 64;
+            if (x >= 0 && x < 32 + AH) {
+                if (x < 32) {
+                    // last row, columns 2x, 2x + 1
+                    const int ay = AH - 1, ax = 2 * x, o = ay * KW + ax;
+                    float2 a = n == 3 ? avg_two<COMP, true, false>(lt + o, lt + KIDF + o, rt + o, rt + KIDF + o, w)
+                                      : avg_two<COMP, false, false>(lt + o, lt + KIDF + o, rt + o, rt + KIDF + o, w);
+                    if (!interior) {
+                        mask(a.x, ay, ax);
+                        mask(a.y, ay, ax + 1);
+                    }
+                    *reinterpret_cast<float2*>(&avg[ay][ax]) = a;
+                } else {
+                    // column 64 of row x - 32
+                    const int ay = x - 32, ax = AW - 1, o = ay * KW + ax;
+                    float2 a = n == 3 ? avg_two<COMP, true, true>(lt + o, lt + KIDF + o, rt + o, rt + KIDF + o, w)
+                                      : avg_two<COMP, false, true>(lt + o, lt + KIDF + o, rt + o, rt + KIDF + o, w);
+                    if (!interior) mask(a.x, ay, ax);
+                    avg[ay][ax] = a.x;
+                }
             }
         }
         __syncthreads();                                     // averages ready; column k no longer needed
