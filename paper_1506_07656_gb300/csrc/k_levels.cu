@@ -18,9 +18,14 @@
 // of the next: the child windows (72 x (2 TH + 1) floats, which cover both
 // shifts +-1 of a shared column) are staged in shared memory by 3-D TMA tensor
 // loads into a ring of NR = 2 (or 3, autotuned) columns; as soon as a patch's
-// averages are formed its left column is released and thread 0 starts the
-// loads of the column NR ahead, which overlap the pooling and rectification.  Each child window reaches
-// shared memory about twice per (up to) four parents instead of four times.
+// averages are formed its left column is released and one thread starts the
+// loads of the column NR ahead, which overlap the pooling and rectification.
+// Each child window reaches shared memory about twice per (up to) four parents
+// instead of four times; the CTAs of one row of patches run together, so the
+// second staging (by the next row of patches) and the window edges shared by
+// neighbouring tiles come from L2, and the maps are read from DRAM about once.
+// Every thread forms the same number of averages and of pooled outputs per
+// patch (the CTA meets a barrier after each phase).
 // (Rows of the pooled maps are padded to 16 floats and the window's first
 // column is a multiple of 4, so every load starts 16-byte aligned; the tensor
 // map zero-fills whatever lies outside the domain.)  Algorithmic bytes per
@@ -215,7 +220,7 @@ __device__ __forceinline__ void level_sweep_body(const DmGeom& g, int l, const C
     child_col_row(g, l, ix0, iy, &cxl, &cyt, &st);
     const int cyb = cyt + (l == 1 ? 1 : S);                  // bottom child row
 
-    // thread 0: start the loads of column j (child column cxl + j*S) into slot j % NR;
+    // start the loads of column j (child column cxl + j*S) into slot j % NR (one thread);
     // a missing child's window is loaded from map index -1, outside the tensor,
     // which the TMA unit fills with zeros without reading memory
     auto stage = [&](int j) {
@@ -345,7 +350,9 @@ __device__ __forceinline__ void level_sweep_body(const DmGeom& g, int l, const C
             }
         }
         __syncthreads();                                     // averages ready; column k no longer needed
-        if (tid == 0 && k + NR <= nrun) stage(k + NR);       // into the slot column k just released
+        // into the slot column k just released; issued from the last warp, so that
+        // warp 0, whose thread 0 waits for the loads, does not carry both
+        if (tid == LEVEL_THREADS - 32 && k + NR <= nrun) stage(k + NR);
         if (n > 0) {
             // 3x3 / 2 max-pool over in-domain averages, first strict maximum, power.
             // A thread owns R = TH/8 vertically adjacent outputs (rows R*warp ..), so
