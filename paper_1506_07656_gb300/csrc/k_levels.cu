@@ -21,9 +21,10 @@
 // averages are formed its left column is released and one thread starts the
 // loads of the column NR ahead, which overlap the pooling and rectification.
 // Each child window reaches shared memory about twice per (up to) four parents
-// instead of four times; the CTAs of one row of patches run together, so the
-// second staging (by the next row of patches) and the window edges shared by
-// neighbouring tiles come from L2, and the maps are read from DRAM about once.
+// instead of four times; the CTAs of one tile row and one row of patches run
+// together, so the second staging (by the next row of patches) and the window
+// edges shared by neighbouring tiles come from L2, and the maps are read from
+// DRAM about 1.1 times.
 // Every thread forms the same number of averages and of pooled outputs per
 // patch (the CTA meets a barrier after each phase).
 // (Rows of the pooled maps are padded to 16 floats and the window's first
@@ -165,10 +166,11 @@ __device__ __forceinline__ int child_at(const DmGeom& g, int l, int cx, int cy, 
     return vprev[c] ? c : -1;
 }
 
-// Level l in [1, L-1].  Work item = (row iy, tile, residue r, run k0) with the
-// residue and run fastest, then the tile, so the CTAs whose windows overlap
-// (neighbouring tiles, neighbouring runs, and -- one row of patches later --
-// the rows that share child windows) run close together in time.  `tmap` maps the pooled maps of
+// Level l in [1, L-1].  Work item = (tile row, row iy, tile column, residue r,
+// run k0) with the residue and run fastest, so the CTAs whose windows overlap
+// (neighbouring runs, neighbouring tiles of a tile row, and -- one row of
+// patches later -- the rows that share child windows) run close together in
+// time.  `tmap` maps the pooled maps of
 // level l-1 as a 3-D array (columns dw[l], rows dh[l], patches) with a
 // 72 x (2 TH + 1) x 1 box.  Dynamic shared memory: a ring of NR columns x 2
 // child windows, then the averages.  Per patch of the run: form the averages
@@ -198,16 +200,21 @@ __device__ __forceinline__ void level_sweep_body(const DmGeom& g, int l, const C
     int cx0, cy0, S;
     child_col_row(g, l, 0, 0, &cx0, &cy0, &S);
     const int per_row = S * runs_per_res;
-    // work item = ((lattice row iy, tile), run): all tiles of one row of
-    // patches run together, so the window edges that neighbouring tiles share
-    // (64-byte memory granules at their x edges, rows at their y edges) come
-    // from DRAM once (at 512x224, level 1: 1.03x the maps read instead of 1.83x
-    // with the tile as the slowest index)
-    const int ntiles = tiles_x * ((oh + TH - 1) / TH);
+    // work item = (tile row, lattice row iy, tile column, run): the CTAs of one
+    // tile row and one row of patches run together, so the window edges that
+    // neighbouring tiles of the row share (64-byte memory granules at their x
+    // edges) come from DRAM once, and the next row of patches, which stages the
+    // same child rows again, follows within a few hundred CTAs, while they are
+    // still in L2 (1024x436, level 1: DRAM reads 1.14x the maps; all tiles of a
+    // row of patches together instead: 2.1x, their child rows exceed the L2
+    // before the next row of patches reads them again; the tile as the slowest
+    // index: 1.83x at 512x224)
     const int rr = item % per_row;
-    const int t1 = item / per_row;
-    const int tile = t1 % ntiles;
-    const int iy = t1 / ntiles;
+    int t = item / per_row;
+    const int tx = t % tiles_x;
+    t /= tiles_x;
+    const int iy = t % g.Ly;
+    const int tile = (t / g.Ly) * tiles_x + tx;
     const int r = rr / runs_per_res, k0 = (rr - r * runs_per_res) * run;
     const int ix0 = r + k0 * S;                              // first patch of the run
     if (ix0 >= g.Lx) return;
