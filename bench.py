@@ -736,16 +736,14 @@ def _measure_batch_uniform(dm, torch, dist, ctx, a, world, local, rank, W, H, np
             "d2h_bytes_per_step": npairs * (n0 * 20 + 4)}
 
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
-# ncu captures summarised in profiles/ (the full workload is too large to
-# capture), scaled to the 1024x436 workload: level 0 from a 512x224 launch by the
-# number of pooled outputs (BF16 1.121 GB, FP32 0.980 GB, x 15.1; FP8 has no
-# capture of its current epilogue); the level pass from its level-1 launch of the
-# tiled kernel at 640x272 by the algorithmic bytes of the whole launch set (same
-# traffic/algorithmic ratio, 4.317 / 2.498 GB = 1.73; the narrow top levels that
-# run the row-streaming kernel move under 0.1 % of the bytes).  None where no
-# capture of the current kernel version exists.
-TRAFFIC_1024x436 = {"level0_bf16": 16.9e9, "level0_fp8": None, "level0_fp32": 14.8e9, "levels": 37.7e9}
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# current kernels, from one ncu capture of one 1024x436 BF16 pair (one pass per
+# launch; profiles/ has the command): level 0 2.107 GB read + 16.243 GB written;
+# the level pass (k_level_sweep for levels 1-4, k_level_stream for 5-7,
+# k_level_top) 18.932 GB read + 5.120 GB written.  The FP32 level-0 kernel is
+# the capture at 512x224 scaled by the number of pooled outputs (x 15.1); FP8
+# has no capture of its current epilogue (None).
+TRAFFIC_1024x436 = {"level0_bf16": 18.35e9, "level0_fp8": None, "level0_fp32": 14.8e9, "levels": 24.05e9}
 
 
 def _prec_code(dm, name):
