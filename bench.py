@@ -435,8 +435,8 @@ def _measure_deepflow(dm, torch, a, pair, stream):
 def _measure_invariant(dm, torch, a, stream, W=512, H=224, prec="bf16"):
     """Scale and rotation invariant form (Sec. 4.2, Algorithm 2): 72 runs of the
     method (9 scales x 8 rotations) on image 1 against image 2 = image 1 turned
-    by a quarter, pooled and verified once.  W x H is the largest size whose
-    45-degree canvases keep the merge keys within 32 bits at this aspect ratio.
+    by a quarter, pooled and verified once, at 512x224 (small enough to time on
+    1, 2 and 4 lanes; the full size is _measure_invariant_full).
     One step = one dm_match_invariant call; K steps timed with CUDA events on
     the library's stream.  Also: the fraction of matches consistent (3 px) with
     the quarter turn, and the same figure for the exact form."""
@@ -492,6 +492,51 @@ def _measure_invariant(dm, torch, a, stream, W=512, H=224, prec="bf16"):
             "ms_per_step_by_lanes": {str(k): v for k, v in by_lanes.items()}, "kernel_launches_per_step": int(launches),
             "status": int(status), "matches": int(len(inv)), "consistent_with_turn": turn(inv),
             "exact_form_matches": int(len(exact)), "exact_form_consistent_with_turn": turn(exact)}
+
+
+def _measure_invariant_full(dm, torch, a, stream, W=1024, H=436, prec="bf16"):
+    """The invariant form at the bench pair's size, 1024x436 against its quarter
+    turn: its 45-degree canvases need 64-bit merge keys (7.4e9 level-1 keys).
+    One lane (the workspace is ~131 GB), 2 timed calls after one warm-up; skipped
+    (None) when the device's free memory does not hold the workspace."""
+    import numpy as np
+    from paper_1506_07656_gb300 import synth
+    img1 = synth.make_pair_smooth(W, H, seed=2, max_disp=1.0, with_flow=False).img1.astype(np.float32)
+    img2 = np.ascontiguousarray(np.rot90(img1, 1))
+    H2, W2 = img2.shape
+    ctx = dm.Context(dm.DM_BF16 if prec == "bf16" else dm.DM_FP32)
+    try:
+        dm.dm_set_batch_lanes(ctx.ctx, 1)
+        need = dm.dm_invariant_workspace_bytes(ctx.ctx, W, H, W2, H2)
+        torch.cuda.empty_cache()
+        if torch.cuda.mem_get_info()[0] < need + 8e9:
+            return None
+        ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+        i1 = torch.from_numpy(img1).cuda()
+        i2 = torch.from_numpy(img2).cuda()
+        P0 = dm.dm_geometry(W, H, W2, H2)["n_patch0"]
+        out = torch.empty((P0, 5), dtype=torch.float32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+        dm.dm_match_invariant(ctx.ctx, i1, i2, ws, out, cnt, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(2):
+            dm.dm_match_invariant(ctx.ctx, i1, i2, ws, out, cnt, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 2
+        status, _ = dm.dm_read_status(ctx.ctx, ws, 1)
+        inv = out[:int(cnt.item())].cpu().numpy().astype(np.float64)
+        del ws
+    finally:
+        ctx.close()
+        torch.cuda.empty_cache()
+    turn = float(np.mean((np.abs(inv[:, 2] - inv[:, 1]) <= 3) & (np.abs(inv[:, 3] - (W - 1 - inv[:, 0])) <= 3))) \
+        if len(inv) else None
+    return {"workload": f"{W}x{H} against its quarter turn (64-bit merge keys)", "transforms": 72, "precision": prec,
+            "pairs_per_s": 1000.0 / ms, "ms_per_step": ms, "lanes": 1, "workspace_gb": need / 1e9,
+            "status": int(status), "matches": int(len(inv)), "consistent_with_turn": turn}
 
 
 BATCH_SIZES = [(320, 240), (640, 480), (1024, 436), (1242, 375)]
@@ -848,6 +893,7 @@ def run_ours(a):
     invariant = None
     if not a.no_invariant and world == 1:
         invariant = _measure_invariant(dm, torch, a, stream)
+        invariant["full_size"] = _measure_invariant_full(dm, torch, a, stream)
         torch.cuda.empty_cache()
     grad = None
     if not a.no_grad and world == 1:
