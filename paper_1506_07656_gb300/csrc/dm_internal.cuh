@@ -174,7 +174,9 @@ __device__ __forceinline__ float2 dm_powf2(float2 x, float lam) {
     p = __ffma2_rn(p, g, make_float2(2.40226507e-01f, 2.40226507e-01f));
     p = __ffma2_rn(p, g, make_float2(6.93147181e-01f, 6.93147181e-01f));
     p = __ffma2_rn(p, g, make_float2(1.0f, 1.0f));
-    const int nt0 = (int)n1.x + (int)n2.x, nt1 = (int)n1.y + (int)n2.y;
+    // n1 + n2 is a sum of two small integers, exact in FP32: one conversion per lane
+    const float2 ntf = __fadd2_rn(n1, n2);
+    const int nt0 = (int)ntf.x, nt1 = (int)ntf.y;
     if (nt0 >= -125 && nt1 >= -125) return __fmul2_rn(p, make_float2(dm_pow2i(nt0), dm_pow2i(nt1)));
     // a result below the normal range: the scalar two-step scaling per lane
     r.x = dm_powf(x.x, lam);

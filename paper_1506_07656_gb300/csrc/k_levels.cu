@@ -370,24 +370,26 @@ __device__ __forceinline__ void level_sweep_body(const DmGeom& g, int l, const C
             const int rx = rx0 + lane;
             const int ty0 = R * warp;
             if (rx < ow) {
-                float hv[2 * R + 1];
-                int hc[2 * R + 1];
+                float hv[2 * R + 1], h0[2 * R + 1], h1[2 * R + 1];
 #pragma unroll
                 for (int kk = 0; kk < 2 * R + 1; kk++) {
                     const int ay = 2 * ty0 + kk;             // average row; map row qy0 + ay
                     const float a0 = avg[ay][2 * lane], a1 = avg[ay][2 * lane + 1], a2 = avg[ay][2 * lane + 2];
-                    // first column holding the row maximum (columns in scan order m_x = -1, 0, 1)
-                    const float m = fmax3(a0, a1, a2);
-                    hv[kk] = m;
-                    hc[kk] = a0 == m ? 0 : (a1 == m ? 1 : 2);
+                    hv[kk] = fmax3(a0, a1, a2);
+                    h0[kk] = a0;
+                    h1[kk] = a1;
                 }
                 float best[R], pw[R];
                 int code[R];
 #pragma unroll
                 for (int j = 0; j < R; j++) {
-                    // first row holding the maximum (m_y = -1, 0, 1): the first maximum in scan order
+                    // first row holding the maximum (m_y = -1, 0, 1), then the first column of
+                    // that row holding it (m_x = -1, 0, 1): the first maximum in scan order
                     best[j] = fmax3(hv[2 * j], hv[2 * j + 1], hv[2 * j + 2]);
-                    code[j] = hv[2 * j] == best[j] ? hc[2 * j] : (hv[2 * j + 1] == best[j] ? 3 + hc[2 * j + 1] : 6 + hc[2 * j + 2]);
+                    const bool r0 = hv[2 * j] == best[j], r1 = hv[2 * j + 1] == best[j];
+                    const float x0 = r0 ? h0[2 * j] : (r1 ? h0[2 * j + 1] : h0[2 * j + 2]);
+                    const float x1 = r0 ? h1[2 * j] : (r1 ? h1[2 * j + 1] : h1[2 * j + 2]);
+                    code[j] = (r0 ? 0 : (r1 ? 3 : 6)) + (x0 == best[j] ? 0 : (x1 == best[j] ? 1 : 2));
                 }
                 // the power of two outputs per packed evaluation (rows past the map
                 // are evaluated on whatever the tile holds there and not stored)
