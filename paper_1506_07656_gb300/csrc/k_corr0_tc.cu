@@ -273,14 +273,26 @@ __device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.syn
 //
 // Horizontal step for C0 row ly: the key maxima of the column triples (2k,
 // 2k+1, 2k+2); positions outside I' are -inf.
-__device__ __forceinline__ void pool_row(const EpiArgs& e, int tx0, int ly, const uint32_t (&r)[9], float (&h)[4]) {
-    // the mask lives in a register, so each key is one logic operation with the
-    // position as its immediate
+template <int POS>
+__device__ __forceinline__ float pool_key(uint32_t r, uint32_t keep) {
+    uint32_t k;
+    asm("lop3.b32 %0, %1, %2, %3, 0xEA;" : "=r"(k) : "r"(r), "r"(keep), "n"(POS));
+    return __uint_as_float(k);
+}
+
+template <int LY>
+__device__ __forceinline__ void pool_row(const EpiArgs& e, int tx0, const uint32_t (&r)[9], float (&h)[4]) {
+    // the mask lives in a register, so each key is one three-input logic
+    // operation ((r & mask) | position, LUT 0xEA) with the position 31 - (3 ly + c)
+    // as its immediate
     uint32_t keep;
     asm("mov.b32 %0, %1;" : "=r"(keep) : "n"(0xFFFFFFE0u));
-    float v[9];
-#pragma unroll
-    for (int c = 0; c < 9; c++) v[c] = __uint_as_float((r[c] & keep) | (uint32_t)(31 - (3 * ly + c)));
+    float v[9] = {pool_key<31 - 3 * LY>(r[0], keep),     pool_key<31 - 3 * LY - 1>(r[1], keep),
+                  pool_key<31 - 3 * LY - 2>(r[2], keep), pool_key<31 - 3 * LY - 3>(r[3], keep),
+                  pool_key<31 - 3 * LY - 4>(r[4], keep), pool_key<31 - 3 * LY - 5>(r[5], keep),
+                  pool_key<31 - 3 * LY - 6>(r[6], keep), pool_key<31 - 3 * LY - 7>(r[7], keep),
+                  pool_key<31 - 3 * LY - 8>(r[8], keep)};
+    const int ly = LY;
     if (!e.interior) {
         const int ty = e.cy0 + ly;
         const bool rin = ty >= 0 && ty < e.H2;
@@ -294,19 +306,26 @@ __device__ __forceinline__ void pool_row(const EpiArgs& e, int tx0, int ly, cons
     for (int k = 0; k < 4; k++) h[k] = fmax3(v[2 * k], v[2 * k + 1], v[2 * k + 2]);
 }
 
-// x^lam = 2^(lam log2 x) with the hardware's approximate base-2 logarithm and
-// exponential (x in (0, 1]: pooled C0 values, never subnormal; 0 gives 0).
-__device__ __forceinline__ float pow_hw(float x, float lam) {
+// (a x)^lam = 2^(lam log2 a + lam log2 x) with the hardware's approximate
+// base-2 logarithm and exponential, for an accumulator a (never subnormal; 0
+// gives 0) and a power-of-two scale x, lc = lam log2 x: one fused multiply-add
+// between the two approximations.
+__device__ __forceinline__ float pow_hw(float a, float lam, float lc) {
     float l, r;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(x));
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(__fmul_rn(l, lam)));
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(a));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(__fmaf_rn(l, lam, lc)));
     return r;
+}
+
+// lam log2 x for a power of two x (its exponent field, exactly)
+__device__ __forceinline__ float lam_log2_pow2(float x, float lam) {
+    return __fmul_rn(lam, (float)((int)((__float_as_uint(x) >> 23) & 0xffu) - 127));
 }
 
 // Vertical step for pooled row y (C0 rows 2y, 2y+1, 2y+2 = m_y -1, 0, +1): the
 // key maximum, its code 3 (row - 2y) + (c - 2k) from the low bits, the power,
 // and the staging of the 4 values and codes.
-__device__ __forceinline__ void pool_out(const EpiArgs& e, int y, float mult, const float (&h)[CY][4],
+__device__ __forceinline__ void pool_out(const EpiArgs& e, int y, float lc, const float (&h)[CY][4],
                                          float* stage_f, unsigned char* stage_c) {
     float f[4];
     uint32_t codes = 0;
@@ -314,7 +333,7 @@ __device__ __forceinline__ void pool_out(const EpiArgs& e, int y, float mult, co
     for (int k = 0; k < 4; k++) {
         const float m = fmax3(h[2 * y][k], h[2 * y + 1][k], h[2 * y + 2][k]);
         const int code = (int)(~__float_as_uint(m) & 0x1Fu) - (6 * y + 2 * k);   // 3 row + c - (6 y + 2 k)
-        f[k] = pow_hw(m * mult, e.lam);
+        f[k] = pow_hw(m, e.lam, lc);
         codes |= (uint32_t)code << (8 * k);
     }
     // staging layout = the TMA box [patch][row][16 columns].  The values' box
@@ -339,6 +358,7 @@ __device__ __forceinline__ void pool_out(const EpiArgs& e, int y, float mult, co
 // pooled row y is finished as soon as its C0 rows 2y .. 2y+2 are in.
 __device__ __forceinline__ void epilogue_tile(const EpiArgs& e, uint32_t b, uint32_t bar_empty, float mult,
                                               float* stage_f, unsigned char* stage_c) {
+    const float lc = lam_log2_pow2(mult, e.lam);
     uint32_t r[CY][9];
     float h[CY][4];
     const uint32_t taddr = e.taddr + b * 256 + 8 * e.part;
@@ -350,26 +370,27 @@ __device__ __forceinline__ void epilogue_tile(const EpiArgs& e, uint32_t b, uint
     for (int ly = 0; ly < 3; ly++) tmem_row_ready(r[ly]);
 #pragma unroll
     for (int ly = 3; ly < 5; ly++) tmem_row(taddr, ly, r[ly]);
-#pragma unroll
-    for (int ly = 0; ly < 3; ly++) pool_row(e, tx0, ly, r[ly], h[ly]);
-    pool_out(e, 0, mult, h, stage_f, stage_c);
+    pool_row<0>(e, tx0, r[0], h[0]);
+    pool_row<1>(e, tx0, r[1], h[1]);
+    pool_row<2>(e, tx0, r[2], h[2]);
+    pool_out(e, 0, lc, h, stage_f, stage_c);
     tmem_wait();
 #pragma unroll
     for (int ly = 3; ly < 5; ly++) tmem_row_ready(r[ly]);
 #pragma unroll
     for (int ly = 5; ly < 7; ly++) tmem_row(taddr, ly, r[ly]);
-#pragma unroll
-    for (int ly = 3; ly < 5; ly++) pool_row(e, tx0, ly, r[ly], h[ly]);
-    pool_out(e, 1, mult, h, stage_f, stage_c);
+    pool_row<3>(e, tx0, r[3], h[3]);
+    pool_row<4>(e, tx0, r[4], h[4]);
+    pool_out(e, 1, lc, h, stage_f, stage_c);
     tmem_wait();
 #pragma unroll
     for (int ly = 5; ly < 7; ly++) tmem_row_ready(r[ly]);
     // every load of this accumulator is complete: hand it back to the MMA warp
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     mbar_arrive(bar_empty);
-#pragma unroll
-    for (int ly = 5; ly < 7; ly++) pool_row(e, tx0, ly, r[ly], h[ly]);
-    pool_out(e, 2, mult, h, stage_f, stage_c);
+    pool_row<5>(e, tx0, r[5], h[5]);
+    pool_row<6>(e, tx0, r[6], h[6]);
+    pool_out(e, 2, lc, h, stage_f, stage_c);
 }
 
 // Per-pair arguments of the level-0 kernel.  One launch serves one pair, or
