@@ -328,14 +328,23 @@ __device__ __forceinline__ float lam_log2_pow2(float x, float lam) {
 __device__ __forceinline__ void pool_out(const EpiArgs& e, int y, float lc, const float (&h)[CY][4],
                                          float* stage_f, unsigned char* stage_c) {
     float f[4];
-    uint32_t codes = 0;
+    uint32_t mb[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         const float m = fmax3(h[2 * y][k], h[2 * y + 1][k], h[2 * y + 2][k]);
-        const int code = (int)(~__float_as_uint(m) & 0x1Fu) - (6 * y + 2 * k);   // 3 row + c - (6 y + 2 k)
+        mb[k] = __float_as_uint(m);
         f[k] = pow_hw(m, e.lam, lc);
-        codes |= (uint32_t)code << (8 * k);
     }
+    // codes 3 row + c - (6 y + 2 k) = (31 - 6 y - 2 k) - (low 5 bits), all four at
+    // once: the maxima's low bytes gathered into one word (byte permutes), masked,
+    // and subtracted bytewise from the packed constants (no byte borrows: every
+    // code is 0..8)
+    uint32_t lo01, lo23, lo;
+    asm("prmt.b32 %0, %1, %2, 0x0040;" : "=r"(lo01) : "r"(mb[0]), "r"(mb[1]));
+    asm("prmt.b32 %0, %1, %2, 0x0040;" : "=r"(lo23) : "r"(mb[2]), "r"(mb[3]));
+    asm("prmt.b32 %0, %1, %2, 0x5410;" : "=r"(lo) : "r"(lo01), "r"(lo23));
+    const uint32_t cst = (uint32_t)(31 - 6 * y) * 0x01010101u - 0x06040200u;   // bytes 31 - 6y - 2k
+    const uint32_t codes = cst - (lo & 0x1F1F1F1Fu);
     // staging layout = the TMA box [patch][row][16 columns].  The values' box
     // rows (64 bytes, four 16-byte chunks) are staged with the tensor map's
     // 64-byte swizzle: the 16-byte chunk index (shared address bits 4-5) is
