@@ -1283,6 +1283,12 @@ dm_status dm_autotune(dm_ctx* ctx, const float* d_img1, int W1, int H1, const fl
                                   const_cast<float*>(py.pooled[0]), const_cast<unsigned char*>(py.amax[0]),
                                   py.tune.m_chunk, st);
     };
+    // one untimed run first: the default shape is timed warm like the candidates after it
+    if ((err = level0()) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cuda_fail(ctx, err, "dm_autotune");
+    }
     float cur = timed(level0);
     if (ctx->cfg.precision != DM_FP32) {
         const int n_mtiles = (g.npatch(0) + 127) / 128;
