@@ -485,10 +485,11 @@ dm_status dm_autotune_batch(dm_ctx* ctx, int n, const dm_pair* pairs, void* d_ws
  *              level-0 kernel (the work unit is one N-tile x that many
  *              M-tiles; candidates split the patches into 1, 2, 3, 4, 6 or 8
  *              chunks; unused by DM_FP32);
- *   chosen[1]  level kernel: pooled rows per CTA tile of the tiled kernel (16
- *              or 8), or 0 for the row-streaming kernel (one warp per patch
- *              and 31-column strip, no shared memory); levels whose stored
- *              maps are at most 16 columns wide always take the latter;
+ *   chosen[1]  level kernel: pooled rows per CTA tile of the tiled kernel (16,
+ *              8 or 4, on 8, 4 or 2 warps), or 0 for the row-streaming kernel
+ *              (one warp per patch and 31-column strip, no shared memory);
+ *              levels whose stored maps are at most 16 columns wide always
+ *              take the latter;
  *   chosen[2]  CTAs per SM of the backtracking expansion kernels (2..32);
  *   chosen[3]  child-window columns in the level kernel's ring (3 or 2).
  * Every candidate computes identical results; only the time differs.  Each
@@ -502,10 +503,10 @@ dm_status dm_autotune(dm_ctx* ctx, const float* d_img1, int W1, int H1, const fl
                       void* d_ws, size_t ws_bytes, int* chosen, void* stream);
 /* The launch shapes used for pairs of these sizes (until dm_autotune has run
  * on them the defaults: all M-tiles in one work unit -- half of them for
- * DM_FP8_E4M3 --, 16, 8, 2): 4 ints as for dm_autotune. */
+ * DM_FP8_E4M3 --, 8, 8, 2): 4 ints as for dm_autotune. */
 dm_status dm_tuned_config(dm_ctx* ctx, int W1, int H1, int W2, int H2, int* chosen);
 /* Set the launch shapes for pairs of these sizes (e.g. a choice saved from an
- * earlier dm_autotune): chosen[0] >= 1, chosen[1] in {0, 8, 16}, chosen[2] in
+ * earlier dm_autotune): chosen[0] >= 1, chosen[1] in {0, 4, 8, 16}, chosen[2] in
  * 1..64, chosen[3] in {2, 3}; DM_EINVAL otherwise. */
 dm_status dm_set_tuned_config(dm_ctx* ctx, int W1, int H1, int W2, int H2, const int* chosen);
 

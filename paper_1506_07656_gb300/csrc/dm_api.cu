@@ -1304,7 +1304,8 @@ dm_status dm_autotune(dm_ctx* ctx, const float* d_img1, int W1, int H1, const fl
     // levels: pooled rows per CTA tile x ring columns
     auto levels = [&]() { return dm_launch_levels(g, py, ctx->cfg.lambda, d_status, st); };
     cur = timed(levels);
-    const int lshapes[4][2] = {{16, 3}, {8, 2}, {8, 3}, {0, 2}};   // rows per tile x ring; 0 = row-streaming kernel
+    // rows per tile x ring (the default first, timed above); 0 = row-streaming kernel
+    const int lshapes[6][2] = {{16, 2}, {16, 3}, {8, 3}, {4, 2}, {4, 3}, {0, 2}};
     for (const auto& sh : lshapes) {
         py.tune.level_th = sh[0];
         py.tune.level_ring = sh[1];
@@ -1411,7 +1412,8 @@ dm_status dm_tuned_config(dm_ctx* ctx, int W1, int H1, int W2, int H2, int* chos
 
 dm_status dm_set_tuned_config(dm_ctx* ctx, int W1, int H1, int W2, int H2, const int* chosen) {
     if (!ctx || !chosen) return DM_EINVAL;
-    if (chosen[0] < 1 || (chosen[1] != 0 && chosen[1] != 8 && chosen[1] != 16) || chosen[2] < 1 || chosen[2] > 64 ||
+    if (chosen[0] < 1 || (chosen[1] != 0 && chosen[1] != 4 && chosen[1] != 8 && chosen[1] != 16) || chosen[2] < 1 ||
+        chosen[2] > 64 ||
         (chosen[3] != 2 && chosen[3] != 3))
         return fail(ctx, DM_EINVAL, "dm_set_tuned_config: invalid launch shapes %d %d %d %d", chosen[0], chosen[1],
                     chosen[2], chosen[3]);

@@ -256,10 +256,11 @@ struct DmTune {
 // Defaults until tuned: the level-0 work unit holds all M-tiles of the pair
 // (the N-tiles are the units; measured at 1024x436 the most robust choice for
 // BF16) or, for the FP8 form, half of them (its best measured split); tile
-// rows 16, 8 CTAs per SM, a ring of 2.
+// rows 8 (on 4 warps; 1024x436: 7.79 ms against 8.31 for 16 rows on 8 warps,
+// 8.71 for 4 rows on 2), 8 CTAs per SM for the backtracking, a ring of 2.
 inline DmTune dm_tune_default(const DmGeom& g, int precision) {
     const int n_mtiles = (g.npatch(0) + 127) / 128;
-    return DmTune{precision == DM_FP8_E4M3 ? (n_mtiles + 1) / 2 : n_mtiles, 16, 8, 2};
+    return DmTune{precision == DM_FP8_E4M3 ? (n_mtiles + 1) / 2 : n_mtiles, 8, 8, 2};
 }
 
 // Pyramid handle (host side).

@@ -13,7 +13,8 @@
 // This pass streams the pooled maps of the level below and does a fixed
 // amount of arithmetic per stored output (~4 averages of 4 values, a 9-way
 // max with argmax, one power).  A CTA owns a tile of 32 x TH pooled outputs
-// (TH = 16 or 8, autotuned) of a run of up to 16 lattice patches on one row,
+// (TH = 8 by default on 4 warps; 16 on 8 or 4 on 2, autotuned) of a run of up
+// to 16 lattice patches on one row,
 // spaced so that the right child column of one patch is the left child column
 // of the next: the child windows (72 x (2 TH + 1) floats, which cover both
 // shifts +-1 of a shared column) are staged in shared memory by 3-D TMA tensor
@@ -66,6 +67,13 @@ constexpr int AW = 2 * TW + 1;                   // average columns per CTA (65)
 constexpr int KW = 72;                           // staged child columns (TMA box width)
 constexpr int AWP = 68;                          // padded row of the averages (16-byte aligned rows)
 constexpr int LEVEL_THREADS = 256;
+// threads of a tiled level CTA for TH pooled rows: 8 warps for 16 rows, 4 for 8,
+// 2 for 4 -- every thread forms two 4-column average groups and two pooled
+// outputs per patch, and smaller CTAs wait less at their per-patch barriers
+// (1024x436 levels: 8 rows on 4 warps 7.79 ms, 16 rows on 8 warps 8.30, 8 rows
+// on 8 warps 10.31)
+template <int TH>
+__host__ __device__ constexpr int level_threads() { return TH == 16 ? 256 : (TH == 8 ? 128 : 64); }
 
 // CTA tile of TW x TH pooled outputs (TH = 8 or 16, chosen by the autotuner):
 // AH rows of averages, child windows of KW x AH floats (KIDF with padding to
@@ -177,7 +185,7 @@ __device__ __forceinline__ int child_at(const DmGeom& g, int l, int cx, int cy, 
 // from its two columns, release the left column (thread 0 starts the loads of
 // the column NR ahead into it), pool, power, store, wait for the next patch's
 // columns; two barriers per patch.
-template <bool COMP, int TH, int NR, bool APPROX>
+template <bool COMP, int TH, int NR, bool APPROX, int NT = LEVEL_THREADS>
 __device__ __forceinline__ void level_sweep_body(const DmGeom& g, int l, const CUtensorMap* tmap_p,
                                                  const unsigned char* __restrict__ vprev, int runs_per_res, int run,
                                                  float* __restrict__ out, unsigned char* __restrict__ amax, float lam,
@@ -308,7 +316,7 @@ __device__ __forceinline__ void level_sweep_body(const DmGeom& g, int l, const C
         const int p = iy * g.Lx + ix;
         if (n > 0) {
             // averages of the tile: rows 0 .. 2 TH - 1 in 16 groups of 4 columns
-            // (columns 0 .. 63), TH / 8 groups per thread; then the last row's 32
+            // (columns 0 .. 63), 32 TH / NT groups per thread; then the last row's 32
             // column pairs and column 64 of every row, one item each for threads
             // from 64 on.  (A tile that reaches past the map holds -inf at the
             // positions outside the domain, which the pooling then never selects.)
@@ -320,8 +328,8 @@ __device__ __forceinline__ void level_sweep_body(const DmGeom& g, int l, const C
                 if (qy < 0 || qy >= mh || qx < 0 || qx >= mw) v = -INFINITY;
             };
 #pragma unroll
-            for (int u = 0; u < TH / 8; u++) {
-                const int e = tid + u * LEVEL_THREADS;
+            for (int u = 0; u < 32 * TH / NT; u++) {
+                const int e = tid + u * NT;
                 const int ay = e >> 4, ax = 4 * (e & 15);
                 const int o = ay * KW + ax;
                 float4 a = n == 3 ? avg_group<COMP, true>(lt + o, lt + KIDF + o, rt + o, rt + KIDF + o, w)
@@ -334,7 +342,8 @@ __device__ __forceinline__ void level_sweep_body(const DmGeom& g, int l, const C
                 }
                 *reinterpret_cast<float4*>(&avg[ay][ax]) = a;
             }
-            const int x = tid - 64;
+            constexpr int XB = NT >= 64 + 32 + AH ? 64 : NT - (32 + AH);   // first thread of the extra items
+            const int x = tid - XB;
             if (x >= 0 && x < 32 + AH) {
                 if (x < 32) {
                     // last row, columns 2x, 2x + 1
@@ -359,14 +368,15 @@ __device__ __forceinline__ void level_sweep_body(const DmGeom& g, int l, const C
         __syncthreads();                                     // averages ready; column k no longer needed
         // into the slot column k just released; issued from the last warp, so that
         // warp 0, whose thread 0 waits for the loads, does not carry both
-        if (tid == LEVEL_THREADS - 32 && k + NR <= nrun) stage(k + NR);
+        if (tid == NT - 32 && k + NR <= nrun) stage(k + NR);
         if (n > 0) {
             // 3x3 / 2 max-pool over in-domain averages, first strict maximum, power.
-            // A thread owns R = TH/8 vertically adjacent outputs (rows R*warp ..), so
+            // A thread owns R = 32 TH / NT vertically adjacent outputs (rows R*warp ..), so
             // the horizontal 3-maxima of the 2R+1 average rows it reads are formed
             // once (a row shared by two outputs serves both); rows are then merged in
             // scan order m_y = -1, 0, 1, which keeps the first strict maximum.
-            constexpr int R = TH / 8;
+            constexpr int R = 32 * TH / NT;
+            static_assert(R >= 1 && 32 + AH <= NT && 32 * TH % NT == 0, "tile rows and threads");
             const int rx = rx0 + lane;
             const int ty0 = R * warp;
             if (rx < ow) {
@@ -417,15 +427,15 @@ __device__ __forceinline__ void level_sweep_body(const DmGeom& g, int l, const C
     }
 }
 
-template <bool COMP, int TH, int NR, bool APPROX = false>
-__global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep(DmGeom g, int l, const __grid_constant__ CUtensorMap tmap,
+template <bool COMP, int TH, int NR, bool APPROX = false, int NT = level_threads<TH>()>
+__global__ void __launch_bounds__(NT) k_level_sweep(DmGeom g, int l, const __grid_constant__ CUtensorMap tmap,
                                                                const unsigned char* __restrict__ vprev,
                                                                int runs_per_res, int run, float* __restrict__ out,
                                                                unsigned char* __restrict__ amax, float lam,
                                                                int* __restrict__ err, const int* __restrict__ proto_of,
                                                                int n_maps, long long inject_wait) {
-    level_sweep_body<COMP, TH, NR, APPROX>(g, l, &tmap, vprev, runs_per_res, run, out, amax, lam, err, proto_of, n_maps,
-                                           inject_wait, (int)blockIdx.x);
+    level_sweep_body<COMP, TH, NR, APPROX, NT>(g, l, &tmap, vprev, runs_per_res, run, out, amax, lam, err, proto_of, n_maps,
+                                               inject_wait, (int)blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -646,16 +656,16 @@ __global__ void k_level_top(DmGeom g, int l, const unsigned char* __restrict__ v
     top[(long long)p * mw * mh + q] = dm_powf(a, lam);
 }
 
-template <bool COMP, int TH, int NR, bool APPROX = false>
+template <bool COMP, int TH, int NR, bool APPROX = false, int NT = level_threads<TH>()>
 cudaError_t launch_sweep(const DmGeom& g, int l, const CUtensorMap& tm, const dm_pyramid& py, int per_res, long long items,
                          float lam, int* status, cudaStream_t st) {
     const size_t smem = (size_t)(NR * 2 * LevelTile<TH>::KIDF + LevelTile<TH>::AH * AWP) * sizeof(float) + 128;
     static std::atomic<unsigned long long> smem_done{0};
-    cudaError_t ea = dm_smem_opt_in(reinterpret_cast<const void*>(k_level_sweep<COMP, TH, NR, APPROX>), (int)smem, smem_done);
+    cudaError_t ea = dm_smem_opt_in(reinterpret_cast<const void*>(k_level_sweep<COMP, TH, NR, APPROX, NT>), (int)smem, smem_done);
     if (ea != cudaSuccess) return ea;
     if (items <= 0) return cudaSuccess;
     if (items > 0x7fffffffLL) return cudaErrorInvalidValue;
-    k_level_sweep<COMP, TH, NR, APPROX><<<(unsigned)items, LEVEL_THREADS, smem, st>>>(g, l, tm, py.valid[l - 1], per_res, level_run(l),
+    k_level_sweep<COMP, TH, NR, APPROX, NT><<<(unsigned)items, NT, smem, st>>>(g, l, tm, py.valid[l - 1], per_res, level_run(l),
                                                                           const_cast<float*>(py.pooled[l]),
                                                                           const_cast<unsigned char*>(py.amax[l]), lam, status,
                                                                           APPROX ? py.proto_of : nullptr, py.n0_maps,
@@ -709,11 +719,12 @@ __device__ __forceinline__ int lv_pair_of(const LvBatch& B, long long blk) {
 }
 
 template <bool COMP, int TH, int NR>
-__global__ void __launch_bounds__(LEVEL_THREADS) k_level_sweep_b(const __grid_constant__ LvBatch B, int l, float lam) {
+__global__ void __launch_bounds__(level_threads<TH>()) k_level_sweep_b(const __grid_constant__ LvBatch B, int l, float lam) {
     const int j = lv_pair_of(B, blockIdx.x);
     const LvPair& P = B.p[j];
-    level_sweep_body<COMP, TH, NR, false>(P.g, l, &P.tmap, P.vprev, P.a, level_run(l), P.out, P.amax, lam, P.err, nullptr,
-                                          0, 0, (int)((long long)blockIdx.x - P.first));
+    level_sweep_body<COMP, TH, NR, false, level_threads<TH>()>(P.g, l, &P.tmap, P.vprev, P.a, level_run(l), P.out, P.amax,
+                                                               lam, P.err, nullptr, 0, 0,
+                                                               (int)((long long)blockIdx.x - P.first));
 }
 
 template <bool COMP>
@@ -783,7 +794,7 @@ cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& py, float lam, i
             // level 1 of an approximate pyramid reads the level-0 maps through the
             // prototype index: its own kernel instance, 16-row tiles, ring of 2
             const bool approx = l == 1 && py.proto_of != nullptr;
-            const int th = approx ? 16 : (py.tune.level_th == 8 ? 8 : 16);
+            const int th = approx ? 16 : (py.tune.level_th == 8 || py.tune.level_th == 4 ? py.tune.level_th : 16);
             CUtensorMap tm;
             // (level 0 holds n0_maps maps: one per atomic patch, or per prototype)
             const cuuint64_t dims[3] = {(cuuint64_t)g.dw[l], (cuuint64_t)g.dh[l],
@@ -806,6 +817,9 @@ cudaError_t dm_launch_levels(const DmGeom& g, const dm_pyramid& py, float lam, i
             else if (th == 8)
                 e = py.compensated ? (r2 ? launch_sweep<true, 8, 2> : launch_sweep<true, 8, 3>)(g, l, tm, py, per_res, items, lam, status, st)
                                    : (r2 ? launch_sweep<false, 8, 2> : launch_sweep<false, 8, 3>)(g, l, tm, py, per_res, items, lam, status, st);
+            else if (th == 4)
+                e = py.compensated ? (r2 ? launch_sweep<true, 4, 2> : launch_sweep<true, 4, 3>)(g, l, tm, py, per_res, items, lam, status, st)
+                                   : (r2 ? launch_sweep<false, 4, 2> : launch_sweep<false, 4, 3>)(g, l, tm, py, per_res, items, lam, status, st);
             else
                 e = py.compensated ? (r2 ? launch_sweep<true, 16, 2> : launch_sweep<true, 16, 3>)(g, l, tm, py, per_res, items, lam, status, st)
                                    : (r2 ? launch_sweep<false, 16, 2> : launch_sweep<false, 16, 3>)(g, l, tm, py, per_res, items, lam, status, st);
@@ -880,8 +894,8 @@ cudaError_t dm_launch_levels_batch(const dm_pyramid* const* pys, int n, float la
             }
         }
         // the pairs below their top: one launch per kernel shape in use.
-        // shape 0: row-streaming; 1 + (rows == 8) + 2 (ring == 3): tiled
-        for (int shape = 0; shape < 5; shape++) {
+        // shape 0: row-streaming; 1 + 2 (rows 16 / 8 / 4 as 0 / 1 / 2) + (ring == 3): tiled
+        for (int shape = 0; shape < 7; shape++) {
             LvBatch B;
             memset(&B, 0, sizeof(B));
             long long blocks = 0;
@@ -890,8 +904,9 @@ cudaError_t dm_launch_levels_batch(const dm_pyramid* const* pys, int n, float la
                 const DmGeom& g = py.g;
                 if (l >= g.L) continue;
                 const bool stream = py.tune.level_th == 0 || g.dw[l + 1] <= 16;
-                const int th = py.tune.level_th == 8 ? 8 : 16, nr = py.tune.level_ring == 3 ? 3 : 2;
-                const int my = stream ? 0 : 1 + (th == 8) + 2 * (nr == 3);
+                const int th = py.tune.level_th == 8 || py.tune.level_th == 4 ? py.tune.level_th : 16;
+                const int nr = py.tune.level_ring == 3 ? 3 : 2;
+                const int my = stream ? 0 : 1 + 2 * (th == 16 ? 0 : (th == 8 ? 1 : 2)) + (nr == 3);
                 if (my != shape) continue;
                 LvPair q = base_pair(j, l);
                 const int S = l == 1 ? 1 : 1 << (l - 1);
@@ -927,16 +942,21 @@ cudaError_t dm_launch_levels_batch(const dm_pyramid* const* pys, int n, float la
                 auto launch = [&](auto kern, int TH, int NR) -> cudaError_t {
                     const int kidf = (((2 * TH + 1) * KW + 31) / 32) * 32;     // LevelTile<TH>::KIDF
                     const size_t smem = (size_t)(NR * 2 * kidf + (2 * TH + 1) * AWP) * sizeof(float) + 128;
-                    static std::atomic<unsigned long long> done[4];
+                    const int nt = TH == 16 ? level_threads<16>() : (TH == 8 ? level_threads<8>() : level_threads<4>());
+                    static std::atomic<unsigned long long> done[6];
                     cudaError_t ea = dm_smem_opt_in(reinterpret_cast<const void*>(kern), (int)smem, done[shape - 1]);
                     if (ea != cudaSuccess) return ea;
-                    kern<<<(unsigned)blocks, LEVEL_THREADS, smem, st>>>(B, l, lam);
+                    kern<<<(unsigned)blocks, nt, smem, st>>>(B, l, lam);
                     return cudaSuccess;
                 };
-                if (shape == 1) e = comp ? launch(k_level_sweep_b<true, 16, 2>, 16, 2) : launch(k_level_sweep_b<false, 16, 2>, 16, 2);
-                else if (shape == 2) e = comp ? launch(k_level_sweep_b<true, 8, 2>, 8, 2) : launch(k_level_sweep_b<false, 8, 2>, 8, 2);
-                else if (shape == 3) e = comp ? launch(k_level_sweep_b<true, 16, 3>, 16, 3) : launch(k_level_sweep_b<false, 16, 3>, 16, 3);
-                else e = comp ? launch(k_level_sweep_b<true, 8, 3>, 8, 3) : launch(k_level_sweep_b<false, 8, 3>, 8, 3);
+                switch (shape) {
+                    case 1: e = comp ? launch(k_level_sweep_b<true, 16, 2>, 16, 2) : launch(k_level_sweep_b<false, 16, 2>, 16, 2); break;
+                    case 2: e = comp ? launch(k_level_sweep_b<true, 16, 3>, 16, 3) : launch(k_level_sweep_b<false, 16, 3>, 16, 3); break;
+                    case 3: e = comp ? launch(k_level_sweep_b<true, 8, 2>, 8, 2) : launch(k_level_sweep_b<false, 8, 2>, 8, 2); break;
+                    case 4: e = comp ? launch(k_level_sweep_b<true, 8, 3>, 8, 3) : launch(k_level_sweep_b<false, 8, 3>, 8, 3); break;
+                    case 5: e = comp ? launch(k_level_sweep_b<true, 4, 2>, 4, 2) : launch(k_level_sweep_b<false, 4, 2>, 4, 2); break;
+                    default: e = comp ? launch(k_level_sweep_b<true, 4, 3>, 4, 3) : launch(k_level_sweep_b<false, 4, 3>, 4, 3); break;
+                }
             }
             if (e != cudaSuccess) return e;
             launches++;

@@ -17,6 +17,8 @@ SHAPES = [
     {"m_chunk": 3, "level_tile_rows": 16, "bt_ctas_per_sm": 32, "level_ring": 2},
     {"m_chunk": 1000, "level_tile_rows": 8, "bt_ctas_per_sm": 1, "level_ring": 2},
     {"m_chunk": 2, "level_tile_rows": 0, "bt_ctas_per_sm": 8, "level_ring": 2},      # row-streaming level kernel
+    {"m_chunk": 2, "level_tile_rows": 4, "bt_ctas_per_sm": 8, "level_ring": 2},      # 4-row tiles on 2 warps
+    {"m_chunk": 1, "level_tile_rows": 4, "bt_ctas_per_sm": 4, "level_ring": 3},
 ]
 
 
@@ -73,12 +75,12 @@ def test_autotune_picks_a_candidate_and_keeps_results(dm_mod, prec):
     ctx = dm.Context(dm.DM_FP32 if prec == "fp32" else dm.DM_BF16)
     try:
         n_mtiles = -(-dm.dm_geometry(W, H, W, H)["n_patch0"] // 128)
-        assert dm.dm_tuned_config(ctx.ctx, W, H, W, H) == {"m_chunk": n_mtiles, "level_tile_rows": 16,
+        assert dm.dm_tuned_config(ctx.ctx, W, H, W, H) == {"m_chunk": n_mtiles, "level_tile_rows": 8,
                                                             "bt_ctas_per_sm": 8, "level_ring": 2}
         before = ctx.match(pr.img1, pr.img2).cpu().numpy()
         chosen = ctx.autotune(pr.img1, pr.img2)
         assert chosen["m_chunk"] in {-(-n_mtiles // k) for k in (1, 2, 3, 4, 6, 8)}
-        assert chosen["level_tile_rows"] in (0, 8, 16)
+        assert chosen["level_tile_rows"] in (0, 4, 8, 16)
         assert chosen["bt_ctas_per_sm"] in (2, 4, 8, 16, 32)
         assert chosen["level_ring"] in (2, 3)
         assert dm.dm_tuned_config(ctx.ctx, W, H, W, H) == chosen
