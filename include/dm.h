@@ -463,18 +463,18 @@ dm_status dm_set_batch_lanes(dm_ctx* ctx, int lanes);
  * default: every pair with its own launches). */
 dm_status dm_set_batch_wave(dm_ctx* ctx, int pairs);
 
-/* Autotuner of the batch shape: runs dm_match_batch on these pairs (twice
- * per candidate, timed with CUDA events on `stream`) for every wave width W in
+/* Autotuner of the batch shape: runs dm_match_batch on these pairs (once
+ * untimed, then twice timed with CUDA events on `stream`, per candidate) for every wave width W in
  * {1, 2, 3, 4, 6, 8} and lanes K in 1..4 with W K slices of lane_bytes within
  * ws_bytes (and W <= n, K <= the number of waves), and keeps the fastest
  * (a candidate must beat the best so far by 2 %) as the context's wave width
  * and lanes.  chosen (may be NULL) receives {W, K}.  Synchronises with the host
  * (not capturable); the pairs' outputs hold the matches of the last run.
- * DM_ENOMEM if ws_bytes is below one lane_bytes.  The measured choice at
- * 1024 x 436 (8 BF16 pairs): W = 1 on 2 lanes (55.6 pairs/s) against waves of
- * 2 on 2 lanes (53.8) and of 4 on one lane (52.0) -- there one pair's
- * kernels already fill the GPU and two lanes overlap one pair's latency-bound
- * steps with another's level 0; waves pay off where pairs are small. */
+ * DM_ENOMEM if ws_bytes is below one lane_bytes.  Measured at 1024 x 436 (8
+ * BF16 pairs, one graph): W = 1 on 2 lanes 61.6 pairs/s, waves of 2 on 2
+ * lanes 60.1, W = 1 on 3 lanes 58.1, waves of 4 on one lane 57.9, W = 1 on
+ * one lane 57.6 -- there one pair's kernels already fill the GPU and two
+ * lanes overlap one pair's latency-bound steps with another's level 0. */
 dm_status dm_autotune_batch(dm_ctx* ctx, int n, const dm_pair* pairs, void* d_ws, size_t ws_bytes, int* chosen,
                             void* stream);
 
@@ -493,8 +493,9 @@ dm_status dm_autotune_batch(dm_ctx* ctx, int n, const dm_pair* pairs, void* d_ws
  *   chosen[2]  CTAs per SM of the backtracking expansion kernels (2..32);
  *   chosen[3]  child-window columns in the level kernel's ring (3 or 2).
  * Every candidate computes identical results; only the time differs.  Each
- * candidate runs twice, timed with CUDA events; a candidate replaces the
- * current choice only when it is at least 2% faster.  Later
+ * candidate runs three times (after one untimed run of the default), timed
+ * with CUDA events, best of three; a candidate replaces the current choice
+ * only when it is at least 3% faster.  Later
  * dm_correlate_pyramid / dm_match / dm_match_batch calls on pairs of these
  * sizes use the choice.  d_img1, d_img2, d_ws as for dm_match (d_ws is used as
  * scratch).  Synchronises `stream` (cannot be captured: tune before capturing
