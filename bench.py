@@ -783,12 +783,12 @@ def _measure_batch_uniform(dm, torch, dist, ctx, a, world, local, rank, W, H, np
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # current kernels, from one ncu capture of one 1024x436 BF16 pair (one pass per
-# launch; profiles/ has the command): level 0 2.107 GB read + 16.243 GB written;
-# the level pass (k_level_sweep for levels 1-4, k_level_stream for 5-7,
-# k_level_top) 18.932 GB read + 5.120 GB written.  The FP32 level-0 kernel is
+# launch; profiles/ has the command): level 0 2.038 GB read + 16.235 GB written;
+# the level pass (k_level_sweep with 8-row tiles for levels 1-4, k_level_stream
+# for 5-7, k_level_top) 20.510 GB read + 5.122 GB written.  The FP32 level-0 kernel is
 # the capture at 512x224 scaled by the number of pooled outputs (x 15.1); FP8
 # has no capture of its current epilogue (None).
-TRAFFIC_1024x436 = {"level0_bf16": 18.35e9, "level0_fp8": None, "level0_fp32": 14.8e9, "levels": 24.05e9}
+TRAFFIC_1024x436 = {"level0_bf16": 18.27e9, "level0_fp8": None, "level0_fp32": 14.8e9, "levels": 25.63e9}
 
 
 def _prec_code(dm, name):
