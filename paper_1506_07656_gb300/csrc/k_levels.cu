@@ -14,7 +14,7 @@
 // amount of arithmetic per stored output (~4 averages of 4 values, a 9-way
 // max with argmax, one power).  A CTA owns a tile of 32 x TH pooled outputs
 // (TH = 8 by default on 4 warps; 16 on 8 or 4 on 2, autotuned) of a run of up
-// to 16 lattice patches on one row,
+// to 32 lattice patches on one row,
 // spaced so that the right child column of one patch is the left child column
 // of the next: the child windows (72 x (2 TH + 1) floats, which cover both
 // shifts +-1 of a shared column) are staged in shared memory by 3-D TMA tensor
@@ -156,9 +156,10 @@ __device__ __forceinline__ float2 avg_two(const float* lt, const float* lb, cons
 // iy - e, iy + e' likewise; the stride S = 2^(l-1) (1 at level 1) makes the
 // right column of one patch the left column of the next, so the run needs
 // run + 1 columns of two child windows each instead of 4 windows per patch.
-// Runs of 16 (measured at 1024x436: 3% faster than 8; shorter runs on the
-// small top levels gained nothing).
-__host__ __device__ inline int level_run(int) { return 16; }
+// Runs of 32 (measured at 1024x436 with 8-row tiles, levels stage: 8 8.09 ms,
+// 16 7.79, 32 7.66, 48 7.67, 64 7.63; 32 keeps more CTAs for small images;
+// shorter runs on the small top levels gained nothing).
+__host__ __device__ inline int level_run(int) { return 32; }
 
 __device__ __forceinline__ void child_col_row(const DmGeom& g, int l, int ix, int iy, int* cx_left, int* cy_top, int* step) {
     if (l == 1) { *cx_left = ix - 1; *cy_top = iy - 1; *step = 1; }
