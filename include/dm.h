@@ -468,7 +468,10 @@ dm_status dm_set_batch_wave(dm_ctx* ctx, int pairs);
  * {1, 2, 3, 4, 6, 8} and lanes K in 1..4 with W K slices of lane_bytes within
  * ws_bytes (and W <= n, K <= the number of waves), and keeps the fastest
  * (a candidate must beat the best so far by 2 %) as the context's wave width
- * and lanes.  chosen (may be NULL) receives {W, K}.  Synchronises with the host
+ * and lanes; then, in that shape, it times the backtracking expansions at 4,
+ * 8 and 16 CTAs per SM for all the batch's pair sizes together (concurrent
+ * lanes share the SMs) and keeps the fastest in their launch shapes (or each
+ * size's own).  chosen (may be NULL) receives {W, K}.  Synchronises with the host
  * (not capturable); the pairs' outputs hold the matches of the last run.
  * DM_ENOMEM if ws_bytes is below one lane_bytes.  Measured at 1024 x 436 (8
  * BF16 pairs, one graph): W = 1 on 2 lanes 61.6 pairs/s, waves of 2 on 2

@@ -1389,6 +1389,52 @@ dm_status dm_autotune_batch(dm_ctx* ctx, int n, const dm_pair* pairs, void* d_ws
         }
         if (rs != DM_OK) break;
     }
+    // then, in that shape, the CTAs per SM of the backtracking expansions for all the
+    // batch's pair sizes together: concurrent lanes share the SMs, so the grid
+    // that is best for a pair alone need not be best here
+    if (rs == DM_OK) {
+        ctx->wave = best_w;
+        ctx->lanes = best_k;
+        std::vector<std::array<int, 4>> sizes;
+        for (int j = 0; j < n; j++) {
+            const std::array<int, 4> key{pairs[j].W1, pairs[j].H1, pairs[j].W2, pairs[j].H2};
+            if (std::find(sizes.begin(), sizes.end(), key) == sizes.end()) sizes.push_back(key);
+        }
+        std::vector<DmTune> tunes0;
+        for (const auto& key : sizes) {
+            DmGeom g;
+            dm_make_geom(key[0], key[1], key[2], key[3], &g);
+            tunes0.push_back(tune_for(ctx, g));
+        }
+        auto set_mult = [&](int m) {
+            std::lock_guard<std::mutex> lk(ctx->tune_mu);
+            for (size_t i = 0; i < sizes.size(); i++) {
+                DmTune t = tunes0[i];
+                if (m > 0) t.bt_mult = m;
+                ctx->tuned[sizes[i]] = t;
+            }
+        };
+        int best_m = 0;                      // 0: each size keeps its own
+        for (int m : {4, 8, 16}) {
+            set_mult(m);
+            float ms = -1.0f;
+            rs = dm_match_batch(ctx, n, pairs, d_ws, (size_t)best_w * best_k * lane, st);
+            for (int r = 0; r < 2 && rs == DM_OK; r++) {
+                cudaEventRecord(e0, st);
+                rs = dm_match_batch(ctx, n, pairs, d_ws, (size_t)best_w * best_k * lane, st);
+                cudaEventRecord(e1, st);
+                float t = -1.0f;
+                if (rs == DM_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&t, e0, e1);
+                if (t >= 0.0f && (ms < 0.0f || t < ms)) ms = t;
+            }
+            if (rs != DM_OK) break;
+            if (ms >= 0.0f && ms < 0.98f * best_ms) {
+                best_ms = ms;
+                best_m = m;
+            }
+        }
+        set_mult(best_m);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rs != DM_OK) {
