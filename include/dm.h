@@ -362,8 +362,8 @@ dm_status dm_inject_fault(dm_ctx* ctx, int kind, long long arg);
  * The backward follows the forward exactly: through the power (Eq. 11), the
  * shifted average (Eq. 12), the max-pooling argmax saved by the forward
  * (Eq. 9) and the level-0 correlation (Eq. 3-4), whose values at the argmax
- * positions are recomputed instead of stored; level 0 is processed in chunks
- * of patches so that its dense block stays below 1 GiB.  All sums have a
+ * positions are recomputed instead of stored; both level-0 products are
+ * gathers over the argmax positions with a nonzero gradient.  All sums have a
  * fixed order: the gradient is deterministic.  d_ws >= dm_grad_workspace_bytes. */
 dm_status dm_grad_workspace_bytes(const dm_ctx* ctx, int W1, int H1, int W2, int H2, size_t* bytes);
 dm_status dm_loss_grad(dm_ctx* ctx, const dm_pyramid* pyr, const float* d_desc1, const float* d_desc2, void* d_ws,

@@ -226,8 +226,7 @@ struct DmGradLayout {
     size_t dP[DM_MAXL];           // f32 pooled layout, l = 0..L-1
     size_t Am, Bm;                // f32 [n0][144] patch vectors, [W2*H2][144] image-2 im2col
     size_t G1, Gim;               // f32 [n0][144], [W2*H2][144] level-0 products
-    size_t dC;                    // f32 [chunk][W2*H2] dense dC0 block
-    int chunk;                    // patches per level-0 chunk
+    size_t box;                   // int4 [n0] bounding box of each patch's level-0 argmax positions
     size_t bytes;
 };
 

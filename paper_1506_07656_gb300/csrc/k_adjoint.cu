@@ -12,11 +12,12 @@
 // Level 0 is recomputed rather than stored: the unrectified C0 at an argmax
 // position is one 144-term dot product.  Of the two level-0 products
 //   G1[p][k] = (1/16) sum_t dC0(p,t) b_t[k],   Gim[t][k] = (1/16) sum_p dC0(p,t) a_p[k]
-// G1 is a gather over the nonzeros of dC0 (at most one per pooled output),
-// one warp per patch; Gim is a dense FP32 GEMM over chunks of patches (the
-// dense dC0 block of a chunk is the only large temporary).  Then G1 is
-// scattered onto the atomic windows of I and Gim gathered (col2im) onto the
-// pixels of I'.
+// both are gathers over the nonzeros of dC0 (at most one per pooled output):
+// G1 one warp per patch, which also leaves each pooled output's coefficient
+// in place of dP0 and the bounding box of the patch's argmax positions; Gim
+// one warp per row segment of 30 positions of I', which visits, in patch
+// order, the patches whose box meets the segment.  Then G1 is scattered onto
+// the atomic windows of I and Gim gathered (col2im) onto the pixels of I'.
 #include "dm_internal.cuh"
 
 namespace {
@@ -191,20 +192,19 @@ __global__ void k_adj_im2col(DmGeom g, const float* __restrict__ d1, const float
 // nonzeros in order; lane j holds k = j + 32 i (i < 5) of the accumulator and
 // of the dot product C0 = (1/16) a_p . b_t (lane partials, then a fixed
 // butterfly sum).  Deterministic: a fixed order throughout.
-// It also writes the same coefficients into row p - p0 of the dense dC0 block
-// of patches [p0, p0 + pc) (zeroed before), added in the same order where two
-// pooled positions share an argmax position, for the other product.
-__global__ void __launch_bounds__(256) k_adj_g1_sparse(DmGeom g, int p0, int pc, const float* __restrict__ dP0,
+// Each nonzero dP0(p, r) is replaced by its coefficient c = dP0(p, r) *
+// lam C0(p, t_r)^(lam-1) (0 where the argmax lies outside I'), and box[p]
+// receives the bounding box (x0, y0, x1, y1) of the patch's positions t_r
+// (empty: x0 > x1), for the transposed product.
+__global__ void __launch_bounds__(256) k_adj_g1_sparse(DmGeom g, float* __restrict__ dP0,
                                                       const unsigned char* __restrict__ amax0,
                                                       const float* __restrict__ Am, const float* __restrict__ Bm,
-                                                      float lam, float* __restrict__ G1, float* __restrict__ dC) {
+                                                      float lam, float* __restrict__ G1, int4* __restrict__ box) {
     const int lane = threadIdx.x & 31;
-    const int pl = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (pl >= pc) return;
-    const int p = p0 + pl;
-    float* dcrow = dC + (long long)pl * g.W2 * g.H2;
+    const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (p >= g.npatch(0)) return;
     const int pw = g.dw[1], ph = g.dh[1], pitch = g.pitch(1), W2 = g.W2;
-    const float* dp = dP0 + (long long)p * g.psize(1);
+    float* dp = dP0 + (long long)p * g.psize(1);
     const unsigned char* am = amax0 + (long long)p * g.psize(1);
     float a[5], acc[5];
 #pragma unroll
@@ -213,22 +213,33 @@ __global__ void __launch_bounds__(256) k_adj_g1_sparse(DmGeom g, int p0, int pc,
         a[i] = k < 144 ? __ldg(Am + (long long)p * 144 + k) : 0.0f;
         acc[i] = 0.0f;
     }
+    int bx0 = INT_MAX, by0 = INT_MAX, bx1 = -1, by1 = -1;
     const int n = pw * ph;
     for (int r0 = 0; r0 < n; r0 += 32) {
         const int r = r0 + lane;
         float d = 0.0f;
         int t = 0;
+        long long o = 0;
+        bool had = false;
         if (r < n) {
             const int rx = r % pw, ry = r / pw;
-            d = dp[(long long)ry * pitch + rx];
-            if (d != 0.0f) {
-                const int code = am[(long long)ry * pitch + rx];
+            o = (long long)ry * pitch + rx;
+            d = dp[o];
+            had = d != 0.0f;
+            if (had) {
+                const int code = am[o];
                 const int tx = 2 * rx + code % 3 - 1, ty = 2 * ry + code / 3 - 1;
                 // (the forward's pooling only ever points inside I')
-                if (code <= 8 && tx >= 0 && ty >= 0 && tx < W2 && ty < g.H2) t = ty * W2 + tx;
-                else d = 0.0f;
+                if (code <= 8 && tx >= 0 && ty >= 0 && tx < W2 && ty < g.H2) {
+                    t = ty * W2 + tx;
+                    bx0 = min(bx0, tx); bx1 = max(bx1, tx);
+                    by0 = min(by0, ty); by1 = max(by1, ty);
+                } else {
+                    d = 0.0f;
+                }
             }
         }
+        float myc = 0.0f;
         unsigned int nz = __ballot_sync(0xffffffffu, d != 0.0f);
         while (nz) {
             const int src = __ffs(nz) - 1;
@@ -244,92 +255,107 @@ __global__ void __launch_bounds__(256) k_adj_g1_sparse(DmGeom g, int p0, int pc,
                 part = __fmaf_rn(a[i], bk[i], part);
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) part = __fadd_rn(part, __shfl_xor_sync(0xffffffffu, part, o));
+            for (int o2 = 16; o2 > 0; o2 >>= 1) part = __fadd_rn(part, __shfl_xor_sync(0xffffffffu, part, o2));
             const float c = __fmul_rn(dv, dpow(__fmul_rn(part, 0.0625f), lam));   // this r's share of dC0(p, t)
             const float w = __fmul_rn(c, 0.0625f);
 #pragma unroll
             for (int i = 0; i < 5; i++) acc[i] = __fmaf_rn(w, bk[i], acc[i]);
-            if (lane == 0) dcrow[tv] = __fadd_rn(dcrow[tv], c);
+            if (lane == src) myc = c;
         }
+        if (had) dp[o] = myc;
     }
 #pragma unroll
     for (int i = 0; i < 5; i++) {
         const int k = lane + 32 * i;
         if (k < 144) G1[(long long)p * 144 + k] = acc[i];
     }
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+        bx0 = min(bx0, __shfl_xor_sync(0xffffffffu, bx0, o2));
+        by0 = min(by0, __shfl_xor_sync(0xffffffffu, by0, o2));
+        bx1 = max(bx1, __shfl_xor_sync(0xffffffffu, bx1, o2));
+        by1 = max(by1, __shfl_xor_sync(0xffffffffu, by1, o2));
+    }
+    if (lane == 0) box[p] = make_int4(bx0, by0, bx1, by1);
 }
 
-// C[m][n] (+)= alpha * sum_k A[k][m] B[k][n] for n < 144: the transposed
-// product of the level-0 backward (m = position of I', k = patch, n = the 144
-// window entries).  128 x 144 tiles, K steps of 16, 256 threads, each 8 rows
-// (m = 8 tm ..) x 9 columns (n = tn + 16 j) of the tile, the next K step's
-// tiles prefetched into registers while the current one is multiplied.
-__global__ void __launch_bounds__(256, 2) k_sgemm_tn144(int M, int K, float alpha, const float* __restrict__ A, long long lda,
-                                                    const float* __restrict__ B, float* __restrict__ C, int accum) {
-    constexpr int BM = 128, BN = 144, BK = 16;
-    __shared__ __align__(16) float As[BK][BM];
-    __shared__ float Bs[BK][BN];
-    const int m0 = blockIdx.x * BM;
-    const int tid = threadIdx.x;
-    const int tm = tid >> 4, tn = tid & 15;
-    float acc[8][9] = {};
-    float ra[8], rb[9];
-    auto fetch = [&](int k0) {
-#pragma unroll
-        for (int e = 0; e < 8; e++) {
-            const int idx = tid + 256 * e, kk = idx >> 7, mm = idx & 127;
-            const int gm = m0 + mm, gk = k0 + kk;
-            ra[e] = (gm < M && gk < K) ? __ldg(A + (long long)gk * lda + gm) : 0.0f;
+// Gim[t][k] = (1/16) sum over the patches p (ascending) and their pooled
+// positions r (row-major) with argmax position t of c(p, r) * a_p[k], c the
+// coefficients left by k_adj_g1_sparse -- the transposed product dC0^T * A
+// restricted to the nonzeros of dC0.  One warp per segment of GSEG positions
+// (tx0 .. tx0+GSEG-1, ty) of I': the pooled outputs that can point into it
+// are rows ty>>1 .. (ty+1)>>1 and columns tx0/2 .. tx0/2+15 (lanes 0-15: the
+// first row, 16-31: the second).  The warp finds, 32 boxes at a time, the
+// patches whose box meets the segment, reads their candidate outputs, and
+// adds each hit's c * a_p into the segment's [GSEG][144] accumulator in
+// shared memory (lane j owns k = j + 32 i): a fixed order per position.
+constexpr int GSEG = 30;
+constexpr int GIM_WARPS = 2;
+
+__global__ void __launch_bounds__(32 * GIM_WARPS) k_adj_gim(DmGeom g, const float* __restrict__ cP,
+                                                           const unsigned char* __restrict__ amax0,
+                                                           const int4* __restrict__ box, const float* __restrict__ Am,
+                                                           float* __restrict__ Gim, int n_seg) {
+    __shared__ float gs[GIM_WARPS][GSEG * 144];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int seg = blockIdx.x * GIM_WARPS + warp;
+    if (seg >= n_seg) return;   // (no block-wide barrier below)
+    const int W2 = g.W2, n0 = g.npatch(0);
+    const int sxn = (W2 + GSEG - 1) / GSEG;
+    const int tx0 = (seg % sxn) * GSEG, ty = seg / sxn;
+    const int tx1 = min(tx0 + GSEG, W2) - 1;
+    float* G = gs[warp];
+    for (int i = lane; i < GSEG * 144; i += 32) G[i] = 0.0f;
+    const int pw = g.dw[1], ph = g.dh[1];
+    const long long psz = g.psize(1);
+    const int ry = (ty >> 1) + (lane >> 4), rx = tx0 / 2 + (lane & 15);
+    const bool cand = ry <= ((ty + 1) >> 1) && ry < ph && rx < pw;
+    const long long off = (long long)ry * g.pitch(1) + rx;
+    for (int pb = 0; pb < n0; pb += 32) {
+        bool meets = false;
+        if (pb + lane < n0) {
+            const int4 bb = __ldg(box + pb + lane);
+            meets = bb.x <= tx1 && bb.z >= tx0 && bb.y <= ty && bb.w >= ty;
         }
+        unsigned int m = __ballot_sync(0xffffffffu, meets);
+        while (m) {
+            const int q = pb + __ffs(m) - 1;
+            m &= m - 1;
+            float c = 0.0f;
+            int tl = -1;
+            if (cand) {
+                c = cP[(long long)q * psz + off];
+                if (c != 0.0f) {
+                    const int code = amax0[(long long)q * psz + off];
+                    const int tx = 2 * rx + code % 3 - 1, tyy = 2 * ry + code / 3 - 1;
+                    if (tyy == ty && tx >= tx0 && tx <= tx1) tl = tx - tx0;
+                }
+            }
+            unsigned int h = __ballot_sync(0xffffffffu, tl >= 0);
+            if (!h) continue;
+            float a[5];
 #pragma unroll
-        for (int e = 0; e < 9; e++) {
-            const int idx = tid + 256 * e, kk = idx / BN, nn = idx % BN;
-            const int gk = k0 + kk;
-            rb[e] = gk < K ? __ldg(B + (long long)gk * BN + nn) : 0.0f;
+            for (int i = 0; i < 5; i++) {
+                const int k = lane + 32 * i;
+                a[i] = k < 144 ? __ldg(Am + (long long)q * 144 + k) : 0.0f;
+            }
+            while (h) {
+                const int src = __ffs(h) - 1;
+                h &= h - 1;
+                const float cv = __shfl_sync(0xffffffffu, c, src);
+                const int t = __shfl_sync(0xffffffffu, tl, src);
+#pragma unroll
+                for (int i = 0; i < 5; i++) {
+                    const int k = lane + 32 * i;
+                    if (k < 144) G[t * 144 + k] = __fmaf_rn(cv, a[i], G[t * 144 + k]);
+                }
+            }
         }
-    };
-    auto stash = [&]() {
-#pragma unroll
-        for (int e = 0; e < 8; e++) {
-            const int idx = tid + 256 * e;
-            As[idx >> 7][idx & 127] = ra[e];
-        }
-#pragma unroll
-        for (int e = 0; e < 9; e++) {
-            const int idx = tid + 256 * e;
-            Bs[idx / BN][idx % BN] = rb[e];
-        }
-    };
-    fetch(0);
-    for (int k0 = 0; k0 < K; k0 += BK) {
-        stash();
-        __syncthreads();
-        if (k0 + BK < K) fetch(k0 + BK);
-#pragma unroll
-        for (int kk = 0; kk < BK; kk++) {
-            const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][8 * tm]);
-            const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][8 * tm + 4]);
-            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            float bv[9];
-#pragma unroll
-            for (int j = 0; j < 9; j++) bv[j] = Bs[kk][tn + 16 * j];
-#pragma unroll
-            for (int i = 0; i < 8; i++)
-#pragma unroll
-                for (int j = 0; j < 9; j++) acc[i][j] = __fmaf_rn(av[i], bv[j], acc[i][j]);
-        }
-        __syncthreads();
     }
-#pragma unroll
-    for (int i = 0; i < 8; i++) {
-        const int gm = m0 + 8 * tm + i;
-        if (gm >= M) continue;
-#pragma unroll
-        for (int j = 0; j < 9; j++) {
-            float* o = C + (long long)gm * BN + tn + 16 * j;
-            const float v = __fmul_rn(alpha, acc[i][j]);
-            *o = accum ? __fadd_rn(*o, v) : v;
-        }
+    __syncwarp();
+    for (int i = lane; i < GSEG * 144; i += 32) {
+        const int tx = tx0 + i / 144;
+        if (tx <= tx1) Gim[((long long)ty * W2 + tx) * 144 + i % 144] = __fmul_rn(0.0625f, G[i]);
     }
 }
 
@@ -378,13 +404,7 @@ void dm_grad_layout(const DmGeom& g, DmGradLayout* o) {
     o->Bm = off; off = dm_align(off + T * 144 * 4);
     o->G1 = off; off = dm_align(off + (size_t)g.npatch(0) * 144 * 4);
     o->Gim = off; off = dm_align(off + T * 144 * 4);
-    // dense dC0 block of one chunk of patches: at most 1 GiB, at least one patch
-    size_t pc = (size_t)1 << 30;
-    pc /= (T * 4);
-    if (pc < 1) pc = 1;
-    if (pc > (size_t)g.npatch(0)) pc = (size_t)g.npatch(0);
-    o->chunk = (int)pc;
-    o->dC = off; off = dm_align(off + pc * T * 4);
+    o->box = off; off = dm_align(off + (size_t)g.npatch(0) * sizeof(int4));
     o->bytes = off;
 }
 
@@ -419,21 +439,14 @@ cudaError_t dm_launch_loss_grad(const DmGeom& g, const dm_pyramid& py, const flo
     float* Bm = reinterpret_cast<float*>(ws + gl.Bm);
     float* G1 = reinterpret_cast<float*>(ws + gl.G1);
     float* Gim = reinterpret_cast<float*>(ws + gl.Gim);
-    float* dC = reinterpret_cast<float*>(ws + gl.dC);
+    int4* box = reinterpret_cast<int4*>(ws + gl.box);
+    float* dP0 = reinterpret_cast<float*>(ws + gl.dP[0]);
     const long long n0 = g.npatch(0), T = (long long)g.W2 * g.H2;
     k_adj_im2col<<<nb((n0 + T) * 144, 256), 256, 0, st>>>(g, d1, d2, Am, Bm);
-    launches++;
-    for (long long p0 = 0; p0 < n0; p0 += gl.chunk) {
-        const int pc = (int)(n0 - p0 < gl.chunk ? n0 - p0 : gl.chunk);
-        // the chunk's dC0 rows and G1 rows from the nonzeros of dC0
-        cudaError_t e = cudaMemsetAsync(dC, 0, (size_t)pc * T * sizeof(float), st);
-        if (e != cudaSuccess) return e;
-        k_adj_g1_sparse<<<nb(pc, 8), 256, 0, st>>>(g, (int)p0, pc, reinterpret_cast<const float*>(ws + gl.dP[0]),
-                                                   py.amax[0], Am, Bm, lam, G1, dC);
-        // Gim (+)= (1/16) dC^T [T x pc] * Am[p0 .. p0+pc) [pc x 144]
-        k_sgemm_tn144<<<nb(T, 128), 256, 0, st>>>((int)T, pc, 0.0625f, dC, T, Am + p0 * 144, Gim, p0 != 0);
-        launches += 2;
-    }
+    k_adj_g1_sparse<<<nb(n0, 8), 256, 0, st>>>(g, dP0, py.amax[0], Am, Bm, lam, G1, box);
+    const long long n_seg = (long long)((g.W2 + GSEG - 1) / GSEG) * g.H2;
+    k_adj_gim<<<nb(n_seg, GIM_WARPS), 32 * GIM_WARPS, 0, st>>>(g, dP0, py.amax[0], box, Am, Gim, (int)n_seg);
+    launches += 3;
     k_adj_g1<<<nb((long long)g.W1 * g.H1 * 9, 256), 256, 0, st>>>(g, G1, g1);
     k_adj_g2<<<nb(T * 9, 256), 256, 0, st>>>(g, Gim, g2);
     launches += 2;
