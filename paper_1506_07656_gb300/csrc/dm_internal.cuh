@@ -227,6 +227,9 @@ struct DmGradLayout {
     size_t Am, Bm;                // f32 [n0][144] patch vectors, [W2*H2][144] image-2 im2col
     size_t G1, Gim;               // f32 [n0][144], [W2*H2][144] level-0 products
     size_t box;                   // int4 [n0] bounding box of each patch's level-0 argmax positions
+    size_t boxA[DM_MAXL + 1];     // int4 [npatch(l)] support box of dA_l per patch, l = 1..L
+    size_t boxP[DM_MAXL];         // int4 [npatch(l)] support box of dP_l per patch, l = 0..L-1
+    size_t par, nch;              // int4 per child: its parents and their divisors (one level at a time)
     size_t bytes;
 };
 

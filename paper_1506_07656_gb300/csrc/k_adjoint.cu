@@ -59,14 +59,14 @@ __device__ __forceinline__ float dpow(float x, float lam) {   // d(x^lam)/dx for
 // dA_L = d(A^lam)/dA at that position (zero elsewhere).
 __global__ void k_adj_top(DmGeom g, const unsigned char* __restrict__ vL, const unsigned char* __restrict__ vprev,
                           const float* __restrict__ top, const float* __restrict__ prev, float lam, int comp,
-                          float* __restrict__ dA, float* __restrict__ parts) {
+                          float* __restrict__ dA, float* __restrict__ parts, int4* __restrict__ boxL) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const int L = g.L;
     if (p >= g.npatch(L)) return;
     const int nq = g.dw[L] * g.dh[L];
     float* d = dA + (long long)p * nq;
     for (int q = 0; q < nq; q++) d[q] = 0.0f;
-    if (!vL[p]) { parts[p] = 0.0f; return; }
+    if (!vL[p]) { parts[p] = 0.0f; boxL[p] = make_int4(0, 0, -1, -1); return; }
     const float* t = top + (long long)p * nq;
     float best = -INFINITY;
     int qb = 0;
@@ -76,6 +76,7 @@ __global__ void k_adj_top(DmGeom g, const unsigned char* __restrict__ vL, const 
     int n;
     const float a = level_average(g, L, p, qb % g.dw[L], qb / g.dw[L], vprev, prev, comp != 0, &n);
     d[qb] = dpow(a, lam);
+    boxL[p] = make_int4(qb % g.dw[L], qb / g.dw[L], qb % g.dw[L], qb / g.dw[L]);
 }
 
 // Deterministic sum of the per-patch maxima (one block).
@@ -92,74 +93,150 @@ __global__ void k_adj_loss(const float* __restrict__ parts, int n, float* __rest
     if (threadIdx.x == 0) *loss = (float)acc[0];
 }
 
+// Parent i (0..3) of child c at level l (c at level l - 1), or -1 where the
+// child is not valid, the parent lies outside the lattice or is not valid;
+// *n = the parent's number of valid children (the divisor of its average).
+__device__ int adj_parent(const DmGeom& g, int l, int c, int i, const unsigned char* vcur,
+                          const unsigned char* vprev, int* n) {
+    *n = 0;
+    if (!vprev[c]) return -1;
+    const int cx = l == 1 ? c % g.P0x : c % g.Lx, cy = l == 1 ? c / g.P0x : c / g.Lx;
+    const int ox = (i >= 2) ? 1 : -1, oy = (i & 1) ? 1 : -1;
+    int ix, iy;
+    if (l == 1) { ix = cx + (1 - ox) / 2; iy = cy + (1 - oy) / 2; }
+    else { const int s = 1 << (l - 2); ix = cx - ox * s; iy = cy - oy * s; }
+    if (ix < 0 || iy < 0 || ix >= g.Lx || iy >= g.Ly) return -1;
+    const int p = iy * g.Lx + ix;
+    if (!vcur[p]) return -1;
+    for (int j = 0; j < 4; j++) {
+        const int cj = dm_child(g, l, ix, iy, j);
+        if (cj >= 0 && vprev[cj]) (*n)++;
+    }
+    return p;
+}
+
+__device__ __forceinline__ bool in_box(const int4& b, int x, int y) {
+    return x >= b.x && x <= b.z && y >= b.y && y <= b.w;
+}
+
+// Support boxes of the gradient, one step down from level l: for child c,
+// par[c] / nch[c] receive its four parents (adj_parent) and their divisors;
+// boxP[c] bounds the pooled positions r where dP_{l-1}(c, r) can be nonzero
+// (the parents' boxes of dA_l shifted by their offsets o_i), and, where
+// m = l - 1 >= 1, boxAm[c] bounds the positions t = 2r + (-1..1) of domain m
+// where dA_m(c, t) can be nonzero.  Supersets: outside them every term of the
+// gathers below is an exact zero, so skipping them leaves every sum unchanged.
+__global__ void k_adj_box(DmGeom g, int l, const unsigned char* __restrict__ vcur, const unsigned char* __restrict__ vprev,
+                          const int4* __restrict__ boxA, int4* __restrict__ boxP, int4* __restrict__ boxAm,
+                          int4* __restrict__ par, int4* __restrict__ nch) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.npatch(l - 1)) return;
+    int x0 = INT_MAX, y0 = INT_MAX, x1 = -1, y1 = -1;
+    int pi[4], ni[4];
+    for (int i = 0; i < 4; i++) pi[i] = adj_parent(g, l, c, i, vcur, vprev, &ni[i]);
+    par[c] = make_int4(pi[0], pi[1], pi[2], pi[3]);
+    nch[c] = make_int4(ni[0], ni[1], ni[2], ni[3]);
+    for (int i = 0; i < 4; i++) {
+        const int p = pi[i];
+        if (p < 0) continue;
+        const int4 b = boxA[p];
+        if (b.x > b.z || b.y > b.w) continue;
+        const int ox = (i >= 2) ? 1 : -1, oy = (i & 1) ? 1 : -1;
+        x0 = min(x0, b.x + ox); x1 = max(x1, b.z + ox);
+        y0 = min(y0, b.y + oy); y1 = max(y1, b.w + oy);
+    }
+    x0 = max(x0, 0); y0 = max(y0, 0);
+    x1 = min(x1, g.dw[l] - 1); y1 = min(y1, g.dh[l] - 1);
+    boxP[c] = make_int4(x0, y0, x1, y1);
+    if (boxAm) {
+        const int m = l - 1;
+        if (x0 > x1 || y0 > y1) boxAm[c] = make_int4(0, 0, -1, -1);
+        else boxAm[c] = make_int4(max(2 * x0 - 1, 0), max(2 * y0 - 1, 0), min(2 * x1 + 1, g.dw[m] - 1),
+                                  min(2 * y1 + 1, g.dh[m] - 1));
+    }
+}
+
+constexpr int ADJ_PPT = 8;   // positions per thread of the per-level passes
+
 // dP_{l-1}(c, r) = sum over the parents p_i = c - 2^l o_i of c (i = 0..3, in
-// order) of dA_l(p_i, r - o_i) / n(p_i).  Grid: (positions of domain l, child).
-__global__ void k_adj_pooled(DmGeom g, int l, const unsigned char* __restrict__ vcur,
-                             const unsigned char* __restrict__ vprev, const float* __restrict__ dA,
-                             float* __restrict__ dP) {
+// order) of dA_l(p_i, r - o_i) / n(p_i).  Grid: (runs of 128 * ADJ_PPT
+// positions of domain l, child); par / nch from k_adj_box.  Positions outside
+// the child's support box, and parent positions outside the parent's,
+// contribute exact zeros and are not read.
+__global__ void __launch_bounds__(128) k_adj_pooled(DmGeom g, int l, const float* __restrict__ dA, float* __restrict__ dP,
+                                                    const int4* __restrict__ boxA, const int4* __restrict__ boxP,
+                                                    const int4* __restrict__ par, const int4* __restrict__ nch) {
     const int c = blockIdx.y;
     const int mw = g.dw[l], mh = g.dh[l], pitch = g.pitch(l);
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= mw * mh) return;
-    const int rx = r % mw, ry = r / mw;
-    float sum = 0.0f;
-    if (vprev[c]) {
-        const int cx = l == 1 ? c % g.P0x : c % g.Lx, cy = l == 1 ? c / g.P0x : c / g.Lx;
+    const int n = mw * mh;
+    float* out = dP + (long long)c * g.psize(l);
+    const int4 bp = boxP[c];
+    const int4 pp = par[c], nn = nch[c];
+    const int pa[4] = {pp.x, pp.y, pp.z, pp.w};
+    const int na[4] = {nn.x, nn.y, nn.z, nn.w};
+    const int r0 = blockIdx.x * (128 * ADJ_PPT) + threadIdx.x;
+#pragma unroll 2
+    for (int j = 0; j < ADJ_PPT; j++) {
+        const int r = r0 + 128 * j;
+        if (r >= n) break;
+        const int rx = r % mw, ry = r / mw;
+        float sum = 0.0f;
+        if (in_box(bp, rx, ry)) {
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
-            const int ox = (i >= 2) ? 1 : -1, oy = (i & 1) ? 1 : -1;
-            int ix, iy;
-            if (l == 1) { ix = cx + (1 - ox) / 2; iy = cy + (1 - oy) / 2; }
-            else { const int s = 1 << (l - 2); ix = cx - ox * s; iy = cy - oy * s; }
-            if (ix < 0 || iy < 0 || ix >= g.Lx || iy >= g.Ly) continue;
-            const int p = iy * g.Lx + ix;
-            if (!vcur[p]) continue;
-            const int qx = rx - ox, qy = ry - oy;
-            if (qx < 0 || qy < 0 || qx >= mw || qy >= mh) continue;
-            int n = 0;
-            for (int j = 0; j < 4; j++) {
-                int cj = dm_child(g, l, ix, iy, j);
-                if (cj >= 0 && vprev[cj]) n++;
+            for (int i = 0; i < 4; i++) {
+                const int p = pa[i];
+                if (p < 0) continue;
+                const int ox = (i >= 2) ? 1 : -1, oy = (i & 1) ? 1 : -1;
+                const int qx = rx - ox, qy = ry - oy;
+                if (qx < 0 || qy < 0 || qx >= mw || qy >= mh) continue;
+                if (!in_box(boxA[p], qx, qy)) continue;
+                const float d = dA[((long long)p * mh + qy) * mw + qx];
+                if (d != 0.0f) sum = __fadd_rn(sum, __fdiv_rn(d, (float)na[i]));
             }
-            const float d = dA[((long long)p * mh + qy) * mw + qx];
-            if (d != 0.0f) sum = __fadd_rn(sum, __fdiv_rn(d, (float)n));
         }
+        out[(long long)ry * pitch + rx] = sum;
     }
-    dP[(long long)c * g.psize(l) + (long long)ry * pitch + rx] = sum;
 }
 
 // dA_{m}(c, t) for m = l-1 >= 1: sum over the pooled positions r whose argmax
 // is t (r = floor/ceil(t/2) per axis, ascending) of dP_m(c, r) * lam A^(lam-1),
 // A the unrectified average at t.  Grid: (positions of domain m, patch).
-__global__ void k_adj_unpool(DmGeom g, int m, const unsigned char* __restrict__ vm, const unsigned char* __restrict__ vprev,
-                             const float* __restrict__ prev, const float* __restrict__ dP,
-                             const unsigned char* __restrict__ amax, float lam, int comp, float* __restrict__ dA) {
+__global__ void __launch_bounds__(128) k_adj_unpool(DmGeom g, int m, const unsigned char* __restrict__ vm,
+                                                    const unsigned char* __restrict__ vprev,
+                                                    const float* __restrict__ prev, const float* __restrict__ dP,
+                                                    const unsigned char* __restrict__ amax, float lam, int comp,
+                                                    float* __restrict__ dA, const int4* __restrict__ boxAm) {
     const int c = blockIdx.y;
     const int tw = g.dw[m], th = g.dh[m];
     const int pw = g.dw[m + 1], ph = g.dh[m + 1], pitch = g.pitch(m + 1);
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= tw * th) return;
-    const int tx = t % tw, ty = t / tw;
-    float sum = 0.0f;
-    if (vm[c]) {
-        float dsum = 0.0f;
-        for (int ry = ty >> 1; ry <= (ty + 1) >> 1; ry++) {
-            if (ry >= ph) continue;
-            for (int rx = tx >> 1; rx <= (tx + 1) >> 1; rx++) {
-                if (rx >= pw) continue;
-                const long long o = (long long)c * g.psize(m + 1) + (long long)ry * pitch + rx;
-                const int code = amax[o];
-                if (2 * rx + code % 3 - 1 != tx || 2 * ry + code / 3 - 1 != ty) continue;
-                dsum = __fadd_rn(dsum, dP[o]);
+    const int4 bb = boxAm[c];
+    const bool live = vm[c] != 0;
+    const int t0 = blockIdx.x * (128 * ADJ_PPT) + threadIdx.x;
+    for (int j = 0; j < ADJ_PPT; j++) {
+        const int t = t0 + 128 * j;
+        if (t >= tw * th) break;
+        const int tx = t % tw, ty = t / tw;
+        float sum = 0.0f;
+        if (live && in_box(bb, tx, ty)) {
+            float dsum = 0.0f;
+            for (int ry = ty >> 1; ry <= (ty + 1) >> 1; ry++) {
+                if (ry >= ph) continue;
+                for (int rx = tx >> 1; rx <= (tx + 1) >> 1; rx++) {
+                    if (rx >= pw) continue;
+                    const long long o = (long long)c * g.psize(m + 1) + (long long)ry * pitch + rx;
+                    const int code = amax[o];
+                    if (2 * rx + code % 3 - 1 != tx || 2 * ry + code / 3 - 1 != ty) continue;
+                    dsum = __fadd_rn(dsum, dP[o]);
+                }
+            }
+            if (dsum != 0.0f) {
+                int n;
+                const float a = level_average(g, m, c, tx, ty, vprev, prev, comp != 0, &n);
+                sum = __fmul_rn(dsum, dpow(a, lam));
             }
         }
-        if (dsum != 0.0f) {
-            int n;
-            const float a = level_average(g, m, c, tx, ty, vprev, prev, comp != 0, &n);
-            sum = __fmul_rn(dsum, dpow(a, lam));
-        }
+        dA[((long long)c * th + ty) * tw + tx] = sum;
     }
-    dA[((long long)c * th + ty) * tw + tx] = sum;
 }
 
 // Patch vectors (A, [n0][144]) and the image-2 im2col (B, [W2*H2][144]) in FP32,
@@ -405,6 +482,12 @@ void dm_grad_layout(const DmGeom& g, DmGradLayout* o) {
     o->G1 = off; off = dm_align(off + (size_t)g.npatch(0) * 144 * 4);
     o->Gim = off; off = dm_align(off + T * 144 * 4);
     o->box = off; off = dm_align(off + (size_t)g.npatch(0) * sizeof(int4));
+    for (int l = 1; l <= g.L; l++) { o->boxA[l] = off; off = dm_align(off + (size_t)g.npatch(l) * sizeof(int4)); }
+    for (int l = 0; l < g.L; l++) { o->boxP[l] = off; off = dm_align(off + (size_t)g.npatch(l) * sizeof(int4)); }
+    // children of any level: the atomic patches, or a lattice level (Lx x Ly >= P0x x P0y)
+    const size_t nchild = (size_t)(g.npatch(0) > g.npatch(1) ? g.npatch(0) : g.npatch(1));
+    o->par = off; off = dm_align(off + nchild * sizeof(int4));
+    o->nch = off; off = dm_align(off + nchild * sizeof(int4));
     o->bytes = off;
 }
 
@@ -413,8 +496,13 @@ cudaError_t dm_launch_loss_grad(const DmGeom& g, const dm_pyramid& py, const flo
     const int L = g.L;
     float* parts = reinterpret_cast<float*>(ws + gl.parts);
     long long launches = 0;
+    auto boxA = [&](int l) { return reinterpret_cast<int4*>(ws + gl.boxA[l]); };
+    auto boxP = [&](int l) { return reinterpret_cast<int4*>(ws + gl.boxP[l]); };
+    int4* par = reinterpret_cast<int4*>(ws + gl.par);
+    int4* nch = reinterpret_cast<int4*>(ws + gl.nch);
     k_adj_top<<<nb(g.npatch(L), 128), 128, 0, st>>>(g, py.valid[L], py.valid[L - 1], py.top, py.pooled[L - 1], lam,
-                                                    py.compensated, reinterpret_cast<float*>(ws + gl.dA[L]), parts);
+                                                    py.compensated, reinterpret_cast<float*>(ws + gl.dA[L]), parts,
+                                                    boxA(L));
     k_adj_loss<<<1, 256, 0, st>>>(parts, g.npatch(L), d_loss);
     launches += 2;
     if (!g1 || !g2) {   // loss only
@@ -423,15 +511,17 @@ cudaError_t dm_launch_loss_grad(const DmGeom& g, const dm_pyramid& py, const flo
     }
     for (int l = L; l >= 1; l--) {
         const int np_child = g.npatch(l - 1);
-        dim3 grid(nb(g.dsize(l), 128), np_child);
-        k_adj_pooled<<<grid, 128, 0, st>>>(g, l, py.valid[l], py.valid[l - 1], reinterpret_cast<const float*>(ws + gl.dA[l]),
-                                           reinterpret_cast<float*>(ws + gl.dP[l - 1]));
-        launches++;
+        k_adj_box<<<nb(np_child, 128), 128, 0, st>>>(g, l, py.valid[l], py.valid[l - 1], boxA(l), boxP(l - 1),
+                                                      l - 1 >= 1 ? boxA(l - 1) : nullptr, par, nch);
+        dim3 grid(nb(g.dsize(l), 128 * ADJ_PPT), np_child);
+        k_adj_pooled<<<grid, 128, 0, st>>>(g, l, reinterpret_cast<const float*>(ws + gl.dA[l]),
+                                           reinterpret_cast<float*>(ws + gl.dP[l - 1]), boxA(l), boxP(l - 1), par, nch);
+        launches += 2;
         if (l - 1 >= 1) {
-            dim3 g2d(nb(g.dsize(l - 1), 128), g.npatch(l - 1));
+            dim3 g2d(nb(g.dsize(l - 1), 128 * ADJ_PPT), g.npatch(l - 1));
             k_adj_unpool<<<g2d, 128, 0, st>>>(g, l - 1, py.valid[l - 1], py.valid[l - 2], py.pooled[l - 2],
                                               reinterpret_cast<const float*>(ws + gl.dP[l - 1]), py.amax[l - 1], lam,
-                                              py.compensated, reinterpret_cast<float*>(ws + gl.dA[l - 1]));
+                                              py.compensated, reinterpret_cast<float*>(ws + gl.dA[l - 1]), boxA(l - 1));
             launches++;
         }
     }
