@@ -269,6 +269,7 @@ __global__ void k_adj_im2col(DmGeom g, const float* __restrict__ d1, const float
 // nonzeros in order; lane j holds k = j + 32 i (i < 5) of the accumulator and
 // of the dot product C0 = (1/16) a_p . b_t (lane partials, then a fixed
 // butterfly sum).  Deterministic: a fixed order throughout.
+// Only the support box of dP0 (k_adj_box) is scanned.
 // Each nonzero dP0(p, r) is replaced by its coefficient c = dP0(p, r) *
 // lam C0(p, t_r)^(lam-1) (0 where the argmax lies outside I'), and box[p]
 // receives the bounding box (x0, y0, x1, y1) of the patch's positions t_r
@@ -276,11 +277,17 @@ __global__ void k_adj_im2col(DmGeom g, const float* __restrict__ d1, const float
 __global__ void __launch_bounds__(256) k_adj_g1_sparse(DmGeom g, float* __restrict__ dP0,
                                                       const unsigned char* __restrict__ amax0,
                                                       const float* __restrict__ Am, const float* __restrict__ Bm,
-                                                      float lam, float* __restrict__ G1, int4* __restrict__ box) {
+                                                      float lam, float* __restrict__ G1, int4* __restrict__ box,
+                                                      const int4* __restrict__ boxP0) {
     const int lane = threadIdx.x & 31;
     const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (p >= g.npatch(0)) return;
-    const int pw = g.dw[1], ph = g.dh[1], pitch = g.pitch(1), W2 = g.W2;
+    const int pitch = g.pitch(1), W2 = g.W2;
+    // the pooled positions outside the support box of dP0 hold exact zeros:
+    // the scan covers the box only, row-major as over the whole map
+    const int4 sb = boxP0[p];
+    const int bw = sb.z >= sb.x ? sb.z - sb.x + 1 : 0;
+    const int bh = sb.w >= sb.y ? sb.w - sb.y + 1 : 0;
     float* dp = dP0 + (long long)p * g.psize(1);
     const unsigned char* am = amax0 + (long long)p * g.psize(1);
     float a[5], acc[5];
@@ -291,7 +298,7 @@ __global__ void __launch_bounds__(256) k_adj_g1_sparse(DmGeom g, float* __restri
         acc[i] = 0.0f;
     }
     int bx0 = INT_MAX, by0 = INT_MAX, bx1 = -1, by1 = -1;
-    const int n = pw * ph;
+    const int n = bw * bh;
     for (int r0 = 0; r0 < n; r0 += 32) {
         const int r = r0 + lane;
         float d = 0.0f;
@@ -299,7 +306,7 @@ __global__ void __launch_bounds__(256) k_adj_g1_sparse(DmGeom g, float* __restri
         long long o = 0;
         bool had = false;
         if (r < n) {
-            const int rx = r % pw, ry = r / pw;
+            const int rx = sb.x + r % bw, ry = sb.y + r / bw;
             o = (long long)ry * pitch + rx;
             d = dp[o];
             had = d != 0.0f;
@@ -396,35 +403,50 @@ __global__ void __launch_bounds__(32 * GIM_WARPS) k_adj_gim(DmGeom g, const floa
         }
         unsigned int m = __ballot_sync(0xffffffffu, meets);
         while (m) {
-            const int q = pb + __ffs(m) - 1;
-            m &= m - 1;
-            float c = 0.0f;
-            int tl = -1;
-            if (cand) {
-                c = cP[(long long)q * psz + off];
-                if (c != 0.0f) {
-                    const int code = amax0[(long long)q * psz + off];
-                    const int tx = 2 * rx + code % 3 - 1, tyy = 2 * ry + code / 3 - 1;
-                    if (tyy == ty && tx >= tx0 && tx <= tx1) tl = tx - tx0;
+            // up to four meeting patches at a time, their candidate outputs
+            // loaded together, then taken in patch order
+            int q[4], nq = 0;
+            while (m && nq < 4) {
+                q[nq++] = pb + __ffs(m) - 1;
+                m &= m - 1;
+            }
+            float cv[4];
+            int code[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                cv[j] = 0.0f;
+                code[j] = 0;
+                if (j < nq && cand) {
+                    cv[j] = cP[(long long)q[j] * psz + off];
+                    code[j] = amax0[(long long)q[j] * psz + off];
                 }
             }
-            unsigned int h = __ballot_sync(0xffffffffu, tl >= 0);
-            if (!h) continue;
-            float a[5];
 #pragma unroll
-            for (int i = 0; i < 5; i++) {
-                const int k = lane + 32 * i;
-                a[i] = k < 144 ? __ldg(Am + (long long)q * 144 + k) : 0.0f;
-            }
-            while (h) {
-                const int src = __ffs(h) - 1;
-                h &= h - 1;
-                const float cv = __shfl_sync(0xffffffffu, c, src);
-                const int t = __shfl_sync(0xffffffffu, tl, src);
+            for (int j = 0; j < 4; j++) {
+                if (j >= nq) break;
+                int tl = -1;
+                if (cv[j] != 0.0f) {
+                    const int tx = 2 * rx + code[j] % 3 - 1, tyy = 2 * ry + code[j] / 3 - 1;
+                    if (tyy == ty && tx >= tx0 && tx <= tx1) tl = tx - tx0;
+                }
+                unsigned int h = __ballot_sync(0xffffffffu, tl >= 0);
+                if (!h) continue;
+                float a[5];
 #pragma unroll
                 for (int i = 0; i < 5; i++) {
                     const int k = lane + 32 * i;
-                    if (k < 144) G[t * 144 + k] = __fmaf_rn(cv, a[i], G[t * 144 + k]);
+                    a[i] = k < 144 ? __ldg(Am + (long long)q[j] * 144 + k) : 0.0f;
+                }
+                while (h) {
+                    const int src = __ffs(h) - 1;
+                    h &= h - 1;
+                    const float c = __shfl_sync(0xffffffffu, cv[j], src);
+                    const int t = __shfl_sync(0xffffffffu, tl, src);
+#pragma unroll
+                    for (int i = 0; i < 5; i++) {
+                        const int k = lane + 32 * i;
+                        if (k < 144) G[t * 144 + k] = __fmaf_rn(c, a[i], G[t * 144 + k]);
+                    }
                 }
             }
         }
@@ -533,7 +555,7 @@ cudaError_t dm_launch_loss_grad(const DmGeom& g, const dm_pyramid& py, const flo
     float* dP0 = reinterpret_cast<float*>(ws + gl.dP[0]);
     const long long n0 = g.npatch(0), T = (long long)g.W2 * g.H2;
     k_adj_im2col<<<nb((n0 + T) * 144, 256), 256, 0, st>>>(g, d1, d2, Am, Bm);
-    k_adj_g1_sparse<<<nb(n0, 8), 256, 0, st>>>(g, dP0, py.amax[0], Am, Bm, lam, G1, box);
+    k_adj_g1_sparse<<<nb(n0, 8), 256, 0, st>>>(g, dP0, py.amax[0], Am, Bm, lam, G1, box, boxP(0));
     const long long n_seg = (long long)((g.W2 + GSEG - 1) / GSEG) * g.H2;
     k_adj_gim<<<nb(n_seg, GIM_WARPS), 32 * GIM_WARPS, 0, st>>>(g, dP0, py.amax[0], box, Am, Gim, (int)n_seg);
     launches += 3;
