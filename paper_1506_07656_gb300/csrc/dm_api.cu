@@ -799,6 +799,7 @@ dm_status dm_grad_workspace_bytes(const dm_ctx* ctx, int W1, int H1, int W2, int
     if (s != DM_OK) return s;
     DmGradLayout gl;
     dm_grad_layout(g, &gl);
+    if (!gl.cap_ok) return fail(const_cast<dm_ctx*>(ctx), DM_EUNSUPPORTED, "dm_grad_workspace_bytes: gradient frontier above 2^32 entries");
     *bytes = gl.bytes;
     return DM_OK;
 }
@@ -811,6 +812,7 @@ dm_status dm_loss_grad(dm_ctx* ctx, const dm_pyramid* pyr, const float* d_desc1,
     if (!aligned256(d_ws)) return fail(ctx, DM_EINVAL, "workspace must be 256-byte aligned");
     DmGradLayout gl;
     dm_grad_layout(pyr->g, &gl);
+    if (!gl.cap_ok) return fail(ctx, DM_EUNSUPPORTED, "dm_loss_grad: gradient frontier above 2^32 entries");
     if (ws_bytes < gl.bytes) return fail(ctx, DM_ENOMEM, "gradient workspace %zu < %zu bytes", ws_bytes, gl.bytes);
     DevGuard dg(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;

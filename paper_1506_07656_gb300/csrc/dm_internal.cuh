@@ -220,6 +220,7 @@ struct DmBtLayout {
 };
 
 // Workspace of the differentiable form (gradient of the top-maxima loss).
+#define DM_GRAD_COUNTS (2 * DM_MAXL + 4)
 struct DmGradLayout {
     size_t parts;                 // f32 [npatch(L)] per-patch maxima
     size_t dA[DM_MAXL + 1];       // f32 [npatch(l)][dh[l]][dw[l]], l = 1..L
@@ -227,9 +228,11 @@ struct DmGradLayout {
     size_t Am, Bm;                // f32 [n0][144] patch vectors, [W2*H2][144] image-2 im2col
     size_t G1, Gim;               // f32 [n0][144], [W2*H2][144] level-0 products
     size_t box;                   // int4 [n0] bounding box of each patch's level-0 argmax positions
-    size_t boxA[DM_MAXL + 1];     // int4 [npatch(l)] support box of dA_l per patch, l = 1..L
-    size_t boxP[DM_MAXL];         // int4 [npatch(l)] support box of dP_l per patch, l = 0..L-1
-    size_t par, nch;              // int4 per child: its parents and their divisors (one level at a time)
+    size_t box0;                  // int4 [n0] box of the nonzeros of dP_0 per patch (x0, y0, -x1, -y1)
+    size_t frontE, frontF;        // int2 [cap] frontiers (patch, position) of the nonzeros of dA_l / dP_l
+    size_t counts;                // u32 [DM_GRAD_COUNTS] frontier sizes per level, then an overflow flag
+    unsigned int cap;             // entries per frontier buffer (bounds every frontier: no overflow)
+    bool cap_ok;                  // false: a frontier could exceed 2^32 entries (refused)
     size_t bytes;
 };
 

@@ -6,9 +6,15 @@
 //   the shifted average A_l = mean_i P_{l-1}(c_i, q+o_i)   (Eq. 12),
 //   the max-pooling with its saved argmax            (Eq. 8-9),
 //   the level-0 correlation C0 = (1/16) a_p . b_t    (Eq. 3-4).
-// Everything is a gather with a fixed summation order, so the gradient is
-// deterministic.  Per level two dense arrays are used: dA_l on the map
-// domain of level l (unrectified averages) and dP_l in the pooled layout.
+// Every value is a gather with a fixed summation order, so the gradient is
+// deterministic.  Per level two dense arrays hold the values: dA_l on the
+// map domain of level l (unrectified averages) and dP_l in the pooled layout,
+// zero outside the gradient's support; only the support is visited: the
+// nonzeros of each array are listed (a frontier, as in the backtracking) and
+// the next array's entries are found from them, each one computed once by
+// its fixed-order gather and claimed by an atomic compare-and-swap on its
+// (zero) slot, so that a value several frontier items reach is written and
+// listed once.
 // Level 0 is recomputed rather than stored: the unrectified C0 at an argmax
 // position is one 144-term dot product.  Of the two level-0 products
 //   G1[p][k] = (1/16) sum_t dC0(p,t) b_t[k],   Gim[t][k] = (1/16) sum_p dC0(p,t) a_p[k]
@@ -56,17 +62,18 @@ __device__ __forceinline__ float dpow(float x, float lam) {   // d(x^lam)/dx for
 }
 
 // Top level: per existing patch, the first maximum of C_L, its value, and
-// dA_L = d(A^lam)/dA at that position (zero elsewhere).
+// dA_L = d(A^lam)/dA at that position (zero elsewhere), listed in E.
 __global__ void k_adj_top(DmGeom g, const unsigned char* __restrict__ vL, const unsigned char* __restrict__ vprev,
                           const float* __restrict__ top, const float* __restrict__ prev, float lam, int comp,
-                          float* __restrict__ dA, float* __restrict__ parts, int4* __restrict__ boxL) {
+                          float* __restrict__ dA, float* __restrict__ parts, int2* __restrict__ E,
+                          unsigned int* __restrict__ nE) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const int L = g.L;
     if (p >= g.npatch(L)) return;
     const int nq = g.dw[L] * g.dh[L];
     float* d = dA + (long long)p * nq;
     for (int q = 0; q < nq; q++) d[q] = 0.0f;
-    if (!vL[p]) { parts[p] = 0.0f; boxL[p] = make_int4(0, 0, -1, -1); return; }
+    if (!vL[p]) { parts[p] = 0.0f; return; }
     const float* t = top + (long long)p * nq;
     float best = -INFINITY;
     int qb = 0;
@@ -76,7 +83,7 @@ __global__ void k_adj_top(DmGeom g, const unsigned char* __restrict__ vL, const 
     int n;
     const float a = level_average(g, L, p, qb % g.dw[L], qb / g.dw[L], vprev, prev, comp != 0, &n);
     d[qb] = dpow(a, lam);
-    boxL[p] = make_int4(qb % g.dw[L], qb / g.dw[L], qb % g.dw[L], qb / g.dw[L]);
+    if (d[qb] != 0.0f) E[atomicAdd(nE, 1u)] = make_int2(p, qb);   // at most npatch(L) entries
 }
 
 // Deterministic sum of the per-patch maxima (one block).
@@ -115,127 +122,111 @@ __device__ int adj_parent(const DmGeom& g, int l, int c, int i, const unsigned c
     return p;
 }
 
-__device__ __forceinline__ bool in_box(const int4& b, int x, int y) {
-    return x >= b.x && x <= b.z && y >= b.y && y <= b.w;
+// Claim the zero slot of a nonzero value: true for the one caller that wrote
+// it (every caller computes the same bits by the same fixed-order gather).
+__device__ __forceinline__ bool claim(float* slot, float v) {
+    return atomicCAS(reinterpret_cast<unsigned int*>(slot), 0u, __float_as_uint(v)) == 0u;
 }
 
-// Support boxes of the gradient, one step down from level l: for child c,
-// par[c] / nch[c] receive its four parents (adj_parent) and their divisors;
-// boxP[c] bounds the pooled positions r where dP_{l-1}(c, r) can be nonzero
-// (the parents' boxes of dA_l shifted by their offsets o_i), and, where
-// m = l - 1 >= 1, boxAm[c] bounds the positions t = 2r + (-1..1) of domain m
-// where dA_m(c, t) can be nonzero.  Supersets: outside them every term of the
-// gathers below is an exact zero, so skipping them leaves every sum unchanged.
-__global__ void k_adj_box(DmGeom g, int l, const unsigned char* __restrict__ vcur, const unsigned char* __restrict__ vprev,
-                          const int4* __restrict__ boxA, int4* __restrict__ boxP, int4* __restrict__ boxAm,
-                          int4* __restrict__ par, int4* __restrict__ nch) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.npatch(l - 1)) return;
-    int x0 = INT_MAX, y0 = INT_MAX, x1 = -1, y1 = -1;
-    int pi[4], ni[4];
-    for (int i = 0; i < 4; i++) pi[i] = adj_parent(g, l, c, i, vcur, vprev, &ni[i]);
-    par[c] = make_int4(pi[0], pi[1], pi[2], pi[3]);
-    nch[c] = make_int4(ni[0], ni[1], ni[2], ni[3]);
-    for (int i = 0; i < 4; i++) {
-        const int p = pi[i];
-        if (p < 0) continue;
-        const int4 b = boxA[p];
-        if (b.x > b.z || b.y > b.w) continue;
-        const int ox = (i >= 2) ? 1 : -1, oy = (i & 1) ? 1 : -1;
-        x0 = min(x0, b.x + ox); x1 = max(x1, b.z + ox);
-        y0 = min(y0, b.y + oy); y1 = max(y1, b.w + oy);
-    }
-    x0 = max(x0, 0); y0 = max(y0, 0);
-    x1 = min(x1, g.dw[l] - 1); y1 = min(y1, g.dh[l] - 1);
-    boxP[c] = make_int4(x0, y0, x1, y1);
-    if (boxAm) {
-        const int m = l - 1;
-        if (x0 > x1 || y0 > y1) boxAm[c] = make_int4(0, 0, -1, -1);
-        else boxAm[c] = make_int4(max(2 * x0 - 1, 0), max(2 * y0 - 1, 0), min(2 * x1 + 1, g.dw[m] - 1),
-                                  min(2 * y1 + 1, g.dh[m] - 1));
-    }
-}
-
-constexpr int ADJ_PPT = 8;   // positions per thread of the per-level passes
-
-// dP_{l-1}(c, r) = sum over the parents p_i = c - 2^l o_i of c (i = 0..3, in
-// order) of dA_l(p_i, r - o_i) / n(p_i).  Grid: (runs of 128 * ADJ_PPT
-// positions of domain l, child); par / nch from k_adj_box.  Positions outside
-// the child's support box, and parent positions outside the parent's,
-// contribute exact zeros and are not read.
-__global__ void __launch_bounds__(128) k_adj_pooled(DmGeom g, int l, const float* __restrict__ dA, float* __restrict__ dP,
-                                                    const int4* __restrict__ boxA, const int4* __restrict__ boxP,
-                                                    const int4* __restrict__ par, const int4* __restrict__ nch) {
-    const int c = blockIdx.y;
+// One step down from level l.  For every nonzero dA_l(p, q) of the frontier E
+// and every child slot i of p: the pooled position r = q + o_i of child c_i
+// at level l - 1, and there
+//   dP_{l-1}(c, r) = sum over the parents p_j = c - 2^l o_j of c (j = 0..3, in
+//   order) of dA_l(p_j, r - o_j) / n(p_j)
+// (every nonzero dP is reached: one of its terms is a listed dA).  Claimed
+// entries are listed in F, or, at l = 1, folded into the box of each atomic
+// patch's nonzeros (x0, y0, -x1, -y1 by atomic minima).  Work item w = 4e + i,
+// grid-stride over the frontier's count.
+__global__ void __launch_bounds__(256) k_adj_down(DmGeom g, int l, const unsigned char* __restrict__ vcur,
+                                                  const unsigned char* __restrict__ vprev, const float* __restrict__ dA,
+                                                  float* __restrict__ dP, const int2* __restrict__ E,
+                                                  const unsigned int* __restrict__ nE, int2* __restrict__ F,
+                                                  unsigned int* __restrict__ nF, unsigned int capF,
+                                                  unsigned int* __restrict__ overflow, int* __restrict__ box0) {
+    const unsigned long long n = 4ull * min(*nE, capF);   // (E and F share one capacity)
     const int mw = g.dw[l], mh = g.dh[l], pitch = g.pitch(l);
-    const int n = mw * mh;
-    float* out = dP + (long long)c * g.psize(l);
-    const int4 bp = boxP[c];
-    const int4 pp = par[c], nn = nch[c];
-    const int pa[4] = {pp.x, pp.y, pp.z, pp.w};
-    const int na[4] = {nn.x, nn.y, nn.z, nn.w};
-    const int r0 = blockIdx.x * (128 * ADJ_PPT) + threadIdx.x;
-#pragma unroll 2
-    for (int j = 0; j < ADJ_PPT; j++) {
-        const int r = r0 + 128 * j;
-        if (r >= n) break;
-        const int rx = r % mw, ry = r / mw;
+    for (unsigned long long w = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; w < n;
+         w += (unsigned long long)gridDim.x * blockDim.x) {
+        const int2 e = E[w >> 2];
+        const int i = (int)(w & 3u);
+        const int p = e.x, qx = e.y % mw, qy = e.y / mw;
+        const int c = dm_child(g, l, p % g.Lx, p / g.Lx, i);
+        if (c < 0 || !vprev[c]) continue;
+        const int rx = qx + ((i >= 2) ? 1 : -1), ry = qy + ((i & 1) ? 1 : -1);
+        if (rx < 0 || ry < 0 || rx >= mw || ry >= mh) continue;
         float sum = 0.0f;
-        if (in_box(bp, rx, ry)) {
 #pragma unroll
-            for (int i = 0; i < 4; i++) {
-                const int p = pa[i];
-                if (p < 0) continue;
-                const int ox = (i >= 2) ? 1 : -1, oy = (i & 1) ? 1 : -1;
-                const int qx = rx - ox, qy = ry - oy;
-                if (qx < 0 || qy < 0 || qx >= mw || qy >= mh) continue;
-                if (!in_box(boxA[p], qx, qy)) continue;
-                const float d = dA[((long long)p * mh + qy) * mw + qx];
-                if (d != 0.0f) sum = __fadd_rn(sum, __fdiv_rn(d, (float)na[i]));
-            }
+        for (int j = 0; j < 4; j++) {
+            int nj;
+            const int pj = adj_parent(g, l, c, j, vcur, vprev, &nj);
+            if (pj < 0) continue;
+            const int sx = rx - ((j >= 2) ? 1 : -1), sy = ry - ((j & 1) ? 1 : -1);
+            if (sx < 0 || sy < 0 || sx >= mw || sy >= mh) continue;
+            const float d = dA[((long long)pj * mh + sy) * mw + sx];
+            if (d != 0.0f) sum = __fadd_rn(sum, __fdiv_rn(d, (float)nj));
         }
-        out[(long long)ry * pitch + rx] = sum;
+        if (sum == 0.0f) continue;
+        if (!claim(dP + (long long)c * g.psize(l) + (long long)ry * pitch + rx, sum)) continue;
+        if (box0) {
+            atomicMin(box0 + 4 * c, rx);
+            atomicMin(box0 + 4 * c + 1, ry);
+            atomicMin(box0 + 4 * c + 2, -rx);
+            atomicMin(box0 + 4 * c + 3, -ry);
+        } else {
+            const unsigned int k = atomicAdd(nF, 1u);
+            if (k < capF) F[k] = make_int2(c, ry * mw + rx);
+            else atomicOr(overflow, 1u);
+        }
     }
 }
 
-// dA_{m}(c, t) for m = l-1 >= 1: sum over the pooled positions r whose argmax
-// is t (r = floor/ceil(t/2) per axis, ascending) of dP_m(c, r) * lam A^(lam-1),
-// A the unrectified average at t.  Grid: (positions of domain m, patch).
-__global__ void __launch_bounds__(128) k_adj_unpool(DmGeom g, int m, const unsigned char* __restrict__ vm,
-                                                    const unsigned char* __restrict__ vprev,
-                                                    const float* __restrict__ prev, const float* __restrict__ dP,
-                                                    const unsigned char* __restrict__ amax, float lam, int comp,
-                                                    float* __restrict__ dA, const int4* __restrict__ boxAm) {
-    const int c = blockIdx.y;
+// One step up to the map domain of level m = l - 1 >= 1.  For every nonzero
+// dP_m(c, r) of the frontier F: its argmax position t = 2r + (m_x, m_y), and
+// there
+//   dA_m(c, t) = (sum over the pooled positions r' whose argmax is t, r' =
+//   floor/ceil(t/2) per axis ascending, of dP_m(c, r')) * lam A^(lam-1),
+// A the unrectified average at t.  Claimed entries are listed in E.
+__global__ void __launch_bounds__(256) k_adj_up(DmGeom g, int m, const unsigned char* __restrict__ vm,
+                                                const unsigned char* __restrict__ vprev,
+                                                const float* __restrict__ prev, const float* __restrict__ dP,
+                                                const unsigned char* __restrict__ amax, float lam, int comp,
+                                                float* __restrict__ dA, const int2* __restrict__ F,
+                                                const unsigned int* __restrict__ nF, int2* __restrict__ E,
+                                                unsigned int* __restrict__ nE, unsigned int capE,
+                                                unsigned int* __restrict__ overflow) {
+    const unsigned long long n = min(*nF, capE);   // (E and F share one capacity)
     const int tw = g.dw[m], th = g.dh[m];
     const int pw = g.dw[m + 1], ph = g.dh[m + 1], pitch = g.pitch(m + 1);
-    const int4 bb = boxAm[c];
-    const bool live = vm[c] != 0;
-    const int t0 = blockIdx.x * (128 * ADJ_PPT) + threadIdx.x;
-    for (int j = 0; j < ADJ_PPT; j++) {
-        const int t = t0 + 128 * j;
-        if (t >= tw * th) break;
-        const int tx = t % tw, ty = t / tw;
-        float sum = 0.0f;
-        if (live && in_box(bb, tx, ty)) {
-            float dsum = 0.0f;
-            for (int ry = ty >> 1; ry <= (ty + 1) >> 1; ry++) {
-                if (ry >= ph) continue;
-                for (int rx = tx >> 1; rx <= (tx + 1) >> 1; rx++) {
-                    if (rx >= pw) continue;
-                    const long long o = (long long)c * g.psize(m + 1) + (long long)ry * pitch + rx;
-                    const int code = amax[o];
-                    if (2 * rx + code % 3 - 1 != tx || 2 * ry + code / 3 - 1 != ty) continue;
-                    dsum = __fadd_rn(dsum, dP[o]);
-                }
-            }
-            if (dsum != 0.0f) {
-                int n;
-                const float a = level_average(g, m, c, tx, ty, vprev, prev, comp != 0, &n);
-                sum = __fmul_rn(dsum, dpow(a, lam));
+    const long long psz = g.psize(m + 1);
+    for (unsigned long long w = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; w < n;
+         w += (unsigned long long)gridDim.x * blockDim.x) {
+        const int2 f = F[w];
+        const int c = f.x, r0x = f.y % pw, r0y = f.y / pw;
+        if (!vm[c]) continue;
+        const int code0 = amax[c * psz + (long long)r0y * pitch + r0x];
+        if (code0 > 8) continue;   // (the forward's pooling never writes one)
+        const int tx = 2 * r0x + code0 % 3 - 1, ty = 2 * r0y + code0 / 3 - 1;
+        if (tx < 0 || ty < 0 || tx >= tw || ty >= th) continue;
+        float dsum = 0.0f;
+        for (int ry = ty >> 1; ry <= (ty + 1) >> 1; ry++) {
+            if (ry >= ph) continue;
+            for (int rx = tx >> 1; rx <= (tx + 1) >> 1; rx++) {
+                if (rx >= pw) continue;
+                const long long o = c * psz + (long long)ry * pitch + rx;
+                const int code = amax[o];
+                if (2 * rx + code % 3 - 1 != tx || 2 * ry + code / 3 - 1 != ty) continue;
+                dsum = __fadd_rn(dsum, dP[o]);
             }
         }
-        dA[((long long)c * th + ty) * tw + tx] = sum;
+        if (dsum == 0.0f) continue;
+        int nn;
+        const float a = level_average(g, m, c, tx, ty, vprev, prev, comp != 0, &nn);
+        const float v = __fmul_rn(dsum, dpow(a, lam));
+        if (v == 0.0f) continue;
+        if (!claim(dA + ((long long)c * th + ty) * tw + tx, v)) continue;
+        const unsigned int k = atomicAdd(nE, 1u);
+        if (k < capE) E[k] = make_int2(c, ty * tw + tx);
+        else atomicOr(overflow, 1u);
     }
 }
 
@@ -269,7 +260,8 @@ __global__ void k_adj_im2col(DmGeom g, const float* __restrict__ d1, const float
 // nonzeros in order; lane j holds k = j + 32 i (i < 5) of the accumulator and
 // of the dot product C0 = (1/16) a_p . b_t (lane partials, then a fixed
 // butterfly sum).  Deterministic: a fixed order throughout.
-// Only the support box of dP0 (k_adj_box) is scanned.
+// Only the box of the nonzeros of dP0 is scanned (boxP0[p] = (x0, y0, -x1, -y1)
+// from k_adj_down; x0 > x1 when the patch has none).
 // Each nonzero dP0(p, r) is replaced by its coefficient c = dP0(p, r) *
 // lam C0(p, t_r)^(lam-1) (0 where the argmax lies outside I'), and box[p]
 // receives the bounding box (x0, y0, x1, y1) of the patch's positions t_r
@@ -285,7 +277,8 @@ __global__ void __launch_bounds__(256) k_adj_g1_sparse(DmGeom g, float* __restri
     const int pitch = g.pitch(1), W2 = g.W2;
     // the pooled positions outside the support box of dP0 hold exact zeros:
     // the scan covers the box only, row-major as over the whole map
-    const int4 sb = boxP0[p];
+    const int4 sbn = boxP0[p];
+    const int4 sb = make_int4(sbn.x, sbn.y, -sbn.z, -sbn.w);
     const int bw = sb.z >= sb.x ? sb.z - sb.x + 1 : 0;
     const int bh = sb.w >= sb.y ? sb.w - sb.y + 1 : 0;
     float* dp = dP0 + (long long)p * g.psize(1);
@@ -504,12 +497,25 @@ void dm_grad_layout(const DmGeom& g, DmGradLayout* o) {
     o->G1 = off; off = dm_align(off + (size_t)g.npatch(0) * 144 * 4);
     o->Gim = off; off = dm_align(off + T * 144 * 4);
     o->box = off; off = dm_align(off + (size_t)g.npatch(0) * sizeof(int4));
-    for (int l = 1; l <= g.L; l++) { o->boxA[l] = off; off = dm_align(off + (size_t)g.npatch(l) * sizeof(int4)); }
-    for (int l = 0; l < g.L; l++) { o->boxP[l] = off; off = dm_align(off + (size_t)g.npatch(l) * sizeof(int4)); }
-    // children of any level: the atomic patches, or a lattice level (Lx x Ly >= P0x x P0y)
-    const size_t nchild = (size_t)(g.npatch(0) > g.npatch(1) ? g.npatch(0) : g.npatch(1));
-    o->par = off; off = dm_align(off + nchild * sizeof(int4));
-    o->nch = off; off = dm_align(off + nchild * sizeof(int4));
+    o->box0 = off; off = dm_align(off + (size_t)g.npatch(0) * sizeof(int4));
+    // frontiers: E_l (nonzeros of dA_l, l >= 1) and F_l (nonzeros of dP_l, l >= 1;
+    // F_0 is folded into box0).  A frontier at level l holds at most
+    // 4^(L-l) npatch(L) entries (each step down has 4 children per entry, each
+    // step up one argmax per entry) and at most its array's size.
+    size_t cap = 0;
+    for (int l = 1; l <= g.L; l++) {
+        size_t tree = (size_t)g.npatch(g.L);
+        for (int k = l; k < g.L && tree < ((size_t)1 << 40); k++) tree *= 4;
+        const size_t eA = (size_t)g.npatch(l) * g.dsize(l);
+        const size_t eP = l < g.L ? (size_t)g.npatch(l) * g.dw[l + 1] * g.dh[l + 1] : 0;
+        cap = std::max(cap, std::min(tree, std::max(eA, eP)));
+    }
+    o->cap_ok = cap <= (size_t)0xffffffffu;   // frontier counts are 32-bit
+    cap = std::min(cap, (size_t)0xffffffffu);
+    o->cap = (unsigned int)cap;
+    o->frontE = off; off = dm_align(off + cap * sizeof(int2));
+    o->frontF = off; off = dm_align(off + cap * sizeof(int2));
+    o->counts = off; off = dm_align(off + (size_t)DM_GRAD_COUNTS * sizeof(unsigned int));
     o->bytes = off;
 }
 
@@ -518,32 +524,46 @@ cudaError_t dm_launch_loss_grad(const DmGeom& g, const dm_pyramid& py, const flo
     const int L = g.L;
     float* parts = reinterpret_cast<float*>(ws + gl.parts);
     long long launches = 0;
-    auto boxA = [&](int l) { return reinterpret_cast<int4*>(ws + gl.boxA[l]); };
-    auto boxP = [&](int l) { return reinterpret_cast<int4*>(ws + gl.boxP[l]); };
-    int4* par = reinterpret_cast<int4*>(ws + gl.par);
-    int4* nch = reinterpret_cast<int4*>(ws + gl.nch);
+    if (!gl.cap_ok) return cudaErrorInvalidValue;
+    int2* E = reinterpret_cast<int2*>(ws + gl.frontE);
+    int2* F = reinterpret_cast<int2*>(ws + gl.frontF);
+    unsigned int* cnt = reinterpret_cast<unsigned int*>(ws + gl.counts);   // [2l]: E_l, [2l+1]: F_l, last: overflow
+    unsigned int* overflow = cnt + DM_GRAD_COUNTS - 1;
+    int* box0 = reinterpret_cast<int*>(ws + gl.box0);
+    cudaError_t em = cudaMemsetAsync(cnt, 0, DM_GRAD_COUNTS * sizeof(unsigned int), st);
+    if (em != cudaSuccess) return em;
     k_adj_top<<<nb(g.npatch(L), 128), 128, 0, st>>>(g, py.valid[L], py.valid[L - 1], py.top, py.pooled[L - 1], lam,
                                                     py.compensated, reinterpret_cast<float*>(ws + gl.dA[L]), parts,
-                                                    boxA(L));
+                                                    E, cnt + 2 * L);
     k_adj_loss<<<1, 256, 0, st>>>(parts, g.npatch(L), d_loss);
     launches += 2;
     if (!g1 || !g2) {   // loss only
         dm_count_launches(launches);
         return cudaGetLastError();
     }
+    // the dense arrays below level L start at zero: the frontier kernels write
+    // only the support (dA_L itself is written whole by k_adj_top)
+    if (L >= 2) {
+        em = cudaMemsetAsync(ws + gl.dA[1], 0, gl.dA[L] - gl.dA[1], st);
+        if (em != cudaSuccess) return em;
+    }
+    em = cudaMemsetAsync(ws + gl.dP[0], 0, gl.dP[L - 1] + (size_t)g.npatch(L - 1) * g.psize(L) * 4 - gl.dP[0], st);
+    if (em == cudaSuccess) em = cudaMemsetAsync(box0, 0x7f, (size_t)g.npatch(0) * sizeof(int4), st);
+    if (em != cudaSuccess) return em;
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned int fgrid = (unsigned int)nsm * 8;
     for (int l = L; l >= 1; l--) {
-        const int np_child = g.npatch(l - 1);
-        k_adj_box<<<nb(np_child, 128), 128, 0, st>>>(g, l, py.valid[l], py.valid[l - 1], boxA(l), boxP(l - 1),
-                                                      l - 1 >= 1 ? boxA(l - 1) : nullptr, par, nch);
-        dim3 grid(nb(g.dsize(l), 128 * ADJ_PPT), np_child);
-        k_adj_pooled<<<grid, 128, 0, st>>>(g, l, reinterpret_cast<const float*>(ws + gl.dA[l]),
-                                           reinterpret_cast<float*>(ws + gl.dP[l - 1]), boxA(l), boxP(l - 1), par, nch);
-        launches += 2;
+        k_adj_down<<<fgrid, 256, 0, st>>>(g, l, py.valid[l], py.valid[l - 1], reinterpret_cast<const float*>(ws + gl.dA[l]),
+                                          reinterpret_cast<float*>(ws + gl.dP[l - 1]), E, cnt + 2 * l, F,
+                                          cnt + 2 * (l - 1) + 1, gl.cap, overflow, l == 1 ? box0 : nullptr);
+        launches++;
         if (l - 1 >= 1) {
-            dim3 g2d(nb(g.dsize(l - 1), 128 * ADJ_PPT), g.npatch(l - 1));
-            k_adj_unpool<<<g2d, 128, 0, st>>>(g, l - 1, py.valid[l - 1], py.valid[l - 2], py.pooled[l - 2],
-                                              reinterpret_cast<const float*>(ws + gl.dP[l - 1]), py.amax[l - 1], lam,
-                                              py.compensated, reinterpret_cast<float*>(ws + gl.dA[l - 1]), boxA(l - 1));
+            k_adj_up<<<fgrid, 256, 0, st>>>(g, l - 1, py.valid[l - 1], py.valid[l - 2], py.pooled[l - 2],
+                                            reinterpret_cast<const float*>(ws + gl.dP[l - 1]), py.amax[l - 1], lam,
+                                            py.compensated, reinterpret_cast<float*>(ws + gl.dA[l - 1]), F,
+                                            cnt + 2 * (l - 1) + 1, E, cnt + 2 * (l - 1), gl.cap, overflow);
             launches++;
         }
     }
@@ -555,7 +575,8 @@ cudaError_t dm_launch_loss_grad(const DmGeom& g, const dm_pyramid& py, const flo
     float* dP0 = reinterpret_cast<float*>(ws + gl.dP[0]);
     const long long n0 = g.npatch(0), T = (long long)g.W2 * g.H2;
     k_adj_im2col<<<nb((n0 + T) * 144, 256), 256, 0, st>>>(g, d1, d2, Am, Bm);
-    k_adj_g1_sparse<<<nb(n0, 8), 256, 0, st>>>(g, dP0, py.amax[0], Am, Bm, lam, G1, box, boxP(0));
+    k_adj_g1_sparse<<<nb(n0, 8), 256, 0, st>>>(g, dP0, py.amax[0], Am, Bm, lam, G1, box,
+                                               reinterpret_cast<const int4*>(box0));
     const long long n_seg = (long long)((g.W2 + GSEG - 1) / GSEG) * g.H2;
     k_adj_gim<<<nb(n_seg, GIM_WARPS), 32 * GIM_WARPS, 0, st>>>(g, dP0, py.amax[0], box, Am, Gim, (int)n_seg);
     launches += 3;
