@@ -184,3 +184,46 @@ def test_autograd_forward_without_backward_frees_the_pyramid(env):
     loss = autograd.top_max_loss(d[0], d[1], ctx)
     loss.backward()
     assert autograd._PyramidHandle.live == before
+
+
+def test_gradient_is_deterministic_and_independent_of_the_workspace(env):
+    """The backward visits only the gradient's support: each value of the
+    per-level arrays is computed by its fixed-order gather and written once,
+    whatever order the frontier lists come in, and the arrays are cleared by
+    the call itself.  So repeated calls give identical bits, also when the
+    workspace holds another pair's arrays or arbitrary bytes before the call."""
+    torch, dm, ctx = env
+    W = H = 256
+    pr = synth.make_pair_smooth(W, H, seed=5001, max_disp=16.0, with_flow=False)
+    other = synth.make_pair_smooth(W, H, seed=5002, max_disp=16.0, with_flow=False)
+    wsd = ctx.workspace("desc", W, H, W, H)
+
+    def desc(img):
+        t = torch.empty((H, W, 9), dtype=torch.float32, device="cuda")
+        dm.dm_descriptors(ctx.ctx, torch.from_numpy(img).cuda(), t, wsd)
+        return t
+
+    d1, d2, e1, e2 = desc(pr.img1), desc(pr.img2), desc(other.img1), desc(other.img2)
+    wsp = torch.empty(dm.dm_workspace_bytes(ctx.ctx, W, H, W, H)["pyramid"], dtype=torch.uint8, device="cuda")
+    wsg = torch.zeros(dm.dm_grad_workspace_bytes(ctx.ctx, W, H, W, H), dtype=torch.uint8, device="cuda")
+
+    def run(a, b):
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        g1, g2 = torch.empty_like(a), torch.empty_like(b)
+        h = dm.dm_correlate_pyramid(ctx.ctx, a, b, wsp)
+        dm.dm_loss_grad(ctx.ctx, h, a, b, wsg, loss, None, g1, g2)
+        torch.cuda.synchronize()
+        dm.dm_pyramid_free(h)
+        return [x.cpu().numpy().view(np.uint32).copy() for x in (loss, g1, g2)]
+
+    first = run(d1, d2)
+    assert np.any(first[1] != 0) and np.any(first[2] != 0)
+    runs = [run(d1, d2)]
+    run(e1, e2)                       # another pair's arrays left in the workspace
+    runs.append(run(d1, d2))
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    wsg.copy_(torch.randint(0, 256, wsg.shape, dtype=torch.uint8, device="cuda", generator=gen))
+    runs.append(run(d1, d2))          # arbitrary bytes in the workspace
+    for r in runs:
+        for a, b in zip(first, r):
+            np.testing.assert_array_equal(a, b)
