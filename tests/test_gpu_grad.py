@@ -50,7 +50,8 @@ def _gpu_loss_grad(torch, dm, ctx, d1, d2, want_grad=True):
     return out
 
 
-@pytest.mark.parametrize("W1,H1,W2,H2,seed", [(20, 16, 22, 15, 1), (37, 29, 41, 23, 2)])
+@pytest.mark.parametrize("W1,H1,W2,H2,seed", [(20, 16, 22, 15, 1), (37, 29, 41, 23, 2),
+                                              (8, 8, 8, 8, 3), (6, 5, 7, 4, 4), (13, 9, 5, 11, 5)])
 def test_gradient_matches_fp64_oracle_random(env, oracle_mod, W1, H1, W2, H2, seed):
     torch, dm, ctx = env
     d1 = synth.random_descriptor_field(W1, H1, seed).astype(np.float32)
