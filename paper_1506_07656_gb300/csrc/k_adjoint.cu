@@ -319,25 +319,39 @@ __global__ void __launch_bounds__(256) k_adj_g1_sparse(DmGeom g, float* __restri
         float myc = 0.0f;
         unsigned int nz = __ballot_sync(0xffffffffu, d != 0.0f);
         while (nz) {
-            const int src = __ffs(nz) - 1;
+            // up to two nonzeros at a time: their windows of I' loaded together,
+            // then taken in order
+            int src[2];
+            src[0] = __ffs(nz) - 1;
             nz &= nz - 1;
-            const float dv = __shfl_sync(0xffffffffu, d, src);
-            const int tv = __shfl_sync(0xffffffffu, t, src);
-            const float* b = Bm + (long long)tv * 144;
-            float bk[5], part = 0.0f;
+            src[1] = nz ? __ffs(nz) - 1 : -1;
+            if (nz) nz &= nz - 1;
+            float bk[2][5];
 #pragma unroll
-            for (int i = 0; i < 5; i++) {
-                const int k = lane + 32 * i;
-                bk[i] = k < 144 ? __ldg(b + k) : 0.0f;
-                part = __fmaf_rn(a[i], bk[i], part);
+            for (int u = 0; u < 2; u++) {
+                const int tv = __shfl_sync(0xffffffffu, t, src[u] < 0 ? 0 : src[u]);
+                const float* b = Bm + (long long)tv * 144;
+#pragma unroll
+                for (int i = 0; i < 5; i++) {
+                    const int k = lane + 32 * i;
+                    bk[u][i] = (src[u] >= 0 && k < 144) ? __ldg(b + k) : 0.0f;
+                }
             }
 #pragma unroll
-            for (int o2 = 16; o2 > 0; o2 >>= 1) part = __fadd_rn(part, __shfl_xor_sync(0xffffffffu, part, o2));
-            const float c = __fmul_rn(dv, dpow(__fmul_rn(part, 0.0625f), lam));   // this r's share of dC0(p, t)
-            const float w = __fmul_rn(c, 0.0625f);
+            for (int u = 0; u < 2; u++) {
+                if (src[u] < 0) break;
+                const float dv = __shfl_sync(0xffffffffu, d, src[u]);
+                float part = 0.0f;
 #pragma unroll
-            for (int i = 0; i < 5; i++) acc[i] = __fmaf_rn(w, bk[i], acc[i]);
-            if (lane == src) myc = c;
+                for (int i = 0; i < 5; i++) part = __fmaf_rn(a[i], bk[u][i], part);
+#pragma unroll
+                for (int o2 = 16; o2 > 0; o2 >>= 1) part = __fadd_rn(part, __shfl_xor_sync(0xffffffffu, part, o2));
+                const float c = __fmul_rn(dv, dpow(__fmul_rn(part, 0.0625f), lam));   // this r's share of dC0(p, t)
+                const float w = __fmul_rn(c, 0.0625f);
+#pragma unroll
+                for (int i = 0; i < 5; i++) acc[i] = __fmaf_rn(w, bk[u][i], acc[i]);
+                if (lane == src[u]) myc = c;
+            }
         }
         if (had) dp[o] = myc;
     }
@@ -388,25 +402,24 @@ __global__ void __launch_bounds__(32 * GIM_WARPS) k_adj_gim(DmGeom g, const floa
     const int ry = (ty >> 1) + (lane >> 4), rx = tx0 / 2 + (lane & 15);
     const bool cand = ry <= ((ty + 1) >> 1) && ry < ph && rx < pw;
     const long long off = (long long)ry * g.pitch(1) + rx;
+    int4 nb4 = lane < n0 ? __ldg(box + lane) : make_int4(0, 0, -1, -1);
     for (int pb = 0; pb < n0; pb += 32) {
-        bool meets = false;
-        if (pb + lane < n0) {
-            const int4 bb = __ldg(box + pb + lane);
-            meets = bb.x <= tx1 && bb.z >= tx0 && bb.y <= ty && bb.w >= ty;
-        }
+        const int4 bb = nb4;   // this chunk's boxes; the next chunk's are loaded meanwhile
+        nb4 = pb + 32 + lane < n0 ? __ldg(box + pb + 32 + lane) : make_int4(0, 0, -1, -1);
+        const bool meets = bb.x <= tx1 && bb.z >= tx0 && bb.y <= ty && bb.w >= ty;
         unsigned int m = __ballot_sync(0xffffffffu, meets);
         while (m) {
-            // up to four meeting patches at a time, their candidate outputs
+            // up to eight meeting patches at a time, their candidate outputs
             // loaded together, then taken in patch order
-            int q[4], nq = 0;
-            while (m && nq < 4) {
+            int q[8], nq = 0;
+            while (m && nq < 8) {
                 q[nq++] = pb + __ffs(m) - 1;
                 m &= m - 1;
             }
-            float cv[4];
-            int code[4];
+            float cv[8];
+            int code[8];
 #pragma unroll
-            for (int j = 0; j < 4; j++) {
+            for (int j = 0; j < 8; j++) {
                 cv[j] = 0.0f;
                 code[j] = 0;
                 if (j < nq && cand) {
@@ -415,7 +428,7 @@ __global__ void __launch_bounds__(32 * GIM_WARPS) k_adj_gim(DmGeom g, const floa
                 }
             }
 #pragma unroll
-            for (int j = 0; j < 4; j++) {
+            for (int j = 0; j < 8; j++) {
                 if (j >= nq) break;
                 int tl = -1;
                 if (cv[j] != 0.0f) {
