@@ -362,9 +362,13 @@ dm_status dm_inject_fault(dm_ctx* ctx, int kind, long long arg);
  * The backward follows the forward exactly: through the power (Eq. 11), the
  * shifted average (Eq. 12), the max-pooling argmax saved by the forward
  * (Eq. 9) and the level-0 correlation (Eq. 3-4), whose values at the argmax
- * positions are recomputed instead of stored; both level-0 products are
- * gathers over the argmax positions with a nonzero gradient.  All sums have a
- * fixed order: the gradient is deterministic.  d_ws >= dm_grad_workspace_bytes. */
+ * positions are recomputed instead of stored; only the gradient's support is
+ * visited, level by level, and both level-0 products are gathers over the
+ * argmax positions with a nonzero gradient.  All sums have a fixed order: the
+ * gradient is deterministic.  d_ws >= dm_grad_workspace_bytes, any contents
+ * (the call clears what it reads).  Both calls return DM_EUNSUPPORTED where a
+ * level's support could exceed 2^32 entries (far beyond any size whose
+ * workspace fits a GPU). */
 dm_status dm_grad_workspace_bytes(const dm_ctx* ctx, int W1, int H1, int W2, int H2, size_t* bytes);
 dm_status dm_loss_grad(dm_ctx* ctx, const dm_pyramid* pyr, const float* d_desc1, const float* d_desc2, void* d_ws,
                        size_t ws_bytes, float* d_loss, float* d_parts, float* d_g1, float* d_g2, void* stream);
