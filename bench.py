@@ -609,7 +609,7 @@ def _measure_grad(dm, torch, a, stream, W=256, H=256, npairs=8):
             "precision": "fp32", "pairs_per_s": npairs * 1000.0 / ms, "ms_per_step": ms,
             "loss_grad_ms_per_pair": grad_ms, "forward_ms_per_pair": ms / npairs - grad_ms,
             "kernel_launches_per_step": int(launches), "loss": [float(x) for x in loss.cpu()],
-            "grad_l2_norm": gnorm, "n_patch0": g["n_patch0"],
+            "grad_l2_norm": gnorm, "n_patch0": g["n_patch0"], "size": [W, H],
             "level0_backward": "both level-0 products as gathers over the argmax positions with a nonzero gradient"}
 
 
@@ -905,6 +905,19 @@ def run_ours(a):
             peaks = json.load(open(pk))
         nsm = torch.cuda.get_device_properties(local).multi_processor_count
         corr, lev = _rooflines(r, head, W, H, peaks, nsm)
+        if grad is not None:
+            # the differentiable step is dominated by its forward's FP32 level 0 (k_corr0_f32);
+            # the forward time also holds the level pass, so this is a lower bound
+            sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+            fpeak = nsm * 128 * 2 * sm_max * 1e6 / 1e12
+            gw, gh = grad["size"]
+            flop = 2.0 * 144 * grad["n_patch0"] * gw * gh
+            ach = flop / (grad["forward_ms_per_pair"] * 1e-3) / 1e12
+            grad["roofline_forward_level0"] = {
+                "bound": "alu", "kernel": "k_corr0_f32 (forward level 0)", "achieved_lower_bound": ach,
+                "peak": fpeak, "unit": "TFLOP/s", "frac_lower_bound": ach / fpeak,
+                "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
+                "algorithmic_flop_per_pair": flop}
         # the dominant kernel of the headline path gets the roofline object
         dominant = corr if r["stages"]["level0_correlation"] >= r["stages"]["levels"] else lev
         cpu = None
