@@ -12,9 +12,10 @@
 // 2,3) so that one packed FP32x2 fma (__ffma2_rn) updates two patches: the
 // instruction issue rate, not the FMA pipes, limited the scalar version.
 // The image-2 descriptor halo (20 rows x 35 columns x 9 channels, one float
-// each: a lane's 32-bit loads fall in distinct banks) and the 32 patch
-// vectors, as [(dx*9+c)*4+dy][patch], are staged in shared memory by
-// asynchronous 4-byte copies (zero-filled outside the images).
+// each: a lane's 32-bit loads fall in distinct banks; each value is paired
+// with itself in registers for the packed fmas) and the 32 patch vectors, as
+// [(dx*9+c)*4+dy][patch], are staged in shared memory by asynchronous 4-byte
+// copies (zero-filled outside the images).
 //
 // Summation order (identical to the FP32 reference): per output,
 // acc = fma(a, b, acc) over dx = 0..3, then channel c = 0..8, then dy = 0..3,
@@ -24,11 +25,13 @@
 // feed all 4 dy offsets of all 17 rows.
 //
 // Epilogue: x1/16, out-of-domain positions masked to -inf, 3x3/2 max-pool
-// with the first strict maximum in scan order (row-major in the window).
-// Each lane first reduces its own column over the three rows of every
-// pooled row (maximum and its first row); the windows then combine three
-// neighbouring columns, odd lanes 2k+1 for pooled row i and even lanes 2k
-// for row i+1 at once, so 30 of 32 lanes produce an output.  Maxima and
+// with the first strict maximum in scan order (row-major in the window),
+// i.e. (no NaN occurs) the smallest scan index among the positions equal to
+// the maximum.  Each lane first reduces its own column over the three rows
+// of every pooled row (maximum and the first row reaching it); the windows
+// then combine three neighbouring columns (the smallest 3 * row + column
+// among the columns reaching the maximum), odd lanes 2k+1 for pooled row i
+// and even lanes 2k for row i+1 at once, so 30 of 32 lanes produce an output.  Maxima and
 // codes are staged in shared memory, then 240 threads raise them to lambda
 // and store rows of 15 consecutive outputs.
 #include "dm_internal.cuh"
