@@ -159,7 +159,8 @@ def oracle_sample_rate(pair, target_s: float = 12.0, max_patches: int | None = N
     per_pair = t * n0 / k + t_desc
     desc = (f"FP32 oracle level-0 correlation+pooling of {k} of {n0} atomic patches of one "
             f"{W1}x{H1} pair ({t:.1f} s), scaled to all patches, plus both descriptors ({t_desc:.2f} s); "
-            f"pyramid levels >= 1 and backtracking not timed (<5% of the oracle's work)")
+            f"pyramid levels >= 1 and backtracking not timed (about 5% of the oracle's work: at 512x224 "
+            f"its backtracking took 1.6 s against 31.9 s for its whole pyramid)")
     return 1.0 / per_pair, cores, desc, k, n0
 
 
