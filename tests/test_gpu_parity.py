@@ -260,3 +260,32 @@ def test_identity_and_translation_on_gpu(torch_cuda, ctx):
     np.testing.assert_array_equal(got[:, 0], got[:, 2])
     np.testing.assert_array_equal(got[:, 1], got[:, 3])
     assert np.abs(got[:, 4] - 5.0).max() < 1e-5
+
+
+@pytest.mark.parametrize("dims,seed", [((64, 48, 64, 48), 11), ((41, 23, 53, 35), 12), ((130, 70, 130, 70), 13)])
+def test_tie_heavy_fields_bit_exact(torch_cuda, ctx, oracle_mod, dims, seed):
+    """Descriptor fields whose entries take three values (0, 1/4, 1/2): the
+    correlations are exact small dyadic sums, so the 3x3 maxima of every level
+    tie often and the first-maximum rule in scan order (and the backtracking's
+    tie rules) decide; the pyramid (values and argmax codes), the merged-tuple
+    counts and the matches must still equal the FP32 oracle bit for bit."""
+    W1, H1, W2, H2 = dims
+    rng = np.random.default_rng(seed)
+    d1 = (rng.integers(0, 3, size=(H1, W1, 9)) * 0.25).astype(np.float32)
+    d2 = (rng.integers(0, 3, size=(H2, W2, 9)) * 0.25).astype(np.float32)
+    pyr = oracle_mod.pyramid(d1, d2, "f32")
+    ties = sum(int(np.sum(pyr.pooled[l] == np.roll(pyr.pooled[l], 1, axis=2))) for l in range(pyr.geom.L))
+    assert ties > 0
+    h, ws, levels = _gpu_pyramid(torch_cuda, ctx, d1, d2)
+    try:
+        _compare_pyramids(pyr, levels)
+        bt = oracle_mod.backtrack(pyr)
+        want = oracle_mod.reciprocal(pyr, bt)
+        got, n, status, reached = _gpu_backtrack(torch_cuda, ctx, h, W1, H1, W2, H2)
+        assert status == 0
+        assert n == len(want)
+        np.testing.assert_array_equal(got, want)
+        assert reached[1:] == bt.reached[1:].tolist()
+    finally:
+        from paper_1506_07656_gb300 import dm
+        dm.dm_pyramid_free(h)
